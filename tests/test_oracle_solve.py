@@ -1,0 +1,304 @@
+"""Pins of the oracle's ant walk and full colony against hand-worked steps, textbook shortest-path
+routines, brute force, exact identities and degenerate cases. No GPU needed."""
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2010_14244_gb300 import workloads as W
+from tests import netbuild as NB
+from tests.test_oracle_primitives import _exact_weights
+
+Q = W.Query
+
+
+def _star(signal_on_1=False, veh01=0, far1=False):
+    """Node 0 -> {1, 2, 3} -> 4. Roads at 45 km/h; lengths 512 / 1024 / 256 dm give free-flow
+    times of exactly 4096 / 8192 / 2048 ms."""
+    roads = [(0, 1, 512, 45, 3, 0), (0, 2, 1024, 45, 3, 0), (0, 3, 256, 45, 3, 0),
+             (1, 4, 512, 45, 3, 1), (2, 4, 512, 45, 3, 0), (3, 4, 512, 45, 3, 0)]
+    coords = [(0, 0)] * 5
+    if far1:
+        coords[1] = (3000, 4000)  # 500 m from the destination; 8 ms/dm at 45 km/h -> h = 40000 ms
+    signals = {1: (10_000, 0, [4000, 6000])} if signal_on_1 else None
+    vehicles = {(0, 1): veh01} if veh01 else None
+    return NB.build(5, roads, coords, signals, vehicles)
+
+
+def test_hand_worked_first_step_kat_draw(orc):
+    """Three candidates with scores 2^-12, 2^-13, 2^-11 (alpha=beta=1, tau=1.0, h=0, no signals):
+    weights 2^29, 2^28, 2^30; S = 7*2^28. The draw for (seed 0, it 0, ant 0, step 0) is the first
+    Philox known-answer vector, 0xe169c58d6627e8d5 / 2^64 = 0.8805..., so r = 6.16 * 2^28 lies in
+    [3*2^28, 7*2^28): the third road (0 -> 3). Then 3 -> 4 is the only choice: T = 2048 + 4096."""
+    net, sig, veh = _star()
+    onet = orc.Net(net, sig, veh)
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+    w = orc.walk_one(onet, orc.Params(), Q(0, 4, 1, 1, 1.0, 1.0, 0.1, 0), tau, it=0, ant=0)
+    assert w["status"] == 0
+    assert [int(net.col[e]) for e in w["route_edges"]] == [3, 4]
+    assert w["T"] == 6144 and w["W"] == 0 and w["steps"] == 2
+
+
+def _expected_pick(orc, weights, seed, it, ant, step):
+    o = orc.philox([it, ant, step, 0], [seed & 0xFFFFFFFF, seed >> 32])
+    rnd = o[0] | (o[1] << 32)
+    r = (rnd * sum(weights)) >> 64
+    acc = 0
+    for i, w in enumerate(weights):
+        acc += w
+        if acc > r:
+            return i
+
+
+def test_hand_worked_step_with_signal_queue_and_heuristic(orc):
+    """Road 0->1 carries 3 vehicles: cap = 3*512/75 = 20, tt = 4096*20/17 = 4818 ms. Node 1 is
+    signalised (cycle 10 s, phase 0 green [0, 4 s) from offset 0; phase order stays [0, 1] since
+    Q_0 = 3 is the longest queue); arrival at 4818 ms waits 10000 - 4818 = 5182 ms, plus queue delay
+    3*2000/3 = 2000 ms. Node 1 lies 500 m from the destination: h = 5000 dm * 8 ms/dm = 40000 ms.
+    So c = 4818 + 7182 + 40000 = 52000 for road 0->1, 8192 for 0->2, 2048 for 0->3."""
+    net, sig, veh = _star(signal_on_1=True, veh01=3, far1=True)
+    onet = orc.Net(net, sig, veh)
+    prep = orc.prepare(onet, orc.Params(), 4)
+    e01 = NB.edge_id(net, 0, 1)
+    assert prep["tt"][e01] == 4818 and prep["qd"][e01] == 2000 and prep["h"][1] == 40000
+    f32 = np.float32
+    scores = [f32(1) / f32(52000), f32(1) / f32(8192), f32(1) / f32(2048)]
+    weights = _exact_weights(scores)
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+    heads = []
+    for ant in range(300):
+        w = orc.walk_one(onet, orc.Params(), Q(0, 4, 300, 1, 1.0, 1.0, 0.1, 77), tau, it=0, ant=ant)
+        pick = _expected_pick(orc, weights, 77, 0, ant, 0)
+        assert int(net.col[w["route_edges"][0]]) == [1, 2, 3][pick]
+        heads.append(pick)
+        if pick == 0:  # went through the signal: T = 52000 - 40000 + road 1->4 (4096 ms)
+            assert w["T"] == 4818 + 7182 + 4096 and w["W"] == 7182
+    assert set(heads) == {0, 1, 2}
+
+
+def test_first_step_frequencies_chi_square(orc):
+    """Scores 2^-12, 2^-13, 2^-11 -> probabilities 2/7, 1/7, 4/7 over Philox draws; and alpha=beta=0
+    gives a uniform choice."""
+    from scipy.stats import chisquare
+
+    net, sig, veh = _star()
+    onet = orc.Net(net, sig, veh)
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+    for a, b, probs in [(1.0, 1.0, [2 / 7, 1 / 7, 4 / 7]), (0.0, 0.0, [1 / 3] * 3)]:
+        counts = [0, 0, 0]
+        n = 6000
+        for ant in range(n):
+            w = orc.walk_one(onet, orc.Params(), Q(0, 4, n, 1, a, b, 0.1, 5), tau, it=0, ant=ant)
+            counts[int(net.col[w["route_edges"][0]]) - 1] += 1
+        assert chisquare(counts, [n * p for p in probs]).pvalue > 1e-4, counts
+
+
+@pytest.mark.parametrize("gseed", range(6))
+def test_free_flow_best_equals_dijkstra_and_brute_force(orc, gseed):
+    """No vehicles, no signals: the best colony route equals the shortest path (Dijkstra) and the
+    minimum over all enumerated simple paths on tiny graphs."""
+    rng = np.random.Generator(np.random.PCG64(100 + gseed))
+    net, sig = W.random_small(7, 10, rng)
+    veh = np.zeros(net.n_edges, np.uint32)
+    onet = orc.Net(net, sig, veh)
+    src, dst = 0, 6
+    timing = NB.Timing(orc, onet, net, sig, dst)
+    opt = NB.td_dijkstra(net, timing, src, dst)
+    assert opt == NB.brute_force_min(net, timing, src, dst)
+    r = orc.solve(onet, orc.Params(), Q(src, dst, 64, 30, 1.0, 2.0, 0.1, gseed))
+    assert r["status"] == 0
+    assert r["travel_ms"] == opt and r["wait_ms"] == 0
+
+
+@pytest.mark.parametrize("gseed", range(6))
+def test_signalised_best_equals_td_dijkstra_and_brute_force(orc, gseed):
+    """Signals everywhere and random vehicles: waits are FIFO, so time-dependent Dijkstra is exact;
+    the colony's best equals it and the brute-force minimum over simple paths."""
+    rng = np.random.Generator(np.random.PCG64(200 + gseed))
+    net, sig = W.random_small(7, 11, rng, signalised_frac=1.0)
+    veh = rng.integers(0, 12, net.n_edges).astype(np.uint32)
+    onet = orc.Net(net, sig, veh)
+    src, dst = 1, 5
+    timing = NB.Timing(orc, onet, net, sig, dst)
+    opt = NB.td_dijkstra(net, timing, src, dst)
+    assert opt == NB.brute_force_min(net, timing, src, dst)
+    r = orc.solve(onet, orc.Params(), Q(src, dst, 64, 40, 1.0, 2.0, 0.1, gseed))
+    assert r["status"] == 0
+    assert r["travel_ms"] == opt
+
+
+def _check_route(orc, net, sig, onet, res, q, params=None):
+    route = [int(v) for v in res["route"]]
+    assert route[0] == q.src and route[-1] == q.dst
+    assert len(set(route)) == len(route)
+    timing = NB.Timing(orc, onet, net, sig, q.dst, params)
+    t = Wt = 0
+    for u, v in zip(route[:-1], route[1:]):
+        e = NB.edge_id(net, u, v)
+        t, w = timing.after(e, t)
+        Wt += w
+    assert t == res["travel_ms"] and Wt == res["wait_ms"] and Wt <= t
+
+
+def test_grid10_route_validity_and_recomputed_times(orc):
+    wl = W.grid10()
+    onet = orc.Net.from_workload(wl)
+    q = wl.queries[0]
+    r = orc.solve(onet, orc.Params(), q)
+    assert r["status"] == 0
+    _check_route(orc, wl.net, wl.signals, onet, r, q)
+    # departure clock shifts signal phases but the route stays valid and timed consistently
+    p = orc.Params(t_dep_ms=123_457)
+    r2 = orc.solve(onet, p, q)
+    _check_route(orc, wl.net, wl.signals, onet, r2, q, p)
+
+
+def _deposit(h_src, T):
+    return (max(h_src, 1) << 32) // T
+
+
+def test_pheromone_conservation_identity(orc):
+    """sum tau' = sum (tau - floor(tau*rho_fix/2^32)) + sum over successful ants of |route| * delta."""
+    wl = W.grid10(n_ants=32, n_iter=1)
+    onet = orc.Net.from_workload(wl)
+    q = wl.queries[0]
+    h_src = int(orc.prepare(onet, orc.Params(), q.dst)["h"][q.src])
+    rfix = orc.rho_fix(q.rho)
+    r1 = orc.solve(onet, orc.Params(), q, want_log=True)
+    log = r1["log"][0]
+    dep = sum(int(s) * _deposit(h_src, int(T)) for st, s, T, _ in log if st == 0)
+    assert dep > 0
+    E = wl.net.n_edges
+    assert int(r1["tau"].sum()) == E * orc.evaporate(2**32, rfix) + dep
+    assert r1["ant_steps"] == int(log[:, 1].sum())
+    # second iteration, starting from the first iteration's table (deterministic prefix)
+    q2 = W.Query(q.src, q.dst, q.n_ants, 2, q.alpha, q.beta, q.rho, q.seed)
+    r2 = orc.solve(onet, orc.Params(), q2, want_log=True)
+    assert (r2["log"][0] == log).all()
+    dep2 = sum(int(s) * _deposit(h_src, int(T)) for st, s, T, _ in r2["log"][1] if st == 0)
+    assert int(r2["tau"].sum()) == sum(orc.evaporate(int(t), rfix) for t in r1["tau"]) + dep2
+    assert int(r2["tau"].min()) >= 1
+
+
+def _star_solve(orc):
+    net, sig, veh = _star()
+    return orc.solve(orc.Net(net, sig, veh), orc.Params(), Q(0, 4, 16, 4, 1.0, 2.0, 0.1, 3), want_log=True)
+
+
+def _grid_solve(orc):
+    wl = W.grid10(n_ants=16, n_iter=6)
+    return orc.solve(orc.Net.from_workload(wl), orc.Params(), wl.queries[0], want_log=True)
+
+
+@pytest.mark.parametrize("case", ["star", "grid10"])
+def test_best_is_min_T_then_lowest_iteration_ant(orc, case):
+    """The reported best is the minimum T; among equal T (many on the star graph), the lowest
+    (iteration, ant)."""
+    r = _star_solve(orc) if case == "star" else _grid_solve(orc)
+    log = r["log"]
+    ok = log[:, :, 0] == 0
+    Ts = np.where(ok, log[:, :, 2].astype(np.int64), np.iinfo(np.int64).max)
+    tmin = Ts.min()
+    it, ant = [int(v) for v in np.argwhere(Ts == tmin)[0]]  # row-major: lowest (it, ant)
+    assert r["travel_ms"] == tmin and (r["best_iter"], r["best_ant"]) == (it, ant)
+    assert r["wait_ms"] == log[it, ant, 3] and r["route_len"] == log[it, ant, 1] + 1
+    assert r["n_success"] == int(ok.sum())
+    if case == "star":
+        assert (Ts == tmin).sum() > 10
+
+
+def test_src_equals_dst(orc):
+    wl = W.grid10()
+    onet = orc.Net.from_workload(wl)
+    r = orc.solve(onet, orc.Params(), Q(5, 5, 8, 3, 1.0, 2.0, 0.1, 0))
+    assert r["status"] == 0 and list(r["route"]) == [5] and r["travel_ms"] == 0 and r["ant_steps"] == 0
+    assert (r["tau"] == 2**32).all()
+
+
+def test_unreachable_destination(orc):
+    net, sig, veh = NB.build(4, [(0, 1, 1000, 50), (1, 2, 1000, 50)])  # node 3 isolated
+    r = orc.solve(orc.Net(net, sig, veh), orc.Params(), Q(0, 3, 8, 4, 1.0, 2.0, 0.1, 0), want_log=True)
+    assert r["status"] == orc.ERR_NO_ROUTE
+    assert set(np.unique(r["log"][:, :, 0])) == {orc.ANT_DEAD_END}
+
+
+def test_step_cap(orc):
+    roads = [(i, i + 1, 1000, 50) for i in range(6)]
+    net, sig, veh = NB.build(7, roads)
+    onet = orc.Net(net, sig, veh)
+    r = orc.solve(onet, orc.Params(max_steps=5), Q(0, 6, 4, 2, 1.0, 2.0, 0.1, 0), want_log=True)
+    assert r["status"] == orc.ERR_NO_ROUTE
+    assert (r["log"][:, :, 0] == orc.ANT_STEP_CAP).all() and (r["log"][:, :, 1] == 5).all()
+    r = orc.solve(onet, orc.Params(max_steps=6), Q(0, 6, 4, 2, 1.0, 2.0, 0.1, 0))
+    assert r["status"] == 0 and r["route_len"] == 7
+
+
+def test_time_cap(orc):
+    """Roads whose free-flow time clamps at 2^26 ms: 16 of them take exactly 2^30 ms (allowed),
+    the 17th exceeds the 2^30 ms cap and the ant fails."""
+    roads = [(i, i + 1, 10**9, 1) for i in range(17)]
+    net, sig, veh = NB.build(18, roads)
+    onet = orc.Net(net, sig, veh)
+    r = orc.solve(onet, orc.Params(), Q(0, 16, 2, 1, 1.0, 2.0, 0.1, 0))
+    assert r["status"] == 0 and r["travel_ms"] == 2**30
+    r = orc.solve(onet, orc.Params(), Q(0, 17, 2, 1, 1.0, 2.0, 0.1, 0), want_log=True)
+    assert r["status"] == orc.ERR_NO_ROUTE and (r["log"][:, :, 0] == orc.ANT_TIME_CAP).all()
+
+
+def test_congestion_threshold_mask(orc):
+    """Fig. 3's threshold: a road over the occupancy threshold is avoided unless all are over."""
+    # 0 -> 1 (congested: 30 of cap 40), 0 -> 2 (empty); both lead to 3
+    roads = [(0, 1, 1000, 50), (0, 2, 1000, 50), (1, 3, 1000, 50), (2, 3, 1000, 50)]
+    net, sig, veh = NB.build(4, roads, vehicles={(0, 1): 30})
+    onet = orc.Net(net, sig, veh)
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+    p = orc.Params(thr_permille=500)  # over half full counts as congested
+    firsts = {int(net.col[orc.walk_one(onet, p, Q(0, 3, 64, 1, 0.0, 0.0, 0.1, 1), tau, 0, k)["route_edges"][0]])
+              for k in range(64)}
+    assert firsts == {2}
+    # both congested -> both allowed again
+    net, sig, veh = NB.build(4, roads, vehicles={(0, 1): 30, (0, 2): 35})
+    onet = orc.Net(net, sig, veh)
+    firsts = {int(net.col[orc.walk_one(onet, p, Q(0, 3, 64, 1, 0.0, 0.0, 0.1, 1), tau, 0, k)["route_edges"][0]])
+              for k in range(64)}
+    assert firsts == {1, 2}
+
+
+def test_invalid_and_unsupported_queries(orc):
+    wl = W.grid10()
+    onet = orc.Net.from_workload(wl)
+    assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, 1.5, 2.0, 0.1, 0))["status"] == orc.ERR_UNSUPPORTED
+    assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, 1.0, 2.0, 1.0, 0))["status"] == orc.ERR_INVALID
+    assert orc.solve(onet, orc.Params(), Q(0, 100, 8, 2, 1.0, 2.0, 0.1, 0))["status"] == orc.ERR_INVALID
+    assert orc.solve(onet, orc.Params(), Q(0, 99, 0, 2, 1.0, 2.0, 0.1, 0))["status"] == orc.ERR_INVALID
+    r = orc.solve(onet, orc.Params(), wl.queries[0], route_cap=3)
+    assert r["status"] == orc.ERR_BUFFER and r["route_len"] > 3
+
+
+def test_queue_preempt_on_network(orc):
+    """Per-phase queues add up the vehicles on each phase's approaches; a queue over 3/4 of the
+    approach storage is preempted first."""
+    # node 2 signalised with 3 phases; approaches 0->2 (phase 0), 1->2 (phase 1), 3->2 (phase 2)
+    roads = [(0, 2, 1000, 50, 3, 0), (1, 2, 1000, 50, 3, 1), (3, 2, 1000, 50, 3, 2)]
+    sigs = {2: (90_000, 0, [30_000, 30_000, 30_000])}
+    # capacities 40 each -> threshold 30. queues 5, 0, 12: no preemption -> longest (2) first,
+    # then non-empty in default order (0), then empty (1)
+    net, sig, veh = NB.build(4, roads, signals=sigs, vehicles={(0, 2): 5, (3, 2): 12}, bidirectional=False)
+    sig.edge_phase[:] = net.orient
+    assert list(orc.queue_preempt(orc.Net(net, sig, veh))[2][:3]) == [2, 0, 1]
+    # queue 31 on phase 1 exceeds its threshold 30
+    net, sig, veh = NB.build(4, roads, signals=sigs, vehicles={(0, 2): 5, (1, 2): 31, (3, 2): 12},
+                             bidirectional=False)
+    assert list(orc.queue_preempt(orc.Net(net, sig, veh))[2][:3]) == [1, 0, 2]
+    # red accumulator above T_max (= cycle) on phase 0 with no queue over threshold
+    red = np.zeros((4, 8), np.uint32)
+    red[2, 0] = 90_001
+    net, sig, veh = NB.build(4, roads, signals=sigs, vehicles={(0, 2): 5, (3, 2): 12}, bidirectional=False)
+    assert list(orc.queue_preempt(orc.Net(net, sig, veh, red))[2][:3]) == [0, 2, 1]
+    # queue 25 on phase 0 lies between half (20) and three quarters (30) of its storage: no
+    # preemption by queue, so the starved phase 2 goes first
+    red[2, 0] = 0
+    red[2, 2] = 90_001
+    net, sig, veh = NB.build(4, roads, signals=sigs, vehicles={(0, 2): 25, (3, 2): 12}, bidirectional=False)
+    assert list(orc.queue_preempt(orc.Net(net, sig, veh, red))[2][:3]) == [2, 0, 1]
