@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the MACO-P route colony on GB300: ant-steps/s and routed queries/s.
+
+Workload (one "step"): the 64x64 perturbed-grid road network (4096 intersections, 14,916 directed roads,
+2-phase signals at every node, 2000 Zipf(1.2) vehicles), 16 origin-destination colonies x 1024 ants x 200
+iterations, alpha=1, beta=2, rho=0.1, run as one device job (construction, evaporation+deposit, best
+tracking and the queue/preemption update every iteration). Every launch starts from fresh pheromone, so
+each step repeats identical work with identical, oracle-checked results.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N]        # the CUDA library
+  python bench.py --impl reference ...                       # the CPU oracle on the host cores
+
+Under torchrun each rank runs an independent replica (colonies are independent problems: weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6772.9
+# DRAM bytes per construction launch from the ncu capture summarised in
+# profiles/construct_grid64.md (None until a capture of the current kernel exists).
+CONSTRUCT_TRAFFIC_BYTES = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gmacop", choices=["gmacop", "reference"])
+    p.add_argument("--mode", type=int, default=0, help="0 auto, 1 iterative, 2 persistent")
+    p.add_argument("--lanes", type=int, default=0, help="lanes per ant (0 = autotune)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload():
+    from paper_2010_14244_gb300 import workloads
+
+    return workloads.grid64()
+
+
+def workload_config(wl):
+    q = wl.queries[0]
+    return {"workload": f"grid64: 64x64 perturbed grid, {wl.net.n_nodes} nodes, {wl.net.n_edges} directed roads, "
+                        f"{len(wl.queries)} OD colonies x {q.n_ants} ants x {q.n_iter} iterations",
+            "nodes": wl.net.n_nodes, "roads": wl.net.n_edges, "colonies": len(wl.queries), "ants": q.n_ants,
+            "iterations": q.n_iter, "alpha": q.alpha, "beta": q.beta, "rho": q.rho}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------ CPU oracle
+_WL = None
+
+
+def _pool_init():
+    global _WL
+    _WL = workload()
+
+
+def _pool_solve(qi):
+    from oracle import oracle as orc
+
+    r = orc.solve_workload_query(_WL, qi, want_tau=False)
+    return r["ant_steps"], r["status"]
+
+
+def oracle_run(pool, n_queries):
+    t0 = time.perf_counter()
+    out = pool.map(_pool_solve, range(n_queries))
+    dt = time.perf_counter() - t0
+    return sum(s for s, _ in out), dt
+
+
+def make_pool():
+    import multiprocessing as mp
+
+    cores = len(os.sched_getaffinity(0))
+    return mp.get_context("spawn").Pool(min(cores, 16), initializer=_pool_init), min(cores, 16)
+
+
+def cpu_baseline_line(n_queries):
+    pool, cores = make_pool()
+    try:
+        steps, dt = oracle_run(pool, n_queries)
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": steps / dt, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"all {n_queries} colonies of the workload (full size), one colony per process, "
+                      f"{cores} processes, {dt:.1f} s wall",
+            "queries_per_s": n_queries / dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = workload()
+    nq = len(wl.queries)
+    pool, cores = make_pool()
+    try:
+        for _ in range(args.warmup):
+            oracle_run(pool, nq)
+        tot_steps, tot_t = 0, 0.0
+        for _ in range(args.steps):
+            s, dt = oracle_run(pool, nq)
+            tot_steps += s
+            tot_t += dt
+    finally:
+        pool.close()
+        pool.join()
+    v = tot_steps / tot_t
+    line = {"impl": "reference", "metric": "ant-steps/s", "value": v, "unit": "ant-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+            "data": "synthetic", "config": workload_config(wl),
+            "queries_per_s": nq * args.steps / tot_t,
+            "cpu_baseline": {"value": v, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: all {nq} colonies at full size over {cores} processes"},
+            "e2e": {"value": v, "unit": "ant-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ GPU
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2010_14244_gb300 import gmacop
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    wl = workload()
+    nq = len(wl.queries)
+    ctx = gmacop.Context(local_rank, stream=stream)
+    ctx.load_workload(wl)
+    ctx.set_params(flags=gmacop.FLAG_KERNEL_TIMING, mode=args.mode, lanes_per_ant=args.lanes)
+    ctx.stage(wl.queries)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.launch()
+        stream.synchronize()
+        res = ctx.collect()
+        assert all(r["status"] == gmacop.OK for r in res), [r["status"] for r in res]
+        steps_per_job = sum(r["ant_steps"] for r in res)
+        launches = ctx.launch_count()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        times, kt = [], dict(construct=0.0, evaporate=0.0, best=0.0, queue=0.0, job=0.0)
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (not timed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.launch()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for k, v in ctx.kernel_times().items():
+                kt[k] += v
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop()
+        res2 = ctx.collect()
+        assert [r["travel_ms"] for r in res2] == [r["travel_ms"] for r in res]
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the public API: densities and queries from pinned host memory, results back
+    e2e = None
+    if not args.no_e2e:
+        veh = torch.from_numpy(wl.vehicles.astype(np.uint32)).pin_memory()
+        veh_np = veh.numpy()
+        e2e_t, e2e_steps, d2h = 0.0, 0, 0
+        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes)
+        with torch.cuda.stream(stream):
+            ctx.set_densities(veh_np)
+            ctx.solve_batch(wl.queries)  # warm (captures the job graph)
+            for _ in range(args.steps):
+                flush.zero_()
+                stream.synchronize()
+                t0 = time.perf_counter()
+                ctx.set_densities(veh_np)
+                out = ctx.solve_batch(wl.queries)
+                e2e_t += time.perf_counter() - t0
+                e2e_steps += sum(r["ant_steps"] for r in out)
+                d2h = nq * 48 + sum(4 * r["route_len"] for r in out)
+        e2e = {"value": e2e_steps / e2e_t, "unit": "ant-steps/s",
+               "h2d_bytes_per_step": int(wl.net.n_edges * 4 + nq * 40), "d2h_bytes_per_step": int(d2h),
+               "queries_per_s": nq * args.steps / e2e_t}
+    ctx.close()
+    if rank != 0:
+        return
+    K = args.steps
+    value = world * steps_per_job * K / (total_ms / 1e3)
+    n, e = wl.net.n_nodes, wl.net.n_edges
+    d = e / n
+    bytes_per_step = 12 + 56 * d  # algorithmic bytes per ant-step of the construction kernel
+    construct_launches = wl.queries[0].n_iter
+    achieved = bytes_per_step * steps_per_job * K / (kt["construct"] / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "ant-steps/s", "value": value, "unit": "ant-steps/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+        "config": dict(workload_config(wl), l2="flushed between timed steps (256 MB write)",
+                       mode=args.mode, lanes_per_ant=args.lanes or "auto"),
+        "queries_per_s": world * nq * K / (total_ms / 1e3),
+        "ant_steps_per_step": steps_per_job,
+        "kernel_ms_per_step": {k: v / K for k, v in kt.items()},
+        "roofline": {"bound": "hbm", "kernel": "construct", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": CONSTRUCT_TRAFFIC_BYTES,
+                     "algorithmic_bytes_per_launch": bytes_per_step * steps_per_job / construct_launches,
+                     "avg_launch_ms": kt["construct"] / (K * construct_launches)},
+        "gpu_launches": launches * K,
+        "clocks": clocks,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(nq)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+
+        backend = "nccl" if args.impl == "gmacop" and torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * gmacop.h -- C ABI of the GB300 (sm_103a) MACO-P route colony library, libgmacop.so.
+ *
+ * The method is GMACO-P (Jindal & Bedi, "GMACO-P: GPU assisted Preemptive MACO algorithm for enabling
+ * Smart Transportation"): ants build origin-to-destination routes over a road graph by choosing the next
+ * road from pheromone and a congestion/signal-aware travel-time heuristic (Sec. 4.1, Fig. 3), successful
+ * ants deposit pheromone and all roads evaporate (Fig. 3 last two lines; Algorithm 2 steps 9-10), and each
+ * signalised intersection reorders its phases by the preemptive rule (Fig. 3 signal block; Algorithm 2
+ * steps 7-8). Algorithm 1 (allocate, copy in, launch, copy out, free) is the host driver this API replaces
+ * with persistent device state: the graph, signals and densities stay resident between calls.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GMP_OK (0) or a GMP_ERR_* code; gmp_strerror() names it, gmp_last_error() gives the
+ *     context's last detailed message.
+ *   - Host pointers (const T*) are read during the call only; the library copies what it keeps. Device
+ *     pointers are named d_* and must be device memory of the context's GPU.
+ *   - Units: lengths and coordinates in decimetres, speeds in km/h, times in milliseconds, pheromone in
+ *     unsigned Q32.32 fixed point (2^32 == 1.0).
+ *   - One context is one GPU + one road graph. A context is not thread-safe: serialise calls on it.
+ *   - Work is issued on the context's stream (gmp_create / gmp_set_stream). Calls that return host data
+ *     synchronise that stream; *_async calls do not.
+ */
+#ifndef GMACOP_H
+#define GMACOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMP_OK 0
+#define GMP_ERR_INVALID_ARG 1 /* argument out of range or inconsistent graph/signal data */
+#define GMP_ERR_NO_ROUTE 2    /* no ant reached the destination in any iteration */
+#define GMP_ERR_OOM 3         /* device allocation failed or the context's memory budget is exceeded */
+#define GMP_ERR_CUDA 4        /* a CUDA runtime call failed (see gmp_last_error) */
+#define GMP_ERR_TIMEOUT 5     /* a bounded device-side wait expired (persistent launch) */
+#define GMP_ERR_UNSUPPORTED 6 /* non-integer alpha/beta, more than 8 phases, degree beyond the kernel limit */
+#define GMP_ERR_BUFFER 7      /* caller buffer too small; the required size is reported */
+#define GMP_ERR_STATE 8       /* call out of order (e.g. solve before gmp_load_graph) */
+
+#define GMP_MAX_PHASES 8
+#define GMP_THRESHOLD_OFF 0xFFFFFFFFu
+#define GMP_FLAG_RANDOM_TAU 1u /* initial pheromone 0.5 + u/2^32, u = Philox(road, 0, 0, 1) word 0 */
+#define GMP_FLAG_ANT_LOG 2u    /* keep a per-(iteration, ant) log {status, steps, T, W} for inspection */
+
+#define GMP_MODE_AUTO 0u       /* library picks */
+#define GMP_MODE_ITERATIVE 1u  /* one kernel sequence per iteration, whole batch, CUDA-graph replay */
+#define GMP_MODE_PERSISTENT 2u /* one persistent launch working through (query, iteration) items */
+
+typedef struct gmp_ctx gmp_ctx;
+
+/* Tunables of the colony (Fig. 3 leaves all of them unstated). Zero means "default" where noted. */
+typedef struct {
+    uint32_t max_steps;     /* roads per ant before it gives up; 0 = min(N-1, 4096) */
+    uint32_t h_sat_ms;      /* saturation headway per lane for queue delays; 0 = 2000 ms */
+    uint32_t thr_permille;  /* Fig. 3 congestion threshold: a road with vehicles*1000 > thr*capacity is
+                               avoided unless every candidate is; GMP_THRESHOLD_OFF disables it */
+    uint32_t flags;         /* GMP_FLAG_* */
+    uint32_t t_dep_ms;      /* departure clock for signal phases, < 2^30 */
+    uint32_t lanes_per_ant; /* lanes of a warp that evaluate one ant's candidates: 0 (autotune), 4, 8, 16, 32 */
+    uint32_t mode;          /* GMP_MODE_* */
+    uint32_t reserved;
+} gmp_params;
+
+/* One origin-destination colony. alpha, beta: integers in [0, 8]; rho in [0, 1). */
+typedef struct {
+    uint32_t src, dst, n_ants, n_iter;
+    float alpha, beta, rho;
+    uint32_t reserved;
+    uint64_t seed;
+} gmp_query;
+
+/* Result of one colony. `route` is a caller-owned buffer of `route_cap` node ids. */
+typedef struct {
+    uint32_t *route;    /* best route as node ids, src first, dst last */
+    uint32_t route_cap; /* capacity of `route` in entries */
+    uint32_t route_len; /* nodes in the best route (required size if status == GMP_ERR_BUFFER) */
+    uint64_t travel_ms; /* T of the best route: min T over all ants, ties to lowest (iteration, ant) */
+    uint64_t wait_ms;   /* signal waits + queue delays along that route */
+    uint64_t ant_steps; /* roads taken by all ants of all iterations, failed ants included */
+    uint64_t n_success; /* ant walks that reached the destination */
+    uint32_t best_iter, best_ant;
+    int32_t status;     /* GMP_OK, GMP_ERR_NO_ROUTE or GMP_ERR_BUFFER */
+    uint32_t reserved;
+} gmp_result;
+
+/* Create a context on CUDA device `device`. mem_budget_bytes bounds the device memory the context may
+ * hold (0 = no bound). cuda_stream is a cudaStream_t to issue work on (NULL = a stream the context owns).
+ * Errors: INVALID_ARG (bad device), CUDA. */
+int gmp_create(gmp_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_stream);
+
+/* Release every device allocation of the context. NULL is ignored. */
+void gmp_destroy(gmp_ctx *ctx);
+
+/* Human-readable name of a return code. Static storage. */
+const char *gmp_strerror(int code);
+
+/* Last detailed error message of the context (static storage inside the context). */
+const char *gmp_last_error(const gmp_ctx *ctx);
+
+/* Issue subsequent work on cuda_stream (NULL = the context's own stream). */
+int gmp_set_stream(gmp_ctx *ctx, void *cuda_stream);
+
+/* Road graph G(N, E) (Fig. 3 "G(N,E) = graph"; Sec. 5: roads with lanes) in CSR form: the roads leaving
+ * node u are row_ptr[u] .. row_ptr[u+1]-1, in the order that breaks ties between equal choices.
+ * col[e]: head node; length_dm[e] >= 1; speed_kmh[e] >= 1; lanes[e] >= 1; x_dm, y_dm: node coordinates,
+ * |x|, |y| <= 2^27. Derives free-flow times and jam capacities on the device. Replaces any previous graph
+ * and resets signals (none) and densities (zero). Errors: INVALID_ARG, OOM, CUDA. */
+int gmp_load_graph(gmp_ctx *ctx, uint32_t n_nodes, uint32_t n_edges, const uint32_t *row_ptr, const uint32_t *col,
+                   const uint32_t *length_dm, const uint16_t *speed_kmh, const uint8_t *lanes, const int32_t *x_dm,
+                   const int32_t *y_dm);
+
+/* Fixed-time signal programmes (Fig. 3 "L: Light, P: Phase"; Algorithm 1 arguments traffic_light, phases).
+ * Per node v: n_phases[v] in 0..8 (0 = unsignalised), cycle_ms[v] in 1..2^24, offset_ms[v] < cycle,
+ * green_ms[v*8 + p] >= 1 for p < n_phases with sum == cycle. edge_phase[e]: approach phase of road e at
+ * its head (< n_phases of the head when signalised). Resets the red-time accumulators to 0 and recomputes
+ * the phase order. Errors: INVALID_ARG, UNSUPPORTED (> 8 phases), STATE (no graph), CUDA. */
+int gmp_set_signals(gmp_ctx *ctx, const uint8_t *n_phases, const uint32_t *cycle_ms, const uint32_t *offset_ms,
+                    const uint32_t *green_ms, const uint8_t *edge_phase);
+
+/* Red-time accumulators t_p of Fig. 3 ("waiting time of vehicle at phase"), N*8 entries in ms. */
+int gmp_set_red_times(gmp_ctx *ctx, const uint32_t *red_ms);
+
+/* Vehicles currently on each road (Sec. 4.2: densities from road sensors; Calc_Dens). Recomputes edge
+ * travel times, queue delays and the phase order on the device. Host array of E entries.
+ * Errors: STATE, CUDA. */
+int gmp_set_densities(gmp_ctx *ctx, const uint32_t *vehicles);
+
+/* Same from device memory (E entries), asynchronous on the context's stream. */
+int gmp_set_densities_async(gmp_ctx *ctx, const uint32_t *d_vehicles);
+
+/* Colony tunables; recomputes threshold flags. Errors: INVALID_ARG. */
+int gmp_set_params(gmp_ctx *ctx, const gmp_params *params);
+int gmp_get_params(const gmp_ctx *ctx, gmp_params *params);
+
+/* One colony (Algorithm 2 for one origin-destination pair): n_iter iterations of n_ants ants each,
+ * then the best route. Synchronous; equivalent to gmp_solve_batch with one query.
+ * Errors: INVALID_ARG, UNSUPPORTED, STATE, OOM, CUDA, TIMEOUT; NO_ROUTE / BUFFER via out->status too. */
+int gmp_solve(gmp_ctx *ctx, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha, float beta,
+              float rho, uint64_t seed, gmp_result *out);
+
+/* n independent colonies on the context's graph in one device job (queries may differ in ants and
+ * iterations). Each result equals that of the query solved alone. Synchronous; host queries and results.
+ * Returns GMP_OK when the job ran (per-query outcomes in results[i].status), else an error code. */
+int gmp_solve_batch(gmp_ctx *ctx, uint32_t n, const gmp_query *queries, gmp_result *results);
+
+/* The three phases of gmp_solve_batch, for callers that keep inputs and outputs on the device:
+ *   gmp_batch_stage   validates and uploads n queries, reserves the device workspace (synchronous);
+ *   gmp_batch_launch  issues the whole job on the stream and returns (no host synchronisation, no copies);
+ *   gmp_batch_collect waits for the job and copies results[0..n) back (routes into caller buffers).
+ * gmp_batch_launch may be called repeatedly on a staged batch; every launch starts from fresh pheromone. */
+int gmp_batch_stage(gmp_ctx *ctx, uint32_t n, const gmp_query *queries);
+int gmp_batch_launch(gmp_ctx *ctx);
+int gmp_batch_collect(gmp_ctx *ctx, gmp_result *results);
+
+/* Pheromone of query `slot` of the last batch after its final iteration: E entries, Q32.32. */
+int gmp_get_pheromone(gmp_ctx *ctx, uint32_t slot, uint64_t *out_tau);
+
+/* Per-(iteration, ant) log of query `slot` (needs GMP_FLAG_ANT_LOG when the batch ran):
+ * n_iter*n_ants*4 entries {status, steps, T, W}; status 0 success, 1 dead end, 2 step cap, 3 time cap. */
+int gmp_get_ant_log(gmp_ctx *ctx, uint32_t slot, uint32_t *out, uint64_t capacity_entries);
+
+/* Current per-node phase order (N*8 entries; positions >= n_phases hold p) -- the preemptive plan. */
+int gmp_get_phase_order(gmp_ctx *ctx, uint8_t *out);
+
+/* Current congested travel time and queue delay per road (E entries each; either may be NULL). */
+int gmp_get_edge_times(gmp_ctx *ctx, uint32_t *tt_ms, uint32_t *qd_ms);
+
+/* Device time of the last launched job, in ms, per kernel family: out[0] construction, out[1] evaporation +
+ * deposit, out[2] best-route tracking, out[3] queue/preemption, out[4] whole job. Needs the stream idle. */
+int gmp_get_kernel_times(gmp_ctx *ctx, float *out_ms5);
+
+/* Count of kernel launches issued by the last gmp_batch_launch. */
+int gmp_get_launch_count(const gmp_ctx *ctx, uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMACOP_H */

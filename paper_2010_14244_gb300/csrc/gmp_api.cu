@@ -1,0 +1,827 @@
+// C ABI of libgmacop.so (declared and documented in include/gmacop.h).
+//
+// Replaces the paper's Algorithm 1 (allocate, copy in, one launch, copy out, free per call) with a
+// context that keeps the graph, signals, densities and batch workspace resident on the GPU, and a
+// whole colony job (init, then per iteration: construction, evaporation+deposit, best tracking,
+// queue/preemption update; then the result rows) captured once as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gmacop.h"
+#include "gmp_internal.h"
+
+using namespace gmp;
+
+namespace {
+
+constexpr uint32_t kKnownFlags = GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | 4u /*kernel timing*/ | 8u /*no graph*/;
+constexpr uint32_t kFlagKernelTiming = 4u;
+constexpr uint32_t kFlagNoGraph = 8u;
+constexpr int32_t kCoordLimit = 1 << 27;
+
+struct BatchKey {
+    uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0;
+    uint64_t log_entries = 0;
+    const void* ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
+};
+
+struct Batch {
+    uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0;
+    uint64_t log_entries = 0;
+    std::vector<gmp_query> hq;
+    bool staged = false, ran = false;
+    KernelConfig kc{};
+    // device workspace
+    DevQuery* dq = nullptr;
+    uint32_t* prefix = nullptr;
+    uint64_t* tau = nullptr;
+    unsigned long long* dep = nullptr;
+    QueryState* qs = nullptr;
+    uint32_t* routes = nullptr;
+    uint32_t* ant_steps = nullptr;
+    uint32_t* ant_wait = nullptr;
+    uint32_t* best_route = nullptr;
+    uint32_t* route_out = nullptr;
+    uint32_t* tickets = nullptr;
+    uint32_t* ant_log = nullptr;
+    uint32_t* tabu = nullptr;
+    DevResult* res = nullptr;
+    // captured job
+    cudaGraphExec_t exec = nullptr;
+    BatchKey key{};
+    uint64_t launches = 0;
+    std::vector<cudaEvent_t> ev;
+    bool timed = false;
+};
+
+}  // namespace
+
+struct gmp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    uint64_t budget = 0, used = 0;
+    std::unordered_map<void*, size_t> sizes;
+    std::string err;
+    gmp_params prm{};
+    bool has_graph = false;
+    uint32_t N = 0, E = 0, maxdeg = 0, kappa = 0;
+    uint32_t *row_ptr = nullptr, *col = nullptr, *len = nullptr, *in_ptr = nullptr, *in_edge = nullptr;
+    uint32_t *ff = nullptr, *cap = nullptr;
+    uint16_t* speed = nullptr;
+    uint8_t* lanes = nullptr;
+    int32_t *x = nullptr, *y = nullptr;
+    uint8_t *nph = nullptr, *ephase = nullptr, *order = nullptr;
+    uint32_t *cycle = nullptr, *offset = nullptr, *green = nullptr, *red = nullptr, *veh = nullptr;
+    EdgeRec* rec = nullptr;
+    std::vector<int32_t> hx, hy;  // host copy of node coordinates (destination lookups at staging)
+    Batch b;
+};
+
+namespace {
+
+int fail(gmp_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define GMP_CUDA(c, call)                                                                          \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail((c), GMP_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define GMP_TRY(x)             \
+    do {                       \
+        int r_ = (x);          \
+        if (r_ != GMP_OK) return r_; \
+    } while (0)
+
+template <class T>
+int dalloc(gmp_ctx* c, T** p, size_t n) {
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(c, GMP_ERR_OOM, "memory budget exceeded: %zu + %zu > %llu bytes", (size_t)c->used, bytes,
+                    (unsigned long long)c->budget);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GMP_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    *p = static_cast<T*>(q);
+    c->used += bytes;
+    c->sizes[q] = bytes;
+    return GMP_OK;
+}
+
+template <class T>
+void dfree(gmp_ctx* c, T** p) {
+    if (*p) {
+        auto it = c->sizes.find((void*)*p);
+        if (it != c->sizes.end()) {
+            c->used -= it->second;
+            c->sizes.erase(it);
+        }
+        cudaFree((void*)*p);
+        *p = nullptr;
+    }
+}
+
+// (Re)allocate a workspace buffer only when it must grow.
+template <class T>
+int ensure(gmp_ctx* c, T** p, size_t n) {
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    if (*p) {
+        auto it = c->sizes.find((void*)*p);
+        if (it != c->sizes.end() && it->second >= bytes) return GMP_OK;
+        dfree(c, p);
+    }
+    return dalloc(c, p, n);
+}
+
+template <class T>
+int upload(gmp_ctx* c, T* d, const T* h, size_t n) {
+    if (n == 0) return GMP_OK;
+    GMP_CUDA(c, cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return GMP_OK;
+}
+
+void drop_graph(Batch& b) {
+    if (b.exec) {
+        cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+    }
+    b.key = BatchKey{};
+}
+
+void drop_events(Batch& b) {
+    for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
+    b.ev.clear();
+}
+
+void free_batch(gmp_ctx* c) {
+    Batch& b = c->b;
+    drop_graph(b);
+    drop_events(b);
+    dfree(c, &b.dq);
+    dfree(c, &b.prefix);
+    dfree(c, &b.tau);
+    dfree(c, &b.dep);
+    dfree(c, &b.qs);
+    dfree(c, &b.routes);
+    dfree(c, &b.ant_steps);
+    dfree(c, &b.ant_wait);
+    dfree(c, &b.best_route);
+    dfree(c, &b.route_out);
+    dfree(c, &b.tickets);
+    dfree(c, &b.ant_log);
+    dfree(c, &b.tabu);
+    dfree(c, &b.res);
+    b.staged = b.ran = false;
+}
+
+void free_graph(gmp_ctx* c) {
+    free_batch(c);
+    dfree(c, &c->row_ptr);
+    dfree(c, &c->col);
+    dfree(c, &c->len);
+    dfree(c, &c->in_ptr);
+    dfree(c, &c->in_edge);
+    dfree(c, &c->ff);
+    dfree(c, &c->cap);
+    dfree(c, &c->speed);
+    dfree(c, &c->lanes);
+    dfree(c, &c->x);
+    dfree(c, &c->y);
+    dfree(c, &c->nph);
+    dfree(c, &c->ephase);
+    dfree(c, &c->order);
+    dfree(c, &c->cycle);
+    dfree(c, &c->offset);
+    dfree(c, &c->green);
+    dfree(c, &c->red);
+    dfree(c, &c->veh);
+    dfree(c, &c->rec);
+    c->has_graph = false;
+    c->N = c->E = 0;
+}
+
+uint32_t hsat_of(const gmp_ctx* c) { return c->prm.h_sat_ms ? c->prm.h_sat_ms : kHsatDefault; }
+
+// Densities or signals or params changed: rebuild road records and the phase order.
+int refresh_dynamic(gmp_ctx* c) {
+    GMP_CUDA(c, launch_edge_dynamic(c->stream, c->E, c->row_ptr, c->col, c->ff, c->cap, c->lanes, c->veh, c->nph,
+                                    c->x, c->y, hsat_of(c), c->prm.thr_permille, c->rec));
+    GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
+                                     c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
+    return GMP_OK;
+}
+
+int sync(gmp_ctx* c) {
+    GMP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GMP_OK;
+}
+
+uint32_t default_max_steps(const gmp_ctx* c) {
+    if (c->prm.max_steps) return c->prm.max_steps;
+    const uint32_t n1 = c->N > 0 ? c->N - 1 : 0;
+    return n1 < 4096u ? n1 : 4096u;
+}
+
+int pick_lanes(const gmp_ctx* c) {
+    if (c->prm.lanes_per_ant) return (int)c->prm.lanes_per_ant;
+    for (int g : {4, 8, 16, 32})
+        if ((uint32_t)construct_max_degree(g) >= c->maxdeg) return g;
+    return 32;
+}
+
+int check_query(gmp_ctx* c, const gmp_query& q, uint32_t idx) {
+    if (q.src >= c->N || q.dst >= c->N)
+        return fail(c, GMP_ERR_INVALID_ARG, "query %u: node out of range (src %u, dst %u, N %u)", idx, q.src, q.dst, c->N);
+    if (q.n_ants == 0 || q.n_iter == 0) return fail(c, GMP_ERR_INVALID_ARG, "query %u: n_ants and n_iter must be >= 1", idx);
+    if ((uint64_t)q.n_ants * q.n_iter > 0xFFFFFFFFull)
+        return fail(c, GMP_ERR_INVALID_ARG, "query %u: n_ants * n_iter must be < 2^32", idx);
+    if (!(q.alpha >= 0.0f && q.alpha <= 8.0f && q.beta >= 0.0f && q.beta <= 8.0f) || floorf(q.alpha) != q.alpha ||
+        floorf(q.beta) != q.beta)
+        return fail(c, GMP_ERR_UNSUPPORTED, "query %u: alpha and beta must be integers in [0, 8]", idx);
+    if (!(q.rho >= 0.0f && q.rho < 1.0f)) return fail(c, GMP_ERR_INVALID_ARG, "query %u: rho must lie in [0, 1)", idx);
+    return GMP_OK;
+}
+
+int record(gmp_ctx* c, Batch& b, size_t i) {
+    GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[i], c->stream, cudaEventRecordExternal));
+    return GMP_OK;
+}
+
+// Issue the whole job on the stream (inside a capture or directly).
+int enqueue_job(gmp_ctx* c) {
+    Batch& b = c->b;
+    cudaStream_t s = c->stream;
+    const bool timed = b.timed;
+    uint64_t n = 0;
+    if (timed) GMP_TRY(record(c, b, 0));
+    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.dep, b.qs,
+                                  b.tickets, b.maxI));
+    ++n;
+    if (timed) GMP_TRY(record(c, b, 1));
+    ConstructArgs a{};
+    a.rec = c->rec;
+    a.row_ptr = c->row_ptr;
+    a.col = c->col;
+    a.queries = b.dq;
+    a.ant_prefix = b.prefix;
+    a.tau = b.tau;
+    a.dep = b.dep;
+    a.qs = b.qs;
+    a.routes = b.routes;
+    a.ant_steps = b.ant_steps;
+    a.ant_wait = b.ant_wait;
+    a.ant_log = b.log_entries ? b.ant_log : nullptr;  // sized at staging
+    a.tickets = b.tickets;
+    a.tabu_global = b.tabu;
+    a.n_queries = b.Q;
+    a.total_ants = b.total_ants;
+    a.n_edges = c->E;
+    a.max_steps = b.max_steps;
+    a.tabu_words = (c->N + 31u) / 32u;
+    a.t_dep = c->prm.t_dep_ms;
+    a.thr_on = c->prm.thr_permille != kThrOff;
+    a.tabu_in_smem = b.kc.tabu_in_smem ? 1u : 0u;
+    a.kappa = c->kappa;
+    for (uint32_t it = 0; it < b.maxI; ++it) {
+        GMP_CUDA(c, launch_construct(s, b.kc, a, it));
+        if (timed) GMP_TRY(record(c, b, 2 + 4 * (size_t)it));
+        GMP_CUDA(c, launch_evaporate(s, b.Q, c->E, b.dq, b.tau, b.dep, it));
+        if (timed) GMP_TRY(record(c, b, 3 + 4 * (size_t)it));
+        GMP_CUDA(c, launch_best_copy(s, b.Q, b.dq, b.qs, b.routes, b.ant_steps, b.ant_wait, b.best_route,
+                                     b.max_steps, it));
+        if (timed) GMP_TRY(record(c, b, 4 + 4 * (size_t)it));
+        // per-iteration queue/preemption update (densities are fixed during a job: same order again)
+        GMP_CUDA(c, launch_queue_preempt(s, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
+                                         c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
+        if (timed) GMP_TRY(record(c, b, 5 + 4 * (size_t)it));
+        n += 4;
+    }
+    GMP_CUDA(c, launch_finalize(s, b.Q, b.dq, b.qs, b.best_route, c->col, b.max_steps, b.res, b.route_out));
+    ++n;
+    if (timed) GMP_TRY(record(c, b, 2 + 4 * (size_t)b.maxI));
+    b.launches = n;
+    return GMP_OK;
+}
+
+BatchKey key_of(const gmp_ctx* c) {
+    const Batch& b = c->b;
+    BatchKey k;
+    k.Q = b.Q;
+    k.maxI = b.maxI;
+    k.total_ants = b.total_ants;
+    k.max_steps = b.max_steps;
+    k.flags = c->prm.flags;
+    k.lanes = (uint32_t)b.kc.lanes;
+    k.grid = (uint32_t)b.kc.grid;
+    k.thr_on = c->prm.thr_permille != kThrOff;
+    k.t_dep = c->prm.t_dep_ms;
+    k.log_entries = b.log_entries;
+    k.ptrs[0] = b.tau;
+    k.ptrs[1] = b.routes;
+    k.ptrs[2] = b.tabu;
+    k.ptrs[3] = c->rec;
+    return k;
+}
+
+}  // namespace
+
+// =====================================================================================================
+extern "C" {
+
+const char* gmp_strerror(int code) {
+    switch (code) {
+        case GMP_OK: return "ok";
+        case GMP_ERR_INVALID_ARG: return "invalid argument";
+        case GMP_ERR_NO_ROUTE: return "no route found";
+        case GMP_ERR_OOM: return "out of device memory or memory budget";
+        case GMP_ERR_CUDA: return "CUDA error";
+        case GMP_ERR_TIMEOUT: return "device wait timed out";
+        case GMP_ERR_UNSUPPORTED: return "unsupported";
+        case GMP_ERR_BUFFER: return "buffer too small";
+        case GMP_ERR_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+const char* gmp_last_error(const gmp_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int gmp_create(gmp_ctx** out, int device, uint64_t mem_budget_bytes, void* cuda_stream) {
+    if (!out) return GMP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return GMP_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return GMP_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return GMP_ERR_CUDA;
+    gmp_ctx* c = new gmp_ctx();
+    c->device = device;
+    c->budget = mem_budget_bytes;
+    c->prm.thr_permille = GMP_THRESHOLD_OFF;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return GMP_ERR_CUDA;
+    }
+    c->stream = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+    *out = c;
+    return GMP_OK;
+}
+
+void gmp_destroy(gmp_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_graph(c);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+int gmp_set_stream(gmp_ctx* c, void* cuda_stream) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    c->stream = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+    return GMP_OK;
+}
+
+int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
+                   const uint32_t* length_dm, const uint16_t* speed_kmh, const uint8_t* lanes, const int32_t* x_dm,
+                   const int32_t* y_dm) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    if (N == 0 || N >= (1u << 31) || E >= (1u << 31))
+        return fail(c, GMP_ERR_INVALID_ARG, "need 1 <= N < 2^31 and E < 2^31");
+    if (!row_ptr || !x_dm || !y_dm || (E && (!col || !length_dm || !speed_kmh || !lanes)))
+        return fail(c, GMP_ERR_INVALID_ARG, "null array");
+    if (row_ptr[0] != 0 || row_ptr[N] != E) return fail(c, GMP_ERR_INVALID_ARG, "row_ptr must start at 0 and end at E");
+    uint32_t maxdeg = 0;
+    for (uint32_t v = 0; v < N; ++v) {
+        if (row_ptr[v + 1] < row_ptr[v]) return fail(c, GMP_ERR_INVALID_ARG, "row_ptr not monotone at %u", v);
+        maxdeg = std::max(maxdeg, row_ptr[v + 1] - row_ptr[v]);
+        if (x_dm[v] > kCoordLimit || x_dm[v] < -kCoordLimit || y_dm[v] > kCoordLimit || y_dm[v] < -kCoordLimit)
+            return fail(c, GMP_ERR_INVALID_ARG, "coordinate of node %u beyond +-2^27 dm", v);
+    }
+    uint32_t vmax = 1;
+    std::vector<uint32_t> in_ptr(N + 1, 0), in_edge(E);
+    for (uint32_t e = 0; e < E; ++e) {
+        if (col[e] >= N) return fail(c, GMP_ERR_INVALID_ARG, "col[%u] out of range", e);
+        if (length_dm[e] == 0 || speed_kmh[e] == 0 || lanes[e] == 0)
+            return fail(c, GMP_ERR_INVALID_ARG, "road %u: length, speed and lanes must be >= 1", e);
+        vmax = std::max<uint32_t>(vmax, speed_kmh[e]);
+        in_ptr[col[e] + 1]++;
+    }
+    for (uint32_t v = 0; v < N; ++v) in_ptr[v + 1] += in_ptr[v];
+    {
+        std::vector<uint32_t> fill(in_ptr.begin(), in_ptr.end() - 1);
+        for (uint32_t e = 0; e < E; ++e) in_edge[fill[col[e]]++] = e;
+    }
+    cudaSetDevice(c->device);
+    sync(c);
+    free_graph(c);
+    c->N = N;
+    c->E = E;
+    c->maxdeg = maxdeg;
+    c->hx.assign(x_dm, x_dm + N);
+    c->hy.assign(y_dm, y_dm + N);
+    c->kappa = (uint32_t)((360ull << 16) / vmax);
+    GMP_TRY(dalloc(c, &c->row_ptr, N + 1));
+    GMP_TRY(dalloc(c, &c->col, E));
+    GMP_TRY(dalloc(c, &c->len, E));
+    GMP_TRY(dalloc(c, &c->in_ptr, N + 1));
+    GMP_TRY(dalloc(c, &c->in_edge, E));
+    GMP_TRY(dalloc(c, &c->ff, E));
+    GMP_TRY(dalloc(c, &c->cap, E));
+    GMP_TRY(dalloc(c, &c->speed, E));
+    GMP_TRY(dalloc(c, &c->lanes, E));
+    GMP_TRY(dalloc(c, &c->x, N));
+    GMP_TRY(dalloc(c, &c->y, N));
+    GMP_TRY(dalloc(c, &c->nph, N));
+    GMP_TRY(dalloc(c, &c->ephase, E));
+    GMP_TRY(dalloc(c, &c->order, (size_t)N * kMaxPhases));
+    GMP_TRY(dalloc(c, &c->cycle, N));
+    GMP_TRY(dalloc(c, &c->offset, N));
+    GMP_TRY(dalloc(c, &c->green, (size_t)N * kMaxPhases));
+    GMP_TRY(dalloc(c, &c->red, (size_t)N * kMaxPhases));
+    GMP_TRY(dalloc(c, &c->veh, E));
+    GMP_TRY(dalloc(c, &c->rec, E));
+    GMP_TRY(upload(c, c->row_ptr, row_ptr, N + 1));
+    GMP_TRY(upload(c, c->col, col, E));
+    GMP_TRY(upload(c, c->len, length_dm, E));
+    GMP_TRY(upload(c, c->speed, speed_kmh, E));
+    GMP_TRY(upload(c, c->lanes, lanes, E));
+    GMP_TRY(upload(c, c->x, x_dm, N));
+    GMP_TRY(upload(c, c->y, y_dm, N));
+    GMP_TRY(upload(c, c->in_ptr, in_ptr.data(), N + 1));
+    GMP_TRY(upload(c, c->in_edge, in_edge.data(), E));
+    GMP_CUDA(c, cudaMemsetAsync(c->nph, 0, N, c->stream));
+    GMP_CUDA(c, cudaMemsetAsync(c->ephase, 0, std::max<size_t>(E, 1), c->stream));
+    GMP_CUDA(c, cudaMemsetAsync(c->cycle, 0, N * 4ull, c->stream));
+    GMP_CUDA(c, cudaMemsetAsync(c->offset, 0, N * 4ull, c->stream));
+    GMP_CUDA(c, cudaMemsetAsync(c->green, 0, N * 4ull * kMaxPhases, c->stream));
+    GMP_CUDA(c, cudaMemsetAsync(c->red, 0, N * 4ull * kMaxPhases, c->stream));
+    GMP_CUDA(c, cudaMemsetAsync(c->veh, 0, std::max<size_t>(E, 1) * 4, c->stream));
+    GMP_CUDA(c, launch_edge_static(c->stream, E, c->len, c->speed, c->lanes, c->ff, c->cap));
+    GMP_TRY(refresh_dynamic(c));
+    GMP_TRY(sync(c));
+    c->has_graph = true;
+    return GMP_OK;
+}
+
+int gmp_set_signals(gmp_ctx* c, const uint8_t* n_phases, const uint32_t* cycle_ms, const uint32_t* offset_ms,
+                    const uint32_t* green_ms, const uint8_t* edge_phase) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (!n_phases || !cycle_ms || !offset_ms || !green_ms || (c->E && !edge_phase))
+        return fail(c, GMP_ERR_INVALID_ARG, "null array");
+    std::vector<uint32_t> row(c->N + 1);
+    for (uint32_t v = 0; v < c->N; ++v) {
+        const uint32_t P = n_phases[v];
+        if (P > kMaxPhases) return fail(c, GMP_ERR_UNSUPPORTED, "node %u: more than 8 phases", v);
+        if (P == 0) continue;
+        const uint32_t cy = cycle_ms[v];
+        if (cy == 0 || cy > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "node %u: cycle must be in 1..2^24 ms", v);
+        if (offset_ms[v] >= cy) return fail(c, GMP_ERR_INVALID_ARG, "node %u: offset must be below the cycle", v);
+        uint64_t sum = 0;
+        for (uint32_t p = 0; p < P; ++p) {
+            if (green_ms[(size_t)v * kMaxPhases + p] == 0)
+                return fail(c, GMP_ERR_INVALID_ARG, "node %u: every phase needs green time", v);
+            sum += green_ms[(size_t)v * kMaxPhases + p];
+        }
+        if (sum != cy) return fail(c, GMP_ERR_INVALID_ARG, "node %u: green times must add up to the cycle", v);
+    }
+    std::vector<uint32_t> hcol(c->E);
+    cudaSetDevice(c->device);
+    if (c->E) GMP_CUDA(c, cudaMemcpy(hcol.data(), c->col, c->E * 4ull, cudaMemcpyDeviceToHost));
+    for (uint32_t e = 0; e < c->E; ++e) {
+        const uint32_t P = n_phases[hcol[e]];
+        if (P > 0 && edge_phase[e] >= P)
+            return fail(c, GMP_ERR_INVALID_ARG, "road %u: approach phase %u beyond the head's %u phases", e, edge_phase[e], P);
+    }
+    sync(c);
+    GMP_TRY(upload(c, c->nph, n_phases, c->N));
+    GMP_TRY(upload(c, c->cycle, cycle_ms, c->N));
+    GMP_TRY(upload(c, c->offset, offset_ms, c->N));
+    GMP_TRY(upload(c, c->green, green_ms, (size_t)c->N * kMaxPhases));
+    GMP_TRY(upload(c, c->ephase, edge_phase, c->E));
+    GMP_CUDA(c, cudaMemsetAsync(c->red, 0, c->N * 4ull * kMaxPhases, c->stream));
+    GMP_TRY(refresh_dynamic(c));
+    return sync(c);
+}
+
+int gmp_set_red_times(gmp_ctx* c, const uint32_t* red_ms) {
+    if (!c || !red_ms) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    cudaSetDevice(c->device);
+    GMP_TRY(upload(c, c->red, red_ms, (size_t)c->N * kMaxPhases));
+    GMP_TRY(refresh_dynamic(c));
+    return sync(c);
+}
+
+int gmp_set_densities(gmp_ctx* c, const uint32_t* vehicles) {
+    if (!c || (!vehicles && c->E)) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    cudaSetDevice(c->device);
+    GMP_TRY(upload(c, c->veh, vehicles, c->E));
+    GMP_TRY(refresh_dynamic(c));
+    return sync(c);
+}
+
+int gmp_set_densities_async(gmp_ctx* c, const uint32_t* d_vehicles) {
+    if (!c || (!d_vehicles && c->E)) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    cudaSetDevice(c->device);
+    if (c->E) GMP_CUDA(c, cudaMemcpyAsync(c->veh, d_vehicles, c->E * 4ull, cudaMemcpyDeviceToDevice, c->stream));
+    return refresh_dynamic(c);
+}
+
+int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
+    if (!c || !p) return GMP_ERR_INVALID_ARG;
+    if (p->flags & ~kKnownFlags) return fail(c, GMP_ERR_INVALID_ARG, "unknown flag bits");
+    if (p->t_dep_ms >= kTCap) return fail(c, GMP_ERR_INVALID_ARG, "t_dep_ms must be below 2^30");
+    if (p->lanes_per_ant && p->lanes_per_ant != 4 && p->lanes_per_ant != 8 && p->lanes_per_ant != 16 &&
+        p->lanes_per_ant != 32)
+        return fail(c, GMP_ERR_INVALID_ARG, "lanes_per_ant must be 0, 4, 8, 16 or 32");
+    if (p->mode > GMP_MODE_PERSISTENT) return fail(c, GMP_ERR_INVALID_ARG, "unknown mode");
+    if (p->max_steps > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "max_steps must be <= 2^24");
+    const bool dyn = p->thr_permille != c->prm.thr_permille || p->h_sat_ms != c->prm.h_sat_ms;
+    c->prm = *p;
+    if (dyn && c->has_graph) {
+        cudaSetDevice(c->device);
+        GMP_TRY(refresh_dynamic(c));
+        GMP_TRY(sync(c));
+    }
+    return GMP_OK;
+}
+
+int gmp_get_params(const gmp_ctx* c, gmp_params* p) {
+    if (!c || !p) return GMP_ERR_INVALID_ARG;
+    *p = c->prm;
+    return GMP_OK;
+}
+
+int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
+    if (!c || (n && !queries)) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (n == 0) return fail(c, GMP_ERR_INVALID_ARG, "empty batch");
+    for (uint32_t i = 0; i < n; ++i) GMP_TRY(check_query(c, queries[i], i));
+    const int lanes = pick_lanes(c);
+    if ((uint32_t)construct_max_degree(lanes) < c->maxdeg)
+        return fail(c, GMP_ERR_UNSUPPORTED, "out-degree %u exceeds %d for %d lanes per ant", c->maxdeg,
+                    construct_max_degree(lanes), lanes);
+    cudaSetDevice(c->device);
+    GMP_TRY(sync(c));
+    Batch& b = c->b;
+    b.hq.assign(queries, queries + n);
+    b.Q = n;
+    b.max_steps = std::max<uint32_t>(default_max_steps(c), 1u);
+    std::vector<DevQuery> hdq(n);
+    std::vector<uint32_t> prefix(n + 1, 0);
+    uint64_t total = 0, logs = 0;
+    uint32_t maxI = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const gmp_query& q = queries[i];
+        DevQuery& d = hdq[i];
+        memset(&d, 0, sizeof d);
+        d.src = q.src;
+        d.dst = q.dst;
+        d.n_ants = q.n_ants;
+        d.n_iter = q.n_iter;
+        d.alpha = (uint32_t)q.alpha;
+        d.beta = (uint32_t)q.beta;
+        d.ant_base = (uint32_t)total;
+        d.active = q.src != q.dst;
+        d.rho_fix = (uint64_t)nearbyint(ldexp((double)q.rho, 32));
+        d.seed = q.seed;
+        d.log_base = logs;
+        prefix[i] = (uint32_t)total;
+        total += q.n_ants;
+        logs += (uint64_t)q.n_ants * q.n_iter;
+        maxI = std::max(maxI, q.n_iter);
+        if (total >= (1ull << 32)) return fail(c, GMP_ERR_INVALID_ARG, "batch holds 2^32 or more ants");
+    }
+    prefix[n] = (uint32_t)total;
+    for (uint32_t i = 0; i < n; ++i) {  // destination coordinates for the heuristic
+        hdq[i].xd = c->hx[queries[i].dst];
+        hdq[i].yd = c->hy[queries[i].dst];
+    }
+    b.total_ants = (uint32_t)total;
+    b.maxI = maxI;
+    b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
+    GMP_CUDA(c, construct_config(c->device, lanes, c->N, b.total_ants, &b.kc));
+    const size_t words = (c->N + 31u) / 32u;
+    GMP_TRY(ensure(c, &b.dq, n));
+    GMP_TRY(ensure(c, &b.prefix, n + 1));
+    GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.qs, n));
+    GMP_TRY(ensure(c, &b.routes, (size_t)b.total_ants * b.max_steps));
+    GMP_TRY(ensure(c, &b.ant_steps, b.total_ants));
+    GMP_TRY(ensure(c, &b.ant_wait, b.total_ants));
+    GMP_TRY(ensure(c, &b.best_route, (size_t)n * b.max_steps));
+    GMP_TRY(ensure(c, &b.route_out, (size_t)n * (b.max_steps + 1)));
+    GMP_TRY(ensure(c, &b.tickets, maxI));
+    GMP_TRY(ensure(c, &b.res, n));
+    if (b.log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)b.log_entries * 4));
+    if (!b.kc.tabu_in_smem)
+        GMP_TRY(ensure(c, &b.tabu, (size_t)b.kc.grid * (b.kc.block / b.kc.lanes) * words));
+    GMP_TRY(upload(c, b.dq, hdq.data(), n));
+    GMP_TRY(upload(c, b.prefix, prefix.data(), n + 1));
+    GMP_TRY(sync(c));
+    b.staged = true;
+    b.ran = false;
+    return GMP_OK;
+}
+
+int gmp_batch_launch(gmp_ctx* c) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    Batch& b = c->b;
+    if (!b.staged) return fail(c, GMP_ERR_STATE, "stage a batch first");
+    cudaSetDevice(c->device);
+    const bool timed = (c->prm.flags & kFlagKernelTiming) != 0;
+    const size_t n_ev = timed ? 3 + 4 * (size_t)b.maxI : 0;
+    if (b.ev.size() != n_ev || b.timed != timed) {
+        drop_graph(b);
+        drop_events(b);
+        b.ev.resize(n_ev);
+        for (size_t i = 0; i < n_ev; ++i) GMP_CUDA(c, cudaEventCreate(&b.ev[i]));
+        b.timed = timed;
+    }
+    if (c->prm.flags & kFlagNoGraph) {
+        GMP_TRY(enqueue_job(c));
+    } else {
+        const BatchKey k = key_of(c);
+        if (!b.exec || !(b.key == k)) {
+            drop_graph(b);
+            cudaGraph_t g = nullptr;
+            GMP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            const int rc = enqueue_job(c);
+            const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+            if (rc != GMP_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            GMP_CUDA(c, ce);
+            const cudaError_t ie = cudaGraphInstantiate(&b.exec, g, 0);
+            cudaGraphDestroy(g);
+            GMP_CUDA(c, ie);
+            b.key = k;
+        }
+        GMP_CUDA(c, cudaGraphLaunch(b.exec, c->stream));
+    }
+    b.ran = true;
+    return GMP_OK;
+}
+
+int gmp_batch_collect(gmp_ctx* c, gmp_result* results) {
+    if (!c || !results) return GMP_ERR_INVALID_ARG;
+    Batch& b = c->b;
+    if (!b.ran) return fail(c, GMP_ERR_STATE, "launch the batch first");
+    cudaSetDevice(c->device);
+    std::vector<DevResult> hr(b.Q);
+    GMP_CUDA(c, cudaMemcpyAsync(hr.data(), b.res, b.Q * sizeof(DevResult), cudaMemcpyDeviceToHost, c->stream));
+    GMP_TRY(sync(c));
+    for (uint32_t i = 0; i < b.Q; ++i) {
+        gmp_result& r = results[i];
+        const DevResult& d = hr[i];
+        r.route_len = d.route_len;
+        r.travel_ms = d.travel_ms;
+        r.wait_ms = d.wait_ms;
+        r.ant_steps = d.ant_steps;
+        r.n_success = d.n_success;
+        r.best_iter = d.best_iter;
+        r.best_ant = d.best_ant;
+        r.status = d.status;
+        if (d.status == GMP_OK) {
+            if (!r.route || r.route_cap < d.route_len) {
+                r.status = GMP_ERR_BUFFER;
+            } else {
+                GMP_CUDA(c, cudaMemcpyAsync(r.route, b.route_out + (size_t)i * (b.max_steps + 1),
+                                            d.route_len * 4ull, cudaMemcpyDeviceToHost, c->stream));
+            }
+        }
+    }
+    return sync(c);
+}
+
+int gmp_solve_batch(gmp_ctx* c, uint32_t n, const gmp_query* queries, gmp_result* results) {
+    GMP_TRY(gmp_batch_stage(c, n, queries));
+    GMP_TRY(gmp_batch_launch(c));
+    return gmp_batch_collect(c, results);
+}
+
+int gmp_solve(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha, float beta,
+              float rho, uint64_t seed, gmp_result* out) {
+    if (!out) return GMP_ERR_INVALID_ARG;
+    gmp_query q;
+    memset(&q, 0, sizeof q);
+    q.src = src;
+    q.dst = dst;
+    q.n_ants = n_ants;
+    q.n_iter = n_iter;
+    q.alpha = alpha;
+    q.beta = beta;
+    q.rho = rho;
+    q.seed = seed;
+    const int rc = gmp_solve_batch(c, 1, &q, out);
+    if (rc != GMP_OK) {
+        out->status = rc;
+        return rc;
+    }
+    return out->status;
+}
+
+int gmp_get_pheromone(gmp_ctx* c, uint32_t slot, uint64_t* out_tau) {
+    if (!c || !out_tau) return GMP_ERR_INVALID_ARG;
+    if (!c->b.ran) return fail(c, GMP_ERR_STATE, "no batch has run");
+    if (slot >= c->b.Q) return fail(c, GMP_ERR_INVALID_ARG, "slot out of range");
+    cudaSetDevice(c->device);
+    GMP_CUDA(c, cudaMemcpyAsync(out_tau, c->b.tau + (size_t)slot * c->E, c->E * 8ull, cudaMemcpyDeviceToHost,
+                                c->stream));
+    return sync(c);
+}
+
+int gmp_get_ant_log(gmp_ctx* c, uint32_t slot, uint32_t* out, uint64_t capacity_entries) {
+    if (!c || !out) return GMP_ERR_INVALID_ARG;
+    Batch& b = c->b;
+    if (!b.ran || !b.log_entries) return fail(c, GMP_ERR_STATE, "no ant log (set GMP_FLAG_ANT_LOG before staging)");
+    if (slot >= b.Q) return fail(c, GMP_ERR_INVALID_ARG, "slot out of range");
+    const gmp_query& q = b.hq[slot];
+    const uint64_t n = (uint64_t)q.n_ants * q.n_iter * 4;
+    if (capacity_entries < n) return fail(c, GMP_ERR_BUFFER, "need %llu entries", (unsigned long long)n);
+    uint64_t base = 0;
+    for (uint32_t i = 0; i < slot; ++i) base += (uint64_t)b.hq[i].n_ants * b.hq[i].n_iter;
+    cudaSetDevice(c->device);
+    GMP_CUDA(c, cudaMemcpyAsync(out, b.ant_log + base * 4, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+int gmp_get_phase_order(gmp_ctx* c, uint8_t* out) {
+    if (!c || !out) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    cudaSetDevice(c->device);
+    GMP_CUDA(c, cudaMemcpyAsync(out, c->order, (size_t)c->N * kMaxPhases, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+int gmp_get_edge_times(gmp_ctx* c, uint32_t* tt_ms, uint32_t* qd_ms) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    std::vector<EdgeRec> h(c->E);
+    cudaSetDevice(c->device);
+    if (c->E) GMP_CUDA(c, cudaMemcpyAsync(h.data(), c->rec, c->E * sizeof(EdgeRec), cudaMemcpyDeviceToHost, c->stream));
+    GMP_TRY(sync(c));
+    for (uint32_t e = 0; e < c->E; ++e) {
+        if (tt_ms) tt_ms[e] = h[e].tt;
+        if (qd_ms) qd_ms[e] = h[e].qd;
+    }
+    return GMP_OK;
+}
+
+int gmp_get_kernel_times(gmp_ctx* c, float* out) {
+    if (!c || !out) return GMP_ERR_INVALID_ARG;
+    Batch& b = c->b;
+    for (int i = 0; i < 5; ++i) out[i] = 0.0f;
+    if (!b.ran || !b.timed || b.ev.empty()) return fail(c, GMP_ERR_STATE, "no timed job has run");
+    cudaSetDevice(c->device);
+    GMP_TRY(sync(c));
+    float ms = 0;
+    for (uint32_t it = 0; it < b.maxI; ++it) {
+        const size_t prev = it == 0 ? 1 : 1 + 4 * (size_t)it;
+        for (int k = 0; k < 4; ++k) {
+            GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[prev + k], b.ev[prev + k + 1]));
+            out[k] += ms;
+        }
+    }
+    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[2 + 4 * (size_t)b.maxI]));
+    out[4] = ms;
+    return GMP_OK;
+}
+
+int gmp_get_launch_count(const gmp_ctx* c, uint64_t* out) {
+    if (!c || !out) return GMP_ERR_INVALID_ARG;
+    *out = c->b.launches;
+    return GMP_OK;
+}
+
+}  // extern "C"

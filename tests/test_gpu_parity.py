@@ -1,0 +1,262 @@
+"""Parity of the sm_103a library (through the C ABI) with the CPU oracle, bit for bit.
+
+Every comparison is exact: routes, travel and wait times, step and success counts, the best
+(iteration, ant), per-ant logs, final pheromone tables, road times and phase orders. The tolerance is
+zero because both sides use integer arithmetic and identically ordered binary32 operations.
+"""
+import numpy as np
+import pytest
+
+from paper_2010_14244_gb300 import workloads as W
+from tests import netbuild as NB
+
+pytestmark = pytest.mark.gpu
+
+Q = W.Query
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_2010_14244_gb300 import build, gmacop
+
+    build.build()
+    return gmacop
+
+
+@pytest.fixture()
+def ctx(gm):
+    c = gm.Context(0)
+    yield c
+    c.close()
+
+
+def _oparams(orc, **kw):
+    return orc.Params(**kw)
+
+
+def _compare(orc, onet, oparams, q, gres, ctx=None, slot=0, log=None):
+    o = orc.solve(onet, oparams, q, want_log=log is not None)
+    assert gres["status"] == o["status"], (gres, {k: v for k, v in o.items() if k not in ("tau", "log")})
+    for k in ("travel_ms", "wait_ms", "ant_steps", "n_success", "route_len"):
+        assert gres[k] == o[k], (k, gres[k], o[k])
+    if o["status"] == 0:
+        assert gres["best_iter"] == o["best_iter"] and gres["best_ant"] == o["best_ant"]
+        np.testing.assert_array_equal(gres["route"], o["route"])
+    if ctx is not None:
+        np.testing.assert_array_equal(ctx.pheromone(slot), o["tau"])
+    if log is not None:
+        np.testing.assert_array_equal(log, o["log"])
+    return o
+
+
+def test_edge_times_and_phase_order(gm, ctx, orc):
+    for wl in (W.grid10(), W.grid64(n_queries=1)):
+        ctx.load_workload(wl)
+        onet = orc.Net.from_workload(wl)
+        prep = orc.prepare(onet, orc.Params(), 0)
+        tt, qd = ctx.edge_times()
+        np.testing.assert_array_equal(tt, prep["tt"])
+        np.testing.assert_array_equal(qd, prep["qd"])
+        np.testing.assert_array_equal(ctx.phase_order(), prep["order"])
+
+
+def test_phase_order_with_red_times_and_queues(gm, ctx, orc):
+    rng = np.random.default_rng(5)
+    net, sig = W.random_small(60, 120, rng, signalised_frac=0.7)
+    # give some nodes 3-8 phases
+    P = np.where(sig.n_phases > 0, rng.integers(2, 9, net.n_nodes), 0).astype(np.uint8)
+    green = np.zeros((net.n_nodes, 8), np.uint32)
+    for v in range(net.n_nodes):
+        if P[v]:
+            green[v, : P[v]] = rng.integers(5000, 30000, P[v])
+    cycle = green.sum(1).astype(np.uint32)
+    offset = (rng.random(net.n_nodes) * np.maximum(cycle, 1)).astype(np.uint32)
+    heads = net.col
+    ephase = np.where(P[heads] > 0, rng.integers(0, 8, net.n_edges) % np.maximum(P[heads], 1), 0).astype(np.uint8)
+    sig = W.SignalTiming(P, cycle, offset, green.ravel(), ephase)
+    veh = rng.integers(0, 60, net.n_edges).astype(np.uint32)
+    red = rng.choice(np.array([0, 1000, 200000], np.uint32), size=(net.n_nodes, 8))
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    ctx.set_red_times(red)
+    onet = orc.Net(net, sig, veh, red)
+    np.testing.assert_array_equal(ctx.phase_order(), orc.queue_preempt(onet))
+    q = Q(0, net.n_nodes - 1, 64, 10, 1.0, 2.0, 0.1, 9)
+    ctx.set_params(flags=gm.FLAG_ANT_LOG)
+    r = ctx.solve_batch([q])[0]
+    _compare(orc, onet, orc.Params(), q, r, ctx, 0, ctx.ant_log(0))
+
+
+def test_grid10_full_parity(gm, ctx, orc):
+    wl = W.grid10()
+    ctx.load_workload(wl)
+    ctx.set_params(flags=gm.FLAG_ANT_LOG)
+    q = wl.queries[0]
+    r = ctx.solve_batch([q])[0]
+    _compare(orc, orc.Net.from_workload(wl), orc.Params(), q, r, ctx, 0, ctx.ant_log(0))
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_grid10_same_result_for_every_lane_count(gm, ctx, orc, lanes):
+    wl = W.grid10(n_ants=48, n_iter=20)
+    ctx.load_workload(wl)
+    ctx.set_params(lanes_per_ant=lanes)
+    r = ctx.solve_batch(wl.queries)[0]
+    _compare(orc, orc.Net.from_workload(wl), orc.Params(), wl.queries[0], r, ctx)
+
+
+@pytest.mark.parametrize("variant", ["random_tau", "threshold", "t_dep", "max_steps", "hsat", "alpha0beta0",
+                                     "alpha2beta3", "no_graph"])
+def test_grid10_variants(gm, ctx, orc, variant):
+    wl = W.grid10(n_ants=32, n_iter=15)
+    ctx.load_workload(wl)
+    q = wl.queries[0]
+    kw, okw = {}, {}
+    if variant == "random_tau":
+        kw["flags"] = okw["flags"] = gm.FLAG_RANDOM_TAU
+    elif variant == "threshold":
+        kw["thr_permille"] = okw["thr_permille"] = 30
+    elif variant == "t_dep":
+        kw["t_dep_ms"] = okw["t_dep_ms"] = 987_654
+    elif variant == "max_steps":
+        kw["max_steps"] = okw["max_steps"] = 20
+    elif variant == "hsat":
+        kw["h_sat_ms"] = okw["h_sat_ms"] = 3100
+    elif variant == "alpha0beta0":
+        q = Q(q.src, q.dst, q.n_ants, q.n_iter, 0.0, 0.0, 0.25, 3)
+    elif variant == "alpha2beta3":
+        q = Q(q.src, q.dst, q.n_ants, q.n_iter, 2.0, 3.0, 0.05, 11)
+    elif variant == "no_graph":
+        kw["flags"] = gm.FLAG_NO_GRAPH
+    ctx.set_params(**kw)
+    r = ctx.solve_batch([q])[0]
+    _compare(orc, orc.Net.from_workload(wl), orc.Params(**okw), q, r, ctx)
+
+
+def test_grid64_batch_parity_reduced(gm, ctx, orc):
+    """Four colonies of 256 ants x 20 iterations in one job; each equals its solo oracle solve."""
+    wl = W.grid64(n_queries=4, n_ants=256, n_iter=20)
+    ctx.load_workload(wl)
+    ctx.set_params(flags=gm.FLAG_ANT_LOG)
+    res = ctx.solve_batch(wl.queries)
+    onet = orc.Net.from_workload(wl)
+    for i, q in enumerate(wl.queries):
+        _compare(orc, onet, orc.Params(), q, res[i], ctx, i, ctx.ant_log(i))
+
+
+def test_ragged_batch_equals_solo(gm, ctx, orc):
+    """Different ants, iterations, alpha/beta/rho and seeds per colony, plus src == dst."""
+    wl = W.grid64(n_queries=5)
+    ctx.load_workload(wl)
+    base = wl.queries
+    qs = [Q(base[0].src, base[0].dst, 96, 7, 1.0, 2.0, 0.1, 5),
+          Q(base[1].src, base[1].dst, 33, 12, 2.0, 1.0, 0.3, 6),
+          Q(base[2].src, base[2].src, 16, 4, 1.0, 2.0, 0.1, 7),
+          Q(base[3].src, base[3].dst, 200, 3, 0.0, 3.0, 0.0, 2**40 + 3),
+          Q(base[4].src, base[4].dst, 1, 25, 1.0, 2.0, 0.5, 9)]
+    res = ctx.solve_batch(qs)
+    onet = orc.Net.from_workload(wl)
+    for i, q in enumerate(qs):
+        _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
+
+
+def test_grid64_full_size_sampled(gm, ctx, orc):
+    """The benchmark's job (16 colonies x 1024 ants x 200 iterations, one launch): three colonies are
+    re-solved by the oracle and must agree exactly, including the final pheromone table."""
+    wl = W.grid64()
+    ctx.load_workload(wl)
+    ctx.set_params(flags=gm.FLAG_KERNEL_TIMING)
+    ctx.stage(wl.queries)
+    ctx.launch()
+    res = ctx.collect()
+    onet = orc.Net.from_workload(wl)
+    for i in (0, 7, 15):
+        _compare(orc, onet, orc.Params(), wl.queries[i], res[i], ctx, i)
+    assert all(r["status"] == 0 for r in res)
+    # a second launch of the staged batch starts from fresh pheromone: identical results
+    ctx.launch()
+    res2 = ctx.collect()
+    for a, b in zip(res, res2):
+        assert a["travel_ms"] == b["travel_ms"] and a["ant_steps"] == b["ant_steps"]
+    kt = ctx.kernel_times()
+    assert kt["construct"] > 0 and kt["job"] >= kt["construct"]
+
+
+def test_large_graph_global_visited_sets(gm, ctx, orc):
+    """A 40k-node planar graph: visited bitmaps no longer fit in shared memory."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    net = W.geometric_network(200, 200, rng)
+    sig = W.two_phase_signals(net, rng.random(net.n_nodes) < 0.6, rng)
+    veh = W.vehicles_poisson(net.n_edges, 1.0, rng)
+    wl = W.Workload("geo40k", net, sig, veh)
+    od = W.hop_filtered_od(net, 2, 20, 60, rng)
+    qs = [Q(s, d, 64, 6, 1.0, 2.0, 0.1, i) for i, (s, d) in enumerate(od)]
+    ctx.load_workload(wl)
+    res = ctx.solve_batch(qs)
+    onet = orc.Net.from_workload(wl)
+    for i, q in enumerate(qs):
+        _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
+
+
+@pytest.mark.parametrize("gseed", range(4))
+def test_tiny_signalised_graphs(gm, ctx, orc, gseed):
+    rng = np.random.Generator(np.random.PCG64(300 + gseed))
+    net, sig = W.random_small(9, 14, rng, signalised_frac=1.0)
+    veh = rng.integers(0, 15, net.n_edges).astype(np.uint32)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    q = Q(0, 8, 40, 12, 1.0, 2.0, 0.1, gseed)
+    r = ctx.solve_batch([q])[0]
+    _compare(orc, orc.Net(net, sig, veh), orc.Params(), q, r, ctx)
+
+
+def test_edge_cases(gm, ctx, orc):
+    net, sig, veh = NB.build(4, [(0, 1, 1000, 50), (1, 2, 1000, 50)])  # node 3 unreachable
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    r = ctx.solve(0, 3, 8, 3)
+    assert r["status"] == gm.ERR_NO_ROUTE and r["ant_steps"] == 3 * 8 * 2
+    r = ctx.solve(2, 2, 8, 3)
+    assert r["status"] == 0 and list(r["route"]) == [2] and r["travel_ms"] == 0 and r["ant_steps"] == 0
+    r = ctx.solve(0, 2, 8, 3, route_cap=2)
+    assert r["status"] == gm.ERR_BUFFER and r["route_len"] == 3
+    with pytest.raises(gm.GmpError) as e:
+        ctx.solve_batch([Q(0, 2, 8, 3, 1.5, 2.0, 0.1, 0)])
+    assert e.value.code == gm.ERR_UNSUPPORTED
+    with pytest.raises(gm.GmpError) as e:
+        ctx.solve_batch([Q(0, 9, 8, 3, 1.0, 2.0, 0.1, 0)])
+    assert e.value.code == gm.ERR_INVALID_ARG
+    with pytest.raises(gm.GmpError) as e:
+        ctx.solve_batch([])
+    assert e.value.code == gm.ERR_INVALID_ARG
+    with pytest.raises(gm.GmpError) as e:
+        ctx.set_params(t_dep_ms=2**30)
+    assert e.value.code == gm.ERR_INVALID_ARG
+
+
+def test_time_cap_and_step_cap(gm, ctx, orc):
+    roads = [(i, i + 1, 10**9, 1) for i in range(17)]
+    net, sig, veh = NB.build(18, roads)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    onet = orc.Net(net, sig, veh)
+    for dst in (16, 17):
+        q = Q(0, dst, 3, 2, 1.0, 2.0, 0.1, 0)
+        _compare(orc, onet, orc.Params(), q, ctx.solve_batch([q])[0], ctx)
+    ctx.set_params(max_steps=5)
+    q = Q(0, 16, 3, 2, 1.0, 2.0, 0.1, 0)
+    _compare(orc, onet, orc.Params(max_steps=5), q, ctx.solve_batch([q])[0], ctx)
+
+
+def test_memory_budget(gm, orc):
+    c = gm.Context(0, mem_budget=1 << 20)
+    wl = W.grid64(n_queries=1)
+    with pytest.raises(gm.GmpError) as e:
+        c.load_workload(wl)
+        c.solve_batch(wl.queries)
+    assert e.value.code == gm.ERR_OOM
+    c.close()
