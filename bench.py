@@ -43,13 +43,24 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="lanes per ant (0 = autotune)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--iterations", type=int, default=0, help="override iterations (profiling runs only)")
+    p.add_argument("--queries", type=int, default=0, help="override colony count (profiling runs only)")
     return p.parse_args()
+
+
+_OVERRIDE = {}
 
 
 def workload():
     from paper_2010_14244_gb300 import workloads
 
-    return workloads.grid64()
+    wl = workloads.grid64()
+    if _OVERRIDE.get("iterations"):
+        for q in wl.queries:
+            q.n_iter = _OVERRIDE["iterations"]
+    if _OVERRIDE.get("queries"):
+        wl.queries = wl.queries[: _OVERRIDE["queries"]]
+    return wl
 
 
 def workload_config(wl):
@@ -307,6 +318,7 @@ def run_gpu(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    _OVERRIDE.update(iterations=args.iterations, queries=args.queries)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
