@@ -23,15 +23,17 @@ using namespace gmp;
 
 namespace {
 
-constexpr uint32_t kKnownFlags = GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | 4u /*kernel timing*/ | 8u /*no graph*/;
-constexpr uint32_t kFlagKernelTiming = 4u;
-constexpr uint32_t kFlagNoGraph = 8u;
+constexpr uint32_t kFlagKernelTiming = 4u;  // event records around every kernel of the job
+constexpr uint32_t kFlagNoGraph = 8u;        // issue the job kernel by kernel instead of replaying a graph
+constexpr uint32_t kFlagNoPrefetch = 16u;    // construction without L1 prefetch of candidate rows
+constexpr uint32_t kKnownFlags =
+    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoPrefetch;
 constexpr int32_t kCoordLimit = 1 << 27;
 
 struct BatchKey {
     uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0;
     uint64_t log_entries = 0;
-    const void* ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    const void* ptrs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
 };
 
@@ -46,6 +48,7 @@ struct Batch {
     uint32_t* prefix = nullptr;
     uint64_t* tau = nullptr;
     unsigned long long* dep = nullptr;
+    uint32_t* heur = nullptr;  // per (colony, road) heuristic table
     QueryState* qs = nullptr;
     uint32_t* routes = nullptr;
     uint32_t* ant_steps = nullptr;
@@ -184,6 +187,7 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.prefix);
     dfree(c, &b.tau);
     dfree(c, &b.dep);
+    dfree(c, &b.heur);
     dfree(c, &b.qs);
     dfree(c, &b.routes);
     dfree(c, &b.ant_steps);
@@ -228,7 +232,7 @@ uint32_t hsat_of(const gmp_ctx* c) { return c->prm.h_sat_ms ? c->prm.h_sat_ms : 
 // Densities or signals or params changed: rebuild road records and the phase order.
 int refresh_dynamic(gmp_ctx* c) {
     GMP_CUDA(c, launch_edge_dynamic(c->stream, c->E, c->row_ptr, c->col, c->ff, c->cap, c->lanes, c->veh, c->nph,
-                                    c->x, c->y, hsat_of(c), c->prm.thr_permille, c->rec));
+                                    hsat_of(c), c->prm.thr_permille, c->rec));
     GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
                                      c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
     return GMP_OK;
@@ -247,8 +251,8 @@ uint32_t default_max_steps(const gmp_ctx* c) {
 
 int pick_lanes(const gmp_ctx* c) {
     if (c->prm.lanes_per_ant) return (int)c->prm.lanes_per_ant;
-    for (int g : {4, 8, 16, 32})
-        if ((uint32_t)construct_max_degree(g) >= c->maxdeg) return g;
+    for (int g : {4, 8, 16, 32})  // one candidate slot per lane when the degree allows
+        if ((uint32_t)g >= c->maxdeg) return g;
     return 32;
 }
 
@@ -277,8 +281,8 @@ int enqueue_job(gmp_ctx* c) {
     const bool timed = b.timed;
     uint64_t n = 0;
     if (timed) GMP_TRY(record(c, b, 0));
-    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.dep, b.qs,
-                                  b.tickets, b.maxI));
+    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.dep,
+                                  b.heur, b.qs, b.tickets, b.maxI));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
     ConstructArgs a{};
@@ -288,6 +292,7 @@ int enqueue_job(gmp_ctx* c) {
     a.queries = b.dq;
     a.ant_prefix = b.prefix;
     a.tau = b.tau;
+    a.hq = b.heur;
     a.dep = b.dep;
     a.qs = b.qs;
     a.routes = b.routes;
@@ -305,6 +310,7 @@ int enqueue_job(gmp_ctx* c) {
     a.thr_on = c->prm.thr_permille != kThrOff;
     a.tabu_in_smem = b.kc.tabu_in_smem ? 1u : 0u;
     a.kappa = c->kappa;
+    a.no_prefetch = (c->prm.flags & kFlagNoPrefetch) ? 1u : 0u;
     for (uint32_t it = 0; it < b.maxI; ++it) {
         GMP_CUDA(c, launch_construct(s, b.kc, a, it));
         if (timed) GMP_TRY(record(c, b, 2 + 4 * (size_t)it));
@@ -334,7 +340,7 @@ BatchKey key_of(const gmp_ctx* c) {
     k.total_ants = b.total_ants;
     k.max_steps = b.max_steps;
     k.flags = c->prm.flags;
-    k.lanes = (uint32_t)b.kc.lanes;
+    k.lanes = (uint32_t)(b.kc.lanes * 16 + b.kc.slots);
     k.grid = (uint32_t)b.kc.grid;
     k.thr_on = c->prm.thr_permille != kThrOff;
     k.t_dep = c->prm.t_dep_ms;
@@ -343,6 +349,7 @@ BatchKey key_of(const gmp_ctx* c) {
     k.ptrs[1] = b.routes;
     k.ptrs[2] = b.tabu;
     k.ptrs[3] = c->rec;
+    k.ptrs[4] = b.heur;
     return k;
 }
 
@@ -586,7 +593,7 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     if (n == 0) return fail(c, GMP_ERR_INVALID_ARG, "empty batch");
     for (uint32_t i = 0; i < n; ++i) GMP_TRY(check_query(c, queries[i], i));
     const int lanes = pick_lanes(c);
-    if ((uint32_t)construct_max_degree(lanes) < c->maxdeg)
+    if ((uint32_t)construct_max_degree(lanes) < c->maxdeg || c->maxdeg > 128u)
         return fail(c, GMP_ERR_UNSUPPORTED, "out-degree %u exceeds %d for %d lanes per ant", c->maxdeg,
                     construct_max_degree(lanes), lanes);
     cudaSetDevice(c->device);
@@ -628,12 +635,13 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.total_ants = (uint32_t)total;
     b.maxI = maxI;
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
-    GMP_CUDA(c, construct_config(c->device, lanes, c->N, b.total_ants, &b.kc));
+    GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, b.total_ants, &b.kc));
     const size_t words = (c->N + 31u) / 32u;
     GMP_TRY(ensure(c, &b.dq, n));
     GMP_TRY(ensure(c, &b.prefix, n + 1));
     GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.heur, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.qs, n));
     GMP_TRY(ensure(c, &b.routes, (size_t)b.total_ants * b.max_steps));
     GMP_TRY(ensure(c, &b.ant_steps, b.total_ants));

@@ -21,8 +21,9 @@ constexpr uint64_t kNoKey = ~0ull;
 enum : uint32_t { kAntSuccess = 0, kAntDeadEnd = 1, kAntStepCap = 2, kAntTimeCap = 3 };
 
 // Per-road record read by the construction kernel: everything one candidate needs in three 16-byte
-// loads (the head's CSR row, congested time, the head signal's green window for this approach, the
-// head's coordinates). Rebuilt whenever densities, signals or the phase order change.
+// loads (the head's CSR row, congested time, queue delay, the head signal's green window for this
+// approach and a reciprocal for reducing arrival times modulo the cycle). Rebuilt whenever densities,
+// signals or the phase order change.
 struct __align__(16) EdgeRec {
     uint32_t head;   // v
     uint32_t vbeg;   // first road out of v
@@ -32,7 +33,7 @@ struct __align__(16) EdgeRec {
     uint32_t cycle;  // cycle of v's signal, 0 = unsignalised
     uint32_t gbeg;   // start of this approach's green window, (offset + start in phase order) mod cycle
     uint32_t glen;   // green time of this approach's phase
-    int32_t hx, hy;  // coordinates of v, dm
+    unsigned long long cmagic;  // floor((2^64 - 1) / cycle), 0 when unsignalised
     uint32_t flags;  // bit 0: road over the congestion threshold
     uint32_t pad;
 };
@@ -104,28 +105,44 @@ __device__ __forceinline__ uint32_t heuristic_ms(int32_t x, int32_t y, int32_t x
     return h > kHClamp ? kHClamp : (uint32_t)h;
 }
 
+// x mod d for x < 2^32 and 1 <= d <= 2^24, with m = floor((2^64 - 1) / d): the quotient estimate
+// floor(x * m / 2^64) is exact or one too small, so one conditional subtraction finishes it.
+__device__ __forceinline__ uint32_t mod_magic(uint32_t x, uint32_t d, unsigned long long m) {
+    const uint32_t q = (uint32_t)__umul64hi((unsigned long long)x, m);
+    const uint32_t r = x - q * d;
+    return r >= d ? r - d : r;
+}
+
 // Signal wait for a vehicle reaching the stop line at absolute time arr: the approach is green during
 // [gbeg, gbeg + glen) modulo the cycle; otherwise it waits for the next start of that window.
-__device__ __forceinline__ uint32_t signal_wait(uint32_t arr, uint32_t cycle, uint32_t gbeg, uint32_t glen) {
-    const uint32_t x = arr % cycle;
+__device__ __forceinline__ uint32_t signal_wait(uint32_t arr, uint32_t cycle, unsigned long long cmagic,
+                                                uint32_t gbeg, uint32_t glen) {
+    const uint32_t x = mod_magic(arr, cycle, cmagic);
     const uint32_t c = x >= gbeg ? x - gbeg : x + (cycle - gbeg);
     return c < glen ? 0u : cycle - c;
 }
 
+// x^k for 0 <= k <= 8 by repeated multiplication left to right (x^0 = 1), without branches.
 __device__ __forceinline__ float pow_int(float x, uint32_t k) {
-    float p = 1.0f;
-    if (k > 0) {
-        p = x;
-        for (uint32_t i = 1; i < k; ++i) p = __fmul_rn(p, x);
+    float p = k ? x : 1.0f;
+#pragma unroll
+    for (uint32_t i = 2; i <= 8; ++i) {
+        const float y = __fmul_rn(p, x);
+        p = i <= k ? y : p;
     }
     return p;
 }
 
 // Next-node desirability: (tau / 2^32)^alpha * (1 / c)^beta, c = travel + wait + remaining bound (ms).
+// __frcp_rn(c) is 1/c rounded to nearest, the same value as the division 1.0f / c.
 __device__ __forceinline__ float score(uint64_t tau, uint32_t alpha, uint32_t c, uint32_t beta) {
     const float tf = __fmul_rn(__ull2float_rn(tau), 0x1p-32f);
-    const float eta = __fdiv_rn(1.0f, __uint2float_rn(c));
+    const float eta = __frcp_rn(__uint2float_rn(c));
     return __fmul_rn(pow_int(tf, alpha), pow_int(eta, beta));
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 // A non-negative binary32 value as mant * 2^(ex - 150) with mant in [2^23, 2^24) (subnormals

@@ -20,6 +20,7 @@ struct ConstructArgs {
     const DevQuery* queries;
     const uint32_t* ant_prefix;  // Q + 1 entries: first global ant of each query
     const uint64_t* tau;         // Q * E
+    const uint32_t* hq;          // Q * E heuristic of each road's head towards the colony's destination
     unsigned long long* dep;     // Q * E deposit accumulators
     QueryState* qs;
     uint32_t* routes;            // total_ants * max_steps road ids
@@ -31,10 +32,12 @@ struct ConstructArgs {
     uint32_t n_queries, total_ants, n_edges, max_steps;
     uint32_t tabu_words, t_dep, thr_on, tabu_in_smem;
     uint32_t kappa;              // floor(360 * 2^16 / v_max)
+    uint32_t no_prefetch;        // 1: skip the L1 prefetch of candidate rows
 };
 
 struct KernelConfig {
     int lanes;             // lanes per ant (G)
+    int slots;             // candidate slots per lane (K)
     int block;             // threads per block
     int grid;              // blocks
     size_t smem;           // dynamic shared memory per block
@@ -46,15 +49,15 @@ cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* len, 
                                const uint8_t* lanes, uint32_t* ff, uint32_t* cap);
 cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
                                 const uint32_t* ff, const uint32_t* cap, const uint8_t* lanes, const uint32_t* veh,
-                                const uint8_t* nph, const int32_t* x, const int32_t* y, uint32_t h_sat,
-                                uint32_t thr, EdgeRec* rec);
+                                const uint8_t* nph, uint32_t h_sat, uint32_t thr, EdgeRec* rec);
 cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_ptr, const uint32_t* in_edge,
                                  const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
                                  const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec);
-cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const int32_t* x,
-                              const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
-                              unsigned long long* dep, QueryState* qs, uint32_t* tickets, uint32_t n_tickets);
+cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
+                              const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
+                              unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
+                              uint32_t n_tickets);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
 cudaError_t launch_evaporate(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, uint64_t* tau,
                              unsigned long long* dep, uint32_t it);
@@ -66,7 +69,8 @@ cudaError_t launch_finalize(cudaStream_t s, uint32_t Q, const DevQuery* q, const
                             uint32_t* route_out);
 
 // Occupancy-derived configuration for a lane count and graph size.
-cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out);
+cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, uint32_t total_ants,
+                             KernelConfig* out);
 int construct_max_degree(int lanes);
 
 }  // namespace gmp

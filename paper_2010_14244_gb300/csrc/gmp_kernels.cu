@@ -34,8 +34,8 @@ __global__ void k_edge_static(uint32_t E, const uint32_t* __restrict__ len, cons
 __global__ void k_edge_dynamic(uint32_t E, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
                                const uint32_t* __restrict__ ff, const uint32_t* __restrict__ cap,
                                const uint8_t* __restrict__ lanes, const uint32_t* __restrict__ veh,
-                               const uint8_t* __restrict__ nph, const int32_t* __restrict__ x,
-                               const int32_t* __restrict__ y, uint32_t h_sat, uint32_t thr, EdgeRec* __restrict__ rec) {
+                               const uint8_t* __restrict__ nph, uint32_t h_sat, uint32_t thr,
+                               EdgeRec* __restrict__ rec) {
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const uint32_t v = col[e], n = veh[e], c = cap[e];
@@ -50,8 +50,6 @@ __global__ void k_edge_dynamic(uint32_t E, const uint32_t* __restrict__ row_ptr,
         qd = d > kTimeClamp ? kTimeClamp : (uint32_t)d;
     }
     r.qd = qd;
-    r.hx = x[v];
-    r.hy = y[v];
     r.flags = (thr != kThrOff && (uint64_t)n * 1000u > (uint64_t)thr * c) ? 1u : 0u;
     r.pad = 0;
 }
@@ -80,6 +78,7 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
             r.cycle = 0;
             r.gbeg = 0;
             r.glen = 0;
+            r.cmagic = 0;
         }
         return;
     }
@@ -146,6 +145,7 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
     }
     for (uint32_t i = P; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
     const uint32_t off = offset[v];
+    const unsigned long long magic = ~0ull / cy;
     for (uint32_t i = ib; i < ie; ++i) {
         const uint32_t e = in_edge[i];
         const uint32_t p = ephase[e] & (kMaxPhases - 1);
@@ -153,26 +153,32 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
         r.cycle = cy;
         r.gbeg = (off + start[p]) % cy;
         r.glen = green[(size_t)v * kMaxPhases + p];
+        r.cmagic = magic;
     }
 }
 
 // ------------------------------------------------------------------------------------------------
 // Batch initialisation: pheromone 1.0 (or Philox-random in [0.5, 1.5)), deposits zero, colony state.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const int32_t* __restrict__ x,
-                             const int32_t* __restrict__ y, uint32_t kappa, uint32_t flags, uint64_t* __restrict__ tau,
-                             unsigned long long* __restrict__ dep, QueryState* __restrict__ qs,
-                             uint32_t* __restrict__ tickets, uint32_t n_tickets) {
+// Calc_Dist for the whole colony up front: hq[e] = h(head(e)) towards this colony's destination.
+__global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
+                             const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
+                             uint32_t flags, uint64_t* __restrict__ tau, unsigned long long* __restrict__ dep,
+                             uint32_t* __restrict__ hq, QueryState* __restrict__ qs, uint32_t* __restrict__ tickets,
+                             uint32_t n_tickets) {
     const uint32_t qi = blockIdx.y;
     const DevQuery Q = q[qi];
     uint64_t* T = tau + (size_t)qi * E;
     unsigned long long* D = dep + (size_t)qi * E;
+    uint32_t* H = hq + (size_t)qi * E;
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         uint64_t t0 = 1ull << 32;
         if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
         T[e] = t0;
         D[e] = 0;
+        const uint32_t v = col[e];
+        H[e] = heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const uint32_t h = heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
@@ -200,7 +206,9 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const i
 template <int G, int K>
 __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery& q, uint32_t qi, uint32_t k,
                                          uint32_t it, uint32_t* tabu, uint32_t lane, uint32_t gmask, uint32_t gbase) {
-    const uint64_t* __restrict__ tau = a.tau + (size_t)qi * a.n_edges;
+    const unsigned long long* __restrict__ tau = reinterpret_cast<const unsigned long long*>(a.tau) +
+                                                 (size_t)qi * a.n_edges;
+    const uint32_t* __restrict__ hq = a.hq + (size_t)qi * a.n_edges;
     const uint32_t slot = q.ant_base + k;
     uint32_t* route = a.routes + (size_t)slot * a.max_steps;
     const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
@@ -219,29 +227,59 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             break;
         }
         const uint32_t deg = end - beg;
-        uint32_t cmask = 0, cong = 0;
-        uint32_t sb[K], hv[K], vb[K], ve[K], tv[K], wv[K];
+        const int nslots = K == 1 ? 1 : (int)((deg + G - 1) / G);  // group-uniform
+        // 1. issue every load of this step: records, pheromone and heuristic of this lane's candidates
+        uint4 r0[K], r1[K], r2[K];
+        unsigned long long te[K];
+        uint32_t he[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            sb[j] = hv[j] = vb[j] = ve[j] = tv[j] = wv[j] = 0;
             const uint32_t idx = lane + (uint32_t)j * G;
-            if (idx < deg) {
+            if (j < nslots && idx < deg) {
                 const uint4* rp = reinterpret_cast<const uint4*>(a.rec + beg + idx);
-                const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
-                const uint64_t te = __ldg(reinterpret_cast<const unsigned long long*>(tau) + beg + idx);
-                hv[j] = r0.x;
-                vb[j] = r0.y;
-                ve[j] = r0.z;
-                tv[j] = r0.w;
-                const bool visited = (tabu[r0.x >> 5] >> (r0.x & 31)) & 1u;
+                r0[j] = __ldg(rp);
+                r1[j] = __ldg(rp + 1);
+                r2[j] = __ldg(rp + 2);
+                te[j] = __ldg(tau + beg + idx);
+                he[j] = __ldg(hq + beg + idx);
+            } else {
+                r0[j] = r1[j] = r2[j] = make_uint4(0, 0, 0, 0);
+                te[j] = 0;
+                he[j] = 0;
+            }
+        }
+        // 2. the draw of this step depends on (iteration, ant, step) only: overlaps the loads
+        const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
+        const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+        // 3. candidates, waits, scores
+        uint32_t cmask = 0, cong = 0;
+        uint32_t sb[K], wv[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            sb[j] = wv[j] = 0;
+            const uint32_t idx = lane + (uint32_t)j * G;
+            if (j < nslots && idx < deg) {
+                const uint32_t v = r0[j].x;
+                const bool visited = (tabu[v >> 5] >> (v & 31)) & 1u;
                 if (!visited) {
+                    if (!a.no_prefetch && r0[j].z > r0[j].y) {  // the next step reads one of these rows
+                        const char* b0 = reinterpret_cast<const char*>(a.rec + r0[j].y);
+                        const char* b1 = reinterpret_cast<const char*>(a.rec + r0[j].z) - 1;
+                        for (const char* p = b0; p <= b1; p += 128) prefetch_l1(p);
+                        prefetch_l1(b1);
+                        prefetch_l1(tau + r0[j].y);
+                        prefetch_l1(hq + r0[j].y);
+                    }
                     cmask |= 1u << j;
-                    if (r2.z & 1u) cong |= 1u << j;
+                    if (r2[j].z & 1u) cong |= 1u << j;
                     uint32_t w = 0;
-                    if (r0.x != q.dst && r1.y != 0) w = signal_wait(a.t_dep + t + r0.w, r1.y, r1.z, r1.w) + r1.x;
-                    const uint32_t h = heuristic_ms((int32_t)r2.x, (int32_t)r2.y, q.xd, q.yd, a.kappa);
+                    const uint32_t cy = r1[j].y;
+                    if (v != q.dst && cy != 0) {
+                        const unsigned long long mg = (unsigned long long)r2[j].x | ((unsigned long long)r2[j].y << 32);
+                        w = signal_wait(a.t_dep + t + r0[j].w, cy, mg, r1[j].z, r1[j].w) + r1[j].x;
+                    }
                     wv[j] = w;
-                    sb[j] = __float_as_uint(score(te, q.alpha, r0.w + w + h, q.beta));
+                    sb[j] = __float_as_uint(score(te[j], q.alpha, r0[j].w + w + he[j], q.beta));
                 }
             }
         }
@@ -254,7 +292,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             status = kAntDeadEnd;
             break;
         }
-        // largest score of the group (non-negative floats order like their bit patterns)
+        // 4. largest score of the group (non-negative floats order like their bit patterns)
         uint32_t mb = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j)
@@ -264,23 +302,28 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         uint32_t mmant;
         int mex;
         split_f32(mb, mmant, mex);
-        // integer weights and their inclusive prefix in CSR order (index lane + j*G)
+        // 5. integer weights and their inclusive prefix in CSR order (index lane + j*G)
         unsigned long long carry = 0, incl[K];
         uint32_t wt[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            wt[j] = (cmask >> j & 1u) ? roulette_weight(sb[j], mmant, mex) : 0u;
-            unsigned long long xs = wt[j];
+            wt[j] = 0;
+            incl[j] = carry;
+            if (j < nslots) {
+                wt[j] = (cmask >> j & 1u) ? roulette_weight(sb[j], mmant, mex) : 0u;
+                unsigned long long xs = wt[j];
 #pragma unroll
-            for (int d = 1; d < G; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(gmask, xs, d, G);
-                if (lane >= (uint32_t)d) xs += y;
+                for (int d = 1; d < G; d <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(gmask, xs, d, G);
+                    if (lane >= (uint32_t)d) xs += y;
+                }
+                incl[j] = carry + xs;
+                if (j + 1 < K) carry += __shfl_sync(gmask, xs, G - 1, G);
+                else carry = __shfl_sync(gmask, incl[j], G - 1, G);
             }
-            incl[j] = carry + xs;
-            carry += __shfl_sync(gmask, xs, G - 1, G);
         }
-        const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
-        const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+        if (K > 1) carry = __shfl_sync(gmask, incl[K - 1], G - 1, G);
+        // 6. roulette: first candidate whose running weight exceeds r = floor(rnd * S / 2^64)
         const unsigned long long r = __umul64hi(rnd, carry);
         int js = -1;
 #pragma unroll
@@ -293,10 +336,10 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         for (int j = 0; j < K; ++j)
             if (js == j) {
                 c_idx = lane + (uint32_t)j * G;
-                c_h = hv[j];
-                c_vb = vb[j];
-                c_ve = ve[j];
-                c_tt = tv[j];
+                c_h = r0[j].x;
+                c_vb = r0[j].y;
+                c_ve = r0[j].z;
+                c_tt = r0[j].w;
                 c_w = wv[j];
             }
         c_idx = __shfl_sync(gmask, c_idx, src_lane, G);
@@ -305,6 +348,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         c_ve = __shfl_sync(gmask, c_ve, src_lane, G);
         c_tt = __shfl_sync(gmask, c_tt, src_lane, G);
         c_w = __shfl_sync(gmask, c_w, src_lane, G);
+        // 7. position update
         const uint32_t e = beg + c_idx;
         t += c_tt + c_w;
         W += c_w;
@@ -463,11 +507,9 @@ cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* len, 
 
 cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
                                 const uint32_t* ff, const uint32_t* cap, const uint8_t* lanes, const uint32_t* veh,
-                                const uint8_t* nph, const int32_t* x, const int32_t* y, uint32_t h_sat,
-                                uint32_t thr, EdgeRec* rec) {
+                                const uint8_t* nph, uint32_t h_sat, uint32_t thr, EdgeRec* rec) {
     if (E == 0) return cudaSuccess;
-    k_edge_dynamic<<<blocks_for(E, 256), 256, 0, s>>>(E, row_ptr, col, ff, cap, lanes, veh, nph, x, y, h_sat, thr,
-                                                      rec);
+    k_edge_dynamic<<<blocks_for(E, 256), 256, 0, s>>>(E, row_ptr, col, ff, cap, lanes, veh, nph, h_sat, thr, rec);
     return cudaGetLastError();
 }
 
@@ -481,11 +523,12 @@ cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const int32_t* x,
-                              const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
-                              unsigned long long* dep, QueryState* qs, uint32_t* tickets, uint32_t n_tickets) {
+cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
+                              const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
+                              unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
+                              uint32_t n_tickets) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
-    k_init_batch<<<grid, 256, 0, s>>>(E, q, x, y, kappa, flags, tau, dep, qs, tickets, n_tickets);
+    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, dep, hq, qs, tickets, n_tickets);
     return cudaGetLastError();
 }
 
@@ -535,6 +578,7 @@ static cudaError_t config_for(int device, uint32_t n_nodes, uint32_t total_ants,
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
     out->lanes = G;
+    out->slots = K;
     out->block = block;
     out->grid = (int)grid;
     out->smem = dyn;
@@ -542,35 +586,36 @@ static cudaError_t config_for(int device, uint32_t n_nodes, uint32_t total_ants,
     return cudaSuccess;
 }
 
-cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out) {
-    switch (lanes) {
-        case 4: return config_for<4, 2>(device, n_nodes, total_ants, out);
-        case 8: return config_for<8, 2>(device, n_nodes, total_ants, out);
-        case 16: return config_for<16, 2>(device, n_nodes, total_ants, out);
-        case 32: return config_for<32, 4>(device, n_nodes, total_ants, out);
-        default: return cudaErrorInvalidValue;
-    }
+// Candidate slots per lane: the fewest of {1, 2, 4} that cover the largest out-degree.
+static int slots_for(int lanes, uint32_t max_degree) {
+    for (int k : {1, 2, 4})
+        if ((uint32_t)(lanes * k) >= max_degree) return k;
+    return 0;
 }
 
-int construct_max_degree(int lanes) {
-    switch (lanes) {
-        case 4: return 8;
-        case 8: return 16;
-        case 16: return 32;
-        case 32: return 128;
-        default: return 0;
-    }
+int construct_max_degree(int lanes) { return lanes * 4; }
+
+cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, uint32_t total_ants,
+                             KernelConfig* out) {
+    const int k = slots_for(lanes, max_degree);
+#define GMP_CFG(G_, K_) \
+    if (lanes == G_ && k == K_) return config_for<G_, K_>(device, n_nodes, total_ants, out);
+    GMP_CFG(4, 1) GMP_CFG(4, 2) GMP_CFG(4, 4) GMP_CFG(8, 1) GMP_CFG(8, 2) GMP_CFG(8, 4)
+    GMP_CFG(16, 1) GMP_CFG(16, 2) GMP_CFG(16, 4) GMP_CFG(32, 1) GMP_CFG(32, 2) GMP_CFG(32, 4)
+#undef GMP_CFG
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it) {
-    switch (kc.lanes) {
-        case 4: k_construct<4, 2><<<kc.grid, kc.block, kc.smem, s>>>(a, it); break;
-        case 8: k_construct<8, 2><<<kc.grid, kc.block, kc.smem, s>>>(a, it); break;
-        case 16: k_construct<16, 2><<<kc.grid, kc.block, kc.smem, s>>>(a, it); break;
-        case 32: k_construct<32, 4><<<kc.grid, kc.block, kc.smem, s>>>(a, it); break;
-        default: return cudaErrorInvalidValue;
+#define GMP_LAUNCH(G_, K_)                                                    \
+    if (kc.lanes == G_ && kc.slots == K_) {                                   \
+        k_construct<G_, K_><<<kc.grid, kc.block, kc.smem, s>>>(a, it);        \
+        return cudaGetLastError();                                            \
     }
-    return cudaGetLastError();
+    GMP_LAUNCH(4, 1) GMP_LAUNCH(4, 2) GMP_LAUNCH(4, 4) GMP_LAUNCH(8, 1) GMP_LAUNCH(8, 2) GMP_LAUNCH(8, 4)
+    GMP_LAUNCH(16, 1) GMP_LAUNCH(16, 2) GMP_LAUNCH(16, 4) GMP_LAUNCH(32, 1) GMP_LAUNCH(32, 2) GMP_LAUNCH(32, 4)
+#undef GMP_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gmp
