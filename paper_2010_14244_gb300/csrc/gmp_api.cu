@@ -25,15 +25,15 @@ namespace {
 
 constexpr uint32_t kFlagKernelTiming = 4u;  // event records around every kernel of the job
 constexpr uint32_t kFlagNoGraph = 8u;        // issue the job kernel by kernel instead of replaying a graph
-constexpr uint32_t kFlagNoPrefetch = 16u;    // construction without L1 prefetch of candidate rows
+constexpr uint32_t kFlagNoLockstep = 16u;    // sub-warp ants without warp lockstep (for comparison)
 constexpr uint32_t kKnownFlags =
-    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoPrefetch;
+    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
 constexpr int32_t kCoordLimit = 1 << 27;
 
 struct BatchKey {
     uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0;
     uint64_t log_entries = 0;
-    const void* ptrs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
 };
 
@@ -47,6 +47,7 @@ struct Batch {
     DevQuery* dq = nullptr;
     uint32_t* prefix = nullptr;
     uint64_t* tau = nullptr;
+    float* tauf = nullptr;
     unsigned long long* dep = nullptr;
     uint32_t* heur = nullptr;  // per (colony, road) heuristic table
     QueryState* qs = nullptr;
@@ -59,6 +60,12 @@ struct Batch {
     uint32_t* ant_log = nullptr;
     uint32_t* tabu = nullptr;
     DevResult* res = nullptr;
+    // persistent job
+    bool persistent = false;
+    IterCounters* ctr = nullptr;
+    uint32_t* qstate = nullptr;
+    uint32_t* qflag = nullptr;
+    uint32_t* misc = nullptr;
     // captured job
     cudaGraphExec_t exec = nullptr;
     BatchKey key{};
@@ -186,6 +193,7 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.dq);
     dfree(c, &b.prefix);
     dfree(c, &b.tau);
+    dfree(c, &b.tauf);
     dfree(c, &b.dep);
     dfree(c, &b.heur);
     dfree(c, &b.qs);
@@ -198,6 +206,10 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.ant_log);
     dfree(c, &b.tabu);
     dfree(c, &b.res);
+    dfree(c, &b.ctr);
+    dfree(c, &b.qstate);
+    dfree(c, &b.qflag);
+    dfree(c, &b.misc);
     b.staged = b.ran = false;
 }
 
@@ -251,7 +263,7 @@ uint32_t default_max_steps(const gmp_ctx* c) {
 
 int pick_lanes(const gmp_ctx* c) {
     if (c->prm.lanes_per_ant) return (int)c->prm.lanes_per_ant;
-    for (int g : {4, 8, 16, 32})  // one candidate slot per lane when the degree allows
+    for (int g : {8, 16, 32})  // one candidate slot per lane when the degree allows
         if ((uint32_t)g >= c->maxdeg) return g;
     return 32;
 }
@@ -274,17 +286,52 @@ int record(gmp_ctx* c, Batch& b, size_t i) {
     return GMP_OK;
 }
 
-// Issue the whole job on the stream (inside a capture or directly).
-int enqueue_job(gmp_ctx* c) {
+ConstructArgs construct_args(gmp_ctx* c);
+
+// The persistent job: init, one persistent launch, result rows.
+int enqueue_persistent(gmp_ctx* c) {
     Batch& b = c->b;
     cudaStream_t s = c->stream;
     const bool timed = b.timed;
-    uint64_t n = 0;
     if (timed) GMP_TRY(record(c, b, 0));
-    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.dep,
-                                  b.heur, b.qs, b.tickets, b.maxI));
-    ++n;
+    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.tauf,
+                                  b.dep, b.heur, b.qs, b.tickets, b.maxI));
+    GMP_CUDA(c, launch_persistent_init(s, b.Q, b.maxI, b.dq, b.ctr, b.qstate, b.qflag, b.misc));
     if (timed) GMP_TRY(record(c, b, 1));
+    PersistentArgs p{};
+    p.c = construct_args(c);
+    p.ctr = b.ctr;
+    p.qstate = b.qstate;
+    p.qflag = b.qflag;
+    p.misc = b.misc;
+    p.tau = b.tau;
+    p.tauf = b.tauf;
+    p.best_route = b.best_route;
+    p.in_ptr = c->in_ptr;
+    p.in_edge = c->in_edge;
+    p.nph = c->nph;
+    p.cycle = c->cycle;
+    p.offset = c->offset;
+    p.green = c->green;
+    p.ephase = c->ephase;
+    p.veh = c->veh;
+    p.cap = c->cap;
+    p.red = c->red;
+    p.order = c->order;
+    p.rec = c->rec;
+    p.n_nodes = c->N;
+    p.max_iter = b.maxI;
+    p.spin_limit = 1u << 23;  // idle polls of ~0.3 us each (seconds) before the job reports a timeout
+    GMP_CUDA(c, launch_persistent(s, b.kc, p));
+    if (timed) GMP_TRY(record(c, b, 2));
+    GMP_CUDA(c, launch_finalize(s, b.Q, b.dq, b.qs, b.best_route, c->col, b.max_steps, b.res, b.route_out));
+    if (timed) GMP_TRY(record(c, b, 3));
+    b.launches = 4;
+    return GMP_OK;
+}
+
+ConstructArgs construct_args(gmp_ctx* c) {
+    Batch& b = c->b;
     ConstructArgs a{};
     a.rec = c->rec;
     a.row_ptr = c->row_ptr;
@@ -292,6 +339,7 @@ int enqueue_job(gmp_ctx* c) {
     a.queries = b.dq;
     a.ant_prefix = b.prefix;
     a.tau = b.tau;
+    a.tauf = b.tauf;
     a.hq = b.heur;
     a.dep = b.dep;
     a.qs = b.qs;
@@ -310,11 +358,26 @@ int enqueue_job(gmp_ctx* c) {
     a.thr_on = c->prm.thr_permille != kThrOff;
     a.tabu_in_smem = b.kc.tabu_in_smem ? 1u : 0u;
     a.kappa = c->kappa;
-    a.no_prefetch = (c->prm.flags & kFlagNoPrefetch) ? 1u : 0u;
+    return a;
+}
+
+// Issue the whole job on the stream (inside a capture or directly).
+int enqueue_job(gmp_ctx* c) {
+    Batch& b = c->b;
+    if (b.persistent) return enqueue_persistent(c);
+    cudaStream_t s = c->stream;
+    const bool timed = b.timed;
+    uint64_t n = 0;
+    if (timed) GMP_TRY(record(c, b, 0));
+    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.tauf,
+                                  b.dep, b.heur, b.qs, b.tickets, b.maxI));
+    ++n;
+    if (timed) GMP_TRY(record(c, b, 1));
+    const ConstructArgs a = construct_args(c);
     for (uint32_t it = 0; it < b.maxI; ++it) {
         GMP_CUDA(c, launch_construct(s, b.kc, a, it));
         if (timed) GMP_TRY(record(c, b, 2 + 4 * (size_t)it));
-        GMP_CUDA(c, launch_evaporate(s, b.Q, c->E, b.dq, b.tau, b.dep, it));
+        GMP_CUDA(c, launch_evaporate(s, b.Q, c->E, b.dq, b.tau, b.tauf, b.dep, it));
         if (timed) GMP_TRY(record(c, b, 3 + 4 * (size_t)it));
         GMP_CUDA(c, launch_best_copy(s, b.Q, b.dq, b.qs, b.routes, b.ant_steps, b.ant_wait, b.best_route,
                                      b.max_steps, it));
@@ -340,7 +403,8 @@ BatchKey key_of(const gmp_ctx* c) {
     k.total_ants = b.total_ants;
     k.max_steps = b.max_steps;
     k.flags = c->prm.flags;
-    k.lanes = (uint32_t)(b.kc.lanes * 16 + b.kc.slots);
+    k.lanes = (uint32_t)(b.kc.lanes * 16 + b.kc.slots) | (b.kc.lockstep ? 0x10000u : 0u) |
+              (b.persistent ? 0x20000u : 0u);
     k.grid = (uint32_t)b.kc.grid;
     k.thr_on = c->prm.thr_permille != kThrOff;
     k.t_dep = c->prm.t_dep_ms;
@@ -350,6 +414,7 @@ BatchKey key_of(const gmp_ctx* c) {
     k.ptrs[2] = b.tabu;
     k.ptrs[3] = c->rec;
     k.ptrs[4] = b.heur;
+    k.ptrs[5] = b.tauf;
     return k;
 }
 
@@ -566,9 +631,9 @@ int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
     if (!c || !p) return GMP_ERR_INVALID_ARG;
     if (p->flags & ~kKnownFlags) return fail(c, GMP_ERR_INVALID_ARG, "unknown flag bits");
     if (p->t_dep_ms >= kTCap) return fail(c, GMP_ERR_INVALID_ARG, "t_dep_ms must be below 2^30");
-    if (p->lanes_per_ant && p->lanes_per_ant != 4 && p->lanes_per_ant != 8 && p->lanes_per_ant != 16 &&
-        p->lanes_per_ant != 32)
-        return fail(c, GMP_ERR_INVALID_ARG, "lanes_per_ant must be 0, 4, 8, 16 or 32");
+    if (p->lanes_per_ant && p->lanes_per_ant != 1 && p->lanes_per_ant != 4 && p->lanes_per_ant != 8 &&
+        p->lanes_per_ant != 16 && p->lanes_per_ant != 32)
+        return fail(c, GMP_ERR_INVALID_ARG, "lanes_per_ant must be 0, 1, 4, 8, 16 or 32");
     if (p->mode > GMP_MODE_PERSISTENT) return fail(c, GMP_ERR_INVALID_ARG, "unknown mode");
     if (p->max_steps > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "max_steps must be <= 2^24");
     const bool dyn = p->thr_permille != c->prm.thr_permille || p->h_sat_ms != c->prm.h_sat_ms;
@@ -596,6 +661,9 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     if ((uint32_t)construct_max_degree(lanes) < c->maxdeg || c->maxdeg > 128u)
         return fail(c, GMP_ERR_UNSUPPORTED, "out-degree %u exceeds %d for %d lanes per ant", c->maxdeg,
                     construct_max_degree(lanes), lanes);
+    if (lanes == 1 && !construct_thread_fits(c->N))
+        return fail(c, GMP_ERR_UNSUPPORTED, "one thread per ant needs the visited bitmaps in shared memory "
+                                            "(N <= 25600)");
     cudaSetDevice(c->device);
     GMP_TRY(sync(c));
     Batch& b = c->b;
@@ -635,11 +703,22 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.total_ants = (uint32_t)total;
     b.maxI = maxI;
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
-    GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, b.total_ants, &b.kc));
+    b.kc = KernelConfig{};
+    b.persistent = c->prm.mode == GMP_MODE_PERSISTENT;
+    if (b.persistent) {
+        if (lanes == 1) return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs 4, 8, 16 or 32 lanes per ant");
+        GMP_CUDA(c, persistent_config(c->device, lanes, c->N, c->maxdeg, &b.kc));
+    } else if (lanes != 1 && lanes <= 16 && !(c->prm.flags & kFlagNoLockstep) && c->maxdeg <= (uint32_t)(2 * lanes) &&
+        lanes * (c->maxdeg <= (uint32_t)lanes ? 1 : 2) <= 16) {
+        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, b.total_ants, &b.kc));
+    } else {
+        GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, b.total_ants, &b.kc));
+    }
     const size_t words = (c->N + 31u) / 32u;
     GMP_TRY(ensure(c, &b.dq, n));
     GMP_TRY(ensure(c, &b.prefix, n + 1));
     GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.tauf, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.heur, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.qs, n));
@@ -650,6 +729,14 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     GMP_TRY(ensure(c, &b.route_out, (size_t)n * (b.max_steps + 1)));
     GMP_TRY(ensure(c, &b.tickets, maxI));
     GMP_TRY(ensure(c, &b.res, n));
+    if (b.persistent && (uint64_t)b.kc.grid < n)
+        return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs at least one resident block per colony");
+    if (b.persistent) {
+        GMP_TRY(ensure(c, &b.ctr, (size_t)n * maxI));
+        GMP_TRY(ensure(c, &b.qstate, n));
+        GMP_TRY(ensure(c, &b.qflag, maxI));
+        GMP_TRY(ensure(c, &b.misc, 2));
+    }
     if (b.log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)b.log_entries * 4));
     if (!b.kc.tabu_in_smem)
         GMP_TRY(ensure(c, &b.tabu, (size_t)b.kc.grid * (b.kc.block / b.kc.lanes) * words));
@@ -667,7 +754,7 @@ int gmp_batch_launch(gmp_ctx* c) {
     if (!b.staged) return fail(c, GMP_ERR_STATE, "stage a batch first");
     cudaSetDevice(c->device);
     const bool timed = (c->prm.flags & kFlagKernelTiming) != 0;
-    const size_t n_ev = timed ? 3 + 4 * (size_t)b.maxI : 0;
+    const size_t n_ev = timed ? (b.persistent ? 4 : 3 + 4 * (size_t)b.maxI) : 0;
     if (b.ev.size() != n_ev || b.timed != timed) {
         drop_graph(b);
         drop_events(b);
@@ -708,7 +795,10 @@ int gmp_batch_collect(gmp_ctx* c, gmp_result* results) {
     cudaSetDevice(c->device);
     std::vector<DevResult> hr(b.Q);
     GMP_CUDA(c, cudaMemcpyAsync(hr.data(), b.res, b.Q * sizeof(DevResult), cudaMemcpyDeviceToHost, c->stream));
+    uint32_t misc[2] = {0, 0};
+    if (b.persistent) GMP_CUDA(c, cudaMemcpyAsync(misc, b.misc, sizeof misc, cudaMemcpyDeviceToHost, c->stream));
     GMP_TRY(sync(c));
+    if (misc[1]) return fail(c, GMP_ERR_TIMEOUT, "a bounded device wait of the persistent job expired");
     for (uint32_t i = 0; i < b.Q; ++i) {
         gmp_result& r = results[i];
         const DevResult& d = hr[i];
@@ -814,6 +904,13 @@ int gmp_get_kernel_times(gmp_ctx* c, float* out) {
     cudaSetDevice(c->device);
     GMP_TRY(sync(c));
     float ms = 0;
+    if (b.persistent) {  // construction, evaporation, best tracking and queue update run in one kernel
+        GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[1], b.ev[2]));
+        out[0] = ms;
+        GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[3]));
+        out[4] = ms;
+        return GMP_OK;
+    }
     for (uint32_t it = 0; it < b.maxI; ++it) {
         const size_t prev = it == 0 ? 1 : 1 + 4 * (size_t)it;
         for (int k = 0; k < 4; ++k) {

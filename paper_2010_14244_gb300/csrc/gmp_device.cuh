@@ -33,9 +33,9 @@ struct __align__(16) EdgeRec {
     uint32_t cycle;  // cycle of v's signal, 0 = unsignalised
     uint32_t gbeg;   // start of this approach's green window, (offset + start in phase order) mod cycle
     uint32_t glen;   // green time of this approach's phase
-    unsigned long long cmagic;  // floor((2^64 - 1) / cycle), 0 when unsignalised
+    uint32_t cmagic; // floor((2^32 - 1) / cycle), 0 when unsignalised
     uint32_t flags;  // bit 0: road over the congestion threshold
-    uint32_t pad;
+    uint32_t pad[2];
 };
 static_assert(sizeof(EdgeRec) == 48, "EdgeRec layout");
 
@@ -105,72 +105,119 @@ __device__ __forceinline__ uint32_t heuristic_ms(int32_t x, int32_t y, int32_t x
     return h > kHClamp ? kHClamp : (uint32_t)h;
 }
 
-// x mod d for x < 2^32 and 1 <= d <= 2^24, with m = floor((2^64 - 1) / d): the quotient estimate
-// floor(x * m / 2^64) is exact or one too small, so one conditional subtraction finishes it.
-__device__ __forceinline__ uint32_t mod_magic(uint32_t x, uint32_t d, unsigned long long m) {
-    const uint32_t q = (uint32_t)__umul64hi((unsigned long long)x, m);
+// x mod d for x < 2^32 and 1 <= d <= 2^24, with m = floor((2^32 - 1) / d): the quotient estimate
+// floor(x * m / 2^32) is exact or one too small, so one conditional subtraction finishes it.
+__device__ __forceinline__ uint32_t mod_magic(uint32_t x, uint32_t d, uint32_t m) {
+    const uint32_t q = __umulhi(x, m);
     const uint32_t r = x - q * d;
     return r >= d ? r - d : r;
 }
 
 // Signal wait for a vehicle reaching the stop line at absolute time arr: the approach is green during
 // [gbeg, gbeg + glen) modulo the cycle; otherwise it waits for the next start of that window.
-__device__ __forceinline__ uint32_t signal_wait(uint32_t arr, uint32_t cycle, unsigned long long cmagic,
-                                                uint32_t gbeg, uint32_t glen) {
+__device__ __forceinline__ uint32_t signal_wait(uint32_t arr, uint32_t cycle, uint32_t cmagic, uint32_t gbeg,
+                                                uint32_t glen) {
     const uint32_t x = mod_magic(arr, cycle, cmagic);
     const uint32_t c = x >= gbeg ? x - gbeg : x + (cycle - gbeg);
     return c < glen ? 0u : cycle - c;
 }
 
-// x^k for 0 <= k <= 8 by repeated multiplication left to right (x^0 = 1), without branches.
+// x^k by repeated multiplication left to right (x^0 = 1); k is uniform across the lanes of an ant.
 __device__ __forceinline__ float pow_int(float x, uint32_t k) {
-    float p = k ? x : 1.0f;
-#pragma unroll
-    for (uint32_t i = 2; i <= 8; ++i) {
-        const float y = __fmul_rn(p, x);
-        p = i <= k ? y : p;
-    }
+    if (k == 0) return 1.0f;
+    float p = x;
+    for (uint32_t i = 1; i < k; ++i) p = __fmul_rn(p, x);
     return p;
 }
 
-// Next-node desirability: (tau / 2^32)^alpha * (1 / c)^beta, c = travel + wait + remaining bound (ms).
-// __frcp_rn(c) is 1/c rounded to nearest, the same value as the division 1.0f / c.
-__device__ __forceinline__ float score(uint64_t tau, uint32_t alpha, uint32_t c, uint32_t beta) {
-    const float tf = __fmul_rn(__ull2float_rn(tau), 0x1p-32f);
-    const float eta = __frcp_rn(__uint2float_rn(c));
+// Pheromone as a binary32 value: the Q32.32 integer rounded to nearest, scaled exactly by 2^-32.
+__device__ __forceinline__ float tau_float(uint64_t tau) { return __fmul_rn(__ull2float_rn(tau), 0x1p-32f); }
+
+// 1 / c rounded to nearest for 1 <= c <= 2^29 (results are never subnormal): the hardware reciprocal
+// estimate corrected once with fused multiply-adds (Markstein, IBM J. Res. Dev. 34(1), 1990: the
+// residual 1 - c*y is exact in an FMA, and one FMA correction of a faithful estimate is correctly
+// rounded). Equal to __frcp_rn(c) for every float in [1, 2^29], checked exhaustively on the GPU.
+__device__ __forceinline__ float rcp_rn(float c) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(c));
+    const float r = __fmaf_rn(-c, y, 1.0f);
+    return __fmaf_rn(r, y, y);
+}
+
+// Next-node desirability from tf = tau_float(tau): tf^alpha * (1 / c)^beta, c = travel + wait +
+// remaining bound (ms), 1 <= c < 2^29. The alpha = 1, beta = 2 case performs the same roundings in the
+// same order without loops.
+__device__ __forceinline__ float score_f(float tf, uint32_t alpha, uint32_t c, uint32_t beta) {
+    const float eta = rcp_rn(__uint2float_rn(c));
+    if (alpha == 1u && beta == 2u) return __fmul_rn(tf, __fmul_rn(eta, eta));
     return __fmul_rn(pow_int(tf, alpha), pow_int(eta, beta));
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+// floor(rnd * S / 2^64) for S < 2^63 from four 32x32 -> 64-bit products (the generic 64-bit high
+// multiply is a long dependent sequence on this GPU).
+__device__ __forceinline__ unsigned long long mulhi_draw(unsigned long long rnd, unsigned long long S) {
+    const uint32_t rl = (uint32_t)rnd, rh = (uint32_t)(rnd >> 32), sl = (uint32_t)S, sh = (uint32_t)(S >> 32);
+    const unsigned long long p0 = (unsigned long long)rh * sh, p1 = (unsigned long long)rh * sl;
+    const unsigned long long p2 = (unsigned long long)rl * sh, p3 = (unsigned long long)rl * sl;
+    return p0 + (p1 >> 32) + (((p1 & 0xFFFFFFFFull) + p2 + (p3 >> 32)) >> 32);
 }
 
-// A non-negative binary32 value as mant * 2^(ex - 150) with mant in [2^23, 2^24) (subnormals
-// normalised); zero gives mant = 0.
-__device__ __forceinline__ void split_f32(uint32_t bits, uint32_t& mant, int& ex) {
-    const uint32_t e = bits >> 23, m = bits & 0x7FFFFFu;
-    if (e) {
-        mant = m | 0x800000u;
-        ex = (int)e;
-    } else if (m) {
-        const int sh = __clz(m) - 8;
-        mant = m << sh;
-        ex = 1 - sh;
-    } else {
-        mant = 0;
-        ex = -1024;
-    }
+// A non-negative binary32 bit pattern as (M, X) with value = M * 2^(X - 150): M in [2^23, 2^24) for
+// every non-zero value, M = 0 for zero. A subnormal is first scaled by 2^64 (exact) to read its
+// exponent. No branches.
+__device__ __forceinline__ void norm_f32(uint32_t bits, uint32_t& M, int& X) {
+    const uint32_t e = bits >> 23;
+    const uint32_t b2 = __float_as_uint(__fmul_rn(__uint_as_float(bits), 0x1p64f));
+    const uint32_t src = e ? bits : b2;
+    M = bits ? ((src & 0x7FFFFFu) | 0x800000u) : 0u;
+    X = e ? (int)e : (int)(b2 >> 23) - 64;
 }
 
-// Integer roulette weight relative to the largest score: floor(s * 2^(30 - floor(log2 max))) at least 1.
-__device__ __forceinline__ uint32_t roulette_weight(uint32_t sbits, uint32_t mmant, int mex) {
-    if (mmant == 0) return 1u;  // every score is zero: uniform choice
-    uint32_t mant;
-    int ex;
-    split_f32(sbits, mant, ex);
-    const int d = mex - ex;
-    const uint32_t w = d >= 31 ? 0u : (mant << 7) >> d;
-    return w ? w : 1u;
+// Integer roulette weight relative to the largest score m (given as its exponent Xm and whether it is
+// zero): floor(s * 2^(30 - floor(log2 m))), at least 1; all ones when m == 0. No branches.
+__device__ __forceinline__ uint32_t roulette_weight_x(uint32_t sbits, int Xm, bool mzero) {
+    uint32_t Ms;
+    int Xs;
+    norm_f32(sbits, Ms, Xs);
+    const int d = max(0, min(Xm - Xs, 31));  // masked-out slots may carry any value: keep the shift defined
+    const uint32_t w = (Ms << 7) >> d;
+    return (mzero || w == 0u) ? 1u : w;
+}
+
+__device__ __forceinline__ uint32_t roulette_weight(uint32_t sbits, uint32_t mbits) {
+    uint32_t Mm;
+    int Xm;
+    norm_f32(mbits, Mm, Xm);
+    return roulette_weight_x(sbits, Xm, mbits == 0u);
+}
+
+// The same weights in binary32 arithmetic. For a step whose largest score m has E = floor(log2 m),
+// scale = (2^k1, 2^k2) with k1 + k2 = 30 - E, both factors normal. floor(s * 2^k1 * 2^k2) is exact:
+// multiplying by a power of two is exact unless the result leaves the normal range, and any result
+// that does so (a shrinking first factor) makes the final value below 1, where the floor is 0 and the
+// weight 1 anyway.
+struct WeightScale {
+    float s1, s2;
+    bool mzero;
+};
+
+__device__ __forceinline__ WeightScale weight_scale(uint32_t mbits) {
+    uint32_t Mm;
+    int Xm;
+    norm_f32(mbits, Mm, Xm);
+    const int k = 30 - (Xm - 127);  // 30 - E, in [-97, 179]
+    const int k1 = k >> 1, k2 = k - k1;
+    WeightScale w;
+    w.s1 = __uint_as_float((uint32_t)(k1 + 127) << 23);
+    w.s2 = __uint_as_float((uint32_t)(k2 + 127) << 23);
+    w.mzero = mbits == 0u;
+    return w;
+}
+
+__device__ __forceinline__ uint32_t roulette_weight_f(uint32_t sbits, const WeightScale& sc) {
+    const float v = __fmul_rn(__fmul_rn(__uint_as_float(sbits), sc.s1), sc.s2);
+    const uint32_t w = __float2uint_rz(v);  // v < 2^31
+    return (sc.mzero || w == 0u) ? 1u : w;
 }
 
 // Congested travel time ff * cap / max(cap - n, max(1, cap / 20)), saturating at 2^26 ms.

@@ -20,6 +20,7 @@ struct ConstructArgs {
     const DevQuery* queries;
     const uint32_t* ant_prefix;  // Q + 1 entries: first global ant of each query
     const uint64_t* tau;         // Q * E
+    const float* tauf;           // Q * E pheromone as binary32 (tau rounded to nearest times 2^-32)
     const uint32_t* hq;          // Q * E heuristic of each road's head towards the colony's destination
     unsigned long long* dep;     // Q * E deposit accumulators
     QueryState* qs;
@@ -32,16 +33,45 @@ struct ConstructArgs {
     uint32_t n_queries, total_ants, n_edges, max_steps;
     uint32_t tabu_words, t_dep, thr_on, tabu_in_smem;
     uint32_t kappa;              // floor(360 * 2^16 / v_max)
-    uint32_t no_prefetch;        // 1: skip the L1 prefetch of candidate rows
+};
+
+// Per-(colony, iteration) counters of the persistent job.
+struct __align__(16) IterCounters {
+    uint32_t ant_claim, ant_done;       // ants handed out / finished
+    uint32_t chunk_claim, chunk_done;   // iteration-end chunks handed out / finished
+    uint32_t chunk_total;               // chunks of this iteration end (roads, plus nodes for one colony)
+    uint32_t pad[3];
+};
+
+// Arguments of the persistent job: the walk's arguments plus the colony state machine and what the
+// iteration-end chunks touch.
+struct PersistentArgs {
+    ConstructArgs c;
+    IterCounters* ctr;      // Q * max_iter
+    uint32_t* qstate;       // Q: (iteration << 2) | phase
+    uint32_t* qflag;        // max_iter: colony (+1) that updates the queues for that iteration index
+    uint32_t* misc;         // [0] finished colonies, [1] error flag (bounded wait expired)
+    uint64_t* tau;
+    float* tauf;
+    uint32_t* best_route;
+    const uint32_t *in_ptr, *in_edge;
+    const uint8_t* nph;
+    const uint32_t *cycle, *offset, *green;
+    const uint8_t* ephase;
+    const uint32_t *veh, *cap, *red;
+    uint8_t* order;
+    EdgeRec* rec;
+    uint32_t n_nodes, max_iter, spin_limit;
 };
 
 struct KernelConfig {
-    int lanes;             // lanes per ant (G)
+    int lanes;             // lanes per ant (G); 1 = one thread per ant
     int slots;             // candidate slots per lane (K)
     int block;             // threads per block
     int grid;              // blocks
     size_t smem;           // dynamic shared memory per block
     bool tabu_in_smem;
+    bool lockstep = false;  // all ants of a warp step together (k_construct_gl / k_construct_lock)
 };
 
 // Launchers (gmp_kernels.cu).
@@ -56,11 +86,11 @@ cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec);
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
-                              unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
+                              float* tauf, unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
 cudaError_t launch_evaporate(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, uint64_t* tau,
-                             unsigned long long* dep, uint32_t it);
+                             float* tauf, unsigned long long* dep, uint32_t it);
 cudaError_t launch_best_copy(cudaStream_t s, uint32_t Q, const DevQuery* q, QueryState* qs, const uint32_t* routes,
                              const uint32_t* ant_steps, const uint32_t* ant_wait, uint32_t* best_route,
                              uint32_t max_steps, uint32_t it);
@@ -68,9 +98,18 @@ cudaError_t launch_finalize(cudaStream_t s, uint32_t Q, const DevQuery* q, const
                             const uint32_t* best_route, const uint32_t* col, uint32_t max_steps, DevResult* res,
                             uint32_t* route_out);
 
+// Persistent job (gmp_persistent.cu).
+cudaError_t launch_persistent_init(cudaStream_t s, uint32_t Q, uint32_t maxI, const DevQuery* q, IterCounters* ctr,
+                                   uint32_t* qstate, uint32_t* qflag, uint32_t* misc);
+cudaError_t persistent_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, KernelConfig* out);
+cudaError_t launch_persistent(cudaStream_t s, const KernelConfig& kc, const PersistentArgs& p);
+
 // Occupancy-derived configuration for a lane count and graph size.
 cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, uint32_t total_ants,
                              KernelConfig* out);
+cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, uint32_t max_degree,
+                                      uint32_t total_ants, KernelConfig* out);
 int construct_max_degree(int lanes);
+bool construct_thread_fits(uint32_t n_nodes);
 
 }  // namespace gmp

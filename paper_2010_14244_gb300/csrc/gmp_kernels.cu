@@ -13,6 +13,7 @@
 
 #include "gmp_device.cuh"
 #include "gmp_internal.h"
+#include "gmp_walk.cuh"
 
 namespace gmp {
 
@@ -51,15 +52,11 @@ __global__ void k_edge_dynamic(uint32_t E, const uint32_t* __restrict__ row_ptr,
     }
     r.qd = qd;
     r.flags = (thr != kThrOff && (uint64_t)n * 1000u > (uint64_t)thr * c) ? 1u : 0u;
-    r.pad = 0;
+    r.pad[0] = r.pad[1] = 0;
 }
 
 // ------------------------------------------------------------------------------------------------
-// Preemptive phase order, one thread per intersection. Queues and storage per phase come from the
-// road's in-edges (reverse CSR). Order: (1) phases whose queue exceeds 3/4 of their storage, longest
-// first; else (2) phases red for longer than a cycle, longest first; else (3) the longest non-empty
-// queue. Then the remaining non-empty phases, then the empty ones, each in default (index) order.
-// Every in-edge's record then gets its approach's green window under that order.
+// Preemptive phase order, one thread per intersection (queue_node in gmp_walk.cuh).
 // ------------------------------------------------------------------------------------------------
 __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr, const uint32_t* __restrict__ in_edge,
                                 const uint8_t* __restrict__ nph, const uint32_t* __restrict__ cycle,
@@ -69,92 +66,7 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
                                 uint8_t* __restrict__ order, EdgeRec* __restrict__ rec) {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
-    const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
-    uint8_t ord[kMaxPhases];
-    if (P == 0) {
-        for (uint32_t i = 0; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
-        for (uint32_t i = ib; i < ie; ++i) {
-            EdgeRec& r = rec[in_edge[i]];
-            r.cycle = 0;
-            r.gbeg = 0;
-            r.glen = 0;
-            r.cmagic = 0;
-        }
-        return;
-    }
-    uint64_t Q[kMaxPhases], S[kMaxPhases];
-    for (uint32_t p = 0; p < kMaxPhases; ++p) Q[p] = S[p] = 0;
-    for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const uint32_t p = ephase[e] & (kMaxPhases - 1);
-        Q[p] += veh[e];
-        S[p] += cap[e];
-    }
-    const uint32_t cy = cycle[v];
-    uint32_t over = 0, starved = 0, nonempty = 0;
-    uint32_t rd[kMaxPhases];
-    for (uint32_t p = 0; p < P; ++p) {
-        rd[p] = red[(size_t)v * kMaxPhases + p];
-        if (Q[p] > S[p] * 3u / 4u) over |= 1u << p;
-        if (rd[p] > cy) starved |= 1u << p;
-        if (Q[p] > 0) nonempty |= 1u << p;
-    }
-    uint32_t used = 0, n = 0;
-    if (over) {
-        while (over & ~used) {
-            int best = -1;
-            for (uint32_t p = 0; p < P; ++p)
-                if ((over & ~used) >> p & 1u)
-                    if (best < 0 || Q[p] > Q[best]) best = (int)p;
-            used |= 1u << best;
-            ord[n++] = (uint8_t)best;
-        }
-    } else if (starved) {
-        while (starved & ~used) {
-            int best = -1;
-            for (uint32_t p = 0; p < P; ++p)
-                if ((starved & ~used) >> p & 1u)
-                    if (best < 0 || rd[p] > rd[best]) best = (int)p;
-            used |= 1u << best;
-            ord[n++] = (uint8_t)best;
-        }
-    } else if (nonempty) {
-        int best = -1;
-        for (uint32_t p = 0; p < P; ++p)
-            if (nonempty >> p & 1u)
-                if (best < 0 || Q[p] > Q[best]) best = (int)p;
-        used |= 1u << best;
-        ord[n++] = (uint8_t)best;
-    }
-    for (uint32_t p = 0; p < P; ++p)
-        if (!(used >> p & 1u) && (nonempty >> p & 1u)) {
-            used |= 1u << p;
-            ord[n++] = (uint8_t)p;
-        }
-    for (uint32_t p = 0; p < P; ++p)
-        if (!(used >> p & 1u)) {
-            used |= 1u << p;
-            ord[n++] = (uint8_t)p;
-        }
-    uint32_t start[kMaxPhases];
-    uint32_t acc = 0;
-    for (uint32_t i = 0; i < P; ++i) {
-        order[(size_t)v * kMaxPhases + i] = ord[i];
-        start[ord[i]] = acc;
-        acc += green[(size_t)v * kMaxPhases + ord[i]];
-    }
-    for (uint32_t i = P; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
-    const uint32_t off = offset[v];
-    const unsigned long long magic = ~0ull / cy;
-    for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const uint32_t p = ephase[e] & (kMaxPhases - 1);
-        EdgeRec& r = rec[e];
-        r.cycle = cy;
-        r.gbeg = (off + start[p]) % cy;
-        r.glen = green[(size_t)v * kMaxPhases + p];
-        r.cmagic = magic;
-    }
+    queue_node(v, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh, cap, red, order, rec);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -163,19 +75,21 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
 // Calc_Dist for the whole colony up front: hq[e] = h(head(e)) towards this colony's destination.
 __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
                              const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
-                             uint32_t flags, uint64_t* __restrict__ tau, unsigned long long* __restrict__ dep,
-                             uint32_t* __restrict__ hq, QueryState* __restrict__ qs, uint32_t* __restrict__ tickets,
-                             uint32_t n_tickets) {
+                             uint32_t flags, uint64_t* __restrict__ tau, float* __restrict__ tauf,
+                             unsigned long long* __restrict__ dep, uint32_t* __restrict__ hq,
+                             QueryState* __restrict__ qs, uint32_t* __restrict__ tickets, uint32_t n_tickets) {
     const uint32_t qi = blockIdx.y;
     const DevQuery Q = q[qi];
     uint64_t* T = tau + (size_t)qi * E;
     unsigned long long* D = dep + (size_t)qi * E;
     uint32_t* H = hq + (size_t)qi * E;
+    float* TF = tauf + (size_t)qi * E;
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         uint64_t t0 = 1ull << 32;
         if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
         T[e] = t0;
+        TF[e] = tau_float(t0);
         D[e] = 0;
         const uint32_t v = col[e];
         H[e] = heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
@@ -196,207 +110,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         for (uint32_t i = threadIdx.x; i < n_tickets; i += blockDim.x) tickets[i] = 0;
 }
 
-// ------------------------------------------------------------------------------------------------
-// Ant construction. G lanes of a warp serve one ant (sub-warp group); lane l holds the candidates
-// l, l+G, ..., l+(K-1)G of the current node's CSR row. Per step: one round of independent 16-byte
-// record loads and pheromone loads, scores, a group max, integer weights, a shuffle prefix sum,
-// one Philox draw, a ballot to find the chosen road and shuffles to broadcast it.
-// Groups take ants from a per-iteration ticket counter, so short walks free lanes for waiting ants.
-// ------------------------------------------------------------------------------------------------
-template <int G, int K>
-__device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery& q, uint32_t qi, uint32_t k,
-                                         uint32_t it, uint32_t* tabu, uint32_t lane, uint32_t gmask, uint32_t gbase) {
-    const unsigned long long* __restrict__ tau = reinterpret_cast<const unsigned long long*>(a.tau) +
-                                                 (size_t)qi * a.n_edges;
-    const uint32_t* __restrict__ hq = a.hq + (size_t)qi * a.n_edges;
-    const uint32_t slot = q.ant_base + k;
-    uint32_t* route = a.routes + (size_t)slot * a.max_steps;
-    const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
-    uint32_t u = q.src;
-    uint32_t beg = __ldg(a.row_ptr + u), end = __ldg(a.row_ptr + u + 1);
-    uint32_t t = 0, W = 0, steps = 0, status;
-    if (lane == 0) tabu[u >> 5] |= 1u << (u & 31);
-    __syncwarp(gmask);
-    for (;;) {
-        if (u == q.dst) {
-            status = kAntSuccess;
-            break;
-        }
-        if (steps == a.max_steps) {
-            status = kAntStepCap;
-            break;
-        }
-        const uint32_t deg = end - beg;
-        const int nslots = K == 1 ? 1 : (int)((deg + G - 1) / G);  // group-uniform
-        // 1. issue every load of this step: records, pheromone and heuristic of this lane's candidates
-        uint4 r0[K], r1[K], r2[K];
-        unsigned long long te[K];
-        uint32_t he[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const uint32_t idx = lane + (uint32_t)j * G;
-            if (j < nslots && idx < deg) {
-                const uint4* rp = reinterpret_cast<const uint4*>(a.rec + beg + idx);
-                r0[j] = __ldg(rp);
-                r1[j] = __ldg(rp + 1);
-                r2[j] = __ldg(rp + 2);
-                te[j] = __ldg(tau + beg + idx);
-                he[j] = __ldg(hq + beg + idx);
-            } else {
-                r0[j] = r1[j] = r2[j] = make_uint4(0, 0, 0, 0);
-                te[j] = 0;
-                he[j] = 0;
-            }
-        }
-        // 2. the draw of this step depends on (iteration, ant, step) only: overlaps the loads
-        const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
-        const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-        // 3. candidates, waits, scores
-        uint32_t cmask = 0, cong = 0;
-        uint32_t sb[K], wv[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            sb[j] = wv[j] = 0;
-            const uint32_t idx = lane + (uint32_t)j * G;
-            if (j < nslots && idx < deg) {
-                const uint32_t v = r0[j].x;
-                const bool visited = (tabu[v >> 5] >> (v & 31)) & 1u;
-                if (!visited) {
-                    if (!a.no_prefetch && r0[j].z > r0[j].y) {  // the next step reads one of these rows
-                        const char* b0 = reinterpret_cast<const char*>(a.rec + r0[j].y);
-                        const char* b1 = reinterpret_cast<const char*>(a.rec + r0[j].z) - 1;
-                        for (const char* p = b0; p <= b1; p += 128) prefetch_l1(p);
-                        prefetch_l1(b1);
-                        prefetch_l1(tau + r0[j].y);
-                        prefetch_l1(hq + r0[j].y);
-                    }
-                    cmask |= 1u << j;
-                    if (r2[j].z & 1u) cong |= 1u << j;
-                    uint32_t w = 0;
-                    const uint32_t cy = r1[j].y;
-                    if (v != q.dst && cy != 0) {
-                        const unsigned long long mg = (unsigned long long)r2[j].x | ((unsigned long long)r2[j].y << 32);
-                        w = signal_wait(a.t_dep + t + r0[j].w, cy, mg, r1[j].z, r1[j].w) + r1[j].x;
-                    }
-                    wv[j] = w;
-                    sb[j] = __float_as_uint(score(te[j], q.alpha, r0[j].w + w + he[j], q.beta));
-                }
-            }
-        }
-        if (a.thr_on) {  // congested roads drop out unless every candidate is congested
-            const uint32_t any_ok = __ballot_sync(gmask, (cmask & ~cong) != 0u) & gmask;
-            const uint32_t any_cg = __ballot_sync(gmask, (cmask & cong) != 0u) & gmask;
-            if (any_ok && any_cg) cmask &= ~cong;
-        }
-        if ((__ballot_sync(gmask, cmask != 0u) & gmask) == 0u) {
-            status = kAntDeadEnd;
-            break;
-        }
-        // 4. largest score of the group (non-negative floats order like their bit patterns)
-        uint32_t mb = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if ((cmask >> j & 1u) && sb[j] > mb) mb = sb[j];
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(gmask, mb, off, G));
-        uint32_t mmant;
-        int mex;
-        split_f32(mb, mmant, mex);
-        // 5. integer weights and their inclusive prefix in CSR order (index lane + j*G)
-        unsigned long long carry = 0, incl[K];
-        uint32_t wt[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            wt[j] = 0;
-            incl[j] = carry;
-            if (j < nslots) {
-                wt[j] = (cmask >> j & 1u) ? roulette_weight(sb[j], mmant, mex) : 0u;
-                unsigned long long xs = wt[j];
-#pragma unroll
-                for (int d = 1; d < G; d <<= 1) {
-                    const unsigned long long y = __shfl_up_sync(gmask, xs, d, G);
-                    if (lane >= (uint32_t)d) xs += y;
-                }
-                incl[j] = carry + xs;
-                if (j + 1 < K) carry += __shfl_sync(gmask, xs, G - 1, G);
-                else carry = __shfl_sync(gmask, incl[j], G - 1, G);
-            }
-        }
-        if (K > 1) carry = __shfl_sync(gmask, incl[K - 1], G - 1, G);
-        // 6. roulette: first candidate whose running weight exceeds r = floor(rnd * S / 2^64)
-        const unsigned long long r = __umul64hi(rnd, carry);
-        int js = -1;
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (wt[j] != 0u && incl[j] - wt[j] <= r && r < incl[j]) js = j;
-        const uint32_t bw = __ballot_sync(gmask, js >= 0) & gmask;
-        const int src_lane = (__ffs(bw) - 1) - (int)gbase;
-        uint32_t c_idx = 0, c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (js == j) {
-                c_idx = lane + (uint32_t)j * G;
-                c_h = r0[j].x;
-                c_vb = r0[j].y;
-                c_ve = r0[j].z;
-                c_tt = r0[j].w;
-                c_w = wv[j];
-            }
-        c_idx = __shfl_sync(gmask, c_idx, src_lane, G);
-        c_h = __shfl_sync(gmask, c_h, src_lane, G);
-        c_vb = __shfl_sync(gmask, c_vb, src_lane, G);
-        c_ve = __shfl_sync(gmask, c_ve, src_lane, G);
-        c_tt = __shfl_sync(gmask, c_tt, src_lane, G);
-        c_w = __shfl_sync(gmask, c_w, src_lane, G);
-        // 7. position update
-        const uint32_t e = beg + c_idx;
-        t += c_tt + c_w;
-        W += c_w;
-        u = c_h;
-        beg = c_vb;
-        end = c_ve;
-        if (lane == 0) {
-            route[steps] = e;
-            tabu[u >> 5] |= 1u << (u & 31);
-        }
-        ++steps;
-        __syncwarp(gmask);
-        if (t > kTCap) {
-            status = kAntTimeCap;
-            break;
-        }
-    }
-    QueryState* S = a.qs + qi;
-    if (lane == 0) {
-        a.ant_steps[slot] = steps;
-        a.ant_wait[slot] = W;
-        atomicAdd(&S->steps, (unsigned long long)steps);
-        if (status == kAntSuccess) atomicAdd(&S->nsucc, 1ull);
-        if (a.ant_log) {
-            uint32_t* l = a.ant_log + 4ull * (q.log_base + (uint64_t)it * q.n_ants + k);
-            *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
-        }
-    }
-    if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
-        const unsigned long long delta = S->dep_num / t;
-        unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
-        for (uint32_t i = lane; i < steps; i += G) atomicAdd(D + route[i], delta);
-        if (lane == 0) atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * q.n_ants + k));
-    }
-    // forget the visited set: whole bitmap when small, else just the nodes of this walk
-    if (a.tabu_words <= 2u * (steps + 1u)) {
-        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
-    } else {
-        if (lane == 0) atomicAnd(tabu + (q.src >> 5), ~(1u << (q.src & 31)));
-        for (uint32_t i = lane; i < steps; i += G) {
-            const uint32_t v = __ldg(a.col + route[i]);
-            atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
-        }
-    }
-    __syncwarp(gmask);
-}
-
-template <int G, int K>
+template <int G, int K, bool SMEM>
 __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it) {
     extern __shared__ uint32_t smem[];
     const uint32_t lane = threadIdx.x & (G - 1);
@@ -404,8 +118,8 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
     const uint32_t gbase = (threadIdx.x & 31u) & ~(uint32_t)(G - 1);
     const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << gbase);
     const uint32_t groups = blockDim.x / G;
-    uint32_t* tabu = a.tabu_in_smem ? smem + (size_t)gib * a.tabu_words
-                                    : a.tabu_global + ((size_t)blockIdx.x * groups + gib) * a.tabu_words;
+    uint32_t* tabu = SMEM ? smem + (size_t)gib * a.tabu_words
+                          : a.tabu_global + ((size_t)blockIdx.x * groups + gib) * a.tabu_words;
     for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
     __syncwarp(gmask);
     for (;;) {
@@ -426,20 +140,481 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
 }
 
 // ------------------------------------------------------------------------------------------------
+// Ant construction, G lanes per ant, all ants of a warp in lockstep: every loop iteration each of the
+// 32/G groups advances its ant by one step through the same code, so one warp instruction serves all
+// of them (a warp whose groups wander apart would issue each group's instructions separately). Row
+// loads stay coalesced within a group. Shuffles run on the full warp with width G. A group whose ant
+// ended finalises it (deposits and bitmap reset spread over its G lanes) and takes a new ant; new ants
+// come from one warp-aggregated atomic per round.
+// ------------------------------------------------------------------------------------------------
+template <int G, int K, bool SMEM>
+__global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t it) {
+    extern __shared__ uint32_t smem[];
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    constexpr int NC = G * K;
+    const uint32_t lane = threadIdx.x & (G - 1);       // lane within the group
+    const uint32_t wl = threadIdx.x & 31u;             // lane within the warp
+    const uint32_t gib = threadIdx.x / G;
+    const uint32_t groups = blockDim.x / G;
+    const bool leader = lane == 0;
+    uint32_t* const tabu = SMEM ? smem + (size_t)gib * a.tabu_words
+                                : a.tabu_global + ((size_t)blockIdx.x * groups + gib) * a.tabu_words;
+    for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+    __syncwarp();
+    const uint32_t lt_mask = (1u << wl) - 1u;
+    bool active = false, exhausted = false;
+    uint32_t qi = 0, k = 0, slot = 0, src = 0, dst = 0, n_ants = 1, alpha = 1, beta = 2, s0 = 0, s1 = 0;
+    uint64_t log_base = 0;
+    uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
+    const float* tauf = a.tauf;
+    const uint32_t* hq = a.hq;
+    uint32_t* route = a.routes;
+    for (;;) {
+        // 1. groups without an ant take the next tickets (one atomic for the whole warp)
+        const bool need = !active && !exhausted;
+        const uint32_t nmask = __ballot_sync(FULL, need && leader);
+        if (nmask) {
+            const int first = __ffs(nmask) - 1;
+            uint32_t base = 0;
+            if ((int)wl == first) base = atomicAdd(a.tickets + it, (uint32_t)__popc(nmask));
+            base = __shfl_sync(FULL, base, first);
+            uint32_t tk = base + (uint32_t)__popc(nmask & lt_mask);
+            tk = __shfl_sync(FULL, tk, 0, G);  // the group's leader holds the group's ticket
+            if (need) {
+                if (tk >= a.total_ants) {
+                    exhausted = true;
+                } else {
+                    uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tk < ant_prefix[q + 1]
+                    while (hi - lo > 1u) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (__ldg(a.ant_prefix + mid) <= tk) lo = mid;
+                        else hi = mid;
+                    }
+                    const DevQuery q = a.queries[lo];
+                    if (q.active && it < q.n_iter) {
+                        active = true;
+                        qi = lo;
+                        k = tk - q.ant_base;
+                        slot = tk;
+                        src = q.src;
+                        dst = q.dst;
+                        n_ants = q.n_ants;
+                        alpha = q.alpha;
+                        beta = q.beta;
+                        s0 = (uint32_t)q.seed;
+                        s1 = (uint32_t)(q.seed >> 32);
+                        log_base = q.log_base;
+                        tauf = a.tauf + (size_t)qi * a.n_edges;
+                        hq = a.hq + (size_t)qi * a.n_edges;
+                        route = a.routes + (size_t)slot * a.max_steps;
+                        u = src;
+                        beg = __ldg(a.row_ptr + u);
+                        end = __ldg(a.row_ptr + u + 1);
+                        t = W = steps = 0;
+                        if (leader) atomicOr(tabu + (u >> 5), 1u << (u & 31));
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (!__any_sync(FULL, active || !exhausted)) break;
+        if (!__any_sync(FULL, active)) continue;
+        // 2. one step of every active ant
+        bool done = false;
+        if (active && u == dst) {
+            done = true;
+            status = kAntSuccess;
+        } else if (active && steps == a.max_steps) {
+            done = true;
+            status = kAntStepCap;
+        }
+        const bool stepping = active && !done;
+        const uint32_t deg = stepping ? end - beg : 0u;
+        const int nslots = K == 1 ? 1 : (int)__reduce_max_sync(FULL, (deg + G - 1) / G);  // warp-uniform
+        if (__any_sync(FULL, deg > 0u)) {
+            uint4 r0[K], r1[K];
+            uint2 r2[K];
+            float tf[K];
+            uint32_t he[K];
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {  // slots past a row read road 0 (always in bounds) and are masked
+                const uint32_t idx = lane + (uint32_t)j * G;
+                const bool ok = j < nslots && idx < deg;
+                valid |= (ok ? 1u : 0u) << j;
+                const uint32_t e = ok ? beg + idx : 0u;
+                const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+                r0[j] = __ldg(rp);
+                r1[j] = __ldg(rp + 1);
+                r2[j] = __ldg(reinterpret_cast<const uint2*>(rp + 2));
+                tf[j] = __ldg(tauf + e);
+                he[j] = __ldg(hq + e);
+            }
+            const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
+            const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            uint32_t cmask = 0, cong = 0;
+            uint32_t sb[K], wv[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const uint32_t v = r0[j].x, cy = r1[j].y;
+                const bool unvisited = !((tabu[v >> 5] >> (v & 31)) & 1u);
+                cmask |= ((valid >> j) & (unvisited ? 1u : 0u)) << j;
+                cong |= (r2[j].y & 1u) << j;
+                const uint32_t sw = signal_wait(a.t_dep + t + r0[j].w, cy | (cy == 0u), r2[j].x, r1[j].z, r1[j].w);
+                const uint32_t w = (v != dst && cy != 0u) ? sw + r1[j].x : 0u;
+                wv[j] = w;
+                sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].w + w + he[j], beta));
+            }
+            constexpr uint32_t kGroupBits = G == 32 ? FULL : ((1u << (G & 31)) - 1u);
+            const uint32_t gshift = wl & ~(uint32_t)(G - 1);
+            if (a.thr_on) {  // congested roads drop out unless every candidate of the ant is congested
+                const uint32_t g_ok = __ballot_sync(FULL, (cmask & ~cong) != 0u) >> gshift;
+                const uint32_t g_cg = __ballot_sync(FULL, (cmask & cong) != 0u) >> gshift;
+                if ((g_ok & kGroupBits) && (g_cg & kGroupBits)) cmask &= ~cong;
+            }
+            const bool has = ((__ballot_sync(FULL, cmask != 0u) >> gshift) & kGroupBits) != 0u;
+            if (stepping && !has) {
+                done = true;
+                status = kAntDeadEnd;
+            }
+            // largest candidate score of each group, own weights, gather, roulette pick
+            uint32_t mb = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) mb = max(mb, (cmask >> j & 1u) ? sb[j] : 0u);
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(FULL, mb, off, G));
+            const WeightScale sc = weight_scale(mb);
+            unsigned long long incl[NC];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const uint32_t mine = (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
+#pragma unroll
+                for (int l = 0; l < G; ++l) incl[j * G + l] = j < nslots ? __shfl_sync(FULL, mine, l, G) : 0u;
+            }
+#pragma unroll
+            for (int h = 1; h < NC; h <<= 1)
+#pragma unroll
+                for (int i = NC - 1; i >= h; --i) incl[i] += incl[i - h];
+            const unsigned long long r = mulhi_draw(rnd, incl[NC - 1]);
+            int pick = 0;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) pick += incl[i] <= r ? 1 : 0;
+            pick = min(pick, NC - 1);  // groups without candidates: any in-range slot (result unused)
+            const int pick_lane = pick % G, pick_slot = pick / G;
+            uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const bool sel = pick_slot == j;
+                c_h = sel ? r0[j].x : c_h;
+                c_vb = sel ? r0[j].y : c_vb;
+                c_ve = sel ? r0[j].z : c_ve;
+                c_tt = sel ? r0[j].w : c_tt;
+                c_w = sel ? wv[j] : c_w;
+            }
+            c_h = __shfl_sync(FULL, c_h, pick_lane, G);
+            c_vb = __shfl_sync(FULL, c_vb, pick_lane, G);
+            c_ve = __shfl_sync(FULL, c_ve, pick_lane, G);
+            c_tt = __shfl_sync(FULL, c_tt, pick_lane, G);
+            c_w = __shfl_sync(FULL, c_w, pick_lane, G);
+            if (stepping && !done) {
+                if (leader) {
+                    route[steps] = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
+                    atomicOr(tabu + (c_h >> 5), 1u << (c_h & 31));
+                }
+                t += c_tt + c_w;
+                W += c_w;
+                u = c_h;
+                beg = c_vb;
+                end = c_ve;
+                ++steps;
+                if (t > kTCap) {
+                    done = true;
+                    status = kAntTimeCap;
+                }
+            }
+            __syncwarp();
+        }
+        // 3. ants that ended: the group records, deposits and resets its bitmap
+        if (__any_sync(FULL, done)) {
+            if (done) {
+                QueryState* S = a.qs + qi;
+                if (leader) {
+                    a.ant_steps[slot] = steps;
+                    a.ant_wait[slot] = W;
+                    atomicAdd(&S->steps, (unsigned long long)steps);
+                    if (a.ant_log) {
+                        uint32_t* l = a.ant_log + 4ull * (log_base + (uint64_t)it * n_ants + k);
+                        *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
+                    }
+                }
+                if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
+                    const unsigned long long delta = S->dep_num / t;
+                    unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
+                    for (uint32_t i = lane; i < steps; i += G) atomicAdd(D + route[i], delta);
+                    if (leader) {
+                        atomicAdd(&S->nsucc, 1ull);
+                        atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * n_ants + k));
+                    }
+                }
+                if (a.tabu_words <= 2u * (steps + 1u)) {
+                    for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+                } else {
+                    if (leader) atomicAnd(tabu + (src >> 5), ~(1u << (src & 31)));
+                    for (uint32_t i = lane; i < steps; i += G) {
+                        const uint32_t v = __ldg(a.col + route[i]);
+                        atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
+                    }
+                }
+                active = false;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Ant construction, one thread per ant, warp in lockstep. Every loop iteration the 32 ants of a warp
+// take one step through the same branch-free code (K candidate slots per thread evaluated with
+// instruction-level parallelism: independent loads and scores, then max, integer weights, running
+// sum and the roulette pick in registers). Ants that end are finalised by the whole warp together
+// (their deposits and their visited bitmap spread over 32 lanes), and the threads that became free
+// take new ants with one warp-aggregated atomic. Visited bitmaps live in shared memory, word w of
+// lane l at [w][l ^ (w mod 32)]: conflict-free both for one word of every lane and for every word of
+// one lane.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tabu_index(uint32_t w, uint32_t l) { return w * 32u + ((l ^ w) & 31u); }
+
+template <int K>
+__global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t it) {
+    extern __shared__ uint32_t smem[];
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t words = a.tabu_words;
+    uint32_t* const tw = smem + (size_t)warp * words * 32u;  // this warp's bitmaps
+    for (uint32_t w = lane; w < words * 32u; w += 32u) tw[w] = 0;
+    __syncwarp();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    // per-thread ant
+    bool active = false, exhausted = false, first = true;
+    uint32_t qi = 0, k = 0, slot = 0, src = 0, dst = 0, n_ants = 1, alpha = 1, beta = 2, s0 = 0, s1 = 0;
+    uint64_t log_base = 0;
+    uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
+    const float* tauf = a.tauf;
+    const uint32_t* hq = a.hq;
+    uint32_t* route = a.routes;
+    const uint32_t n_threads = gridDim.x * blockDim.x;
+    for (;;) {
+        // 1. threads without an ant take the next ticket (the first one statically, no atomic)
+        const bool need = !active && !exhausted;
+        const uint32_t nmask = __ballot_sync(FULL, need);
+        if (nmask) {
+            uint32_t tk = blockIdx.x * blockDim.x + threadIdx.x;
+            if (!first) {
+                const int leader = __ffs(nmask) - 1;
+                uint32_t base = 0;
+                if ((int)lane == leader) base = atomicAdd(a.tickets + it, (uint32_t)__popc(nmask));
+                base = __shfl_sync(FULL, base, leader);
+                tk = n_threads + base + (uint32_t)__popc(nmask & lt_mask);
+            }
+            first = false;
+            if (need) {
+                if (tk >= a.total_ants) {
+                    exhausted = true;
+                } else {
+                    uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tk < ant_prefix[q + 1]
+                    while (hi - lo > 1u) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (__ldg(a.ant_prefix + mid) <= tk) lo = mid;
+                        else hi = mid;
+                    }
+                    const DevQuery q = a.queries[lo];
+                    if (q.active && it < q.n_iter) {
+                        active = true;
+                        qi = lo;
+                        k = tk - q.ant_base;
+                        slot = tk;
+                        src = q.src;
+                        dst = q.dst;
+                        n_ants = q.n_ants;
+                        alpha = q.alpha;
+                        beta = q.beta;
+                        s0 = (uint32_t)q.seed;
+                        s1 = (uint32_t)(q.seed >> 32);
+                        log_base = q.log_base;
+                        tauf = a.tauf + (size_t)qi * a.n_edges;
+                        hq = a.hq + (size_t)qi * a.n_edges;
+                        route = a.routes + (size_t)slot * a.max_steps;
+                        u = src;
+                        beg = __ldg(a.row_ptr + u);
+                        end = __ldg(a.row_ptr + u + 1);
+                        t = W = steps = 0;
+                        tw[tabu_index(u >> 5, lane)] |= 1u << (u & 31);
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULL, active || !exhausted)) break;
+        if (!__any_sync(FULL, active)) continue;
+        // 2. one step of every active ant
+        bool done = false;
+        if (active && u == dst) {
+            done = true;
+            status = kAntSuccess;
+        } else if (active && steps == a.max_steps) {
+            done = true;
+            status = kAntStepCap;
+        }
+        const bool stepping = active && !done;
+        const uint32_t deg = stepping ? end - beg : 0u;
+        const uint32_t wmax = __reduce_max_sync(FULL, deg);
+        if (wmax > 0u) {
+            uint4 r0[K], r1[K];
+            uint2 r2[K];
+            float tf[K];
+            uint32_t he[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if ((uint32_t)j < wmax) {  // warp-uniform; slots past a row read road 0 and are masked
+                    const uint32_t e = (uint32_t)j < deg ? beg + j : 0u;
+                    const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+                    r0[j] = __ldg(rp);
+                    r1[j] = __ldg(rp + 1);
+                    r2[j] = __ldg(reinterpret_cast<const uint2*>(rp + 2));
+                    tf[j] = __ldg(tauf + e);
+                    he[j] = __ldg(hq + e);
+                } else {
+                    r0[j] = r1[j] = make_uint4(0, 0, 0, 0);
+                    r2[j] = make_uint2(0, 0);
+                    tf[j] = 0.0f;
+                    he[j] = 0;
+                }
+            }
+            const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
+            const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            uint32_t cmask = 0, cong = 0;
+            uint32_t sb[K], wv[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                sb[j] = wv[j] = 0;
+                if ((uint32_t)j < wmax) {
+                    const uint32_t v = r0[j].x, cy = r1[j].y;
+                    const bool unvisited = !((tw[tabu_index(v >> 5, lane)] >> (v & 31)) & 1u);
+                    cmask |= (((uint32_t)j < deg && unvisited) ? 1u : 0u) << j;
+                    cong |= (r2[j].y & 1u) << j;
+                    const uint32_t sw =
+                        signal_wait(a.t_dep + t + r0[j].w, cy | (cy == 0u), r2[j].x, r1[j].z, r1[j].w);
+                    const uint32_t w = (v != dst && cy != 0u) ? sw + r1[j].x : 0u;
+                    wv[j] = w;
+                    sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].w + w + he[j], beta));
+                }
+            }
+            if (a.thr_on && (cmask & ~cong) && (cmask & cong)) cmask &= ~cong;
+            if (stepping && cmask == 0u) {
+                done = true;
+                status = kAntDeadEnd;
+            }
+            uint32_t mb = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) mb = max(mb, (cmask >> j & 1u) ? sb[j] : 0u);
+            const WeightScale sc = weight_scale(mb);
+            unsigned long long incl[K], S = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                S += (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
+                incl[j] = S;
+            }
+            const unsigned long long r = mulhi_draw(rnd, S);
+            int js = 0;
+            bool found = false;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {  // first candidate whose running weight exceeds r
+                const bool hit = !found && (cmask >> j & 1u) && incl[j] > r;
+                js = hit ? j : js;
+                found |= hit;
+            }
+            uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const bool sel = js == j;
+                c_h = sel ? r0[j].x : c_h;
+                c_vb = sel ? r0[j].y : c_vb;
+                c_ve = sel ? r0[j].z : c_ve;
+                c_tt = sel ? r0[j].w : c_tt;
+                c_w = sel ? wv[j] : c_w;
+            }
+            if (stepping && !done) {
+                route[steps] = beg + (uint32_t)js;
+                t += c_tt + c_w;
+                W += c_w;
+                u = c_h;
+                beg = c_vb;
+                end = c_ve;
+                tw[tabu_index(u >> 5, lane)] |= 1u << (u & 31);
+                ++steps;
+                if (t > kTCap) {
+                    done = true;
+                    status = kAntTimeCap;
+                }
+            }
+        }
+        // 3. ants that ended: per-ant records by their own lane, deposits and bitmap reset by the warp
+        uint32_t fmask = __ballot_sync(FULL, done);
+        if (fmask) {
+            unsigned long long delta = 0;
+            if (done) {
+                QueryState* S = a.qs + qi;
+                a.ant_steps[slot] = steps;
+                a.ant_wait[slot] = W;
+                atomicAdd(&S->steps, (unsigned long long)steps);
+                if (a.ant_log) {
+                    uint32_t* l = a.ant_log + 4ull * (log_base + (uint64_t)it * n_ants + k);
+                    *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
+                }
+                if (status == kAntSuccess) {
+                    atomicAdd(&S->nsucc, 1ull);
+                    delta = S->dep_num / t;
+                    atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * n_ants + k));
+                }
+            }
+            __syncwarp();
+            while (fmask) {
+                const int f = __ffs(fmask) - 1;
+                fmask &= fmask - 1u;
+                const unsigned long long fd = __shfl_sync(FULL, delta, f);
+                const uint32_t fsteps = __shfl_sync(FULL, steps, f);
+                const uint32_t fqi = __shfl_sync(FULL, qi, f);
+                const uint32_t fslot = __shfl_sync(FULL, slot, f);
+                if (fd) {  // Updt_Pher: deposit dep_num / T on every road of the route
+                    unsigned long long* D = a.dep + (size_t)fqi * a.n_edges;
+                    const uint32_t* fr = a.routes + (size_t)fslot * a.max_steps;
+                    for (uint32_t i = lane; i < fsteps; i += 32u) atomicAdd(D + fr[i], fd);
+                }
+                for (uint32_t w = lane; w < words; w += 32u) tw[tabu_index(w, (uint32_t)f)] = 0;
+            }
+            __syncwarp();
+            if (done) active = false;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Evap_Pher + Updt_Pher: tau <- tau - floor(tau * rho_fix / 2^32) + D ; D <- 0.
 // ------------------------------------------------------------------------------------------------
 __global__ void k_evaporate(uint32_t E, const DevQuery* __restrict__ q, uint64_t* __restrict__ tau,
-                            unsigned long long* __restrict__ dep, uint32_t it) {
+                            float* __restrict__ tauf, unsigned long long* __restrict__ dep, uint32_t it) {
     const uint32_t qi = blockIdx.y;
     const uint32_t active = q[qi].active, n_iter = q[qi].n_iter;
     if (!active || it >= n_iter) return;
     const uint64_t rf = q[qi].rho_fix;
     uint64_t* T = tau + (size_t)qi * E;
+    float* TF = tauf + (size_t)qi * E;
     unsigned long long* D = dep + (size_t)qi * E;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         const uint64_t t = T[e];
         const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
-        T[e] = t - ((hi << 32) | (lo >> 32)) + D[e];
+        const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + D[e];
+        T[e] = nt;
+        TF[e] = tau_float(nt);
         D[e] = 0;
     }
 }
@@ -525,18 +700,18 @@ cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_
 
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
-                              unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
+                              float* tauf, unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
-    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, dep, hq, qs, tickets, n_tickets);
+    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, tauf, dep, hq, qs, tickets, n_tickets);
     return cudaGetLastError();
 }
 
 cudaError_t launch_evaporate(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, uint64_t* tau,
-                             unsigned long long* dep, uint32_t it) {
+                             float* tauf, unsigned long long* dep, uint32_t it) {
     if (E == 0) return cudaSuccess;
     dim3 grid(blocks_for(E, 1024), Q);
-    k_evaporate<<<grid, 256, 0, s>>>(E, q, tau, dep, it);
+    k_evaporate<<<grid, 256, 0, s>>>(E, q, tau, tauf, dep, it);
     return cudaGetLastError();
 }
 
@@ -563,12 +738,16 @@ static cudaError_t config_for(int device, uint32_t n_nodes, uint32_t total_ants,
     const bool in_smem = smem <= 64u * 1024u;
     const size_t dyn = in_smem ? smem : 0;
     cudaError_t err;
-    if (dyn > 48u * 1024u) {
-        err = cudaFuncSetAttribute(k_construct<G, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (err != cudaSuccess) return err;
-    }
     int per_sm = 0, sms = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct<G, K>, block, dyn);
+    if (in_smem) {
+        if (dyn > 48u * 1024u) {
+            err = cudaFuncSetAttribute(k_construct<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (err != cudaSuccess) return err;
+        }
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct<G, K, true>, block, dyn);
+    } else {
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct<G, K, false>, block, 0);
+    }
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (err != cudaSuccess) return err;
@@ -593,10 +772,49 @@ static int slots_for(int lanes, uint32_t max_degree) {
     return 0;
 }
 
-int construct_max_degree(int lanes) { return lanes * 4; }
+int construct_max_degree(int lanes) { return lanes == 1 ? 8 : lanes * 4; }
+
+// Lockstep thread-per-ant variant: visited bitmaps of every thread of the block in shared memory.
+template <int K>
+static cudaError_t config_t(int device, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out) {
+    const int block = 64;
+    const uint32_t words = (n_nodes + 31u) / 32u;
+    const size_t smem = (size_t)block * words * 4u;
+    if (smem > 200u * 1024u) return cudaErrorInvalidValue;
+    cudaError_t err;
+    if (smem > 48u * 1024u) {
+        err = cudaFuncSetAttribute(k_construct_lock<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    int per_sm = 0, sms = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_lock<K>, block, smem);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidValue;
+    const uint64_t need = ((uint64_t)total_ants + block - 1) / block;
+    uint64_t grid = (uint64_t)per_sm * sms;
+    if (need < grid) grid = need;
+    out->lanes = 1;
+    out->slots = K;
+    out->block = block;
+    out->grid = (int)(grid < 1 ? 1 : grid);
+    out->smem = smem;
+    out->tabu_in_smem = true;
+    out->lockstep = false;  // dispatched on lanes == 1
+    return cudaSuccess;
+}
+
+bool construct_thread_fits(uint32_t n_nodes) { return 64ull * ((n_nodes + 31u) / 32u) * 4u <= 200u * 1024u; }
 
 cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, uint32_t total_ants,
                              KernelConfig* out) {
+    if (lanes == 1) {
+        if (max_degree <= 4) return config_t<4>(device, n_nodes, total_ants, out);
+        if (max_degree <= 6) return config_t<6>(device, n_nodes, total_ants, out);
+        if (max_degree <= 8) return config_t<8>(device, n_nodes, total_ants, out);
+        return cudaErrorInvalidValue;
+    }
     const int k = slots_for(lanes, max_degree);
 #define GMP_CFG(G_, K_) \
     if (lanes == G_ && k == K_) return config_for<G_, K_>(device, n_nodes, total_ants, out);
@@ -606,11 +824,78 @@ cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t m
     return cudaErrorInvalidValue;
 }
 
+template <int G, int K>
+static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out) {
+    const int block = 128;
+    const int groups = block / G;
+    const uint32_t words = (n_nodes + 31u) / 32u;
+    const size_t smem = (size_t)groups * words * 4u;
+    const bool in_smem = smem <= 64u * 1024u;
+    const size_t dyn = in_smem ? smem : 0;
+    cudaError_t err;
+    int per_sm = 0, sms = 0;
+    if (in_smem) {
+        if (dyn > 48u * 1024u) {
+            err = cudaFuncSetAttribute(k_construct_gl<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dyn);
+            if (err != cudaSuccess) return err;
+        }
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true>, block, dyn);
+    } else {
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, false>, block, 0);
+    }
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t need = ((uint64_t)total_ants + groups - 1) / groups;
+    uint64_t grid = (uint64_t)per_sm * sms;
+    if (need < grid) grid = need;
+    out->lanes = G;
+    out->slots = K;
+    out->block = block;
+    out->grid = (int)(grid < 1 ? 1 : grid);
+    out->smem = dyn;
+    out->tabu_in_smem = in_smem;
+    out->lockstep = true;
+    return cudaSuccess;
+}
+
+cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, uint32_t max_degree,
+                                      uint32_t total_ants, KernelConfig* out) {
+    const int k = (uint32_t)lanes >= max_degree ? 1 : ((uint32_t)(2 * lanes) >= max_degree ? 2 : 0);
+    if (lanes == 4 && k == 1) return config_gl<4, 1>(device, n_nodes, total_ants, out);
+    if (lanes == 4 && k == 2) return config_gl<4, 2>(device, n_nodes, total_ants, out);
+    if (lanes == 8 && k == 1) return config_gl<8, 1>(device, n_nodes, total_ants, out);
+    if (lanes == 8 && k == 2) return config_gl<8, 2>(device, n_nodes, total_ants, out);
+    if (lanes == 16 && k == 1) return config_gl<16, 1>(device, n_nodes, total_ants, out);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it) {
-#define GMP_LAUNCH(G_, K_)                                                    \
-    if (kc.lanes == G_ && kc.slots == K_) {                                   \
-        k_construct<G_, K_><<<kc.grid, kc.block, kc.smem, s>>>(a, it);        \
-        return cudaGetLastError();                                            \
+    if (kc.lockstep) {
+#define GMP_LAUNCH_GL(G_, K_)                                                                     \
+    if (kc.lanes == G_ && kc.slots == K_) {                                                       \
+        if (kc.tabu_in_smem) k_construct_gl<G_, K_, true><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
+        else k_construct_gl<G_, K_, false><<<kc.grid, kc.block, 0, s>>>(a, it);                  \
+        return cudaGetLastError();                                                                \
+    }
+        GMP_LAUNCH_GL(4, 1) GMP_LAUNCH_GL(4, 2) GMP_LAUNCH_GL(8, 1) GMP_LAUNCH_GL(8, 2) GMP_LAUNCH_GL(16, 1)
+#undef GMP_LAUNCH_GL
+        return cudaErrorInvalidValue;
+    }
+#define GMP_LAUNCH(G_, K_)                                                            \
+    if (kc.lanes == G_ && kc.slots == K_) {                                           \
+        if (kc.tabu_in_smem) k_construct<G_, K_, true><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
+        else k_construct<G_, K_, false><<<kc.grid, kc.block, 0, s>>>(a, it);          \
+        return cudaGetLastError();                                                    \
+    }
+    if (kc.lanes == 1) {
+        if (kc.slots == 4) k_construct_lock<4><<<kc.grid, kc.block, kc.smem, s>>>(a, it);
+        else if (kc.slots == 6) k_construct_lock<6><<<kc.grid, kc.block, kc.smem, s>>>(a, it);
+        else if (kc.slots == 8) k_construct_lock<8><<<kc.grid, kc.block, kc.smem, s>>>(a, it);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
     }
     GMP_LAUNCH(4, 1) GMP_LAUNCH(4, 2) GMP_LAUNCH(4, 4) GMP_LAUNCH(8, 1) GMP_LAUNCH(8, 2) GMP_LAUNCH(8, 4)
     GMP_LAUNCH(16, 1) GMP_LAUNCH(16, 2) GMP_LAUNCH(16, 4) GMP_LAUNCH(32, 1) GMP_LAUNCH(32, 2) GMP_LAUNCH(32, 4)

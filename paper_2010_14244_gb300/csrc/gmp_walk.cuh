@@ -1,0 +1,326 @@
+// Device routines shared by the iteration kernels (gmp_kernels.cu) and the persistent job
+// (gmp_persistent.cu): the sub-warp ant walk and the preemptive phase order of one intersection.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gmp_device.cuh"
+#include "gmp_internal.h"
+
+namespace gmp {
+
+// Preemptive phase order of intersection v (Calc_Dens / Comp_Thres; Fig. 3 signal block): queues and
+// storage per phase from the node's in-edges; order (1) phases whose queue exceeds 3/4 of their
+// storage, longest first; else (2) phases red for longer than a cycle, longest first; else (3) the
+// longest non-empty queue; then the remaining non-empty phases, then the empty ones, each in index
+// order. Every in-edge's record then gets its approach's green window under that order.
+__device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restrict__ in_ptr,
+                                           const uint32_t* __restrict__ in_edge, const uint8_t* __restrict__ nph,
+                                           const uint32_t* __restrict__ cycle, const uint32_t* __restrict__ offset,
+                                           const uint32_t* __restrict__ green, const uint8_t* __restrict__ ephase,
+                                           const uint32_t* __restrict__ veh, const uint32_t* __restrict__ cap,
+                                           const uint32_t* __restrict__ red, uint8_t* __restrict__ order,
+                                           EdgeRec* __restrict__ rec) {
+    const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
+    uint8_t ord[kMaxPhases];
+    if (P == 0) {
+        for (uint32_t i = 0; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
+        for (uint32_t i = ib; i < ie; ++i) {
+            EdgeRec& r = rec[in_edge[i]];
+            r.cycle = 0;
+            r.gbeg = 0;
+            r.glen = 0;
+            r.cmagic = 0;
+        }
+        return;
+    }
+    uint64_t Q[kMaxPhases], S[kMaxPhases];
+    for (uint32_t p = 0; p < kMaxPhases; ++p) Q[p] = S[p] = 0;
+    for (uint32_t i = ib; i < ie; ++i) {
+        const uint32_t e = in_edge[i];
+        const uint32_t p = ephase[e] & (kMaxPhases - 1);
+        Q[p] += veh[e];
+        S[p] += cap[e];
+    }
+    const uint32_t cy = cycle[v];
+    uint32_t over = 0, starved = 0, nonempty = 0;
+    uint32_t rd[kMaxPhases];
+    for (uint32_t p = 0; p < P; ++p) {
+        rd[p] = red[(size_t)v * kMaxPhases + p];
+        if (Q[p] > S[p] * 3u / 4u) over |= 1u << p;
+        if (rd[p] > cy) starved |= 1u << p;
+        if (Q[p] > 0) nonempty |= 1u << p;
+    }
+    uint32_t used = 0, n = 0;
+    if (over) {
+        while (over & ~used) {
+            int best = -1;
+            for (uint32_t p = 0; p < P; ++p)
+                if ((over & ~used) >> p & 1u)
+                    if (best < 0 || Q[p] > Q[best]) best = (int)p;
+            used |= 1u << best;
+            ord[n++] = (uint8_t)best;
+        }
+    } else if (starved) {
+        while (starved & ~used) {
+            int best = -1;
+            for (uint32_t p = 0; p < P; ++p)
+                if ((starved & ~used) >> p & 1u)
+                    if (best < 0 || rd[p] > rd[best]) best = (int)p;
+            used |= 1u << best;
+            ord[n++] = (uint8_t)best;
+        }
+    } else if (nonempty) {
+        int best = -1;
+        for (uint32_t p = 0; p < P; ++p)
+            if (nonempty >> p & 1u)
+                if (best < 0 || Q[p] > Q[best]) best = (int)p;
+        used |= 1u << best;
+        ord[n++] = (uint8_t)best;
+    }
+    for (uint32_t p = 0; p < P; ++p)
+        if (!(used >> p & 1u) && (nonempty >> p & 1u)) {
+            used |= 1u << p;
+            ord[n++] = (uint8_t)p;
+        }
+    for (uint32_t p = 0; p < P; ++p)
+        if (!(used >> p & 1u)) {
+            used |= 1u << p;
+            ord[n++] = (uint8_t)p;
+        }
+    uint32_t start[kMaxPhases];
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < P; ++i) {
+        order[(size_t)v * kMaxPhases + i] = ord[i];
+        start[ord[i]] = acc;
+        acc += green[(size_t)v * kMaxPhases + ord[i]];
+    }
+    for (uint32_t i = P; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
+    const uint32_t off = offset[v];
+    const uint32_t magic = 0xFFFFFFFFu / cy;
+    for (uint32_t i = ib; i < ie; ++i) {
+        const uint32_t e = in_edge[i];
+        const uint32_t p = ephase[e] & (kMaxPhases - 1);
+        EdgeRec& r = rec[e];
+        r.cycle = cy;
+        r.gbeg = (off + start[p]) % cy;
+        r.glen = green[(size_t)v * kMaxPhases + p];
+        r.cmagic = magic;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Ant construction. G lanes of a warp serve one ant (sub-warp group); lane l holds the candidates
+// l, l+G, ..., l+(K-1)G of the current node's CSR row. Per step: one round of independent 16-byte
+// record loads and pheromone loads, scores, a group max, integer weights, a shuffle prefix sum,
+// one Philox draw, a ballot to find the chosen road and shuffles to broadcast it.
+// Groups take ants from a per-iteration ticket counter, so short walks free lanes for waiting ants.
+// ------------------------------------------------------------------------------------------------
+template <int G, int K>
+__device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery& q, uint32_t qi, uint32_t k,
+                                         uint32_t it, uint32_t* tabu, uint32_t lane, uint32_t gmask, uint32_t gbase) {
+    constexpr int NC = G * K;              // candidate slots of the group
+    constexpr bool kGather = NC <= 16;     // every lane gathers all scores and picks locally
+    constexpr uint32_t kNone = 0xFFFFFFFFu;  // not a candidate (scores are non-negative floats)
+    const float* __restrict__ tauf = a.tauf + (size_t)qi * a.n_edges;
+    const uint32_t* __restrict__ hq = a.hq + (size_t)qi * a.n_edges;
+    const uint32_t slot = q.ant_base + k;
+    uint32_t* route = a.routes + (size_t)slot * a.max_steps;
+    const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
+    uint32_t u = q.src;
+    uint32_t beg = __ldg(a.row_ptr + u), end = __ldg(a.row_ptr + u + 1);
+    uint32_t t = 0, W = 0, steps = 0, status;
+    if (lane == 0) atomicOr(tabu + (u >> 5), 1u << (u & 31));
+    __syncwarp(gmask);
+    for (;;) {
+        if (u == q.dst) {
+            status = kAntSuccess;
+            break;
+        }
+        if (steps == a.max_steps) {
+            status = kAntStepCap;
+            break;
+        }
+        const uint32_t deg = end - beg;
+        const int nslots = K == 1 ? 1 : (int)((deg + G - 1) / G);  // group-uniform
+        // 1. issue every load of this step: records, pheromone and heuristic of this lane's candidates
+        uint4 r0[K], r1[K];
+        uint2 r2[K];
+        float tf[K];
+        uint32_t he[K];
+        uint32_t valid = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {  // slots past the row read road 0 (always in bounds) and are masked
+            const uint32_t idx = lane + (uint32_t)j * G;
+            const bool ok = j < nslots && idx < deg;
+            valid |= (ok ? 1u : 0u) << j;
+            const uint32_t e = ok ? beg + idx : 0u;
+            const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+            r0[j] = __ldg(rp);
+            r1[j] = __ldg(rp + 1);
+            r2[j] = __ldg(reinterpret_cast<const uint2*>(rp + 2));
+            tf[j] = __ldg(tauf + e);
+            he[j] = __ldg(hq + e);
+        }
+        // 2. the draw of this step depends on (iteration, ant, step) only: overlaps the loads
+        const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
+        const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+        // 3. candidates, waits, scores
+        uint32_t cmask = 0, cong = 0;
+        uint32_t sb[K], wv[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t v = r0[j].x, cy = r1[j].y;
+            const bool unvisited = !((tabu[v >> 5] >> (v & 31)) & 1u);
+            cmask |= ((valid >> j) & (unvisited ? 1u : 0u)) << j;
+            cong |= (r2[j].y & 1u) << j;
+            const uint32_t sw = signal_wait(a.t_dep + t + r0[j].w, cy | (cy == 0u), r2[j].x, r1[j].z, r1[j].w);
+            const uint32_t w = (v != q.dst && cy != 0u) ? sw + r1[j].x : 0u;
+            wv[j] = w;
+            sb[j] = __float_as_uint(score_f(tf[j], q.alpha, r0[j].w + w + he[j], q.beta));
+        }
+        if (a.thr_on) {  // congested roads drop out unless every candidate is congested
+            const uint32_t any_ok = __ballot_sync(gmask, (cmask & ~cong) != 0u) & gmask;
+            const uint32_t any_cg = __ballot_sync(gmask, (cmask & cong) != 0u) & gmask;
+            if (any_ok && any_cg) cmask &= ~cong;
+        }
+        int pick_lane, pick_slot;
+        if constexpr (kGather) {
+            if ((__ballot_sync(gmask, cmask != 0u) & gmask) == 0u) {
+                status = kAntDeadEnd;
+                break;
+            }
+            // 4. largest candidate score of the group (non-negative floats order like their bits)
+            uint32_t mb = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) mb = max(mb, (cmask >> j & 1u) ? sb[j] : 0u);
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(gmask, mb, off, G));
+            // 5. own integer weights; every lane gathers the group's weights and picks locally
+            const WeightScale sc = weight_scale(mb);
+            unsigned long long incl[NC];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const uint32_t mine = (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
+#pragma unroll
+                for (int l = 0; l < G; ++l) incl[j * G + l] = j < nslots ? __shfl_sync(gmask, mine, l, G) : 0u;
+            }
+#pragma unroll
+            for (int h = 1; h < NC; h <<= 1)  // inclusive running sums in log depth (Kogge-Stone)
+#pragma unroll
+                for (int i = NC - 1; i >= h; --i) incl[i] += incl[i - h];
+            // roulette: the first candidate (CSR order = index lane + j*G) whose running weight exceeds
+            // r is the number of running weights <= r
+            const unsigned long long r = mulhi_draw(rnd, incl[NC - 1]);
+            int pick = 0;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) pick += incl[i] <= r ? 1 : 0;
+            pick_lane = pick % G;
+            pick_slot = pick / G;
+        } else {
+            if ((__ballot_sync(gmask, cmask != 0u) & gmask) == 0u) {
+                status = kAntDeadEnd;
+                break;
+            }
+            // 4. largest score of the group (non-negative floats order like their bit patterns)
+            uint32_t mb = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if ((cmask >> j & 1u) && sb[j] > mb) mb = sb[j];
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(gmask, mb, off, G));
+            // 5. integer weights, inclusive prefix in CSR order (index lane + j*G) by shuffles, roulette
+            const WeightScale sc = weight_scale(mb);
+            unsigned long long carry = 0, incl[K];
+            uint32_t wt[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                wt[j] = 0;
+                incl[j] = carry;
+                if (j < nslots) {
+                    wt[j] = (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
+                    unsigned long long xs = wt[j];
+#pragma unroll
+                    for (int d = 1; d < G; d <<= 1) {
+                        const unsigned long long y = __shfl_up_sync(gmask, xs, d, G);
+                        if (lane >= (uint32_t)d) xs += y;
+                    }
+                    incl[j] = carry + xs;
+                    carry = __shfl_sync(gmask, incl[j], G - 1, G);
+                }
+            }
+            const unsigned long long r = mulhi_draw(rnd, carry);
+            int js = -1;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (wt[j] != 0u && incl[j] - wt[j] <= r && r < incl[j]) js = j;
+            const uint32_t bw = __ballot_sync(gmask, js >= 0) & gmask;
+            pick_lane = (__ffs(bw) - 1) - (int)gbase;
+            pick_slot = __shfl_sync(gmask, js, pick_lane, G);
+        }
+        // 6. the chosen candidate's data from the lane that evaluated it
+        uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (pick_slot == j) {
+                c_h = r0[j].x;
+                c_vb = r0[j].y;
+                c_ve = r0[j].z;
+                c_tt = r0[j].w;
+                c_w = wv[j];
+            }
+        c_h = __shfl_sync(gmask, c_h, pick_lane, G);
+        c_vb = __shfl_sync(gmask, c_vb, pick_lane, G);
+        c_ve = __shfl_sync(gmask, c_ve, pick_lane, G);
+        c_tt = __shfl_sync(gmask, c_tt, pick_lane, G);
+        c_w = __shfl_sync(gmask, c_w, pick_lane, G);
+        // 7. position update
+        const uint32_t e = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
+        t += c_tt + c_w;
+        W += c_w;
+        u = c_h;
+        beg = c_vb;
+        end = c_ve;
+        if (lane == 0) {
+            route[steps] = e;
+            atomicOr(tabu + (u >> 5), 1u << (u & 31));
+        }
+        ++steps;
+        __syncwarp(gmask);
+        if (t > kTCap) {
+            status = kAntTimeCap;
+            break;
+        }
+    }
+    QueryState* S = a.qs + qi;
+    if (lane == 0) {
+        a.ant_steps[slot] = steps;
+        a.ant_wait[slot] = W;
+        atomicAdd(&S->steps, (unsigned long long)steps);
+        if (status == kAntSuccess) atomicAdd(&S->nsucc, 1ull);
+        if (a.ant_log) {
+            uint32_t* l = a.ant_log + 4ull * (q.log_base + (uint64_t)it * q.n_ants + k);
+            *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
+        }
+    }
+    if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
+        const unsigned long long delta = S->dep_num / t;
+        unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
+        for (uint32_t i = lane; i < steps; i += G) atomicAdd(D + route[i], delta);
+        if (lane == 0) atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * q.n_ants + k));
+    }
+    // forget the visited set: whole bitmap when small, else just the nodes of this walk
+    if (a.tabu_words <= 2u * (steps + 1u)) {
+        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+    } else {
+        if (lane == 0) atomicAnd(tabu + (q.src >> 5), ~(1u << (q.src & 31)));
+        for (uint32_t i = lane; i < steps; i += G) {
+            const uint32_t v = __ldg(a.col + route[i]);
+            atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
+        }
+    }
+    __syncwarp(gmask);
+}
+
+}  // namespace gmp

@@ -18,7 +18,7 @@ FLAG_RANDOM_TAU = 1
 FLAG_ANT_LOG = 2
 FLAG_KERNEL_TIMING = 4
 FLAG_NO_GRAPH = 8
-FLAG_NO_PREFETCH = 16
+FLAG_NO_LOCKSTEP = 16
 MODE_AUTO, MODE_ITERATIVE, MODE_PERSISTENT = 0, 1, 2
 
 _LIB = None

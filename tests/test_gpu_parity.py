@@ -88,16 +88,17 @@ def test_phase_order_with_red_times_and_queues(gm, ctx, orc):
     _compare(orc, onet, orc.Params(), q, r, ctx, 0, ctx.ant_log(0))
 
 
-def test_grid10_full_parity(gm, ctx, orc):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_grid10_full_parity(gm, ctx, orc, mode):
     wl = W.grid10()
     ctx.load_workload(wl)
-    ctx.set_params(flags=gm.FLAG_ANT_LOG)
+    ctx.set_params(flags=gm.FLAG_ANT_LOG, mode=mode)
     q = wl.queries[0]
     r = ctx.solve_batch([q])[0]
     _compare(orc, orc.Net.from_workload(wl), orc.Params(), q, r, ctx, 0, ctx.ant_log(0))
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 4, 8, 16, 32])
 def test_grid10_same_result_for_every_lane_count(gm, ctx, orc, lanes):
     wl = W.grid10(n_ants=48, n_iter=20)
     ctx.load_workload(wl)
@@ -134,21 +135,24 @@ def test_grid10_variants(gm, ctx, orc, variant):
     _compare(orc, orc.Net.from_workload(wl), orc.Params(**okw), q, r, ctx)
 
 
-def test_grid64_batch_parity_reduced(gm, ctx, orc):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_grid64_batch_parity_reduced(gm, ctx, orc, mode):
     """Four colonies of 256 ants x 20 iterations in one job; each equals its solo oracle solve."""
     wl = W.grid64(n_queries=4, n_ants=256, n_iter=20)
     ctx.load_workload(wl)
-    ctx.set_params(flags=gm.FLAG_ANT_LOG)
+    ctx.set_params(flags=gm.FLAG_ANT_LOG, mode=mode)
     res = ctx.solve_batch(wl.queries)
     onet = orc.Net.from_workload(wl)
     for i, q in enumerate(wl.queries):
         _compare(orc, onet, orc.Params(), q, res[i], ctx, i, ctx.ant_log(i))
 
 
-def test_ragged_batch_equals_solo(gm, ctx, orc):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_ragged_batch_equals_solo(gm, ctx, orc, mode):
     """Different ants, iterations, alpha/beta/rho and seeds per colony, plus src == dst."""
     wl = W.grid64(n_queries=5)
     ctx.load_workload(wl)
+    ctx.set_params(mode=mode)
     base = wl.queries
     qs = [Q(base[0].src, base[0].dst, 96, 7, 1.0, 2.0, 0.1, 5),
           Q(base[1].src, base[1].dst, 33, 12, 2.0, 1.0, 0.3, 6),
@@ -161,12 +165,13 @@ def test_ragged_batch_equals_solo(gm, ctx, orc):
         _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
 
 
-def test_grid64_full_size_sampled(gm, ctx, orc):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_grid64_full_size_sampled(gm, ctx, orc, mode):
     """The benchmark's job (16 colonies x 1024 ants x 200 iterations, one launch): three colonies are
     re-solved by the oracle and must agree exactly, including the final pheromone table."""
     wl = W.grid64()
     ctx.load_workload(wl)
-    ctx.set_params(flags=gm.FLAG_KERNEL_TIMING)
+    ctx.set_params(flags=gm.FLAG_KERNEL_TIMING, mode=mode)
     ctx.stage(wl.queries)
     ctx.launch()
     res = ctx.collect()
@@ -183,7 +188,8 @@ def test_grid64_full_size_sampled(gm, ctx, orc):
     assert kt["construct"] > 0 and kt["job"] >= kt["construct"]
 
 
-def test_large_graph_global_visited_sets(gm, ctx, orc):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_large_graph_global_visited_sets(gm, ctx, orc, mode):
     """A 40k-node planar graph: visited bitmaps no longer fit in shared memory."""
     rng = np.random.Generator(np.random.PCG64(8))
     net = W.geometric_network(200, 200, rng)
@@ -193,6 +199,7 @@ def test_large_graph_global_visited_sets(gm, ctx, orc):
     od = W.hop_filtered_od(net, 2, 20, 60, rng)
     qs = [Q(s, d, 64, 6, 1.0, 2.0, 0.1, i) for i, (s, d) in enumerate(od)]
     ctx.load_workload(wl)
+    ctx.set_params(mode=mode)
     res = ctx.solve_batch(qs)
     onet = orc.Net.from_workload(wl)
     for i, q in enumerate(qs):
