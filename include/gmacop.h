@@ -174,6 +174,33 @@ int gmp_get_kernel_times(gmp_ctx *ctx, float *out_ms5);
 /* Count of kernel launches issued by the last gmp_batch_launch. */
 int gmp_get_launch_count(const gmp_ctx *ctx, uint64_t *out);
 
+/* Result row written to device memory by gmp_solve_static (the same fields as gmp_result, without the
+ * route buffer; status GMP_OK or GMP_ERR_NO_ROUTE; route_len counts nodes). */
+typedef struct {
+    uint64_t travel_ms, wait_ms, ant_steps, n_success;
+    uint32_t route_len, best_iter, best_ant;
+    int32_t status;
+} gmp_device_result;
+
+/* Size of the library's static scratch array used by gmp_solve_static. */
+#define GMP_STATIC_SCRATCH_BYTES ((uint64_t)32 << 20)
+
+/* One colony on the context's graph that allocates no device memory during the call. The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc while they solve (a loop that must never
+ * wait on the allocator, an exhausted memory pool or quota, a framework that owns every allocation).
+ * Every temporary lives in a device array of GMP_STATIC_SCRATCH_BYTES that the library defines at file
+ * scope; the caller passes the outputs: d_result (one row) and d_route (route_cap >= max_steps + 1
+ * entries), both device memory of the context's GPU. The work is issued on the context's stream and
+ * the call returns without waiting; synchronise that stream before reading the outputs. The first call
+ * on a device looks the array's address up, so make it before any stream capture. Every call reuses the
+ * same array (which keeps the previous call's data; each call re-initialises what it needs), so calls
+ * that overlap on the GPU race. The colony runs like gmp_solve (same results, the ant log excepted).
+ * Errors: INVALID_ARG, UNSUPPORTED, STATE, CUDA; BUFFER when route_cap is short or when the colony's
+ * temporaries (about 24 bytes per road plus 4 * n_ants * max_steps bytes) exceed the array. */
+int gmp_solve_static(gmp_ctx *ctx, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha,
+                     float beta, float rho, uint64_t seed, gmp_device_result *d_result, uint32_t *d_route,
+                     uint32_t route_cap);
+
 #ifdef __cplusplus
 }
 #endif

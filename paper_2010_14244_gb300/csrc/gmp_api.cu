@@ -930,3 +930,156 @@ int gmp_get_launch_count(const gmp_ctx* c, uint64_t* out) {
 }
 
 }  // extern "C"
+
+// =====================================================================================================
+// gmp_solve_static: one colony without any device allocation by the call.
+//
+// Some callers cannot allocate device memory when they solve: code running where cudaMalloc is
+// forbidden or unsafe (inside a latency-critical loop that must never block on the allocator, under a
+// device memory pool or quota that is already spent, or from a framework that owns all allocations).
+// For them this entry point keeps every temporary of the colony in one file-scope device array of
+// GMP_STATIC_SCRATCH_BYTES and writes the result into buffers the caller already owns. The array
+// exists on every GPU that loads the library, for the life of the process. Its device address is
+// looked up once per device, by the first call on that device, which should therefore come before
+// any stream capture. All calls share the array and it keeps the last call's contents: every call
+// re-initialises what must start from zero or from its initial value, and calls whose work overlaps
+// on the GPU (for example on two streams) race on it.
+// =====================================================================================================
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[GMP_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+void* g_static_ptr[kStaticMaxDevices] = {nullptr};
+
+__global__ void k_static_query(DevQuery q, DevQuery* __restrict__ dq, uint32_t* __restrict__ prefix) {
+    dq[0] = q;
+    prefix[0] = 0;
+    prefix[1] = q.n_ants;
+}
+
+size_t align256(size_t n) { return (n + 255u) & ~(size_t)255u; }
+
+}  // namespace
+
+extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha,
+                                float beta, float rho, uint64_t seed, gmp_device_result* d_result, uint32_t* d_route,
+                                uint32_t route_cap) {
+    static_assert(sizeof(gmp_device_result) == sizeof(DevResult), "result row layout");
+    if (!c || !d_result || !d_route) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    gmp_query qq;
+    memset(&qq, 0, sizeof qq);
+    qq.src = src;
+    qq.dst = dst;
+    qq.n_ants = n_ants;
+    qq.n_iter = n_iter;
+    qq.alpha = alpha;
+    qq.beta = beta;
+    qq.rho = rho;
+    qq.seed = seed;
+    GMP_TRY(check_query(c, qq, 0));
+    if (c->device < 0 || c->device >= kStaticMaxDevices) return fail(c, GMP_ERR_UNSUPPORTED, "device index too high");
+    const int lanes = pick_lanes(c);
+    if ((uint32_t)construct_max_degree(lanes) < c->maxdeg || c->maxdeg > 128u || lanes == 1)
+        return fail(c, GMP_ERR_UNSUPPORTED, "out-degree %u is beyond the static solve's kernels", c->maxdeg);
+    GMP_CUDA(c, cudaSetDevice(c->device));
+    if (!g_static_ptr[c->device]) {  // first call on this device: where the scratch array lives
+        void* p = nullptr;
+        GMP_CUDA(c, cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_ptr[c->device] = p;
+    }
+    const uint32_t S = std::max<uint32_t>(default_max_steps(c), 1u);
+    if (route_cap < S + 1u)
+        return fail(c, GMP_ERR_BUFFER, "route buffer needs %u entries (max_steps + 1)", S + 1u);
+    KernelConfig kc{};
+    if (lanes <= 16 && c->maxdeg <= (uint32_t)(2 * lanes) && lanes * (c->maxdeg <= (uint32_t)lanes ? 1 : 2) <= 16)
+        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, n_ants, &kc));
+    else
+        GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, n_ants, &kc));
+    // carve the scratch array
+    const size_t E = c->E, words = (c->N + 31u) / 32u;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align256(std::max<size_t>(bytes, 1));
+        return o;
+    };
+    const size_t o_dq = take(sizeof(DevQuery)), o_prefix = take(8), o_qs = take(sizeof(QueryState));
+    const size_t o_tickets = take((size_t)n_iter * 4), o_tau = take(E * 8), o_tauf = take(E * 4), o_dep = take(E * 8);
+    const size_t o_heur = take(E * 4), o_routes = take((size_t)n_ants * S * 4), o_steps = take((size_t)n_ants * 4);
+    const size_t o_wait = take((size_t)n_ants * 4), o_best = take((size_t)S * 4);
+    const size_t o_tabu = kc.tabu_in_smem ? 0 : take((size_t)kc.grid * (kc.block / kc.lanes) * words * 4);
+    if (off > GMP_STATIC_SCRATCH_BYTES)
+        return fail(c, GMP_ERR_BUFFER, "this colony needs %zu bytes of static scratch, the limit is %llu", off,
+                    (unsigned long long)GMP_STATIC_SCRATCH_BYTES);
+    unsigned char* base = static_cast<unsigned char*>(g_static_ptr[c->device]);
+    DevQuery* dq = reinterpret_cast<DevQuery*>(base + o_dq);
+    uint32_t* prefix = reinterpret_cast<uint32_t*>(base + o_prefix);
+    QueryState* qs = reinterpret_cast<QueryState*>(base + o_qs);
+    uint32_t* tickets = reinterpret_cast<uint32_t*>(base + o_tickets);
+    uint64_t* tau = reinterpret_cast<uint64_t*>(base + o_tau);
+    float* tauf = reinterpret_cast<float*>(base + o_tauf);
+    unsigned long long* dep = reinterpret_cast<unsigned long long*>(base + o_dep);
+    uint32_t* heur = reinterpret_cast<uint32_t*>(base + o_heur);
+    uint32_t* routes = reinterpret_cast<uint32_t*>(base + o_routes);
+    uint32_t* ant_steps = reinterpret_cast<uint32_t*>(base + o_steps);
+    uint32_t* ant_wait = reinterpret_cast<uint32_t*>(base + o_wait);
+    uint32_t* best_route = reinterpret_cast<uint32_t*>(base + o_best);
+    uint32_t* tabu = kc.tabu_in_smem ? nullptr : reinterpret_cast<uint32_t*>(base + o_tabu);
+    DevQuery hq{};
+    hq.src = src;
+    hq.dst = dst;
+    hq.n_ants = n_ants;
+    hq.n_iter = n_iter;
+    hq.alpha = (uint32_t)alpha;
+    hq.beta = (uint32_t)beta;
+    hq.ant_base = 0;
+    hq.active = src != dst;
+    hq.rho_fix = (uint64_t)nearbyint(ldexp((double)rho, 32));
+    hq.seed = seed;
+    hq.xd = c->hx[dst];
+    hq.yd = c->hy[dst];
+    hq.log_base = 0;
+    cudaStream_t s = c->stream;
+    k_static_query<<<1, 1, 0, s>>>(hq, dq, prefix);
+    GMP_CUDA(c, cudaGetLastError());
+    // init clears the pheromone, deposits, colony state and ticket counters left by the previous call
+    GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, tauf, dep, heur,
+                                  qs, tickets, n_iter));
+    ConstructArgs a{};
+    a.rec = c->rec;
+    a.row_ptr = c->row_ptr;
+    a.col = c->col;
+    a.queries = dq;
+    a.ant_prefix = prefix;
+    a.tau = tau;
+    a.tauf = tauf;
+    a.hq = heur;
+    a.dep = dep;
+    a.qs = qs;
+    a.routes = routes;
+    a.ant_steps = ant_steps;
+    a.ant_wait = ant_wait;
+    a.ant_log = nullptr;
+    a.tickets = tickets;
+    a.tabu_global = tabu;
+    a.n_queries = 1;
+    a.total_ants = n_ants;
+    a.n_edges = c->E;
+    a.max_steps = S;
+    a.tabu_words = (uint32_t)words;
+    a.t_dep = c->prm.t_dep_ms;
+    a.thr_on = c->prm.thr_permille != kThrOff;
+    a.tabu_in_smem = kc.tabu_in_smem ? 1u : 0u;
+    a.kappa = c->kappa;
+    for (uint32_t it = 0; it < n_iter; ++it) {
+        GMP_CUDA(c, launch_construct(s, kc, a, it));
+        GMP_CUDA(c, launch_evaporate(s, 1, c->E, dq, tau, tauf, dep, it));
+        GMP_CUDA(c, launch_best_copy(s, 1, dq, qs, routes, ant_steps, ant_wait, best_route, S, it));
+        GMP_CUDA(c, launch_queue_preempt(s, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
+                                         c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
+    }
+    GMP_CUDA(c, launch_finalize(s, 1, dq, qs, best_route, c->col, S, reinterpret_cast<DevResult*>(d_result), d_route));
+    return GMP_OK;
+}

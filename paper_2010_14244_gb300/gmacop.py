@@ -69,6 +69,7 @@ SIGNATURES = {
     "gmp_get_edge_times": (_i32, [_vp, _vp, _vp]),
     "gmp_get_kernel_times": (_i32, [_vp, _vp]),
     "gmp_get_launch_count": (_i32, [_vp, C.POINTER(_u64)]),
+    "gmp_solve_static": (_i32, [_vp, _u32, _u32, _u32, _u32, _f32, _f32, _f32, _u64, _vp, _vp, _u32]),
 }
 
 
@@ -230,6 +231,12 @@ class Context:
         if rc not in (OK, ERR_NO_ROUTE, ERR_BUFFER):
             raise GmpError(rc, lib().gmp_last_error(self._h).decode())
         return self._result(r, buf)
+
+    def solve_static(self, src, dst, n_ants, n_iter, alpha, beta, rho, seed, d_result: int, d_route: int,
+                     route_cap: int):
+        """gmp_solve_static: device pointers for the result row and the route; asynchronous."""
+        self._check(lib().gmp_solve_static(self._h, src, dst, n_ants, n_iter, alpha, beta, rho, seed,
+                                           C.c_void_p(d_result), C.c_void_p(d_route), route_cap))
 
     # ---------------------------------------------------------------- inspection
     def pheromone(self, slot=0) -> np.ndarray:
