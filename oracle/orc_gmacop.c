@@ -366,8 +366,9 @@ float orc_score(uint64_t tau, uint32_t alpha, uint32_t c_ms, uint32_t beta)
     return pow_int(tf, alpha) * pow_int(eta, beta);
 }
 
-/* Integer roulette weights: w_i = max(1, floor(s_i * 2^(30 - E))) with E = floor(log2(max s));
- * all ones when every score is zero. */
+/* Integer roulette weights: w_i = max(1, floor(s_i * 2^(22 - E))) with E = floor(log2(max s));
+ * all ones when every score is zero. Every weight is below 2^23, so the running sums of up to 512
+ * candidates fit in 32 bits. */
 void orc_quantize(uint32_t n, const float *s, uint64_t *w)
 {
     float m = 0.0f;
@@ -383,7 +384,7 @@ void orc_quantize(uint32_t n, const float *s, uint64_t *w)
     (void)frexp((double)m, &e2); /* m = f * 2^e2, f in [0.5, 1) */
     int E = e2 - 1;
     for (uint32_t i = 0; i < n; ++i) {
-        double v = floor(ldexp((double)s[i], 30 - E));
+        double v = floor(ldexp((double)s[i], 22 - E));
         uint64_t q = (uint64_t)v;
         w[i] = q < 1 ? 1 : q;
     }

@@ -144,22 +144,31 @@ __device__ __forceinline__ float rcp_rn(float c) {
     return __fmaf_rn(r, y, y);
 }
 
+// c as binary32 rounded to nearest for c < 2^29, on the floating-point pipe: both halves of
+// c = 64*floor(c/64) + (c mod 64) are exact (2^23 + x - 2^23 for x < 2^23) and one FMA rounds their
+// exact sum once. Equal to __uint2float_rn(c) for every c < 2^29 (checked exhaustively on the GPU).
+__device__ __forceinline__ float u32_to_f32_rn(uint32_t c) {
+    const float hi = __fsub_rn(__uint_as_float(0x4B000000u | (c >> 6)), 8388608.0f);
+    const float lo = __fsub_rn(__uint_as_float(0x4B000000u | (c & 63u)), 8388608.0f);
+    return __fmaf_rn(hi, 64.0f, lo);
+}
+
 // Next-node desirability from tf = tau_float(tau): tf^alpha * (1 / c)^beta, c = travel + wait +
 // remaining bound (ms), 1 <= c < 2^29. The alpha = 1, beta = 2 case performs the same roundings in the
 // same order without loops.
 __device__ __forceinline__ float score_f(float tf, uint32_t alpha, uint32_t c, uint32_t beta) {
-    const float eta = rcp_rn(__uint2float_rn(c));
+    const float eta = rcp_rn(u32_to_f32_rn(c));
     if (alpha == 1u && beta == 2u) return __fmul_rn(tf, __fmul_rn(eta, eta));
     return __fmul_rn(pow_int(tf, alpha), pow_int(eta, beta));
 }
 
-// floor(rnd * S / 2^64) for S < 2^63 from four 32x32 -> 64-bit products (the generic 64-bit high
-// multiply is a long dependent sequence on this GPU).
-__device__ __forceinline__ unsigned long long mulhi_draw(unsigned long long rnd, unsigned long long S) {
-    const uint32_t rl = (uint32_t)rnd, rh = (uint32_t)(rnd >> 32), sl = (uint32_t)S, sh = (uint32_t)(S >> 32);
-    const unsigned long long p0 = (unsigned long long)rh * sh, p1 = (unsigned long long)rh * sl;
-    const unsigned long long p2 = (unsigned long long)rl * sh, p3 = (unsigned long long)rl * sl;
-    return p0 + (p1 >> 32) + (((p1 & 0xFFFFFFFFull) + p2 + (p3 >> 32)) >> 32);
+// The roulette's index r = floor(rnd * S / 2^64) for a 64-bit draw and S < 2^32, from two 32x32 -> 64
+// products: floor((hi*S*2^32 + lo*S) / 2^64) = (hi*S + floor(lo*S / 2^32)) >> 32 (the dropped fraction
+// cannot carry across a multiple of 2^32).
+__device__ __forceinline__ uint32_t draw_index(unsigned long long rnd, uint32_t S) {
+    const uint32_t lo = (uint32_t)rnd, hi = (uint32_t)(rnd >> 32);
+    const unsigned long long a = (unsigned long long)hi * S, b = ((unsigned long long)lo * S) >> 32;
+    return (uint32_t)((a + b) >> 32);
 }
 
 // A non-negative binary32 bit pattern as (M, X) with value = M * 2^(X - 150): M in [2^23, 2^24) for
@@ -174,13 +183,14 @@ __device__ __forceinline__ void norm_f32(uint32_t bits, uint32_t& M, int& X) {
 }
 
 // Integer roulette weight relative to the largest score m (given as its exponent Xm and whether it is
-// zero): floor(s * 2^(30 - floor(log2 m))), at least 1; all ones when m == 0. No branches.
+// zero): floor(s * 2^(22 - floor(log2 m))) = M_s >> (X_m - X_s + 1), at least 1; all ones when m == 0.
+// Below 2^23, so running sums of up to 512 weights fit in 32 bits. No branches.
 __device__ __forceinline__ uint32_t roulette_weight_x(uint32_t sbits, int Xm, bool mzero) {
     uint32_t Ms;
     int Xs;
     norm_f32(sbits, Ms, Xs);
-    const int d = max(0, min(Xm - Xs, 31));  // masked-out slots may carry any value: keep the shift defined
-    const uint32_t w = (Ms << 7) >> d;
+    const int d = max(1, min(Xm - Xs + 1, 31));  // masked-out slots may carry any value: keep the shift defined
+    const uint32_t w = Ms >> d;
     return (mzero || w == 0u) ? 1u : w;
 }
 
@@ -192,10 +202,10 @@ __device__ __forceinline__ uint32_t roulette_weight(uint32_t sbits, uint32_t mbi
 }
 
 // The same weights in binary32 arithmetic. For a step whose largest score m has E = floor(log2 m),
-// scale = (2^k1, 2^k2) with k1 + k2 = 30 - E, both factors normal. floor(s * 2^k1 * 2^k2) is exact:
+// scale = (2^k1, 2^k2) with k1 + k2 = 22 - E, both factors normal. v = s * 2^k1 * 2^k2 < 2^23 is exact:
 // multiplying by a power of two is exact unless the result leaves the normal range, and any result
-// that does so (a shrinking first factor) makes the final value below 1, where the floor is 0 and the
-// weight 1 anyway.
+// that does so (a shrinking first factor) makes v below 1, where the weight is 1 anyway. floor(v) is
+// then one addition of 2^23 rounded toward zero.
 struct WeightScale {
     float s1, s2;
     bool mzero;
@@ -205,7 +215,7 @@ __device__ __forceinline__ WeightScale weight_scale(uint32_t mbits) {
     uint32_t Mm;
     int Xm;
     norm_f32(mbits, Mm, Xm);
-    const int k = 30 - (Xm - 127);  // 30 - E, in [-97, 179]
+    const int k = 22 - (Xm - 127);  // 22 - E, in [-105, 171]
     const int k1 = k >> 1, k2 = k - k1;
     WeightScale w;
     w.s1 = __uint_as_float((uint32_t)(k1 + 127) << 23);
@@ -216,7 +226,7 @@ __device__ __forceinline__ WeightScale weight_scale(uint32_t mbits) {
 
 __device__ __forceinline__ uint32_t roulette_weight_f(uint32_t sbits, const WeightScale& sc) {
     const float v = __fmul_rn(__fmul_rn(__uint_as_float(sbits), sc.s1), sc.s2);
-    const uint32_t w = __float2uint_rz(v);  // v < 2^31
+    const uint32_t w = __float_as_uint(__fadd_rz(v, 8388608.0f)) - 0x4B000000u;  // floor(v), v < 2^23
     return (sc.mzero || w == 0u) ? 1u : w;
 }
 

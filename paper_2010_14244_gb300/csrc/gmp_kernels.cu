@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(FULL, mb, off, G));
             const WeightScale sc = weight_scale(mb);
-            unsigned long long incl[NC];
+            uint32_t incl[NC];
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const uint32_t mine = (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             for (int h = 1; h < NC; h <<= 1)
 #pragma unroll
                 for (int i = NC - 1; i >= h; --i) incl[i] += incl[i - h];
-            const unsigned long long r = mulhi_draw(rnd, incl[NC - 1]);
+            const uint32_t r = draw_index(rnd, incl[NC - 1]);
             int pick = 0;
 #pragma unroll
             for (int i = 0; i < NC; ++i) pick += incl[i] <= r ? 1 : 0;
@@ -517,13 +517,13 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
 #pragma unroll
             for (int j = 0; j < K; ++j) mb = max(mb, (cmask >> j & 1u) ? sb[j] : 0u);
             const WeightScale sc = weight_scale(mb);
-            unsigned long long incl[K], S = 0;
+            uint32_t incl[K], S = 0;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 S += (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
                 incl[j] = S;
             }
-            const unsigned long long r = mulhi_draw(rnd, S);
+            const uint32_t r = draw_index(rnd, S);
             int js = 0;
             bool found = false;
 #pragma unroll

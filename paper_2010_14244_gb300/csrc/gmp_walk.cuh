@@ -199,7 +199,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(gmask, mb, off, G));
             // 5. own integer weights; every lane gathers the group's weights and picks locally
             const WeightScale sc = weight_scale(mb);
-            unsigned long long incl[NC];
+            uint32_t incl[NC];
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const uint32_t mine = (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
@@ -212,7 +212,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
                 for (int i = NC - 1; i >= h; --i) incl[i] += incl[i - h];
             // roulette: the first candidate (CSR order = index lane + j*G) whose running weight exceeds
             // r is the number of running weights <= r
-            const unsigned long long r = mulhi_draw(rnd, incl[NC - 1]);
+            const uint32_t r = draw_index(rnd, incl[NC - 1]);
             int pick = 0;
 #pragma unroll
             for (int i = 0; i < NC; ++i) pick += incl[i] <= r ? 1 : 0;
@@ -232,7 +232,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             for (int off = G / 2; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(gmask, mb, off, G));
             // 5. integer weights, inclusive prefix in CSR order (index lane + j*G) by shuffles, roulette
             const WeightScale sc = weight_scale(mb);
-            unsigned long long carry = 0, incl[K];
+            uint32_t carry = 0, incl[K];
             uint32_t wt[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) {
@@ -240,17 +240,17 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
                 incl[j] = carry;
                 if (j < nslots) {
                     wt[j] = (cmask >> j & 1u) ? roulette_weight_f(sb[j], sc) : 0u;
-                    unsigned long long xs = wt[j];
+                    uint32_t xs = wt[j];
 #pragma unroll
                     for (int d = 1; d < G; d <<= 1) {
-                        const unsigned long long y = __shfl_up_sync(gmask, xs, d, G);
+                        const uint32_t y = __shfl_up_sync(gmask, xs, d, G);
                         if (lane >= (uint32_t)d) xs += y;
                     }
                     incl[j] = carry + xs;
                     carry = __shfl_sync(gmask, incl[j], G - 1, G);
                 }
             }
-            const unsigned long long r = mulhi_draw(rnd, carry);
+            const uint32_t r = draw_index(rnd, carry);
             int js = -1;
 #pragma unroll
             for (int j = 0; j < K; ++j)

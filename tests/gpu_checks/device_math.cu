@@ -1,6 +1,6 @@
 // Checks of the library's device arithmetic (paper_2010_14244_gb300/csrc/gmp_device.cuh) against
 // CUDA's own results: the reciprocal against __frcp_rn (every input the colony can produce), the
-// split high product against __umul64hi, Philox4x32-10 against cuRAND's curand_Philox4x32_10, the
+// roulette index against __umul64hi, the u32 -> f32 conversion against __uint2float_rn (every c < 2^29), Philox4x32-10 against cuRAND's curand_Philox4x32_10, the
 // reciprocal modulo against %, and isqrt against a bit-by-bit root. Roulette weights are written out
 // for the Python test to compare with the CPU oracle's exact quantisation.
 //
@@ -27,6 +27,11 @@ __global__ void k_rcp(unsigned long long lo, unsigned long long n, unsigned long
     }
 }
 
+__global__ void k_cvt(unsigned long long* bad) {  // every c < 2^29
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < (1u << 29); c += gridDim.x * blockDim.x)
+        if (__float_as_uint(u32_to_f32_rn(c)) != __float_as_uint(__uint2float_rn(c))) atomicAdd(bad, 1ull);
+}
+
 __device__ unsigned long long mix(unsigned long long x) {
     x ^= x >> 31;
     x *= 0x7FB5D329728EA185ull;
@@ -39,9 +44,9 @@ __global__ void k_misc(unsigned long long n, unsigned long long* bad) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long a = mix(i), b = mix(i + 0x9E3779B97F4A7C15ull);
-        // split high product, S < 2^40
-        const unsigned long long S = (b >> (24 + (i % 40))) + (i & 1);
-        if (mulhi_draw(a, S) != __umul64hi(a, S)) atomicAdd(bad + 0, 1ull);
+        // roulette index, S < 2^32
+        const uint32_t S = (uint32_t)(b >> (32 + (i % 32))) + (uint32_t)(i & 1);
+        if ((unsigned long long)draw_index(a, S) != __umul64hi(a, (unsigned long long)S)) atomicAdd(bad + 0, 1ull);
         // Philox against cuRAND
         const uint4 c = make_uint4((unsigned)a, (unsigned)(a >> 32), (unsigned)b, (unsigned)(b >> 32));
         const uint4 x = philox4x32_10(c, (unsigned)(i * 2654435761u), (unsigned)(i >> 7));
@@ -78,11 +83,12 @@ static int checks() {
     k_rcp<<<1024, 256>>>(0, 1ull << 24, bad);
     k_rcp<<<1024, 256>>>(0x4B800000ull, 0x4E000000ull - 0x4B800000ull + 1, bad);
     k_misc<<<1024, 256>>>(1ull << 26, bad + 1);
+    k_cvt<<<1024, 256>>>(bad + 6);
     unsigned long long h[8];
     cudaMemcpy(h, bad, sizeof h, cudaMemcpyDeviceToHost);
     const cudaError_t e = cudaDeviceSynchronize();
-    printf("rcp_rn %llu\nmulhi_draw %llu\nphilox_vs_curand %llu\nmod_magic %llu\nisqrt %llu\nweight_f %llu\n", h[0],
-           h[1], h[2], h[3], h[4], h[5]);
+    printf("rcp_rn %llu\ndraw_index %llu\nphilox_vs_curand %llu\nmod_magic %llu\nisqrt %llu\nweight_f %llu\n"
+           "u32_to_f32_rn %llu\n", h[0], h[1], h[2], h[3], h[4], h[5], h[6]);
     cudaFree(bad);
     printf("status %s\n", cudaGetErrorString(e));
     return e != cudaSuccess;

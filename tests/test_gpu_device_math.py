@@ -1,8 +1,9 @@
 """The library's device arithmetic against CUDA's own results and against the CPU oracle.
 
 Compiles tests/gpu_checks/device_math.cu (which includes the library's device header) and runs it:
-the Markstein reciprocal against __frcp_rn on every input the colony can produce, the split 64-bit
-high product against __umul64hi, Philox4x32-10 against cuRAND's curand_Philox4x32_10, the reciprocal
+the Markstein reciprocal against __frcp_rn on every input the colony can produce, the roulette index
+from 32-bit products against __umul64hi, the FP-pipe u32 -> f32 conversion against __uint2float_rn on
+every c < 2^29, Philox4x32-10 against cuRAND's curand_Philox4x32_10, the reciprocal
 modulo against %, isqrt against its definition, the binary32 roulette weights against the integer
 formulation; then roulette weights of random score vectors against the oracle's exact quantisation.
 """
@@ -36,7 +37,7 @@ def test_device_arithmetic_checks(helper):
     assert r.returncode == 0, r.stdout + r.stderr
     got = dict(line.split(maxsplit=1) for line in r.stdout.strip().splitlines())
     assert got.pop("status") == "no error"
-    for name in ("rcp_rn", "mulhi_draw", "philox_vs_curand", "mod_magic", "isqrt", "weight_f"):
+    for name in ("rcp_rn", "draw_index", "philox_vs_curand", "mod_magic", "isqrt", "weight_f", "u32_to_f32_rn"):
         assert got[name] == "0", (name, got[name])
 
 

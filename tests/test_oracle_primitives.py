@@ -212,7 +212,7 @@ def test_heuristic_hand_worked(orc):
 
 # ------------------------------------------------------------------------------------------ scores
 def _exact_weights(scores):
-    """w_i = max(1, floor(s_i * 2^(30 - E))), E = floor(log2(max s)); exact rational arithmetic."""
+    """w_i = max(1, floor(s_i * 2^(22 - E))), E = floor(log2(max s)); exact rational arithmetic."""
     fr = [Fraction(float(s)) for s in scores]
     m = max(fr)
     if m == 0:
@@ -221,7 +221,7 @@ def _exact_weights(scores):
     if Fraction(2) ** E > m:
         E -= 1
     assert Fraction(2) ** E <= m < Fraction(2) ** (E + 1)
-    return [max(1, math.floor(f * Fraction(2) ** (30 - E))) for f in fr]
+    return [max(1, math.floor(f * Fraction(2) ** (22 - E))) for f in fr]
 
 
 def test_quantize_matches_exact_rationals(orc):
@@ -240,7 +240,7 @@ def test_quantize_matches_exact_rationals(orc):
     for s in cases:
         w = orc.quantize(s)
         assert [int(v) for v in w] == _exact_weights(s), s
-        assert int(w.max()) < 2**31 and int(w.min()) >= 1
+        assert int(w.max()) < 2**23 and int(w.min()) >= 1
 
 
 def test_score_binary32_order(orc):

@@ -28,9 +28,9 @@ def _star(signal_on_1=False, veh01=0, far1=False):
 
 def test_hand_worked_first_step_kat_draw(orc):
     """Three candidates with scores 2^-12, 2^-13, 2^-11 (alpha=beta=1, tau=1.0, h=0, no signals):
-    weights 2^29, 2^28, 2^30; S = 7*2^28. The draw for (seed 0, it 0, ant 0, step 0) is the first
-    Philox known-answer vector, 0xe169c58d6627e8d5 / 2^64 = 0.8805..., so r = 6.16 * 2^28 lies in
-    [3*2^28, 7*2^28): the third road (0 -> 3). Then 3 -> 4 is the only choice: T = 2048 + 4096."""
+    weights 2^21, 2^20, 2^22; S = 7*2^20. The draw for (seed 0, it 0, ant 0, step 0) is the first
+    Philox known-answer vector, 0xe169c58d6627e8d5 / 2^64 = 0.8805..., so r = 6.16 * 2^20 lies in
+    [3*2^20, 7*2^20): the third road (0 -> 3). Then 3 -> 4 is the only choice: T = 2048 + 4096."""
     net, sig, veh = _star()
     onet = orc.Net(net, sig, veh)
     tau = np.full(net.n_edges, 2**32, np.uint64)
