@@ -83,6 +83,7 @@ def lib():
             "orc_prepare": (C.c_int, [vp, vp, u32, vp, vp, vp, vp, vp, vp]),
             "orc_walk_one": (C.c_int, [vp, vp, vp, vp, u32, u32, vp, vp, vp, vp]),
             "orc_solve": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp]),
+            "orc_tick": (C.c_int, [vp, vp, u64, u32, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -237,6 +238,19 @@ def queue_preempt(net: Net, params: Params | None = None) -> np.ndarray:
     if rc != OK:
         raise RuntimeError(f"orc_queue_preempt failed: {rc}")
     return order
+
+
+def tick(net: Net, params: Params, t_now: int, dt: int, order):
+    """One serving tick: returns (vehicles, red_ms N x 8, new order N x 8)."""
+    o = np.ascontiguousarray(order, np.uint8).reshape(-1)
+    veh = np.zeros(net.n_edges, np.uint32)
+    red = np.zeros((net.n_nodes, 8), np.uint32)
+    new_order = np.zeros((net.n_nodes, 8), np.uint8)
+    pr = params.c()
+    rc = lib().orc_tick(C.addressof(net.c), C.addressof(pr), t_now, dt, _p(o), _p(veh), _p(red), _p(new_order))
+    if rc != OK:
+        raise RuntimeError(f"orc_tick failed: {rc}")
+    return veh, red, new_order
 
 
 def walk_one(net: Net, params: Params, query, tau, it=0, ant=0):

@@ -766,3 +766,92 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
     free(best_route);
     return res->status;
 }
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Serving tick: the queue / preemption update with dt > 0 (Fig. 3 signal block; Calc_Dens and        */
+/* Comp_Thres of Sec. 4.2 applied to vehicles that move). One step of length dt at clock t_now:        */
+/*   green phase of each signalised node from its current phase order (every approach is served at an  */
+/*   unsignalised node); each served road discharges min(n, c) vehicles, c = lanes*(t_now+dt)/h_sat -   */
+/*   lanes*t_now/h_sat (saturation flow counted on the whole clock, so no fraction is lost); a node's    */
+/*   discharge K is split over its d out-roads, K/d each and one more for the first K mod d in CSR      */
+/*   order (vehicles leave the network at nodes without out-roads); red-time accumulators: 0 for the    */
+/*   green phase, + dt (saturating at 2^32-1) for other phases with a queue, 0 for empty phases (queues */
+/*   counted before the discharge); then the phase order is recomputed from the new state. Vehicle      */
+/*   counts are 32-bit and wrap like unsigned arithmetic.                                                */
+/* ------------------------------------------------------------------------------------------------ */
+static uint32_t green_phase_at(uint64_t t, uint32_t cycle, uint32_t offset, const uint32_t *green,
+                               const uint8_t *order, uint32_t P)
+{
+    uint64_t c = (t % cycle + cycle - (offset % cycle)) % cycle;
+    uint64_t start = 0;
+    for (uint32_t i = 0; i < P; ++i) {
+        uint32_t p = order[i];
+        if (c >= start && c < start + green[p])
+            return p;
+        start += green[p];
+    }
+    return order[P - 1]; /* unreachable: greens cover the cycle */
+}
+
+int orc_tick(const orc_net *g, const orc_params *prm, uint64_t t_now, uint32_t dt, const uint8_t *order,
+             uint32_t *veh_out, uint32_t *red_out, uint8_t *order_out)
+{
+    uint32_t N = g->n_nodes, E = g->n_edges, hsat = hsat_of(prm);
+    uint32_t *leave = calloc((size_t)E + 1, sizeof(uint32_t));
+    uint64_t *K = calloc((size_t)N + 1, sizeof(uint64_t));
+    uint64_t *Q = calloc((size_t)N * ORC_MAX_PHASES + 1, sizeof(uint64_t));
+    uint32_t *gph = malloc(sizeof(uint32_t) * ((size_t)N + 1));
+    if (!leave || !K || !Q || !gph) {
+        free(leave);
+        free(K);
+        free(Q);
+        free(gph);
+        return ORC_ERR_OOM;
+    }
+    for (uint32_t v = 0; v < N; ++v)
+        gph[v] = g->n_phases[v] ? green_phase_at(t_now, g->cycle_ms[v], g->offset_ms[v],
+                                                 g->green_ms + (size_t)v * ORC_MAX_PHASES,
+                                                 order + (size_t)v * ORC_MAX_PHASES, g->n_phases[v])
+                                : 0xFFFFFFFFu;
+    /* queues before the discharge, and the discharge of every served road */
+    for (uint32_t u = 0; u < N; ++u)
+        for (uint32_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; ++e) {
+            uint32_t v = g->col[e], n = g->vehicles[e];
+            if (g->n_phases[v])
+                Q[(size_t)v * ORC_MAX_PHASES + g->edge_phase[e]] += n;
+            if (g->n_phases[v] == 0 || g->edge_phase[e] == gph[v]) {
+                /* saturation flow lanes/h_sat, counted on the whole clock so no fraction is lost */
+                uint64_t cap = (uint64_t)g->lanes[e] * (t_now + dt) / hsat - (uint64_t)g->lanes[e] * t_now / hsat;
+                leave[e] = (uint32_t)(n < cap ? n : cap);
+                K[v] += leave[e];
+            }
+        }
+    /* the discharge of each node goes to its out-roads */
+    for (uint32_t u = 0; u < N; ++u) {
+        uint32_t b = g->row_ptr[u], d = g->row_ptr[u + 1] - b;
+        for (uint32_t j = 0; j < d; ++j) {
+            uint32_t e = b + j;
+            uint64_t in = K[u] / d + (j < K[u] % d ? 1u : 0u);
+            veh_out[e] = (uint32_t)(g->vehicles[e] - leave[e] + in);
+        }
+    }
+    for (uint32_t v = 0; v < N; ++v)
+        for (uint32_t p = 0; p < ORC_MAX_PHASES; ++p) {
+            size_t i = (size_t)v * ORC_MAX_PHASES + p;
+            uint32_t r = g->red_ms ? g->red_ms[i] : 0u;
+            if (g->n_phases[v] == 0 || p >= g->n_phases[v] || p == gph[v] || Q[i] == 0)
+                red_out[i] = 0;
+            else
+                red_out[i] = r > 0xFFFFFFFFu - dt ? 0xFFFFFFFFu : r + dt;
+        }
+    /* the new phase order from the new vehicles and red times */
+    orc_net g2 = *g;
+    g2.vehicles = veh_out;
+    g2.red_ms = red_out;
+    int rc = orc_queue_preempt(&g2, prm, order_out);
+    free(leave);
+    free(K);
+    free(Q);
+    free(gph);
+    return rc;
+}
