@@ -60,7 +60,8 @@ typedef struct {
     uint32_t t_dep_ms;      /* departure clock for signal phases, < 2^30 */
     uint32_t lanes_per_ant; /* lanes of a warp that evaluate one ant's candidates: 0 (autotune), 4, 8, 16, 32 */
     uint32_t mode;          /* GMP_MODE_* */
-    uint32_t reserved;
+    uint32_t queue_chunk;   /* persistent mode: intersections per queue-update work item; 0 (= 16), 8, 16,
+                               32 or 64 */
 } gmp_params;
 
 /* One origin-destination colony. alpha, beta: integers in [0, 8]; rho in [0, 1). */
@@ -130,6 +131,129 @@ int gmp_set_densities(gmp_ctx *ctx, const uint32_t *vehicles);
 /* Same from device memory (E entries), asynchronous on the context's stream. */
 int gmp_set_densities_async(gmp_ctx *ctx, const uint32_t *d_vehicles);
 
+/* Read back the vehicles on each road (host array of E entries) and the red-time accumulators (host
+ * array of N*8 entries, ms), as the last density update or tick left them. Synchronous.
+ * Errors: INVALID_ARG, STATE, CUDA. */
+int gmp_get_densities(gmp_ctx *ctx, uint32_t *vehicles);
+int gmp_get_red_times(gmp_ctx *ctx, uint32_t *red_ms);
+
+/* Serving tick: advances the traffic state held by the context by dt_ms at clock t_now_ms (the queue and
+ * preemption update of the Fig. 3 signal block, Calc_Dens / Comp_Thres of Sec. 4.2, with vehicles
+ * that move). In order:
+ *   - the phase green at t_now_ms under each node's current phase order (windows laid out from the
+ *     node's offset); every approach of an unsignalised node is served;
+ *   - each served road discharges min(n, c) vehicles, c = lanes*(t_now+dt)/h_sat - lanes*t_now/h_sat
+ *     in integer division (the saturation flow counted on the whole clock);
+ *   - a node's discharge K goes to its d out-roads, K/d each and one more to each of the first K mod d
+ *     in CSR order; vehicles reaching a node without out-roads leave the network; counts are 32-bit
+ *     and wrap as unsigned arithmetic;
+ *   - red-time accumulators: 0 for the green phase and for phases whose approaches are empty before the
+ *     discharge, + dt_ms (saturating at 2^32-1) for the others;
+ *   - road travel times, queue delays and the phase order are recomputed from the new state.
+ * Asynchronous on the context's stream: it is ordered after any job already launched there and before
+ * any launched later. Requires t_now_ms <= 2^48 and dt_ms <= 2^30. Its scratch (E*4 + N*8 bytes) is
+ * allocated with the graph. Errors: INVALID_ARG, STATE, CUDA. */
+int gmp_tick(gmp_ctx *ctx, uint64_t t_now_ms, uint32_t dt_ms);
+
+/* Schedule chosen by gmp_autotune. */
+typedef struct {
+    uint32_t lanes_per_ant; /* lanes of a warp per ant (ants per warp = 32 / lanes; 1 = one thread per ant) */
+    uint32_t mode;          /* GMP_MODE_ITERATIVE or GMP_MODE_PERSISTENT */
+    uint32_t queue_chunk;   /* persistent mode: intersections per queue-update work item; 0 otherwise */
+    uint32_t lockstep;      /* 1 when the ants of a warp step together (iterative mode) */
+    uint32_t from_cache;    /* 1 when this size bucket was tuned earlier in the process: nothing was timed */
+    uint32_t n_tried;       /* schedules timed */
+    float best_ms;          /* probe job time of the chosen schedule (0 from the cache) */
+    float default_ms;       /* probe job time of the untuned schedule (0 from the cache) */
+    uint32_t bucket[4];     /* size bucket: SM count, ceil(log2 N), max out-degree, ceil(log2 probe ants) */
+} gmp_tune_result;
+
+/* Autotuner for the batched job (no counterpart in the paper, whose kernels have one fixed shape). All
+ * schedules give the same results bit for bit, so only speed differs. The first call for a size bucket
+ * times a probe job (the n probe queries with n_iter clamped to probe_iter, 0 = 8) under every schedule
+ * the graph admits: lanes per ant 1/4/8/16/32, warp lockstep or free-running groups, the iterative or
+ * the persistent job with queue chunks 8/16/32/64. Each is run once to warm up, then twice timed on
+ * the context's stream; the fastest wins. The choice is cached for the process by bucket and written
+ * into the context's parameters (lanes_per_ant, mode, queue_chunk, the lockstep flag); later calls in
+ * the same bucket apply the cached choice without timing. Replaces any staged batch. Synchronous.
+ * Errors: INVALID_ARG, STATE, UNSUPPORTED (no schedule ran), and those of gmp_batch_stage. */
+int gmp_autotune(gmp_ctx *ctx, uint32_t n, const gmp_query *probe, uint32_t probe_iter, gmp_tune_result *out);
+
+/* Forget every cached autotuner choice of the process. */
+void gmp_autotune_reset(void);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Route server: continuous batching over several contexts (no counterpart in the paper, which routes */
+/* one vehicle at a time in Fig. 3).                                                                  */
+/* ---------------------------------------------------------------------------------------------- */
+typedef struct gmp_server gmp_server;
+
+typedef struct {
+    uint32_t max_batch; /* requests per job at most (a slot's memory budget may admit fewer) */
+    uint32_t max_ants;  /* largest n_ants a request may ask for */
+    uint32_t max_iter;  /* largest n_iter a request may ask for */
+    uint32_t reserved;
+} gmp_server_config;
+
+/* One finished request. Times are host steady-clock nanoseconds. */
+typedef struct {
+    uint64_t tag;         /* the caller's id from gmp_server_submit */
+    uint64_t t_submit_ns; /* submitted */
+    uint64_t t_launch_ns; /* its job was launched */
+    uint64_t t_done_ns;   /* the server saw its job finished (at a gmp_server_pump) */
+    uint64_t clock_ms;    /* traffic clock of the state it was solved on: t_now + dt of the last tick
+                             issued before its job (0 before any tick) */
+    uint32_t slot;        /* the slot that ran it */
+    uint32_t batch_size;  /* requests in that job */
+    gmp_result result;    /* route points into the buffer given to gmp_server_take; status as for
+                             gmp_batch_collect, or the error that failed the whole job */
+} gmp_served;
+
+typedef struct {
+    uint32_t queued;       /* waiting for a slot */
+    uint32_t in_flight;    /* in jobs on the GPU */
+    uint32_t busy_slots;   /* slots with a job on the GPU */
+    uint32_t done_waiting; /* finished, not yet taken */
+    uint64_t jobs;         /* jobs launched so far */
+    uint64_t completed;    /* requests finished so far */
+    uint64_t rejected;     /* requests refused at submission */
+} gmp_server_stats;
+
+/* Create a server over n_slots contexts. Each context must already hold the same road graph, signals,
+ * densities, red times and parameters (one replica per slot; the server does not copy them); the
+ * server uses them exclusively until it is destroyed, and does not destroy them. For every slot the
+ * server reserves (gmp_batch_reserve) the workspace of a job of `cap` requests with max_ants ants and
+ * max_iter iterations each, where cap starts at max_batch and shrinks until the context's memory budget
+ * admits it: that is the slot's admission limit. Errors: INVALID_ARG, STATE, OOM (not even one request
+ * fits), and those of gmp_batch_reserve. */
+int gmp_server_create(gmp_server **out, gmp_ctx *const *slots, uint32_t n_slots, const gmp_server_config *cfg);
+void gmp_server_destroy(gmp_server *srv);
+const char *gmp_server_last_error(const gmp_server *srv);
+
+/* Requests per job admitted on a slot. */
+int gmp_server_slot_capacity(const gmp_server *srv, uint32_t slot, uint32_t *requests_per_job);
+
+/* Queue one request (FIFO). Checked at once: a request that a job would refuse, or one above max_ants
+ * or max_iter, is refused here with that error and counted as rejected. */
+int gmp_server_submit(gmp_server *srv, const gmp_query *query, uint64_t tag);
+
+/* Issue the traffic tick gmp_tick(t_now_ms, dt_ms) on every slot's stream: it runs after the slot's job
+ * on the GPU, if any, and before its next one. The serving clock becomes t_now_ms + dt_ms; every job
+ * launched afterwards departs at that clock (the server sets the slot's t_dep_ms), so the clock must stay
+ * below 2^30 ms. Errors: INVALID_ARG, and those of gmp_tick. */
+int gmp_server_tick(gmp_server *srv, uint64_t t_now_ms, uint32_t dt_ms);
+
+/* One non-blocking round of the loop: collect every job that has finished, then give every idle slot
+ * the requests waiting at the head of the queue (up to its admission limit) as one job and launch it.
+ * Fills *stats when non-NULL. */
+int gmp_server_pump(gmp_server *srv, gmp_server_stats *stats);
+
+/* Move up to max_n finished requests, oldest first, into out[]; their routes are copied back to back into
+ * route_buf (route_entries entries). Stops early when the next route does not fit.
+ * Errors: INVALID_ARG, BUFFER (not even the first route fits). */
+int gmp_server_take(gmp_server *srv, uint32_t max_n, gmp_served *out, uint32_t *route_buf, uint64_t route_entries,
+                    uint32_t *n_out);
+
 /* Colony tunables; recomputes threshold flags. Errors: INVALID_ARG. */
 int gmp_set_params(gmp_ctx *ctx, const gmp_params *params);
 int gmp_get_params(const gmp_ctx *ctx, gmp_params *params);
@@ -153,6 +277,18 @@ int gmp_solve_batch(gmp_ctx *ctx, uint32_t n, const gmp_query *queries, gmp_resu
 int gmp_batch_stage(gmp_ctx *ctx, uint32_t n, const gmp_query *queries);
 int gmp_batch_launch(gmp_ctx *ctx);
 int gmp_batch_collect(gmp_ctx *ctx, gmp_result *results);
+
+/* Reserve the device workspace of the largest job the caller will stage: n colonies, total_ants ants
+ * per iteration (summed over the colonies), up to max_iter iterations, under the current parameters
+ * (lanes, mode, ant log). Buffers only grow, so staging any job within these bounds afterwards allocates
+ * nothing (and so never waits on the allocator while jobs of other contexts run). Drops any staged
+ * batch; on OOM the whole workspace is released. Synchronous.
+ * Errors: INVALID_ARG, STATE, UNSUPPORTED, OOM (the memory budget or the device cannot hold it), CUDA. */
+int gmp_batch_reserve(gmp_ctx *ctx, uint32_t n, uint64_t total_ants, uint32_t max_iter);
+
+/* Non-blocking: *ready = 1 when the last launched job has finished on the device, else 0.
+ * Errors: INVALID_ARG, STATE (nothing launched), CUDA (the job failed). */
+int gmp_batch_ready(gmp_ctx *ctx, int *ready);
 
 /* Pheromone of query `slot` of the last batch after its final iteration: E entries, Q32.32. */
 int gmp_get_pheromone(gmp_ctx *ctx, uint32_t slot, uint64_t *out_tau);

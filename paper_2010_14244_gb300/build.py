@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libgmacop.so")
 
-SOURCES = ["gmp_api.cu", "gmp_kernels.cu", "gmp_persistent.cu"]
+SOURCES = ["gmp_api.cu", "gmp_kernels.cu", "gmp_persistent.cu", "gmp_tune.cu", "gmp_serve.cu"]
 HEADERS = ["gmp_device.cuh", "gmp_internal.h", "gmp_walk.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=false", "-prec-div=true",

@@ -25,13 +25,16 @@ namespace {
 
 constexpr uint32_t kFlagKernelTiming = 4u;  // event records around every kernel of the job
 constexpr uint32_t kFlagNoGraph = 8u;        // issue the job kernel by kernel instead of replaying a graph
-constexpr uint32_t kFlagNoLockstep = 16u;    // sub-warp ants without warp lockstep (for comparison)
+constexpr uint32_t kFlagNoLockstep = kFlagNoLockstepBit;  // sub-warp ants without warp lockstep
 constexpr uint32_t kKnownFlags =
     GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
 constexpr int32_t kCoordLimit = 1 << 27;
+constexpr uint64_t kTickClockMax = 1ull << 48;  // lanes * (t + dt) stays below 2^64
+constexpr uint32_t kTickDtMax = 1u << 30;
 
 struct BatchKey {
-    uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0;
+    uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0,
+             chunk = 0;
     uint64_t log_entries = 0;
     const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
@@ -72,6 +75,7 @@ struct Batch {
     uint64_t launches = 0;
     std::vector<cudaEvent_t> ev;
     bool timed = false;
+    cudaEvent_t done = nullptr;  // recorded after every launch (gmp_batch_ready)
 };
 
 }  // namespace
@@ -94,9 +98,35 @@ struct gmp_ctx {
     uint8_t *nph = nullptr, *ephase = nullptr, *order = nullptr;
     uint32_t *cycle = nullptr, *offset = nullptr, *green = nullptr, *red = nullptr, *veh = nullptr;
     EdgeRec* rec = nullptr;
+    uint32_t* tick_leave = nullptr;        // serving tick: discharge of each road (E)
+    unsigned long long* tick_K = nullptr;  // serving tick: discharge of each node (N)
     std::vector<int32_t> hx, hy;  // host copy of node coordinates (destination lookups at staging)
     Batch b;
 };
+
+namespace gmp {
+
+uint32_t default_lanes(uint32_t maxdeg) {
+    for (uint32_t g : {8u, 16u, 32u})  // one candidate slot per lane when the degree allows
+        if (g >= maxdeg) return g;
+    return 32u;
+}
+
+bool lockstep_fits(int lanes, uint32_t maxdeg) {
+    if (lanes == 1) return true;  // one thread per ant always steps in lockstep
+    return lanes <= 16 && maxdeg <= (uint32_t)(2 * lanes) && lanes * (maxdeg <= (uint32_t)lanes ? 1 : 2) <= 16;
+}
+
+CtxInfo ctx_info(const gmp_ctx* c) {
+    return CtxInfo{c->device, c->stream, c->N, c->E, c->maxdeg, c->has_graph, c->budget, c->used};
+}
+
+int ctx_fail(gmp_ctx* c, int code, const char* msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+}  // namespace gmp
 
 namespace {
 
@@ -190,6 +220,10 @@ void free_batch(gmp_ctx* c) {
     Batch& b = c->b;
     drop_graph(b);
     drop_events(b);
+    if (b.done) {
+        cudaEventDestroy(b.done);
+        b.done = nullptr;
+    }
     dfree(c, &b.dq);
     dfree(c, &b.prefix);
     dfree(c, &b.tau);
@@ -235,6 +269,8 @@ void free_graph(gmp_ctx* c) {
     dfree(c, &c->red);
     dfree(c, &c->veh);
     dfree(c, &c->rec);
+    dfree(c, &c->tick_leave);
+    dfree(c, &c->tick_K);
     c->has_graph = false;
     c->N = c->E = 0;
 }
@@ -263,9 +299,7 @@ uint32_t default_max_steps(const gmp_ctx* c) {
 
 int pick_lanes(const gmp_ctx* c) {
     if (c->prm.lanes_per_ant) return (int)c->prm.lanes_per_ant;
-    for (int g : {8, 16, 32})  // one candidate slot per lane when the degree allows
-        if ((uint32_t)g >= c->maxdeg) return g;
-    return 32;
+    return (int)default_lanes(c->maxdeg);
 }
 
 int check_query(gmp_ctx* c, const gmp_query& q, uint32_t idx) {
@@ -321,6 +355,7 @@ int enqueue_persistent(gmp_ctx* c) {
     p.rec = c->rec;
     p.n_nodes = c->N;
     p.max_iter = b.maxI;
+    p.node_chunk = c->prm.queue_chunk ? c->prm.queue_chunk : 16u;
     p.spin_limit = 1u << 23;  // idle polls of ~0.3 us each (seconds) before the job reports a timeout
     GMP_CUDA(c, launch_persistent(s, b.kc, p));
     if (timed) GMP_TRY(record(c, b, 2));
@@ -397,8 +432,9 @@ int enqueue_job(gmp_ctx* c) {
 
 BatchKey key_of(const gmp_ctx* c) {
     const Batch& b = c->b;
-    BatchKey k;
+    BatchKey k{};
     k.Q = b.Q;
+    k.chunk = c->prm.queue_chunk;
     k.maxI = b.maxI;
     k.total_ants = b.total_ants;
     k.max_steps = b.max_steps;
@@ -537,6 +573,8 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     GMP_TRY(dalloc(c, &c->red, (size_t)N * kMaxPhases));
     GMP_TRY(dalloc(c, &c->veh, E));
     GMP_TRY(dalloc(c, &c->rec, E));
+    GMP_TRY(dalloc(c, &c->tick_leave, E));
+    GMP_TRY(dalloc(c, &c->tick_K, N));
     GMP_TRY(upload(c, c->row_ptr, row_ptr, N + 1));
     GMP_TRY(upload(c, c->col, col, E));
     GMP_TRY(upload(c, c->len, length_dm, E));
@@ -635,6 +673,8 @@ int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
         p->lanes_per_ant != 16 && p->lanes_per_ant != 32)
         return fail(c, GMP_ERR_INVALID_ARG, "lanes_per_ant must be 0, 1, 4, 8, 16 or 32");
     if (p->mode > GMP_MODE_PERSISTENT) return fail(c, GMP_ERR_INVALID_ARG, "unknown mode");
+    if (p->queue_chunk && p->queue_chunk != 8 && p->queue_chunk != 16 && p->queue_chunk != 32 && p->queue_chunk != 64)
+        return fail(c, GMP_ERR_INVALID_ARG, "queue_chunk must be 0, 8, 16, 32 or 64");
     if (p->max_steps > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "max_steps must be <= 2^24");
     const bool dyn = p->thr_permille != c->prm.thr_permille || p->h_sat_ms != c->prm.h_sat_ms;
     c->prm = *p;
@@ -649,6 +689,89 @@ int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
 int gmp_get_params(const gmp_ctx* c, gmp_params* p) {
     if (!c || !p) return GMP_ERR_INVALID_ARG;
     *p = c->prm;
+    return GMP_OK;
+}
+
+namespace {
+
+// Launch shape of the job for the context's parameters and `total_ants` ants per iteration.
+int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc) {
+    *kc = KernelConfig{};
+    const uint32_t ants = (uint32_t)std::min<uint64_t>(total_ants, 0xFFFFFFFFull);
+    if (c->prm.mode == GMP_MODE_PERSISTENT) {
+        if (lanes == 1) return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs 4, 8, 16 or 32 lanes per ant");
+        GMP_CUDA(c, persistent_config(c->device, lanes, c->N, c->maxdeg, kc));
+    } else if (lanes != 1 && !(c->prm.flags & kFlagNoLockstep) && lockstep_fits(lanes, c->maxdeg)) {
+        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, ants, kc));
+    } else {
+        GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, ants, kc));
+    }
+    return GMP_OK;
+}
+
+// Device workspace of a job with n colonies, total_ants ants per iteration and at most maxI iterations
+// (buffers only grow, so a reservation for the largest job makes later staging allocation-free).
+int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI, uint64_t log_entries,
+                      const KernelConfig& kc) {
+    Batch& b = c->b;
+    const bool persistent = c->prm.mode == GMP_MODE_PERSISTENT;
+    const size_t words = (c->N + 31u) / 32u;
+    const size_t max_steps = std::max<uint32_t>(default_max_steps(c), 1u);
+    if (persistent && (uint64_t)kc.grid < n)
+        return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs at least one resident block per colony");
+    GMP_TRY(ensure(c, &b.dq, n));
+    GMP_TRY(ensure(c, &b.prefix, n + 1));
+    GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.tauf, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.heur, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.qs, n));
+    GMP_TRY(ensure(c, &b.routes, (size_t)total_ants * max_steps));
+    GMP_TRY(ensure(c, &b.ant_steps, (size_t)total_ants));
+    GMP_TRY(ensure(c, &b.ant_wait, (size_t)total_ants));
+    GMP_TRY(ensure(c, &b.best_route, (size_t)n * max_steps));
+    GMP_TRY(ensure(c, &b.route_out, (size_t)n * (max_steps + 1)));
+    GMP_TRY(ensure(c, &b.tickets, maxI));
+    GMP_TRY(ensure(c, &b.res, n));
+    if (persistent) {
+        GMP_TRY(ensure(c, &b.ctr, (size_t)n * maxI));
+        GMP_TRY(ensure(c, &b.qstate, n));
+        GMP_TRY(ensure(c, &b.qflag, maxI));
+        GMP_TRY(ensure(c, &b.misc, 2));
+    }
+    if (log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)log_entries * 4));
+    if (!kc.tabu_in_smem) GMP_TRY(ensure(c, &b.tabu, (size_t)kc.grid * (kc.block / kc.lanes) * words));
+    return GMP_OK;
+}
+
+}  // namespace
+
+int gmp_batch_reserve(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max_iter) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (n == 0 || total_ants == 0 || max_iter == 0 || total_ants >= (1ull << 32))
+        return fail(c, GMP_ERR_INVALID_ARG, "reserve needs n >= 1, 1 <= total_ants < 2^32, max_iter >= 1");
+    cudaSetDevice(c->device);
+    GMP_TRY(sync(c));
+    KernelConfig kc{};
+    GMP_TRY(job_config(c, pick_lanes(c), total_ants, &kc));
+    const uint64_t logs = (c->prm.flags & GMP_FLAG_ANT_LOG) ? total_ants * max_iter : 0;
+    c->b.staged = c->b.ran = false;  // buffers may move: stage again
+    const int rc = reserve_workspace(c, n, total_ants, max_iter, logs, kc);
+    if (rc == GMP_ERR_OOM) free_batch(c);  // hold nothing from a reservation that did not fit
+    return rc;
+}
+
+int gmp_batch_ready(gmp_ctx* c, int* ready) {
+    if (!c || !ready) return GMP_ERR_INVALID_ARG;
+    if (!c->b.ran || !c->b.done) return fail(c, GMP_ERR_STATE, "launch the batch first");
+    const cudaError_t e = cudaEventQuery(c->b.done);
+    if (e == cudaErrorNotReady) {
+        *ready = 0;
+        return GMP_OK;
+    }
+    GMP_CUDA(c, e);
+    *ready = 1;
     return GMP_OK;
 }
 
@@ -703,43 +826,9 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.total_ants = (uint32_t)total;
     b.maxI = maxI;
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
-    b.kc = KernelConfig{};
     b.persistent = c->prm.mode == GMP_MODE_PERSISTENT;
-    if (b.persistent) {
-        if (lanes == 1) return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs 4, 8, 16 or 32 lanes per ant");
-        GMP_CUDA(c, persistent_config(c->device, lanes, c->N, c->maxdeg, &b.kc));
-    } else if (lanes != 1 && lanes <= 16 && !(c->prm.flags & kFlagNoLockstep) && c->maxdeg <= (uint32_t)(2 * lanes) &&
-        lanes * (c->maxdeg <= (uint32_t)lanes ? 1 : 2) <= 16) {
-        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, b.total_ants, &b.kc));
-    } else {
-        GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, b.total_ants, &b.kc));
-    }
-    const size_t words = (c->N + 31u) / 32u;
-    GMP_TRY(ensure(c, &b.dq, n));
-    GMP_TRY(ensure(c, &b.prefix, n + 1));
-    GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.tauf, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.heur, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.qs, n));
-    GMP_TRY(ensure(c, &b.routes, (size_t)b.total_ants * b.max_steps));
-    GMP_TRY(ensure(c, &b.ant_steps, b.total_ants));
-    GMP_TRY(ensure(c, &b.ant_wait, b.total_ants));
-    GMP_TRY(ensure(c, &b.best_route, (size_t)n * b.max_steps));
-    GMP_TRY(ensure(c, &b.route_out, (size_t)n * (b.max_steps + 1)));
-    GMP_TRY(ensure(c, &b.tickets, maxI));
-    GMP_TRY(ensure(c, &b.res, n));
-    if (b.persistent && (uint64_t)b.kc.grid < n)
-        return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs at least one resident block per colony");
-    if (b.persistent) {
-        GMP_TRY(ensure(c, &b.ctr, (size_t)n * maxI));
-        GMP_TRY(ensure(c, &b.qstate, n));
-        GMP_TRY(ensure(c, &b.qflag, maxI));
-        GMP_TRY(ensure(c, &b.misc, 2));
-    }
-    if (b.log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)b.log_entries * 4));
-    if (!b.kc.tabu_in_smem)
-        GMP_TRY(ensure(c, &b.tabu, (size_t)b.kc.grid * (b.kc.block / b.kc.lanes) * words));
+    GMP_TRY(job_config(c, lanes, b.total_ants, &b.kc));
+    GMP_TRY(reserve_workspace(c, n, b.total_ants, maxI, b.log_entries, b.kc));
     GMP_TRY(upload(c, b.dq, hdq.data(), n));
     GMP_TRY(upload(c, b.prefix, prefix.data(), n + 1));
     GMP_TRY(sync(c));
@@ -784,6 +873,8 @@ int gmp_batch_launch(gmp_ctx* c) {
         }
         GMP_CUDA(c, cudaGraphLaunch(b.exec, c->stream));
     }
+    if (!b.done) GMP_CUDA(c, cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+    GMP_CUDA(c, cudaEventRecord(b.done, c->stream));
     b.ran = true;
     return GMP_OK;
 }
@@ -880,6 +971,34 @@ int gmp_get_phase_order(gmp_ctx* c, uint8_t* out) {
     cudaSetDevice(c->device);
     GMP_CUDA(c, cudaMemcpyAsync(out, c->order, (size_t)c->N * kMaxPhases, cudaMemcpyDeviceToHost, c->stream));
     return sync(c);
+}
+
+int gmp_get_densities(gmp_ctx* c, uint32_t* vehicles) {
+    if (!c || (!vehicles && c->E)) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    cudaSetDevice(c->device);
+    if (c->E) GMP_CUDA(c, cudaMemcpyAsync(vehicles, c->veh, c->E * 4ull, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+int gmp_get_red_times(gmp_ctx* c, uint32_t* red_ms) {
+    if (!c || !red_ms) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    cudaSetDevice(c->device);
+    GMP_CUDA(c, cudaMemcpyAsync(red_ms, c->red, (size_t)c->N * kMaxPhases * 4, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+int gmp_tick(gmp_ctx* c, uint64_t t_now_ms, uint32_t dt_ms) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (t_now_ms > kTickClockMax || dt_ms > kTickDtMax)
+        return fail(c, GMP_ERR_INVALID_ARG, "tick clock must be <= 2^48 ms and dt <= 2^30 ms");
+    cudaSetDevice(c->device);
+    GMP_CUDA(c, launch_tick(c->stream, c->N, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
+                            c->ephase, c->lanes, c->veh, c->order, t_now_ms, dt_ms, hsat_of(c), c->tick_leave,
+                            c->tick_K, c->red));
+    return refresh_dynamic(c);
 }
 
 int gmp_get_edge_times(gmp_ctx* c, uint32_t* tt_ms, uint32_t* qd_ms) {
@@ -1083,3 +1202,9 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     GMP_CUDA(c, launch_finalize(s, 1, dq, qs, best_route, c->col, S, reinterpret_cast<DevResult*>(d_result), d_route));
     return GMP_OK;
 }
+
+namespace gmp {
+
+int ctx_check_query(gmp_ctx* c, const gmp_query& q) { return check_query(c, q, 0); }
+
+}  // namespace gmp

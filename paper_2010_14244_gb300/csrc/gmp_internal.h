@@ -62,6 +62,7 @@ struct PersistentArgs {
     uint8_t* order;
     EdgeRec* rec;
     uint32_t n_nodes, max_iter, spin_limit;
+    uint32_t node_chunk;  // intersections per queue-update chunk (8..64)
 };
 
 struct KernelConfig {
@@ -84,6 +85,11 @@ cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_
                                  const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
                                  const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec);
+cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
+                        const uint32_t* in_edge, const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
+                        const uint32_t* green, const uint8_t* ephase, const uint8_t* lanes, uint32_t* veh,
+                        const uint8_t* order, uint64_t t_now, uint32_t dt, uint32_t h_sat, uint32_t* leave,
+                        unsigned long long* K, uint32_t* red);
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               float* tauf, unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
@@ -111,5 +117,20 @@ cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, u
                                       uint32_t total_ants, KernelConfig* out);
 int construct_max_degree(int lanes);
 bool construct_thread_fits(uint32_t n_nodes);
+
+// Context internals for the host-side layers built on the C ABI (autotuner, server) (gmp_api.cu).
+constexpr uint32_t kFlagNoLockstepBit = 16u;  // params.flags bit: free-running groups instead of lockstep
+struct CtxInfo {
+    int device;
+    cudaStream_t stream;
+    uint32_t N, E, maxdeg;
+    bool has_graph;
+    uint64_t budget, used;  // device memory bound (0 = none) and bytes held
+};
+CtxInfo ctx_info(const gmp_ctx* c);
+int ctx_fail(gmp_ctx* c, int code, const char* msg);
+uint32_t default_lanes(uint32_t maxdeg);  // lanes per ant when the parameters leave it open
+bool lockstep_fits(int lanes, uint32_t maxdeg);  // the warp-lockstep construction kernel covers this shape
+int ctx_check_query(gmp_ctx* c, const gmp_query& q);  // the checks gmp_batch_stage applies to one query
 
 }  // namespace gmp

@@ -70,6 +70,85 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
 }
 
 // ------------------------------------------------------------------------------------------------
+// Serving tick: the queue/preemption update with dt > 0 (Fig. 3 signal block, Calc_Dens and Comp_Thres
+// of Sec. 4.2 applied to moving vehicles). Two passes, then the usual refresh of road records and
+// phase orders from the new vehicles and red times.
+// ------------------------------------------------------------------------------------------------
+// Node pass (one thread per node, over its approaches): the phase green at t_now under the current
+// order (every approach is served at an unsignalised node), the discharge of every served approach
+// (saturation flow counted on the whole clock), the node's total discharge, and its red-time update
+// (0 for the green phase and empty phases, + dt saturating otherwise; queues before the discharge).
+__global__ void k_tick_node(uint32_t N, const uint32_t* __restrict__ in_ptr, const uint32_t* __restrict__ in_edge,
+                            const uint8_t* __restrict__ nph, const uint32_t* __restrict__ cycle,
+                            const uint32_t* __restrict__ offset, const uint32_t* __restrict__ green,
+                            const uint8_t* __restrict__ ephase, const uint8_t* __restrict__ lanes,
+                            const uint32_t* __restrict__ veh, const uint8_t* __restrict__ order, uint64_t t_now,
+                            uint32_t dt, uint32_t h_sat, uint32_t* __restrict__ leave,
+                            unsigned long long* __restrict__ K, uint32_t* __restrict__ red) {
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
+    uint32_t gph = 0xFFFFFFFFu;
+    if (P) {
+        const uint32_t cy = cycle[v];
+        const uint32_t c = (uint32_t)((t_now % cy + cy - offset[v] % cy) % cy);  // position in the cycle
+        uint32_t start = 0;
+        for (uint32_t i = 0; i < P; ++i) {
+            const uint32_t p = order[(size_t)v * kMaxPhases + i];
+            const uint32_t g = green[(size_t)v * kMaxPhases + p];
+            if (c >= start && c < start + g) {
+                gph = p;
+                break;
+            }
+            start += g;
+        }
+    }
+    uint64_t Q[kMaxPhases];
+    for (uint32_t p = 0; p < kMaxPhases; ++p) Q[p] = 0;
+    unsigned long long k = 0;
+    for (uint32_t i = ib; i < ie; ++i) {
+        const uint32_t e = in_edge[i];
+        const uint32_t n = veh[e], p = ephase[e];
+        uint32_t out = 0;
+        if (P) Q[p & (kMaxPhases - 1)] += n;
+        if (P == 0 || p == gph) {
+            const uint64_t L = lanes[e];
+            const uint64_t cap = L * (t_now + dt) / h_sat - L * t_now / h_sat;
+            out = n < cap ? n : (uint32_t)cap;
+        }
+        leave[e] = out;
+        k += out;
+    }
+    K[v] = k;
+    for (uint32_t p = 0; p < kMaxPhases; ++p) {
+        uint32_t& r = red[(size_t)v * kMaxPhases + p];
+        if (P == 0 || p >= P || p == gph || Q[p] == 0)
+            r = 0;
+        else
+            r = r > 0xFFFFFFFFu - dt ? 0xFFFFFFFFu : r + dt;
+    }
+}
+
+// Scatter pass (one thread per node, over its out-roads): a road keeps what it did not discharge and
+// gains its share of its tail node's discharge, K/d each and one more for the first K mod d roads in
+// CSR order. Vehicles that reach a node without out-roads leave the network.
+__global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
+                               const unsigned long long* __restrict__ K, const uint32_t* __restrict__ leave,
+                               uint32_t* __restrict__ veh) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= N) return;
+    const uint32_t b = row_ptr[u], d = row_ptr[u + 1] - b;
+    if (d == 0) return;
+    const unsigned long long k = K[u];
+    const unsigned long long share = k / d;
+    const uint32_t extra = (uint32_t)(k - share * d);
+    for (uint32_t j = 0; j < d; ++j) {
+        const uint32_t e = b + j;
+        veh[e] = (uint32_t)(veh[e] - leave[e] + share + (j < extra ? 1u : 0u));
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Batch initialisation: pheromone 1.0 (or Philox-random in [0.5, 1.5)), deposits zero, colony state.
 // ------------------------------------------------------------------------------------------------
 // Calc_Dist for the whole colony up front: hq[e] = h(head(e)) towards this colony's destination.
@@ -695,6 +774,18 @@ cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_
     if (N == 0) return cudaSuccess;
     k_queue_preempt<<<blocks_for(N, 128), 128, 0, s>>>(N, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh,
                                                         cap, red, order, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
+                        const uint32_t* in_edge, const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
+                        const uint32_t* green, const uint8_t* ephase, const uint8_t* lanes, uint32_t* veh,
+                        const uint8_t* order, uint64_t t_now, uint32_t dt, uint32_t h_sat, uint32_t* leave,
+                        unsigned long long* K, uint32_t* red) {
+    if (N == 0) return cudaSuccess;
+    k_tick_node<<<blocks_for(N, 128), 128, 0, s>>>(N, in_ptr, in_edge, nph, cycle, offset, green, ephase, lanes, veh,
+                                                    order, t_now, dt, h_sat, leave, K, red);
+    k_tick_scatter<<<blocks_for(N, 128), 128, 0, s>>>(N, row_ptr, K, leave, veh);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,6 @@ namespace gmp {
 
 enum : uint32_t { kPhaseAnts = 0, kPhaseEnd = 1, kPhaseDone = 2 };
 constexpr uint32_t kEdgeChunk = 64;   // roads per evaporation chunk (a few per lane, all loads in flight)
-constexpr uint32_t kNodeChunk = 16;   // intersections per queue-update chunk
 
 __device__ __forceinline__ uint32_t load_acquire(const uint32_t* p) {
     uint32_t v;
@@ -67,7 +66,8 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
     __syncwarp(gmask);
     const uint32_t Q = a.n_queries, E = a.n_edges;
     const uint32_t n_edge_chunks = (E + kEdgeChunk - 1) / kEdgeChunk;
-    const uint32_t n_node_chunks = (p.n_nodes + kNodeChunk - 1) / kNodeChunk;
+    const uint32_t node_chunk = p.node_chunk;  // intersections per queue-update chunk
+    const uint32_t n_node_chunks = (p.n_nodes + node_chunk - 1) / node_chunk;
     // colony qi is served by the blocks b == qi (mod Q), so the groups of a warp share a colony and go
     // through its phases together; j is this group's rank among the colony's groups
     const uint32_t qi = blockIdx.x % Q, j = (blockIdx.x / Q) * groups + gib;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
                         }
                     }
                 } else {  // queue / preemption update of intersections [v0, v1) (densities fixed: same order)
-                    const uint32_t v0 = (c - n_edge_chunks) * kNodeChunk, v1 = min(p.n_nodes, v0 + kNodeChunk);
+                    const uint32_t v0 = (c - n_edge_chunks) * node_chunk, v1 = min(p.n_nodes, v0 + node_chunk);
                     for (uint32_t v = v0 + lane; v < v1; v += G)
                         queue_node(v, p.in_ptr, p.in_edge, p.nph, p.cycle, p.offset, p.green, p.ephase, p.veh,
                                    p.cap, p.red, p.order, p.rec);

@@ -1,0 +1,188 @@
+// Schedule autotuner (gmp_autotune, declared in include/gmacop.h).
+//
+// Every schedule computes the same results bit for bit: lanes per ant (ants per warp = 32 / lanes),
+// warp lockstep or free-running groups, the iterative job or the persistent job, and the persistent
+// job's queue-update chunk change only how the same arithmetic is laid onto the GPU. So the tuner may
+// pick whatever runs fastest. It times a short probe job (the caller's queries with their iteration
+// counts clamped) under every schedule the graph admits and keeps the fastest, once per size bucket
+// of the process: (SM count, ceil(log2 N), maximum out-degree, ceil(log2 ants per iteration)).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "gmacop.h"
+#include "gmp_internal.h"
+
+using namespace gmp;
+
+namespace {
+
+struct Schedule {
+    uint32_t lanes, mode, chunk, free_running;
+};
+
+using Bucket = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
+
+std::mutex g_mu;
+std::map<Bucket, Schedule> g_cache;
+
+uint32_t ceil_log2(uint64_t x) {
+    uint32_t k = 0;
+    while ((1ull << k) < x) ++k;
+    return k;
+}
+
+// The schedule of an untuned context: iterative job, lanes per ant from the degree, warp lockstep
+// where the lockstep kernel covers the shape.
+Schedule default_schedule(uint32_t maxdeg) {
+    const uint32_t g = default_lanes(maxdeg);
+    return {g, GMP_MODE_ITERATIVE, 0, 0};
+}
+
+uint32_t runs_lockstep(const Schedule& s, uint32_t maxdeg) {
+    return s.mode == GMP_MODE_ITERATIVE && !s.free_running && lockstep_fits((int)s.lanes, maxdeg) ? 1u : 0u;
+}
+
+std::vector<Schedule> candidates(uint32_t n_nodes, uint32_t maxdeg) {
+    const Schedule d = default_schedule(maxdeg);
+    std::vector<Schedule> out{d};  // timed first
+    auto add = [&](Schedule s) {
+        if (!(s.lanes == d.lanes && s.mode == d.mode && s.chunk == d.chunk && s.free_running == d.free_running))
+            out.push_back(s);
+    };
+    if (construct_thread_fits(n_nodes) && (uint32_t)construct_max_degree(1) >= maxdeg)
+        add({1, GMP_MODE_ITERATIVE, 0, 0});
+    for (uint32_t g : {4u, 8u, 16u, 32u}) {
+        if ((uint32_t)construct_max_degree((int)g) < maxdeg) continue;
+        add({g, GMP_MODE_ITERATIVE, 0, 0});
+        if (lockstep_fits((int)g, maxdeg)) add({g, GMP_MODE_ITERATIVE, 0, 1});
+        for (uint32_t ch : {8u, 16u, 32u, 64u}) add({g, GMP_MODE_PERSISTENT, ch, 0});
+    }
+    return out;
+}
+
+gmp_params with_schedule(gmp_params p, const Schedule& s) {
+    p.lanes_per_ant = s.lanes;
+    p.mode = s.mode;
+    p.queue_chunk = s.chunk;
+    p.flags = (p.flags & ~kFlagNoLockstepBit) | (s.free_running ? kFlagNoLockstepBit : 0u);
+    return p;
+}
+
+// Probe job time under the context's current parameters: one launch to warm up (and capture), then
+// the best of two timed launches. Returns a negative value when the schedule does not run here.
+float time_probe(gmp_ctx* c, uint32_t n, const gmp_query* q, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    if (gmp_batch_stage(c, n, q) != GMP_OK) return -1.0f;
+    std::vector<gmp_result> res(n);
+    for (auto& r : res) memset(&r, 0, sizeof r);
+    if (gmp_batch_launch(c) != GMP_OK || gmp_batch_collect(c, res.data()) != GMP_OK) return -1.0f;
+    float best = -1.0f;
+    for (int rep = 0; rep < 2; ++rep) {
+        if (cudaEventRecord(e0, s) != cudaSuccess) return -1.0f;
+        if (gmp_batch_launch(c) != GMP_OK) return -1.0f;
+        if (cudaEventRecord(e1, s) != cudaSuccess) return -1.0f;
+        if (gmp_batch_collect(c, res.data()) != GMP_OK) return -1.0f;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0f;
+        if (best < 0.0f || ms < best) best = ms;
+    }
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_iter, gmp_tune_result* out) {
+    if (!c || !out || (n && !probe)) return GMP_ERR_INVALID_ARG;
+    if (n == 0) return ctx_fail(c, GMP_ERR_INVALID_ARG, "autotune needs at least one probe query");
+    const CtxInfo info = ctx_info(c);
+    if (!info.has_graph) return ctx_fail(c, GMP_ERR_STATE, "load a graph first");
+    memset(out, 0, sizeof *out);
+    int sms = 0;
+    cudaSetDevice(info.device);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, info.device) != cudaSuccess)
+        return ctx_fail(c, GMP_ERR_CUDA, "cannot read the SM count");
+    const uint32_t it_cap = probe_iter ? probe_iter : 8u;
+    std::vector<gmp_query> q(probe, probe + n);
+    uint64_t ants = 0;
+    for (auto& x : q) {
+        x.n_iter = std::min(x.n_iter, it_cap);
+        ants += x.n_ants;
+    }
+    const Bucket key{(uint32_t)sms, ceil_log2(info.N), info.maxdeg, ceil_log2(ants)};
+    out->bucket[0] = std::get<0>(key);
+    out->bucket[1] = std::get<1>(key);
+    out->bucket[2] = std::get<2>(key);
+    out->bucket[3] = std::get<3>(key);
+    gmp_params base{};
+    gmp_get_params(c, &base);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            const Schedule s = it->second;
+            const gmp_params p = with_schedule(base, s);
+            const int rc = gmp_set_params(c, &p);
+            if (rc != GMP_OK) return rc;
+            out->lanes_per_ant = s.lanes;
+            out->mode = s.mode;
+            out->queue_chunk = s.chunk;
+            out->lockstep = runs_lockstep(s, info.maxdeg);
+            out->from_cache = 1;
+            return GMP_OK;
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return ctx_fail(c, GMP_ERR_CUDA, "cudaEventCreate failed");
+    }
+    const std::vector<Schedule> cand = candidates(info.N, info.maxdeg);
+    Schedule best{};
+    float best_ms = -1.0f;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        const gmp_params p = with_schedule(base, cand[i]);
+        if (gmp_set_params(c, &p) != GMP_OK) continue;
+        const float ms = time_probe(c, n, q.data(), info.stream, e0, e1);
+        if (ms < 0.0f) continue;
+        ++out->n_tried;
+        if (i == 0) out->default_ms = ms;
+        if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms < 0.0f) {
+        gmp_set_params(c, &base);
+        return ctx_fail(c, GMP_ERR_UNSUPPORTED, "no schedule could run the probe");
+    }
+    const gmp_params p = with_schedule(base, best);
+    const int rc = gmp_set_params(c, &p);
+    if (rc != GMP_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_cache[key] = best;
+    }
+    out->lanes_per_ant = best.lanes;
+    out->mode = best.mode;
+    out->queue_chunk = best.chunk;
+    out->lockstep = runs_lockstep(best, info.maxdeg);
+    out->best_ms = best_ms;
+    return GMP_OK;
+}
+
+void gmp_autotune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache.clear();
+}
+
+}  // extern "C"

@@ -24,10 +24,27 @@ MODE_AUTO, MODE_ITERATIVE, MODE_PERSISTENT = 0, 1, 2
 _LIB = None
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("lanes_per_ant", C.c_uint32), ("mode", C.c_uint32), ("queue_chunk", C.c_uint32),
+                ("lockstep", C.c_uint32), ("from_cache", C.c_uint32), ("n_tried", C.c_uint32),
+                ("best_ms", C.c_float), ("default_ms", C.c_float), ("bucket", C.c_uint32 * 4)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_uint32), ("max_ants", C.c_uint32), ("max_iter", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_uint32), ("in_flight", C.c_uint32), ("busy_slots", C.c_uint32),
+                ("done_waiting", C.c_uint32), ("jobs", C.c_uint64), ("completed", C.c_uint64),
+                ("rejected", C.c_uint64)]
+
+
 class Params(C.Structure):
     _fields_ = [("max_steps", C.c_uint32), ("h_sat_ms", C.c_uint32), ("thr_permille", C.c_uint32),
                 ("flags", C.c_uint32), ("t_dep_ms", C.c_uint32), ("lanes_per_ant", C.c_uint32),
-                ("mode", C.c_uint32), ("reserved", C.c_uint32)]
+                ("mode", C.c_uint32), ("queue_chunk", C.c_uint32)]
 
 
 class Query(C.Structure):
@@ -41,6 +58,12 @@ class Result(C.Structure):
                 ("travel_ms", C.c_uint64), ("wait_ms", C.c_uint64), ("ant_steps", C.c_uint64),
                 ("n_success", C.c_uint64), ("best_iter", C.c_uint32), ("best_ant", C.c_uint32),
                 ("status", C.c_int32), ("reserved", C.c_uint32)]
+
+
+class Served(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("t_submit_ns", C.c_uint64), ("t_launch_ns", C.c_uint64),
+                ("t_done_ns", C.c_uint64), ("clock_ms", C.c_uint64), ("slot", C.c_uint32),
+                ("batch_size", C.c_uint32), ("result", Result)]
 
 
 # name -> (restype, argtypes); the same names as include/gmacop.h
@@ -66,6 +89,21 @@ SIGNATURES = {
     "gmp_get_pheromone": (_i32, [_vp, _u32, _vp]),
     "gmp_get_ant_log": (_i32, [_vp, _u32, _vp, _u64]),
     "gmp_get_phase_order": (_i32, [_vp, _vp]),
+    "gmp_get_densities": (_i32, [_vp, _vp]),
+    "gmp_get_red_times": (_i32, [_vp, _vp]),
+    "gmp_tick": (_i32, [_vp, _u64, _u32]),
+    "gmp_autotune": (_i32, [_vp, _u32, C.POINTER(Query), _u32, C.POINTER(TuneResult)]),
+    "gmp_autotune_reset": (None, []),
+    "gmp_batch_reserve": (_i32, [_vp, _u32, _u64, _u32]),
+    "gmp_batch_ready": (_i32, [_vp, C.POINTER(C.c_int)]),
+    "gmp_server_create": (_i32, [C.POINTER(_vp), C.POINTER(_vp), _u32, C.POINTER(ServerConfig)]),
+    "gmp_server_destroy": (None, [_vp]),
+    "gmp_server_last_error": (C.c_char_p, [_vp]),
+    "gmp_server_slot_capacity": (_i32, [_vp, _u32, C.POINTER(_u32)]),
+    "gmp_server_submit": (_i32, [_vp, C.POINTER(Query), _u64]),
+    "gmp_server_tick": (_i32, [_vp, _u64, _u32]),
+    "gmp_server_pump": (_i32, [_vp, C.POINTER(ServerStats)]),
+    "gmp_server_take": (_i32, [_vp, _u32, C.POINTER(Served), _vp, _u64, C.POINTER(_u32)]),
     "gmp_get_edge_times": (_i32, [_vp, _vp, _vp]),
     "gmp_get_kernel_times": (_i32, [_vp, _vp]),
     "gmp_get_launch_count": (_i32, [_vp, C.POINTER(_u64)]),
@@ -169,8 +207,8 @@ class Context:
         self.set_densities(wl.vehicles)
 
     def set_params(self, max_steps=0, h_sat_ms=0, thr_permille=THRESHOLD_OFF, flags=0, t_dep_ms=0,
-                   lanes_per_ant=0, mode=MODE_AUTO):
-        p = Params(max_steps, h_sat_ms, thr_permille, flags, t_dep_ms, lanes_per_ant, mode, 0)
+                   lanes_per_ant=0, mode=MODE_AUTO, queue_chunk=0):
+        p = Params(max_steps, h_sat_ms, thr_permille, flags, t_dep_ms, lanes_per_ant, mode, queue_chunk)
         self._check(lib().gmp_set_params(self._h, C.byref(p)))
 
     def get_params(self) -> dict:
@@ -255,6 +293,42 @@ class Context:
         self._check(lib().gmp_get_phase_order(self._h, _p(out)))
         return out
 
+    def densities(self) -> np.ndarray:
+        out = np.zeros(self.n_edges, np.uint32)
+        self._check(lib().gmp_get_densities(self._h, _p(out)))
+        return out
+
+    def red_times(self) -> np.ndarray:
+        out = np.zeros((self.n_nodes, 8), np.uint32)
+        self._check(lib().gmp_get_red_times(self._h, _p(out)))
+        return out
+
+    def tick(self, t_now_ms: int, dt_ms: int):
+        """gmp_tick: advance the traffic state by dt_ms at clock t_now_ms (asynchronous)."""
+        self._check(lib().gmp_tick(self._h, t_now_ms, dt_ms))
+
+    def autotune(self, probe_queries, probe_iter=0) -> dict:
+        """gmp_autotune: time the schedules on a probe job (or reuse the bucket's cached choice) and
+        apply the fastest to this context."""
+        arr = (Query * len(probe_queries))(*[self._cq(q) for q in probe_queries])
+        r = TuneResult()
+        self._check(lib().gmp_autotune(self._h, len(probe_queries), arr, probe_iter, C.byref(r)))
+        out = {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "bucket"}
+        out["bucket"] = list(r.bucket)
+        return out
+
+    @staticmethod
+    def autotune_reset():
+        lib().gmp_autotune_reset()
+
+    def reserve(self, n_queries: int, total_ants: int, max_iter: int):
+        self._check(lib().gmp_batch_reserve(self._h, n_queries, total_ants, max_iter))
+
+    def ready(self) -> bool:
+        r = C.c_int()
+        self._check(lib().gmp_batch_ready(self._h, C.byref(r)))
+        return bool(r.value)
+
     def edge_times(self):
         tt = np.zeros(self.n_edges, np.uint32)
         qd = np.zeros(self.n_edges, np.uint32)
@@ -271,3 +345,74 @@ class Context:
         n = C.c_uint64()
         self._check(lib().gmp_get_launch_count(self._h, C.byref(n)))
         return int(n.value)
+
+
+class Server:
+    """gmp_server: continuous batching over slot contexts that hold replicas of one traffic state."""
+
+    def __init__(self, slots, max_batch: int, max_ants: int, max_iter: int):
+        self.slots = list(slots)
+        arr = (_vp * len(self.slots))(*[c._h.value for c in self.slots])
+        cfg = ServerConfig(max_batch, max_ants, max_iter, 0)
+        self._h = C.c_void_p()
+        rc = lib().gmp_server_create(C.byref(self._h), arr, len(self.slots), C.byref(cfg))
+        if rc != OK:
+            raise GmpError(rc, lib().gmp_last_error(self.slots[0]._h).decode())
+        self.route_cap = self.slots[0].n_nodes + 1
+        self._buf = np.zeros(1 << 16, np.uint32)
+        self._out = (Served * 256)()
+
+    def close(self):
+        if self._h:
+            lib().gmp_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise GmpError(rc, lib().gmp_server_last_error(self._h).decode())
+
+    def capacity(self, slot: int) -> int:
+        n = _u32()
+        self._check(lib().gmp_server_slot_capacity(self._h, slot, C.byref(n)))
+        return int(n.value)
+
+    def submit(self, q, tag: int):
+        cq = Context._cq(q)
+        self._check(lib().gmp_server_submit(self._h, C.byref(cq), tag))
+
+    def tick(self, t_now_ms: int, dt_ms: int):
+        self._check(lib().gmp_server_tick(self._h, t_now_ms, dt_ms))
+
+    def pump(self) -> dict:
+        st = ServerStats()
+        self._check(lib().gmp_server_pump(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def take(self) -> list[dict]:
+        out = []
+        while True:
+            n = _u32()
+            rc = lib().gmp_server_take(self._h, len(self._out), self._out, _p(self._buf), self._buf.size, C.byref(n))
+            if rc == ERR_BUFFER:
+                self._buf = np.zeros(self._buf.size * 4, np.uint32)
+                continue
+            self._check(rc)
+            base = self._buf.ctypes.data
+            for i in range(n.value):
+                s = self._out[i]
+                r = s.result
+                off = (C.cast(r.route, C.c_void_p).value - base) // 4 if r.route else 0
+                route = self._buf[off:off + r.route_len].copy() if r.status == OK else np.zeros(0, np.uint32)
+                out.append(dict(tag=s.tag, t_submit_ns=s.t_submit_ns, t_launch_ns=s.t_launch_ns,
+                                t_done_ns=s.t_done_ns, clock_ms=s.clock_ms, slot=s.slot, batch_size=s.batch_size,
+                                status=r.status, route_len=r.route_len, travel_ms=r.travel_ms, wait_ms=r.wait_ms,
+                                ant_steps=r.ant_steps, n_success=r.n_success, best_iter=r.best_iter,
+                                best_ant=r.best_ant, route=route))
+            if n.value == 0:
+                return out

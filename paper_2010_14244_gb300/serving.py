@@ -1,0 +1,121 @@
+"""Serving loop on the C ABI: Poisson route requests, periodic traffic ticks, continuous batching.
+
+The loop only marshals: arrivals are submitted to the native server (gmp_server_*), which admits them
+into jobs on idle slots; ticks advance the device-resident traffic state on every slot; finished
+requests are taken back with their host timestamps. Latency is measured from each request's scheduled
+arrival time to the moment the server saw its job finish (both on the host's monotonic clock).
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import gmacop as G
+from .workloads import Query
+
+
+def make_server(wl, n_slots: int, max_batch: int, max_ants: int, max_iter: int, mem_budget: int = 0,
+                device: int = 0, params: dict | None = None):
+    """Slot contexts holding replicas of the workload's traffic state, and a server over them."""
+    slots = []
+    for _ in range(n_slots):
+        c = G.Context(device, mem_budget)
+        c.load_workload(wl)
+        if params:
+            c.set_params(**params)
+        slots.append(c)
+    return G.Server(slots, max_batch, max_ants, max_iter), slots
+
+
+@dataclass
+class ServeReport:
+    offered_per_s: float
+    window_s: float
+    submitted: int
+    completed: int
+    latencies_ms: np.ndarray = field(repr=False)
+    ant_steps: int
+    jobs: int
+    ticks: int
+    mean_batch: float
+    results: list = field(repr=False, default_factory=list)
+
+    def summary(self) -> dict:
+        lat = self.latencies_ms
+        return {
+            "offered_req_per_s": self.offered_per_s,
+            "window_s": self.window_s,
+            "submitted": self.submitted,
+            "completed": self.completed,
+            "queries_per_s": self.completed / self.window_s if self.window_s else 0.0,
+            "ant_steps_per_s": self.ant_steps / self.window_s if self.window_s else 0.0,
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "mean_batch": self.mean_batch,
+            "jobs": self.jobs,
+            "ticks": self.ticks,
+        }
+
+
+def uniform_requests(n_nodes: int, n_ants: int, n_iter: int, seed: int = 0):
+    """Uniform origin-destination requests (src != dst), seeded; the request's own seed is its index."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def make(i: int) -> Query:
+        s = int(rng.integers(n_nodes))
+        d = int(rng.integers(n_nodes - 1))
+        d += d >= s
+        return Query(s, d, n_ants, n_iter, 1.0, 2.0, 0.1, 1_000_003 * i + seed)
+
+    return make
+
+
+def run_poisson(server: G.Server, make_request, rate_per_s: float, duration_s: float, warmup_s: float = 0.0,
+                tick_ms: int = 1000, clock_start_ms: int = 0, seed: int = 0, drain_s: float = 30.0,
+                keep_results: bool = False) -> ServeReport:
+    """Offer Poisson arrivals at rate_per_s for warmup_s + duration_s seconds, tick the traffic state
+    every tick_ms of wall time, and report the requests that arrived inside the measured window."""
+    rng = np.random.Generator(np.random.PCG64(seed + 17))
+    total = warmup_s + duration_s
+    t0 = time.perf_counter_ns()
+    arrivals: dict[int, int] = {}  # tag -> scheduled arrival (ns, monotonic)
+    next_arr = rng.exponential(1.0 / rate_per_s)
+    next_tick = tick_ms / 1000.0
+    clock = clock_start_ms
+    tag = 0
+    ticks = 0
+    done: list[dict] = []
+    deadline = total + drain_s
+    while True:
+        now = (time.perf_counter_ns() - t0) * 1e-9
+        while next_arr <= now and next_arr < total:
+            q = make_request(tag)
+            arrivals[tag] = t0 + int(next_arr * 1e9)
+            server.submit(q, tag)
+            tag += 1
+            next_arr += rng.exponential(1.0 / rate_per_s)
+        if now >= next_tick and now < total:
+            server.tick(clock, tick_ms)
+            clock += tick_ms
+            ticks += 1
+            next_tick += tick_ms / 1000.0
+        st = server.pump()
+        done.extend(server.take())
+        if now >= total and st["queued"] == 0 and st["in_flight"] == 0 and st["done_waiting"] == 0:
+            break
+        if now >= deadline:
+            break
+    w0 = t0 + int(warmup_s * 1e9)
+    w1 = t0 + int(total * 1e9)
+    win = [r for r in done if w0 <= arrivals[r["tag"]] < w1]
+    lat = np.array([(r["t_done_ns"] - arrivals[r["tag"]]) * 1e-6 for r in win], np.float64)
+    last_done = max((r["t_done_ns"] for r in win), default=w1)
+    window = (max(w1, last_done) - w0) * 1e-9
+    return ServeReport(offered_per_s=rate_per_s, window_s=window,
+                       submitted=sum(1 for a in arrivals.values() if w0 <= a < w1), completed=len(win),
+                       latencies_ms=lat, ant_steps=int(sum(r["ant_steps"] for r in win)),
+                       jobs=int(st["jobs"]), ticks=ticks,
+                       mean_batch=float(np.mean([r["batch_size"] for r in win])) if win else 0.0,
+                       results=done if keep_results else [])

@@ -1,0 +1,189 @@
+"""Serving: continuous batching over slot contexts with traffic ticks between jobs.
+
+Each served result must equal the same request solved alone on a context whose traffic state went
+through the same ticks (and departing at the same clock), bit for bit; a sample is also checked against
+the oracle's tick chain and colony. Admission follows the slots' memory budgets."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2010_14244_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_2010_14244_gb300 import build, gmacop
+
+    build.build()
+    return gmacop
+
+
+def _mixed_requests(n_nodes, n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        s = int(rng.integers(n_nodes))
+        d = int(rng.integers(n_nodes - 1))
+        d += d >= s
+        out.append(W.Query(s, d, int(rng.choice([16, 48, 64])), int(rng.choice([3, 5, 8])), 1.0, 2.0, 0.1,
+                           1000 + 7 * i))
+    return out
+
+
+def _same(a, b):
+    for k in ("status", "travel_ms", "wait_ms", "ant_steps", "n_success", "best_iter", "best_ant", "route_len"):
+        assert a[k] == b[k], (k, a[k], b[k])
+    np.testing.assert_array_equal(a["route"], b["route"])
+
+
+def test_served_equals_alone_and_oracle(gm, orc):
+    from paper_2010_14244_gb300 import serving
+
+    wl = W.grid10()
+    srv, slots = serving.make_server(wl, n_slots=3, max_batch=6, max_ants=64, max_iter=8)
+    reqs = _mixed_requests(wl.net.n_nodes, 30, seed=3)
+    ticks = [(0, 1000), (1000, 2500), (3500, 700)]
+    done = []
+    try:
+        # waves: submit some, pump (jobs start), tick between waves while jobs are still on the GPU
+        waves = [reqs[0:9], reqs[9:14], reqs[14:25], reqs[25:30]]
+        for w, wave in enumerate(waves):
+            for i, q in enumerate(wave):
+                srv.submit(q, reqs.index(q))
+                if i % 3 == 2:
+                    srv.pump()
+            srv.pump()
+            done += srv.take()
+            if w < len(ticks):
+                srv.tick(*ticks[w])
+        for _ in range(200000):
+            st = srv.pump()
+            done += srv.take()
+            if st["queued"] == 0 and st["in_flight"] == 0 and st["done_waiting"] == 0:
+                break
+        assert len(done) == len(reqs) and sorted(r["tag"] for r in done) == list(range(len(reqs)))
+        assert max(r["batch_size"] for r in done) > 1
+        assert len({r["slot"] for r in done}) > 1
+        clocks = sorted({r["clock_ms"] for r in done})
+        assert len(clocks) > 1
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()
+    # the same requests alone, on a context replaying the ticks
+    ref = gm.Context(0)
+    try:
+        ref.load_workload(wl)
+        by_clock = {}
+        for r in done:
+            by_clock.setdefault(r["clock_ms"], []).append(r)
+        clock = 0
+        pending = list(ticks)
+        while True:
+            for r in by_clock.pop(clock, []):
+                q = reqs[r["tag"]]
+                ref.set_params(t_dep_ms=clock)
+                alone = ref.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed)
+                _same(r, alone)
+            if not pending:
+                break
+            t, dt = pending.pop(0)
+            ref.tick(t, dt)
+            clock = t + dt
+        assert not by_clock
+    finally:
+        ref.close()
+    # a sample against the oracle: its own tick chain, then the colony departing at that clock
+    veh = wl.vehicles.copy()
+    red = np.zeros((wl.net.n_nodes, 8), np.uint32)
+    order = orc.queue_preempt(orc.Net(wl.net, wl.signals, veh, red))
+    states = {0: (veh, red)}
+    for t, dt in ticks:
+        veh, red, order = orc.tick(orc.Net(wl.net, wl.signals, veh, red), orc.Params(), t, dt, order)
+        states[t + dt] = (veh, red)
+    for r in done[::5]:
+        v, rd = states[r["clock_ms"]]
+        o = orc.solve(orc.Net(wl.net, wl.signals, v, rd), orc.Params(t_dep_ms=r["clock_ms"]), reqs[r["tag"]],
+                      want_tau=False)
+        assert r["status"] == o["status"] and r["travel_ms"] == o["travel_ms"] and r["wait_ms"] == o["wait_ms"]
+        if o["status"] == 0:
+            np.testing.assert_array_equal(r["route"], o["route"])
+
+
+def test_admission_follows_memory_budget(gm):
+    from paper_2010_14244_gb300 import serving
+
+    wl = W.grid64(n_queries=1)
+    per_query = wl.net.n_edges * 24  # pheromone, its float copy, deposits and heuristic
+    probe = gm.Context(0)
+    probe.load_workload(wl)
+    base = probe.get_params()
+    probe.close()
+    assert base["mode"] == 0
+    budget = 64 << 20
+    srv, slots = serving.make_server(wl, n_slots=2, max_batch=512, max_ants=256, max_iter=10, mem_budget=budget)
+    try:
+        cap = srv.capacity(0)
+        assert 1 <= cap < 512
+        assert cap * per_query < budget
+        reqs = _mixed_requests(wl.net.n_nodes, 3 * cap, seed=4)
+        for i, q in enumerate(reqs):
+            srv.submit(dataclasses.replace(q, n_iter=2), i)
+        done = []
+        for _ in range(200000):
+            st = srv.pump()
+            done += srv.take()
+            if st["queued"] == 0 and st["in_flight"] == 0 and st["done_waiting"] == 0:
+                break
+        assert len(done) == len(reqs)
+        assert max(r["batch_size"] for r in done) <= cap
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()
+
+
+def test_submit_refuses_bad_requests(gm):
+    from paper_2010_14244_gb300 import serving
+
+    wl = W.grid10()
+    srv, slots = serving.make_server(wl, n_slots=1, max_batch=4, max_ants=32, max_iter=4)
+    try:
+        with pytest.raises(gm.GmpError) as ei:
+            srv.submit(W.Query(0, 99, 64, 2, 1.0, 2.0, 0.1, 1), 0)
+        assert ei.value.code == gm.ERR_INVALID_ARG
+        with pytest.raises(gm.GmpError) as ei:
+            srv.submit(W.Query(0, 100, 8, 2, 1.0, 2.0, 0.1, 1), 1)
+        assert ei.value.code == gm.ERR_INVALID_ARG
+        with pytest.raises(gm.GmpError) as ei:
+            srv.submit(W.Query(0, 9, 8, 2, 1.5, 2.0, 0.1, 1), 2)
+        assert ei.value.code == gm.ERR_UNSUPPORTED
+        with pytest.raises(gm.GmpError) as ei:
+            srv.tick((1 << 30) - 10, 100)
+        assert ei.value.code == gm.ERR_INVALID_ARG
+        assert srv.pump()["rejected"] == 3
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()
+
+
+def test_poisson_loop_reports_latency(gm):
+    from paper_2010_14244_gb300 import serving
+
+    wl = W.grid64(n_queries=1)
+    srv, slots = serving.make_server(wl, n_slots=4, max_batch=64, max_ants=128, max_iter=10)
+    try:
+        rep = serving.run_poisson(srv, serving.uniform_requests(wl.net.n_nodes, 128, 10, seed=1), rate_per_s=400,
+                                  duration_s=1.5, warmup_s=0.3, tick_ms=500)
+        s = rep.summary()
+        assert rep.completed == rep.submitted > 100
+        assert s["ticks"] >= 2 and s["p50_ms"] <= s["p99_ms"]
+        assert s["queries_per_s"] > 100
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()

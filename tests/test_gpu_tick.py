@@ -1,0 +1,114 @@
+"""Parity of the serving tick (gmp_tick) with the oracle's tick, bit for bit: vehicles on every road,
+red-time accumulators, phase orders and road times after every tick of a long sequence; and a colony
+solved on the ticked state equals the oracle's colony on the same state."""
+import random
+
+import numpy as np
+import pytest
+
+from paper_2010_14244_gb300 import workloads as W
+from tests import netbuild as NB
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    from paper_2010_14244_gb300 import build, gmacop
+
+    build.build()
+    return gmacop
+
+
+@pytest.fixture()
+def ctx(gm):
+    c = gm.Context(0)
+    yield c
+    c.close()
+
+
+def _run_ticks(ctx, orc, net, sig, veh, n_ticks, seed, h_sat_ms=0, check_every=1):
+    rng = random.Random(seed)
+    prm = orc.Params(h_sat_ms=h_sat_ms)
+    red = np.zeros((net.n_nodes, 8), np.uint32)
+    order = orc.queue_preempt(orc.Net(net, sig, veh, red))
+    t = rng.randrange(0, 100_000)
+    for k in range(n_ticks):
+        dt = rng.choice([0, 1, 250, 1000, 2000, 3700, 15_000])
+        ctx.tick(t, dt)
+        veh, red, order = orc.tick(orc.Net(net, sig, veh, red), prm, t, dt, order)
+        t += dt
+        if k % check_every == 0 or k == n_ticks - 1:
+            np.testing.assert_array_equal(ctx.densities(), veh, err_msg=f"tick {k}")
+            np.testing.assert_array_equal(ctx.red_times(), red, err_msg=f"tick {k}")
+            np.testing.assert_array_equal(ctx.phase_order(), order, err_msg=f"tick {k}")
+    prep = orc.prepare(orc.Net(net, sig, veh, red), prm, 0)
+    tt, qd = ctx.edge_times()
+    np.testing.assert_array_equal(tt, prep["tt"])
+    np.testing.assert_array_equal(qd, prep["qd"])
+    return veh, red, t
+
+
+@pytest.mark.parametrize("name", ["grid10", "grid64"])
+def test_tick_sequence_matches_oracle(gm, ctx, orc, name):
+    wl = W.grid10() if name == "grid10" else W.grid64(n_queries=1)
+    ctx.load_workload(wl)
+    _run_ticks(ctx, orc, wl.net, wl.signals, wl.vehicles.copy(), 40, seed=11)
+
+
+def test_tick_congested_and_custom_hsat(gm, ctx, orc):
+    """Densities above the 3/4-storage threshold on many approaches (preemption by queue length) and
+    a non-default saturation headway."""
+    wl = W.grid64(n_queries=1)
+    veh = (wl.vehicles.astype(np.uint64) * 12 + 7).astype(np.uint32)
+    ctx.load_workload(wl)
+    ctx.set_densities(veh)
+    ctx.set_params(h_sat_ms=1700)
+    _run_ticks(ctx, orc, wl.net, wl.signals, veh, 25, seed=12, h_sat_ms=1700)
+
+
+def test_tick_sinks_and_unsignalised(gm, ctx, orc):
+    """Nodes without out-roads absorb vehicles; unsignalised heads serve every approach."""
+    rng = np.random.default_rng(5)
+    roads = []
+    for u in range(40):
+        for v in rng.choice(60, size=rng.integers(1, 4), replace=False):
+            if v != u:
+                roads.append((u, int(v), int(rng.integers(300, 4000)), 50, int(rng.integers(1, 4)),
+                              int(rng.integers(0, 2))))
+    sigs = {v: (20_000, int(rng.integers(0, 20_000)), [12_000, 8_000]) for v in range(0, 60, 3)}
+    net, sig, veh = NB.build(60, roads, signals=sigs, bidirectional=False)
+    veh[:] = rng.integers(0, 60, size=veh.size)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    veh2, _, _ = _run_ticks(ctx, orc, net, sig, veh.copy(), 30, seed=13)
+    assert int(veh2.sum()) < int(veh.sum())  # vehicles left through nodes 40..59's missing out-roads
+
+
+def test_solve_after_ticks_matches_oracle(gm, ctx, orc):
+    wl = W.grid10()
+    ctx.load_workload(wl)
+    veh, red, t = _run_ticks(ctx, orc, wl.net, wl.signals, wl.vehicles.copy(), 12, seed=14, check_every=4)
+    onet = orc.Net(wl.net, wl.signals, veh, red)
+    t_dep = t % (1 << 29)
+    ctx.set_params(t_dep_ms=t_dep)
+    q = W.Query(3, 96, 32, 6, 1.0, 2.0, 0.1, 99)
+    g = ctx.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed)
+    o = orc.solve(onet, orc.Params(t_dep_ms=t_dep), q)
+    assert g["status"] == o["status"] == 0
+    assert g["travel_ms"] == o["travel_ms"] and g["wait_ms"] == o["wait_ms"]
+    np.testing.assert_array_equal(g["route"], o["route"])
+
+
+def test_tick_argument_errors(gm, ctx):
+    with pytest.raises(gm.GmpError) as ei:
+        ctx.tick(0, 1000)
+    assert ei.value.code == gm.ERR_STATE
+    ctx.load_workload(W.grid10())
+    with pytest.raises(gm.GmpError) as ei:
+        ctx.tick((1 << 48) + 1, 1000)
+    assert ei.value.code == gm.ERR_INVALID_ARG
+    with pytest.raises(gm.GmpError) as ei:
+        ctx.tick(0, (1 << 30) + 1)
+    assert ei.value.code == gm.ERR_INVALID_ARG
