@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="lanes per ant (0 = autotune)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the one-colony-per-launch comparison")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     p.add_argument("--iterations", type=int, default=0, help="override iterations (profiling runs only)")
     p.add_argument("--queries", type=int, default=0, help="override colony count (profiling runs only)")
     return p.parse_args()
@@ -207,6 +209,32 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------ serving
+SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S = 4, 1500.0, 2.0, 0.5
+SERVE_ANTS, SERVE_ITERS = 128, 30
+
+
+def serving_leg(wl):
+    """Route requests on the same road network: Poisson arrivals with uniform origin-destination pairs,
+    128 ants x 30 iterations each, traffic ticks every second, continuous batching over slot contexts."""
+    from paper_2010_14244_gb300 import serving
+
+    srv, slots = serving.make_server(wl, n_slots=SERVE_SLOTS, max_batch=256, max_ants=SERVE_ANTS,
+                                     max_iter=SERVE_ITERS)
+    try:
+        make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=5)
+        rep = serving.run_poisson(srv, make, rate_per_s=SERVE_RATE, duration_s=SERVE_WINDOW_S,
+                                  warmup_s=SERVE_WARMUP_S, tick_ms=1000)
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()
+    out = rep.summary()
+    out.update(slots=SERVE_SLOTS, ants=SERVE_ANTS, iterations=SERVE_ITERS, arrivals="poisson, uniform OD",
+               tick="1 s (queue/preemption update with vehicle discharge)")
+    return out
+
+
 # ------------------------------------------------------------------------------------------ GPU
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
@@ -221,10 +249,18 @@ def run_gpu(args, rank, world, local_rank):
     ctx = gmacop.Context(local_rank, stream=stream)
     ctx.load_workload(wl)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # schedule: the autotuner's choice for this size bucket (timed on a 32-iteration probe of the same
+    # colonies, not inside any timed region), unless the command line fixes one
+    tune = None
+    if args.lanes == 0 and args.mode == 0:
+        tune = ctx.autotune(wl.queries, probe_iter=32)
+    else:
+        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes)
+    sched = {k: v for k, v in ctx.get_params().items() if k in ("mode", "lanes_per_ant", "queue_chunk", "flags")}
 
     def timed_region(flags):
         """K steps, each bracketed by CUDA events on the library's stream, L2 flushed in between."""
-        ctx.set_params(flags=flags, mode=args.mode, lanes_per_ant=args.lanes)
+        ctx.set_params(**dict(sched, flags=sched["flags"] | flags))
         ctx.stage(wl.queries)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
@@ -233,7 +269,7 @@ def run_gpu(args, rank, world, local_rank):
             if world > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
-            times, kt = [], dict(construct=0.0, evaporate=0.0, best=0.0, queue=0.0, job=0.0)
+            times, kt = [], dict(construct=0.0, iter_end=0.0, init_finalize=0.0, job=0.0)
             for _ in range(args.steps):
                 flush.zero_()  # L2 flush between timed steps (not timed)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -269,13 +305,28 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
 
+    # the plain form: each colony its own job (stage, launch, collect), one after another
+    plain = None
+    if not args.no_plain:
+        ctx.set_params(**sched)
+        with torch.cuda.stream(stream):
+            ctx.solve_batch(wl.queries[:1])  # warm (captures the one-colony job graph)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            plain_steps = 0
+            for q in wl.queries:
+                plain_steps += ctx.solve_batch([q])[0]["ant_steps"]
+            plain_t = time.perf_counter() - t0
+        plain = {"queries_per_s": nq / plain_t, "ant_steps_per_s": plain_steps / plain_t, "ms": plain_t * 1e3,
+                 "how": f"the same {nq} colonies, each solved as its own job (stage, launch, collect) in sequence"}
+
     # end to end through the public API: densities and queries from pinned host memory, results back
     e2e = None
     if not args.no_e2e:
         veh = torch.from_numpy(wl.vehicles.astype(np.uint32)).pin_memory()
         veh_np = veh.numpy()
         e2e_t, e2e_steps, d2h = 0.0, 0, 0
-        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes)
+        ctx.set_params(**sched)
         with torch.cuda.stream(stream):
             ctx.set_densities(veh_np)
             ctx.solve_batch(wl.queries)  # warm (captures the job graph)
@@ -292,6 +343,9 @@ def run_gpu(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(wl.net.n_edges * 4 + nq * 40), "d2h_bytes_per_step": int(d2h),
                "queries_per_s": nq * args.steps / e2e_t}
     ctx.close()
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_leg(wl)
     if rank != 0:
         return
     K = args.steps
@@ -307,7 +361,9 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
         "config": dict(workload_config(wl), l2="flushed between timed steps (256 MB write)",
-                       mode=args.mode, lanes_per_ant=args.lanes or "auto"),
+                       schedule={k: sched[k] for k in ("mode", "lanes_per_ant", "queue_chunk")},
+                       lockstep=None if tune is None else tune["lockstep"],
+                       schedule_source="autotuned" if tune is not None else "command line"),
         "queries_per_s": world * nq * K / (total_ms / 1e3),
         "ant_steps_per_step": steps_per_job,
         "kernel_ms_per_step": {k: v / K for k, v in kt.items()},
@@ -322,6 +378,12 @@ def run_gpu(args, rank, world, local_rank):
     }
     if e2e:
         line["e2e"] = e2e
+    if plain:
+        line["plain_one_colony_per_launch"] = plain
+    if tune is not None:
+        line["autotune"] = {k: tune[k] for k in ("n_tried", "best_ms", "default_ms", "bucket")}
+    if serving:
+        line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(nq)
     print(json.dumps(line), flush=True)

@@ -4,9 +4,8 @@
  * The method is GMACO-P (Jindal & Bedi, "GMACO-P: GPU assisted Preemptive MACO algorithm for enabling
  * Smart Transportation"): ants build origin-to-destination routes over a road graph by choosing the next
  * road from pheromone and a congestion/signal-aware travel-time heuristic (Sec. 4.1, Fig. 3), successful
- * ants deposit pheromone and all roads evaporate (Fig. 3 last two lines; Algorithm 2 steps 9-10), and each
- * signalised intersection reorders its phases by the preemptive rule (Fig. 3 signal block; Algorithm 2
- * steps 7-8). Algorithm 1 (allocate, copy in, launch, copy out, free) is the host driver this API replaces
+ * ants deposit pheromone and all roads evaporate (Fig. 3; Algorithm 2), and each signalised
+ * intersection reorders its phases by the preemptive rule (Fig. 3 signal block; Algorithm 2). Algorithm 1 (allocate, copy in, launch, copy out, free) is the host driver this API replaces
  * with persistent device state: the graph, signals and densities stay resident between calls.
  *
  * Conventions for every entry point:
@@ -173,7 +172,8 @@ typedef struct {
  * times a probe job (the n probe queries with n_iter clamped to probe_iter, 0 = 8) under every schedule
  * the graph admits: lanes per ant 1/4/8/16/32, warp lockstep or free-running groups, the iterative or
  * the persistent job with queue chunks 8/16/32/64. Each is run once to warm up, then twice timed on
- * the context's stream; the fastest wins. The choice is cached for the process by bucket and written
+ * the context's stream (best of two); the untuned schedule is timed first and a schedule replaces the
+ * best so far only when it is at least 3% faster. The choice is cached for the process by bucket and written
  * into the context's parameters (lanes_per_ant, mode, queue_chunk, the lockstep flag); later calls in
  * the same bucket apply the cached choice without timing. Replaces any staged batch. Synchronous.
  * Errors: INVALID_ARG, STATE, UNSUPPORTED (no schedule ran), and those of gmp_batch_stage. */
@@ -303,8 +303,10 @@ int gmp_get_phase_order(gmp_ctx *ctx, uint8_t *out);
 /* Current congested travel time and queue delay per road (E entries each; either may be NULL). */
 int gmp_get_edge_times(gmp_ctx *ctx, uint32_t *tt_ms, uint32_t *qd_ms);
 
-/* Device time of the last launched job, in ms, per kernel family: out[0] construction, out[1] evaporation +
- * deposit, out[2] best-route tracking, out[3] queue/preemption, out[4] whole job. Needs the stream idle. */
+/* Device time of the last launched job (staged with the per-kernel timing flag), in ms: out[0] construction,
+ * out[1] iteration end (evaporation + deposit, best-route tracking and queue/preemption in one kernel),
+ * out[2] initialisation + result rows, out[3] 0, out[4] whole job. In the persistent job everything but
+ * initialisation and the result rows is one kernel, reported as out[0]. Needs the stream idle. */
 int gmp_get_kernel_times(gmp_ctx *ctx, float *out_ms5);
 
 /* Count of kernel launches issued by the last gmp_batch_launch. */

@@ -194,8 +194,8 @@ uint32_t orc_queue_delay_ms(uint32_t n, uint32_t h_sat_ms, uint32_t lanes, int h
 }
 
 /* ------------------------------------------------------------------------------------------------ */
-/* Preemptive signal rule (Fig. 3 signal block; Calc_Dens / Comp_Thres, Sec. 4.2 and Algorithm 2      */
-/* steps 7-8). Produces the order in which the phases receive green in the next cycle; green          */
+/* Preemptive signal rule (Fig. 3 signal block; Calc_Dens / Comp_Thres, Sec. 4.2 and Algorithm 2).    */
+/* Produces the order in which the phases receive green in the next cycle; green                      */
 /* durations stay as programmed.                                                                       */
 /* ------------------------------------------------------------------------------------------------ */
 void orc_phase_order(uint32_t n_phases, const uint64_t *Q, const uint64_t *Th, const uint32_t *red_ms,
@@ -346,7 +346,7 @@ uint32_t orc_heuristic_ms(int32_t x, int32_t y, int32_t xd, int32_t yd, uint64_t
 }
 
 /* ------------------------------------------------------------------------------------------------ */
-/* Next-node rule (Fig. 3 "select node"; Algorithm 2 step 5): roulette over tau^alpha * eta^beta.     */
+/* Next-node rule (Fig. 3 "select node"; Algorithm 2): roulette over tau^alpha * eta^beta.     */
 /* ------------------------------------------------------------------------------------------------ */
 static float pow_int(float x, uint32_t k)
 {
@@ -641,7 +641,7 @@ int orc_walk_one(const orc_net *g, const orc_params *prm, const orc_query *q, co
     return st;
 }
 
-/* Initial pheromone (Algorithm 2 step 3): 1.0 in Q32.32, or with the random flag
+/* Initial pheromone (Algorithm 2): 1.0 in Q32.32, or with the random flag
  * 0.5 + u/2^32 where u is word 0 of Philox(counter = (road, 0, 0, 1), key = seed). */
 void orc_init_tau(uint32_t E, uint64_t seed, uint32_t flags, uint64_t *tau)
 {

@@ -322,6 +322,39 @@ int record(gmp_ctx* c, Batch& b, size_t i) {
 
 ConstructArgs construct_args(gmp_ctx* c);
 
+// Arguments of the iteration-end kernel for a job's workspace (the context supplies the queue state).
+IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* tau, float* tauf,
+                          unsigned long long* dep, QueryState* qs, const uint32_t* routes, const uint32_t* ant_steps,
+                          const uint32_t* ant_wait, uint32_t* best_route, uint32_t max_steps) {
+    IterEndArgs e{};
+    e.n_queries = Q;
+    e.n_edges = c->E;
+    e.n_nodes = c->N;
+    e.max_steps = max_steps;
+    e.q = dq;
+    e.tau = tau;
+    e.tauf = tauf;
+    e.dep = dep;
+    e.qs = qs;
+    e.routes = routes;
+    e.ant_steps = ant_steps;
+    e.ant_wait = ant_wait;
+    e.best_route = best_route;
+    e.in_ptr = c->in_ptr;
+    e.in_edge = c->in_edge;
+    e.nph = c->nph;
+    e.cycle = c->cycle;
+    e.offset = c->offset;
+    e.green = c->green;
+    e.ephase = c->ephase;
+    e.veh = c->veh;
+    e.cap = c->cap;
+    e.red = c->red;
+    e.order = c->order;
+    e.rec = c->rec;
+    return e;
+}
+
 // The persistent job: init, one persistent launch, result rows.
 int enqueue_persistent(gmp_ctx* c) {
     Batch& b = c->b;
@@ -409,23 +442,19 @@ int enqueue_job(gmp_ctx* c) {
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
     const ConstructArgs a = construct_args(c);
+    IterEndArgs e = iter_end_args(c, b.Q, b.dq, b.tau, b.tauf, b.dep, b.qs, b.routes, b.ant_steps, b.ant_wait,
+                                  b.best_route, b.max_steps);
     for (uint32_t it = 0; it < b.maxI; ++it) {
         GMP_CUDA(c, launch_construct(s, b.kc, a, it));
-        if (timed) GMP_TRY(record(c, b, 2 + 4 * (size_t)it));
-        GMP_CUDA(c, launch_evaporate(s, b.Q, c->E, b.dq, b.tau, b.tauf, b.dep, it));
-        if (timed) GMP_TRY(record(c, b, 3 + 4 * (size_t)it));
-        GMP_CUDA(c, launch_best_copy(s, b.Q, b.dq, b.qs, b.routes, b.ant_steps, b.ant_wait, b.best_route,
-                                     b.max_steps, it));
-        if (timed) GMP_TRY(record(c, b, 4 + 4 * (size_t)it));
-        // per-iteration queue/preemption update (densities are fixed during a job: same order again)
-        GMP_CUDA(c, launch_queue_preempt(s, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
-                                         c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
-        if (timed) GMP_TRY(record(c, b, 5 + 4 * (size_t)it));
-        n += 4;
+        if (timed) GMP_TRY(record(c, b, 2 + 2 * (size_t)it));
+        e.it = it;
+        GMP_CUDA(c, launch_iter_end(s, e));
+        if (timed) GMP_TRY(record(c, b, 3 + 2 * (size_t)it));
+        n += 2;
     }
     GMP_CUDA(c, launch_finalize(s, b.Q, b.dq, b.qs, b.best_route, c->col, b.max_steps, b.res, b.route_out));
     ++n;
-    if (timed) GMP_TRY(record(c, b, 2 + 4 * (size_t)b.maxI));
+    if (timed) GMP_TRY(record(c, b, 2 + 2 * (size_t)b.maxI));
     b.launches = n;
     return GMP_OK;
 }
@@ -843,7 +872,7 @@ int gmp_batch_launch(gmp_ctx* c) {
     if (!b.staged) return fail(c, GMP_ERR_STATE, "stage a batch first");
     cudaSetDevice(c->device);
     const bool timed = (c->prm.flags & kFlagKernelTiming) != 0;
-    const size_t n_ev = timed ? (b.persistent ? 4 : 3 + 4 * (size_t)b.maxI) : 0;
+    const size_t n_ev = timed ? (b.persistent ? 4 : 3 + 2 * (size_t)b.maxI) : 0;
     if (b.ev.size() != n_ev || b.timed != timed) {
         drop_graph(b);
         drop_events(b);
@@ -1031,13 +1060,17 @@ int gmp_get_kernel_times(gmp_ctx* c, float* out) {
         return GMP_OK;
     }
     for (uint32_t it = 0; it < b.maxI; ++it) {
-        const size_t prev = it == 0 ? 1 : 1 + 4 * (size_t)it;
-        for (int k = 0; k < 4; ++k) {
+        const size_t prev = 1 + 2 * (size_t)it;
+        for (int k = 0; k < 2; ++k) {
             GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[prev + k], b.ev[prev + k + 1]));
             out[k] += ms;
         }
     }
-    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[2 + 4 * (size_t)b.maxI]));
+    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
+    out[2] = ms;
+    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[1 + 2 * (size_t)b.maxI], b.ev[2 + 2 * (size_t)b.maxI]));
+    out[2] += ms;
+    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[2 + 2 * (size_t)b.maxI]));
     out[4] = ms;
     return GMP_OK;
 }
@@ -1192,12 +1225,11 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     a.thr_on = c->prm.thr_permille != kThrOff;
     a.tabu_in_smem = kc.tabu_in_smem ? 1u : 0u;
     a.kappa = c->kappa;
+    IterEndArgs e = iter_end_args(c, 1, dq, tau, tauf, dep, qs, routes, ant_steps, ant_wait, best_route, S);
     for (uint32_t it = 0; it < n_iter; ++it) {
         GMP_CUDA(c, launch_construct(s, kc, a, it));
-        GMP_CUDA(c, launch_evaporate(s, 1, c->E, dq, tau, tauf, dep, it));
-        GMP_CUDA(c, launch_best_copy(s, 1, dq, qs, routes, ant_steps, ant_wait, best_route, S, it));
-        GMP_CUDA(c, launch_queue_preempt(s, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
-                                         c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
+        e.it = it;
+        GMP_CUDA(c, launch_iter_end(s, e));
     }
     GMP_CUDA(c, launch_finalize(s, 1, dq, qs, best_route, c->col, S, reinterpret_cast<DevResult*>(d_result), d_route));
     return GMP_OK;

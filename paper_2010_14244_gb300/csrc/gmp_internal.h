@@ -35,6 +35,26 @@ struct ConstructArgs {
     uint32_t kappa;              // floor(360 * 2^16 / v_max)
 };
 
+// Arguments of the fused iteration-end kernel (evaporation + deposits, best route, queue update).
+struct IterEndArgs {
+    uint32_t n_queries, n_edges, n_nodes, it, max_steps;
+    uint32_t evap_blocks;  // blocks per colony for the evaporation (set by the launcher)
+    const DevQuery* q;
+    uint64_t* tau;
+    float* tauf;
+    unsigned long long* dep;
+    QueryState* qs;
+    const uint32_t *routes, *ant_steps, *ant_wait;
+    uint32_t* best_route;
+    const uint32_t *in_ptr, *in_edge;
+    const uint8_t* nph;
+    const uint32_t *cycle, *offset, *green;
+    const uint8_t* ephase;
+    const uint32_t *veh, *cap, *red;
+    uint8_t* order;
+    EdgeRec* rec;
+};
+
 // Per-(colony, iteration) counters of the persistent job.
 struct __align__(16) IterCounters {
     uint32_t ant_claim, ant_done;       // ants handed out / finished
@@ -95,11 +115,7 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               float* tauf, unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
-cudaError_t launch_evaporate(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, uint64_t* tau,
-                             float* tauf, unsigned long long* dep, uint32_t it);
-cudaError_t launch_best_copy(cudaStream_t s, uint32_t Q, const DevQuery* q, QueryState* qs, const uint32_t* routes,
-                             const uint32_t* ant_steps, const uint32_t* ant_wait, uint32_t* best_route,
-                             uint32_t max_steps, uint32_t it);
+cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& a);
 cudaError_t launch_finalize(cudaStream_t s, uint32_t Q, const DevQuery* q, const QueryState* qs,
                             const uint32_t* best_route, const uint32_t* col, uint32_t max_steps, DevResult* res,
                             uint32_t* route_out);

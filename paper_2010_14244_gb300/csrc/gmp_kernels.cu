@@ -3,10 +3,10 @@
 //   k_edge_static     road free-flow time and jam capacity                         (graph load)
 //   k_edge_dynamic    congested travel time, queue delay, threshold flag per road   (Calc_Dens inputs)
 //   k_queue_preempt   per-intersection phase order by the preemptive rule         (Calc_Dens, Comp_Thres)
-//   k_init_batch      initial pheromone, per-colony state                          (Algorithm 2 step 3)
+//   k_init_batch      initial pheromone, per-colony state                          (Algorithm 2)       
 //   k_construct<G,K>  ant walks: Adj_Neigh, next-node roulette, Eval_Rout, position update, deposits
-//   k_evaporate       Evap_Pher fused with the deposits of Updt_Pher
-//   k_best_copy       best-route tracking
+//   k_iter_end        Evap_Pher fused with the deposits of Updt_Pher, best-route tracking and the
+//                     per-iteration queue/preemption update, in one launch
 //   k_finalize        best route as node ids + counters
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -679,45 +679,76 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
 // ------------------------------------------------------------------------------------------------
 // Evap_Pher + Updt_Pher: tau <- tau - floor(tau * rho_fix / 2^32) + D ; D <- 0.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_evaporate(uint32_t E, const DevQuery* __restrict__ q, uint64_t* __restrict__ tau,
-                            float* __restrict__ tauf, unsigned long long* __restrict__ dep, uint32_t it) {
-    const uint32_t qi = blockIdx.y;
-    const uint32_t active = q[qi].active, n_iter = q[qi].n_iter;
-    if (!active || it >= n_iter) return;
-    const uint64_t rf = q[qi].rho_fix;
-    uint64_t* T = tau + (size_t)qi * E;
-    float* TF = tauf + (size_t)qi * E;
-    unsigned long long* D = dep + (size_t)qi * E;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        const uint64_t t = T[e];
-        const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
-        const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + D[e];
-        T[e] = nt;
-        TF[e] = tau_float(nt);
-        D[e] = 0;
-    }
-}
+// Iteration end, one launch for three independent pieces of work (all read what the construction
+// kernel wrote, none reads what another writes):
+//   Evap_Pher + Updt_Pher  tau <- tau - floor(tau * rho_fix / 2^32) + D, D <- 0, per (colony, road);
+//   best-route tracking    when a colony's best key came from this iteration, keep that ant's route;
+//   Calc_Dens / Comp_Thres the per-intersection phase order (densities are fixed within a job, so the
+//                          update reproduces the same order; it runs because the iteration calls it).
+// Blocks [0, nev) evaporate kEvapPer roads per thread with every load issued first; the next Q blocks
+// copy best routes; the rest update intersections.
+constexpr uint32_t kEvapPer = 4;
+constexpr uint32_t kIterEndBlock = 256;
 
-// Best-route tracking: when the colony's best key came from this iteration, keep that ant's route.
-__global__ void k_best_copy(const DevQuery* __restrict__ q, QueryState* __restrict__ qs,
-                            const uint32_t* __restrict__ routes, const uint32_t* __restrict__ ant_steps,
-                            const uint32_t* __restrict__ ant_wait, uint32_t* __restrict__ best_route,
-                            uint32_t max_steps, uint32_t it) {
-    const uint32_t qi = blockIdx.x;
-    const DevQuery Q = q[qi];
-    if (!Q.active || it >= Q.n_iter) return;
-    const unsigned long long key = qs[qi].best_key;
-    if (key == kNoKey) return;
-    const uint32_t low = (uint32_t)key;
-    if (low / Q.n_ants != it) return;
-    const uint32_t slot = Q.ant_base + low % Q.n_ants;
-    const uint32_t len = ant_steps[slot];
-    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
-        best_route[(size_t)qi * max_steps + i] = routes[(size_t)slot * max_steps + i];
-    if (threadIdx.x == 0) {
-        qs[qi].best_len = len;
-        qs[qi].best_W = ant_wait[slot];
+__global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
+    uint32_t b = blockIdx.x;
+    const uint32_t nev = a.n_queries * a.evap_blocks;
+    if (b < nev) {
+        const uint32_t qi = b / a.evap_blocks, chunk = b - qi * a.evap_blocks;
+        const DevQuery& Q = a.q[qi];
+        if (!Q.active || a.it >= Q.n_iter) return;
+        const uint64_t rf = Q.rho_fix;
+        const size_t off = (size_t)qi * a.n_edges;
+        uint64_t* T = a.tau + off;
+        float* TF = a.tauf + off;
+        unsigned long long* D = a.dep + off;
+        const uint32_t e0 = chunk * kIterEndBlock * kEvapPer + threadIdx.x;
+        uint64_t tv[kEvapPer];
+        unsigned long long dv[kEvapPer];
+#pragma unroll
+        for (uint32_t i = 0; i < kEvapPer; ++i) {
+            const uint32_t e = e0 + i * kIterEndBlock;
+            tv[i] = e < a.n_edges ? T[e] : 0;
+            dv[i] = e < a.n_edges ? D[e] : 0;
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kEvapPer; ++i) {
+            const uint32_t e = e0 + i * kIterEndBlock;
+            if (e < a.n_edges) {
+                const uint64_t t = tv[i];
+                const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
+                const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + dv[i];
+                T[e] = nt;
+                TF[e] = tau_float(nt);
+                D[e] = 0;
+            }
+        }
+        return;
     }
+    b -= nev;
+    if (b < a.n_queries) {
+        const uint32_t qi = b;
+        const DevQuery Q = a.q[qi];
+        if (!Q.active || a.it >= Q.n_iter) return;
+        const unsigned long long key = a.qs[qi].best_key;
+        if (key == kNoKey) return;
+        const uint32_t low = (uint32_t)key;
+        if (low / Q.n_ants != a.it) return;
+        const uint32_t slot = Q.ant_base + low % Q.n_ants;
+        const uint32_t len = a.ant_steps[slot];
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+            a.best_route[(size_t)qi * a.max_steps + i] = a.routes[(size_t)slot * a.max_steps + i];
+        if (threadIdx.x == 0) {
+            a.qs[qi].best_len = len;
+            a.qs[qi].best_W = a.ant_wait[slot];
+        }
+        return;
+    }
+    b -= a.n_queries;
+    const uint32_t v = b * blockDim.x + threadIdx.x;
+    if (v < a.n_nodes)
+        queue_node(v, a.in_ptr, a.in_edge, a.nph, a.cycle, a.offset, a.green, a.ephase, a.veh, a.cap, a.red,
+                   a.order, a.rec);
 }
 
 __global__ void k_finalize(const DevQuery* __restrict__ q, const QueryState* __restrict__ qs,
@@ -798,18 +829,13 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
     return cudaGetLastError();
 }
 
-cudaError_t launch_evaporate(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, uint64_t* tau,
-                             float* tauf, unsigned long long* dep, uint32_t it) {
-    if (E == 0) return cudaSuccess;
-    dim3 grid(blocks_for(E, 1024), Q);
-    k_evaporate<<<grid, 256, 0, s>>>(E, q, tau, tauf, dep, it);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_best_copy(cudaStream_t s, uint32_t Q, const DevQuery* q, QueryState* qs, const uint32_t* routes,
-                             const uint32_t* ant_steps, const uint32_t* ant_wait, uint32_t* best_route,
-                             uint32_t max_steps, uint32_t it) {
-    k_best_copy<<<Q, 128, 0, s>>>(q, qs, routes, ant_steps, ant_wait, best_route, max_steps, it);
+cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& args) {
+    IterEndArgs a = args;
+    a.evap_blocks = (a.n_edges + kIterEndBlock * kEvapPer - 1) / (kIterEndBlock * kEvapPer);
+    const uint64_t blocks = (uint64_t)a.n_queries * a.evap_blocks + a.n_queries +
+                            (a.n_nodes + kIterEndBlock - 1) / kIterEndBlock;
+    if (blocks == 0) return cudaSuccess;
+    k_iter_end<<<(uint32_t)blocks, kIterEndBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 

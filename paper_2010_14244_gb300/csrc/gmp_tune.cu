@@ -29,6 +29,8 @@ struct Schedule {
 
 using Bucket = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
 
+constexpr float kMargin = 0.03f;  // relative speed-up a schedule needs over the best so far
+
 std::mutex g_mu;
 std::map<Bucket, Schedule> g_cache;
 
@@ -154,7 +156,9 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
         if (ms < 0.0f) continue;
         ++out->n_tried;
         if (i == 0) out->default_ms = ms;
-        if (best_ms < 0.0f || ms < best_ms) {
+        // a schedule must beat the best so far by kMargin to replace it: the default (timed first)
+        // stays unless something is clearly faster, so timing noise does not flip the choice
+        if (best_ms < 0.0f || ms < best_ms * (1.0f - kMargin)) {
             best_ms = ms;
             best = cand[i];
         }

@@ -338,7 +338,7 @@ class Context:
     def kernel_times(self) -> dict:
         out = np.zeros(5, np.float32)
         self._check(lib().gmp_get_kernel_times(self._h, _p(out)))
-        return dict(construct=float(out[0]), evaporate=float(out[1]), best=float(out[2]), queue=float(out[3]),
+        return dict(construct=float(out[0]), iter_end=float(out[1]), init_finalize=float(out[2]),
                     job=float(out[4]))
 
     def launch_count(self) -> int:
