@@ -61,6 +61,8 @@ typedef struct {
     uint32_t mode;          /* GMP_MODE_* */
     uint32_t queue_chunk;   /* persistent mode: intersections per queue-update work item; 0 (= 16), 8, 16,
                                32 or 64 */
+    uint32_t branches;      /* iterative mode: the colonies are split into this many contiguous ranges that
+                               run as concurrent chains of launches; 0 = min(colonies, 16), at most 64 */
 } gmp_params;
 
 /* One origin-destination colony. alpha, beta: integers in [0, 8]; rho in [0, 1). */
@@ -160,6 +162,7 @@ typedef struct {
     uint32_t mode;          /* GMP_MODE_ITERATIVE or GMP_MODE_PERSISTENT */
     uint32_t queue_chunk;   /* persistent mode: intersections per queue-update work item; 0 otherwise */
     uint32_t lockstep;      /* 1 when the ants of a warp step together (iterative mode) */
+    uint32_t branches;      /* iterative mode: concurrent colony chains (0 = the default) */
     uint32_t from_cache;    /* 1 when this size bucket was tuned earlier in the process: nothing was timed */
     uint32_t n_tried;       /* schedules timed */
     float best_ms;          /* probe job time of the chosen schedule (0 from the cache) */
@@ -171,10 +174,11 @@ typedef struct {
  * schedules give the same results bit for bit, so only speed differs. The first call for a size bucket
  * times a probe job (the n probe queries with n_iter clamped to probe_iter, 0 = 8) under every schedule
  * the graph admits: lanes per ant 1/4/8/16/32, warp lockstep or free-running groups, the iterative or
- * the persistent job with queue chunks 8/16/32/64. Each is run once to warm up, then twice timed on
+ * the persistent job with queue chunks 8/16/32/64, and then, for the best iterative schedule, 1, 4, 32 or
+ * 64 concurrent colony chains instead of the default. Each is run once to warm up, then twice timed on
  * the context's stream (best of two); the untuned schedule is timed first and a schedule replaces the
  * best so far only when it is at least 3% faster. The choice is cached for the process by bucket and written
- * into the context's parameters (lanes_per_ant, mode, queue_chunk, the lockstep flag); later calls in
+ * into the context's parameters (lanes_per_ant, mode, queue_chunk, branches, the lockstep flag); later calls in
  * the same bucket apply the cached choice without timing. Replaces any staged batch. Synchronous.
  * Errors: INVALID_ARG, STATE, UNSUPPORTED (no schedule ran), and those of gmp_batch_stage. */
 int gmp_autotune(gmp_ctx *ctx, uint32_t n, const gmp_query *probe, uint32_t probe_iter, gmp_tune_result *out);
@@ -305,8 +309,9 @@ int gmp_get_edge_times(gmp_ctx *ctx, uint32_t *tt_ms, uint32_t *qd_ms);
 
 /* Device time of the last launched job (staged with the per-kernel timing flag), in ms: out[0] construction,
  * out[1] iteration end (evaporation + deposit, best-route tracking and queue/preemption in one kernel),
- * out[2] initialisation + result rows, out[3] 0, out[4] whole job. In the persistent job everything but
- * initialisation and the result rows is one kernel, reported as out[0]. Needs the stream idle. */
+ * both summed over the concurrent colony chains (which overlap in time), out[2] initialisation + result
+ * rows, out[3] 0, out[4] whole job. In the persistent job everything but initialisation and the result
+ * rows is one kernel, reported as out[0]. Needs the stream idle. */
 int gmp_get_kernel_times(gmp_ctx *ctx, float *out_ms5);
 
 /* Count of kernel launches issued by the last gmp_batch_launch. */

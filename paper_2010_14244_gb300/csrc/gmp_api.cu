@@ -30,11 +30,13 @@ constexpr uint32_t kKnownFlags =
     GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
 constexpr int32_t kCoordLimit = 1 << 27;
 constexpr uint64_t kTickClockMax = 1ull << 48;  // lanes * (t + dt) stays below 2^64
+constexpr uint32_t kDefaultBranches = 16;        // concurrent colony chains of an iterative job
+constexpr uint32_t kMaxBranches = 64;
 constexpr uint32_t kTickDtMax = 1u << 30;
 
 struct BatchKey {
     uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0,
-             chunk = 0;
+             chunk = 0, branches = 0, pad = 0;
     uint64_t log_entries = 0;
     const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
@@ -76,7 +78,28 @@ struct Batch {
     std::vector<cudaEvent_t> ev;
     bool timed = false;
     cudaEvent_t done = nullptr;  // recorded after every launch (gmp_batch_ready)
+    // iterative job: contiguous colony ranges run as concurrent chains of launches
+    struct Branch {
+        uint32_t q0, q1, ants, ticket_base, maxI;
+        KernelConfig kc;
+        size_t tabu_off;  // words into the global visited-bitmap pool
+    };
+    std::vector<Branch> br;
+    std::vector<Branch> exec_br;  // the chain plan baked into `exec`
 };
+
+bool same_plan(const std::vector<Batch::Branch>& x, const std::vector<Batch::Branch>& y) {
+    if (x.size() != y.size()) return false;
+    for (size_t i = 0; i < x.size(); ++i) {
+        const Batch::Branch &a = x[i], &b = y[i];
+        if (a.q0 != b.q0 || a.q1 != b.q1 || a.ants != b.ants || a.ticket_base != b.ticket_base || a.maxI != b.maxI ||
+            a.tabu_off != b.tabu_off || a.kc.grid != b.kc.grid || a.kc.block != b.kc.block ||
+            a.kc.lanes != b.kc.lanes || a.kc.slots != b.kc.slots || a.kc.smem != b.kc.smem ||
+            a.kc.tabu_in_smem != b.kc.tabu_in_smem || a.kc.lockstep != b.kc.lockstep)
+            return false;
+    }
+    return true;
+}
 
 }  // namespace
 
@@ -102,6 +125,9 @@ struct gmp_ctx {
     unsigned long long* tick_K = nullptr;  // serving tick: discharge of each node (N)
     std::vector<int32_t> hx, hy;  // host copy of node coordinates (destination lookups at staging)
     Batch b;
+    std::vector<cudaStream_t> bstreams;  // streams of the concurrent colony chains
+    std::vector<cudaEvent_t> bjoin;      // one join event per chain
+    cudaEvent_t bfork = nullptr;
 };
 
 namespace gmp {
@@ -430,31 +456,96 @@ ConstructArgs construct_args(gmp_ctx* c) {
 }
 
 // Issue the whole job on the stream (inside a capture or directly).
+// Per-kernel timing events of the iterative job: [0] start, [1] after init, [2] after the chains join,
+// [3] after the result rows; then per chain its start and, per iteration, after construction and after
+// the iteration end.
+size_t branch_event_base(const Batch& b, size_t j) {
+    size_t base = 4;
+    for (size_t i = 0; i < j; ++i) base += 1 + 2 * (size_t)b.br[i].maxI;
+    return base;
+}
+
+size_t job_event_count(const Batch& b) {
+    if (b.persistent) return 4;
+    return branch_event_base(b, b.br.size());
+}
+
+int ensure_branch_streams(gmp_ctx* c, size_t n) {
+    if (!c->bfork) GMP_CUDA(c, cudaEventCreateWithFlags(&c->bfork, cudaEventDisableTiming));
+    while (c->bstreams.size() < n) {
+        cudaStream_t st = nullptr;
+        GMP_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        c->bstreams.push_back(st);
+        cudaEvent_t e = nullptr;
+        GMP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->bjoin.push_back(e);
+    }
+    return GMP_OK;
+}
+
+// Issue the whole job on the stream (inside a capture or directly). Colony ranges run as concurrent
+// chains (fork from the context's stream after init, join before the result rows): a chain moves on to
+// its next iteration as soon as its own colonies finish, so the job takes as long as its slowest chain
+// instead of the sum over iterations of the slowest ant of any colony.
 int enqueue_job(gmp_ctx* c) {
     Batch& b = c->b;
     if (b.persistent) return enqueue_persistent(c);
     cudaStream_t s = c->stream;
     const bool timed = b.timed;
+    const size_t B = b.br.size();
     uint64_t n = 0;
     if (timed) GMP_TRY(record(c, b, 0));
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.tauf,
-                                  b.dep, b.heur, b.qs, b.tickets, b.maxI));
+                                  b.dep, b.heur, b.qs, b.tickets, b.maxI * (uint32_t)B));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
-    const ConstructArgs a = construct_args(c);
-    IterEndArgs e = iter_end_args(c, b.Q, b.dq, b.tau, b.tauf, b.dep, b.qs, b.routes, b.ant_steps, b.ant_wait,
-                                  b.best_route, b.max_steps);
-    for (uint32_t it = 0; it < b.maxI; ++it) {
-        GMP_CUDA(c, launch_construct(s, b.kc, a, it));
-        if (timed) GMP_TRY(record(c, b, 2 + 2 * (size_t)it));
-        e.it = it;
-        GMP_CUDA(c, launch_iter_end(s, e));
-        if (timed) GMP_TRY(record(c, b, 3 + 2 * (size_t)it));
-        n += 2;
+    if (B > 1) {
+        GMP_TRY(ensure_branch_streams(c, B));
+        GMP_CUDA(c, cudaEventRecord(c->bfork, s));
     }
+    const ConstructArgs base = construct_args(c);
+    for (size_t j = 0; j < B; ++j) {
+        const Batch::Branch& r = b.br[j];
+        cudaStream_t bs = B > 1 ? c->bstreams[j] : s;
+        if (B > 1) GMP_CUDA(c, cudaStreamWaitEvent(bs, c->bfork, 0));
+        const size_t eb = branch_event_base(b, j);
+        if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb], bs, cudaEventRecordExternal));
+        ConstructArgs a = base;
+        const size_t co = (size_t)r.q0 * c->E;
+        a.queries = b.dq + r.q0;
+        a.ant_prefix = b.prefix + r.q0;
+        a.tau = b.tau + co;
+        a.tauf = b.tauf + co;
+        a.hq = b.heur + co;
+        a.dep = b.dep + co;
+        a.qs = b.qs + r.q0;
+        a.tickets = b.tickets + (size_t)j * b.maxI;
+        a.tabu_global = b.tabu ? b.tabu + r.tabu_off : nullptr;
+        a.n_queries = r.q1 - r.q0;
+        a.total_ants = r.ants;
+        a.ticket_base = r.ticket_base;
+        a.tabu_in_smem = r.kc.tabu_in_smem ? 1u : 0u;
+        IterEndArgs e = iter_end_args(c, r.q1 - r.q0, b.dq + r.q0, b.tau + co, b.tauf + co, b.dep + co, b.qs + r.q0,
+                                      b.routes, b.ant_steps, b.ant_wait, b.best_route + (size_t)r.q0 * b.max_steps,
+                                      b.max_steps);
+        if (j > 0) e.n_nodes = 0;  // the queue update of an iteration runs once, in the first chain
+        for (uint32_t it = 0; it < r.maxI; ++it) {
+            GMP_CUDA(c, launch_construct(bs, r.kc, a, it));
+            if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 1 + 2 * it], bs, cudaEventRecordExternal));
+            e.it = it;
+            GMP_CUDA(c, launch_iter_end(bs, e));
+            if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 2 + 2 * it], bs, cudaEventRecordExternal));
+            n += 2;
+        }
+        if (B > 1) {
+            GMP_CUDA(c, cudaEventRecord(c->bjoin[j], bs));
+            GMP_CUDA(c, cudaStreamWaitEvent(s, c->bjoin[j], 0));
+        }
+    }
+    if (timed) GMP_TRY(record(c, b, 2));
     GMP_CUDA(c, launch_finalize(s, b.Q, b.dq, b.qs, b.best_route, c->col, b.max_steps, b.res, b.route_out));
     ++n;
-    if (timed) GMP_TRY(record(c, b, 2 + 2 * (size_t)b.maxI));
+    if (timed) GMP_TRY(record(c, b, 3));
     b.launches = n;
     return GMP_OK;
 }
@@ -464,6 +555,7 @@ BatchKey key_of(const gmp_ctx* c) {
     BatchKey k{};
     k.Q = b.Q;
     k.chunk = c->prm.queue_chunk;
+    k.branches = (uint32_t)b.br.size();
     k.maxI = b.maxI;
     k.total_ants = b.total_ants;
     k.max_steps = b.max_steps;
@@ -533,6 +625,9 @@ void gmp_destroy(gmp_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     free_graph(c);
+    for (cudaStream_t st : c->bstreams) cudaStreamDestroy(st);
+    for (cudaEvent_t e : c->bjoin) cudaEventDestroy(e);
+    if (c->bfork) cudaEventDestroy(c->bfork);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -704,6 +799,7 @@ int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
     if (p->mode > GMP_MODE_PERSISTENT) return fail(c, GMP_ERR_INVALID_ARG, "unknown mode");
     if (p->queue_chunk && p->queue_chunk != 8 && p->queue_chunk != 16 && p->queue_chunk != 32 && p->queue_chunk != 64)
         return fail(c, GMP_ERR_INVALID_ARG, "queue_chunk must be 0, 8, 16, 32 or 64");
+    if (p->branches > kMaxBranches) return fail(c, GMP_ERR_INVALID_ARG, "branches must be at most 64");
     if (p->max_steps > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "max_steps must be <= 2^24");
     const bool dyn = p->thr_permille != c->prm.thr_permille || p->h_sat_ms != c->prm.h_sat_ms;
     c->prm = *p;
@@ -722,6 +818,13 @@ int gmp_get_params(const gmp_ctx* c, gmp_params* p) {
 }
 
 namespace {
+
+// Concurrent colony chains of an iterative job with n colonies: params.branches (0 = up to 16).
+uint32_t branch_count(const gmp_ctx* c, uint32_t n) {
+    if (c->prm.mode == GMP_MODE_PERSISTENT || n == 0) return 1;
+    const uint32_t want = c->prm.branches ? c->prm.branches : kDefaultBranches;
+    return std::max<uint32_t>(1u, std::min(n, want));
+}
 
 // Launch shape of the job for the context's parameters and `total_ants` ants per iteration.
 int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc) {
@@ -760,7 +863,7 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
     GMP_TRY(ensure(c, &b.ant_wait, (size_t)total_ants));
     GMP_TRY(ensure(c, &b.best_route, (size_t)n * max_steps));
     GMP_TRY(ensure(c, &b.route_out, (size_t)n * (max_steps + 1)));
-    GMP_TRY(ensure(c, &b.tickets, maxI));
+    GMP_TRY(ensure(c, &b.tickets, (size_t)maxI * branch_count(c, n)));
     GMP_TRY(ensure(c, &b.res, n));
     if (persistent) {
         GMP_TRY(ensure(c, &b.ctr, (size_t)n * maxI));
@@ -769,7 +872,41 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
         GMP_TRY(ensure(c, &b.misc, 2));
     }
     if (log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)log_entries * 4));
-    if (!kc.tabu_in_smem) GMP_TRY(ensure(c, &b.tabu, (size_t)kc.grid * (kc.block / kc.lanes) * words));
+    // visited bitmaps in global memory: the job's grid plus one block per concurrent chain (chain grids
+    // are shares of the job's grid, rounded up)
+    if (!kc.tabu_in_smem)
+        GMP_TRY(ensure(c, &b.tabu, ((size_t)kc.grid + branch_count(c, n)) * (kc.block / kc.lanes) * words));
+    return GMP_OK;
+}
+
+// Split the staged job into concurrent chains of contiguous colonies. Each chain's construction grid is
+// its own need, capped at its share (by ants) of the whole job's grid.
+int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
+    Batch& b = c->b;
+    b.br.clear();
+    if (b.persistent) return GMP_OK;
+    const uint32_t B = branch_count(c, b.Q);
+    const size_t words = (c->N + 31u) / 32u;
+    size_t off = 0;
+    for (uint32_t j = 0; j < B; ++j) {
+        Batch::Branch r{};
+        r.q0 = (uint32_t)((uint64_t)b.Q * j / B);
+        r.q1 = (uint32_t)((uint64_t)b.Q * (j + 1) / B);
+        r.ticket_base = prefix[r.q0];
+        r.ants = prefix[r.q1] - prefix[r.q0];
+        r.maxI = 0;
+        for (uint32_t i = r.q0; i < r.q1; ++i) r.maxI = std::max(r.maxI, b.hq[i].n_iter);
+        if (B == 1) {
+            r.kc = b.kc;
+        } else {
+            GMP_TRY(job_config(c, lanes, std::max<uint32_t>(r.ants, 1u), &r.kc));
+            const uint64_t share = ((uint64_t)b.kc.grid * r.ants + b.total_ants - 1) / std::max<uint32_t>(b.total_ants, 1u);
+            r.kc.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)r.kc.grid, share));
+        }
+        r.tabu_off = off;
+        if (!r.kc.tabu_in_smem) off += (size_t)r.kc.grid * (r.kc.block / r.kc.lanes) * words;
+        b.br.push_back(r);
+    }
     return GMP_OK;
 }
 
@@ -857,6 +994,7 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
     b.persistent = c->prm.mode == GMP_MODE_PERSISTENT;
     GMP_TRY(job_config(c, lanes, b.total_ants, &b.kc));
+    GMP_TRY(plan_branches(c, lanes, prefix));
     GMP_TRY(reserve_workspace(c, n, b.total_ants, maxI, b.log_entries, b.kc));
     GMP_TRY(upload(c, b.dq, hdq.data(), n));
     GMP_TRY(upload(c, b.prefix, prefix.data(), n + 1));
@@ -872,7 +1010,7 @@ int gmp_batch_launch(gmp_ctx* c) {
     if (!b.staged) return fail(c, GMP_ERR_STATE, "stage a batch first");
     cudaSetDevice(c->device);
     const bool timed = (c->prm.flags & kFlagKernelTiming) != 0;
-    const size_t n_ev = timed ? (b.persistent ? 4 : 3 + 2 * (size_t)b.maxI) : 0;
+    const size_t n_ev = timed ? job_event_count(b) : 0;
     if (b.ev.size() != n_ev || b.timed != timed) {
         drop_graph(b);
         drop_events(b);
@@ -884,7 +1022,7 @@ int gmp_batch_launch(gmp_ctx* c) {
         GMP_TRY(enqueue_job(c));
     } else {
         const BatchKey k = key_of(c);
-        if (!b.exec || !(b.key == k)) {
+        if (!b.exec || !(b.key == k) || !same_plan(b.br, b.exec_br)) {
             drop_graph(b);
             cudaGraph_t g = nullptr;
             GMP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -899,6 +1037,7 @@ int gmp_batch_launch(gmp_ctx* c) {
             cudaGraphDestroy(g);
             GMP_CUDA(c, ie);
             b.key = k;
+            b.exec_br = b.br;
         }
         GMP_CUDA(c, cudaGraphLaunch(b.exec, c->stream));
     }
@@ -1059,18 +1198,21 @@ int gmp_get_kernel_times(gmp_ctx* c, float* out) {
         out[4] = ms;
         return GMP_OK;
     }
-    for (uint32_t it = 0; it < b.maxI; ++it) {
-        const size_t prev = 1 + 2 * (size_t)it;
-        for (int k = 0; k < 2; ++k) {
-            GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[prev + k], b.ev[prev + k + 1]));
-            out[k] += ms;
+    for (size_t j = 0; j < b.br.size(); ++j) {  // summed over chains (concurrent chains overlap)
+        const size_t eb = branch_event_base(b, j);
+        for (uint32_t it = 0; it < b.br[j].maxI; ++it) {
+            const size_t prev = eb + 2 * (size_t)it;
+            for (int k = 0; k < 2; ++k) {
+                GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[prev + k], b.ev[prev + k + 1]));
+                out[k] += ms;
+            }
         }
     }
     GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[1]));
     out[2] = ms;
-    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[1 + 2 * (size_t)b.maxI], b.ev[2 + 2 * (size_t)b.maxI]));
+    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[2], b.ev[3]));
     out[2] += ms;
-    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[2 + 2 * (size_t)b.maxI]));
+    GMP_CUDA(c, cudaEventElapsedTime(&ms, b.ev[0], b.ev[3]));
     out[4] = ms;
     return GMP_OK;
 }

@@ -33,6 +33,9 @@ struct ConstructArgs {
     uint32_t n_queries, total_ants, n_edges, max_steps;
     uint32_t tabu_words, t_dep, thr_on, tabu_in_smem;
     uint32_t kappa;              // floor(360 * 2^16 / v_max)
+    uint32_t ticket_base;        // job-wide index of this launch's first ant (its colonies are a
+                                 // contiguous range: queries, ant_prefix and the per-colony tables
+                                 // point at the range's first colony)
 };
 
 // Arguments of the fused iteration-end kernel (evaporation + deposits, best route, queue update).

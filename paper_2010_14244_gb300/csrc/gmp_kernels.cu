@@ -206,15 +206,16 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
         if (lane == 0) ticket = atomicAdd(a.tickets + it, 1u);
         ticket = __shfl_sync(gmask, ticket, 0, G);
         if (ticket >= a.total_ants) break;
-        uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= ticket < ant_prefix[q + 1]
+        const uint32_t tg = a.ticket_base + ticket;  // the ant's index in the whole job
+        uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tg < ant_prefix[q + 1]
         while (hi - lo > 1u) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(a.ant_prefix + mid) <= ticket) lo = mid;
+            if (__ldg(a.ant_prefix + mid) <= tg) lo = mid;
             else hi = mid;
         }
         const DevQuery q = a.queries[lo];
         if (!q.active || it >= q.n_iter) continue;
-        walk_ant<G, K>(a, q, lo, ticket - q.ant_base, it, tabu, lane, gmask, gbase);
+        walk_ant<G, K>(a, q, lo, tg - q.ant_base, it, tabu, lane, gmask, gbase);
     }
 }
 
@@ -263,18 +264,19 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 if (tk >= a.total_ants) {
                     exhausted = true;
                 } else {
-                    uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tk < ant_prefix[q + 1]
+                    const uint32_t tg = a.ticket_base + tk;  // the ant's index in the whole job
+                    uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tg < ant_prefix[q + 1]
                     while (hi - lo > 1u) {
                         const uint32_t mid = (lo + hi) >> 1;
-                        if (__ldg(a.ant_prefix + mid) <= tk) lo = mid;
+                        if (__ldg(a.ant_prefix + mid) <= tg) lo = mid;
                         else hi = mid;
                     }
                     const DevQuery q = a.queries[lo];
                     if (q.active && it < q.n_iter) {
                         active = true;
                         qi = lo;
-                        k = tk - q.ant_base;
-                        slot = tk;
+                        k = tg - q.ant_base;
+                        slot = tg;
                         src = q.src;
                         dst = q.dst;
                         n_ants = q.n_ants;
@@ -500,18 +502,19 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 if (tk >= a.total_ants) {
                     exhausted = true;
                 } else {
-                    uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tk < ant_prefix[q + 1]
+                    const uint32_t tg = a.ticket_base + tk;  // the ant's index in the whole job
+                    uint32_t lo = 0, hi = a.n_queries;  // query with ant_prefix[q] <= tg < ant_prefix[q + 1]
                     while (hi - lo > 1u) {
                         const uint32_t mid = (lo + hi) >> 1;
-                        if (__ldg(a.ant_prefix + mid) <= tk) lo = mid;
+                        if (__ldg(a.ant_prefix + mid) <= tg) lo = mid;
                         else hi = mid;
                     }
                     const DevQuery q = a.queries[lo];
                     if (q.active && it < q.n_iter) {
                         active = true;
                         qi = lo;
-                        k = tk - q.ant_base;
-                        slot = tk;
+                        k = tg - q.ant_base;
+                        slot = tg;
                         src = q.src;
                         dst = q.dst;
                         n_ants = q.n_ants;

@@ -24,7 +24,7 @@ using namespace gmp;
 namespace {
 
 struct Schedule {
-    uint32_t lanes, mode, chunk, free_running;
+    uint32_t lanes, mode, chunk, free_running, branches;
 };
 
 using Bucket = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
@@ -44,7 +44,7 @@ uint32_t ceil_log2(uint64_t x) {
 // where the lockstep kernel covers the shape.
 Schedule default_schedule(uint32_t maxdeg) {
     const uint32_t g = default_lanes(maxdeg);
-    return {g, GMP_MODE_ITERATIVE, 0, 0};
+    return {g, GMP_MODE_ITERATIVE, 0, 0, 0};
 }
 
 uint32_t runs_lockstep(const Schedule& s, uint32_t maxdeg) {
@@ -55,16 +55,17 @@ std::vector<Schedule> candidates(uint32_t n_nodes, uint32_t maxdeg) {
     const Schedule d = default_schedule(maxdeg);
     std::vector<Schedule> out{d};  // timed first
     auto add = [&](Schedule s) {
-        if (!(s.lanes == d.lanes && s.mode == d.mode && s.chunk == d.chunk && s.free_running == d.free_running))
+        if (!(s.lanes == d.lanes && s.mode == d.mode && s.chunk == d.chunk && s.free_running == d.free_running &&
+              s.branches == d.branches))
             out.push_back(s);
     };
     if (construct_thread_fits(n_nodes) && (uint32_t)construct_max_degree(1) >= maxdeg)
-        add({1, GMP_MODE_ITERATIVE, 0, 0});
+        add({1, GMP_MODE_ITERATIVE, 0, 0, 0});
     for (uint32_t g : {4u, 8u, 16u, 32u}) {
         if ((uint32_t)construct_max_degree((int)g) < maxdeg) continue;
-        add({g, GMP_MODE_ITERATIVE, 0, 0});
-        if (lockstep_fits((int)g, maxdeg)) add({g, GMP_MODE_ITERATIVE, 0, 1});
-        for (uint32_t ch : {8u, 16u, 32u, 64u}) add({g, GMP_MODE_PERSISTENT, ch, 0});
+        add({g, GMP_MODE_ITERATIVE, 0, 0, 0});
+        if (lockstep_fits((int)g, maxdeg)) add({g, GMP_MODE_ITERATIVE, 0, 1, 0});
+        for (uint32_t ch : {8u, 16u, 32u, 64u}) add({g, GMP_MODE_PERSISTENT, ch, 0, 0});
     }
     return out;
 }
@@ -73,6 +74,7 @@ gmp_params with_schedule(gmp_params p, const Schedule& s) {
     p.lanes_per_ant = s.lanes;
     p.mode = s.mode;
     p.queue_chunk = s.chunk;
+    p.branches = s.branches;
     p.flags = (p.flags & ~kFlagNoLockstepBit) | (s.free_running ? kFlagNoLockstepBit : 0u);
     return p;
 }
@@ -137,6 +139,7 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
             out->mode = s.mode;
             out->queue_chunk = s.chunk;
             out->lockstep = runs_lockstep(s, info.maxdeg);
+            out->branches = s.branches;
             out->from_cache = 1;
             return GMP_OK;
         }
@@ -149,18 +152,27 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
     const std::vector<Schedule> cand = candidates(info.N, info.maxdeg);
     Schedule best{};
     float best_ms = -1.0f;
-    for (size_t i = 0; i < cand.size(); ++i) {
-        const gmp_params p = with_schedule(base, cand[i]);
-        if (gmp_set_params(c, &p) != GMP_OK) continue;
+    auto try_schedule = [&](const Schedule& sc, bool is_default) {
+        const gmp_params p = with_schedule(base, sc);
+        if (gmp_set_params(c, &p) != GMP_OK) return;
         const float ms = time_probe(c, n, q.data(), info.stream, e0, e1);
-        if (ms < 0.0f) continue;
+        if (ms < 0.0f) return;
         ++out->n_tried;
-        if (i == 0) out->default_ms = ms;
+        if (is_default) out->default_ms = ms;
         // a schedule must beat the best so far by kMargin to replace it: the default (timed first)
         // stays unless something is clearly faster, so timing noise does not flip the choice
         if (best_ms < 0.0f || ms < best_ms * (1.0f - kMargin)) {
             best_ms = ms;
-            best = cand[i];
+            best = sc;
+        }
+    };
+    for (size_t i = 0; i < cand.size(); ++i) try_schedule(cand[i], i == 0);
+    if (best_ms >= 0.0f && best.mode == GMP_MODE_ITERATIVE) {  // then the chain count of the best
+        const Schedule b0 = best;
+        for (uint32_t br : {1u, 4u, 32u, 64u}) {
+            Schedule v = b0;
+            v.branches = br;
+            try_schedule(v, false);
         }
     }
     cudaEventDestroy(e0);
@@ -180,6 +192,7 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
     out->mode = best.mode;
     out->queue_chunk = best.chunk;
     out->lockstep = runs_lockstep(best, info.maxdeg);
+    out->branches = best.branches;
     out->best_ms = best_ms;
     return GMP_OK;
 }
