@@ -246,6 +246,9 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     uint32_t qi = 0, k = 0, slot = 0, src = 0, dst = 0, n_ants = 1, alpha = 1, beta = 2, s0 = 0, s1 = 0;
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
+    // Philox draws of the next G steps, one per lane: lane l holds the draw of step rb_base + l
+    uint32_t rb_base = 0, rb_x = 0, rb_y = 0;
+    bool rb_valid = false;
     const float* tauf = a.tauf;
     const uint32_t* hq = a.hq;
     uint32_t* route = a.routes;
@@ -292,6 +295,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         beg = __ldg(a.row_ptr + u);
                         end = __ldg(a.row_ptr + u + 1);
                         t = W = steps = 0;
+                        rb_valid = false;
                         if (leader) atomicOr(tabu + (u >> 5), 1u << (u & 31));
                     }
                 }
@@ -331,8 +335,18 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 tf[j] = __ldg(tauf + e);
                 he[j] = __ldg(hq + e);
             }
-            const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
-            const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            // when any group of the warp has used up its buffered draws, every group refills from its
+            // current step (lane l computes the draw of step + l), so refills stay rare and warp-wide
+            if (__any_sync(FULL, stepping && (!rb_valid || steps - rb_base >= (uint32_t)G))) {
+                const uint4 o = philox4x32_10(make_uint4(it, k, steps + lane, 0u), s0, s1);
+                rb_x = o.x;
+                rb_y = o.y;
+                rb_base = steps;
+                rb_valid = true;
+            }
+            const uint32_t rsrc = (steps - rb_base) & (uint32_t)(G - 1);
+            const uint32_t rx = __shfl_sync(FULL, rb_x, rsrc, G), ry = __shfl_sync(FULL, rb_y, rsrc, G);
+            const unsigned long long rnd = (unsigned long long)rx | ((unsigned long long)ry << 32);
             uint32_t cmask = 0, cong = 0;
             uint32_t sb[K], wv[K];
 #pragma unroll
