@@ -114,7 +114,7 @@ int gmp_load_graph(gmp_ctx *ctx, uint32_t n_nodes, uint32_t n_edges, const uint3
                    const int32_t *y_dm);
 
 /* Fixed-time signal programmes (Fig. 3 "L: Light, P: Phase"; Algorithm 1 arguments traffic_light, phases).
- * Per node v: n_phases[v] in 0..8 (0 = unsignalised), cycle_ms[v] in 1..2^24, offset_ms[v] < cycle,
+ * Per node v: n_phases[v] in 0..8 (0 = unsignalised), cycle_ms[v] in 1..2^24-1, offset_ms[v] < cycle,
  * green_ms[v*8 + p] >= 1 for p < n_phases with sum == cycle. edge_phase[e]: approach phase of road e at
  * its head (< n_phases of the head when signalised). Resets the red-time accumulators to 0 and recomputes
  * the phase order. Errors: INVALID_ARG, UNSUPPORTED (> 8 phases), STATE (no graph), CUDA. */

@@ -52,9 +52,8 @@ struct Batch {
     DevQuery* dq = nullptr;
     uint32_t* prefix = nullptr;
     uint64_t* tau = nullptr;
-    float* tauf = nullptr;
+    uint2* th = nullptr;  // per (colony, road): pheromone as binary32 bits, heuristic (ms)
     unsigned long long* dep = nullptr;
-    uint32_t* heur = nullptr;  // per (colony, road) heuristic table
     QueryState* qs = nullptr;
     uint32_t* routes = nullptr;
     uint32_t* ant_steps = nullptr;
@@ -253,9 +252,8 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.dq);
     dfree(c, &b.prefix);
     dfree(c, &b.tau);
-    dfree(c, &b.tauf);
+    dfree(c, &b.th);
     dfree(c, &b.dep);
-    dfree(c, &b.heur);
     dfree(c, &b.qs);
     dfree(c, &b.routes);
     dfree(c, &b.ant_steps);
@@ -307,7 +305,7 @@ uint32_t hsat_of(const gmp_ctx* c) { return c->prm.h_sat_ms ? c->prm.h_sat_ms : 
 int refresh_dynamic(gmp_ctx* c) {
     GMP_CUDA(c, launch_edge_dynamic(c->stream, c->E, c->row_ptr, c->col, c->ff, c->cap, c->lanes, c->veh, c->nph,
                                     hsat_of(c), c->prm.thr_permille, c->rec));
-    GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
+    GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
                                      c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
     return GMP_OK;
 }
@@ -349,7 +347,7 @@ int record(gmp_ctx* c, Batch& b, size_t i) {
 ConstructArgs construct_args(gmp_ctx* c);
 
 // Arguments of the iteration-end kernel for a job's workspace (the context supplies the queue state).
-IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* tau, float* tauf,
+IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* tau, uint2* th,
                           unsigned long long* dep, QueryState* qs, const uint32_t* routes, const uint32_t* ant_steps,
                           const uint32_t* ant_wait, uint32_t* best_route, uint32_t max_steps) {
     IterEndArgs e{};
@@ -359,13 +357,14 @@ IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* 
     e.max_steps = max_steps;
     e.q = dq;
     e.tau = tau;
-    e.tauf = tauf;
+    e.th = th;
     e.dep = dep;
     e.qs = qs;
     e.routes = routes;
     e.ant_steps = ant_steps;
     e.ant_wait = ant_wait;
     e.best_route = best_route;
+    e.row_ptr = c->row_ptr;
     e.in_ptr = c->in_ptr;
     e.in_edge = c->in_edge;
     e.nph = c->nph;
@@ -387,8 +386,8 @@ int enqueue_persistent(gmp_ctx* c) {
     cudaStream_t s = c->stream;
     const bool timed = b.timed;
     if (timed) GMP_TRY(record(c, b, 0));
-    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.tauf,
-                                  b.dep, b.heur, b.qs, b.tickets, b.maxI));
+    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
+                                  b.dep, b.qs, b.tickets, b.maxI));
     GMP_CUDA(c, launch_persistent_init(s, b.Q, b.maxI, b.dq, b.ctr, b.qstate, b.qflag, b.misc));
     if (timed) GMP_TRY(record(c, b, 1));
     PersistentArgs p{};
@@ -398,7 +397,7 @@ int enqueue_persistent(gmp_ctx* c) {
     p.qflag = b.qflag;
     p.misc = b.misc;
     p.tau = b.tau;
-    p.tauf = b.tauf;
+    p.th = b.th;
     p.best_route = b.best_route;
     p.in_ptr = c->in_ptr;
     p.in_edge = c->in_edge;
@@ -433,8 +432,7 @@ ConstructArgs construct_args(gmp_ctx* c) {
     a.queries = b.dq;
     a.ant_prefix = b.prefix;
     a.tau = b.tau;
-    a.tauf = b.tauf;
-    a.hq = b.heur;
+    a.th = b.th;
     a.dep = b.dep;
     a.qs = b.qs;
     a.routes = b.routes;
@@ -495,8 +493,8 @@ int enqueue_job(gmp_ctx* c) {
     const size_t B = b.br.size();
     uint64_t n = 0;
     if (timed) GMP_TRY(record(c, b, 0));
-    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.tauf,
-                                  b.dep, b.heur, b.qs, b.tickets, b.maxI * (uint32_t)B));
+    GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
+                                  b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
     if (B > 1) {
@@ -515,8 +513,7 @@ int enqueue_job(gmp_ctx* c) {
         a.queries = b.dq + r.q0;
         a.ant_prefix = b.prefix + r.q0;
         a.tau = b.tau + co;
-        a.tauf = b.tauf + co;
-        a.hq = b.heur + co;
+        a.th = b.th + co;
         a.dep = b.dep + co;
         a.qs = b.qs + r.q0;
         a.tickets = b.tickets + (size_t)j * b.maxI;
@@ -525,7 +522,7 @@ int enqueue_job(gmp_ctx* c) {
         a.total_ants = r.ants;
         a.ticket_base = r.ticket_base;
         a.tabu_in_smem = r.kc.tabu_in_smem ? 1u : 0u;
-        IterEndArgs e = iter_end_args(c, r.q1 - r.q0, b.dq + r.q0, b.tau + co, b.tauf + co, b.dep + co, b.qs + r.q0,
+        IterEndArgs e = iter_end_args(c, r.q1 - r.q0, b.dq + r.q0, b.tau + co, b.th + co, b.dep + co, b.qs + r.q0,
                                       b.routes, b.ant_steps, b.ant_wait, b.best_route + (size_t)r.q0 * b.max_steps,
                                       b.max_steps);
         if (j > 0) e.n_nodes = 0;  // the queue update of an iteration runs once, in the first chain
@@ -570,8 +567,8 @@ BatchKey key_of(const gmp_ctx* c) {
     k.ptrs[1] = b.routes;
     k.ptrs[2] = b.tabu;
     k.ptrs[3] = c->rec;
-    k.ptrs[4] = b.heur;
-    k.ptrs[5] = b.tauf;
+    k.ptrs[4] = b.th;
+    k.ptrs[5] = b.dep;
     return k;
 }
 
@@ -734,7 +731,7 @@ int gmp_set_signals(gmp_ctx* c, const uint8_t* n_phases, const uint32_t* cycle_m
         if (P > kMaxPhases) return fail(c, GMP_ERR_UNSUPPORTED, "node %u: more than 8 phases", v);
         if (P == 0) continue;
         const uint32_t cy = cycle_ms[v];
-        if (cy == 0 || cy > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "node %u: cycle must be in 1..2^24 ms", v);
+        if (cy == 0 || cy > kCycleMask) return fail(c, GMP_ERR_INVALID_ARG, "node %u: cycle must be in 1..2^24-1 ms", v);
         if (offset_ms[v] >= cy) return fail(c, GMP_ERR_INVALID_ARG, "node %u: offset must be below the cycle", v);
         uint64_t sum = 0;
         for (uint32_t p = 0; p < P; ++p) {
@@ -854,9 +851,8 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
     GMP_TRY(ensure(c, &b.dq, n));
     GMP_TRY(ensure(c, &b.prefix, n + 1));
     GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.tauf, (size_t)n * c->E));
+    GMP_TRY(ensure(c, &b.th, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.heur, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.qs, n));
     GMP_TRY(ensure(c, &b.routes, (size_t)total_ants * max_steps));
     GMP_TRY(ensure(c, &b.ant_steps, (size_t)total_ants));
@@ -1178,7 +1174,7 @@ int gmp_get_edge_times(gmp_ctx* c, uint32_t* tt_ms, uint32_t* qd_ms) {
     GMP_TRY(sync(c));
     for (uint32_t e = 0; e < c->E; ++e) {
         if (tt_ms) tt_ms[e] = h[e].tt;
-        if (qd_ms) qd_ms[e] = h[e].qd;
+        if (qd_ms) qd_ms[e] = h[e].qd_fl & kQdMask;
     }
     return GMP_OK;
 }
@@ -1300,8 +1296,8 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
         return o;
     };
     const size_t o_dq = take(sizeof(DevQuery)), o_prefix = take(8), o_qs = take(sizeof(QueryState));
-    const size_t o_tickets = take((size_t)n_iter * 4), o_tau = take(E * 8), o_tauf = take(E * 4), o_dep = take(E * 8);
-    const size_t o_heur = take(E * 4), o_routes = take((size_t)n_ants * S * 4), o_steps = take((size_t)n_ants * 4);
+    const size_t o_tickets = take((size_t)n_iter * 4), o_tau = take(E * 8), o_th = take(E * 8), o_dep = take(E * 8);
+    const size_t o_routes = take((size_t)n_ants * S * 4), o_steps = take((size_t)n_ants * 4);
     const size_t o_wait = take((size_t)n_ants * 4), o_best = take((size_t)S * 4);
     const size_t o_tabu = kc.tabu_in_smem ? 0 : take((size_t)kc.grid * (kc.block / kc.lanes) * words * 4);
     if (off > GMP_STATIC_SCRATCH_BYTES)
@@ -1313,9 +1309,8 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     QueryState* qs = reinterpret_cast<QueryState*>(base + o_qs);
     uint32_t* tickets = reinterpret_cast<uint32_t*>(base + o_tickets);
     uint64_t* tau = reinterpret_cast<uint64_t*>(base + o_tau);
-    float* tauf = reinterpret_cast<float*>(base + o_tauf);
+    uint2* th = reinterpret_cast<uint2*>(base + o_th);
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(base + o_dep);
-    uint32_t* heur = reinterpret_cast<uint32_t*>(base + o_heur);
     uint32_t* routes = reinterpret_cast<uint32_t*>(base + o_routes);
     uint32_t* ant_steps = reinterpret_cast<uint32_t*>(base + o_steps);
     uint32_t* ant_wait = reinterpret_cast<uint32_t*>(base + o_wait);
@@ -1339,7 +1334,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     k_static_query<<<1, 1, 0, s>>>(hq, dq, prefix);
     GMP_CUDA(c, cudaGetLastError());
     // init clears the pheromone, deposits, colony state and ticket counters left by the previous call
-    GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, tauf, dep, heur,
+    GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, th, dep,
                                   qs, tickets, n_iter));
     ConstructArgs a{};
     a.rec = c->rec;
@@ -1348,8 +1343,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     a.queries = dq;
     a.ant_prefix = prefix;
     a.tau = tau;
-    a.tauf = tauf;
-    a.hq = heur;
+    a.th = th;
     a.dep = dep;
     a.qs = qs;
     a.routes = routes;
@@ -1367,7 +1361,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     a.thr_on = c->prm.thr_permille != kThrOff;
     a.tabu_in_smem = kc.tabu_in_smem ? 1u : 0u;
     a.kappa = c->kappa;
-    IterEndArgs e = iter_end_args(c, 1, dq, tau, tauf, dep, qs, routes, ant_steps, ant_wait, best_route, S);
+    IterEndArgs e = iter_end_args(c, 1, dq, tau, th, dep, qs, routes, ant_steps, ant_wait, best_route, S);
     for (uint32_t it = 0; it < n_iter; ++it) {
         GMP_CUDA(c, launch_construct(s, kc, a, it));
         e.it = it;

@@ -20,24 +20,24 @@ constexpr uint64_t kNoKey = ~0ull;
 
 enum : uint32_t { kAntSuccess = 0, kAntDeadEnd = 1, kAntStepCap = 2, kAntTimeCap = 3 };
 
-// Per-road record read by the construction kernel: everything one candidate needs in three 16-byte
-// loads (the head's CSR row, congested time, queue delay, the head signal's green window for this
-// approach and a reciprocal for reducing arrival times modulo the cycle). Rebuilt whenever densities,
-// signals or the phase order change.
+// Per-road record read by the construction kernel: everything one candidate needs in two 16-byte
+// loads. The first half (head, its CSR row start, congested time, queue delay and the congestion flag)
+// follows the densities; the second half (the head's out-degree, and its signal cycle, this approach's
+// green window and a reciprocal for reducing arrival times modulo the cycle) follows the phase order.
 struct __align__(16) EdgeRec {
-    uint32_t head;   // v
-    uint32_t vbeg;   // first road out of v
-    uint32_t vend;   // one past the last road out of v
-    uint32_t tt;     // congested travel time, ms
-    uint32_t qd;     // queue discharge delay at v (0 when v is unsignalised), ms
-    uint32_t cycle;  // cycle of v's signal, 0 = unsignalised
-    uint32_t gbeg;   // start of this approach's green window, (offset + start in phase order) mod cycle
-    uint32_t glen;   // green time of this approach's phase
-    uint32_t cmagic; // floor((2^32 - 1) / cycle), 0 when unsignalised
-    uint32_t flags;  // bit 0: road over the congestion threshold
-    uint32_t pad[2];
+    uint32_t head;    // v
+    uint32_t vbeg;    // first road out of v
+    uint32_t tt;      // congested travel time, ms
+    uint32_t qd_fl;   // queue discharge delay at v, ms (bits 0-30; 0 when v is unsignalised) |
+                      // road over the congestion threshold (bit 31)
+    uint32_t cyc_deg; // cycle of v's signal (bits 0-23; 0 = unsignalised) | out-degree of v (bits 24-31)
+    uint32_t gbeg;    // start of this approach's green window, (offset + start in phase order) mod cycle
+    uint32_t glen;    // green time of this approach's phase
+    uint32_t cmagic;  // floor((2^32 - 1) / cycle), 0 when unsignalised
 };
-static_assert(sizeof(EdgeRec) == 48, "EdgeRec layout");
+static_assert(sizeof(EdgeRec) == 32, "EdgeRec layout");
+constexpr uint32_t kCycleMask = 0xFFFFFFu;  // cycles are below 2^24 ms
+constexpr uint32_t kQdMask = 0x7FFFFFFFu;
 
 // One colony of a batch, as the kernels read it.
 struct __align__(16) DevQuery {

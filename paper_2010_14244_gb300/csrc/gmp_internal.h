@@ -20,8 +20,8 @@ struct ConstructArgs {
     const DevQuery* queries;
     const uint32_t* ant_prefix;  // Q + 1 entries: first global ant of each query
     const uint64_t* tau;         // Q * E
-    const float* tauf;           // Q * E pheromone as binary32 (tau rounded to nearest times 2^-32)
-    const uint32_t* hq;          // Q * E heuristic of each road's head towards the colony's destination
+    const uint2* th;             // Q * E pairs: pheromone as binary32 bits (tau rounded to nearest times
+                                 // 2^-32) and the heuristic of the road's head towards the destination
     unsigned long long* dep;     // Q * E deposit accumulators
     QueryState* qs;
     uint32_t* routes;            // total_ants * max_steps road ids
@@ -44,12 +44,12 @@ struct IterEndArgs {
     uint32_t evap_blocks;  // blocks per colony for the evaporation (set by the launcher)
     const DevQuery* q;
     uint64_t* tau;
-    float* tauf;
+    uint2* th;
     unsigned long long* dep;
     QueryState* qs;
     const uint32_t *routes, *ant_steps, *ant_wait;
     uint32_t* best_route;
-    const uint32_t *in_ptr, *in_edge;
+    const uint32_t *row_ptr, *in_ptr, *in_edge;
     const uint8_t* nph;
     const uint32_t *cycle, *offset, *green;
     const uint8_t* ephase;
@@ -75,7 +75,7 @@ struct PersistentArgs {
     uint32_t* qflag;        // max_iter: colony (+1) that updates the queues for that iteration index
     uint32_t* misc;         // [0] finished colonies, [1] error flag (bounded wait expired)
     uint64_t* tau;
-    float* tauf;
+    uint2* th;
     uint32_t* best_route;
     const uint32_t *in_ptr, *in_edge;
     const uint8_t* nph;
@@ -104,7 +104,8 @@ cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* len, 
 cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
                                 const uint32_t* ff, const uint32_t* cap, const uint8_t* lanes, const uint32_t* veh,
                                 const uint8_t* nph, uint32_t h_sat, uint32_t thr, EdgeRec* rec);
-cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_ptr, const uint32_t* in_edge,
+cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
+                                 const uint32_t* in_edge,
                                  const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
                                  const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec);
@@ -115,7 +116,7 @@ cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, con
                         unsigned long long* K, uint32_t* red);
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
-                              float* tauf, unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
+                              uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
 cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& a);

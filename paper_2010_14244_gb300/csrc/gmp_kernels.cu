@@ -40,25 +40,21 @@ __global__ void k_edge_dynamic(uint32_t E, const uint32_t* __restrict__ row_ptr,
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const uint32_t v = col[e], n = veh[e], c = cap[e];
-    EdgeRec& r = rec[e];
-    r.head = v;
-    r.vbeg = row_ptr[v];
-    r.vend = row_ptr[v + 1];
-    r.tt = edge_time_ms(ff[e], c, n);
     uint32_t qd = 0;
     if (nph[v] > 0) {
         const uint64_t d = (uint64_t)n * h_sat / lanes[e];
         qd = d > kTimeClamp ? kTimeClamp : (uint32_t)d;
     }
-    r.qd = qd;
-    r.flags = (thr != kThrOff && (uint64_t)n * 1000u > (uint64_t)thr * c) ? 1u : 0u;
-    r.pad[0] = r.pad[1] = 0;
+    const uint32_t fl = (thr != kThrOff && (uint64_t)n * 1000u > (uint64_t)thr * c) ? 1u : 0u;
+    uint4* r = reinterpret_cast<uint4*>(rec + e);  // first half of the record (see EdgeRec)
+    *r = make_uint4(v, row_ptr[v], edge_time_ms(ff[e], c, n), qd | (fl << 31));
 }
 
 // ------------------------------------------------------------------------------------------------
 // Preemptive phase order, one thread per intersection (queue_node in gmp_walk.cuh).
 // ------------------------------------------------------------------------------------------------
-__global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr, const uint32_t* __restrict__ in_edge,
+__global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ in_ptr,
+                                const uint32_t* __restrict__ in_edge,
                                 const uint8_t* __restrict__ nph, const uint32_t* __restrict__ cycle,
                                 const uint32_t* __restrict__ offset, const uint32_t* __restrict__ green,
                                 const uint8_t* __restrict__ ephase, const uint32_t* __restrict__ veh,
@@ -66,7 +62,7 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ in_ptr,
                                 uint8_t* __restrict__ order, EdgeRec* __restrict__ rec) {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
-    queue_node(v, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh, cap, red, order, rec);
+    queue_node(v, row_ptr, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh, cap, red, order, rec);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -151,27 +147,25 @@ __global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
 // ------------------------------------------------------------------------------------------------
 // Batch initialisation: pheromone 1.0 (or Philox-random in [0.5, 1.5)), deposits zero, colony state.
 // ------------------------------------------------------------------------------------------------
-// Calc_Dist for the whole colony up front: hq[e] = h(head(e)) towards this colony's destination.
+// Calc_Dist for the whole colony up front: th[e].y = h(head(e)) towards this colony's destination,
+// next to th[e].x, the pheromone as binary32 bits (one 8-byte load per candidate).
 __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
                              const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
-                             uint32_t flags, uint64_t* __restrict__ tau, float* __restrict__ tauf,
-                             unsigned long long* __restrict__ dep, uint32_t* __restrict__ hq,
-                             QueryState* __restrict__ qs, uint32_t* __restrict__ tickets, uint32_t n_tickets) {
+                             uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
+                             unsigned long long* __restrict__ dep, QueryState* __restrict__ qs, uint32_t* __restrict__ tickets, uint32_t n_tickets) {
     const uint32_t qi = blockIdx.y;
     const DevQuery Q = q[qi];
     uint64_t* T = tau + (size_t)qi * E;
     unsigned long long* D = dep + (size_t)qi * E;
-    uint32_t* H = hq + (size_t)qi * E;
-    float* TF = tauf + (size_t)qi * E;
+    uint2* TH = th + (size_t)qi * E;
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         uint64_t t0 = 1ull << 32;
         if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
         T[e] = t0;
-        TF[e] = tau_float(t0);
         D[e] = 0;
         const uint32_t v = col[e];
-        H[e] = heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
+        TH[e] = make_uint2(__float_as_uint(tau_float(t0)), heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const uint32_t h = heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
@@ -249,8 +243,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     // Philox draws of the next G steps, one per lane: lane l holds the draw of step rb_base + l
     uint32_t rb_base = 0, rb_x = 0, rb_y = 0;
     bool rb_valid = false;
-    const float* tauf = a.tauf;
-    const uint32_t* hq = a.hq;
+    const uint2* th = a.th;
     uint32_t* route = a.routes;
     for (;;) {
         // 1. groups without an ant take the next tickets (one atomic for the whole warp)
@@ -288,8 +281,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         s0 = (uint32_t)q.seed;
                         s1 = (uint32_t)(q.seed >> 32);
                         log_base = q.log_base;
-                        tauf = a.tauf + (size_t)qi * a.n_edges;
-                        hq = a.hq + (size_t)qi * a.n_edges;
+                        th = a.th + (size_t)qi * a.n_edges;
                         route = a.routes + (size_t)slot * a.max_steps;
                         u = src;
                         beg = __ldg(a.row_ptr + u);
@@ -318,7 +310,6 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
         const int nslots = K == 1 ? 1 : (int)__reduce_max_sync(FULL, (deg + G - 1) / G);  // warp-uniform
         if (__any_sync(FULL, deg > 0u)) {
             uint4 r0[K], r1[K];
-            uint2 r2[K];
             float tf[K];
             uint32_t he[K];
             uint32_t valid = 0;
@@ -331,9 +322,9 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
                 r0[j] = __ldg(rp);
                 r1[j] = __ldg(rp + 1);
-                r2[j] = __ldg(reinterpret_cast<const uint2*>(rp + 2));
-                tf[j] = __ldg(tauf + e);
-                he[j] = __ldg(hq + e);
+                const uint2 ph = __ldg(th + e);
+                tf[j] = __uint_as_float(ph.x);
+                he[j] = ph.y;
             }
             // when any group of the warp has used up its buffered draws, every group refills from its
             // current step (lane l computes the draw of step + l), so refills stay rare and warp-wide
@@ -351,14 +342,14 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             uint32_t sb[K], wv[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const uint32_t v = r0[j].x, cy = r1[j].y;
+                const uint32_t v = r0[j].x, cy = r1[j].x & kCycleMask;
                 const bool unvisited = !((tabu[v >> 5] >> (v & 31)) & 1u);
                 cmask |= ((valid >> j) & (unvisited ? 1u : 0u)) << j;
-                cong |= (r2[j].y & 1u) << j;
-                const uint32_t sw = signal_wait(a.t_dep + t + r0[j].w, cy | (cy == 0u), r2[j].x, r1[j].z, r1[j].w);
-                const uint32_t w = (v != dst && cy != 0u) ? sw + r1[j].x : 0u;
+                cong |= (r0[j].w >> 31) << j;
+                const uint32_t sw = signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
+                const uint32_t w = (v != dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
                 wv[j] = w;
-                sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].w + w + he[j], beta));
+                sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].z + w + he[j], beta));
             }
             constexpr uint32_t kGroupBits = G == 32 ? FULL : ((1u << (G & 31)) - 1u);
             const uint32_t gshift = wl & ~(uint32_t)(G - 1);
@@ -402,8 +393,8 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 const bool sel = pick_slot == j;
                 c_h = sel ? r0[j].x : c_h;
                 c_vb = sel ? r0[j].y : c_vb;
-                c_ve = sel ? r0[j].z : c_ve;
-                c_tt = sel ? r0[j].w : c_tt;
+                c_ve = sel ? r0[j].y + (r1[j].x >> 24) : c_ve;
+                c_tt = sel ? r0[j].z : c_tt;
                 c_w = sel ? wv[j] : c_w;
             }
             c_h = __shfl_sync(FULL, c_h, pick_lane, G);
@@ -494,8 +485,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
     uint32_t qi = 0, k = 0, slot = 0, src = 0, dst = 0, n_ants = 1, alpha = 1, beta = 2, s0 = 0, s1 = 0;
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
-    const float* tauf = a.tauf;
-    const uint32_t* hq = a.hq;
+    const uint2* th = a.th;
     uint32_t* route = a.routes;
     const uint32_t n_threads = gridDim.x * blockDim.x;
     for (;;) {
@@ -537,8 +527,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                         s0 = (uint32_t)q.seed;
                         s1 = (uint32_t)(q.seed >> 32);
                         log_base = q.log_base;
-                        tauf = a.tauf + (size_t)qi * a.n_edges;
-                        hq = a.hq + (size_t)qi * a.n_edges;
+                        th = a.th + (size_t)qi * a.n_edges;
                         route = a.routes + (size_t)slot * a.max_steps;
                         u = src;
                         beg = __ldg(a.row_ptr + u);
@@ -565,7 +554,6 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
         const uint32_t wmax = __reduce_max_sync(FULL, deg);
         if (wmax > 0u) {
             uint4 r0[K], r1[K];
-            uint2 r2[K];
             float tf[K];
             uint32_t he[K];
 #pragma unroll
@@ -575,12 +563,11 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                     const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
                     r0[j] = __ldg(rp);
                     r1[j] = __ldg(rp + 1);
-                    r2[j] = __ldg(reinterpret_cast<const uint2*>(rp + 2));
-                    tf[j] = __ldg(tauf + e);
-                    he[j] = __ldg(hq + e);
+                        const uint2 ph = __ldg(th + e);
+                    tf[j] = __uint_as_float(ph.x);
+                    he[j] = ph.y;
                 } else {
                     r0[j] = r1[j] = make_uint4(0, 0, 0, 0);
-                    r2[j] = make_uint2(0, 0);
                     tf[j] = 0.0f;
                     he[j] = 0;
                 }
@@ -593,15 +580,15 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
             for (int j = 0; j < K; ++j) {
                 sb[j] = wv[j] = 0;
                 if ((uint32_t)j < wmax) {
-                    const uint32_t v = r0[j].x, cy = r1[j].y;
+                    const uint32_t v = r0[j].x, cy = r1[j].x & kCycleMask;
                     const bool unvisited = !((tw[tabu_index(v >> 5, lane)] >> (v & 31)) & 1u);
                     cmask |= (((uint32_t)j < deg && unvisited) ? 1u : 0u) << j;
-                    cong |= (r2[j].y & 1u) << j;
+                    cong |= (r0[j].w >> 31) << j;
                     const uint32_t sw =
-                        signal_wait(a.t_dep + t + r0[j].w, cy | (cy == 0u), r2[j].x, r1[j].z, r1[j].w);
-                    const uint32_t w = (v != dst && cy != 0u) ? sw + r1[j].x : 0u;
+                        signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
+                    const uint32_t w = (v != dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
                     wv[j] = w;
-                    sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].w + w + he[j], beta));
+                    sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].z + w + he[j], beta));
                 }
             }
             if (a.thr_on && (cmask & ~cong) && (cmask & cong)) cmask &= ~cong;
@@ -634,8 +621,8 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 const bool sel = js == j;
                 c_h = sel ? r0[j].x : c_h;
                 c_vb = sel ? r0[j].y : c_vb;
-                c_ve = sel ? r0[j].z : c_ve;
-                c_tt = sel ? r0[j].w : c_tt;
+                c_ve = sel ? r0[j].y + (r1[j].x >> 24) : c_ve;
+                c_tt = sel ? r0[j].z : c_tt;
                 c_w = sel ? wv[j] : c_w;
             }
             if (stepping && !done) {
@@ -717,7 +704,7 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
         const uint64_t rf = Q.rho_fix;
         const size_t off = (size_t)qi * a.n_edges;
         uint64_t* T = a.tau + off;
-        float* TF = a.tauf + off;
+        uint32_t* TF = reinterpret_cast<uint32_t*>(a.th + off);  // pheromone half of each pair
         unsigned long long* D = a.dep + off;
         const uint32_t e0 = chunk * kIterEndBlock * kEvapPer + threadIdx.x;
         uint64_t tv[kEvapPer];
@@ -736,7 +723,7 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
                 const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
                 const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + dv[i];
                 T[e] = nt;
-                TF[e] = tau_float(nt);
+                TF[2 * (size_t)e] = __float_as_uint(tau_float(nt));
                 D[e] = 0;
             }
         }
@@ -764,7 +751,7 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
     b -= a.n_queries;
     const uint32_t v = b * blockDim.x + threadIdx.x;
     if (v < a.n_nodes)
-        queue_node(v, a.in_ptr, a.in_edge, a.nph, a.cycle, a.offset, a.green, a.ephase, a.veh, a.cap, a.red,
+        queue_node(v, a.row_ptr, a.in_ptr, a.in_edge, a.nph, a.cycle, a.offset, a.green, a.ephase, a.veh, a.cap, a.red,
                    a.order, a.rec);
 }
 
@@ -815,12 +802,13 @@ cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_
     return cudaGetLastError();
 }
 
-cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* in_ptr, const uint32_t* in_edge,
+cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
+                                 const uint32_t* in_edge,
                                  const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
                                  const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec) {
     if (N == 0) return cudaSuccess;
-    k_queue_preempt<<<blocks_for(N, 128), 128, 0, s>>>(N, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh,
+    k_queue_preempt<<<blocks_for(N, 128), 128, 0, s>>>(N, row_ptr, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh,
                                                         cap, red, order, rec);
     return cudaGetLastError();
 }
@@ -839,10 +827,10 @@ cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, con
 
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
-                              float* tauf, unsigned long long* dep, uint32_t* hq, QueryState* qs, uint32_t* tickets,
+                              uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
-    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, tauf, dep, hq, qs, tickets, n_tickets);
+    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets);
     return cudaGetLastError();
 }
 

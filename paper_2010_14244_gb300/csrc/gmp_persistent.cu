@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
                 if (c < n_edge_chunks) {  // Evap_Pher + Updt_Pher on roads [e0, e1) of this colony
                     const uint64_t rf = q.rho_fix;
                     uint64_t* T = p.tau + (size_t)qi * E;
-                    float* TF = p.tauf + (size_t)qi * E;
+                    uint32_t* TF = reinterpret_cast<uint32_t*>(p.th + (size_t)qi * E);  // pheromone halves
                     unsigned long long* D = a.dep + (size_t)qi * E;
                     constexpr int PER = (int)(kEdgeChunk / G);
                     const uint32_t e0 = c * kEdgeChunk;
@@ -167,14 +167,14 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
                             const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
                             const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + dv[i];
                             T[e] = nt;
-                            TF[e] = tau_float(nt);
+                            TF[2 * (size_t)e] = __float_as_uint(tau_float(nt));
                             D[e] = 0;
                         }
                     }
                 } else {  // queue / preemption update of intersections [v0, v1) (densities fixed: same order)
                     const uint32_t v0 = (c - n_edge_chunks) * node_chunk, v1 = min(p.n_nodes, v0 + node_chunk);
                     for (uint32_t v = v0 + lane; v < v1; v += G)
-                        queue_node(v, p.in_ptr, p.in_edge, p.nph, p.cycle, p.offset, p.green, p.ephase, p.veh,
+                        queue_node(v, a.row_ptr, p.in_ptr, p.in_edge, p.nph, p.cycle, p.offset, p.green, p.ephase, p.veh,
                                    p.cap, p.red, p.order, p.rec);
                 }
                 __threadfence();

@@ -15,7 +15,8 @@ namespace gmp {
 // storage, longest first; else (2) phases red for longer than a cycle, longest first; else (3) the
 // longest non-empty queue; then the remaining non-empty phases, then the empty ones, each in index
 // order. Every in-edge's record then gets its approach's green window under that order.
-__device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restrict__ in_ptr,
+__device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restrict__ row_ptr,
+                                           const uint32_t* __restrict__ in_ptr,
                                            const uint32_t* __restrict__ in_edge, const uint8_t* __restrict__ nph,
                                            const uint32_t* __restrict__ cycle, const uint32_t* __restrict__ offset,
                                            const uint32_t* __restrict__ green, const uint8_t* __restrict__ ephase,
@@ -23,16 +24,12 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
                                            const uint32_t* __restrict__ red, uint8_t* __restrict__ order,
                                            EdgeRec* __restrict__ rec) {
     const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
+    const uint32_t deg = min(row_ptr[v + 1] - row_ptr[v], 255u) << 24;  // out-degree of v (at most 128 runs)
     uint8_t ord[kMaxPhases];
     if (P == 0) {
         for (uint32_t i = 0; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
-        for (uint32_t i = ib; i < ie; ++i) {
-            EdgeRec& r = rec[in_edge[i]];
-            r.cycle = 0;
-            r.gbeg = 0;
-            r.glen = 0;
-            r.cmagic = 0;
-        }
+        for (uint32_t i = ib; i < ie; ++i)  // second half of the record (see EdgeRec)
+            reinterpret_cast<uint4*>(rec + in_edge[i])[1] = make_uint4(deg, 0u, 0u, 0u);
         return;
     }
     uint64_t Q[kMaxPhases], S[kMaxPhases];
@@ -102,11 +99,8 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
     for (uint32_t i = ib; i < ie; ++i) {
         const uint32_t e = in_edge[i];
         const uint32_t p = ephase[e] & (kMaxPhases - 1);
-        EdgeRec& r = rec[e];
-        r.cycle = cy;
-        r.gbeg = (off + start[p]) % cy;
-        r.glen = green[(size_t)v * kMaxPhases + p];
-        r.cmagic = magic;
+        reinterpret_cast<uint4*>(rec + e)[1] =
+            make_uint4(cy | deg, (off + start[p]) % cy, green[(size_t)v * kMaxPhases + p], magic);
     }
 }
 
@@ -123,8 +117,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     constexpr int NC = G * K;              // candidate slots of the group
     constexpr bool kGather = NC <= 16;     // every lane gathers all scores and picks locally
     constexpr uint32_t kNone = 0xFFFFFFFFu;  // not a candidate (scores are non-negative floats)
-    const float* __restrict__ tauf = a.tauf + (size_t)qi * a.n_edges;
-    const uint32_t* __restrict__ hq = a.hq + (size_t)qi * a.n_edges;
+    const uint2* __restrict__ th = a.th + (size_t)qi * a.n_edges;
     const uint32_t slot = q.ant_base + k;
     uint32_t* route = a.routes + (size_t)slot * a.max_steps;
     const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
@@ -146,7 +139,6 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         const int nslots = K == 1 ? 1 : (int)((deg + G - 1) / G);  // group-uniform
         // 1. issue every load of this step: records, pheromone and heuristic of this lane's candidates
         uint4 r0[K], r1[K];
-        uint2 r2[K];
         float tf[K];
         uint32_t he[K];
         uint32_t valid = 0;
@@ -159,9 +151,9 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
             r0[j] = __ldg(rp);
             r1[j] = __ldg(rp + 1);
-            r2[j] = __ldg(reinterpret_cast<const uint2*>(rp + 2));
-            tf[j] = __ldg(tauf + e);
-            he[j] = __ldg(hq + e);
+            const uint2 ph = __ldg(th + e);
+            tf[j] = __uint_as_float(ph.x);
+            he[j] = ph.y;
         }
         // 2. the draw of this step depends on (iteration, ant, step) only: overlaps the loads
         const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
@@ -171,14 +163,14 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         uint32_t sb[K], wv[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const uint32_t v = r0[j].x, cy = r1[j].y;
+            const uint32_t v = r0[j].x, cy = r1[j].x & kCycleMask;
             const bool unvisited = !((tabu[v >> 5] >> (v & 31)) & 1u);
             cmask |= ((valid >> j) & (unvisited ? 1u : 0u)) << j;
-            cong |= (r2[j].y & 1u) << j;
-            const uint32_t sw = signal_wait(a.t_dep + t + r0[j].w, cy | (cy == 0u), r2[j].x, r1[j].z, r1[j].w);
-            const uint32_t w = (v != q.dst && cy != 0u) ? sw + r1[j].x : 0u;
+            cong |= (r0[j].w >> 31) << j;
+            const uint32_t sw = signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
+            const uint32_t w = (v != q.dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
             wv[j] = w;
-            sb[j] = __float_as_uint(score_f(tf[j], q.alpha, r0[j].w + w + he[j], q.beta));
+            sb[j] = __float_as_uint(score_f(tf[j], q.alpha, r0[j].z + w + he[j], q.beta));
         }
         if (a.thr_on) {  // congested roads drop out unless every candidate is congested
             const uint32_t any_ok = __ballot_sync(gmask, (cmask & ~cong) != 0u) & gmask;
@@ -266,8 +258,8 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             if (pick_slot == j) {
                 c_h = r0[j].x;
                 c_vb = r0[j].y;
-                c_ve = r0[j].z;
-                c_tt = r0[j].w;
+                c_ve = r0[j].y + (r1[j].x >> 24);
+                c_tt = r0[j].z;
                 c_w = wv[j];
             }
         c_h = __shfl_sync(gmask, c_h, pick_lane, G);
