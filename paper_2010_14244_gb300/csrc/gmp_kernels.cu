@@ -305,6 +305,10 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             done = true;
             status = kAntStepCap;
         }
+        if (active && !done && end == beg) {  // a node without out-roads ends the walk here
+            done = true;
+            status = kAntDeadEnd;
+        }
         const bool stepping = active && !done;
         const uint32_t deg = stepping ? end - beg : 0u;
         const int nslots = K == 1 ? 1 : (int)__reduce_max_sync(FULL, (deg + G - 1) / G);  // warp-uniform
@@ -548,6 +552,10 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
         } else if (active && steps == a.max_steps) {
             done = true;
             status = kAntStepCap;
+        }
+        if (active && !done && end == beg) {  // a node without out-roads ends the walk here
+            done = true;
+            status = kAntDeadEnd;
         }
         const bool stepping = active && !done;
         const uint32_t deg = stepping ? end - beg : 0u;

@@ -274,3 +274,30 @@ def test_memory_budget(gm, orc):
         c.solve_batch(wl.queries)
     assert e.value.code == gm.ERR_OOM
     c.close()
+
+
+@pytest.mark.parametrize("sched", ["lanes1", "lanes4", "lanes8", "lanes16", "lanes32", "persistent"])
+def test_directed_graph_with_sinks(gm, ctx, orc, sched):
+    """One-way roads and nodes without out-roads: ants that reach a sink end as dead ends (Fig. 3 gives
+    an ant no way out of such a node), under every kernel shape, including warps whose every ant sits at
+    a sink in the same step."""
+    rng = np.random.default_rng(17)
+    roads = []
+    for u in range(45):
+        for v in rng.choice(60, size=int(rng.integers(1, 4)), replace=False):
+            if v != u:
+                roads.append((u, int(v), int(rng.integers(300, 3000)), 50, 3, int(rng.integers(0, 2))))
+    sigs = {v: (30_000, int(rng.integers(0, 30_000)), [18_000, 12_000]) for v in range(0, 60, 4)}
+    net, sig, veh = NB.build(60, roads, signals=sigs, bidirectional=False)
+    veh[:] = rng.integers(0, 20, size=veh.size)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    kw = dict(mode=2, lanes_per_ant=8) if sched == "persistent" else dict(mode=1, lanes_per_ant=int(sched[5:]))
+    ctx.set_params(**kw)
+    qs = [Q(s, d, 48, 5, 1.0, 2.0, 0.1, 100 + i) for i, (s, d) in enumerate([(0, 50), (3, 44), (7, 59), (10, 20)])]
+    res = ctx.solve_batch(qs)
+    onet = orc.Net(net, sig, veh)
+    for i, q in enumerate(qs):
+        o = _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
+        assert o["n_success"] < q.n_ants * q.n_iter  # some ants die at sinks or dead ends
