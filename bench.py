@@ -137,6 +137,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value over the ranks (the slowest rank's time); NCCL ranks reduce on their GPU."""
+    if world <= 1:
+        return x
+    import torch
+
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------------------------------ CPU oracle
 _WL = None
 
@@ -300,11 +312,7 @@ def run_gpu(args, rank, world, local_rank):
     times_k, kt = timed_region(gmacop.FLAG_KERNEL_TIMING)
     res2 = ctx.collect()
     assert [r["travel_ms"] for r in res2] == [r["travel_ms"] for r in res]
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), world)
 
     # the plain form: each colony its own job (stage, launch, collect), one after another
     plain = None
