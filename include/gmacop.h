@@ -187,6 +187,26 @@ int gmp_autotune(gmp_ctx *ctx, uint32_t n, const gmp_query *probe, uint32_t prob
 void gmp_autotune_reset(void);
 
 /* ---------------------------------------------------------------------------------------------- */
+/* Many road graphs in one launch (the ragged multi-graph batch; the paper solves one graph).         */
+/* ---------------------------------------------------------------------------------------------- */
+typedef struct gmp_multi gmp_multi;
+
+/* A handle that launches the staged jobs of several contexts (each holding its own road graph, on the
+ * handle's device) as one captured CUDA graph on a stream of its own. Errors: INVALID_ARG, CUDA. */
+int gmp_multi_create(gmp_multi **out, int device);
+void gmp_multi_destroy(gmp_multi *multi);
+const char *gmp_multi_last_error(const gmp_multi *multi);
+
+/* Launch the batches staged on ctxs[0..n) (gmp_batch_stage on each first; iterative mode) together: one
+ * fork per context into its own concurrent colony chains, one join, one graph launch. The capture is kept
+ * and replayed while the same contexts keep batches of the same shape. The launch is ordered after work
+ * already queued on every context's stream, and every context's stream is ordered after the launch, so
+ * gmp_batch_ready and gmp_batch_collect are then used per context as after gmp_batch_launch. Each result
+ * equals that of its batch launched alone. Asynchronous. A context may appear once.
+ * Errors: INVALID_ARG, STATE (a context without a staged batch), UNSUPPORTED (persistent mode), CUDA. */
+int gmp_multi_launch(gmp_multi *multi, gmp_ctx *const *ctxs, uint32_t n);
+
+/* ---------------------------------------------------------------------------------------------- */
 /* Route server: continuous batching over several contexts (no counterpart in the paper, which routes */
 /* one vehicle at a time in Fig. 3).                                                                  */
 /* ---------------------------------------------------------------------------------------------- */

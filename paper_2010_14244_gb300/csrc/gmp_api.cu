@@ -1000,11 +1000,11 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     return GMP_OK;
 }
 
-int gmp_batch_launch(gmp_ctx* c) {
-    if (!c) return GMP_ERR_INVALID_ARG;
+namespace {
+
+// Per-kernel timing events for the staged job (created when the timing flag is set).
+int prepare_events(gmp_ctx* c) {
     Batch& b = c->b;
-    if (!b.staged) return fail(c, GMP_ERR_STATE, "stage a batch first");
-    cudaSetDevice(c->device);
     const bool timed = (c->prm.flags & kFlagKernelTiming) != 0;
     const size_t n_ev = timed ? job_event_count(b) : 0;
     if (b.ev.size() != n_ev || b.timed != timed) {
@@ -1014,6 +1014,27 @@ int gmp_batch_launch(gmp_ctx* c) {
         for (size_t i = 0; i < n_ev; ++i) GMP_CUDA(c, cudaEventCreate(&b.ev[i]));
         b.timed = timed;
     }
+    return GMP_OK;
+}
+
+// The staged job was launched (by itself or inside a multi-graph launch): mark its completion point
+// on the context's stream.
+int mark_launched(gmp_ctx* c) {
+    Batch& b = c->b;
+    if (!b.done) GMP_CUDA(c, cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+    GMP_CUDA(c, cudaEventRecord(b.done, c->stream));
+    b.ran = true;
+    return GMP_OK;
+}
+
+}  // namespace
+
+int gmp_batch_launch(gmp_ctx* c) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    Batch& b = c->b;
+    if (!b.staged) return fail(c, GMP_ERR_STATE, "stage a batch first");
+    cudaSetDevice(c->device);
+    GMP_TRY(prepare_events(c));
     if (c->prm.flags & kFlagNoGraph) {
         GMP_TRY(enqueue_job(c));
     } else {
@@ -1037,10 +1058,7 @@ int gmp_batch_launch(gmp_ctx* c) {
         }
         GMP_CUDA(c, cudaGraphLaunch(b.exec, c->stream));
     }
-    if (!b.done) GMP_CUDA(c, cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
-    GMP_CUDA(c, cudaEventRecord(b.done, c->stream));
-    b.ran = true;
-    return GMP_OK;
+    return mark_launched(c);
 }
 
 int gmp_batch_collect(gmp_ctx* c, gmp_result* results) {
@@ -1216,6 +1234,171 @@ int gmp_get_kernel_times(gmp_ctx* c, float* out) {
 int gmp_get_launch_count(const gmp_ctx* c, uint64_t* out) {
     if (!c || !out) return GMP_ERR_INVALID_ARG;
     *out = c->b.launches;
+    return GMP_OK;
+}
+
+}  // extern "C"
+
+// =====================================================================================================
+// gmp_multi: the staged jobs of several contexts (one road graph each) as one captured launch.
+// =====================================================================================================
+struct gmp_multi {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> joins, pre;
+    cudaGraphExec_t exec = nullptr;
+    struct Member {
+        gmp_ctx* c;
+        cudaStream_t st;
+        BatchKey key;
+        std::vector<Batch::Branch> plan;
+    };
+    std::vector<Member> members;  // what `exec` was captured from
+    std::string err;
+};
+
+namespace {
+
+int mfail(gmp_multi* m, int code, const std::string& msg) {
+    m->err = msg;
+    return code;
+}
+
+bool same_members(const gmp_multi* m, gmp_ctx* const* ctxs, uint32_t n) {
+    if (m->members.size() != n) return false;
+    for (uint32_t i = 0; i < n; ++i) {
+        const gmp_multi::Member& x = m->members[i];
+        if (x.c != ctxs[i] || x.st != ctxs[i]->stream || !(x.key == key_of(ctxs[i])) ||
+            !same_plan(x.plan, ctxs[i]->b.br))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gmp_multi_create(gmp_multi** out, int device) {
+    if (!out) return GMP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return GMP_ERR_CUDA;
+    }
+    gmp_multi* m = new gmp_multi();
+    m->device = device;
+    if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        gmp_multi_destroy(m);
+        return GMP_ERR_CUDA;
+    }
+    *out = m;
+    return GMP_OK;
+}
+
+void gmp_multi_destroy(gmp_multi* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    for (cudaEvent_t e : m->joins) cudaEventDestroy(e);
+    for (cudaEvent_t e : m->pre) cudaEventDestroy(e);
+    if (m->fork) cudaEventDestroy(m->fork);
+    if (m->done) cudaEventDestroy(m->done);
+    if (m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+const char* gmp_multi_last_error(const gmp_multi* m) { return m ? m->err.c_str() : "null handle"; }
+
+int gmp_multi_launch(gmp_multi* m, gmp_ctx* const* ctxs, uint32_t n) {
+    if (!m || !ctxs || n == 0) return GMP_ERR_INVALID_ARG;
+    cudaSetDevice(m->device);
+    for (uint32_t i = 0; i < n; ++i) {
+        gmp_ctx* c = ctxs[i];
+        if (!c) return mfail(m, GMP_ERR_INVALID_ARG, "null context");
+        if (c->device != m->device) return mfail(m, GMP_ERR_INVALID_ARG, "contexts must be on the handle's device");
+        if (!c->b.staged) return mfail(m, GMP_ERR_STATE, "every context needs a staged batch");
+        if (c->b.persistent) return mfail(m, GMP_ERR_UNSUPPORTED, "the multi-graph launch runs iterative jobs");
+        for (uint32_t j = 0; j < i; ++j)
+            if (ctxs[j] == c) return mfail(m, GMP_ERR_INVALID_ARG, "a context appears twice");
+        const int rc = prepare_events(c);
+        if (rc != GMP_OK) return mfail(m, rc, c->err);
+        const int rb = ensure_branch_streams(c, c->b.br.size() > 1 ? c->b.br.size() : 0);
+        if (rb != GMP_OK) return mfail(m, rb, c->err);
+    }
+    while (m->joins.size() < n) {
+        cudaEvent_t e = nullptr, p = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (e) cudaEventDestroy(e);
+            return mfail(m, GMP_ERR_CUDA, "cudaEventCreate failed");
+        }
+        m->joins.push_back(e);
+        m->pre.push_back(p);
+    }
+    if (!m->exec || !same_members(m, ctxs, n)) {
+        if (m->exec) {
+            cudaGraphExecDestroy(m->exec);
+            m->exec = nullptr;
+        }
+        m->members.clear();
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return mfail(m, GMP_ERR_CUDA, cudaGetErrorString(ce));
+        int rc = cudaEventRecord(m->fork, m->stream) == cudaSuccess ? GMP_OK : GMP_ERR_CUDA;
+        for (uint32_t i = 0; i < n && rc == GMP_OK; ++i) {
+            gmp_ctx* c = ctxs[i];
+            if (cudaStreamWaitEvent(c->stream, m->fork, 0) != cudaSuccess) {
+                rc = GMP_ERR_CUDA;
+                break;
+            }
+            rc = enqueue_job(c);
+            if (rc != GMP_OK) {
+                m->err = c->err;
+                break;
+            }
+            if (cudaEventRecord(m->joins[i], c->stream) != cudaSuccess ||
+                cudaStreamWaitEvent(m->stream, m->joins[i], 0) != cudaSuccess)
+                rc = GMP_ERR_CUDA;
+        }
+        ce = cudaStreamEndCapture(m->stream, &g);
+        if (rc != GMP_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return mfail(m, rc != GMP_OK ? rc : GMP_ERR_CUDA, rc != GMP_OK ? m->err : cudaGetErrorString(ce));
+        }
+        ce = cudaGraphInstantiate(&m->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            m->exec = nullptr;
+            return mfail(m, GMP_ERR_CUDA, cudaGetErrorString(ce));
+        }
+        for (uint32_t i = 0; i < n; ++i)
+            m->members.push_back(gmp_multi::Member{ctxs[i], ctxs[i]->stream, key_of(ctxs[i]), ctxs[i]->b.br});
+    }
+    // the launch waits for work already queued on every context's stream; each context's stream then
+    // waits for the launch, so gmp_batch_ready / gmp_batch_collect work per context as usual
+    for (uint32_t i = 0; i < n; ++i) {
+        if (cudaEventRecord(m->pre[i], ctxs[i]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(m->stream, m->pre[i], 0) != cudaSuccess)
+            return mfail(m, GMP_ERR_CUDA, "ordering after the contexts' streams failed");
+    }
+    cudaError_t le = cudaGraphLaunch(m->exec, m->stream);
+    if (le != cudaSuccess) return mfail(m, GMP_ERR_CUDA, cudaGetErrorString(le));
+    if (cudaEventRecord(m->done, m->stream) != cudaSuccess) return mfail(m, GMP_ERR_CUDA, "event record failed");
+    for (uint32_t i = 0; i < n; ++i) {
+        gmp_ctx* c = ctxs[i];
+        if (cudaStreamWaitEvent(c->stream, m->done, 0) != cudaSuccess)
+            return mfail(m, GMP_ERR_CUDA, "ordering the contexts after the launch failed");
+        const int rc = mark_launched(c);
+        if (rc != GMP_OK) return mfail(m, rc, c->err);
+    }
     return GMP_OK;
 }
 

@@ -96,6 +96,10 @@ SIGNATURES = {
     "gmp_autotune": (_i32, [_vp, _u32, C.POINTER(Query), _u32, C.POINTER(TuneResult)]),
     "gmp_autotune_reset": (None, []),
     "gmp_batch_reserve": (_i32, [_vp, _u32, _u64, _u32]),
+    "gmp_multi_create": (_i32, [C.POINTER(_vp), _i32]),
+    "gmp_multi_destroy": (None, [_vp]),
+    "gmp_multi_last_error": (C.c_char_p, [_vp]),
+    "gmp_multi_launch": (_i32, [_vp, C.POINTER(_vp), _u32]),
     "gmp_batch_ready": (_i32, [_vp, C.POINTER(C.c_int)]),
     "gmp_server_create": (_i32, [C.POINTER(_vp), C.POINTER(_vp), _u32, C.POINTER(ServerConfig)]),
     "gmp_server_destroy": (None, [_vp]),
@@ -417,3 +421,37 @@ class Server:
                                 best_ant=r.best_ant, route=route))
             if n.value == 0:
                 return out
+
+
+class Multi:
+    """gmp_multi: the staged batches of several contexts (one road graph each) in one launch."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        rc = lib().gmp_multi_create(C.byref(self._h), device)
+        if rc != OK:
+            raise GmpError(rc, "gmp_multi_create failed")
+
+    def close(self):
+        if self._h:
+            lib().gmp_multi_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch(self, contexts):
+        arr = (_vp * len(contexts))(*[c._h.value for c in contexts])
+        rc = lib().gmp_multi_launch(self._h, arr, len(contexts))
+        if rc != OK:
+            raise GmpError(rc, lib().gmp_multi_last_error(self._h).decode())
+
+    def solve(self, contexts, batches, route_cap=None) -> list[list[dict]]:
+        """Stage batches[i] on contexts[i], launch all in one go, collect every context's results."""
+        for c, qs in zip(contexts, batches):
+            c.stage(qs)
+        self.launch(contexts)
+        return [c.collect(route_cap) for c in contexts]

@@ -334,6 +334,27 @@ def geo100k(n_queries=512, n_ants=256, n_iter=100) -> Workload:
                     "100k-node jittered-lattice planar graph, 60% signalised, Poisson(1) vehicles/road")
 
 
+def city_batch(n_graphs=64, n_min=1000, n_max=200_000, q_lo=8, q_hi=64, ants_lo=128, ants_hi=1024, n_iter=50,
+               seed=4) -> list[Workload]:
+    """Independent city graphs for one multi-graph launch: node counts log-uniform in [n_min, n_max] (same
+    planar generator as geo100k, avg out-degree 2.8, 60% signalised), mean density U[0.5, 3] vehicles per
+    road (Poisson), q_lo..q_hi uniform OD queries per graph with ants_lo..ants_hi ants each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for g in range(n_graphs):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        rows = max(2, int(np.sqrt(n)))
+        cols = max(2, n // rows)
+        net = geometric_network(rows, cols, rng)
+        sig = two_phase_signals(net, rng.random(net.n_nodes) < 0.6, rng)
+        veh = vehicles_poisson(net.n_edges, float(rng.uniform(0.5, 3.0)), rng)
+        nq = int(rng.integers(q_lo, q_hi + 1))
+        qs = [Query(s, d, int(rng.integers(ants_lo, ants_hi + 1)), n_iter, 1.0, 2.0, 0.1, 1000 * g + i)
+              for i, (s, d) in enumerate(uniform_od(net.n_nodes, nq, rng))]
+        out.append(Workload(f"city{g}", net, sig, veh, qs, f"{net.n_nodes}-node planar city graph"))
+    return out
+
+
 def random_small(n_nodes, n_undirected, rng, signalised_frac=0.0, len_lo=1000, len_hi=5000,
                  spacing_dm=1000) -> tuple[RoadNetwork, SignalTiming]:
     """Small connected random road graph on a sparse lattice layout (for brute-force checks)."""
