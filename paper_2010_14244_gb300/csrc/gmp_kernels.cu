@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
 // of them (a warp whose groups wander apart would issue each group's instructions separately). Row
 // loads stay coalesced within a group. Shuffles run on the full warp with width G. A group whose ant
 // ended finalises it (deposits and bitmap reset spread over its G lanes) and takes a new ant; new ants
-// come from one warp-aggregated atomic per round.
+// come from one warp-aggregated atomic per round. The loads of an ant's next row are issued as soon as
+// it moves, so their latency overlaps the end of the step and the loop's bookkeeping.
 // ------------------------------------------------------------------------------------------------
 template <int G, int K, bool SMEM>
 __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t it) {
@@ -245,10 +246,15 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     bool rb_valid = false;
     const uint2* th = a.th;
     uint32_t* route = a.routes;
+    bool want = true;  // warp-uniform: some group may need a ticket (at the start, after an ant ended)
+    // the next step's candidate loads, issued as soon as the ant moves (software pipelining)
+    uint4 p0[K], p1[K];
+    uint2 pth[K];
+    bool pre = false;
     for (;;) {
         // 1. groups without an ant take the next tickets (one atomic for the whole warp)
         const bool need = !active && !exhausted;
-        const uint32_t nmask = __ballot_sync(FULL, need && leader);
+        const uint32_t nmask = want ? __ballot_sync(FULL, need && leader) : 0u;
         if (nmask) {
             const int first = __ffs(nmask) - 1;
             uint32_t base = 0;
@@ -288,14 +294,18 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         end = __ldg(a.row_ptr + u + 1);
                         t = W = steps = 0;
                         rb_valid = false;
+                        pre = false;
                         if (leader) atomicOr(tabu + (u >> 5), 1u << (u & 31));
                     }
                 }
             }
             __syncwarp();
         }
-        if (!__any_sync(FULL, active || !exhausted)) break;
-        if (!__any_sync(FULL, active)) continue;
+        if (want) want = __any_sync(FULL, !active && !exhausted);  // tickets of colonies without work
+        if (!__any_sync(FULL, active)) {
+            if (want) continue;
+            break;  // no ant and no tickets left
+        }
         // 2. one step of every active ant
         bool done = false;
         if (active && u == dst) {
@@ -312,7 +322,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
         const bool stepping = active && !done;
         const uint32_t deg = stepping ? end - beg : 0u;
         const int nslots = K == 1 ? 1 : (int)__reduce_max_sync(FULL, (deg + G - 1) / G);  // warp-uniform
-        if (__any_sync(FULL, deg > 0u)) {
+        {  // runs for every warp with an active ant (a warp whose ants all just ended masks everything)
             uint4 r0[K], r1[K];
             float tf[K];
             uint32_t he[K];
@@ -322,11 +332,18 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 const uint32_t idx = lane + (uint32_t)j * G;
                 const bool ok = j < nslots && idx < deg;
                 valid |= (ok ? 1u : 0u) << j;
-                const uint32_t e = ok ? beg + idx : 0u;
-                const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
-                r0[j] = __ldg(rp);
-                r1[j] = __ldg(rp + 1);
-                const uint2 ph = __ldg(th + e);
+                uint2 ph;
+                if (pre) {
+                    r0[j] = p0[j];
+                    r1[j] = p1[j];
+                    ph = pth[j];
+                } else {
+                    const uint32_t e = ok ? beg + idx : 0u;
+                    const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+                    r0[j] = __ldg(rp);
+                    r1[j] = __ldg(rp + 1);
+                    ph = __ldg(th + e);
+                }
                 tf[j] = __uint_as_float(ph.x);
                 he[j] = ph.y;
             }
@@ -421,11 +438,25 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                     done = true;
                     status = kAntTimeCap;
                 }
+#pragma unroll
+                for (int j = 0; j < K; ++j) {  // the rows of the next step, read past the masked slots as road 0
+                    const uint32_t idx = lane + (uint32_t)j * G;
+                    const uint32_t e = idx < end - beg ? beg + idx : 0u;
+                    const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+                    p0[j] = __ldg(rp);
+                    p1[j] = __ldg(rp + 1);
+                    pth[j] = __ldg(th + e);
+                }
+                pre = true;
+            } else {
+                pre = false;
             }
             __syncwarp();
         }
         // 3. ants that ended: the group records, deposits and resets its bitmap
-        if (__any_sync(FULL, done)) {
+        const bool any_done = __any_sync(FULL, done);
+        want = want || any_done;
+        if (any_done) {
             if (done) {
                 QueryState* S = a.qs + qi;
                 if (leader) {
