@@ -222,7 +222,7 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------------------------ serving
-SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S = 4, 1500.0, 2.0, 0.5
+SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S, SERVE_MAX_BATCH = 16, 5000.0, 2.0, 0.5, 64
 SERVE_ANTS, SERVE_ITERS = 128, 30
 
 
@@ -231,7 +231,7 @@ def serving_leg(wl):
     128 ants x 30 iterations each, traffic ticks every second, continuous batching over slot contexts."""
     from paper_2010_14244_gb300 import serving
 
-    srv, slots = serving.make_server(wl, n_slots=SERVE_SLOTS, max_batch=256, max_ants=SERVE_ANTS,
+    srv, slots = serving.make_server(wl, n_slots=SERVE_SLOTS, max_batch=SERVE_MAX_BATCH, max_ants=SERVE_ANTS,
                                      max_iter=SERVE_ITERS)
     try:
         make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=5)

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <string>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -24,13 +25,14 @@ using namespace gmp;
 namespace {
 
 constexpr uint32_t kFlagKernelTiming = 4u;  // event records around every kernel of the job
-constexpr uint32_t kFlagNoGraph = 8u;        // issue the job kernel by kernel instead of replaying a graph
+constexpr uint32_t kFlagNoGraph = kFlagNoGraphBit;  // issue the job kernel by kernel instead of replaying a graph
 constexpr uint32_t kFlagNoLockstep = kFlagNoLockstepBit;  // sub-warp ants without warp lockstep
 constexpr uint32_t kKnownFlags =
     GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
 constexpr int32_t kCoordLimit = 1 << 27;
 constexpr uint64_t kTickClockMax = 1ull << 48;  // lanes * (t + dt) stays below 2^64
 constexpr uint32_t kDefaultBranches = 16;        // concurrent colony chains of an iterative job
+constexpr size_t kMaxCachedGraphs = 32;          // executable graphs kept per context, by topology
 constexpr uint32_t kMaxBranches = 64;
 constexpr uint32_t kTickDtMax = 1u << 30;
 
@@ -71,7 +73,8 @@ struct Batch {
     uint32_t* qflag = nullptr;
     uint32_t* misc = nullptr;
     // captured job
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec = nullptr;  // the executable graph of the staged job (one of `execs`)
+    std::map<std::vector<uint32_t>, cudaGraphExec_t> execs;  // by topology, refreshed by graph update
     BatchKey key{};
     uint64_t launches = 0;
     std::vector<cudaEvent_t> ev;
@@ -86,6 +89,21 @@ struct Batch {
     std::vector<Branch> br;
     std::vector<Branch> exec_br;  // the chain plan baked into `exec`
 };
+
+// What fixes the node structure of a captured job: the job form, timing events, the chains with their
+// iteration counts and kernel shapes. Jobs with equal topology differ only in kernel parameters.
+std::vector<uint32_t> topology_of(const Batch& b) {
+    std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, (uint32_t)b.br.size(), b.maxI,
+                            (uint32_t)b.kc.lanes, (uint32_t)b.kc.slots, b.kc.lockstep ? 1u : 0u,
+                            b.kc.tabu_in_smem ? 1u : 0u, (uint32_t)b.kc.block};
+    for (const Batch::Branch& r : b.br) {
+        t.push_back(r.maxI);
+        t.push_back((uint32_t)r.kc.lanes | (uint32_t)r.kc.slots << 8 | (r.kc.lockstep ? 1u << 16 : 0u) |
+                    (r.kc.tabu_in_smem ? 1u << 17 : 0u));
+        t.push_back((uint32_t)r.kc.block);
+    }
+    return t;
+}
 
 bool same_plan(const std::vector<Batch::Branch>& x, const std::vector<Batch::Branch>& y) {
     if (x.size() != y.size()) return false;
@@ -229,10 +247,9 @@ int upload(gmp_ctx* c, T* d, const T* h, size_t n) {
 }
 
 void drop_graph(Batch& b) {
-    if (b.exec) {
-        cudaGraphExecDestroy(b.exec);
-        b.exec = nullptr;
-    }
+    for (auto& kv : b.execs) cudaGraphExecDestroy(kv.second);
+    b.execs.clear();
+    b.exec = nullptr;
     b.key = BatchKey{};
 }
 
@@ -1040,7 +1057,9 @@ int gmp_batch_launch(gmp_ctx* c) {
     } else {
         const BatchKey k = key_of(c);
         if (!b.exec || !(b.key == k) || !same_plan(b.br, b.exec_br)) {
-            drop_graph(b);
+            // capture the job; an executable graph of the same topology (chain count, iterations per
+            // chain, kernel shapes) is updated in place with the new parameters, which costs far less
+            // than instantiating one (jobs of a server change shape with every batch)
             cudaGraph_t g = nullptr;
             GMP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             const int rc = enqueue_job(c);
@@ -1050,9 +1069,30 @@ int gmp_batch_launch(gmp_ctx* c) {
                 return rc;
             }
             GMP_CUDA(c, ce);
-            const cudaError_t ie = cudaGraphInstantiate(&b.exec, g, 0);
+            const std::vector<uint32_t> sig = topology_of(b);
+            b.exec = nullptr;
+            auto hit = b.execs.find(sig);
+            if (hit != b.execs.end()) {
+                cudaGraphExecUpdateResultInfo info{};
+                if (cudaGraphExecUpdate(hit->second, g, &info) == cudaSuccess) {
+                    b.exec = hit->second;
+                } else {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(hit->second);
+                    b.execs.erase(hit);
+                }
+            }
+            if (!b.exec) {
+                if (b.execs.size() >= kMaxCachedGraphs) drop_graph(b);
+                const cudaError_t ie = cudaGraphInstantiate(&b.exec, g, 0);
+                if (ie != cudaSuccess) {
+                    b.exec = nullptr;
+                    cudaGraphDestroy(g);
+                    GMP_CUDA(c, ie);
+                }
+                b.execs[sig] = b.exec;
+            }
             cudaGraphDestroy(g);
-            GMP_CUDA(c, ie);
             b.key = k;
             b.exec_br = b.br;
         }

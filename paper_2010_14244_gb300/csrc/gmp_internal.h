@@ -139,6 +139,7 @@ int construct_max_degree(int lanes);
 bool construct_thread_fits(uint32_t n_nodes);
 
 // Context internals for the host-side layers built on the C ABI (autotuner, server) (gmp_api.cu).
+constexpr uint32_t kFlagNoGraphBit = 8u;      // params.flags bit: launch kernel by kernel, no graph capture
 constexpr uint32_t kFlagNoLockstepBit = 16u;  // params.flags bit: free-running groups instead of lockstep
 struct CtxInfo {
     int device;
