@@ -88,6 +88,7 @@ struct Batch {
     };
     std::vector<Branch> br;
     std::vector<Branch> exec_br;  // the chain plan baked into `exec`
+    size_t tabu_used = 0;         // words of the global visited-bitmap pool this job uses
 };
 
 // What fixes the node structure of a captured job: the job form, timing events, the chains with their
@@ -406,6 +407,7 @@ int enqueue_persistent(gmp_ctx* c) {
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
                                   b.dep, b.qs, b.tickets, b.maxI));
     GMP_CUDA(c, launch_persistent_init(s, b.Q, b.maxI, b.dq, b.ctr, b.qstate, b.qflag, b.misc));
+    if (b.tabu && b.tabu_used) GMP_CUDA(c, cudaMemsetAsync(b.tabu, 0, b.tabu_used * 4, s));
     if (timed) GMP_TRY(record(c, b, 1));
     PersistentArgs p{};
     p.c = construct_args(c);
@@ -514,6 +516,8 @@ int enqueue_job(gmp_ctx* c) {
                                   b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
+    // global visited bitmaps start clean; each walk clears its own bits when it ends
+    if (b.tabu && b.tabu_used) GMP_CUDA(c, cudaMemsetAsync(b.tabu, 0, b.tabu_used * 4, s));
     if (B > 1) {
         GMP_TRY(ensure_branch_streams(c, B));
         GMP_CUDA(c, cudaEventRecord(c->bfork, s));
@@ -897,7 +901,11 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
 int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
     Batch& b = c->b;
     b.br.clear();
-    if (b.persistent) return GMP_OK;
+    b.tabu_used = 0;
+    if (b.persistent) {
+        if (!b.kc.tabu_in_smem) b.tabu_used = (size_t)b.kc.grid * (b.kc.block / b.kc.lanes) * ((c->N + 31u) / 32u);
+        return GMP_OK;
+    }
     const uint32_t B = branch_count(c, b.Q);
     const size_t words = (c->N + 31u) / 32u;
     size_t off = 0;
@@ -920,6 +928,7 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
         if (!r.kc.tabu_in_smem) off += (size_t)r.kc.grid * (r.kc.block / r.kc.lanes) * words;
         b.br.push_back(r);
     }
+    b.tabu_used = off;
     return GMP_OK;
 }
 
@@ -1559,6 +1568,8 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     // init clears the pheromone, deposits, colony state and ticket counters left by the previous call
     GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, th, dep,
                                   qs, tickets, n_iter));
+    if (tabu)  // global visited bitmaps start clean; each walk clears its own bits when it ends
+        GMP_CUDA(c, cudaMemsetAsync(tabu, 0, (size_t)kc.grid * (kc.block / kc.lanes) * words * 4, s));
     ConstructArgs a{};
     a.rec = c->rec;
     a.row_ptr = c->row_ptr;

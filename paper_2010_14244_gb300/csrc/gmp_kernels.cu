@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
     const uint32_t groups = blockDim.x / G;
     uint32_t* tabu = SMEM ? smem + (size_t)gib * a.tabu_words
                           : a.tabu_global + ((size_t)blockIdx.x * groups + gib) * a.tabu_words;
-    for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+    // shared bitmaps start uncleared; global ones are cleared once per job and every walk clears its
+    // own bits when it ends
+    if (SMEM)
+        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
     __syncwarp(gmask);
     for (;;) {
         uint32_t ticket = 0;
@@ -234,7 +237,10 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     const bool leader = lane == 0;
     uint32_t* const tabu = SMEM ? smem + (size_t)gib * a.tabu_words
                                 : a.tabu_global + ((size_t)blockIdx.x * groups + gib) * a.tabu_words;
-    for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+    // shared bitmaps start uncleared; global ones are cleared once per job and every walk clears its
+    // own bits when it ends
+    if (SMEM)
+        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
     __syncwarp();
     const uint32_t lt_mask = (1u << wl) - 1u;
     bool active = false, exhausted = false;

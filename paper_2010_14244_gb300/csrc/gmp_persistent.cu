@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
     const uint32_t groups = blockDim.x / G;
     uint32_t* tabu = SMEM ? smem + (size_t)gib * a.tabu_words
                           : a.tabu_global + ((size_t)blockIdx.x * groups + gib) * a.tabu_words;
-    for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+    if (SMEM)  // global bitmaps are cleared once per job; every walk clears its own bits when it ends
+        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
     __syncwarp(gmask);
     const uint32_t Q = a.n_queries, E = a.n_edges;
     const uint32_t n_edge_chunks = (E + kEdgeChunk - 1) / kEdgeChunk;
