@@ -269,7 +269,7 @@ def run_gpu(args, rank, world, local_rank):
     else:
         ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes)
     sched = {k: v for k, v in ctx.get_params().items()
-             if k in ("mode", "lanes_per_ant", "queue_chunk", "branches", "flags")}
+             if k in ("mode", "lanes_per_ant", "queue_chunk", "branches", "tau_layout", "flags")}
 
     def timed_region(flags):
         """K steps, each bracketed by CUDA events on the library's stream, L2 flushed in between."""
@@ -373,7 +373,8 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
         "config": dict(workload_config(wl), l2="flushed between timed steps (256 MB write)",
-                       schedule={k: sched[k] for k in ("mode", "lanes_per_ant", "queue_chunk", "branches")},
+                       schedule={k: sched[k] for k in ("mode", "lanes_per_ant", "queue_chunk", "branches",
+                                                        "tau_layout")},
                        lockstep=None if tune is None else tune["lockstep"],
                        schedule_source="autotuned" if tune is not None else "command line"),
         "queries_per_s": world * nq * K / (total_ms / 1e3),

@@ -63,7 +63,16 @@ typedef struct {
                                32 or 64 */
     uint32_t branches;      /* iterative mode: the colonies are split into this many contiguous ranges that
                                run as concurrent chains of launches; 0 = min(colonies, 16), at most 64 */
+    uint32_t tau_layout;    /* pheromone tables: GMP_TAU_AUTO, GMP_TAU_DENSE or GMP_TAU_SPARSE (same results) */
 } gmp_params;
+
+/* Pheromone layouts. Dense: every road's pheromone is evaporated every iteration. Sparse: roads that never
+ * received a deposit all hold one value per colony (the baseline, evaporated once per iteration) and only
+ * roads with deposits are evaporated one by one; iterative mode with the constant initial pheromone only.
+ * AUTO takes sparse for graphs of at least 65536 roads when it applies, dense otherwise. */
+#define GMP_TAU_AUTO 0u
+#define GMP_TAU_DENSE 1u
+#define GMP_TAU_SPARSE 2u
 
 /* One origin-destination colony. alpha, beta: integers in [0, 8]; rho in [0, 1). */
 typedef struct {

@@ -33,12 +33,13 @@ constexpr int32_t kCoordLimit = 1 << 27;
 constexpr uint64_t kTickClockMax = 1ull << 48;  // lanes * (t + dt) stays below 2^64
 constexpr uint32_t kDefaultBranches = 16;        // concurrent colony chains of an iterative job
 constexpr size_t kMaxCachedGraphs = 32;          // executable graphs kept per context, by topology
+constexpr uint32_t kSparseMinEdges = 1u << 16;   // GMP_TAU_AUTO: sparse pheromone from this many roads
 constexpr uint32_t kMaxBranches = 64;
 constexpr uint32_t kTickDtMax = 1u << 30;
 
 struct BatchKey {
     uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0,
-             chunk = 0, branches = 0, pad = 0;
+             chunk = 0, branches = 0, sparse = 0;
     uint64_t log_entries = 0;
     const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
@@ -53,7 +54,11 @@ struct Batch {
     // device workspace
     DevQuery* dq = nullptr;
     uint32_t* prefix = nullptr;
-    uint64_t* tau = nullptr;
+    uint64_t* tau = nullptr;      // dense layout: Q * E
+    bool sparse = false;          // sparse layout: baseline + registered roads (see EdgeRec notes)
+    uint32_t* tflag = nullptr;    // sparse: Q * tflag_words registered-road bitmap
+    uint32_t* list_e = nullptr;   // sparse: Q * E registered roads
+    uint64_t* list_tau = nullptr; // sparse: Q * E their pheromone
     uint2* th = nullptr;  // per (colony, road): pheromone as binary32 bits, heuristic (ms)
     unsigned long long* dep = nullptr;
     QueryState* qs = nullptr;
@@ -271,6 +276,9 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.prefix);
     dfree(c, &b.tau);
     dfree(c, &b.th);
+    dfree(c, &b.tflag);
+    dfree(c, &b.list_e);
+    dfree(c, &b.list_tau);
     dfree(c, &b.dep);
     dfree(c, &b.qs);
     dfree(c, &b.routes);
@@ -331,6 +339,16 @@ int refresh_dynamic(gmp_ctx* c) {
 int sync(gmp_ctx* c) {
     GMP_CUDA(c, cudaStreamSynchronize(c->stream));
     return GMP_OK;
+}
+
+uint32_t tflag_words(const gmp_ctx* c) { return (c->E + 31u) / 32u; }
+
+// The pheromone layout of the next job (results are the same in both).
+bool use_sparse(const gmp_ctx* c) {
+    if (c->prm.mode == GMP_MODE_PERSISTENT || (c->prm.flags & GMP_FLAG_RANDOM_TAU)) return false;
+    if (c->prm.tau_layout == GMP_TAU_SPARSE) return true;
+    if (c->prm.tau_layout == GMP_TAU_DENSE) return false;
+    return c->E >= kSparseMinEdges;
 }
 
 uint32_t default_max_steps(const gmp_ctx* c) {
@@ -405,7 +423,7 @@ int enqueue_persistent(gmp_ctx* c) {
     const bool timed = b.timed;
     if (timed) GMP_TRY(record(c, b, 0));
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
-                                  b.dep, b.qs, b.tickets, b.maxI));
+                                  b.dep, b.qs, b.tickets, b.maxI, 0u, nullptr, 0u));
     GMP_CUDA(c, launch_persistent_init(s, b.Q, b.maxI, b.dq, b.ctr, b.qstate, b.qflag, b.misc));
     if (b.tabu && b.tabu_used) GMP_CUDA(c, cudaMemsetAsync(b.tabu, 0, b.tabu_used * 4, s));
     if (timed) GMP_TRY(record(c, b, 1));
@@ -469,6 +487,11 @@ ConstructArgs construct_args(gmp_ctx* c) {
     a.thr_on = c->prm.thr_permille != kThrOff;
     a.tabu_in_smem = b.kc.tabu_in_smem ? 1u : 0u;
     a.kappa = c->kappa;
+    a.sparse = b.sparse ? 1u : 0u;
+    a.tflag_words = tflag_words(c);
+    a.tflag = b.tflag;
+    a.list_e = b.list_e;
+    a.list_tau = b.list_tau;
     return a;
 }
 
@@ -513,7 +536,8 @@ int enqueue_job(gmp_ctx* c) {
     uint64_t n = 0;
     if (timed) GMP_TRY(record(c, b, 0));
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
-                                  b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B));
+                                  b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B, b.sparse ? 1u : 0u, b.tflag,
+                                  tflag_words(c)));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
     // global visited bitmaps start clean; each walk clears its own bits when it ends
@@ -538,6 +562,11 @@ int enqueue_job(gmp_ctx* c) {
         a.dep = b.dep + co;
         a.qs = b.qs + r.q0;
         a.tickets = b.tickets + (size_t)j * b.maxI;
+        if (b.sparse) {
+            a.tflag = b.tflag + (size_t)r.q0 * a.tflag_words;
+            a.list_e = b.list_e + co;
+            a.list_tau = b.list_tau + co;
+        }
         a.tabu_global = b.tabu ? b.tabu + r.tabu_off : nullptr;
         a.n_queries = r.q1 - r.q0;
         a.total_ants = r.ants;
@@ -547,6 +576,11 @@ int enqueue_job(gmp_ctx* c) {
                                       b.routes, b.ant_steps, b.ant_wait, b.best_route + (size_t)r.q0 * b.max_steps,
                                       b.max_steps);
         if (j > 0) e.n_nodes = 0;  // the queue update of an iteration runs once, in the first chain
+        if (b.sparse) {
+            e.sparse = 1;
+            e.list_e = b.list_e + co;
+            e.list_tau = b.list_tau + co;
+        }
         for (uint32_t it = 0; it < r.maxI; ++it) {
             GMP_CUDA(c, launch_construct(bs, r.kc, a, it));
             if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 1 + 2 * it], bs, cudaEventRecordExternal));
@@ -574,6 +608,7 @@ BatchKey key_of(const gmp_ctx* c) {
     k.Q = b.Q;
     k.chunk = c->prm.queue_chunk;
     k.branches = (uint32_t)b.br.size();
+    k.sparse = b.sparse ? 1u : 0u;
     k.maxI = b.maxI;
     k.total_ants = b.total_ants;
     k.max_steps = b.max_steps;
@@ -818,6 +853,7 @@ int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
     if (p->queue_chunk && p->queue_chunk != 8 && p->queue_chunk != 16 && p->queue_chunk != 32 && p->queue_chunk != 64)
         return fail(c, GMP_ERR_INVALID_ARG, "queue_chunk must be 0, 8, 16, 32 or 64");
     if (p->branches > kMaxBranches) return fail(c, GMP_ERR_INVALID_ARG, "branches must be at most 64");
+    if (p->tau_layout > GMP_TAU_SPARSE) return fail(c, GMP_ERR_INVALID_ARG, "unknown tau_layout");
     if (p->max_steps > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "max_steps must be <= 2^24");
     const bool dyn = p->thr_permille != c->prm.thr_permille || p->h_sat_ms != c->prm.h_sat_ms;
     c->prm = *p;
@@ -871,7 +907,13 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
         return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs at least one resident block per colony");
     GMP_TRY(ensure(c, &b.dq, n));
     GMP_TRY(ensure(c, &b.prefix, n + 1));
-    GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
+    if (use_sparse(c)) {
+        GMP_TRY(ensure(c, &b.tflag, (size_t)n * tflag_words(c)));
+        GMP_TRY(ensure(c, &b.list_e, (size_t)n * c->E));
+        GMP_TRY(ensure(c, &b.list_tau, (size_t)n * c->E));
+    } else {
+        GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
+    }
     GMP_TRY(ensure(c, &b.th, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
     GMP_TRY(ensure(c, &b.qs, n));
@@ -1015,6 +1057,9 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.maxI = maxI;
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
     b.persistent = c->prm.mode == GMP_MODE_PERSISTENT;
+    if (c->prm.tau_layout == GMP_TAU_SPARSE && (b.persistent || (c->prm.flags & GMP_FLAG_RANDOM_TAU)))
+        return fail(c, GMP_ERR_UNSUPPORTED, "the sparse pheromone layout needs the iterative job and 1.0 initial pheromone");
+    b.sparse = use_sparse(c);
     GMP_TRY(job_config(c, lanes, b.total_ants, &b.kc));
     GMP_TRY(plan_branches(c, lanes, prefix));
     GMP_TRY(reserve_workspace(c, n, b.total_ants, maxI, b.log_entries, b.kc));
@@ -1176,9 +1221,24 @@ int gmp_get_pheromone(gmp_ctx* c, uint32_t slot, uint64_t* out_tau) {
     if (!c->b.ran) return fail(c, GMP_ERR_STATE, "no batch has run");
     if (slot >= c->b.Q) return fail(c, GMP_ERR_INVALID_ARG, "slot out of range");
     cudaSetDevice(c->device);
-    GMP_CUDA(c, cudaMemcpyAsync(out_tau, c->b.tau + (size_t)slot * c->E, c->E * 8ull, cudaMemcpyDeviceToHost,
-                                c->stream));
-    return sync(c);
+    Batch& b = c->b;
+    if (!b.sparse) {
+        GMP_CUDA(c, cudaMemcpyAsync(out_tau, b.tau + (size_t)slot * c->E, c->E * 8ull, cudaMemcpyDeviceToHost,
+                                    c->stream));
+        return sync(c);
+    }
+    // sparse layout: the baseline on every road, then the registered roads' own values
+    uint64_t* tmp = nullptr;
+    GMP_TRY(dalloc(c, &tmp, c->E));
+    const size_t co = (size_t)slot * c->E;
+    int rc = GMP_OK;
+    if (launch_materialize_tau(c->stream, c->E, b.qs + slot, b.list_e + co, b.list_tau + co, tmp) != cudaSuccess ||
+        cudaMemcpyAsync(out_tau, tmp, c->E * 8ull, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        rc = fail(c, GMP_ERR_CUDA, "reading the sparse pheromone table failed");
+    if (rc == GMP_OK) rc = sync(c);
+    sync(c);
+    dfree(c, &tmp);
+    return rc;
 }
 
 int gmp_get_ant_log(gmp_ctx* c, uint32_t slot, uint32_t* out, uint64_t capacity_entries) {
@@ -1567,7 +1627,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     GMP_CUDA(c, cudaGetLastError());
     // init clears the pheromone, deposits, colony state and ticket counters left by the previous call
     GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, th, dep,
-                                  qs, tickets, n_iter));
+                                  qs, tickets, n_iter, 0u, nullptr, 0u));
     if (tabu)  // global visited bitmaps start clean; each walk clears its own bits when it ends
         GMP_CUDA(c, cudaMemsetAsync(tabu, 0, (size_t)kc.grid * (kc.block / kc.lanes) * words * 4, s));
     ConstructArgs a{};

@@ -59,8 +59,12 @@ struct __align__(16) QueryState {
     uint32_t best_len;            // roads in the best route
     uint32_t best_W;              // waits along the best route
     uint32_t pad[2];
+    // sparse pheromone layout: every road without a deposit so far holds the same value, the baseline
+    unsigned long long base_tau;  // baseline tau of the current iteration (Q32.32)
+    uint32_t base_tf;             // its binary32 image (bits)
+    uint32_t n_touched;           // roads with a deposit so far (entries of the colony's touched list)
 };
-static_assert(sizeof(QueryState) == 48, "QueryState layout");
+static_assert(sizeof(QueryState) == 64, "QueryState layout");
 
 // Result row copied back to the host.
 struct __align__(16) DevResult {

@@ -36,12 +36,22 @@ struct ConstructArgs {
     uint32_t ticket_base;        // job-wide index of this launch's first ant (its colonies are a
                                  // contiguous range: queries, ant_prefix and the per-colony tables
                                  // point at the range's first colony)
+    // sparse pheromone layout (sparse != 0): th[e].x == 0 marks a road without a deposit so far, whose
+    // pheromone is the colony's baseline; a road's first deposit registers it in the colony's list
+    uint32_t sparse;
+    uint32_t tflag_words;        // words per colony of the registered-road bitmap
+    uint32_t* tflag;             // Q * tflag_words
+    uint32_t* list_e;            // Q * E registered roads
+    uint64_t* list_tau;          // Q * E their tau
 };
 
 // Arguments of the fused iteration-end kernel (evaporation + deposits, best route, queue update).
 struct IterEndArgs {
     uint32_t n_queries, n_edges, n_nodes, it, max_steps;
     uint32_t evap_blocks;  // blocks per colony for the evaporation (set by the launcher)
+    uint32_t sparse;       // sparse pheromone layout: evaporate the registered roads and the baseline
+    uint32_t* list_e;
+    uint64_t* list_tau;
     const DevQuery* q;
     uint64_t* tau;
     uint2* th;
@@ -117,7 +127,9 @@ cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, con
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
-                              uint32_t n_tickets);
+                              uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words);
+cudaError_t launch_materialize_tau(cudaStream_t s, uint32_t E, const QueryState* qs, const uint32_t* list_e,
+                                   const uint64_t* list_tau, uint64_t* out);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
 cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& a);
 cudaError_t launch_finalize(cudaStream_t s, uint32_t Q, const DevQuery* q, const QueryState* qs,

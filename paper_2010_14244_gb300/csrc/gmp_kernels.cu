@@ -152,7 +152,9 @@ __global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
 __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
                              const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
                              uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
-                             unsigned long long* __restrict__ dep, QueryState* __restrict__ qs, uint32_t* __restrict__ tickets, uint32_t n_tickets) {
+                             unsigned long long* __restrict__ dep, QueryState* __restrict__ qs,
+                             uint32_t* __restrict__ tickets, uint32_t n_tickets, uint32_t sparse,
+                             uint32_t* __restrict__ tflag, uint32_t tflag_words) {
     const uint32_t qi = blockIdx.y;
     const DevQuery Q = q[qi];
     uint64_t* T = tau + (size_t)qi * E;
@@ -160,13 +162,21 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
     uint2* TH = th + (size_t)qi * E;
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const uint32_t v = col[e];
+        const uint32_t h = heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
+        D[e] = 0;
+        if (sparse) {  // no road has a deposit yet: every road holds the baseline
+            TH[e] = make_uint2(0u, h);
+            continue;
+        }
         uint64_t t0 = 1ull << 32;
         if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
         T[e] = t0;
-        D[e] = 0;
-        const uint32_t v = col[e];
-        TH[e] = make_uint2(__float_as_uint(tau_float(t0)), heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa));
+        TH[e] = make_uint2(__float_as_uint(tau_float(t0)), h);
     }
+    if (sparse)
+        for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
+            tflag[(size_t)qi * tflag_words + w] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const uint32_t h = heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
         QueryState S;
@@ -177,6 +187,9 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         S.best_len = 0;
         S.best_W = 0;
         S.pad[0] = S.pad[1] = 0;
+        S.base_tau = 1ull << 32;
+        S.base_tf = __float_as_uint(tau_float(1ull << 32));
+        S.n_touched = 0;
         qs[qi] = S;
     }
     if (qi == 0 && blockIdx.x == 0)
@@ -251,6 +264,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     uint32_t rb_base = 0, rb_x = 0, rb_y = 0;
     bool rb_valid = false;
     const uint2* th = a.th;
+    float base_tf = 0.0f;  // sparse layout: the colony's baseline pheromone of this iteration
     uint32_t* route = a.routes;
     bool want = true;  // warp-uniform: some group may need a ticket (at the start, after an ant ended)
     // the next step's candidate loads, issued as soon as the ant moves (software pipelining)
@@ -294,6 +308,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         s1 = (uint32_t)(q.seed >> 32);
                         log_base = q.log_base;
                         th = a.th + (size_t)qi * a.n_edges;
+                        base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
                         route = a.routes + (size_t)slot * a.max_steps;
                         u = src;
                         beg = __ldg(a.row_ptr + u);
@@ -350,7 +365,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                     r1[j] = __ldg(rp + 1);
                     ph = __ldg(th + e);
                 }
-                tf[j] = __uint_as_float(ph.x);
+                tf[j] = ph.x ? __uint_as_float(ph.x) : base_tf;  // 0: the road still holds the baseline
                 he[j] = ph.y;
             }
             // when any group of the warp has used up its buffered draws, every group refills from its
@@ -477,7 +492,10 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
                     const unsigned long long delta = S->dep_num / t;
                     unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
-                    for (uint32_t i = lane; i < steps; i += G) atomicAdd(D + route[i], delta);
+                    for (uint32_t i = lane; i < steps; i += G) {
+                        atomicAdd(D + route[i], delta);
+                        if (a.sparse) register_road(a, qi, S, route[i]);
+                    }
                     if (leader) {
                         atomicAdd(&S->nsucc, 1ull);
                         atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * n_ants + k));
@@ -527,6 +545,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
     const uint2* th = a.th;
+    float base_tf = 0.0f;  // sparse layout: the colony's baseline pheromone of this iteration
     uint32_t* route = a.routes;
     const uint32_t n_threads = gridDim.x * blockDim.x;
     for (;;) {
@@ -569,6 +588,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                         s1 = (uint32_t)(q.seed >> 32);
                         log_base = q.log_base;
                         th = a.th + (size_t)qi * a.n_edges;
+                        base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
                         route = a.routes + (size_t)slot * a.max_steps;
                         u = src;
                         beg = __ldg(a.row_ptr + u);
@@ -609,7 +629,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                     r0[j] = __ldg(rp);
                     r1[j] = __ldg(rp + 1);
                         const uint2 ph = __ldg(th + e);
-                    tf[j] = __uint_as_float(ph.x);
+                    tf[j] = ph.x ? __uint_as_float(ph.x) : base_tf;  // 0: the road still holds the baseline
                     he[j] = ph.y;
                 } else {
                     r0[j] = r1[j] = make_uint4(0, 0, 0, 0);
@@ -715,7 +735,10 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 if (fd) {  // Updt_Pher: deposit dep_num / T on every road of the route
                     unsigned long long* D = a.dep + (size_t)fqi * a.n_edges;
                     const uint32_t* fr = a.routes + (size_t)fslot * a.max_steps;
-                    for (uint32_t i = lane; i < fsteps; i += 32u) atomicAdd(D + fr[i], fd);
+                    for (uint32_t i = lane; i < fsteps; i += 32u) {
+                        atomicAdd(D + fr[i], fd);
+                        if (a.sparse) register_road(a, fqi, a.qs + fqi, fr[i]);
+                    }
                 }
                 for (uint32_t w = lane; w < words; w += 32u) tw[tabu_index(w, (uint32_t)f)] = 0;
             }
@@ -748,6 +771,23 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
         if (!Q.active || a.it >= Q.n_iter) return;
         const uint64_t rf = Q.rho_fix;
         const size_t off = (size_t)qi * a.n_edges;
+        if (a.sparse) {  // only the roads with deposits so far hold their own pheromone
+            const uint32_t n = a.qs[qi].n_touched;
+            const uint32_t* LE = a.list_e + off;
+            uint64_t* LT = a.list_tau + off;
+            unsigned long long* D = a.dep + off;
+            uint32_t* TF = reinterpret_cast<uint32_t*>(a.th + off);
+            for (uint32_t i = chunk * kIterEndBlock + threadIdx.x; i < n; i += a.evap_blocks * kIterEndBlock) {
+                const uint32_t e = LE[i];
+                const uint64_t t = LT[i];
+                const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
+                const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + D[e];
+                LT[i] = nt;
+                D[e] = 0;
+                TF[2 * (size_t)e] = __float_as_uint(tau_float(nt));
+            }
+            return;
+        }
         uint64_t* T = a.tau + off;
         uint32_t* TF = reinterpret_cast<uint32_t*>(a.th + off);  // pheromone half of each pair
         unsigned long long* D = a.dep + off;
@@ -779,6 +819,13 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
         const uint32_t qi = b;
         const DevQuery Q = a.q[qi];
         if (!Q.active || a.it >= Q.n_iter) return;
+        if (a.sparse && threadIdx.x == 0) {  // the baseline: every road without a deposit evaporates alike
+            const uint64_t t = a.qs[qi].base_tau, rf = Q.rho_fix;
+            const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
+            const uint64_t nt = t - ((hi << 32) | (lo >> 32));
+            a.qs[qi].base_tau = nt;
+            a.qs[qi].base_tf = __float_as_uint(tau_float(nt));
+        }
         const unsigned long long key = a.qs[qi].best_key;
         if (key == kNoKey) return;
         const uint32_t low = (uint32_t)key;
@@ -873,9 +920,10 @@ cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, con
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
-                              uint32_t n_tickets) {
+                              uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
-    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets);
+    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, sparse,
+                                      tflag, tflag_words);
     return cudaGetLastError();
 }
 
@@ -886,6 +934,26 @@ cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& args) {
                             (a.n_nodes + kIterEndBlock - 1) / kIterEndBlock;
     if (blocks == 0) return cudaSuccess;
     k_iter_end<<<(uint32_t)blocks, kIterEndBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Dense pheromone of one colony from the sparse layout: the baseline everywhere, then the registered
+// roads' own values (for reading the table back).
+__global__ void k_materialize_tau(uint32_t E, const QueryState* __restrict__ qs, const uint32_t* __restrict__ list_e,
+                                  const uint64_t* __restrict__ list_tau, uint64_t* __restrict__ out, uint32_t phase) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (phase == 0) {
+        if (i < E) out[i] = qs->base_tau;
+    } else if (i < qs->n_touched) {
+        out[list_e[i]] = list_tau[i];
+    }
+}
+
+cudaError_t launch_materialize_tau(cudaStream_t s, uint32_t E, const QueryState* qs, const uint32_t* list_e,
+                                   const uint64_t* list_tau, uint64_t* out) {
+    if (E == 0) return cudaSuccess;
+    k_materialize_tau<<<blocks_for(E, 256), 256, 0, s>>>(E, qs, list_e, list_tau, out, 0);
+    k_materialize_tau<<<blocks_for(E, 256), 256, 0, s>>>(E, qs, list_e, list_tau, out, 1);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,19 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
     }
 }
 
+// Sparse pheromone layout: a road's first deposit of the job registers it in its colony's list,
+// with the pheromone it held until then (the colony's baseline of this iteration); from then on the
+// iteration end evaporates it on its own. The flag test before the atomic skips registered roads.
+__device__ __forceinline__ void register_road(const ConstructArgs& a, uint32_t qi, QueryState* S, uint32_t e) {
+    uint32_t* F = a.tflag + (size_t)qi * a.tflag_words + (e >> 5);
+    const uint32_t bit = 1u << (e & 31);
+    if (*(volatile const uint32_t*)F & bit) return;
+    if (atomicOr(F, bit) & bit) return;
+    const uint32_t idx = atomicAdd(&S->n_touched, 1u);
+    a.list_e[(size_t)qi * a.n_edges + idx] = e;
+    a.list_tau[(size_t)qi * a.n_edges + idx] = S->base_tau;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Ant construction. G lanes of a warp serve one ant (sub-warp group); lane l holds the candidates
 // l, l+G, ..., l+(K-1)G of the current node's CSR row. Per step: one round of independent 16-byte
@@ -118,6 +131,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     constexpr bool kGather = NC <= 16;     // every lane gathers all scores and picks locally
     constexpr uint32_t kNone = 0xFFFFFFFFu;  // not a candidate (scores are non-negative floats)
     const uint2* __restrict__ th = a.th + (size_t)qi * a.n_edges;
+    const float base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
     const uint32_t slot = q.ant_base + k;
     uint32_t* route = a.routes + (size_t)slot * a.max_steps;
     const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
@@ -152,7 +166,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             r0[j] = __ldg(rp);
             r1[j] = __ldg(rp + 1);
             const uint2 ph = __ldg(th + e);
-            tf[j] = __uint_as_float(ph.x);
+            tf[j] = ph.x ? __uint_as_float(ph.x) : base_tf;  // 0: the road still holds the baseline
             he[j] = ph.y;
         }
         // 2. the draw of this step depends on (iteration, ant, step) only: overlaps the loads
@@ -299,7 +313,10 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
         const unsigned long long delta = S->dep_num / t;
         unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
-        for (uint32_t i = lane; i < steps; i += G) atomicAdd(D + route[i], delta);
+        for (uint32_t i = lane; i < steps; i += G) {
+            atomicAdd(D + route[i], delta);
+            if (a.sparse) register_road(a, qi, S, route[i]);
+        }
         if (lane == 0) atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * q.n_ants + k));
     }
     // forget the visited set: whole bitmap when small, else just the nodes of this walk

@@ -20,6 +20,7 @@ FLAG_KERNEL_TIMING = 4
 FLAG_NO_GRAPH = 8
 FLAG_NO_LOCKSTEP = 16
 MODE_AUTO, MODE_ITERATIVE, MODE_PERSISTENT = 0, 1, 2
+TAU_AUTO, TAU_DENSE, TAU_SPARSE = 0, 1, 2
 
 _LIB = None
 
@@ -45,7 +46,8 @@ class ServerStats(C.Structure):
 class Params(C.Structure):
     _fields_ = [("max_steps", C.c_uint32), ("h_sat_ms", C.c_uint32), ("thr_permille", C.c_uint32),
                 ("flags", C.c_uint32), ("t_dep_ms", C.c_uint32), ("lanes_per_ant", C.c_uint32),
-                ("mode", C.c_uint32), ("queue_chunk", C.c_uint32), ("branches", C.c_uint32)]
+                ("mode", C.c_uint32), ("queue_chunk", C.c_uint32), ("branches", C.c_uint32),
+                ("tau_layout", C.c_uint32)]
 
 
 class Query(C.Structure):
@@ -212,8 +214,9 @@ class Context:
         self.set_densities(wl.vehicles)
 
     def set_params(self, max_steps=0, h_sat_ms=0, thr_permille=THRESHOLD_OFF, flags=0, t_dep_ms=0,
-                   lanes_per_ant=0, mode=MODE_AUTO, queue_chunk=0, branches=0):
-        p = Params(max_steps, h_sat_ms, thr_permille, flags, t_dep_ms, lanes_per_ant, mode, queue_chunk, branches)
+                   lanes_per_ant=0, mode=MODE_AUTO, queue_chunk=0, branches=0, tau_layout=TAU_AUTO):
+        p = Params(max_steps, h_sat_ms, thr_permille, flags, t_dep_ms, lanes_per_ant, mode, queue_chunk, branches,
+                   tau_layout)
         self._check(lib().gmp_set_params(self._h, C.byref(p)))
 
     def get_params(self) -> dict:

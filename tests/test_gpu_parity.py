@@ -33,7 +33,8 @@ def ctx(gm):
 # job schedules: the iterative job as one chain, as two and as the default number of concurrent colony
 # chains, and the persistent job
 SCHEDULES = {"chains1": dict(mode=1, branches=1), "chains2": dict(mode=1, branches=2),
-             "chains_default": dict(mode=1), "persistent": dict(mode=2)}
+             "chains_default": dict(mode=1), "persistent": dict(mode=2),
+             "sparse_tau": dict(mode=1, tau_layout=2), "dense_tau": dict(mode=1, tau_layout=1)}
 
 
 def _oparams(orc, **kw):
@@ -94,11 +95,14 @@ def test_phase_order_with_red_times_and_queues(gm, ctx, orc):
     _compare(orc, onet, orc.Params(), q, r, ctx, 0, ctx.ant_log(0))
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, "sparse"])
 def test_grid10_full_parity(gm, ctx, orc, mode):
     wl = W.grid10()
     ctx.load_workload(wl)
-    ctx.set_params(flags=gm.FLAG_ANT_LOG, mode=mode)
+    if mode == "sparse":  # pheromone as a baseline plus the roads with deposits: same tables and routes
+        ctx.set_params(flags=gm.FLAG_ANT_LOG, mode=1, tau_layout=gm.TAU_SPARSE)
+    else:
+        ctx.set_params(flags=gm.FLAG_ANT_LOG, mode=mode)
     q = wl.queries[0]
     r = ctx.solve_batch([q])[0]
     _compare(orc, orc.Net.from_workload(wl), orc.Params(), q, r, ctx, 0, ctx.ant_log(0))
@@ -301,3 +305,16 @@ def test_directed_graph_with_sinks(gm, ctx, orc, sched):
     for i, q in enumerate(qs):
         o = _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
         assert o["n_success"] < q.n_ants * q.n_iter  # some ants die at sinks or dead ends
+
+
+def test_sparse_layout_refusals(gm, ctx):
+    ctx.load_workload(W.grid10())
+    q = W.grid10().queries[0]
+    for kw in (dict(mode=2, tau_layout=2), dict(mode=1, tau_layout=2, flags=gm.FLAG_RANDOM_TAU)):
+        ctx.set_params(**kw)
+        with pytest.raises(gm.GmpError) as ei:
+            ctx.solve_batch([q])
+        assert ei.value.code == gm.ERR_UNSUPPORTED
+    with pytest.raises(gm.GmpError) as ei:
+        ctx.set_params(tau_layout=3)
+    assert ei.value.code == gm.ERR_INVALID_ARG
