@@ -575,7 +575,7 @@ int enqueue_job(gmp_ctx* c) {
         IterEndArgs e = iter_end_args(c, r.q1 - r.q0, b.dq + r.q0, b.tau + co, b.th + co, b.dep + co, b.qs + r.q0,
                                       b.routes, b.ant_steps, b.ant_wait, b.best_route + (size_t)r.q0 * b.max_steps,
                                       b.max_steps);
-        if (j > 0) e.n_nodes = 0;  // the queue update of an iteration runs once, in the first chain
+        const uint32_t n_nodes = e.n_nodes;
         if (b.sparse) {
             e.sparse = 1;
             e.list_e = b.list_e + co;
@@ -585,6 +585,9 @@ int enqueue_job(gmp_ctx* c) {
             GMP_CUDA(c, launch_construct(bs, r.kc, a, it));
             if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 1 + 2 * it], bs, cudaEventRecordExternal));
             e.it = it;
+            // the queue update of iteration `it` runs once, in chain it mod B (densities are fixed during a
+            // job, so every chain would compute the same order): the chains share that work evenly
+            e.n_nodes = (it % B == j) ? n_nodes : 0u;
             GMP_CUDA(c, launch_iter_end(bs, e));
             if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 2 + 2 * it], bs, cudaEventRecordExternal));
             n += 2;

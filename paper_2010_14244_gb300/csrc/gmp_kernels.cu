@@ -760,6 +760,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
 // Blocks [0, nev) evaporate kEvapPer roads per thread with every load issued first; the next Q blocks
 // copy best routes; the rest update intersections.
 constexpr uint32_t kEvapPer = 4;
+constexpr uint32_t kSparseEvapBlocks = 8;
 constexpr uint32_t kIterEndBlock = 256;
 
 __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
@@ -930,6 +931,8 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
 cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& args) {
     IterEndArgs a = args;
     a.evap_blocks = (a.n_edges + kIterEndBlock * kEvapPer - 1) / (kIterEndBlock * kEvapPer);
+    // sparse layout: a few blocks per colony stride over its registered roads (far fewer than E)
+    if (a.sparse && a.evap_blocks > kSparseEvapBlocks) a.evap_blocks = kSparseEvapBlocks;
     const uint64_t blocks = (uint64_t)a.n_queries * a.evap_blocks + a.n_queries +
                             (a.n_nodes + kIterEndBlock - 1) / kIterEndBlock;
     if (blocks == 0) return cudaSuccess;

@@ -334,6 +334,16 @@ def geo100k(n_queries=512, n_ants=256, n_iter=100) -> Workload:
                     "100k-node jittered-lattice planar graph, 60% signalised, Poisson(1) vehicles/road")
 
 
+def geo1m_serving() -> Workload:
+    """1M-node planar road graph (same generator as geo100k, 60% signalised) carrying 5M vehicles placed
+    uniformly on its roads; route requests are generated by the serving loop (uniform OD pairs)."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    net = geometric_network(1000, 1000, rng)
+    sig = two_phase_signals(net, rng.random(net.n_nodes) < 0.6, rng)
+    veh = vehicles_uniform(net.n_edges, 5_000_000, rng)
+    return Workload("geo1m", net, sig, veh, [], "1M-node planar graph, 60% signalised, 5M vehicles")
+
+
 def city_batch(n_graphs=64, n_min=1000, n_max=200_000, q_lo=8, q_hi=64, ants_lo=128, ants_hi=1024, n_iter=50,
                seed=4) -> list[Workload]:
     """Independent city graphs for one multi-graph launch: node counts log-uniform in [n_min, n_max] (same
