@@ -226,6 +226,28 @@ SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S, SERVE_MAX_BATCH = 16, 5
 SERVE_ANTS, SERVE_ITERS = 128, 30
 
 
+def serving_leg_1m():
+    """Route requests on a 1M-node planar road graph with 5M vehicles: Poisson arrivals at 20k req/s with
+    uniform origin-destination pairs, 128 ants x 30 iterations each, 1 s traffic ticks, 16 slots."""
+    from paper_2010_14244_gb300 import serving, workloads
+
+    wl = workloads.geo1m_serving()
+    srv, slots = serving.make_server(wl, n_slots=16, max_batch=128, max_ants=SERVE_ANTS, max_iter=SERVE_ITERS)
+    try:
+        make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
+        rep = serving.run_poisson(srv, make, rate_per_s=20000.0, duration_s=SERVE_WINDOW_S,
+                                  warmup_s=SERVE_WARMUP_S, tick_ms=1000)
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()
+    out = rep.summary()
+    out.update(slots=16, ants=SERVE_ANTS, iterations=SERVE_ITERS, arrivals="poisson, uniform OD",
+               network=f"{wl.net.n_nodes} nodes, {wl.net.n_edges} roads, 5M vehicles",
+               tick="1 s (queue/preemption update with vehicle discharge)")
+    return out
+
+
 def serving_leg(wl):
     """Route requests on the same road network: Poisson arrivals with uniform origin-destination pairs,
     128 ants x 30 iterations each, traffic ticks every second, continuous batching over slot contexts."""
@@ -352,9 +374,10 @@ def run_gpu(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(wl.net.n_edges * 4 + nq * 40), "d2h_bytes_per_step": int(d2h),
                "queries_per_s": nq * args.steps / e2e_t}
     ctx.close()
-    serving = None
+    serving = serving_1m = None
     if not args.no_serving and rank == 0:
         serving = serving_leg(wl)
+        serving_1m = serving_leg_1m()
     if rank != 0:
         return
     K = args.steps
@@ -400,6 +423,8 @@ def run_gpu(args, rank, world, local_rank):
         line["autotune"] = {k: tune[k] for k in ("n_tried", "best_ms", "default_ms", "bucket")}
     if serving:
         line["serving"] = serving
+    if serving_1m:
+        line["serving_1m_nodes"] = serving_1m
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(nq)
     print(json.dumps(line), flush=True)
