@@ -99,14 +99,18 @@ __global__ void k_tick_node(uint32_t N, const uint32_t* __restrict__ in_ptr, con
             start += g;
         }
     }
-    uint64_t Q[kMaxPhases];
-    for (uint32_t p = 0; p < kMaxPhases; ++p) Q[p] = 0;
+    uint64_t Q[kMaxPhases];  // registers: indexed at compile-time indices only (unrolled, masked)
+#pragma unroll
+    for (uint32_t q = 0; q < kMaxPhases; ++q) Q[q] = 0;
     unsigned long long k = 0;
     for (uint32_t i = ib; i < ie; ++i) {
         const uint32_t e = in_edge[i];
         const uint32_t n = veh[e], p = ephase[e];
         uint32_t out = 0;
-        if (P) Q[p & (kMaxPhases - 1)] += n;
+        if (P) {
+#pragma unroll
+            for (uint32_t q = 0; q < kMaxPhases; ++q) Q[q] += (p & (kMaxPhases - 1)) == q ? n : 0u;
+        }
         if (P == 0 || p == gph) {
             const uint64_t L = lanes[e];
             const uint64_t cap = L * (t_now + dt) / h_sat - L * t_now / h_sat;
@@ -116,6 +120,7 @@ __global__ void k_tick_node(uint32_t N, const uint32_t* __restrict__ in_ptr, con
         k += out;
     }
     K[v] = k;
+#pragma unroll
     for (uint32_t p = 0; p < kMaxPhases; ++p) {
         uint32_t& r = red[(size_t)v * kMaxPhases + p];
         if (P == 0 || p >= P || p == gph || Q[p] == 0)

@@ -25,82 +25,95 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
                                            EdgeRec* __restrict__ rec) {
     const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
     const uint32_t deg = min(row_ptr[v + 1] - row_ptr[v], 255u) << 24;  // out-degree of v (at most 128 runs)
-    uint8_t ord[kMaxPhases];
     if (P == 0) {
         for (uint32_t i = 0; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
         for (uint32_t i = ib; i < ie; ++i)  // second half of the record (see EdgeRec)
             reinterpret_cast<uint4*>(rec + in_edge[i])[1] = make_uint4(deg, 0u, 0u, 0u);
         return;
     }
+    // everything below stays in registers: phase-indexed values are only read and written at
+    // compile-time indices (loops over the 8 possible phases are unrolled and masked)
     uint64_t Q[kMaxPhases], S[kMaxPhases];
-    for (uint32_t p = 0; p < kMaxPhases; ++p) Q[p] = S[p] = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxPhases; ++k) Q[k] = S[k] = 0;
     for (uint32_t i = ib; i < ie; ++i) {
         const uint32_t e = in_edge[i];
         const uint32_t p = ephase[e] & (kMaxPhases - 1);
-        Q[p] += veh[e];
-        S[p] += cap[e];
+        const uint32_t n = veh[e], c = cap[e];
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxPhases; ++k) {
+            Q[k] += p == k ? n : 0u;
+            S[k] += p == k ? c : 0u;
+        }
     }
     const uint32_t cy = cycle[v];
     uint32_t over = 0, starved = 0, nonempty = 0;
-    uint32_t rd[kMaxPhases];
-    for (uint32_t p = 0; p < P; ++p) {
-        rd[p] = red[(size_t)v * kMaxPhases + p];
-        if (Q[p] > S[p] * 3u / 4u) over |= 1u << p;
-        if (rd[p] > cy) starved |= 1u << p;
-        if (Q[p] > 0) nonempty |= 1u << p;
+    uint32_t rd[kMaxPhases], gr[kMaxPhases];
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxPhases; ++k) {
+        rd[k] = k < P ? red[(size_t)v * kMaxPhases + k] : 0u;
+        gr[k] = k < P ? green[(size_t)v * kMaxPhases + k] : 0u;
+        if (k < P) {
+            if (Q[k] > S[k] * 3u / 4u) over |= 1u << k;
+            if (rd[k] > cy) starved |= 1u << k;
+            if (Q[k] > 0) nonempty |= 1u << k;
+        }
     }
-    uint32_t used = 0, n = 0;
+    // the phases that go first, with the value that orders them (longest first, then lower index)
+    uint32_t prio = 0;
+    bool by_q = true;
     if (over) {
-        while (over & ~used) {
-            int best = -1;
-            for (uint32_t p = 0; p < P; ++p)
-                if ((over & ~used) >> p & 1u)
-                    if (best < 0 || Q[p] > Q[best]) best = (int)p;
-            used |= 1u << best;
-            ord[n++] = (uint8_t)best;
-        }
+        prio = over;
     } else if (starved) {
-        while (starved & ~used) {
-            int best = -1;
-            for (uint32_t p = 0; p < P; ++p)
-                if ((starved & ~used) >> p & 1u)
-                    if (best < 0 || rd[p] > rd[best]) best = (int)p;
-            used |= 1u << best;
-            ord[n++] = (uint8_t)best;
-        }
-    } else if (nonempty) {
+        prio = starved;
+        by_q = false;
+    } else if (nonempty) {  // the longest non-empty queue (first in index order on ties)
         int best = -1;
-        for (uint32_t p = 0; p < P; ++p)
-            if (nonempty >> p & 1u)
-                if (best < 0 || Q[p] > Q[best]) best = (int)p;
-        used |= 1u << best;
-        ord[n++] = (uint8_t)best;
+        uint64_t bq = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxPhases; ++k)
+            if ((nonempty >> k & 1u) && (best < 0 || Q[k] > bq)) {
+                best = (int)k;
+                bq = Q[k];
+            }
+        prio = 1u << best;
     }
-    for (uint32_t p = 0; p < P; ++p)
-        if (!(used >> p & 1u) && (nonempty >> p & 1u)) {
-            used |= 1u << p;
-            ord[n++] = (uint8_t)p;
-        }
-    for (uint32_t p = 0; p < P; ++p)
-        if (!(used >> p & 1u)) {
-            used |= 1u << p;
-            ord[n++] = (uint8_t)p;
-        }
+    // sort key per phase: prioritised phases by value descending, then the other non-empty phases, then
+    // the empty ones, each in index order; the position of a phase in the plan is its rank by key
+    constexpr uint64_t kVmax = (1ull << 48) - 1;
+    uint64_t key[kMaxPhases];
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxPhases; ++k) {
+        const uint64_t val = by_q ? Q[k] : (uint64_t)rd[k];
+        const uint64_t grp = (prio >> k & 1u) ? 0u : ((nonempty >> k & 1u) ? 1u : 2u);
+        key[k] = (grp << 60) | (grp == 0 ? (kVmax - (val < kVmax ? val : kVmax)) << 4 : 0u) | k;
+    }
     uint32_t start[kMaxPhases];
-    uint32_t acc = 0;
-    for (uint32_t i = 0; i < P; ++i) {
-        order[(size_t)v * kMaxPhases + i] = ord[i];
-        start[ord[i]] = acc;
-        acc += green[(size_t)v * kMaxPhases + ord[i]];
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxPhases; ++k) {
+        uint32_t rank = 0, st = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < kMaxPhases; ++q)
+            if (q < P && key[q] < key[k]) {
+                ++rank;
+                st += gr[q];
+            }
+        start[k] = st;
+        if (k < P) order[(size_t)v * kMaxPhases + rank] = (uint8_t)k;
+        else order[(size_t)v * kMaxPhases + k] = (uint8_t)k;
     }
-    for (uint32_t i = P; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
     const uint32_t off = offset[v];
     const uint32_t magic = 0xFFFFFFFFu / cy;
     for (uint32_t i = ib; i < ie; ++i) {
         const uint32_t e = in_edge[i];
         const uint32_t p = ephase[e] & (kMaxPhases - 1);
-        reinterpret_cast<uint4*>(rec + e)[1] =
-            make_uint4(cy | deg, (off + start[p]) % cy, green[(size_t)v * kMaxPhases + p], magic);
+        uint32_t st = 0, gl = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxPhases; ++k) {
+            st = p == k ? start[k] : st;
+            gl = p == k ? gr[k] : gl;
+        }
+        reinterpret_cast<uint4*>(rec + e)[1] = make_uint4(cy | deg, (off + st) % cy, gl, magic);
     }
 }
 
