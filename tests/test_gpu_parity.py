@@ -181,10 +181,17 @@ def test_grid64_full_size_sampled(gm, ctx, orc, mode):
     re-solved by the oracle and must agree exactly, including the final pheromone table."""
     wl = W.grid64()
     ctx.load_workload(wl)
+    ctx.set_params(mode=mode)  # the benchmark's launch configuration (no timing events)
+    ctx.stage(wl.queries)
+    ctx.launch()
+    res0 = ctx.collect()
     ctx.set_params(flags=gm.FLAG_KERNEL_TIMING, mode=mode)
     ctx.stage(wl.queries)
     ctx.launch()
     res = ctx.collect()
+    for a, b in zip(res0, res):  # events around every kernel change nothing
+        assert a["travel_ms"] == b["travel_ms"] and a["ant_steps"] == b["ant_steps"]
+        np.testing.assert_array_equal(a["route"], b["route"])
     onet = orc.Net.from_workload(wl)
     for i in (0, 7, 15):
         _compare(orc, onet, orc.Params(), wl.queries[i], res[i], ctx, i)
@@ -318,3 +325,29 @@ def test_sparse_layout_refusals(gm, ctx):
     with pytest.raises(gm.GmpError) as ei:
         ctx.set_params(tau_layout=3)
     assert ei.value.code == gm.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("deg", [20, 100])
+def test_high_degree_hub(gm, ctx, orc, deg):
+    """A hub with `deg` one-way roads out (several candidate slots per lane, up to the 128-road limit of
+    32 lanes x 4 slots), each spoke leading to the destination."""
+    roads = [(0, 1 + i, 1000 + 37 * i, 50, 3, 0) for i in range(deg)]
+    roads += [(1 + i, deg + 1, 2000 + 91 * (deg - i), 50, 3, 0) for i in range(deg)]
+    net, sig, veh = NB.build(deg + 2, roads, bidirectional=False)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    q = Q(0, deg + 1, 64, 8, 1.0, 2.0, 0.1, deg)
+    r = ctx.solve_batch([q])[0]
+    _compare(orc, orc.Net(net, sig, veh), orc.Params(), q, r, ctx, 0)
+
+
+def test_degree_above_limit_is_refused(gm, ctx):
+    roads = [(0, 1 + i, 1000, 50, 3, 0) for i in range(130)] + [(1, 131, 1000, 50, 3, 0)]
+    net, sig, veh = NB.build(132, roads, bidirectional=False)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    with pytest.raises(gm.GmpError) as ei:
+        ctx.solve_batch([Q(0, 131, 8, 2, 1.0, 2.0, 0.1, 0)])
+    assert ei.value.code == gm.ERR_UNSUPPORTED
