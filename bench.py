@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-colony-per-launch comparison")
-    p.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving legs and the geo100k job")
     p.add_argument("--iterations", type=int, default=0, help="override iterations (profiling runs only)")
     p.add_argument("--queries", type=int, default=0, help="override colony count (profiling runs only)")
     return p.parse_args()
@@ -226,6 +226,45 @@ SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S, SERVE_MAX_BATCH = 16, 5
 SERVE_ANTS, SERVE_ITERS = 128, 30
 
 
+def geo100k_leg():
+    """The batched job on the 100k-node planar graph: 512 colonies x 256 ants x 100 iterations in one job
+    (autotuned schedule; the sparse pheromone layout applies at this size)."""
+    import torch
+
+    from paper_2010_14244_gb300 import gmacop, workloads
+
+    wl = workloads.geo100k()
+    stream = torch.cuda.Stream()
+    ctx = gmacop.Context(0, stream=stream)
+    try:
+        ctx.load_workload(wl)
+        tune = ctx.autotune(wl.queries, probe_iter=8)
+        ctx.stage(wl.queries)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                ctx.launch()
+            stream.synchronize()
+            for _ in range(3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.launch()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        res = ctx.collect()
+    finally:
+        ctx.close()
+    ms = statistics.median(times)
+    steps = sum(r["ant_steps"] for r in res)
+    return {"workload": "geo100k: 100k-node planar graph, 280k roads, 512 OD colonies x 256 ants x 100 iterations",
+            "ms_per_job": ms, "ant_steps_per_s": steps / (ms / 1e3), "queries_per_s": len(res) / (ms / 1e3),
+            "routes_found": int(sum(r["status"] == 0 for r in res)),
+            "schedule": {k: tune[k] for k in ("lanes_per_ant", "mode", "branches", "lockstep")}}
+
+
 def serving_leg_1m():
     """Route requests on a 1M-node planar road graph with 5M vehicles: Poisson arrivals at 20k req/s with
     uniform origin-destination pairs, 128 ants x 30 iterations each, 1 s traffic ticks, 16 slots."""
@@ -374,10 +413,11 @@ def run_gpu(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(wl.net.n_edges * 4 + nq * 40), "d2h_bytes_per_step": int(d2h),
                "queries_per_s": nq * args.steps / e2e_t}
     ctx.close()
-    serving = serving_1m = None
+    serving = serving_1m = geo = None
     if not args.no_serving and rank == 0:
         serving = serving_leg(wl)
         serving_1m = serving_leg_1m()
+        geo = geo100k_leg()
     if rank != 0:
         return
     K = args.steps
@@ -425,6 +465,8 @@ def run_gpu(args, rank, world, local_rank):
         line["serving"] = serving
     if serving_1m:
         line["serving_1m_nodes"] = serving_1m
+    if geo:
+        line["batched_geo100k"] = geo
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(nq)
     print(json.dumps(line), flush=True)
