@@ -142,7 +142,6 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
                                          uint32_t it, uint32_t* tabu, uint32_t lane, uint32_t gmask, uint32_t gbase) {
     constexpr int NC = G * K;              // candidate slots of the group
     constexpr bool kGather = NC <= 16;     // every lane gathers all scores and picks locally
-    constexpr uint32_t kNone = 0xFFFFFFFFu;  // not a candidate (scores are non-negative floats)
     const uint2* __restrict__ th = a.th + (size_t)qi * a.n_edges;
     const float base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
     const uint32_t slot = q.ant_base + k;
