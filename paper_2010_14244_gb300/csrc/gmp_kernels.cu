@@ -984,7 +984,9 @@ static cudaError_t config_for(int device, uint32_t n_nodes, uint32_t total_ants,
     int per_sm = 0, sms = 0;
     if (in_smem) {
         if (dyn > 48u * 1024u) {
-            err = cudaFuncSetAttribute(k_construct<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            // per kernel function, shared by every context: the cap of in-smem bitmaps, not this size
+            err = cudaFuncSetAttribute(k_construct<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       64 * 1024);
             if (err != cudaSuccess) return err;
         }
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct<G, K, true>, block, dyn);
@@ -1026,7 +1028,8 @@ static cudaError_t config_t(int device, uint32_t n_nodes, uint32_t total_ants, K
     if (smem > 200u * 1024u) return cudaErrorInvalidValue;
     cudaError_t err;
     if (smem > 48u * 1024u) {
-        err = cudaFuncSetAttribute(k_construct_lock<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // per kernel function, shared by every context: the cap of this kernel's bitmaps, not this size
+        err = cudaFuncSetAttribute(k_construct_lock<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (err != cudaSuccess) return err;
     }
     int per_sm = 0, sms = 0;
@@ -1079,8 +1082,9 @@ static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, 
     int per_sm = 0, sms = 0;
     if (in_smem) {
         if (dyn > 48u * 1024u) {
+            // per kernel function, shared by every context: the cap of in-smem bitmaps, not this size
             err = cudaFuncSetAttribute(k_construct_gl<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)dyn);
+                                       64 * 1024);
             if (err != cudaSuccess) return err;
         }
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true>, block, dyn);

@@ -218,7 +218,9 @@ static cudaError_t config_p(int device, uint32_t n_nodes, KernelConfig* out) {
     int per_sm = 0, sms = 0;
     if (in_smem) {
         if (dyn > 48u * 1024u) {
-            err = cudaFuncSetAttribute(k_persistent<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            // per kernel function, shared by every context: the cap of in-smem bitmaps, not this size
+            err = cudaFuncSetAttribute(k_persistent<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       64 * 1024);
             if (err != cudaSuccess) return err;
         }
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<G, K, true>, block, dyn);

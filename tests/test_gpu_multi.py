@@ -82,3 +82,37 @@ def test_multi_refuses(gm):
     finally:
         m.close()
         c.close()
+
+
+def test_graphs_with_different_shared_memory_sizes(gm, orc):
+    """Two graphs whose visited bitmaps need different amounts of shared memory above the default
+    48 KB (30k and 26k nodes: 60 KB and 52 KB per block at 8 lanes per ant), staged one after the other
+    and launched together."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    wls = []
+    for rows in (150, 130):
+        net = W.geometric_network(rows, 200, rng)
+        sig = W.two_phase_signals(net, rng.random(net.n_nodes) < 0.6, rng)
+        veh = W.vehicles_poisson(net.n_edges, 1.0, rng)
+        od = W.uniform_od(net.n_nodes, 2, rng)
+        qs = [W.Query(s, d, 32, 3, 1.0, 2.0, 0.1, 50 + i) for i, (s, d) in enumerate(od)]
+        wls.append(W.Workload(f"geo{rows}", net, sig, veh, qs))
+    m = gm.Multi(0)
+    ctxs = []
+    try:
+        for wl in wls:
+            c = gm.Context(0)
+            c.load_workload(wl)
+            c.set_params(lanes_per_ant=8, mode=1)
+            ctxs.append(c)
+        res = m.solve(ctxs, [wl.queries for wl in wls])
+        for wl, rr in zip(wls, res):
+            onet = orc.Net.from_workload(wl)
+            for q, r in zip(wl.queries, rr):
+                o = orc.solve(onet, orc.Params(), q, want_tau=False)
+                assert r["status"] == o["status"] and r["travel_ms"] == o["travel_ms"]
+                assert r["ant_steps"] == o["ant_steps"]
+    finally:
+        m.close()
+        for c in ctxs:
+            c.close()
