@@ -15,6 +15,10 @@ _LIB = None
 
 THR_OFF = 0xFFFFFFFF
 FLAG_RANDOM_TAU = 1
+FLAG_REPULSIVE = 32
+FLAG_UNIT_DEPOSIT = 64
+FLAG_EVAP_UNUSED = 128
+FLAG_PAPER_LITERAL = FLAG_REPULSIVE | FLAG_UNIT_DEPOSIT | FLAG_EVAP_UNUSED
 ANT_SUCCESS, ANT_DEAD_END, ANT_STEP_CAP, ANT_TIME_CAP = 0, 1, 2, 3
 OK, ERR_INVALID, ERR_NO_ROUTE, ERR_OOM, ERR_UNSUPPORTED, ERR_BUFFER = 0, 1, 2, 3, 6, 7
 
@@ -75,6 +79,8 @@ def lib():
             "orc_kappa": (u64, [u32]),
             "orc_heuristic_ms": (u32, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, u64]),
             "orc_score": (f32, [u64, u32, u32, u32]),
+            "orc_score_f": (f32, [u64, u32, u32, u32, u32]),
+            "orc_tau_factor": (f32, [u64, u32]),
             "orc_quantize": (None, [u32, vp, vp]),
             "orc_roulette_pick": (u32, [u32, vp, u64]),
             "orc_rho_fix": (u64, [f32]),
@@ -154,8 +160,14 @@ def heuristic_ms(x, y, xd, yd, kap):
     return int(lib().orc_heuristic_ms(x, y, xd, yd, kap))
 
 
-def score(tau, alpha, c_ms, beta) -> np.float32:
-    return np.float32(lib().orc_score(tau, alpha, c_ms, beta))
+def score(tau, alpha, c_ms, beta, flags=None) -> np.float32:
+    if flags is None:
+        return np.float32(lib().orc_score(tau, alpha, c_ms, beta))
+    return np.float32(lib().orc_score_f(tau, alpha, c_ms, beta, flags))
+
+
+def tau_factor(tau, flags=0) -> np.float32:
+    return np.float32(lib().orc_tau_factor(tau, flags))
 
 
 def quantize(scores) -> np.ndarray:

@@ -17,12 +17,15 @@
  *   orc_free_flow_ms ...  pinned: hand-worked values and monotonicity (the paper gives no formula)
  *   orc_signal_wait_ms    pinned: millisecond-by-millisecond signal simulation
  *   orc_phase_order       pinned: an independent rule-by-rule enumeration over small tables
+ *   orc_score_f           pinned: hand-worked scores, saturation at FLT_MAX, reciprocal pheromone
  *   orc_quantize          pinned: exact rational arithmetic (Python fractions)
  *   orc_walk_one          pinned: hand-worked single-ant steps, chi-square frequency checks
  *   orc_solve             pinned: Dijkstra / time-dependent Dijkstra / brute-force simple-path
- *                         enumeration on tiny graphs, route validity, pheromone conservation identity;
+ *                         enumeration on tiny graphs, route validity, pheromone conservation identity,
+ *                         closed forms of the unit-deposit / unused-only-evaporation variant;
  *                         the best route on large graphs is parity-unpinned (a metaheuristic optimum)
  */
+#include <float.h>
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -36,6 +39,10 @@
 #define ORC_DEFAULT_HSAT 2000u
 #define ORC_THR_OFF 0xFFFFFFFFu
 #define ORC_FLAG_RANDOM_TAU 1u
+/* The paper's own MACO-P variant (Sec. 4.1 bullets, Fig. 3, Algorithm 2), one reading per flag: */
+#define ORC_FLAG_REPULSIVE 32u    /* prefer less pheromone: the score reads 1/tau in place of tau */
+#define ORC_FLAG_UNIT_DEPOSIT 64u /* Ph_road++: a successful ant adds exactly 1.0 to each road it used */
+#define ORC_FLAG_EVAP_UNUSED 128u /* deposits first, then only roads without a deposit evaporate */
 
 enum {
     ORC_OK = 0,
@@ -65,7 +72,7 @@ typedef struct {
     uint32_t max_steps;    /* 0 = min(N-1, 4096) */
     uint32_t h_sat_ms;     /* 0 = 2000 ms saturation headway */
     uint32_t thr_permille; /* occupancy threshold in vehicles per 1000 capacity; 0xFFFFFFFF = off */
-    uint32_t flags;        /* bit 0: Philox-random initial pheromone */
+    uint32_t flags;        /* ORC_FLAG_* */
     uint32_t t_dep_ms;     /* departure clock, below 2^30 */
     uint32_t reserved;
 } orc_params;
@@ -358,12 +365,29 @@ static float pow_int(float x, uint32_t k)
     return p;
 }
 
-/* s = (tau * 2^-32)^alpha * (1 / c)^beta, each step one rounded binary32 operation. */
-float orc_score(uint64_t tau, uint32_t alpha, uint32_t c_ms, uint32_t beta)
+/* The pheromone factor of a score as binary32: tau * 2^-32, or its reciprocal (one rounded division)
+ * when less pheromone is preferred. tau >= 1, so both are normal and at most 2^32. */
+float orc_tau_factor(uint64_t tau, uint32_t flags)
 {
     float tf = (float)tau * 0x1p-32f;
+    return (flags & ORC_FLAG_REPULSIVE) ? 1.0f / tf : tf;
+}
+
+/* s = f^alpha * (1 / c)^beta with f = orc_tau_factor(tau), each step one rounded binary32 operation.
+ * f^alpha saturates at the largest finite binary32 (f < 2^32 overflows from alpha = 5 on), so every
+ * score is finite and eta^beta <= 1 keeps the product finite too. */
+float orc_score_f(uint64_t tau, uint32_t alpha, uint32_t c_ms, uint32_t beta, uint32_t flags)
+{
+    float p = pow_int(orc_tau_factor(tau, flags), alpha);
+    if (p > FLT_MAX)
+        p = FLT_MAX;
     float eta = 1.0f / (float)c_ms;
-    return pow_int(tf, alpha) * pow_int(eta, beta);
+    return p * pow_int(eta, beta);
+}
+
+float orc_score(uint64_t tau, uint32_t alpha, uint32_t c_ms, uint32_t beta)
+{
+    return orc_score_f(tau, alpha, c_ms, beta, 0u);
 }
 
 /* Integer roulette weights: w_i = max(1, floor(s_i * 2^(22 - E))) with E = floor(log2(max s));
@@ -423,7 +447,7 @@ uint64_t orc_evaporate(uint64_t tau, uint64_t rho_fix)
 /* ------------------------------------------------------------------------------------------------ */
 typedef struct {
     const orc_net *g;
-    uint32_t max_steps, thr, t_dep;
+    uint32_t max_steps, thr, t_dep, flags;
     uint32_t *ff, *cap, *tt, *qd, *h;
     uint8_t *order; /* N*8 */
     uint8_t *visited;
@@ -497,6 +521,7 @@ static int state_init(orc_state *S, const orc_net *g, const orc_params *prm, uin
     S->max_steps = (prm && prm->max_steps) ? prm->max_steps : def_steps;
     S->thr = prm ? prm->thr_permille : ORC_THR_OFF;
     S->t_dep = prm ? prm->t_dep_ms : 0u;
+    S->flags = prm ? prm->flags : 0u;
     return ORC_OK;
 }
 
@@ -560,7 +585,7 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
             }
             uint32_t c = S->tt[e] + w + S->h[v];
             S->waitv[i] = w;
-            S->score[i] = orc_score(tau[e], alpha, c, beta);
+            S->score[i] = orc_score_f(tau[e], alpha, c, beta, S->flags);
         }
         orc_quantize(n, S->score, S->w);
         uint32_t pick = orc_roulette_pick(n, S->w, draw64(q->seed, it, ant, steps, 0));
@@ -661,6 +686,9 @@ void orc_init_tau(uint32_t E, uint64_t seed, uint32_t flags, uint64_t *tau)
  *   for it in 0..I-1: every ant walks on the pheromone of the previous iteration; successful ants
  *   deposit floor(max(h(src),1) * 2^32 / T) on each road of their route; then every road evaporates
  *   and receives its deposits; then the per-intersection phase order is recomputed.
+ * The paper's own variant, by flags: ORC_FLAG_UNIT_DEPOSIT makes each deposit exactly 1.0 (Ph_road++);
+ * ORC_FLAG_EVAP_UNUSED adds the deposits first and then evaporates only the roads that received none
+ * (Updt_Pher before Evap_Pher, which decrements unused roads); ORC_FLAG_REPULSIVE acts in the walk.
  * route_nodes receives the best route (min T, then lowest (iteration, ant)) as node ids, src first.
  * tau_out (E entries, may be NULL) receives the final pheromone. ant_log (may be NULL) receives per
  * (iteration, ant) {status, steps, T, W}.
@@ -702,6 +730,7 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
     } else {
         uint64_t rho_fix = orc_rho_fix(q->rho);
         uint64_t dep_num = (uint64_t)(S.h[q->src] > 0 ? S.h[q->src] : 1u) << 32;
+        int unit = (S.flags & ORC_FLAG_UNIT_DEPOSIT) != 0;
         for (uint32_t it = 0; it < q->n_iter; ++it) {
             memset(D, 0, sizeof(uint64_t) * E);
             for (uint32_t k = 0; k < q->n_ants; ++k) {
@@ -719,7 +748,7 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
                     continue;
                 res->n_success++;
                 /* Updt_Pher: every successful ant deposits on the roads it used */
-                uint64_t delta = dep_num / T;
+                uint64_t delta = unit ? (uint64_t)1 << 32 : dep_num / T;
                 for (uint32_t i = 0; i < steps; ++i)
                     D[route[i]] += delta;
                 uint64_t key = ((uint64_t)T << 32) | ((uint64_t)it * q->n_ants + k);
@@ -730,9 +759,18 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
                     memcpy(best_route, route, sizeof(uint32_t) * steps);
                 }
             }
-            /* Evap_Pher + deposit */
-            for (uint32_t e = 0; e < E; ++e)
-                tau[e] = orc_evaporate(tau[e], rho_fix) + D[e];
+            if (S.flags & ORC_FLAG_EVAP_UNUSED) {
+                /* Updt_Pher, then Evap_Pher on the roads no successful ant used */
+                for (uint32_t e = 0; e < E; ++e)
+                    tau[e] += D[e];
+                for (uint32_t e = 0; e < E; ++e)
+                    if (D[e] == 0)
+                        tau[e] = orc_evaporate(tau[e], rho_fix);
+            } else {
+                /* Evap_Pher + deposit */
+                for (uint32_t e = 0; e < E; ++e)
+                    tau[e] = orc_evaporate(tau[e], rho_fix) + D[e];
+            }
             /* per-iteration queue/preemption update (densities are fixed during a solve) */
             orc_queue_preempt(g, prm, S.order);
         }
