@@ -42,6 +42,12 @@ extern "C" {
 #define GMP_THRESHOLD_OFF 0xFFFFFFFFu
 #define GMP_FLAG_RANDOM_TAU 1u /* initial pheromone 0.5 + u/2^32, u = Philox(road, 0, 0, 1) word 0 */
 #define GMP_FLAG_ANT_LOG 2u    /* keep a per-(iteration, ant) log {status, steps, T, W} for inspection */
+/* The paper's own MACO-P pheromone variant (Sec. 4.1 bullets, Fig. 3, Algorithm 2), one flag per part;
+ * every kernel shape and both pheromone layouts honour them. */
+#define GMP_FLAG_REPULSIVE 32u    /* next-node rule prefers less pheromone: scores use (1/tau)^alpha */
+#define GMP_FLAG_UNIT_DEPOSIT 64u /* Ph_road++: each successful ant adds exactly 1.0 to each road used */
+#define GMP_FLAG_EVAP_UNUSED 128u /* deposits first; only roads without a deposit that iteration evaporate */
+#define GMP_FLAG_PAPER_LITERAL (GMP_FLAG_REPULSIVE | GMP_FLAG_UNIT_DEPOSIT | GMP_FLAG_EVAP_UNUSED)
 
 #define GMP_MODE_AUTO 0u       /* library picks */
 #define GMP_MODE_ITERATIVE 1u  /* one kernel sequence per iteration, whole batch, CUDA-graph replay */

@@ -28,7 +28,7 @@ constexpr uint32_t kFlagKernelTiming = 4u;  // event records around every kernel
 constexpr uint32_t kFlagNoGraph = kFlagNoGraphBit;  // issue the job kernel by kernel instead of replaying a graph
 constexpr uint32_t kFlagNoLockstep = kFlagNoLockstepBit;  // sub-warp ants without warp lockstep
 constexpr uint32_t kKnownFlags =
-    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
+    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | GMP_FLAG_PAPER_LITERAL | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
 constexpr int32_t kCoordLimit = 1 << 27;
 constexpr uint64_t kTickClockMax = 1ull << 48;  // lanes * (t + dt) stays below 2^64
 constexpr uint32_t kDefaultBranches = 16;        // concurrent colony chains of an iterative job
@@ -391,6 +391,7 @@ IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* 
     e.n_edges = c->E;
     e.n_nodes = c->N;
     e.max_steps = max_steps;
+    e.flags = c->prm.flags;
     e.q = dq;
     e.tau = tau;
     e.th = th;
@@ -450,6 +451,7 @@ int enqueue_persistent(gmp_ctx* c) {
     p.rec = c->rec;
     p.n_nodes = c->N;
     p.max_iter = b.maxI;
+    p.flags = c->prm.flags;
     p.node_chunk = c->prm.queue_chunk ? c->prm.queue_chunk : 16u;
     p.spin_limit = 1u << 23;  // idle polls of ~0.3 us each (seconds) before the job reports a timeout
     GMP_CUDA(c, launch_persistent(s, b.kc, p));

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gmacop.h"
+
 namespace gmp {
 
 constexpr uint32_t kMaxPhases = 8;
@@ -53,7 +55,8 @@ static_assert(sizeof(DevQuery) == 64, "DevQuery layout");
 // Per-colony running state.
 struct __align__(16) QueryState {
     unsigned long long best_key;  // (T << 32) | (iteration * n_ants + ant); kNoKey = none yet
-    unsigned long long dep_num;   // max(h(src), 1) << 32: a successful ant deposits dep_num / T per road
+    unsigned long long dep_num;   // max(h(src), 1) << 32: a successful ant deposits dep_num / T per road;
+                                  // 0 under GMP_FLAG_UNIT_DEPOSIT (every deposit is 1.0)
     unsigned long long steps;     // roads taken by all ants
     unsigned long long nsucc;     // successful walks
     uint32_t best_len;            // roads in the best route
@@ -137,6 +140,29 @@ __device__ __forceinline__ float pow_int(float x, uint32_t k) {
 // Pheromone as a binary32 value: the Q32.32 integer rounded to nearest, scaled exactly by 2^-32.
 __device__ __forceinline__ float tau_float(uint64_t tau) { return __fmul_rn(__ull2float_rn(tau), 0x1p-32f); }
 
+// The binary32 word a candidate's score reads for pheromone tau (bits): tau_float(tau), or under
+// GMP_FLAG_REPULSIVE its reciprocal rounded to nearest, so that less pheromone scores higher (Sec. 4.1).
+// tau >= 1, so both are normal, at most 2^32 and never 0 (0 marks a road at the sparse baseline).
+__device__ __forceinline__ uint32_t tau_word(uint64_t tau, uint32_t flags) {
+    const float tf = tau_float(tau);
+    return __float_as_uint((flags & GMP_FLAG_REPULSIVE) ? __frcp_rn(tf) : tf);
+}
+
+// One iteration's pheromone update of a road holding tau with deposits d (Evap_Pher, Updt_Pher):
+// tau - floor(tau * rho_fix / 2^32) + d; under GMP_FLAG_EVAP_UNUSED a road with deposits keeps tau + d
+// and only a road without any evaporates.
+__device__ __forceinline__ uint64_t tau_next(uint64_t t, uint64_t rho_fix, uint64_t d, uint32_t flags) {
+    const uint64_t lo = t * rho_fix, hi = __umul64hi(t, rho_fix);
+    const uint64_t ev = t - ((hi << 32) | (lo >> 32));
+    return ((flags & GMP_FLAG_EVAP_UNUSED) && d) ? t + d : ev + d;
+}
+
+// Deposit of a successful ant of elapsed time T on each road of its route (Updt_Pher): dep_num / T, or
+// exactly 1.0 when dep_num is 0 (GMP_FLAG_UNIT_DEPOSIT, the paper's Ph_road++).
+__device__ __forceinline__ unsigned long long ant_deposit(unsigned long long dep_num, uint32_t T) {
+    return dep_num ? dep_num / T : (1ull << 32);
+}
+
 // 1 / c rounded to nearest for 1 <= c <= 2^29 (results are never subnormal): the hardware reciprocal
 // estimate corrected once with fused multiply-adds (Markstein, IBM J. Res. Dev. 34(1), 1990: the
 // residual 1 - c*y is exact in an FMA, and one FMA correction of a faithful estimate is correctly
@@ -157,13 +183,15 @@ __device__ __forceinline__ float u32_to_f32_rn(uint32_t c) {
     return __fmaf_rn(hi, 64.0f, lo);
 }
 
-// Next-node desirability from tf = tau_float(tau): tf^alpha * (1 / c)^beta, c = travel + wait +
-// remaining bound (ms), 1 <= c < 2^29. The alpha = 1, beta = 2 case performs the same roundings in the
-// same order without loops.
+// Next-node desirability from the pheromone word tf (tau_word): tf^alpha * (1 / c)^beta, c = travel +
+// wait + remaining bound (ms), 1 <= c < 2^29. tf < 2^32, so tf^alpha can overflow from alpha = 5 on:
+// it saturates at the largest finite binary32, and eta^beta <= 1 keeps every score finite (the roulette
+// weights need a finite maximum). The alpha = 1, beta = 2 case performs the same roundings in the same
+// order without loops (it cannot overflow).
 __device__ __forceinline__ float score_f(float tf, uint32_t alpha, uint32_t c, uint32_t beta) {
     const float eta = rcp_rn(u32_to_f32_rn(c));
     if (alpha == 1u && beta == 2u) return __fmul_rn(tf, __fmul_rn(eta, eta));
-    return __fmul_rn(pow_int(tf, alpha), pow_int(eta, beta));
+    return __fmul_rn(fminf(pow_int(tf, alpha), 3.40282347e38f), pow_int(eta, beta));
 }
 
 // The roulette's index r = floor(rnd * S / 2^64) for a 64-bit draw and S < 2^32, from two 32x32 -> 64

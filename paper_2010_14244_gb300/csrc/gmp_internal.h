@@ -50,6 +50,7 @@ struct IterEndArgs {
     uint32_t n_queries, n_edges, n_nodes, it, max_steps;
     uint32_t evap_blocks;  // blocks per colony for the evaporation (set by the launcher)
     uint32_t sparse;       // sparse pheromone layout: evaporate the registered roads and the baseline
+    uint32_t flags;        // GMP_FLAG_* of the context (repulsive pheromone word, unused-only evaporation)
     uint32_t* list_e;
     uint64_t* list_tau;
     const DevQuery* q;
@@ -95,6 +96,7 @@ struct PersistentArgs {
     uint8_t* order;
     EdgeRec* rec;
     uint32_t n_nodes, max_iter, spin_limit;
+    uint32_t flags;       // GMP_FLAG_* of the context
     uint32_t node_chunk;  // intersections per queue-update chunk (8..64)
 };
 

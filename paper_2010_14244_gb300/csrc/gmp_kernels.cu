@@ -177,7 +177,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         uint64_t t0 = 1ull << 32;
         if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
         T[e] = t0;
-        TH[e] = make_uint2(__float_as_uint(tau_float(t0)), h);
+        TH[e] = make_uint2(tau_word(t0, flags), h);
     }
     if (sparse)
         for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
@@ -186,14 +186,14 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         const uint32_t h = heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
         QueryState S;
         S.best_key = Q.active ? kNoKey : 0ull;
-        S.dep_num = (unsigned long long)(h > 0 ? h : 1u) << 32;
+        S.dep_num = (flags & GMP_FLAG_UNIT_DEPOSIT) ? 0ull : (unsigned long long)(h > 0 ? h : 1u) << 32;
         S.steps = 0;
         S.nsucc = 0;
         S.best_len = 0;
         S.best_W = 0;
         S.pad[0] = S.pad[1] = 0;
         S.base_tau = 1ull << 32;
-        S.base_tf = __float_as_uint(tau_float(1ull << 32));
+        S.base_tf = tau_word(1ull << 32, flags);
         S.n_touched = 0;
         qs[qi] = S;
     }
@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
                     }
                 }
-                if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
-                    const unsigned long long delta = S->dep_num / t;
+                if (status == kAntSuccess) {  // Updt_Pher: deposit ant_deposit() on every road of the route
+                    const unsigned long long delta = ant_deposit(S->dep_num, t);
                     unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
                     for (uint32_t i = lane; i < steps; i += G) {
                         atomicAdd(D + route[i], delta);
@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 }
                 if (status == kAntSuccess) {
                     atomicAdd(&S->nsucc, 1ull);
-                    delta = S->dep_num / t;
+                    delta = ant_deposit(S->dep_num, t);
                     atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * n_ants + k));
                 }
             }
@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 const uint32_t fsteps = __shfl_sync(FULL, steps, f);
                 const uint32_t fqi = __shfl_sync(FULL, qi, f);
                 const uint32_t fslot = __shfl_sync(FULL, slot, f);
-                if (fd) {  // Updt_Pher: deposit dep_num / T on every road of the route
+                if (fd) {  // Updt_Pher: deposit ant_deposit() on every road of the route
                     unsigned long long* D = a.dep + (size_t)fqi * a.n_edges;
                     const uint32_t* fr = a.routes + (size_t)fslot * a.max_steps;
                     for (uint32_t i = lane; i < fsteps; i += 32u) {
@@ -754,11 +754,13 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
 }
 
 // ------------------------------------------------------------------------------------------------
-// Evap_Pher + Updt_Pher: tau <- tau - floor(tau * rho_fix / 2^32) + D ; D <- 0.
+// Evap_Pher + Updt_Pher: tau <- tau - floor(tau * rho_fix / 2^32) + D ; D <- 0 (tau_next).
 // ------------------------------------------------------------------------------------------------
 // Iteration end, one launch for three independent pieces of work (all read what the construction
 // kernel wrote, none reads what another writes):
-//   Evap_Pher + Updt_Pher  tau <- tau - floor(tau * rho_fix / 2^32) + D, D <- 0, per (colony, road);
+//   Evap_Pher + Updt_Pher  tau <- tau - floor(tau * rho_fix / 2^32) + D, D <- 0, per (colony, road)
+//                          (under GMP_FLAG_EVAP_UNUSED a road with D > 0 keeps tau + D), then the
+//                          road's binary32 pheromone word (tau_word);
 //   best-route tracking    when a colony's best key came from this iteration, keep that ant's route;
 //   Calc_Dens / Comp_Thres the per-intersection phase order (densities are fixed within a job, so the
 //                          update reproduces the same order; it runs because the iteration calls it).
@@ -785,12 +787,10 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
             uint32_t* TF = reinterpret_cast<uint32_t*>(a.th + off);
             for (uint32_t i = chunk * kIterEndBlock + threadIdx.x; i < n; i += a.evap_blocks * kIterEndBlock) {
                 const uint32_t e = LE[i];
-                const uint64_t t = LT[i];
-                const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
-                const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + D[e];
+                const uint64_t nt = tau_next(LT[i], rf, D[e], a.flags);
                 LT[i] = nt;
                 D[e] = 0;
-                TF[2 * (size_t)e] = __float_as_uint(tau_float(nt));
+                TF[2 * (size_t)e] = tau_word(nt, a.flags);
             }
             return;
         }
@@ -810,11 +810,9 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
         for (uint32_t i = 0; i < kEvapPer; ++i) {
             const uint32_t e = e0 + i * kIterEndBlock;
             if (e < a.n_edges) {
-                const uint64_t t = tv[i];
-                const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
-                const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + dv[i];
+                const uint64_t nt = tau_next(tv[i], rf, dv[i], a.flags);
                 T[e] = nt;
-                TF[2 * (size_t)e] = __float_as_uint(tau_float(nt));
+                TF[2 * (size_t)e] = tau_word(nt, a.flags);
                 D[e] = 0;
             }
         }
@@ -826,11 +824,9 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
         const DevQuery Q = a.q[qi];
         if (!Q.active || a.it >= Q.n_iter) return;
         if (a.sparse && threadIdx.x == 0) {  // the baseline: every road without a deposit evaporates alike
-            const uint64_t t = a.qs[qi].base_tau, rf = Q.rho_fix;
-            const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
-            const uint64_t nt = t - ((hi << 32) | (lo >> 32));
+            const uint64_t nt = tau_next(a.qs[qi].base_tau, Q.rho_fix, 0, a.flags);
             a.qs[qi].base_tau = nt;
-            a.qs[qi].base_tf = __float_as_uint(tau_float(nt));
+            a.qs[qi].base_tf = tau_word(nt, a.flags);
         }
         const unsigned long long key = a.qs[qi].best_key;
         if (key == kNoKey) return;

@@ -164,11 +164,9 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
                     for (int i = 0; i < PER; ++i) {
                         const uint32_t e = e0 + lane + (uint32_t)i * G;
                         if (e < E) {
-                            const uint64_t t = tv[i];
-                            const uint64_t lo = t * rf, hi = __umul64hi(t, rf);
-                            const uint64_t nt = t - ((hi << 32) | (lo >> 32)) + dv[i];
+                            const uint64_t nt = tau_next(tv[i], rf, dv[i], p.flags);
                             T[e] = nt;
-                            TF[2 * (size_t)e] = __float_as_uint(tau_float(nt));
+                            TF[2 * (size_t)e] = tau_word(nt, p.flags);
                             D[e] = 0;
                         }
                     }

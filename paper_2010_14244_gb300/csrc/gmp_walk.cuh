@@ -322,8 +322,8 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
         }
     }
-    if (status == kAntSuccess) {  // Updt_Pher: deposit dep_num / T on every road of the route
-        const unsigned long long delta = S->dep_num / t;
+    if (status == kAntSuccess) {  // Updt_Pher: deposit ant_deposit() on every road of the route
+        const unsigned long long delta = ant_deposit(S->dep_num, t);
         unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
         for (uint32_t i = lane; i < steps; i += G) {
             atomicAdd(D + route[i], delta);

@@ -19,6 +19,10 @@ FLAG_ANT_LOG = 2
 FLAG_KERNEL_TIMING = 4
 FLAG_NO_GRAPH = 8
 FLAG_NO_LOCKSTEP = 16
+FLAG_REPULSIVE = 32
+FLAG_UNIT_DEPOSIT = 64
+FLAG_EVAP_UNUSED = 128
+FLAG_PAPER_LITERAL = FLAG_REPULSIVE | FLAG_UNIT_DEPOSIT | FLAG_EVAP_UNUSED
 MODE_AUTO, MODE_ITERATIVE, MODE_PERSISTENT = 0, 1, 2
 TAU_AUTO, TAU_DENSE, TAU_SPARSE = 0, 1, 2
 
