@@ -81,6 +81,10 @@ def lib():
             "orc_score": (f32, [u64, u32, u32, u32]),
             "orc_score_f": (f32, [u64, u32, u32, u32, u32]),
             "orc_tau_factor": (f32, [u64, u32]),
+            "orc_log2": (f32, [f32]),
+            "orc_exp2": (f32, [f32]),
+            "orc_score_frac": (f32, [u64, f32, u32, f32, u32]),
+            "orc_frac_constants": (None, [vp]),
             "orc_quantize": (None, [u32, vp, vp]),
             "orc_roulette_pick": (u32, [u32, vp, u64]),
             "orc_rho_fix": (u64, [f32]),
@@ -168,6 +172,24 @@ def score(tau, alpha, c_ms, beta, flags=None) -> np.float32:
 
 def tau_factor(tau, flags=0) -> np.float32:
     return np.float32(lib().orc_tau_factor(tau, flags))
+
+
+def log2f(x) -> np.float32:
+    return np.float32(lib().orc_log2(float(x)))
+
+
+def exp2f(x) -> np.float32:
+    return np.float32(lib().orc_exp2(float(x)))
+
+
+def score_frac(tau, alpha, c_ms, beta, flags=0) -> np.float32:
+    return np.float32(lib().orc_score_frac(tau, float(alpha), c_ms, float(beta), flags))
+
+
+def frac_constants() -> np.ndarray:
+    out = np.zeros(14, np.float32)
+    lib().orc_frac_constants(_p(out))
+    return out
 
 
 def quantize(scores) -> np.ndarray:

@@ -18,6 +18,9 @@
  *   orc_signal_wait_ms    pinned: millisecond-by-millisecond signal simulation
  *   orc_phase_order       pinned: an independent rule-by-rule enumeration over small tables
  *   orc_score_f           pinned: hand-worked scores, saturation at FLT_MAX, reciprocal pheromone
+ *   orc_log2, orc_exp2    pinned: error bounds against double-precision log2 / exp2, exact special
+ *                         values, series constants against their exact values (Python fractions)
+ *   orc_score_frac        pinned: error bound against double-precision powers, chi-square frequencies
  *   orc_quantize          pinned: exact rational arithmetic (Python fractions)
  *   orc_walk_one          pinned: hand-worked single-ant steps, chi-square frequency checks
  *   orc_solve             pinned: Dijkstra / time-dependent Dijkstra / brute-force simple-path
@@ -390,6 +393,102 @@ float orc_score(uint64_t tau, uint32_t alpha, uint32_t c_ms, uint32_t beta)
     return orc_score_f(tau, alpha, c_ms, beta, 0u);
 }
 
+/* ------------------------------------------------------------------------------------------------ */
+/* Non-integer alpha / beta: the score as 2^L, L = alpha*log2(f) - beta*log2(c), with a binary32       */
+/* log2 and exp2 of our own. Both are fixed sequences of single rounded binary32 operations.          */
+/* ------------------------------------------------------------------------------------------------ */
+/* Series coefficients, each the nearest binary32 to its exact value:
+ * 1/3, 1/5, 1/7, 1/9 (atanh), 2/ln 2, and ln(2)^k / k! for k = 1..8 (Taylor series of 2^f). */
+static const float LOG_C3 = 0x1.555556p-2f, LOG_C5 = 0x1.99999ap-3f, LOG_C7 = 0x1.24924ap-3f,
+                   LOG_C9 = 0x1.c71c72p-4f, LOG_K = 0x1.715476p+1f;
+static const float EXP_C[9] = {1.0f,          0x1.62e430p-1f, 0x1.ebfbe0p-3f, 0x1.c6b08ep-5f, 0x1.3b2ab6p-7f,
+                               0x1.5d87fep-10f, 0x1.430912p-13f, 0x1.ffcbfcp-17f, 0x1.62c022p-20f};
+
+void orc_frac_constants(float out[14])
+{
+    out[0] = LOG_C3;
+    out[1] = LOG_C5;
+    out[2] = LOG_C7;
+    out[3] = LOG_C9;
+    out[4] = LOG_K;
+    for (int k = 0; k < 9; ++k)
+        out[5 + k] = EXP_C[k];
+}
+
+static float bits_to_float(uint32_t b)
+{
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+static uint32_t float_to_bits(float f)
+{
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return b;
+}
+
+/* log2 x for a positive normal binary32 x. Range reduction as in Cody & Waite (Software Manual for
+ * the Elementary Functions, 1980): x = 2^e * m with m in (1/sqrt 2, sqrt 2]; then
+ * ln m = 2 atanh(t), t = (m - 1) / (m + 1), |t| <= 0.1716, by the atanh series through t^9:
+ * log2 m = t * (2/ln 2) * (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9) (truncation below 2^-28 relative). */
+float orc_log2(float x)
+{
+    uint32_t b = float_to_bits(x);
+    int e = (int)(b >> 23) - 127;
+    uint32_t mb = (b & 0x7FFFFFu) | 0x3F800000u;
+    if (mb > 0x3FB504F3u) { /* m above sqrt 2 (rounded down): use m/2 */
+        mb -= 0x00800000u;
+        e += 1;
+    }
+    float m = bits_to_float(mb);
+    float t = (m - 1.0f) / (m + 1.0f);
+    float t2 = t * t;
+    float p = LOG_C9;
+    p = p * t2 + LOG_C7;
+    p = p * t2 + LOG_C5;
+    p = p * t2 + LOG_C3;
+    p = p * t2 + 1.0f;
+    float r = (t * LOG_K) * p;
+    return (float)e + r;
+}
+
+/* 2^L in binary32: FLT_MAX for L >= 128 (saturation, as for integer exponents), 0 below -150;
+ * otherwise n = floor(L), f = L - n in [0, 1) (exact), 2^f by its Taylor series through f^8 in Horner
+ * form (truncation below 2^-26 relative), capped below 2, times 2^n in two exact power-of-two steps
+ * (the second rounds only into the subnormal range). */
+float orc_exp2(float L)
+{
+    if (!(L < 128.0f))
+        return FLT_MAX;
+    if (L < -150.0f)
+        return 0.0f;
+    float n = floorf(L);
+    float f = L - n;
+    float p = EXP_C[8];
+    for (int k = 7; k >= 0; --k)
+        p = p * f + EXP_C[k];
+    const float below2 = 0x1.fffffep0f;
+    if (p > below2)
+        p = below2;
+    int ni = (int)n;
+    int n1 = ni >= 0 ? ni / 2 : -((-ni + 1) / 2); /* floor(ni / 2) */
+    int n2 = ni - n1;
+    float s1 = bits_to_float((uint32_t)(n1 + 127) << 23), s2 = bits_to_float((uint32_t)(n2 + 127) << 23);
+    return (p * s1) * s2;
+}
+
+/* Score for non-integer exponents: 2^(alpha*log2 f - beta*log2 c), f = orc_tau_factor(tau), c as
+ * binary32 (rounded to nearest above 2^24). Equals f^alpha * (1/c)^beta up to the error bound pinned
+ * in the tests. */
+float orc_score_frac(uint64_t tau, float alpha, uint32_t c_ms, float beta, uint32_t flags)
+{
+    float A = alpha * orc_log2(orc_tau_factor(tau, flags));
+    float B = beta * orc_log2((float)c_ms);
+    return orc_exp2(A - B);
+}
+
 /* Integer roulette weights: w_i = max(1, floor(s_i * 2^(22 - E))) with E = floor(log2(max s));
  * all ones when every score is zero. Every weight is below 2^23, so the running sums of up to 512
  * candidates fit in 32 bits. */
@@ -527,7 +626,7 @@ static int state_init(orc_state *S, const orc_net *g, const orc_params *prm, uin
 
 /* One ant of iteration `it`: builds a simple path from src (Fig. 3 body for one vehicle, with the
  * roulette next-node rule). Writes the roads taken to route_edges; returns the ant status. */
-static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta, const uint64_t *tau,
+static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta, int frac, const uint64_t *tau,
                 uint32_t it, uint32_t ant, uint32_t *route_edges, uint32_t *steps_out, uint32_t *T_out,
                 uint32_t *W_out)
 {
@@ -585,7 +684,8 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
             }
             uint32_t c = S->tt[e] + w + S->h[v];
             S->waitv[i] = w;
-            S->score[i] = orc_score_f(tau[e], alpha, c, beta, S->flags);
+            S->score[i] = frac ? orc_score_frac(tau[e], q->alpha, c, q->beta, S->flags)
+                               : orc_score_f(tau[e], alpha, c, beta, S->flags);
         }
         orc_quantize(n, S->score, S->w);
         uint32_t pick = orc_roulette_pick(n, S->w, draw64(q->seed, it, ant, steps, 0));
@@ -607,7 +707,8 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
     return status;
 }
 
-static int query_ok(const orc_net *g, const orc_query *q, uint32_t *alpha, uint32_t *beta)
+/* alpha, beta in [0, 8]; integers take the repeated-multiplication score, anything else the 2^L score. */
+static int query_ok(const orc_net *g, const orc_query *q, uint32_t *alpha, uint32_t *beta, int *frac)
 {
     if (q->src >= g->n_nodes || q->dst >= g->n_nodes || q->n_ants == 0 || q->n_iter == 0)
         return ORC_ERR_INVALID;
@@ -615,10 +716,9 @@ static int query_ok(const orc_net *g, const orc_query *q, uint32_t *alpha, uint3
         return ORC_ERR_INVALID;
     if (!(q->alpha >= 0.0f && q->alpha <= 8.0f && q->beta >= 0.0f && q->beta <= 8.0f))
         return ORC_ERR_UNSUPPORTED;
-    if (floorf(q->alpha) != q->alpha || floorf(q->beta) != q->beta)
-        return ORC_ERR_UNSUPPORTED;
     if (!(q->rho >= 0.0f && q->rho < 1.0f))
         return ORC_ERR_INVALID;
+    *frac = floorf(q->alpha) != q->alpha || floorf(q->beta) != q->beta;
     *alpha = (uint32_t)q->alpha;
     *beta = (uint32_t)q->beta;
     return ORC_OK;
@@ -654,14 +754,15 @@ int orc_walk_one(const orc_net *g, const orc_params *prm, const orc_query *q, co
                  uint32_t ant, uint32_t *route_edges, uint32_t *steps, uint32_t *T, uint32_t *W)
 {
     uint32_t alpha, beta;
-    int rc = query_ok(g, q, &alpha, &beta);
+    int frac;
+    int rc = query_ok(g, q, &alpha, &beta, &frac);
     if (rc != ORC_OK)
         return -rc;
     orc_state S;
     rc = state_init(&S, g, prm, q->dst);
     if (rc != ORC_OK)
         return -rc;
-    int st = walk(&S, q, alpha, beta, tau, it, ant, route_edges, steps, T, W);
+    int st = walk(&S, q, alpha, beta, frac, tau, it, ant, route_edges, steps, T, W);
     state_free(&S);
     return st;
 }
@@ -698,7 +799,8 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
 {
     memset(res, 0, sizeof *res);
     uint32_t alpha, beta;
-    int rc = query_ok(g, q, &alpha, &beta);
+    int frac;
+    int rc = query_ok(g, q, &alpha, &beta, &frac);
     if (rc != ORC_OK) {
         res->status = rc;
         return rc;
@@ -735,7 +837,7 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
             memset(D, 0, sizeof(uint64_t) * E);
             for (uint32_t k = 0; k < q->n_ants; ++k) {
                 uint32_t steps, T, W;
-                int st = walk(&S, q, alpha, beta, tau, it, k, route, &steps, &T, &W);
+                int st = walk(&S, q, alpha, beta, frac, tau, it, k, route, &steps, &T, &W);
                 res->ant_steps += steps;
                 if (ant_log) {
                     uint32_t *l = ant_log + 4 * ((size_t)it * q->n_ants + k);

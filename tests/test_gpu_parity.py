@@ -249,7 +249,10 @@ def test_edge_cases(gm, ctx, orc):
     r = ctx.solve(0, 2, 8, 3, route_cap=2)
     assert r["status"] == gm.ERR_BUFFER and r["route_len"] == 3
     with pytest.raises(gm.GmpError) as e:
-        ctx.solve_batch([Q(0, 2, 8, 3, 1.5, 2.0, 0.1, 0)])
+        ctx.solve_batch([Q(0, 2, 8, 3, 8.5, 2.0, 0.1, 0)])
+    assert e.value.code == gm.ERR_UNSUPPORTED
+    with pytest.raises(gm.GmpError) as e:
+        ctx.solve_batch([Q(0, 2, 8, 3, 1.0, float("nan"), 0.1, 0)])
     assert e.value.code == gm.ERR_UNSUPPORTED
     with pytest.raises(gm.GmpError) as e:
         ctx.solve_batch([Q(0, 9, 8, 3, 1.0, 2.0, 0.1, 0)])

@@ -159,7 +159,7 @@ def test_submit_refuses_bad_requests(gm):
             srv.submit(W.Query(0, 100, 8, 2, 1.0, 2.0, 0.1, 1), 1)
         assert ei.value.code == gm.ERR_INVALID_ARG
         with pytest.raises(gm.GmpError) as ei:
-            srv.submit(W.Query(0, 9, 8, 2, 1.5, 2.0, 0.1, 1), 2)
+            srv.submit(W.Query(0, 9, 8, 2, 9.0, 2.0, 0.1, 1), 2)
         assert ei.value.code == gm.ERR_UNSUPPORTED
         with pytest.raises(gm.GmpError) as ei:
             srv.tick((1 << 30) - 10, 100)

@@ -268,7 +268,9 @@ def test_congestion_threshold_mask(orc):
 def test_invalid_and_unsupported_queries(orc):
     wl = W.grid10()
     onet = orc.Net.from_workload(wl)
-    assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, 1.5, 2.0, 0.1, 0))["status"] == orc.ERR_UNSUPPORTED
+    assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, 8.5, 2.0, 0.1, 0))["status"] == orc.ERR_UNSUPPORTED
+    assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, 1.0, -0.5, 0.1, 0))["status"] == orc.ERR_UNSUPPORTED
+    assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, float("nan"), 2.0, 0.1, 0))["status"] == orc.ERR_UNSUPPORTED
     assert orc.solve(onet, orc.Params(), Q(0, 99, 8, 2, 1.0, 2.0, 1.0, 0))["status"] == orc.ERR_INVALID
     assert orc.solve(onet, orc.Params(), Q(0, 100, 8, 2, 1.0, 2.0, 0.1, 0))["status"] == orc.ERR_INVALID
     assert orc.solve(onet, orc.Params(), Q(0, 99, 0, 2, 1.0, 2.0, 0.1, 0))["status"] == orc.ERR_INVALID
