@@ -34,7 +34,7 @@ extern "C" {
 #define GMP_ERR_OOM 3         /* device allocation failed or the context's memory budget is exceeded */
 #define GMP_ERR_CUDA 4        /* a CUDA runtime call failed (see gmp_last_error) */
 #define GMP_ERR_TIMEOUT 5     /* a bounded device-side wait expired (persistent launch) */
-#define GMP_ERR_UNSUPPORTED 6 /* non-integer alpha/beta, more than 8 phases, degree beyond the kernel limit */
+#define GMP_ERR_UNSUPPORTED 6 /* alpha/beta outside [0, 8], more than 8 phases, degree beyond the kernel limit */
 #define GMP_ERR_BUFFER 7      /* caller buffer too small; the required size is reported */
 #define GMP_ERR_STATE 8       /* call out of order (e.g. solve before gmp_load_graph) */
 
@@ -80,7 +80,10 @@ typedef struct {
 #define GMP_TAU_DENSE 1u
 #define GMP_TAU_SPARSE 2u
 
-/* One origin-destination colony. alpha, beta: integers in [0, 8]; rho in [0, 1). */
+/* One origin-destination colony. alpha, beta in [0, 8]: integers score f^alpha * (1/c)^beta by repeated
+ * binary32 multiplication; other values score 2^(alpha log2 f - beta log2 c) with the library's own
+ * binary32 log2 and exp2 (within 2^-21 (alpha |log2 f| + beta log2 c + 1) relative of the exact power).
+ * rho in [0, 1). */
 typedef struct {
     uint32_t src, dst, n_ants, n_iter;
     float alpha, beta, rho;

@@ -101,11 +101,11 @@ struct Batch {
 std::vector<uint32_t> topology_of(const Batch& b) {
     std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, (uint32_t)b.br.size(), b.maxI,
                             (uint32_t)b.kc.lanes, (uint32_t)b.kc.slots, b.kc.lockstep ? 1u : 0u,
-                            b.kc.tabu_in_smem ? 1u : 0u, (uint32_t)b.kc.block};
+                            b.kc.tabu_in_smem ? 1u : 0u, (uint32_t)b.kc.block, b.kc.frac ? 1u : 0u};
     for (const Batch::Branch& r : b.br) {
         t.push_back(r.maxI);
         t.push_back((uint32_t)r.kc.lanes | (uint32_t)r.kc.slots << 8 | (r.kc.lockstep ? 1u << 16 : 0u) |
-                    (r.kc.tabu_in_smem ? 1u << 17 : 0u));
+                    (r.kc.tabu_in_smem ? 1u << 17 : 0u) | (r.kc.frac ? 1u << 18 : 0u));
         t.push_back((uint32_t)r.kc.block);
     }
     return t;
@@ -118,7 +118,7 @@ bool same_plan(const std::vector<Batch::Branch>& x, const std::vector<Batch::Bra
         if (a.q0 != b.q0 || a.q1 != b.q1 || a.ants != b.ants || a.ticket_base != b.ticket_base || a.maxI != b.maxI ||
             a.tabu_off != b.tabu_off || a.kc.grid != b.kc.grid || a.kc.block != b.kc.block ||
             a.kc.lanes != b.kc.lanes || a.kc.slots != b.kc.slots || a.kc.smem != b.kc.smem ||
-            a.kc.tabu_in_smem != b.kc.tabu_in_smem || a.kc.lockstep != b.kc.lockstep)
+            a.kc.tabu_in_smem != b.kc.tabu_in_smem || a.kc.lockstep != b.kc.lockstep || a.kc.frac != b.kc.frac)
             return false;
     }
     return true;
@@ -368,11 +368,23 @@ int check_query(gmp_ctx* c, const gmp_query& q, uint32_t idx) {
     if (q.n_ants == 0 || q.n_iter == 0) return fail(c, GMP_ERR_INVALID_ARG, "query %u: n_ants and n_iter must be >= 1", idx);
     if ((uint64_t)q.n_ants * q.n_iter > 0xFFFFFFFFull)
         return fail(c, GMP_ERR_INVALID_ARG, "query %u: n_ants * n_iter must be < 2^32", idx);
-    if (!(q.alpha >= 0.0f && q.alpha <= 8.0f && q.beta >= 0.0f && q.beta <= 8.0f) || floorf(q.alpha) != q.alpha ||
-        floorf(q.beta) != q.beta)
-        return fail(c, GMP_ERR_UNSUPPORTED, "query %u: alpha and beta must be integers in [0, 8]", idx);
+    if (!(q.alpha >= 0.0f && q.alpha <= 8.0f && q.beta >= 0.0f && q.beta <= 8.0f))
+        return fail(c, GMP_ERR_UNSUPPORTED, "query %u: alpha and beta must lie in [0, 8]", idx);
     if (!(q.rho >= 0.0f && q.rho < 1.0f)) return fail(c, GMP_ERR_INVALID_ARG, "query %u: rho must lie in [0, 1)", idx);
     return GMP_OK;
+}
+
+// Exponents as the kernels take them: integers as integers (repeated multiplication); otherwise both
+// as binary32 bits with kQueryFracExp set in `active` (the 2^L score). Call after `active` is set.
+void set_exponents(DevQuery& d, float alpha, float beta) {
+    if (floorf(alpha) != alpha || floorf(beta) != beta) {
+        memcpy(&d.alpha, &alpha, sizeof alpha);
+        memcpy(&d.beta, &beta, sizeof beta);
+        if (d.active) d.active |= kQueryFracExp;
+    } else {
+        d.alpha = (uint32_t)alpha;
+        d.beta = (uint32_t)beta;
+    }
 }
 
 int record(gmp_ctx* c, Batch& b, size_t i) {
@@ -885,15 +897,16 @@ uint32_t branch_count(const gmp_ctx* c, uint32_t n) {
     return std::max<uint32_t>(1u, std::min(n, want));
 }
 
-// Launch shape of the job for the context's parameters and `total_ants` ants per iteration.
-int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc) {
+// Launch shape of the job for the context's parameters and `total_ants` ants per iteration; `frac` when
+// some colony of the job has non-integer exponents.
+int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc, bool frac = false) {
     *kc = KernelConfig{};
     const uint32_t ants = (uint32_t)std::min<uint64_t>(total_ants, 0xFFFFFFFFull);
     if (c->prm.mode == GMP_MODE_PERSISTENT) {
         if (lanes == 1) return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs 4, 8, 16 or 32 lanes per ant");
         GMP_CUDA(c, persistent_config(c->device, lanes, c->N, c->maxdeg, kc));
     } else if (lanes != 1 && !(c->prm.flags & kFlagNoLockstep) && lockstep_fits(lanes, c->maxdeg)) {
-        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, ants, kc));
+        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, ants, frac, kc));
     } else {
         GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, ants, kc));
     }
@@ -967,7 +980,7 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
         if (B == 1) {
             r.kc = b.kc;
         } else {
-            GMP_TRY(job_config(c, lanes, std::max<uint32_t>(r.ants, 1u), &r.kc));
+            GMP_TRY(job_config(c, lanes, std::max<uint32_t>(r.ants, 1u), &r.kc, b.kc.frac));
             const uint64_t share = ((uint64_t)b.kc.grid * r.ants + b.total_ants - 1) / std::max<uint32_t>(b.total_ants, 1u);
             r.kc.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)r.kc.grid, share));
         }
@@ -1040,10 +1053,9 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
         d.dst = q.dst;
         d.n_ants = q.n_ants;
         d.n_iter = q.n_iter;
-        d.alpha = (uint32_t)q.alpha;
-        d.beta = (uint32_t)q.beta;
         d.ant_base = (uint32_t)total;
         d.active = q.src != q.dst;
+        set_exponents(d, q.alpha, q.beta);
         d.rho_fix = (uint64_t)nearbyint(ldexp((double)q.rho, 32));
         d.seed = q.seed;
         d.log_base = logs;
@@ -1065,7 +1077,9 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     if (c->prm.tau_layout == GMP_TAU_SPARSE && (b.persistent || (c->prm.flags & GMP_FLAG_RANDOM_TAU)))
         return fail(c, GMP_ERR_UNSUPPORTED, "the sparse pheromone layout needs the iterative job and 1.0 initial pheromone");
     b.sparse = use_sparse(c);
-    GMP_TRY(job_config(c, lanes, b.total_ants, &b.kc));
+    bool frac = false;
+    for (uint32_t i = 0; i < n; ++i) frac = frac || (hdq[i].active & kQueryFracExp) != 0u;
+    GMP_TRY(job_config(c, lanes, b.total_ants, &b.kc, frac));
     GMP_TRY(plan_branches(c, lanes, prefix));
     GMP_TRY(reserve_workspace(c, n, b.total_ants, maxI, b.log_entries, b.kc));
     GMP_TRY(upload(c, b.dq, hdq.data(), n));
@@ -1581,7 +1595,8 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
         return fail(c, GMP_ERR_BUFFER, "route buffer needs %u entries (max_steps + 1)", S + 1u);
     KernelConfig kc{};
     if (lanes <= 16 && c->maxdeg <= (uint32_t)(2 * lanes) && lanes * (c->maxdeg <= (uint32_t)lanes ? 1 : 2) <= 16)
-        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, n_ants, &kc));
+        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, n_ants,
+                                              floorf(alpha) != alpha || floorf(beta) != beta, &kc));
     else
         GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, n_ants, &kc));
     // carve the scratch array
@@ -1618,10 +1633,9 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     hq.dst = dst;
     hq.n_ants = n_ants;
     hq.n_iter = n_iter;
-    hq.alpha = (uint32_t)alpha;
-    hq.beta = (uint32_t)beta;
     hq.ant_base = 0;
     hq.active = src != dst;
+    set_exponents(hq, alpha, beta);
     hq.rho_fix = (uint64_t)nearbyint(ldexp((double)rho, 32));
     hq.seed = seed;
     hq.xd = c->hx[dst];

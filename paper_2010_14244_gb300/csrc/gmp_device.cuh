@@ -44,7 +44,8 @@ constexpr uint32_t kQdMask = 0x7FFFFFFFu;
 // One colony of a batch, as the kernels read it.
 struct __align__(16) DevQuery {
     uint32_t src, dst, n_ants, n_iter;
-    uint32_t alpha, beta, ant_base, active;  // active == 0 when src == dst (answered without ants)
+    uint32_t alpha, beta, ant_base, active;  // active == 0 when src == dst (answered without ants); with
+                                             // kQueryFracExp set, alpha and beta hold binary32 bits
     uint64_t rho_fix;                        // round(rho * 2^32)
     uint64_t seed;
     int32_t xd, yd;                          // destination coordinates
@@ -183,6 +184,74 @@ __device__ __forceinline__ float u32_to_f32_rn(uint32_t c) {
     return __fmaf_rn(hi, 64.0f, lo);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Non-integer alpha / beta: the score as 2^L, L = alpha*log2(f) - beta*log2(c), from a binary32 log2
+// and exp2 of our own (single rounded operations, no FMA contraction).
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kQueryFracExp = 2u;  // DevQuery::active bit: alpha and beta are binary32 bits
+
+// Series coefficients, each the binary32 nearest its exact value: 1/3, 1/5, 1/7, 1/9 and 2/ln 2 for
+// the atanh series of log2; ln(2)^k / k! for k = 1..8 for the Taylor series of 2^f.
+constexpr float kLogC3 = 0x1.555556p-2f, kLogC5 = 0x1.99999ap-3f, kLogC7 = 0x1.24924ap-3f, kLogC9 = 0x1.c71c72p-4f,
+                kLogK = 0x1.715476p+1f;
+constexpr float kExpC1 = 0x1.62e430p-1f, kExpC2 = 0x1.ebfbe0p-3f, kExpC3 = 0x1.c6b08ep-5f, kExpC4 = 0x1.3b2ab6p-7f,
+                kExpC5 = 0x1.5d87fep-10f, kExpC6 = 0x1.430912p-13f, kExpC7 = 0x1.ffcbfcp-17f,
+                kExpC8 = 0x1.62c022p-20f;
+
+// log2 x for a positive normal x: x = 2^e * m with m in (1/sqrt 2, sqrt 2] (the range reduction of
+// Cody & Waite, Software Manual for the Elementary Functions, 1980), then ln m = 2 atanh(t),
+// t = (m - 1) / (m + 1), |t| <= 0.1716, by the atanh series through t^9 (truncation below 2^-28).
+__device__ __forceinline__ float log2_cw(float x) {
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)(b >> 23) - 127;
+    uint32_t mb = (b & 0x7FFFFFu) | 0x3F800000u;
+    if (mb > 0x3FB504F3u) {  // m above sqrt 2 (rounded down): use m / 2
+        mb -= 0x00800000u;
+        ++e;
+    }
+    const float m = __uint_as_float(mb);
+    const float t = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float t2 = __fmul_rn(t, t);
+    float p = kLogC9;
+    p = __fadd_rn(__fmul_rn(p, t2), kLogC7);
+    p = __fadd_rn(__fmul_rn(p, t2), kLogC5);
+    p = __fadd_rn(__fmul_rn(p, t2), kLogC3);
+    p = __fadd_rn(__fmul_rn(p, t2), 1.0f);
+    return __fadd_rn(__int2float_rn(e), __fmul_rn(__fmul_rn(t, kLogK), p));
+}
+
+// 2^L: the largest finite binary32 for L >= 128 (saturation, as for integer exponents), 0 below -150;
+// else n = floor(L), f = L - n in [0, 1) (exact), 2^f by its Taylor series through f^8 (truncation
+// below 2^-26) capped below 2, scaled by 2^n in two exact power-of-two steps (the second rounds only
+// into the subnormal range).
+__device__ __forceinline__ float exp2_sat(float L) {
+    if (!(L < 128.0f)) return 3.40282347e38f;
+    if (L < -150.0f) return 0.0f;
+    const float n = floorf(L);
+    const float f = __fsub_rn(L, n);
+    float p = kExpC8;
+    p = __fadd_rn(__fmul_rn(p, f), kExpC7);
+    p = __fadd_rn(__fmul_rn(p, f), kExpC6);
+    p = __fadd_rn(__fmul_rn(p, f), kExpC5);
+    p = __fadd_rn(__fmul_rn(p, f), kExpC4);
+    p = __fadd_rn(__fmul_rn(p, f), kExpC3);
+    p = __fadd_rn(__fmul_rn(p, f), kExpC2);
+    p = __fadd_rn(__fmul_rn(p, f), kExpC1);
+    p = __fadd_rn(__fmul_rn(p, f), 1.0f);
+    p = fminf(p, 0x1.fffffep0f);
+    const int ni = (int)n;
+    const int n1 = ni >> 1, n2 = ni - n1;  // floor(n / 2): both in [-75, 64]
+    return __fmul_rn(__fmul_rn(p, __uint_as_float((uint32_t)(n1 + 127) << 23)),
+                     __uint_as_float((uint32_t)(n2 + 127) << 23));
+}
+
+// Score for non-integer exponents (alpha, beta in [0, 8] as floats): 2^(alpha log2 tf - beta log2 c).
+__device__ __forceinline__ float score_frac(float tf, float alpha, uint32_t c, float beta) {
+    const float A = __fmul_rn(alpha, log2_cw(tf));
+    const float B = __fmul_rn(beta, log2_cw(u32_to_f32_rn(c)));
+    return exp2_sat(__fsub_rn(A, B));
+}
+
 // Next-node desirability from the pheromone word tf (tau_word): tf^alpha * (1 / c)^beta, c = travel +
 // wait + remaining bound (ms), 1 <= c < 2^29. tf < 2^32, so tf^alpha can overflow from alpha = 5 on:
 // it saturates at the largest finite binary32, and eta^beta <= 1 keeps every score finite (the roulette
@@ -192,6 +261,13 @@ __device__ __forceinline__ float score_f(float tf, uint32_t alpha, uint32_t c, u
     const float eta = rcp_rn(u32_to_f32_rn(c));
     if (alpha == 1u && beta == 2u) return __fmul_rn(tf, __fmul_rn(eta, eta));
     return __fmul_rn(fminf(pow_int(tf, alpha), 3.40282347e38f), pow_int(eta, beta));
+}
+
+// The score of a colony: integer exponents by score_f, others (frac) by score_frac with alpha and beta
+// as binary32 bits.
+__device__ __forceinline__ float score_q(float tf, uint32_t alpha, uint32_t c, uint32_t beta, bool frac) {
+    if (frac) return score_frac(tf, __uint_as_float(alpha), c, __uint_as_float(beta));
+    return score_f(tf, alpha, c, beta);
 }
 
 // The roulette's index r = floor(rnd * S / 2^64) for a 64-bit draw and S < 2^32, from two 32x32 -> 64

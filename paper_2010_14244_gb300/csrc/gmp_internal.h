@@ -108,6 +108,8 @@ struct KernelConfig {
     size_t smem;           // dynamic shared memory per block
     bool tabu_in_smem;
     bool lockstep = false;  // all ants of a warp step together (k_construct_gl / k_construct_lock)
+    bool frac = false;      // some colony has non-integer exponents: the lockstep kernel's instantiation
+                            // with the 2^L score (the others check each colony at run time)
 };
 
 // Launchers (gmp_kernels.cu).
@@ -148,7 +150,7 @@ cudaError_t launch_persistent(cudaStream_t s, const KernelConfig& kc, const Pers
 cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, uint32_t total_ants,
                              KernelConfig* out);
 cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, uint32_t max_degree,
-                                      uint32_t total_ants, KernelConfig* out);
+                                      uint32_t total_ants, bool frac, KernelConfig* out);
 int construct_max_degree(int lanes);
 bool construct_thread_fits(uint32_t n_nodes);
 

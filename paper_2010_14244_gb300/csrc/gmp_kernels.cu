@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
 // come from one warp-aggregated atomic per round. The loads of an ant's next row are issued as soon as
 // it moves, so their latency overlaps the end of the step and the loop's bookkeeping.
 // ------------------------------------------------------------------------------------------------
-template <int G, int K, bool SMEM>
+template <int G, int K, bool SMEM, bool FRAC>
 __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t it) {
     extern __shared__ uint32_t smem[];
     constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     const uint32_t lt_mask = (1u << wl) - 1u;
     bool active = false, exhausted = false;
     uint32_t qi = 0, k = 0, slot = 0, src = 0, dst = 0, n_ants = 1, alpha = 1, beta = 2, s0 = 0, s1 = 0;
+    bool frac = false;  // non-integer exponents (FRAC instantiations only): alpha and beta are binary32 bits
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
     // Philox draws of the next G steps, one per lane: lane l holds the draw of step rb_base + l
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         n_ants = q.n_ants;
                         alpha = q.alpha;
                         beta = q.beta;
+                        frac = FRAC && (q.active & kQueryFracExp) != 0u;
                         s0 = (uint32_t)q.seed;
                         s1 = (uint32_t)(q.seed >> 32);
                         log_base = q.log_base;
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 const uint32_t sw = signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
                 const uint32_t w = (v != dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
                 wv[j] = w;
-                sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].z + w + he[j], beta));
+                sb[j] = __float_as_uint(score_q(tf[j], alpha, r0[j].z + w + he[j], beta, frac));
             }
             constexpr uint32_t kGroupBits = G == 32 ? FULL : ((1u << (G & 31)) - 1u);
             const uint32_t gshift = wl & ~(uint32_t)(G - 1);
@@ -547,6 +549,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
     // per-thread ant
     bool active = false, exhausted = false, first = true;
     uint32_t qi = 0, k = 0, slot = 0, src = 0, dst = 0, n_ants = 1, alpha = 1, beta = 2, s0 = 0, s1 = 0;
+    bool frac = false;  // non-integer exponents: alpha and beta are binary32 bits
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
     const uint2* th = a.th;
@@ -589,6 +592,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                         n_ants = q.n_ants;
                         alpha = q.alpha;
                         beta = q.beta;
+                        frac = (q.active & kQueryFracExp) != 0u;
                         s0 = (uint32_t)q.seed;
                         s1 = (uint32_t)(q.seed >> 32);
                         log_base = q.log_base;
@@ -658,7 +662,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                         signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
                     const uint32_t w = (v != dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
                     wv[j] = w;
-                    sb[j] = __float_as_uint(score_f(tf[j], alpha, r0[j].z + w + he[j], beta));
+                    sb[j] = __float_as_uint(score_q(tf[j], alpha, r0[j].z + w + he[j], beta, frac));
                 }
             }
             if (a.thr_on && (cmask & ~cong) && (cmask & cong)) cmask &= ~cong;
@@ -1067,7 +1071,7 @@ cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t m
 }
 
 template <int G, int K>
-static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out) {
+static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, bool frac, KernelConfig* out) {
     const int block = 128;
     const int groups = block / G;
     const uint32_t words = (n_nodes + 31u) / 32u;
@@ -1079,13 +1083,20 @@ static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, 
     if (in_smem) {
         if (dyn > 48u * 1024u) {
             // per kernel function, shared by every context: the cap of in-smem bitmaps, not this size
-            err = cudaFuncSetAttribute(k_construct_gl<G, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            err = cudaFuncSetAttribute(k_construct_gl<G, K, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        64 * 1024);
+            if (err == cudaSuccess)
+                err = cudaFuncSetAttribute(k_construct_gl<G, K, true, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
             if (err != cudaSuccess) return err;
         }
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true>, block, dyn);
+        err = frac ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true, true>, block, dyn)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true, false>, block,
+                                                                   dyn);
     } else {
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, false>, block, 0);
+        err = frac ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, false, true>, block, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, false, false>, block,
+                                                                   0);
     }
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -1101,27 +1112,33 @@ static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, 
     out->smem = dyn;
     out->tabu_in_smem = in_smem;
     out->lockstep = true;
+    out->frac = frac;
     return cudaSuccess;
 }
 
 cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, uint32_t max_degree,
-                                      uint32_t total_ants, KernelConfig* out) {
+                                      uint32_t total_ants, bool frac, KernelConfig* out) {
     const int k = (uint32_t)lanes >= max_degree ? 1 : ((uint32_t)(2 * lanes) >= max_degree ? 2 : 0);
-    if (lanes == 4 && k == 1) return config_gl<4, 1>(device, n_nodes, total_ants, out);
-    if (lanes == 4 && k == 2) return config_gl<4, 2>(device, n_nodes, total_ants, out);
-    if (lanes == 8 && k == 1) return config_gl<8, 1>(device, n_nodes, total_ants, out);
-    if (lanes == 8 && k == 2) return config_gl<8, 2>(device, n_nodes, total_ants, out);
-    if (lanes == 16 && k == 1) return config_gl<16, 1>(device, n_nodes, total_ants, out);
+    if (lanes == 4 && k == 1) return config_gl<4, 1>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 4 && k == 2) return config_gl<4, 2>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 8 && k == 1) return config_gl<8, 1>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 8 && k == 2) return config_gl<8, 2>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 16 && k == 1) return config_gl<16, 1>(device, n_nodes, total_ants, frac, out);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it) {
     if (kc.lockstep) {
-#define GMP_LAUNCH_GL(G_, K_)                                                                     \
-    if (kc.lanes == G_ && kc.slots == K_) {                                                       \
-        if (kc.tabu_in_smem) k_construct_gl<G_, K_, true><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
-        else k_construct_gl<G_, K_, false><<<kc.grid, kc.block, 0, s>>>(a, it);                  \
-        return cudaGetLastError();                                                                \
+#define GMP_LAUNCH_GL(G_, K_)                                                                            \
+    if (kc.lanes == G_ && kc.slots == K_) {                                                              \
+        if (kc.frac) {                                                                                   \
+            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, true><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
+            else k_construct_gl<G_, K_, false, true><<<kc.grid, kc.block, 0, s>>>(a, it);               \
+        } else {                                                                                         \
+            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, false><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
+            else k_construct_gl<G_, K_, false, false><<<kc.grid, kc.block, 0, s>>>(a, it);              \
+        }                                                                                                \
+        return cudaGetLastError();                                                                       \
     }
         GMP_LAUNCH_GL(4, 1) GMP_LAUNCH_GL(4, 2) GMP_LAUNCH_GL(8, 1) GMP_LAUNCH_GL(8, 2) GMP_LAUNCH_GL(16, 1)
 #undef GMP_LAUNCH_GL

@@ -144,6 +144,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     constexpr bool kGather = NC <= 16;     // every lane gathers all scores and picks locally
     const uint2* __restrict__ th = a.th + (size_t)qi * a.n_edges;
     const float base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
+    const bool frac = (q.active & kQueryFracExp) != 0u;
     const uint32_t slot = q.ant_base + k;
     uint32_t* route = a.routes + (size_t)slot * a.max_steps;
     const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
@@ -196,7 +197,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             const uint32_t sw = signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
             const uint32_t w = (v != q.dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
             wv[j] = w;
-            sb[j] = __float_as_uint(score_f(tf[j], q.alpha, r0[j].z + w + he[j], q.beta));
+            sb[j] = __float_as_uint(score_q(tf[j], q.alpha, r0[j].z + w + he[j], q.beta, frac));
         }
         if (a.thr_on) {  // congested roads drop out unless every candidate is congested
             const uint32_t any_ok = __ballot_sync(gmask, (cmask & ~cong) != 0u) & gmask;

@@ -76,6 +76,45 @@ __global__ void k_weights(const unsigned* off, const unsigned* len, const float*
     for (unsigned i = 0; i < len[v]; ++i) w[off[v] + i] = roulette_weight_f(__float_as_uint(s[off[v] + i]), sc);
 }
 
+// Non-integer-exponent arithmetic, one record per thread: log2_cw(x), exp2_sat(L), score_frac(tf, a, c, b).
+struct FracIn {
+    float x, L, tf, alpha;
+    unsigned c;
+    float beta;
+};
+
+__global__ void k_frac(const FracIn* in, float* out, unsigned n) {
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const FracIn r = in[i];
+    out[3 * (size_t)i] = log2_cw(r.x);
+    out[3 * (size_t)i + 1] = exp2_sat(r.L);
+    out[3 * (size_t)i + 2] = score_frac(r.tf, r.alpha, r.c, r.beta);
+}
+
+static int frac(const char* in, const char* out) {
+    FILE* f = fopen(in, "rb");
+    if (!f) return 2;
+    unsigned n = 0;
+    if (fread(&n, 4, 1, f) != 1) return 2;
+    std::vector<FracIn> rec(n);
+    if (n && fread(rec.data(), sizeof(FracIn), n, f) != n) return 2;
+    fclose(f);
+    FracIn* din;
+    float* dout;
+    cudaMalloc(&din, sizeof(FracIn) * (size_t)n + 32);
+    cudaMalloc(&dout, 12 * (size_t)n + 16);
+    cudaMemcpy(din, rec.data(), sizeof(FracIn) * (size_t)n, cudaMemcpyHostToDevice);
+    k_frac<<<(n + 255) / 256, 256>>>(din, dout, n);
+    std::vector<float> res(3 * (size_t)n);
+    cudaMemcpy(res.data(), dout, 12 * (size_t)n, cudaMemcpyDeviceToHost);
+    if (cudaDeviceSynchronize() != cudaSuccess) return 3;
+    FILE* g = fopen(out, "wb");
+    fwrite(res.data(), 4, res.size(), g);
+    fclose(g);
+    return 0;
+}
+
 static int checks() {
     unsigned long long* bad;
     cudaMalloc(&bad, 8 * sizeof(unsigned long long));
@@ -131,5 +170,6 @@ static int weights(const char* in, const char* out) {
 
 int main(int argc, char** argv) {
     if (argc >= 2 && std::string_view(argv[1]) == "weights" && argc == 4) return weights(argv[2], argv[3]);
+    if (argc >= 2 && std::string_view(argv[1]) == "frac" && argc == 4) return frac(argv[2], argv[3]);
     return checks();
 }
