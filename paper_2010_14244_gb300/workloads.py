@@ -365,6 +365,38 @@ def city_batch(n_graphs=64, n_min=1000, n_max=200_000, q_lo=8, q_hi=64, ants_lo=
     return out
 
 
+def city52(seed=52) -> Workload:
+    """52 intersections joined by 64 two-way streets (128 directed roads, 3 lanes): a synthetic network
+    of the size of the paper's North-West Delhi map (Sec. 5), whose data is not published. A 4 x 13
+    lattice (800 m spacing, +-25 % jitter) keeps 64 of its 87 street segments at random, connected;
+    lengths are the straight line x U[1.0, 1.25], speeds U{30,50,70} km/h, 2-phase signals at nodes
+    with three or more streets, no background vehicles (the simulated vehicles are the traffic)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows, cols, sp = 4, 13, 8000
+    n = rows * cols
+    gx, gy = np.meshgrid(np.arange(cols), np.arange(rows))
+    x = np.round((gx.ravel() + rng.uniform(-0.25, 0.25, n)) * sp).astype(np.int64)
+    y = np.round((gy.ravel() + rng.uniform(-0.25, 0.25, n)) * sp).astype(np.int64)
+    pairs = [(r * cols + c, r * cols + c + 1) for r in range(rows) for c in range(cols - 1)]
+    pairs += [(r * cols + c, (r + 1) * cols + c) for r in range(rows - 1) for c in range(cols)]
+    pa = np.array([p for p, _ in pairs], np.int64)
+    pb = np.array([q for _, q in pairs], np.int64)
+    while True:
+        keep = np.sort(rng.choice(pa.size, size=64, replace=False))
+        if _connected(n, pa[keep], pb[keep]):
+            break
+    a, b = pa[keep], pb[keep]
+    dx, dy = np.abs(x[a] - x[b]), np.abs(y[a] - y[b])
+    eucl = np.sqrt((dx * dx + dy * dy).astype(np.float64))
+    length = np.ceil(eucl * rng.uniform(1.0, 1.25, a.size)).astype(np.int64)
+    speed = rng.choice(np.array(SPEEDS_KMH), size=a.size)
+    orient = (dy > dx).astype(np.int64)
+    net = csr_from_roads(n, a, b, length, speed, np.full(a.size, 3), orient, x, y)
+    sig = two_phase_signals(net, np.diff(net.row_ptr.astype(np.int64)) >= 3, rng)
+    return Workload("city52", net, sig, np.zeros(net.n_edges, np.uint32), [],
+                    "52 intersections, 128 directed roads, 3 lanes, 2-phase signals at 3+-street nodes")
+
+
 def random_small(n_nodes, n_undirected, rng, signalised_frac=0.0, len_lo=1000, len_hi=5000,
                  spacing_dm=1000) -> tuple[RoadNetwork, SignalTiming]:
     """Small connected random road graph on a sparse lattice layout (for brute-force checks)."""
