@@ -19,6 +19,7 @@ FLAG_REPULSIVE = 32
 FLAG_UNIT_DEPOSIT = 64
 FLAG_EVAP_UNUSED = 128
 FLAG_PAPER_LITERAL = FLAG_REPULSIVE | FLAG_UNIT_DEPOSIT | FLAG_EVAP_UNUSED
+FLAG_EXACT_H = 256
 ANT_SUCCESS, ANT_DEAD_END, ANT_STEP_CAP, ANT_TIME_CAP = 0, 1, 2, 3
 OK, ERR_INVALID, ERR_NO_ROUTE, ERR_OOM, ERR_UNSUPPORTED, ERR_BUFFER = 0, 1, 2, 3, 6, 7
 

@@ -21,6 +21,8 @@
  *   orc_log2, orc_exp2    pinned: error bounds against double-precision log2 / exp2, exact special
  *                         values, series constants against their exact values (Python fractions)
  *   orc_score_frac        pinned: error bound against double-precision powers, chi-square frequencies
+ *   orc_exact_heuristic   pinned: scipy's Dijkstra on the reversed graph, brute force over simple paths,
+ *                         the clamp for nodes that cannot reach the destination
  *   orc_quantize          pinned: exact rational arithmetic (Python fractions)
  *   orc_walk_one          pinned: hand-worked single-ant steps, chi-square frequency checks
  *   orc_solve             pinned: Dijkstra / time-dependent Dijkstra / brute-force simple-path
@@ -46,6 +48,7 @@
 #define ORC_FLAG_REPULSIVE 32u    /* prefer less pheromone: the score reads 1/tau in place of tau */
 #define ORC_FLAG_UNIT_DEPOSIT 64u /* Ph_road++: a successful ant adds exactly 1.0 to each road it used */
 #define ORC_FLAG_EVAP_UNUSED 128u /* deposits first, then only roads without a deposit evaporate */
+#define ORC_FLAG_EXACT_H 256u     /* Calc_Dist exactly: least congested travel time to the destination */
 
 enum {
     ORC_OK = 0,
@@ -542,6 +545,127 @@ uint64_t orc_evaporate(uint64_t tau, uint64_t rho_fix)
 }
 
 /* ------------------------------------------------------------------------------------------------ */
+/* Exact Calc_Dist (Algorithm 2 computes the distance to the destination over the routes of the      */
+/* graph): h(v) = the least sum of congested travel times over the roads of a path from v to dst,      */
+/* by Dijkstra's algorithm from dst over the reversed roads; nodes that cannot reach dst, and sums     */
+/* beyond it, take the clamp 2^28. Waits are not included, so h never exceeds the remaining time.      */
+/* ------------------------------------------------------------------------------------------------ */
+int orc_exact_heuristic(const orc_net *g, const uint32_t *tt, uint32_t dst, uint32_t *h)
+{
+    uint32_t N = g->n_nodes, E = g->n_edges;
+    uint32_t *rptr = calloc((size_t)N + 1, sizeof(uint32_t)), *redge = malloc(sizeof(uint32_t) * (E + 1));
+    uint32_t *tail = malloc(sizeof(uint32_t) * (E + 1));
+    uint64_t *dist = malloc(sizeof(uint64_t) * (N + 1));
+    uint8_t *done = calloc((size_t)N + 1, 1);
+    if (!rptr || !redge || !tail || !dist || !done) {
+        free(rptr);
+        free(redge);
+        free(tail);
+        free(dist);
+        free(done);
+        return ORC_ERR_OOM;
+    }
+    /* roads grouped by head: the reversed graph */
+    for (uint32_t u = 0; u < N; ++u)
+        for (uint32_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; ++e) {
+            tail[e] = u;
+            rptr[g->col[e] + 1]++;
+        }
+    for (uint32_t v = 0; v < N; ++v)
+        rptr[v + 1] += rptr[v];
+    {
+        uint32_t *fill = malloc(sizeof(uint32_t) * (N + 1));
+        if (!fill) {
+            free(rptr);
+            free(redge);
+            free(tail);
+            free(dist);
+            free(done);
+            return ORC_ERR_OOM;
+        }
+        memcpy(fill, rptr, sizeof(uint32_t) * N);
+        for (uint32_t e = 0; e < E; ++e)
+            redge[fill[g->col[e]]++] = e;
+        free(fill);
+    }
+    for (uint32_t v = 0; v < N; ++v)
+        dist[v] = UINT64_MAX;
+    dist[dst] = 0;
+    /* Dijkstra with a binary min-heap of (distance, node) entries and lazy deletion: an entry whose
+     * distance is above the node's current one is stale and skipped */
+    size_t cap = (size_t)E + 2, n_heap = 0;
+    uint64_t *hk = malloc(sizeof(uint64_t) * cap);
+    uint32_t *hv = malloc(sizeof(uint32_t) * cap);
+    if (!hk || !hv) {
+        free(hk);
+        free(hv);
+        free(rptr);
+        free(redge);
+        free(tail);
+        free(dist);
+        free(done);
+        return ORC_ERR_OOM;
+    }
+#define HEAP_SWAP(a, b)                                                                                  \
+    do {                                                                                                 \
+        uint64_t tk = hk[a];                                                                             \
+        uint32_t tv = hv[a];                                                                             \
+        hk[a] = hk[b];                                                                                   \
+        hv[a] = hv[b];                                                                                   \
+        hk[b] = tk;                                                                                      \
+        hv[b] = tv;                                                                                      \
+    } while (0)
+    hk[0] = 0;
+    hv[0] = dst;
+    n_heap = 1;
+    while (n_heap > 0) {
+        uint64_t d = hk[0];
+        uint32_t u = hv[0];
+        hk[0] = hk[--n_heap]; /* pop the root, sift the last entry down */
+        hv[0] = hv[n_heap];
+        for (size_t i = 0;;) {
+            size_t l = 2 * i + 1, r = l + 1, m = i;
+            if (l < n_heap && hk[l] < hk[m])
+                m = l;
+            if (r < n_heap && hk[r] < hk[m])
+                m = r;
+            if (m == i)
+                break;
+            HEAP_SWAP(i, m);
+            i = m;
+        }
+        if (done[u] || d > dist[u])
+            continue;
+        done[u] = 1;
+        for (uint32_t i = rptr[u]; i < rptr[u + 1]; ++i) {
+            uint32_t e = redge[i], v = tail[e];
+            uint64_t nd = dist[u] + tt[e];
+            if (nd < dist[v]) {
+                dist[v] = nd;
+                size_t j = n_heap++; /* push, sift up (each road pushes at most once: cap = E + 2) */
+                hk[j] = nd;
+                hv[j] = v;
+                while (j > 0 && hk[(j - 1) / 2] > hk[j]) {
+                    HEAP_SWAP(j, (j - 1) / 2);
+                    j = (j - 1) / 2;
+                }
+            }
+        }
+    }
+#undef HEAP_SWAP
+    free(hk);
+    free(hv);
+    for (uint32_t v = 0; v < N; ++v)
+        h[v] = dist[v] > ORC_H_CLAMP ? ORC_H_CLAMP : (uint32_t)dist[v];
+    free(rptr);
+    free(redge);
+    free(tail);
+    free(dist);
+    free(done);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
 /* Solve state                                                                                          */
 /* ------------------------------------------------------------------------------------------------ */
 typedef struct {
@@ -609,8 +733,16 @@ static int state_init(orc_state *S, const orc_net *g, const orc_params *prm, uin
                 vmax = g->speed_kmh[e];
         }
     uint64_t kappa = orc_kappa(vmax);
-    for (uint32_t v = 0; v < N; ++v)
-        S->h[v] = orc_heuristic_ms(g->x_dm[v], g->y_dm[v], g->x_dm[dst], g->y_dm[dst], kappa);
+    if (prm && (prm->flags & ORC_FLAG_EXACT_H)) {
+        int hr = orc_exact_heuristic(g, S->tt, dst, S->h);
+        if (hr != ORC_OK) {
+            state_free(S);
+            return hr;
+        }
+    } else {
+        for (uint32_t v = 0; v < N; ++v)
+            S->h[v] = orc_heuristic_ms(g->x_dm[v], g->y_dm[v], g->x_dm[dst], g->y_dm[dst], kappa);
+    }
     int rc = orc_queue_preempt(g, prm, S->order);
     if (rc != ORC_OK) {
         state_free(S);
