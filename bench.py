@@ -412,6 +412,34 @@ def run_gpu(args, rank, world, local_rank):
         e2e = {"value": e2e_steps / e2e_t, "unit": "ant-steps/s",
                "h2d_bytes_per_step": int(wl.net.n_edges * 4 + nq * 40), "d2h_bytes_per_step": int(d2h),
                "queries_per_s": nq * args.steps / e2e_t}
+    # the same colonies with the exact heuristic (a different colony, so not the headline): its job time,
+    # ant-steps and routes next to the default straight-line bound's
+    exact = None
+    if not args.no_plain:
+        ctx.set_params(**dict(sched, flags=sched["flags"] | gmacop.FLAG_EXACT_H))
+        ctx.stage(wl.queries)
+        ex_times = []
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                ctx.launch()
+            stream.synchronize()
+            for _ in range(3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.launch()
+                e1.record(stream)
+                e1.synchronize()
+                ex_times.append(e0.elapsed_time(e1))
+        rex = ctx.collect()
+        ex_ms = statistics.median(ex_times)
+        ex_steps = sum(r["ant_steps"] for r in rex)
+        exact = {"ms_per_job": ex_ms, "ant_steps_per_job": ex_steps, "ant_steps_per_s": ex_steps / (ex_ms / 1e3),
+                 "queries_per_s": nq / (ex_ms / 1e3), "successful_ants": int(sum(r["n_success"] for r in rex)),
+                 "successful_ants_default": int(sum(r["n_success"] for r in res)),
+                 "mean_best_travel_s": float(np.mean([r["travel_ms"] for r in rex]) / 1e3),
+                 "mean_best_travel_s_default": float(np.mean([r["travel_ms"] for r in res]) / 1e3)}
+        ctx.set_params(**sched)
     ctx.close()
     serving = serving_1m = geo = None
     if not args.no_serving and rank == 0:
@@ -467,6 +495,8 @@ def run_gpu(args, rank, world, local_rank):
         line["serving_1m_nodes"] = serving_1m
     if geo:
         line["batched_geo100k"] = geo
+    if exact:
+        line["exact_heuristic"] = exact
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(nq)
     print(json.dumps(line), flush=True)

@@ -33,7 +33,7 @@ extern "C" {
 #define GMP_ERR_NO_ROUTE 2    /* no ant reached the destination in any iteration */
 #define GMP_ERR_OOM 3         /* device allocation failed or the context's memory budget is exceeded */
 #define GMP_ERR_CUDA 4        /* a CUDA runtime call failed (see gmp_last_error) */
-#define GMP_ERR_TIMEOUT 5     /* a bounded device-side wait expired (persistent launch) */
+#define GMP_ERR_TIMEOUT 5     /* a bounded device-side wait or loop expired (persistent launch, exact heuristic) */
 #define GMP_ERR_UNSUPPORTED 6 /* alpha/beta outside [0, 8], more than 8 phases, degree beyond the kernel limit */
 #define GMP_ERR_BUFFER 7      /* caller buffer too small; the required size is reported */
 #define GMP_ERR_STATE 8       /* call out of order (e.g. solve before gmp_load_graph) */
@@ -48,6 +48,11 @@ extern "C" {
 #define GMP_FLAG_UNIT_DEPOSIT 64u /* Ph_road++: each successful ant adds exactly 1.0 to each road used */
 #define GMP_FLAG_EVAP_UNUSED 128u /* deposits first; only roads without a deposit that iteration evaporate */
 #define GMP_FLAG_PAPER_LITERAL (GMP_FLAG_REPULSIVE | GMP_FLAG_UNIT_DEPOSIT | GMP_FLAG_EVAP_UNUSED)
+/* Calc_Dist exactly (Algorithm 2): h(v) = the least sum of congested travel times over a path from v to
+ * the colony's destination (2^28 when there is none), computed on the GPU per colony at the start of each
+ * job, in place of the straight-line bound; it also sets the deposit numerator h(src). Needs
+ * Q * (12 N + N / 8) bytes more workspace; gmp_solve_static refuses it (GMP_ERR_UNSUPPORTED). */
+#define GMP_FLAG_EXACT_H 256u
 
 #define GMP_MODE_AUTO 0u       /* library picks */
 #define GMP_MODE_ITERATIVE 1u  /* one kernel sequence per iteration, whole batch, CUDA-graph replay */

@@ -28,7 +28,8 @@ constexpr uint32_t kFlagKernelTiming = 4u;  // event records around every kernel
 constexpr uint32_t kFlagNoGraph = kFlagNoGraphBit;  // issue the job kernel by kernel instead of replaying a graph
 constexpr uint32_t kFlagNoLockstep = kFlagNoLockstepBit;  // sub-warp ants without warp lockstep
 constexpr uint32_t kKnownFlags =
-    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | GMP_FLAG_PAPER_LITERAL | kFlagKernelTiming | kFlagNoGraph | kFlagNoLockstep;
+    GMP_FLAG_RANDOM_TAU | GMP_FLAG_ANT_LOG | GMP_FLAG_PAPER_LITERAL | GMP_FLAG_EXACT_H | kFlagKernelTiming | kFlagNoGraph |
+    kFlagNoLockstep;
 constexpr int32_t kCoordLimit = 1 << 27;
 constexpr uint64_t kTickClockMax = 1ull << 48;  // lanes * (t + dt) stays below 2^64
 constexpr uint32_t kDefaultBranches = 16;        // concurrent colony chains of an iterative job
@@ -76,7 +77,12 @@ struct Batch {
     IterCounters* ctr = nullptr;
     uint32_t* qstate = nullptr;
     uint32_t* qflag = nullptr;
-    uint32_t* misc = nullptr;
+    uint32_t* misc = nullptr;  // [0] finished colonies, [1] persistent wait expired, [2] exact-h level bound
+    // exact Calc_Dist (GMP_FLAG_EXACT_H)
+    bool exact_h = false;
+    uint32_t* hdist = nullptr;   // Q * N bounds
+    uint32_t* hqueue = nullptr;  // Q * 2N frontiers
+    uint32_t* hmark = nullptr;   // Q * ceil(N / 32) queued marks
     // captured job
     cudaGraphExec_t exec = nullptr;  // the executable graph of the staged job (one of `execs`)
     std::map<std::vector<uint32_t>, cudaGraphExec_t> execs;  // by topology, refreshed by graph update
@@ -99,7 +105,7 @@ struct Batch {
 // What fixes the node structure of a captured job: the job form, timing events, the chains with their
 // iteration counts and kernel shapes. Jobs with equal topology differ only in kernel parameters.
 std::vector<uint32_t> topology_of(const Batch& b) {
-    std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, (uint32_t)b.br.size(), b.maxI,
+    std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, b.exact_h ? 1u : 0u, (uint32_t)b.br.size(), b.maxI,
                             (uint32_t)b.kc.lanes, (uint32_t)b.kc.slots, b.kc.lockstep ? 1u : 0u,
                             b.kc.tabu_in_smem ? 1u : 0u, (uint32_t)b.kc.block, b.kc.frac ? 1u : 0u};
     for (const Batch::Branch& r : b.br) {
@@ -137,6 +143,7 @@ struct gmp_ctx {
     bool has_graph = false;
     uint32_t N = 0, E = 0, maxdeg = 0, kappa = 0;
     uint32_t *row_ptr = nullptr, *col = nullptr, *len = nullptr, *in_ptr = nullptr, *in_edge = nullptr;
+    uint32_t* in_tail = nullptr;  // tail of each in_edge entry (exact Calc_Dist relaxes towards tails)
     uint32_t *ff = nullptr, *cap = nullptr;
     uint16_t* speed = nullptr;
     uint8_t* lanes = nullptr;
@@ -294,6 +301,9 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.qstate);
     dfree(c, &b.qflag);
     dfree(c, &b.misc);
+    dfree(c, &b.hdist);
+    dfree(c, &b.hqueue);
+    dfree(c, &b.hmark);
     b.staged = b.ran = false;
 }
 
@@ -304,6 +314,7 @@ void free_graph(gmp_ctx* c) {
     dfree(c, &c->len);
     dfree(c, &c->in_ptr);
     dfree(c, &c->in_edge);
+    dfree(c, &c->in_tail);
     dfree(c, &c->ff);
     dfree(c, &c->cap);
     dfree(c, &c->speed);
@@ -429,14 +440,25 @@ IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* 
     return e;
 }
 
+// Exact Calc_Dist of every colony of the job, ahead of the initialisation that reads it.
+int enqueue_exact_h(gmp_ctx* c) {
+    Batch& b = c->b;
+    if (!b.exact_h) return GMP_OK;
+    GMP_CUDA(c, cudaMemsetAsync(b.misc + 2, 0, 4, c->stream));
+    GMP_CUDA(c, launch_exact_h(c->stream, b.Q, c->N, b.dq, c->in_ptr, c->in_edge, c->in_tail, c->rec, b.hdist,
+                               b.hqueue, b.hmark, b.misc + 2));
+    return GMP_OK;
+}
+
 // The persistent job: init, one persistent launch, result rows.
 int enqueue_persistent(gmp_ctx* c) {
     Batch& b = c->b;
     cudaStream_t s = c->stream;
     const bool timed = b.timed;
     if (timed) GMP_TRY(record(c, b, 0));
+    GMP_TRY(enqueue_exact_h(c));
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
-                                  b.dep, b.qs, b.tickets, b.maxI, 0u, nullptr, 0u));
+                                  b.dep, b.qs, b.tickets, b.maxI, 0u, nullptr, 0u, b.exact_h ? b.hdist : nullptr, c->N));
     GMP_CUDA(c, launch_persistent_init(s, b.Q, b.maxI, b.dq, b.ctr, b.qstate, b.qflag, b.misc));
     if (b.tabu && b.tabu_used) GMP_CUDA(c, cudaMemsetAsync(b.tabu, 0, b.tabu_used * 4, s));
     if (timed) GMP_TRY(record(c, b, 1));
@@ -470,7 +492,7 @@ int enqueue_persistent(gmp_ctx* c) {
     if (timed) GMP_TRY(record(c, b, 2));
     GMP_CUDA(c, launch_finalize(s, b.Q, b.dq, b.qs, b.best_route, c->col, b.max_steps, b.res, b.route_out));
     if (timed) GMP_TRY(record(c, b, 3));
-    b.launches = 4;
+    b.launches = b.exact_h ? 5 : 4;
     return GMP_OK;
 }
 
@@ -549,9 +571,11 @@ int enqueue_job(gmp_ctx* c) {
     const size_t B = b.br.size();
     uint64_t n = 0;
     if (timed) GMP_TRY(record(c, b, 0));
+    GMP_TRY(enqueue_exact_h(c));
+    if (b.exact_h) ++n;
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
                                   b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B, b.sparse ? 1u : 0u, b.tflag,
-                                  tflag_words(c)));
+                                  tflag_words(c), b.exact_h ? b.hdist : nullptr, c->N));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
     // global visited bitmaps start clean; each walk clears its own bits when it ends
@@ -725,7 +749,7 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
             return fail(c, GMP_ERR_INVALID_ARG, "coordinate of node %u beyond +-2^27 dm", v);
     }
     uint32_t vmax = 1;
-    std::vector<uint32_t> in_ptr(N + 1, 0), in_edge(E);
+    std::vector<uint32_t> in_ptr(N + 1, 0), in_edge(E), in_tail(E);
     for (uint32_t e = 0; e < E; ++e) {
         if (col[e] >= N) return fail(c, GMP_ERR_INVALID_ARG, "col[%u] out of range", e);
         if (length_dm[e] == 0 || speed_kmh[e] == 0 || lanes[e] == 0)
@@ -735,8 +759,11 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     }
     for (uint32_t v = 0; v < N; ++v) in_ptr[v + 1] += in_ptr[v];
     {
-        std::vector<uint32_t> fill(in_ptr.begin(), in_ptr.end() - 1);
+        std::vector<uint32_t> fill(in_ptr.begin(), in_ptr.end() - 1), tail_of(E);
         for (uint32_t e = 0; e < E; ++e) in_edge[fill[col[e]]++] = e;
+        for (uint32_t u = 0; u < N; ++u)
+            for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) tail_of[e] = u;
+        for (uint32_t i = 0; i < E; ++i) in_tail[i] = tail_of[in_edge[i]];
     }
     cudaSetDevice(c->device);
     sync(c);
@@ -752,6 +779,7 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     GMP_TRY(dalloc(c, &c->len, E));
     GMP_TRY(dalloc(c, &c->in_ptr, N + 1));
     GMP_TRY(dalloc(c, &c->in_edge, E));
+    GMP_TRY(dalloc(c, &c->in_tail, E));
     GMP_TRY(dalloc(c, &c->ff, E));
     GMP_TRY(dalloc(c, &c->cap, E));
     GMP_TRY(dalloc(c, &c->speed, E));
@@ -778,6 +806,7 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     GMP_TRY(upload(c, c->y, y_dm, N));
     GMP_TRY(upload(c, c->in_ptr, in_ptr.data(), N + 1));
     GMP_TRY(upload(c, c->in_edge, in_edge.data(), E));
+    GMP_TRY(upload(c, c->in_tail, in_tail.data(), E));
     GMP_CUDA(c, cudaMemsetAsync(c->nph, 0, N, c->stream));
     GMP_CUDA(c, cudaMemsetAsync(c->ephase, 0, std::max<size_t>(E, 1), c->stream));
     GMP_CUDA(c, cudaMemsetAsync(c->cycle, 0, N * 4ull, c->stream));
@@ -946,7 +975,12 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
         GMP_TRY(ensure(c, &b.ctr, (size_t)n * maxI));
         GMP_TRY(ensure(c, &b.qstate, n));
         GMP_TRY(ensure(c, &b.qflag, maxI));
-        GMP_TRY(ensure(c, &b.misc, 2));
+    }
+    if (persistent || (c->prm.flags & GMP_FLAG_EXACT_H)) GMP_TRY(ensure(c, &b.misc, 3));
+    if (c->prm.flags & GMP_FLAG_EXACT_H) {
+        GMP_TRY(ensure(c, &b.hdist, (size_t)n * c->N));
+        GMP_TRY(ensure(c, &b.hqueue, (size_t)n * 2 * c->N));
+        GMP_TRY(ensure(c, &b.hmark, (size_t)n * words));
     }
     if (log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)log_entries * 4));
     // visited bitmaps in global memory: the job's grid plus one block per concurrent chain (chain grids
@@ -1074,6 +1108,7 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.maxI = maxI;
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
     b.persistent = c->prm.mode == GMP_MODE_PERSISTENT;
+    b.exact_h = (c->prm.flags & GMP_FLAG_EXACT_H) != 0;
     if (c->prm.tau_layout == GMP_TAU_SPARSE && (b.persistent || (c->prm.flags & GMP_FLAG_RANDOM_TAU)))
         return fail(c, GMP_ERR_UNSUPPORTED, "the sparse pheromone layout needs the iterative job and 1.0 initial pheromone");
     b.sparse = use_sparse(c);
@@ -1181,10 +1216,12 @@ int gmp_batch_collect(gmp_ctx* c, gmp_result* results) {
     cudaSetDevice(c->device);
     std::vector<DevResult> hr(b.Q);
     GMP_CUDA(c, cudaMemcpyAsync(hr.data(), b.res, b.Q * sizeof(DevResult), cudaMemcpyDeviceToHost, c->stream));
-    uint32_t misc[2] = {0, 0};
-    if (b.persistent) GMP_CUDA(c, cudaMemcpyAsync(misc, b.misc, sizeof misc, cudaMemcpyDeviceToHost, c->stream));
+    uint32_t misc[3] = {0, 0, 0};
+    if (b.persistent || b.exact_h)
+        GMP_CUDA(c, cudaMemcpyAsync(misc, b.misc, sizeof misc, cudaMemcpyDeviceToHost, c->stream));
     GMP_TRY(sync(c));
-    if (misc[1]) return fail(c, GMP_ERR_TIMEOUT, "a bounded device wait of the persistent job expired");
+    if (b.persistent && misc[1]) return fail(c, GMP_ERR_TIMEOUT, "a bounded device wait of the persistent job expired");
+    if (b.exact_h && misc[2]) return fail(c, GMP_ERR_TIMEOUT, "the exact heuristic's relaxation passed its level bound");
     for (uint32_t i = 0; i < b.Q; ++i) {
         gmp_result& r = results[i];
         const DevResult& d = hr[i];
@@ -1580,6 +1617,8 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     qq.rho = rho;
     qq.seed = seed;
     GMP_TRY(check_query(c, qq, 0));
+    if (c->prm.flags & GMP_FLAG_EXACT_H)
+        return fail(c, GMP_ERR_UNSUPPORTED, "the allocation-free solve has no room for the exact heuristic");
     if (c->device < 0 || c->device >= kStaticMaxDevices) return fail(c, GMP_ERR_UNSUPPORTED, "device index too high");
     const int lanes = pick_lanes(c);
     if ((uint32_t)construct_max_degree(lanes) < c->maxdeg || c->maxdeg > 128u || lanes == 1)
@@ -1646,7 +1685,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     GMP_CUDA(c, cudaGetLastError());
     // init clears the pheromone, deposits, colony state and ticket counters left by the previous call
     GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, th, dep,
-                                  qs, tickets, n_iter, 0u, nullptr, 0u));
+                                  qs, tickets, n_iter, 0u, nullptr, 0u, nullptr, c->N));
     if (tabu)  // global visited bitmaps start clean; each walk clears its own bits when it ends
         GMP_CUDA(c, cudaMemsetAsync(tabu, 0, (size_t)kc.grid * (kc.block / kc.lanes) * words * 4, s));
     ConstructArgs a{};

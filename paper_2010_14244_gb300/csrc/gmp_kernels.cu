@@ -150,17 +150,102 @@ __global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
 }
 
 // ------------------------------------------------------------------------------------------------
+// Exact Calc_Dist (GMP_FLAG_EXACT_H): per colony, h(v) = the least sum of congested travel times over
+// the roads of a path from v to the colony's destination, saturating at 2^28 (also for nodes that
+// cannot reach it). One block per colony relaxes from the destination over the reversed roads, level by
+// level (label-correcting Bellman-Ford): a level first unmarks its frontier, then lowers each frontier
+// node's predecessors with atomicMin and queues every predecessor it lowered once (the mark bitmap).
+// The saturating sums are monotone, so the fixpoint is the clamped exact distance in any relaxation
+// order. A node reaches its final bound within as many levels as its shortest path has roads, so there
+// are at most N levels; a block that gets past N sets err[0] (it cannot happen) and stops.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kExactHBlock = 512;
+
+__global__ void __launch_bounds__(kExactHBlock) k_exact_h(uint32_t N, const DevQuery* __restrict__ q,
+                                                          const uint32_t* __restrict__ in_ptr,
+                                                          const uint32_t* __restrict__ in_edge,
+                                                          const uint32_t* __restrict__ in_tail,
+                                                          const EdgeRec* __restrict__ rec, uint32_t* hdist,
+                                                          uint32_t* queue, uint32_t* mark, uint32_t words,
+                                                          uint32_t* err) {
+    const uint32_t qi = blockIdx.x;
+    const uint32_t dst = q[qi].dst;
+    uint32_t* dist = hdist + (size_t)qi * N;
+    uint32_t* qa = queue + (size_t)qi * 2u * N;  // this level's frontier
+    uint32_t* qb = qa + N;                       // the next level's
+    uint32_t* mk = mark + (size_t)qi * words;
+    __shared__ uint32_t n_next;
+    for (uint32_t v = threadIdx.x; v < N; v += blockDim.x) dist[v] = kHClamp;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) mk[w] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dist[dst] = 0;
+        qa[0] = dst;
+        mk[dst >> 5] = 1u << (dst & 31);
+        n_next = 0;
+    }
+    __syncthreads();
+    uint32_t n_cur = 1;
+    for (uint32_t level = 0; n_cur > 0; ++level) {
+        if (level > N) {
+            if (threadIdx.x == 0) atomicExch(err, 1u);
+            return;
+        }
+        for (uint32_t i = threadIdx.x; i < n_cur; i += blockDim.x) {  // a node lowered again may requeue
+            const uint32_t u = qa[i];
+            atomicAnd(mk + (u >> 5), ~(1u << (u & 31)));
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n_cur; i += blockDim.x) {
+            const uint32_t u = qa[i];
+            const uint32_t du = __ldcg(dist + u);  // bounds change by atomics (in L2): skip L1
+            const uint32_t k1 = in_ptr[u + 1];
+            for (uint32_t k0 = in_ptr[u]; k0 < k1; k0 += 4) {
+                // up to four in-roads: every load first, then the atomics of the relaxations that
+                // improve on the bound read (most do not; a stale read only costs an atomic)
+                uint32_t vv[4], nd[4], cur[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool ok = k0 + j < k1;
+                    vv[j] = ok ? in_tail[k0 + j] : 0u;
+                    nd[j] = ok ? min(du + rec[in_edge[k0 + j]].tt, kHClamp) : kHClamp;
+                    cur[j] = ok ? __ldcg(dist + vv[j]) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (nd[j] < cur[j] && nd[j] < atomicMin(dist + vv[j], nd[j])) {
+                        const uint32_t bit = 1u << (vv[j] & 31);
+                        if (!(atomicOr(mk + (vv[j] >> 5), bit) & bit)) qb[atomicAdd(&n_next, 1u)] = vv[j];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        n_cur = n_next;
+        uint32_t* t = qa;
+        qa = qb;
+        qb = t;
+        __syncthreads();
+        if (threadIdx.x == 0) n_next = 0;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Batch initialisation: pheromone 1.0 (or Philox-random in [0.5, 1.5)), deposits zero, colony state.
 // ------------------------------------------------------------------------------------------------
 // Calc_Dist for the whole colony up front: th[e].y = h(head(e)) towards this colony's destination,
-// next to th[e].x, the pheromone as binary32 bits (one 8-byte load per candidate).
+// next to th[e].x, the pheromone as binary32 bits (one 8-byte load per candidate). h is the
+// straight-line bound, or with hdist (GMP_FLAG_EXACT_H) the colony's row of exact bounds (N per colony).
 __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
                              const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
                              uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
                              unsigned long long* __restrict__ dep, QueryState* __restrict__ qs,
                              uint32_t* __restrict__ tickets, uint32_t n_tickets, uint32_t sparse,
-                             uint32_t* __restrict__ tflag, uint32_t tflag_words) {
+                             uint32_t* __restrict__ tflag, uint32_t tflag_words,
+                             const uint32_t* __restrict__ hdist, uint32_t N) {
     const uint32_t qi = blockIdx.y;
+    const uint32_t* hrow = hdist ? hdist + (size_t)qi * N : nullptr;
     const DevQuery Q = q[qi];
     uint64_t* T = tau + (size_t)qi * E;
     unsigned long long* D = dep + (size_t)qi * E;
@@ -168,7 +253,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         const uint32_t v = col[e];
-        const uint32_t h = heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
+        const uint32_t h = hrow ? hrow[v] : heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
         D[e] = 0;
         if (sparse) {  // no road has a deposit yet: every road holds the baseline
             TH[e] = make_uint2(0u, h);
@@ -183,7 +268,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
             tflag[(size_t)qi * tflag_words + w] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t h = heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
+        const uint32_t h = hrow ? hrow[Q.src] : heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
         QueryState S;
         S.best_key = Q.active ? kNoKey : 0ull;
         S.dep_num = (flags & GMP_FLAG_UNIT_DEPOSIT) ? 0ull : (unsigned long long)(h > 0 ? h : 1u) << 32;
@@ -926,10 +1011,20 @@ cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, con
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
-                              uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words) {
+                              uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
+                              const uint32_t* hdist, uint32_t N) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
     k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, sparse,
-                                      tflag, tflag_words);
+                                      tflag, tflag_words, hdist, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,
+                           const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t* hdist,
+                           uint32_t* queue, uint32_t* mark, uint32_t* err) {
+    if (Q == 0 || N == 0) return cudaSuccess;
+    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, hdist, queue, mark, (N + 31u) / 32u,
+                                         err);
     return cudaGetLastError();
 }
 

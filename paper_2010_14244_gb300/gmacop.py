@@ -23,6 +23,7 @@ FLAG_REPULSIVE = 32
 FLAG_UNIT_DEPOSIT = 64
 FLAG_EVAP_UNUSED = 128
 FLAG_PAPER_LITERAL = FLAG_REPULSIVE | FLAG_UNIT_DEPOSIT | FLAG_EVAP_UNUSED
+FLAG_EXACT_H = 256
 MODE_AUTO, MODE_ITERATIVE, MODE_PERSISTENT = 0, 1, 2
 TAU_AUTO, TAU_DENSE, TAU_SPARSE = 0, 1, 2
 

@@ -3,8 +3,11 @@
     python -m paper_2010_14244_gb300.run_workload grid64 --iterations 6 --repeat 2
     python -m paper_2010_14244_gb300.run_workload geo100k --queries 64 --iterations 4
     python -m paper_2010_14244_gb300.run_workload geo1m --queries 64 --ants 128 --iterations 30 --ticks 3
+    python -m paper_2010_14244_gb300.run_workload grid64 --flags 256      # exact heuristic
 
-Prints one JSON line per run with the job's device time (CUDA events on the library's stream).
+Prints one JSON line per run with the job's device time (CUDA events on the library's stream) and the
+library's per-kernel-group times of that job with --kernel-times (construction, iteration end,
+init + finalize, whole job).
 """
 from __future__ import annotations
 
@@ -24,6 +27,8 @@ def main():
     p.add_argument("--lanes", type=int, default=0)
     p.add_argument("--mode", type=int, default=0)
     p.add_argument("--tau-layout", type=int, default=0)
+    p.add_argument("--flags", type=int, default=0, help="GMP_FLAG_* bits (e.g. 256: exact heuristic)")
+    p.add_argument("--kernel-times", action="store_true", help="events around every kernel; report their times")
     args = p.parse_args()
 
     import dataclasses
@@ -49,7 +54,7 @@ def main():
     stream = torch.cuda.Stream()
     ctx = gmacop.Context(0, stream=stream)
     ctx.load_workload(wl)
-    ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, tau_layout=args.tau_layout)
+    ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, tau_layout=args.tau_layout, flags=args.flags | (gmacop.FLAG_KERNEL_TIMING if args.kernel_times else 0))
     ctx.stage(qs)
     clock = 0
     for r in range(args.repeat):
@@ -65,6 +70,7 @@ def main():
             e1.synchronize()
         res = ctx.collect()
         print(json.dumps({"run": r, "workload": args.workload, "colonies": len(qs), "job_ms": e0.elapsed_time(e1),
+                          "kernel_ms": ctx.kernel_times() if args.kernel_times else None,
                           "host_ms": (time.perf_counter() - t0) * 1e3,
                           "ant_steps": int(sum(x["ant_steps"] for x in res)),
                           "found": int(sum(x["status"] == 0 for x in res))}), flush=True)
