@@ -139,6 +139,8 @@ class VehicleSim:
         src = np.asarray(src, np.int64)
         dst = np.asarray(dst, np.int64)
         n = src.size
+        if n >= 1 << 20 or cfg.seed >= 1 << 24:
+            raise ValueError("colony seeds pack (seed, vehicle, decision) into 24 + 20 + 20 bits")
         depart = np.zeros(n, np.int64) if depart_ms is None else np.asarray(depart_ms, np.int64)
         state = np.where(src == dst, ARRIVED, AT_NODE)
         node = src.copy()

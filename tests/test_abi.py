@@ -71,3 +71,20 @@ def test_built_for_sm_103a():
     from paper_2010_14244_gb300 import build
 
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_header_constants_match_binding_and_oracle():
+    """Every GMP_FLAG_*, GMP_MODE_* and GMP_TAU_* value of the header equals the binding's constant of the
+    same name, and the flag bits both sides of the parity tests use mean the same on the oracle."""
+    from oracle import oracle as orc
+    from paper_2010_14244_gb300 import gmacop
+
+    text = "".join(open(h).read() for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define GMP_((?:FLAG|MODE|TAU)_\w+) (\d+)u?", text)}
+    assert {"FLAG_RANDOM_TAU", "FLAG_REPULSIVE", "FLAG_UNIT_DEPOSIT", "FLAG_EVAP_UNUSED", "FLAG_EXACT_H"} <= set(consts)
+    for name, v in consts.items():
+        assert getattr(gmacop, name) == v, name
+    assert gmacop.FLAG_PAPER_LITERAL == gmacop.FLAG_REPULSIVE | gmacop.FLAG_UNIT_DEPOSIT | gmacop.FLAG_EVAP_UNUSED
+    for name in ("FLAG_RANDOM_TAU", "FLAG_REPULSIVE", "FLAG_UNIT_DEPOSIT", "FLAG_EVAP_UNUSED", "FLAG_PAPER_LITERAL",
+                 "FLAG_EXACT_H"):
+        assert getattr(orc, name) == getattr(gmacop, name), name
