@@ -236,7 +236,11 @@ __global__ void __launch_bounds__(kExactHBlock) k_exact_h(uint32_t N, const DevQ
 // ------------------------------------------------------------------------------------------------
 // Calc_Dist for the whole colony up front: th[e].y = h(head(e)) towards this colony's destination,
 // next to th[e].x, the pheromone as binary32 bits (one 8-byte load per candidate). h is the
-// straight-line bound, or with hdist (GMP_FLAG_EXACT_H) the colony's row of exact bounds (N per colony).
+// straight-line bound, or with EXACT (GMP_FLAG_EXACT_H) the colony's row of hdist (N per colony). EXACT
+// and REP (GMP_FLAG_REPULSIVE: the pheromone word is a reciprocal) are template parameters so that the
+// default instantiation keeps its small register footprint: this kernel writes every road of every
+// colony and needs the occupancy.
+template <bool EXACT, bool REP>
 __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
                              const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
                              uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
@@ -245,7 +249,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
                              uint32_t* __restrict__ tflag, uint32_t tflag_words,
                              const uint32_t* __restrict__ hdist, uint32_t N) {
     const uint32_t qi = blockIdx.y;
-    const uint32_t* hrow = hdist ? hdist + (size_t)qi * N : nullptr;
+    const uint32_t* hrow = EXACT ? hdist + (size_t)qi * N : nullptr;
     const DevQuery Q = q[qi];
     uint64_t* T = tau + (size_t)qi * E;
     unsigned long long* D = dep + (size_t)qi * E;
@@ -253,7 +257,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         const uint32_t v = col[e];
-        const uint32_t h = hrow ? hrow[v] : heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
+        const uint32_t h = EXACT ? hrow[v] : heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
         D[e] = 0;
         if (sparse) {  // no road has a deposit yet: every road holds the baseline
             TH[e] = make_uint2(0u, h);
@@ -262,13 +266,13 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         uint64_t t0 = 1ull << 32;
         if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
         T[e] = t0;
-        TH[e] = make_uint2(tau_word(t0, flags), h);
+        TH[e] = make_uint2(tau_word(t0, REP ? GMP_FLAG_REPULSIVE : 0u), h);
     }
     if (sparse)
         for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
             tflag[(size_t)qi * tflag_words + w] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t h = hrow ? hrow[Q.src] : heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
+        const uint32_t h = EXACT ? hrow[Q.src] : heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
         QueryState S;
         S.best_key = Q.active ? kNoKey : 0ull;
         S.dep_num = (flags & GMP_FLAG_UNIT_DEPOSIT) ? 0ull : (unsigned long long)(h > 0 ? h : 1u) << 32;
@@ -278,7 +282,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
         S.best_W = 0;
         S.pad[0] = S.pad[1] = 0;
         S.base_tau = 1ull << 32;
-        S.base_tf = tau_word(1ull << 32, flags);
+        S.base_tf = tau_word(1ull << 32, REP ? GMP_FLAG_REPULSIVE : 0u);
         S.n_touched = 0;
         qs[qi] = S;
     }
@@ -1014,8 +1018,18 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
                               const uint32_t* hdist, uint32_t N) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
-    k_init_batch<<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, sparse,
-                                      tflag, tflag_words, hdist, N);
+#define GMP_INIT(EX_, REP_)                                                                                 \
+    k_init_batch<EX_, REP_><<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, \
+                                                 sparse, tflag, tflag_words, hdist, N)
+    const bool rep = (flags & GMP_FLAG_REPULSIVE) != 0;
+    if (hdist) {
+        if (rep) GMP_INIT(true, true);
+        else GMP_INIT(true, false);
+    } else {
+        if (rep) GMP_INIT(false, true);
+        else GMP_INIT(false, false);
+    }
+#undef GMP_INIT
     return cudaGetLastError();
 }
 

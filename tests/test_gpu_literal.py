@@ -102,3 +102,15 @@ def test_saturated_repulsive_scores(gm, ctx, orc, sched):
     ctx.set_params(flags=flags, **SCHEDULES[sched])
     r = ctx.solve_batch([q])[0]
     _compare(orc, onet, orc.Params(flags=flags), q, r, ctx)
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_random_initial_pheromone_repulsive(gm, ctx, orc, exact):
+    """Philox-random initial pheromone read through the reciprocal word (and with the exact heuristic)."""
+    wl = W.grid10(n_ants=32, n_iter=10)
+    ctx.load_workload(wl)
+    flags = gm.FLAG_RANDOM_TAU | gm.FLAG_REPULSIVE | (gm.FLAG_EXACT_H if exact else 0)
+    ctx.set_params(flags=flags | gm.FLAG_ANT_LOG)
+    q = Q(wl.queries[0].src, wl.queries[0].dst, 32, 10, 2.0, 1.0, 0.15, 77)
+    r = ctx.solve_batch([q])[0]
+    _compare(orc, orc.Net.from_workload(wl), orc.Params(flags=flags), q, r, ctx, 0, ctx.ant_log(0))
