@@ -51,6 +51,7 @@ struct Batch {
     uint64_t log_entries = 0;
     std::vector<gmp_query> hq;
     bool staged = false, ran = false;
+    bool dep_dirty = false;  // the deposit accumulators may hold a stopped job's deposits
     KernelConfig kc{};
     // device workspace
     DevQuery* dq = nullptr;
@@ -458,7 +459,8 @@ int enqueue_persistent(gmp_ctx* c) {
     if (timed) GMP_TRY(record(c, b, 0));
     GMP_TRY(enqueue_exact_h(c));
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
-                                  b.dep, b.qs, b.tickets, b.maxI, 0u, nullptr, 0u, b.exact_h ? b.hdist : nullptr, c->N));
+                                  b.dep, b.qs, b.tickets, b.maxI, 0u, nullptr, 0u, b.exact_h ? b.hdist : nullptr, c->N,
+                                  true));
     GMP_CUDA(c, launch_persistent_init(s, b.Q, b.maxI, b.dq, b.ctr, b.qstate, b.qflag, b.misc));
     if (b.tabu && b.tabu_used) GMP_CUDA(c, cudaMemsetAsync(b.tabu, 0, b.tabu_used * 4, s));
     if (timed) GMP_TRY(record(c, b, 1));
@@ -575,7 +577,7 @@ int enqueue_job(gmp_ctx* c) {
     if (b.exact_h) ++n;
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
                                   b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B, b.sparse ? 1u : 0u, b.tflag,
-                                  tflag_words(c), b.exact_h ? b.hdist : nullptr, c->N));
+                                  tflag_words(c), b.exact_h ? b.hdist : nullptr, c->N, false));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
     // global visited bitmaps start clean; each walk clears its own bits when it ends
@@ -962,7 +964,17 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
         GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
     }
     GMP_TRY(ensure(c, &b.th, (size_t)n * c->E));
-    GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
+    // deposit accumulators: zeroed when allocated (or after a job that may have stopped mid-iteration);
+    // iterative jobs then keep them zero without clearing them at init
+    {
+        unsigned long long* before = b.dep;
+        const size_t have = before ? c->sizes[(void*)before] : 0;
+        GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
+        if (b.dep != before || c->sizes[(void*)b.dep] != have || b.dep_dirty) {
+            GMP_CUDA(c, cudaMemsetAsync(b.dep, 0, c->sizes[(void*)b.dep], c->stream));
+            b.dep_dirty = false;
+        }
+    }
     GMP_TRY(ensure(c, &b.qs, n));
     GMP_TRY(ensure(c, &b.routes, (size_t)total_ants * max_steps));
     GMP_TRY(ensure(c, &b.ant_steps, (size_t)total_ants));
@@ -1220,7 +1232,10 @@ int gmp_batch_collect(gmp_ctx* c, gmp_result* results) {
     if (b.persistent || b.exact_h)
         GMP_CUDA(c, cudaMemcpyAsync(misc, b.misc, sizeof misc, cudaMemcpyDeviceToHost, c->stream));
     GMP_TRY(sync(c));
-    if (b.persistent && misc[1]) return fail(c, GMP_ERR_TIMEOUT, "a bounded device wait of the persistent job expired");
+    if (b.persistent && misc[1]) {
+        b.dep_dirty = true;
+        return fail(c, GMP_ERR_TIMEOUT, "a bounded device wait of the persistent job expired");
+    }
     if (b.exact_h && misc[2]) return fail(c, GMP_ERR_TIMEOUT, "the exact heuristic's relaxation passed its level bound");
     for (uint32_t i = 0; i < b.Q; ++i) {
         gmp_result& r = results[i];
@@ -1685,7 +1700,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     GMP_CUDA(c, cudaGetLastError());
     // init clears the pheromone, deposits, colony state and ticket counters left by the previous call
     GMP_CUDA(c, launch_init_batch(s, 1, c->E, dq, c->col, c->x, c->y, c->kappa, c->prm.flags, tau, th, dep,
-                                  qs, tickets, n_iter, 0u, nullptr, 0u, nullptr, c->N));
+                                  qs, tickets, n_iter, 0u, nullptr, 0u, nullptr, c->N, true));
     if (tabu)  // global visited bitmaps start clean; each walk clears its own bits when it ends
         GMP_CUDA(c, cudaMemsetAsync(tabu, 0, (size_t)kc.grid * (kc.block / kc.lanes) * words * 4, s));
     ConstructArgs a{};

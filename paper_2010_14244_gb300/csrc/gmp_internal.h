@@ -132,7 +132,7 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
-                              const uint32_t* hdist, uint32_t N);
+                              const uint32_t* hdist, uint32_t N, bool zero_dep);
 // Exact Calc_Dist (GMP_FLAG_EXACT_H) of Q colonies into hdist (Q * N); queue (Q * 2N) and mark
 // (Q * ceil(N / 32)) are scratch; err[0] is set if a colony exceeded N relaxation levels.
 cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,

@@ -232,7 +232,9 @@ __global__ void __launch_bounds__(kExactHBlock) k_exact_h(uint32_t N, const DevQ
 }
 
 // ------------------------------------------------------------------------------------------------
-// Batch initialisation: pheromone 1.0 (or Philox-random in [0.5, 1.5)), deposits zero, colony state.
+// Batch initialisation: pheromone 1.0 (or Philox-random in [0.5, 1.5)), colony state, and with zero_dep the
+// deposit accumulators (an iterative job leaves them zero: every iteration end clears the deposits it
+// applies, and a road only receives deposits in an iteration whose end processes it).
 // ------------------------------------------------------------------------------------------------
 // Calc_Dist for the whole colony up front: th[e].y = h(head(e)) towards this colony's destination,
 // next to th[e].x, the pheromone as binary32 bits (one 8-byte load per candidate). h is the
@@ -241,13 +243,14 @@ __global__ void __launch_bounds__(kExactHBlock) k_exact_h(uint32_t N, const DevQ
 // default instantiation keeps its small register footprint: this kernel writes every road of every
 // colony and needs the occupancy.
 template <bool EXACT, bool REP>
-__global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
-                             const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
-                             uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
-                             unsigned long long* __restrict__ dep, QueryState* __restrict__ qs,
-                             uint32_t* __restrict__ tickets, uint32_t n_tickets, uint32_t sparse,
-                             uint32_t* __restrict__ tflag, uint32_t tflag_words,
-                             const uint32_t* __restrict__ hdist, uint32_t N) {
+__global__ void __launch_bounds__(256, 8)
+k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
+             const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
+             uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
+             unsigned long long* __restrict__ dep, QueryState* __restrict__ qs,
+             uint32_t* __restrict__ tickets, uint32_t n_tickets, uint32_t sparse,
+             uint32_t* __restrict__ tflag, uint32_t tflag_words,
+             const uint32_t* __restrict__ hdist, uint32_t N, uint32_t zero_dep) {
     const uint32_t qi = blockIdx.y;
     const uint32_t* hrow = EXACT ? hdist + (size_t)qi * N : nullptr;
     const DevQuery Q = q[qi];
@@ -258,7 +261,7 @@ __global__ void k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const u
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         const uint32_t v = col[e];
         const uint32_t h = EXACT ? hrow[v] : heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
-        D[e] = 0;
+        if (zero_dep) D[e] = 0;
         if (sparse) {  // no road has a deposit yet: every road holds the baseline
             TH[e] = make_uint2(0u, h);
             continue;
@@ -1016,11 +1019,11 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
-                              const uint32_t* hdist, uint32_t N) {
+                              const uint32_t* hdist, uint32_t N, bool zero_dep) {
     dim3 grid(blocks_for(E ? E : 1, 1024), Q);
 #define GMP_INIT(EX_, REP_)                                                                                 \
     k_init_batch<EX_, REP_><<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, \
-                                                 sparse, tflag, tflag_words, hdist, N)
+                                                 sparse, tflag, tflag_words, hdist, N, zero_dep ? 1u : 0u)
     const bool rep = (flags & GMP_FLAG_REPULSIVE) != 0;
     if (hdist) {
         if (rep) GMP_INIT(true, true);

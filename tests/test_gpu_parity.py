@@ -4,6 +4,8 @@ Every comparison is exact: routes, travel and wait times, step and success count
 (iteration, ant), per-ant logs, final pheromone tables, road times and phase orders. The tolerance is
 zero because both sides use integer arithmetic and identically ordered binary32 operations.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -354,3 +356,21 @@ def test_degree_above_limit_is_refused(gm, ctx):
     with pytest.raises(gm.GmpError) as ei:
         ctx.solve_batch([Q(0, 131, 8, 2, 1.0, 2.0, 0.1, 0)])
     assert ei.value.code == gm.ERR_UNSUPPORTED
+
+
+def test_consecutive_jobs_on_one_context(gm, ctx, orc):
+    """Iterative jobs do not clear the deposit accumulators at init (each job leaves them zero); a context
+    that runs jobs of growing and shrinking size, switching between the persistent job and both pheromone
+    layouts, must still match the oracle colony for colony."""
+    wl = W.grid64(n_queries=6, n_ants=64, n_iter=6)
+    ctx.load_workload(wl)
+    onet = orc.Net.from_workload(wl)
+    plan = [(dict(mode=1), [0, 1, 2]), (dict(mode=1), [0, 1, 2, 3, 4, 5]), (dict(mode=2), [3, 4]),
+            (dict(mode=1, tau_layout=2), [5, 4, 3, 2]), (dict(mode=1, tau_layout=1), [1]),
+            (dict(mode=1), [2, 0, 5, 1, 4])]
+    for n, (kw, idx) in enumerate(plan):
+        qs = [dataclasses.replace(wl.queries[i], seed=100 * n + i) for i in idx]
+        ctx.set_params(**kw)
+        res = ctx.solve_batch(qs)
+        for j, q in enumerate(qs):
+            _compare(orc, onet, orc.Params(), q, res[j], ctx, j)
