@@ -83,7 +83,7 @@ struct Batch {
     bool exact_h = false;
     uint32_t* hdist = nullptr;   // Q * N bounds
     uint32_t* hqueue = nullptr;  // Q * 2N frontiers
-    uint32_t* hmark = nullptr;   // Q * ceil(N / 32) queued marks
+    uint32_t* hstamp = nullptr;  // Q * N level stamps (a node is queued once per level)
     // captured job
     cudaGraphExec_t exec = nullptr;  // the executable graph of the staged job (one of `execs`)
     std::map<std::vector<uint32_t>, cudaGraphExec_t> execs;  // by topology, refreshed by graph update
@@ -304,7 +304,7 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.misc);
     dfree(c, &b.hdist);
     dfree(c, &b.hqueue);
-    dfree(c, &b.hmark);
+    dfree(c, &b.hstamp);
     b.staged = b.ran = false;
 }
 
@@ -447,7 +447,7 @@ int enqueue_exact_h(gmp_ctx* c) {
     if (!b.exact_h) return GMP_OK;
     GMP_CUDA(c, cudaMemsetAsync(b.misc + 2, 0, 4, c->stream));
     GMP_CUDA(c, launch_exact_h(c->stream, b.Q, c->N, b.dq, c->in_ptr, c->in_edge, c->in_tail, c->rec, b.hdist,
-                               b.hqueue, b.hmark, b.misc + 2));
+                               b.hqueue, b.hstamp, b.misc + 2));
     return GMP_OK;
 }
 
@@ -992,7 +992,7 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
     if (c->prm.flags & GMP_FLAG_EXACT_H) {
         GMP_TRY(ensure(c, &b.hdist, (size_t)n * c->N));
         GMP_TRY(ensure(c, &b.hqueue, (size_t)n * 2 * c->N));
-        GMP_TRY(ensure(c, &b.hmark, (size_t)n * words));
+        GMP_TRY(ensure(c, &b.hstamp, (size_t)n * c->N));
     }
     if (log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)log_entries * 4));
     // visited bitmaps in global memory: the job's grid plus one block per concurrent chain (chain grids

@@ -153,49 +153,50 @@ __global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
 // Exact Calc_Dist (GMP_FLAG_EXACT_H): per colony, h(v) = the least sum of congested travel times over
 // the roads of a path from v to the colony's destination, saturating at 2^28 (also for nodes that
 // cannot reach it). One block per colony relaxes from the destination over the reversed roads, level by
-// level (label-correcting Bellman-Ford): a level first unmarks its frontier, then lowers each frontier
-// node's predecessors with atomicMin and queues every predecessor it lowered once (the mark bitmap).
-// The saturating sums are monotone, so the fixpoint is the clamped exact distance in any relaxation
-// order. A node reaches its final bound within as many levels as its shortest path has roads, so there
-// are at most N levels; a block that gets past N sets err[0] (it cannot happen) and stops.
+// level (label-correcting Bellman-Ford): level L lowers the bounds of its frontier's predecessors with
+// atomicMin and queues each node it lowered into frontier L + 1 once, by stamping the node with L + 1
+// (atomicExch: only the first stamp of a level queues it). The saturating sums are monotone, so the
+// fixpoint is the clamped exact distance in any relaxation order. A node reaches its final bound within
+// as many levels as its shortest path has roads, so there are at most N levels; a block that gets past
+// N sets err[0] (it cannot happen) and stops. Two barriers per level: frontier sizes alternate between
+// two shared counters, and the one a level reads is cleared for reuse two levels later.
 // ------------------------------------------------------------------------------------------------
 constexpr uint32_t kExactHBlock = 512;
 
-__global__ void __launch_bounds__(kExactHBlock) k_exact_h(uint32_t N, const DevQuery* __restrict__ q,
-                                                          const uint32_t* __restrict__ in_ptr,
-                                                          const uint32_t* __restrict__ in_edge,
-                                                          const uint32_t* __restrict__ in_tail,
-                                                          const EdgeRec* __restrict__ rec, uint32_t* hdist,
-                                                          uint32_t* queue, uint32_t* mark, uint32_t words,
-                                                          uint32_t* err) {
+__global__ void __launch_bounds__(kExactHBlock, 4)
+k_exact_h(uint32_t N, const DevQuery* __restrict__ q, const uint32_t* __restrict__ in_ptr,
+          const uint32_t* __restrict__ in_edge, const uint32_t* __restrict__ in_tail, const EdgeRec* __restrict__ rec,
+          uint32_t* hdist, uint32_t* queue, uint32_t* stamp_all, uint32_t* err) {
     const uint32_t qi = blockIdx.x;
     const uint32_t dst = q[qi].dst;
     uint32_t* dist = hdist + (size_t)qi * N;
     uint32_t* qa = queue + (size_t)qi * 2u * N;  // this level's frontier
     uint32_t* qb = qa + N;                       // the next level's
-    uint32_t* mk = mark + (size_t)qi * words;
-    __shared__ uint32_t n_next;
-    for (uint32_t v = threadIdx.x; v < N; v += blockDim.x) dist[v] = kHClamp;
-    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) mk[w] = 0;
+    uint32_t* stamp = stamp_all + (size_t)qi * N;
+    __shared__ uint32_t cnt[2];
+    for (uint32_t v = threadIdx.x; v < N; v += blockDim.x) {
+        dist[v] = kHClamp;
+        stamp[v] = 0;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         dist[dst] = 0;
-        qa[0] = dst;
-        mk[dst >> 5] = 1u << (dst & 31);
-        n_next = 0;
+        qa[0] = dst;  // frontier 0 (stamp 0)
+        cnt[0] = 1;
+        cnt[1] = 0;
     }
     __syncthreads();
-    uint32_t n_cur = 1;
-    for (uint32_t level = 0; n_cur > 0; ++level) {
+    for (uint32_t level = 0;; ++level) {
+        const uint32_t n_cur = cnt[level & 1u];
+        if (n_cur == 0) break;
         if (level > N) {
             if (threadIdx.x == 0) atomicExch(err, 1u);
             return;
         }
-        for (uint32_t i = threadIdx.x; i < n_cur; i += blockDim.x) {  // a node lowered again may requeue
-            const uint32_t u = qa[i];
-            atomicAnd(mk + (u >> 5), ~(1u << (u & 31)));
-        }
-        __syncthreads();
+        __syncthreads();  // every thread has read this level's count
+        if (threadIdx.x == 0) cnt[level & 1u] = 0;  // the counter of frontier level + 2
+        uint32_t* const next_cnt = cnt + ((level + 1u) & 1u);
+        const uint32_t mark = level + 1u;
         for (uint32_t i = threadIdx.x; i < n_cur; i += blockDim.x) {
             const uint32_t u = qa[i];
             const uint32_t du = __ldcg(dist + u);  // bounds change by atomics (in L2): skip L1
@@ -212,22 +213,15 @@ __global__ void __launch_bounds__(kExactHBlock) k_exact_h(uint32_t N, const DevQ
                     cur[j] = ok ? __ldcg(dist + vv[j]) : 0u;
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (nd[j] < cur[j] && nd[j] < atomicMin(dist + vv[j], nd[j])) {
-                        const uint32_t bit = 1u << (vv[j] & 31);
-                        if (!(atomicOr(mk + (vv[j] >> 5), bit) & bit)) qb[atomicAdd(&n_next, 1u)] = vv[j];
-                    }
-                }
+                for (int j = 0; j < 4; ++j)
+                    if (nd[j] < cur[j] && nd[j] < atomicMin(dist + vv[j], nd[j]) && atomicExch(stamp + vv[j], mark) != mark)
+                        qb[atomicAdd(next_cnt, 1u)] = vv[j];
             }
         }
-        __syncthreads();
-        n_cur = n_next;
-        uint32_t* t = qa;
+        uint32_t* const t = qa;
         qa = qb;
         qb = t;
-        __syncthreads();
-        if (threadIdx.x == 0) n_next = 0;
-        __syncthreads();
+        __syncthreads();  // frontier level + 1 is complete
     }
 }
 
@@ -1038,10 +1032,9 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
 
 cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,
                            const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t* hdist,
-                           uint32_t* queue, uint32_t* mark, uint32_t* err) {
+                           uint32_t* queue, uint32_t* stamp, uint32_t* err) {
     if (Q == 0 || N == 0) return cudaSuccess;
-    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, hdist, queue, mark, (N + 31u) / 32u,
-                                         err);
+    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, hdist, queue, stamp, err);
     return cudaGetLastError();
 }
 
