@@ -116,3 +116,35 @@ def test_graphs_with_different_shared_memory_sizes(gm, orc):
         m.close()
         for c in ctxs:
             c.close()
+
+
+def test_variants_in_one_launch(gm, orc):
+    """Graphs whose contexts use different options share one launch: the exact heuristic with the
+    paper-literal pheromone rules, non-integer exponents, and the defaults. Each equals its graph alone
+    and the oracle."""
+    cities = W.city_batch(n_graphs=3, n_min=500, n_max=3000, q_lo=2, q_hi=3, ants_lo=32, ants_hi=64, n_iter=5)
+    opts = [dict(flags=gm.FLAG_EXACT_H | gm.FLAG_PAPER_LITERAL), dict(), dict(flags=gm.FLAG_EXACT_H)]
+    batches = [wl.queries for wl in cities]
+    batches[1] = [dataclasses.replace(q, alpha=1.5, beta=2.25) for q in batches[1]]
+    ctxs = []
+    m = gm.Multi(0)
+    try:
+        for wl, o in zip(cities, opts):
+            c = gm.Context(0)
+            c.load_workload(wl)
+            c.set_params(**o)
+            ctxs.append(c)
+        res = m.solve(ctxs, batches)
+        for c, qs, r in zip(ctxs, batches, res):
+            for a, b in zip(r, c.solve_batch(qs)):
+                _same(a, b)
+        for wl, o, qs, r in zip(cities, opts, batches, res):
+            onet = orc.Net.from_workload(wl)
+            q, got = qs[0], r[0]
+            exp = orc.solve(onet, orc.Params(flags=o.get("flags", 0)), q, want_tau=False)
+            for k in ("status", "travel_ms", "ant_steps", "n_success"):
+                assert got[k] == exp[k], (k, got[k], exp[k])
+    finally:
+        m.close()
+        for c in ctxs:
+            c.close()

@@ -187,3 +187,40 @@ def test_poisson_loop_reports_latency(gm):
         srv.close()
         for c in slots:
             c.close()
+
+
+def test_served_variants_equal_alone(gm):
+    """Slots running the exact heuristic with the paper-literal rules serve requests with integer and
+    non-integer exponents; each result equals the same request solved alone with the same options."""
+    from paper_2010_14244_gb300 import serving
+
+    wl = W.grid10()
+    opts = dict(flags=gm.FLAG_EXACT_H | gm.FLAG_PAPER_LITERAL)
+    srv, slots = serving.make_server(wl, n_slots=2, max_batch=5, max_ants=64, max_iter=8, params=opts)
+    reqs = _mixed_requests(wl.net.n_nodes, 14, seed=21)
+    reqs = [dataclasses.replace(q, alpha=q.alpha + (0.5 if i % 2 else 0.0)) for i, q in enumerate(reqs)]
+    done = []
+    try:
+        for i, q in enumerate(reqs):
+            srv.submit(q, i)
+            if i % 4 == 3:
+                srv.pump()
+        for _ in range(200000):
+            st = srv.pump()
+            done += srv.take()
+            if st["queued"] == 0 and st["in_flight"] == 0 and st["done_waiting"] == 0:
+                break
+    finally:
+        srv.close()
+        for c in slots:
+            c.close()
+    assert sorted(r["tag"] for r in done) == list(range(len(reqs)))
+    ref = gm.Context(0)
+    try:
+        ref.load_workload(wl)
+        ref.set_params(**opts)
+        for r in done:
+            q = reqs[r["tag"]]
+            _same(r, ref.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed))
+    finally:
+        ref.close()
