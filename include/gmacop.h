@@ -51,7 +51,7 @@ extern "C" {
 /* Calc_Dist exactly (Algorithm 2): h(v) = the least sum of congested travel times over a path from v to
  * the colony's destination (2^28 when there is none), computed on the GPU per colony at the start of each
  * job, in place of the straight-line bound; it also sets the deposit numerator h(src). Needs
- * Q * 16 N bytes more workspace; gmp_solve_static refuses it (GMP_ERR_UNSUPPORTED). */
+ * Q * 28 N bytes more workspace; gmp_solve_static refuses it (GMP_ERR_UNSUPPORTED). */
 #define GMP_FLAG_EXACT_H 256u
 
 #define GMP_MODE_AUTO 0u       /* library picks */

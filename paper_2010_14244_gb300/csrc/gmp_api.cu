@@ -82,8 +82,8 @@ struct Batch {
     // exact Calc_Dist (GMP_FLAG_EXACT_H)
     bool exact_h = false;
     uint32_t* hdist = nullptr;   // Q * N bounds
-    uint32_t* hqueue = nullptr;  // Q * 2N frontiers
-    uint32_t* hstamp = nullptr;  // Q * N level stamps (a node is queued once per level)
+    uint32_t* hqueue = nullptr;  // Q * 4N: near frontiers (2N) and far piles (2N)
+    uint32_t* hstamp = nullptr;  // Q * 2N: near (per level) and far (per epoch) stamps
     // captured job
     cudaGraphExec_t exec = nullptr;  // the executable graph of the staged job (one of `execs`)
     std::map<std::vector<uint32_t>, cudaGraphExec_t> execs;  // by topology, refreshed by graph update
@@ -143,6 +143,7 @@ struct gmp_ctx {
     gmp_params prm{};
     bool has_graph = false;
     uint32_t N = 0, E = 0, maxdeg = 0, kappa = 0;
+    uint32_t h_delta = 1;  // exact heuristic: near-far threshold step, 16 x the mean free-flow road time (ms)
     uint32_t *row_ptr = nullptr, *col = nullptr, *len = nullptr, *in_ptr = nullptr, *in_edge = nullptr;
     uint32_t* in_tail = nullptr;  // tail of each in_edge entry (exact Calc_Dist relaxes towards tails)
     uint32_t *ff = nullptr, *cap = nullptr;
@@ -446,8 +447,8 @@ int enqueue_exact_h(gmp_ctx* c) {
     Batch& b = c->b;
     if (!b.exact_h) return GMP_OK;
     GMP_CUDA(c, cudaMemsetAsync(b.misc + 2, 0, 4, c->stream));
-    GMP_CUDA(c, launch_exact_h(c->stream, b.Q, c->N, b.dq, c->in_ptr, c->in_edge, c->in_tail, c->rec, b.hdist,
-                               b.hqueue, b.hstamp, b.misc + 2));
+    GMP_CUDA(c, launch_exact_h(c->stream, b.Q, c->N, b.dq, c->in_ptr, c->in_edge, c->in_tail, c->rec, c->h_delta,
+                               b.hdist, b.hqueue, b.hstamp, b.misc + 2));
     return GMP_OK;
 }
 
@@ -776,6 +777,11 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     c->hx.assign(x_dm, x_dm + N);
     c->hy.assign(y_dm, y_dm + N);
     c->kappa = (uint32_t)((360ull << 16) / vmax);
+    {
+        uint64_t ff_sum = 0;  // free-flow times as the road kernels compute them (a tuning input only)
+        for (uint32_t e = 0; e < E; ++e) ff_sum += ((uint64_t)length_dm[e] * 360u + speed_kmh[e] / 2u) / speed_kmh[e];
+        c->h_delta = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(16u * (E ? ff_sum / E : 1u), 1u), 1u << 27);
+    }
     GMP_TRY(dalloc(c, &c->row_ptr, N + 1));
     GMP_TRY(dalloc(c, &c->col, E));
     GMP_TRY(dalloc(c, &c->len, E));
@@ -991,8 +997,8 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
     if (persistent || (c->prm.flags & GMP_FLAG_EXACT_H)) GMP_TRY(ensure(c, &b.misc, 3));
     if (c->prm.flags & GMP_FLAG_EXACT_H) {
         GMP_TRY(ensure(c, &b.hdist, (size_t)n * c->N));
-        GMP_TRY(ensure(c, &b.hqueue, (size_t)n * 2 * c->N));
-        GMP_TRY(ensure(c, &b.hstamp, (size_t)n * c->N));
+        GMP_TRY(ensure(c, &b.hqueue, (size_t)n * 4 * c->N));
+        GMP_TRY(ensure(c, &b.hstamp, (size_t)n * 2 * c->N));
     }
     if (log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)log_entries * 4));
     // visited bitmaps in global memory: the job's grid plus one block per concurrent chain (chain grids

@@ -133,11 +133,12 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
                               const uint32_t* hdist, uint32_t N, bool zero_dep);
-// Exact Calc_Dist (GMP_FLAG_EXACT_H) of Q colonies into hdist (Q * N); queue (Q * 2N) and stamp (Q * N)
-// are scratch; err[0] is set if a colony exceeded N relaxation levels.
+// Exact Calc_Dist (GMP_FLAG_EXACT_H) of Q colonies into hdist (Q * N), in near-far order with threshold
+// step delta (ms; work only, not results); queue (Q * 4N) and stamps (Q * 2N) are scratch; err[0] is set
+// if a colony ran past its level guard.
 cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,
-                           const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t* hdist,
-                           uint32_t* queue, uint32_t* stamp, uint32_t* err);
+                           const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t delta,
+                           uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err);
 cudaError_t launch_materialize_tau(cudaStream_t s, uint32_t E, const QueryState* qs, const uint32_t* list_e,
                                    const uint64_t* list_tau, uint64_t* out);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);

@@ -152,76 +152,119 @@ __global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
 // ------------------------------------------------------------------------------------------------
 // Exact Calc_Dist (GMP_FLAG_EXACT_H): per colony, h(v) = the least sum of congested travel times over
 // the roads of a path from v to the colony's destination, saturating at 2^28 (also for nodes that
-// cannot reach it). One block per colony relaxes from the destination over the reversed roads, level by
-// level (label-correcting Bellman-Ford): level L lowers the bounds of its frontier's predecessors with
-// atomicMin and queues each node it lowered into frontier L + 1 once, by stamping the node with L + 1
-// (atomicExch: only the first stamp of a level queues it). The saturating sums are monotone, so the
-// fixpoint is the clamped exact distance in any relaxation order. A node reaches its final bound within
-// as many levels as its shortest path has roads, so there are at most N levels; a block that gets past
-// N sets err[0] (it cannot happen) and stops. Two barriers per level: frontier sizes alternate between
-// two shared counters, and the one a level reads is cleared for reuse two levels later.
+// cannot reach it). One block per colony relaxes from the destination over the reversed roads with
+// atomicMin on the bounds, in near-far order (Davidson, Baxter, Garland & Owens, IPDPS 2014): a level
+// relaxes the near frontier; a node it lowers below the threshold T joins the next near frontier (once
+// per level: stamped with the level), one lowered to T or above joins the far pile (once per epoch:
+// stamped with the epoch). When the near frontier runs dry, T grows to max(T + delta, least far bound
+// + delta) and the far nodes below it become the next frontier; the rest stay far. The saturating sums
+// are monotone, so the fixpoint is the clamped exact distance in any relaxation order: delta and the
+// order only change the amount of work. Each epoch settles at least one node; a colony that runs past
+// 4N + 4096 levels (far beyond anything observed) sets err[0] and stops.
 // ------------------------------------------------------------------------------------------------
 constexpr uint32_t kExactHBlock = 512;
 
 __global__ void __launch_bounds__(kExactHBlock, 4)
 k_exact_h(uint32_t N, const DevQuery* __restrict__ q, const uint32_t* __restrict__ in_ptr,
           const uint32_t* __restrict__ in_edge, const uint32_t* __restrict__ in_tail, const EdgeRec* __restrict__ rec,
-          uint32_t* hdist, uint32_t* queue, uint32_t* stamp_all, uint32_t* err) {
+          uint32_t delta, uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err) {
     const uint32_t qi = blockIdx.x;
     const uint32_t dst = q[qi].dst;
     uint32_t* dist = hdist + (size_t)qi * N;
-    uint32_t* qa = queue + (size_t)qi * 2u * N;  // this level's frontier
-    uint32_t* qb = qa + N;                       // the next level's
-    uint32_t* stamp = stamp_all + (size_t)qi * N;
-    __shared__ uint32_t cnt[2];
+    uint32_t* nstamp = stamps + (size_t)qi * 2u * N;  // near: level + 1 of the frontier a node last joined
+    uint32_t* fstamp = nstamp + N;                    // far: epoch + 1 of the pile a node last joined
+    uint32_t* qa = queue + (size_t)qi * 4u * N;       // near frontier of this level
+    uint32_t* qb = qa + N;                            // near frontier of the next level
+    uint32_t* fa = qb + N;                            // far pile of this epoch
+    uint32_t* fb = fa + N;                            // far pile of the next epoch
+    __shared__ uint32_t ncnt[2], fcnt[2], fmin;
     for (uint32_t v = threadIdx.x; v < N; v += blockDim.x) {
         dist[v] = kHClamp;
-        stamp[v] = 0;
+        nstamp[v] = 0;
+        fstamp[v] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         dist[dst] = 0;
-        qa[0] = dst;  // frontier 0 (stamp 0)
-        cnt[0] = 1;
-        cnt[1] = 0;
+        qa[0] = dst;  // frontier of level 0 (stamp 0)
+        ncnt[0] = 1;
+        ncnt[1] = 0;
+        fcnt[0] = 0;
+        fcnt[1] = 0;
+        fmin = 0xFFFFFFFFu;
     }
     __syncthreads();
+    const uint32_t guard = N > (1u << 29) ? 0xFFFFFFFFu : 4u * N + 4096u;
+    uint32_t T = delta, epoch = 0, fsel = 0;
     for (uint32_t level = 0;; ++level) {
-        const uint32_t n_cur = cnt[level & 1u];
-        if (n_cur == 0) break;
-        if (level > N) {
+        if (level > guard) {
             if (threadIdx.x == 0) atomicExch(err, 1u);
             return;
         }
-        __syncthreads();  // every thread has read this level's count
-        if (threadIdx.x == 0) cnt[level & 1u] = 0;  // the counter of frontier level + 2
-        uint32_t* const next_cnt = cnt + ((level + 1u) & 1u);
+        const uint32_t n_cur = ncnt[level & 1u];
+        const uint32_t nf = fcnt[fsel];
+        if (n_cur == 0 && nf == 0) break;
+        __syncthreads();  // every thread has read this level's counts
+        if (threadIdx.x == 0) ncnt[level & 1u] = 0;  // the counter of the near frontier of level + 2
+        uint32_t* const next_cnt = ncnt + ((level + 1u) & 1u);
         const uint32_t mark = level + 1u;
-        for (uint32_t i = threadIdx.x; i < n_cur; i += blockDim.x) {
-            const uint32_t u = qa[i];
-            const uint32_t du = __ldcg(dist + u);  // bounds change by atomics (in L2): skip L1
-            const uint32_t k1 = in_ptr[u + 1];
-            for (uint32_t k0 = in_ptr[u]; k0 < k1; k0 += 4) {
-                // up to four in-roads: every load first, then the atomics of the relaxations that
-                // improve on the bound read (most do not; a stale read only costs an atomic)
-                uint32_t vv[4], nd[4], cur[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool ok = k0 + j < k1;
-                    vv[j] = ok ? in_tail[k0 + j] : 0u;
-                    nd[j] = ok ? min(du + rec[in_edge[k0 + j]].tt, kHClamp) : kHClamp;
-                    cur[j] = ok ? __ldcg(dist + vv[j]) : 0u;
+        if (n_cur == 0) {  // the near frontier ran dry: a new epoch splits the far pile
+            uint32_t* const far_cur = fsel ? fb : fa;
+            uint32_t* const far_nxt = fsel ? fa : fb;
+            for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) atomicMin(&fmin, __ldcg(dist + far_cur[i]));
+            __syncthreads();
+            const uint32_t lo = fmin;  // below 2^28: far nodes were lowered below the clamp
+            T = max(T + delta, lo + delta);
+            ++epoch;
+            const uint32_t fmark = epoch + 1u;
+            for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
+                const uint32_t v = far_cur[i];
+                if (__ldcg(dist + v) < T) {
+                    if (atomicExch(nstamp + v, mark) != mark) qb[atomicAdd(next_cnt, 1u)] = v;
+                } else if (atomicExch(fstamp + v, fmark) != fmark) {
+                    far_nxt[atomicAdd(&fcnt[fsel ^ 1u], 1u)] = v;
                 }
+            }
+            __syncthreads();  // the split is complete; every thread has read fmin and fcnt[fsel]
+            if (threadIdx.x == 0) {
+                fcnt[fsel] = 0;
+                fmin = 0xFFFFFFFFu;
+            }
+            fsel ^= 1u;
+        } else {
+            uint32_t* const far_cur = fsel ? fb : fa;
+            const uint32_t fmark = epoch + 1u;
+            for (uint32_t i = threadIdx.x; i < n_cur; i += blockDim.x) {
+                const uint32_t u = qa[i];
+                const uint32_t du = __ldcg(dist + u);  // bounds change by atomics (in L2): skip L1
+                const uint32_t k1 = in_ptr[u + 1];
+                for (uint32_t k0 = in_ptr[u]; k0 < k1; k0 += 4) {
+                    // up to four in-roads: every load first, then the atomics of the relaxations that
+                    // improve on the bound read (most do not; a stale read only costs an atomic)
+                    uint32_t vv[4], nd[4], cur[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (nd[j] < cur[j] && nd[j] < atomicMin(dist + vv[j], nd[j]) && atomicExch(stamp + vv[j], mark) != mark)
-                        qb[atomicAdd(next_cnt, 1u)] = vv[j];
+                    for (int j = 0; j < 4; ++j) {
+                        const bool ok = k0 + j < k1;
+                        vv[j] = ok ? in_tail[k0 + j] : 0u;
+                        nd[j] = ok ? min(du + rec[in_edge[k0 + j]].tt, kHClamp) : kHClamp;
+                        cur[j] = ok ? __ldcg(dist + vv[j]) : 0u;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!(nd[j] < cur[j] && nd[j] < atomicMin(dist + vv[j], nd[j]))) continue;
+                        if (nd[j] < T) {
+                            if (atomicExch(nstamp + vv[j], mark) != mark) qb[atomicAdd(next_cnt, 1u)] = vv[j];
+                        } else if (atomicExch(fstamp + vv[j], fmark) != fmark) {
+                            far_cur[atomicAdd(&fcnt[fsel], 1u)] = vv[j];
+                        }
+                    }
+                }
             }
         }
         uint32_t* const t = qa;
         qa = qb;
         qb = t;
-        __syncthreads();  // frontier level + 1 is complete
+        __syncthreads();  // the next near frontier (and far pile) is complete
     }
 }
 
@@ -1031,10 +1074,10 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
 }
 
 cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,
-                           const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t* hdist,
-                           uint32_t* queue, uint32_t* stamp, uint32_t* err) {
+                           const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t delta,
+                           uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err) {
     if (Q == 0 || N == 0) return cudaSuccess;
-    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, hdist, queue, stamp, err);
+    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, delta, hdist, queue, stamps, err);
     return cudaGetLastError();
 }
 
