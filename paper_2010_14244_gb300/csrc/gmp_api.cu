@@ -79,6 +79,7 @@ struct Batch {
     uint32_t* qstate = nullptr;
     uint32_t* qflag = nullptr;
     uint32_t* misc = nullptr;  // [0] finished colonies, [1] persistent wait expired, [2] exact-h level bound
+    bool queue_general = false;  // intersections with more than two phases: a queue pass of their own
     // exact Calc_Dist (GMP_FLAG_EXACT_H)
     bool exact_h = false;
     uint32_t* hdist = nullptr;   // Q * N bounds
@@ -106,7 +107,8 @@ struct Batch {
 // What fixes the node structure of a captured job: the job form, timing events, the chains with their
 // iteration counts and kernel shapes. Jobs with equal topology differ only in kernel parameters.
 std::vector<uint32_t> topology_of(const Batch& b) {
-    std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, b.exact_h ? 1u : 0u, (uint32_t)b.br.size(), b.maxI,
+    std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, b.exact_h ? 1u : 0u, b.queue_general ? 1u : 0u,
+                            (uint32_t)b.br.size(), b.maxI,
                             (uint32_t)b.kc.lanes, (uint32_t)b.kc.slots, b.kc.lockstep ? 1u : 0u,
                             b.kc.tabu_in_smem ? 1u : 0u, (uint32_t)b.kc.block, b.kc.frac ? 1u : 0u};
     for (const Batch::Branch& r : b.br) {
@@ -144,6 +146,7 @@ struct gmp_ctx {
     bool has_graph = false;
     uint32_t N = 0, E = 0, maxdeg = 0, kappa = 0;
     uint32_t h_delta = 1;  // exact heuristic: near-far threshold step, 16 x the mean free-flow road time (ms)
+    uint32_t max_phases = 0;  // most phases at any intersection (above 2: the iteration end's general pass)
     uint32_t *row_ptr = nullptr, *col = nullptr, *len = nullptr, *in_ptr = nullptr, *in_edge = nullptr;
     uint32_t* in_tail = nullptr;  // tail of each in_edge entry (exact Calc_Dist relaxes towards tails)
     uint32_t *ff = nullptr, *cap = nullptr;
@@ -344,7 +347,7 @@ uint32_t hsat_of(const gmp_ctx* c) { return c->prm.h_sat_ms ? c->prm.h_sat_ms : 
 int refresh_dynamic(gmp_ctx* c) {
     GMP_CUDA(c, launch_edge_dynamic(c->stream, c->E, c->row_ptr, c->col, c->ff, c->cap, c->lanes, c->veh, c->nph,
                                     hsat_of(c), c->prm.thr_permille, c->rec));
-    GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
+    GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, 0u, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
                                      c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
     return GMP_OK;
 }
@@ -630,6 +633,12 @@ int enqueue_job(gmp_ctx* c) {
             // job, so every chain would compute the same order): the chains share that work evenly
             e.n_nodes = (it % B == j) ? n_nodes : 0u;
             GMP_CUDA(c, launch_iter_end(bs, e));
+            if (e.n_nodes && b.queue_general) {  // the iteration end updated the intersections with <= 2 phases
+                GMP_CUDA(c, launch_queue_preempt(bs, c->N, 3u, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle,
+                                                 c->offset, c->green, c->ephase, c->veh, c->cap, c->red, c->order,
+                                                 c->rec));
+                ++n;
+            }
             if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 2 + 2 * it], bs, cudaEventRecordExternal));
             n += 2;
         }
@@ -777,6 +786,7 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     c->hx.assign(x_dm, x_dm + N);
     c->hy.assign(y_dm, y_dm + N);
     c->kappa = (uint32_t)((360ull << 16) / vmax);
+    c->max_phases = 0;  // no signals until gmp_set_signals
     {
         uint64_t ff_sum = 0;  // free-flow times as the road kernels compute them (a tuning input only)
         for (uint32_t e = 0; e < E; ++e) ff_sum += ((uint64_t)length_dm[e] * 360u + speed_kmh[e] / 2u) / speed_kmh[e];
@@ -861,6 +871,8 @@ int gmp_set_signals(gmp_ctx* c, const uint8_t* n_phases, const uint32_t* cycle_m
     }
     sync(c);
     GMP_TRY(upload(c, c->nph, n_phases, c->N));
+    c->max_phases = 0;
+    for (uint32_t v = 0; v < c->N; ++v) c->max_phases = std::max<uint32_t>(c->max_phases, n_phases[v]);
     GMP_TRY(upload(c, c->cycle, cycle_ms, c->N));
     GMP_TRY(upload(c, c->offset, offset_ms, c->N));
     GMP_TRY(upload(c, c->green, green_ms, (size_t)c->N * kMaxPhases));
@@ -1127,6 +1139,7 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     b.log_entries = (c->prm.flags & GMP_FLAG_ANT_LOG) ? logs : 0;
     b.persistent = c->prm.mode == GMP_MODE_PERSISTENT;
     b.exact_h = (c->prm.flags & GMP_FLAG_EXACT_H) != 0;
+    b.queue_general = c->max_phases > 2;
     if (c->prm.tau_layout == GMP_TAU_SPARSE && (b.persistent || (c->prm.flags & GMP_FLAG_RANDOM_TAU)))
         return fail(c, GMP_ERR_UNSUPPORTED, "the sparse pheromone layout needs the iterative job and 1.0 initial pheromone");
     b.sparse = use_sparse(c);

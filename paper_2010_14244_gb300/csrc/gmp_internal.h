@@ -118,8 +118,9 @@ cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* len, 
 cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
                                 const uint32_t* ff, const uint32_t* cap, const uint8_t* lanes, const uint32_t* veh,
                                 const uint8_t* nph, uint32_t h_sat, uint32_t thr, EdgeRec* rec);
-cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
-                                 const uint32_t* in_edge,
+// The queue / preemption update of the intersections with at least min_phases phases (0: all).
+cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, uint32_t min_phases, const uint32_t* row_ptr,
+                                 const uint32_t* in_ptr, const uint32_t* in_edge,
                                  const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
                                  const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec);

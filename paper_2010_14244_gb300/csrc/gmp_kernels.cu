@@ -51,9 +51,11 @@ __global__ void k_edge_dynamic(uint32_t E, const uint32_t* __restrict__ row_ptr,
 }
 
 // ------------------------------------------------------------------------------------------------
-// Preemptive phase order, one thread per intersection (queue_node in gmp_walk.cuh).
+// Preemptive phase order, one thread per intersection (queue_node in gmp_walk.cuh), for the
+// intersections with at least min_phases phases.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ in_ptr,
+__global__ void k_queue_preempt(uint32_t N, uint32_t min_phases, const uint32_t* __restrict__ row_ptr,
+                                const uint32_t* __restrict__ in_ptr,
                                 const uint32_t* __restrict__ in_edge,
                                 const uint8_t* __restrict__ nph, const uint32_t* __restrict__ cycle,
                                 const uint32_t* __restrict__ offset, const uint32_t* __restrict__ green,
@@ -61,7 +63,7 @@ __global__ void k_queue_preempt(uint32_t N, const uint32_t* __restrict__ row_ptr
                                 const uint32_t* __restrict__ cap, const uint32_t* __restrict__ red,
                                 uint8_t* __restrict__ order, EdgeRec* __restrict__ rec) {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= N) return;
+    if (v >= N || nph[v] < min_phases) return;
     queue_node(v, row_ptr, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh, cap, red, order, rec);
 }
 
@@ -977,9 +979,9 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
     }
     b -= a.n_queries;
     const uint32_t v = b * blockDim.x + threadIdx.x;
-    if (v < a.n_nodes)
-        queue_node(v, a.row_ptr, a.in_ptr, a.in_edge, a.nph, a.cycle, a.offset, a.green, a.ephase, a.veh, a.cap, a.red,
-                   a.order, a.rec);
+    if (v < a.n_nodes)  // intersections with more than two phases: a separate launch (queue_node)
+        queue_node_small(v, a.row_ptr, a.in_ptr, a.in_edge, a.nph, a.cycle, a.offset, a.green, a.ephase, a.veh, a.cap,
+                         a.red, a.order, a.rec);
 }
 
 __global__ void k_finalize(const DevQuery* __restrict__ q, const QueryState* __restrict__ qs,
@@ -1029,14 +1031,14 @@ cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_
     return cudaGetLastError();
 }
 
-cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
-                                 const uint32_t* in_edge,
+cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, uint32_t min_phases, const uint32_t* row_ptr,
+                                 const uint32_t* in_ptr, const uint32_t* in_edge,
                                  const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
                                  const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
                                  const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec) {
     if (N == 0) return cudaSuccess;
-    k_queue_preempt<<<blocks_for(N, 128), 128, 0, s>>>(N, row_ptr, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh,
-                                                        cap, red, order, rec);
+    k_queue_preempt<<<blocks_for(N, 128), 128, 0, s>>>(N, min_phases, row_ptr, in_ptr, in_edge, nph, cycle, offset,
+                                                        green, ephase, veh, cap, red, order, rec);
     return cudaGetLastError();
 }
 

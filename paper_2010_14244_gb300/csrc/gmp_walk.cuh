@@ -117,6 +117,81 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
     }
 }
 
+// queue_node for a node with at most two phases (unsignalised nodes, and every junction the generators
+// build), with the same results in far fewer registers: two keys decide the whole order. Returns false,
+// doing nothing, for a node with more phases (queue_node handles those). Phase p of a road into a
+// signalised node is below its phase count and the greens add up to the cycle (both checked when the
+// signals are set), so only phases 0 and 1 occur here.
+__device__ __forceinline__ bool queue_node_small(uint32_t v, const uint32_t* __restrict__ row_ptr,
+                                                 const uint32_t* __restrict__ in_ptr,
+                                                 const uint32_t* __restrict__ in_edge, const uint8_t* __restrict__ nph,
+                                                 const uint32_t* __restrict__ cycle,
+                                                 const uint32_t* __restrict__ offset,
+                                                 const uint32_t* __restrict__ green,
+                                                 const uint8_t* __restrict__ ephase,
+                                                 const uint32_t* __restrict__ veh, const uint32_t* __restrict__ cap,
+                                                 const uint32_t* __restrict__ red, uint8_t* __restrict__ order,
+                                                 EdgeRec* __restrict__ rec) {
+    const uint32_t P = nph[v];
+    if (P > 2) return false;
+    const uint32_t ib = in_ptr[v], ie = in_ptr[v + 1];
+    const uint32_t deg = min(row_ptr[v + 1] - row_ptr[v], 255u) << 24;  // out-degree of v (at most 128 runs)
+    uint2* const ord = reinterpret_cast<uint2*>(order + (size_t)v * kMaxPhases);
+    if (P == 0) {
+        *ord = make_uint2(0x03020100u, 0x07060504u);  // identity order
+        for (uint32_t i = ib; i < ie; ++i)  // second half of the record (see EdgeRec)
+            reinterpret_cast<uint4*>(rec + in_edge[i])[1] = make_uint4(deg, 0u, 0u, 0u);
+        return true;
+    }
+    uint64_t Q0 = 0, Q1 = 0, S0 = 0, S1 = 0;
+    for (uint32_t i = ib; i < ie; ++i) {
+        const uint32_t e = in_edge[i];
+        const bool p1 = (ephase[e] & (kMaxPhases - 1)) != 0u;
+        const uint32_t n = veh[e], c = cap[e];
+        Q0 += p1 ? 0u : n;
+        S0 += p1 ? 0u : c;
+        Q1 += p1 ? n : 0u;
+        S1 += p1 ? c : 0u;
+    }
+    const uint32_t cy = cycle[v];
+    const uint32_t rd0 = red[(size_t)v * kMaxPhases], g0 = green[(size_t)v * kMaxPhases];
+    const uint32_t rd1 = P > 1 ? red[(size_t)v * kMaxPhases + 1] : 0u;
+    const uint32_t g1 = P > 1 ? green[(size_t)v * kMaxPhases + 1] : 0u;
+    const uint32_t valid = P > 1 ? 3u : 1u;
+    const uint32_t over = ((Q0 > S0 * 3u / 4u ? 1u : 0u) | (Q1 > S1 * 3u / 4u ? 2u : 0u)) & valid;
+    const uint32_t starved = ((rd0 > cy ? 1u : 0u) | (rd1 > cy ? 2u : 0u)) & valid;
+    const uint32_t nonempty = ((Q0 > 0 ? 1u : 0u) | (Q1 > 0 ? 2u : 0u)) & valid;
+    uint32_t prio = 0;
+    bool by_q = true;
+    if (over) {
+        prio = over;
+    } else if (starved) {
+        prio = starved;
+        by_q = false;
+    } else if (nonempty) {  // the longest non-empty queue, phase 0 on ties
+        prio = ((nonempty & 1u) && (!(nonempty & 2u) || Q0 >= Q1)) ? 1u : 2u;
+    }
+    // the sort keys of queue_node; phase 0 goes first when its key is the smaller one
+    constexpr uint64_t kVmax = (1ull << 48) - 1;
+    const uint64_t v0 = by_q ? Q0 : (uint64_t)rd0, v1 = by_q ? Q1 : (uint64_t)rd1;
+    const uint64_t grp0 = (prio & 1u) ? 0u : ((nonempty & 1u) ? 1u : 2u);
+    const uint64_t grp1 = (prio & 2u) ? 0u : ((nonempty & 2u) ? 1u : 2u);
+    const uint64_t key0 = (grp0 << 60) | (grp0 == 0 ? (kVmax - (v0 < kVmax ? v0 : kVmax)) << 4 : 0u);
+    const uint64_t key1 = (grp1 << 60) | (grp1 == 0 ? (kVmax - (v1 < kVmax ? v1 : kVmax)) << 4 : 0u) | 1u;
+    const bool first0 = P == 1 || key0 < key1;
+    *ord = make_uint2(first0 ? 0x03020100u : 0x03020001u, 0x07060504u);
+    const uint32_t st0 = first0 ? 0u : g1, st1 = first0 ? g0 : 0u;  // green-window starts in plan order
+    const uint32_t off = offset[v];
+    const uint32_t magic = 0xFFFFFFFFu / cy;
+    for (uint32_t i = ib; i < ie; ++i) {
+        const uint32_t e = in_edge[i];
+        const bool p1 = (ephase[e] & (kMaxPhases - 1)) != 0u;
+        reinterpret_cast<uint4*>(rec + e)[1] =
+            make_uint4(cy | deg, (off + (p1 ? st1 : st0)) % cy, p1 ? g1 : g0, magic);
+    }
+    return true;
+}
+
 // Sparse pheromone layout: a road's first deposit of the job registers it in its colony's list,
 // with the pheromone it held until then (the colony's baseline of this iteration); from then on the
 // iteration end evaporates it on its own. The flag test before the atomic skips registered roads.

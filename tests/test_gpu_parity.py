@@ -374,3 +374,39 @@ def test_consecutive_jobs_on_one_context(gm, ctx, orc):
         res = ctx.solve_batch(qs)
         for j, q in enumerate(qs):
             _compare(orc, onet, orc.Params(), q, res[j], ctx, j)
+
+
+@pytest.mark.parametrize("sched", ["chains_default", "chains1", "persistent"])
+def test_queue_update_fast_and_general_paths(gm, ctx, orc, sched):
+    """Intersections with one or two phases take the iteration end's small path, the others a general pass
+    of their own: a graph mixing 0-8 phases, heavy queues (some over 3/4 of capacity) and long red times
+    (some starved) must keep the oracle's phase orders through a multi-iteration job."""
+    rng = np.random.default_rng(31)
+    net, sig = W.random_small(200, 420, rng, signalised_frac=0.8)
+    P = np.where(sig.n_phases > 0, rng.choice([1, 2, 2, 2, 3, 5, 8], net.n_nodes), 0).astype(np.uint8)
+    green = np.zeros((net.n_nodes, 8), np.uint32)
+    for v in range(net.n_nodes):
+        if P[v]:
+            green[v, : P[v]] = rng.integers(4000, 30000, P[v])
+    cycle = green.sum(1).astype(np.uint32)
+    offset = (rng.random(net.n_nodes) * np.maximum(cycle, 1)).astype(np.uint32)
+    ephase = np.where(P[net.col] > 0, rng.integers(0, 8, net.n_edges) % np.maximum(P[net.col], 1), 0).astype(np.uint8)
+    sig = W.SignalTiming(P, cycle, offset, green.ravel(), ephase)
+    veh = rng.integers(0, 120, net.n_edges).astype(np.uint32)
+    red = rng.choice(np.array([0, 3000, 90000, 400000], np.uint32), size=(net.n_nodes, 8))
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    ctx.set_red_times(red)
+    ctx.set_params(**SCHEDULES[sched])
+    onet = orc.Net(net, sig, veh, red)
+    want = orc.queue_preempt(onet)
+    np.testing.assert_array_equal(ctx.phase_order(), want)
+    qs = [Q(int(s), int(d), 24, 7, 1.0, 2.0, 0.1, 60 + i) for i, (s, d) in enumerate(W.uniform_od(net.n_nodes, 5, rng))]
+    res = ctx.solve_batch(qs)
+    for i, q in enumerate(qs):
+        _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
+    np.testing.assert_array_equal(ctx.phase_order(), want)
+    tt, qd = ctx.edge_times()
+    prep = orc.prepare(onet, orc.Params(), 0)
+    np.testing.assert_array_equal(tt, prep["tt"])
