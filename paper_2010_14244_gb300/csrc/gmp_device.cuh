@@ -96,19 +96,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// floor(sqrt(n)) for n < 2^58: a binary32 estimate corrected to the exact integer root.
-__device__ __forceinline__ uint64_t isqrt_u64(uint64_t n) {
-    uint64_t r = (uint64_t)__fsqrt_rn(__ull2float_rn(n));
-    while (r * r > n) --r;
-    while ((r + 1) * (r + 1) <= n) ++r;
+// floor(sqrt(n)) for n < 2^58: a binary32 estimate corrected to the exact integer root (below 2^29, so
+// the checks are single 32 x 32 -> 64-bit products).
+__device__ __forceinline__ uint32_t isqrt_u64(uint64_t n) {
+    uint32_t r = (uint32_t)__fsqrt_rn(__ull2float_rn(n));
+    while ((uint64_t)r * r > n) --r;
+    while ((uint64_t)(r + 1u) * (r + 1u) <= n) ++r;
     return r;
 }
 
 // Calc_Dist: admissible remaining-time bound, floor(isqrt(dx^2 + dy^2) * kappa / 2^16), kappa =
-// floor(360 * 2^16 / v_max) ms per dm in Q16.16.
+// floor(360 * 2^16 / v_max) ms per dm in Q16.16. Coordinates lie within +-2^27 dm (checked when the graph
+// is loaded), so the differences fit in 32 bits and their squares are single wide products.
 __device__ __forceinline__ uint32_t heuristic_ms(int32_t x, int32_t y, int32_t xd, int32_t yd, uint32_t kappa) {
-    const int64_t dx = (int64_t)x - xd, dy = (int64_t)y - yd;
-    const uint64_t d = isqrt_u64((uint64_t)(dx * dx) + (uint64_t)(dy * dy));
+    const int32_t dx = x - xd, dy = y - yd;
+    const uint64_t d = isqrt_u64((uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy));
     const uint64_t h = (d * kappa) >> 16;
     return h > kHClamp ? kHClamp : (uint32_t)h;
 }
