@@ -196,7 +196,6 @@ def uniform_od(n_nodes, n_pairs, rng):
 def hop_filtered_od(net: RoadNetwork, n_pairs, lo, hi, rng):
     """Uniform OD pairs whose BFS hop count lies in [lo, hi]."""
     from scipy.sparse import csr_matrix
-    from scipy.sparse.csgraph import breadth_first_order  # noqa: F401  (kept for clarity)
     from scipy.sparse.csgraph import shortest_path
 
     n = net.n_nodes

@@ -1,7 +1,6 @@
 """Parity of the paper-literal pheromone variant (repulsive scores, unit deposits, unused-only
 evaporation; Sec. 4.1, Fig. 3, Algorithm 2) and of saturated scores, GPU against the oracle bit for bit,
 through the C ABI, for every kernel shape and both pheromone layouts."""
-import numpy as np
 import pytest
 
 from paper_2010_14244_gb300 import workloads as W

@@ -10,7 +10,6 @@ import random
 from fractions import Fraction
 
 import numpy as np
-import pytest
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

@@ -1,8 +1,5 @@
 """Pins of the oracle's ant walk and full colony against hand-worked steps, textbook shortest-path
 routines, brute force, exact identities and degenerate cases. No GPU needed."""
-import random
-from fractions import Fraction
-
 import numpy as np
 import pytest
 
