@@ -127,6 +127,16 @@ const char *gmp_last_error(const gmp_ctx *ctx);
 /* Issue subsequent work on cuda_stream (NULL = the context's own stream). */
 int gmp_set_stream(gmp_ctx *ctx, void *cuda_stream);
 
+/* Optional: place every device allocation of the context (graph, traffic state, batch workspace) inside
+ * caller-owned device memory [dev_ptr, dev_ptr + bytes), for example a tensor from the caller's allocator,
+ * instead of cudaMalloc. Call it before gmp_load_graph. The memory must be 256-byte aligned device memory
+ * of the context's GPU and stay valid, and untouched by the caller, until gmp_destroy; the library never
+ * frees it. Allocations are first fit in 256-byte multiples with free runs merged. A request that does
+ * not fit fails with GMP_ERR_OOM, and the memory budget of gmp_create still applies. dev_ptr == NULL
+ * unbinds (also only before gmp_load_graph). Errors: INVALID_ARG (alignment, size, not device memory of
+ * this GPU), STATE (the context already holds device memory). */
+int gmp_bind_workspace(gmp_ctx *ctx, void *dev_ptr, uint64_t bytes);
+
 /* Road graph G(N, E) (Fig. 3 "G(N,E) = graph"; Sec. 5: roads with lanes) in CSR form: the roads leaving
  * node u are row_ptr[u] .. row_ptr[u+1]-1, in the order that breaks ties between equal choices.
  * col[e]: head node; length_dm[e] >= 1; speed_kmh[e] >= 1; lanes[e] >= 1; x_dm, y_dm: node coordinates,

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <string>
+#include <iterator>
 #include <map>
 #include <unordered_map>
 #include <vector>
@@ -141,6 +142,11 @@ struct gmp_ctx {
     cudaStream_t own_stream = nullptr;
     uint64_t budget = 0, used = 0;
     std::unordered_map<void*, size_t> sizes;
+    // caller-owned device memory (gmp_bind_workspace): allocations are carved from it instead of cudaMalloc
+    char* arena = nullptr;
+    uint64_t arena_bytes = 0;
+    std::map<uint64_t, uint64_t> arena_free;           // offset -> length of each free run
+    std::unordered_map<void*, uint64_t> arena_blocks;  // allocation -> length carved for it
     std::string err;
     gmp_params prm{};
     bool has_graph = false;
@@ -214,6 +220,44 @@ int fail(gmp_ctx* c, int code, const char* fmt, ...) {
         if (r_ != GMP_OK) return r_; \
     } while (0)
 
+// First fit in the bound workspace: runs of 256-byte multiples, split on allocation.
+void* arena_take(gmp_ctx* c, size_t bytes) {
+    const uint64_t need = ((uint64_t)bytes + 255u) & ~(uint64_t)255u;
+    for (auto it = c->arena_free.begin(); it != c->arena_free.end(); ++it) {
+        if (it->second < need) continue;
+        const uint64_t off = it->first, len = it->second;
+        c->arena_free.erase(it);
+        if (len > need) c->arena_free[off + need] = len - need;
+        void* q = c->arena + off;
+        c->arena_blocks[q] = need;
+        return q;
+    }
+    return nullptr;
+}
+
+// Return a block to the bound workspace, merging it with free neighbours. Like cudaFree, it first waits
+// for the context's work (every job joins its chains back into the context's stream).
+void arena_give(gmp_ctx* c, void* q) {
+    cudaStreamSynchronize(c->stream);
+    auto b = c->arena_blocks.find(q);
+    if (b == c->arena_blocks.end()) return;
+    uint64_t off = (uint64_t)((char*)q - c->arena), len = b->second;
+    c->arena_blocks.erase(b);
+    auto next = c->arena_free.lower_bound(off);
+    if (next != c->arena_free.end() && next->first == off + len) {
+        len += next->second;
+        next = c->arena_free.erase(next);
+    }
+    if (next != c->arena_free.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += len;
+            return;
+        }
+    }
+    c->arena_free[off] = len;
+}
+
 template <class T>
 int dalloc(gmp_ctx* c, T** p, size_t n) {
     const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
@@ -221,10 +265,15 @@ int dalloc(gmp_ctx* c, T** p, size_t n) {
         return fail(c, GMP_ERR_OOM, "memory budget exceeded: %zu + %zu > %llu bytes", (size_t)c->used, bytes,
                     (unsigned long long)c->budget);
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, GMP_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    if (c->arena) {
+        q = arena_take(c, bytes);
+        if (!q) return fail(c, GMP_ERR_OOM, "bound workspace exhausted: no free run of %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GMP_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
     }
     *p = static_cast<T*>(q);
     c->used += bytes;
@@ -240,7 +289,8 @@ void dfree(gmp_ctx* c, T** p) {
             c->used -= it->second;
             c->sizes.erase(it);
         }
-        cudaFree((void*)*p);
+        if (c->arena_blocks.count((void*)*p)) arena_give(c, (void*)*p);
+        else cudaFree((void*)*p);
         *p = nullptr;
     }
 }
@@ -741,6 +791,33 @@ void gmp_destroy(gmp_ctx* c) {
 int gmp_set_stream(gmp_ctx* c, void* cuda_stream) {
     if (!c) return GMP_ERR_INVALID_ARG;
     c->stream = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+    return GMP_OK;
+}
+
+int gmp_bind_workspace(gmp_ctx* c, void* dev_ptr, uint64_t bytes) {
+    if (!c) return GMP_ERR_INVALID_ARG;
+    if (c->has_graph || !c->sizes.empty())
+        return fail(c, GMP_ERR_STATE, "bind the workspace before gmp_load_graph (the context holds device memory)");
+    if (!dev_ptr) {
+        c->arena = nullptr;
+        c->arena_bytes = 0;
+        c->arena_free.clear();
+        c->arena_blocks.clear();
+        return GMP_OK;
+    }
+    if ((uintptr_t)dev_ptr % 256u != 0 || bytes < 256u)
+        return fail(c, GMP_ERR_INVALID_ARG, "workspace must be 256-byte aligned and at least 256 bytes");
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, dev_ptr) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+        attr.device != c->device) {
+        cudaGetLastError();
+        return fail(c, GMP_ERR_INVALID_ARG, "workspace must be device memory of the context's GPU");
+    }
+    c->arena = static_cast<char*>(dev_ptr);
+    c->arena_bytes = bytes & ~(uint64_t)255u;
+    c->arena_free.clear();
+    c->arena_blocks.clear();
+    c->arena_free[0] = c->arena_bytes;
     return GMP_OK;
 }
 

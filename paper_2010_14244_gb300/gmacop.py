@@ -82,6 +82,7 @@ SIGNATURES = {
     "gmp_strerror": (C.c_char_p, [_i32]),
     "gmp_last_error": (C.c_char_p, [_vp]),
     "gmp_set_stream": (_i32, [_vp, _vp]),
+    "gmp_bind_workspace": (_i32, [_vp, _vp, _u64]),
     "gmp_load_graph": (_i32, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gmp_set_signals": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "gmp_set_red_times": (_i32, [_vp, _vp]),
@@ -183,6 +184,11 @@ class Context:
     def set_stream(self, stream=None):
         handle = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._check(lib().gmp_set_stream(self._h, handle))
+
+    def bind_workspace(self, dev_ptr: int, nbytes: int):
+        """gmp_bind_workspace: carve every later device allocation of this context from caller-owned
+        device memory (e.g. tensor.data_ptr() of a uint8 CUDA tensor kept alive until close())."""
+        self._check(lib().gmp_bind_workspace(self._h, C.c_void_p(dev_ptr) if dev_ptr else None, nbytes))
 
     # ---------------------------------------------------------------- inputs
     def load_graph(self, net):
