@@ -179,17 +179,27 @@ def make_pool():
     return mp.get_context("spawn").Pool(min(cores, 16), initializer=_pool_init), min(cores, 16)
 
 
+def _one_core_solve(qi):
+    t0 = time.perf_counter()
+    steps, _ = _pool_solve(qi)
+    return steps, time.perf_counter() - t0
+
+
 def cpu_baseline_line(n_queries):
     pool, cores = make_pool()
     try:
         steps, dt = oracle_run(pool, n_queries)
+        # one colony alone in one process (one core), the same oracle
+        one_steps, one_dt = pool.apply(_one_core_solve, (0,))
     finally:
         pool.close()
         pool.join()
     return {"value": steps / dt, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"all {n_queries} colonies of the workload (full size), one colony per process, "
                       f"{cores} processes, {dt:.1f} s wall",
-            "queries_per_s": n_queries / dt}
+            "queries_per_s": n_queries / dt,
+            "one_core": {"value": one_steps / one_dt, "unit": "ant-steps/s", "queries_per_s": 1.0 / one_dt,
+                         "sample": f"colony 0 of the workload alone in one process, {one_dt:.2f} s"}}
 
 
 def run_reference(args, rank, world):
