@@ -385,6 +385,18 @@ def run_gpu(args, rank, world, local_rank):
     assert [r["travel_ms"] for r in res2] == [r["travel_ms"] for r in res]
     total_ms = max_over_ranks(sum(times), world)
 
+    # the job's critical path, from a per-ant log of the same job (not timed): iterations are synchronous,
+    # so each colony takes at least the sum over iterations of its longest walk, one dependent step after
+    # another; the slowest colony bounds the job
+    ctx.set_params(**dict(sched, flags=sched["flags"] | gmacop.FLAG_ANT_LOG))
+    ctx.solve_batch(wl.queries)
+    longest = [int(ctx.ant_log(i)[:, :, 1].max(axis=1).sum()) for i in range(nq)]
+    crit_steps = max(longest)
+    critical = {"longest_walk_steps_summed_over_iterations": crit_steps, "colony": int(np.argmax(longest)),
+                "us_per_critical_step": (total_ms / args.steps) * 1e3 / crit_steps,
+                "how": "job device time / (max over colonies of the sum over iterations of the longest walk)"}
+    ctx.set_params(**sched)
+
     # the plain form: each colony its own job (stage, launch, collect), one after another
     plain = None
     if not args.no_plain:
@@ -490,6 +502,7 @@ def run_gpu(args, rank, world, local_rank):
                      "time": "job device time (construction launches of concurrent chains overlap)",
                      "construct_launches_per_job": construct_launches,
                      "avg_launch_ms_summed_over_chains": kt["construct"] / (K * max(construct_launches, 1))},
+        "critical_path": critical,
         "gpu_launches": launches * K,
         "clocks": clocks,
     }
