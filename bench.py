@@ -392,10 +392,31 @@ def run_gpu(args, rank, world, local_rank):
     ctx.solve_batch(wl.queries)
     longest = [int(ctx.ant_log(i)[:, :, 1].max(axis=1).sum()) for i in range(nq)]
     crit_steps = max(longest)
-    critical = {"longest_walk_steps_summed_over_iterations": crit_steps, "colony": int(np.argmax(longest)),
-                "us_per_critical_step": (total_ms / args.steps) * 1e3 / crit_steps,
-                "how": "job device time / (max over colonies of the sum over iterations of the longest walk)"}
+    slow = int(np.argmax(longest))
+    # the slowest colony alone, as its own job in the same schedule (not timed with the rest): its walks are
+    # the same as in the batch, so the batch costs job / alone times its own critical chain
     ctx.set_params(**sched)
+    ctx.stage([wl.queries[slow]])
+    alone = []
+    with torch.cuda.stream(stream):
+        ctx.launch()
+        stream.synchronize()
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.launch()
+            e1.record(stream)
+            e1.synchronize()
+            alone.append(e0.elapsed_time(e1))
+    assert ctx.collect()[0]["travel_ms"] == res[slow]["travel_ms"]
+    alone_ms = statistics.median(alone)
+    critical = {"longest_walk_steps_summed_over_iterations": crit_steps, "colony": slow,
+                "us_per_critical_step": (total_ms / args.steps) * 1e3 / crit_steps,
+                "slowest_colony_alone_ms": alone_ms,
+                "job_over_slowest_colony_alone": (total_ms / args.steps) / alone_ms,
+                "how": "job device time / (max over colonies of the sum over iterations of the longest walk); "
+                       "the slowest colony alone is its own job, same schedule, median of 3"}
 
     # the plain form: each colony its own job (stage, launch, collect), one after another
     plain = None
