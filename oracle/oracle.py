@@ -5,6 +5,7 @@ Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg 
 from __future__ import annotations
 
 import ctypes as C
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -64,7 +65,8 @@ class Params:
 def lib():
     global _LIB
     if _LIB is None:
-        path = _build.build()
+        # ORC_LIB names a library built from a modified copy of the source (the planted-mistake tests)
+        path = os.environ.get("ORC_LIB") or _build.build()
         L = C.CDLL(path)
         u32, u64, f32, vp = C.c_uint32, C.c_uint64, C.c_float, C.c_void_p
         sig = {

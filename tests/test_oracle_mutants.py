@@ -1,0 +1,135 @@
+"""Planted mistakes in a copy of the oracle. Each mutant changes one thing in one function of
+oracle/orc_gmacop.c: a dropped term, a wrong sign, index, constant, shift or comparison. The test compiles
+it from a temporary copy (the oracle's own source and library are never touched) and runs the pins of the
+part it changes against that library (ORC_LIB). The pins must fail. An unmodified copy built the same way
+must pass them, which shows that the harness itself works. No GPU.
+
+Not planted: `key < best_key` against `key <= best_key` in the best-route rule. Keys are unique
+(T, iteration, ant), so the two are equivalent and no test can tell them apart.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "orc_gmacop.c")
+
+PRIM, SOLVE, TICK = "test_oracle_primitives.py", "test_oracle_solve.py", "test_oracle_tick.py"
+EXACT, FRAC, LIT = "test_oracle_exact_h.py", "test_oracle_frac.py", "test_oracle_literal.py"
+
+# (name, text in the oracle, its replacement, pin modules that must catch it)
+MUTANTS = [
+    # Philox4x32-10 (known-answer vectors) and the draw's counter layout
+    ("philox_multiplier", "M0 = 0xD2511F53u", "M0 = 0xD2511F55u", [PRIM]),
+    ("philox_key_schedule", "k1 += W1;", "k1 += W0;", [PRIM]),
+    ("philox_word_swap", "uint32_t y0 = hi1 ^ x1 ^ k0;", "uint32_t y0 = hi1 ^ x1 ^ k1;", [PRIM]),
+    ("draw_counter_order", "uint32_t c[4] = {it, ant, step, stream};", "uint32_t c[4] = {ant, it, step, stream};",
+     [SOLVE]),
+    # road attributes and the straight-line bound
+    ("isqrt_comparison", "if (n >= root + bit) {", "if (n > root + bit) {", [PRIM]),
+    ("free_flow_no_rounding", "(uint64_t)length_dm * 360u + speed_kmh / 2u", "(uint64_t)length_dm * 360u", [PRIM]),
+    ("capacity_spacing", "lanes * length_dm / 75u", "lanes * length_dm / 70u", [PRIM]),
+    ("edge_time_floor", "uint64_t floor_den = cap / 20u;", "uint64_t floor_den = cap / 10u;", [PRIM]),
+    ("edge_time_denominator", "den = cap - n;", "den = cap - n + 1;", [PRIM]),
+    ("queue_delay_lanes", "(uint64_t)n * h_sat_ms / lanes;", "(uint64_t)n * h_sat_ms;", [PRIM]),
+    ("kappa_speed", "((uint64_t)360u << 16) / v_max_kmh", "((uint64_t)360u << 16) / (v_max_kmh + 1)", [PRIM, SOLVE]),
+    ("heuristic_dy_term", "(uint64_t)(dx * dx) + (uint64_t)(dy * dy)", "(uint64_t)(dx * dx) + (uint64_t)(dx * dx)",
+     [PRIM, SOLVE]),
+    # the preemptive phase order and the signal wait
+    ("threshold_fraction", "* 3u / 4u; /* Comp_Thres", "* 2u / 3u; /* Comp_Thres", [PRIM, TICK]),
+    ("over_longest_first", "Q[p] > Th[p] && (best < 0 || Q[p] > Q[best])", "Q[p] > Th[p] && (best < 0 || Q[p] < Q[best])",
+     [PRIM]),
+    ("starvation_not_strict", "if (red_ms[p] > T_max)", "if (red_ms[p] >= T_max)", [PRIM, TICK]),
+    ("empty_phases_not_last", "if (!used[p] && Q[p] > 0) {", "if (!used[p]) {", [PRIM]),
+    ("green_window_end", "if (c >= start && c < start + green[phase])", "if (c >= start && c <= start + green[phase])",
+     [PRIM]),
+    ("signal_offset_sign", "(arr_ms % cycle + cycle - (offset % cycle)) % cycle", "(arr_ms % cycle + (offset % cycle)) % cycle",
+     [PRIM]),
+    # the next-node rule
+    ("score_beta_minus_one", "return p * pow_int(eta, beta);", "return p * pow_int(eta, beta ? beta - 1 : 0);",
+     [PRIM, SOLVE]),
+    ("score_alpha_plus_one", "pow_int(orc_tau_factor(tau, flags), alpha);", "pow_int(orc_tau_factor(tau, flags), alpha + 1);",
+     [PRIM, SOLVE]),
+    ("weight_scale", "floor(ldexp((double)s[i], 22 - E))", "floor(ldexp((double)s[i], 21 - E))", [PRIM]),
+    ("roulette_not_strict", "if (acc > r)", "if (acc >= r)", [PRIM, SOLVE]),
+    ("cost_without_heuristic", "uint32_t c = S->tt[e] + w + S->h[v];", "uint32_t c = S->tt[e] + w;", [SOLVE]),
+    ("wait_at_destination", "if (v != q->dst && g->n_phases[v] > 0) {", "if (g->n_phases[v] > 0) {", [SOLVE]),
+    ("time_without_wait", "t += (uint64_t)S->tt[e] + S->waitv[pick];", "t += (uint64_t)S->tt[e];", [SOLVE]),
+    ("no_visited_rule", "if (!S->visited[g->col[e]])", "if (1)", [SOLVE]),
+    # pheromone: initial value, evaporation, deposits
+    ("random_tau_word", "tau[e] = ((uint64_t)1 << 31) + o[0];", "tau[e] = ((uint64_t)1 << 31) + o[1];", [PRIM]),
+    ("rho_fix_scale", "ldexp((double)rho, 32)", "ldexp((double)rho, 31)", [PRIM, SOLVE]),
+    ("evaporation_shift", "(((unsigned __int128)tau * rho_fix) >> 32)", "(((unsigned __int128)tau * rho_fix) >> 33)",
+     [PRIM, SOLVE]),
+    ("deposit_numerator", "(uint64_t)(S.h[q->src] > 0 ? S.h[q->src] : 1u) << 32",
+     "(uint64_t)(S.h[q->src] > 0 ? S.h[q->src] : 1u) << 31", [SOLVE]),
+    ("deposit_denominator", "dep_num / T;", "dep_num / (T + 1);", [SOLVE]),
+    # the paper-literal variant
+    ("repulsive_not_reciprocal", "return (flags & ORC_FLAG_REPULSIVE) ? 1.0f / tf : tf;", "return tf;", [LIT]),
+    ("unit_deposit_half", "uint64_t delta = unit ? (uint64_t)1 << 32", "uint64_t delta = unit ? (uint64_t)1 << 31", [LIT]),
+    ("evaporate_used_roads", "if (D[e] == 0)", "if (D[e] != 0)", [LIT]),
+    # non-integer exponents
+    ("log2_constant", "LOG_C7 = 0x1.24924ap-3f", "LOG_C7 = 0x1.249250p-3f", [FRAC]),
+    ("exp2_power_split", "int n2 = ni - n1;", "int n2 = ni - n1 + 1;", [FRAC]),
+    ("exp2_series_term", "for (int k = 7; k >= 0; --k)", "for (int k = 7; k >= 1; --k)", [FRAC]),
+    # exact Calc_Dist
+    ("dijkstra_relaxation", "uint64_t nd = dist[u] + tt[e];", "uint64_t nd = dist[u] + tt[e] + 1;", [EXACT]),
+    ("dijkstra_heap_order", "if (l < n_heap && hk[l] < hk[m])", "if (l < n_heap && hk[l] > hk[m])", [EXACT]),
+    # serving tick
+    ("tick_discharge_clock", "(uint64_t)g->lanes[e] * (t_now + dt) / hsat - (uint64_t)g->lanes[e] * t_now / hsat",
+     "(uint64_t)g->lanes[e] * dt / hsat", [TICK]),
+    ("tick_split_remainder", "(j < K[u] % d ? 1u : 0u)", "(j + 1 < K[u] % d ? 1u : 0u)", [TICK]),
+    ("tick_red_empty_phase", "p == gph[v] || Q[i] == 0)", "p == gph[v])", [TICK]),
+]
+
+
+def _cflags():
+    sys.path.insert(0, ROOT)
+    from oracle import build
+
+    return build.CFLAGS
+
+
+def _run(name, old, new, modules, workdir, cflags):
+    """Build the mutant (or the unmodified copy when old is None) and run its pins; returns pytest's code."""
+    src = open(SRC).read()
+    if old is not None:
+        src = src.replace(old, new, 1)
+    path = os.path.join(workdir, name + ".c")
+    lib = os.path.join(workdir, "lib" + name + ".so")
+    with open(path, "w") as f:
+        f.write(src)
+    subprocess.run([os.environ.get("CC", "gcc"), *cflags, "-o", lib, path, "-lm"], check=True, capture_output=True)
+    env = dict(os.environ, ORC_LIB=lib)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+    cmd += [os.path.join(ROOT, "tests", m) for m in modules]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode, r.stdout[-400:]
+
+
+def test_each_mutant_text_occurs_once():
+    src = open(SRC).read()
+    names = [m[0] for m in MUTANTS]
+    assert len(set(names)) == len(names)
+    for name, old, new, _ in MUTANTS:
+        assert src.count(old) == 1, name
+        assert old != new, name
+
+
+def test_planted_mistakes_fail_their_pins():
+    cflags = _cflags()
+    every = sorted({m for *_, mods in MUTANTS for m in mods})
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
+            control = ex.submit(_run, "unmodified", None, None, every, tmp, cflags)
+            runs = [ex.submit(_run, name, old, new, mods, tmp, cflags) for name, old, new, mods in MUTANTS]
+            name, code, out = control.result()
+            assert code == 0, f"the unmodified copy must pass every pin module:\n{out}"
+            survivors = []
+            for f in runs:
+                name, code, out = f.result()
+                if code != 1:  # 1: tests failed; 0: the mutant survived; other codes: the run broke
+                    survivors.append((name, code, out))
+    assert not survivors, survivors

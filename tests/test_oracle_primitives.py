@@ -11,6 +11,8 @@ from fractions import Fraction
 
 import numpy as np
 
+from tests import netbuild as NB
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -190,6 +192,20 @@ def test_phase_order_paper_cases(orc):
     assert orc.phase_order(3, [1, 7, 3], [5, 5, 5], [99, 0, 0], 60) == [1, 0, 2]
     # no queue above threshold: the starved phase goes first
     assert orc.phase_order(3, [1, 4, 3], [5, 5, 5], [0, 0, 99], 60) == [2, 0, 1]
+
+
+def test_queue_threshold_is_three_quarters_of_storage(orc):
+    """Comp_Thres on a hand-built junction: the phase-0 approach stores 3 * 2500 dm / 7.5 m = 100
+    vehicles, so its threshold is 75; the phase-1 approach stores 1000 and holds 80. Up to 75 vehicles
+    on phase 0 no queue is over, and the longer queue (phase 1) goes first. From 76 on, phase 0 is over
+    its threshold and takes precedence."""
+    roads = [(0, 2, 2500, 50, 3, 0), (1, 2, 25000, 50, 3, 1)]
+    for n0, want in [(70, [1, 0]), (75, [1, 0]), (76, [0, 1])]:
+        net, sig, veh = NB.build(3, roads, signals={2: (60000, 0, [30000, 30000])},
+                                 vehicles={(0, 2): n0, (1, 2): 80}, bidirectional=False)
+        order = orc.queue_preempt(orc.Net(net, sig, veh))
+        assert list(order[2][:2]) == want, n0
+        assert list(order[2][2:]) == [2, 3, 4, 5, 6, 7]
 
 
 # ------------------------------------------------------------------------------------------ heuristic
