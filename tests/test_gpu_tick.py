@@ -56,6 +56,31 @@ def test_tick_sequence_matches_oracle(gm, ctx, orc, name):
     _run_ticks(ctx, orc, wl.net, wl.signals, wl.vehicles.copy(), 40, seed=11)
 
 
+def test_tick_red_times_saturate(gm, ctx, orc):
+    """Red-time accumulators a few seconds below 2^32 - 1 on every phase: the tick's growth saturates
+    instead of wrapping, and the phase orders that follow (every queued phase starved, ties broken by
+    phase index) match the oracle."""
+    wl = W.grid10()
+    rng = np.random.Generator(np.random.PCG64(31))
+    red = (2**32 - 1 - rng.integers(0, 6000, size=(wl.net.n_nodes, 8))).astype(np.uint32)
+    red[rng.random((wl.net.n_nodes, 8)) < 0.3] = 2**32 - 1
+    ctx.load_workload(wl)
+    ctx.set_red_times(red)
+    onet = orc.Net(wl.net, wl.signals, wl.vehicles, red)
+    order = orc.queue_preempt(onet)
+    np.testing.assert_array_equal(ctx.phase_order(), order)
+    veh = wl.vehicles.copy()
+    t = 5000
+    for dt in (3700, 1000, 0, 2000):
+        ctx.tick(t, dt)
+        veh, red, order = orc.tick(orc.Net(wl.net, wl.signals, veh, red), orc.Params(), t, dt, order)
+        t += dt
+        np.testing.assert_array_equal(ctx.densities(), veh)
+        np.testing.assert_array_equal(ctx.red_times(), red)
+        np.testing.assert_array_equal(ctx.phase_order(), order)
+    assert (red == 2**32 - 1).sum() > 0
+
+
 def test_tick_congested_and_custom_hsat(gm, ctx, orc):
     """Densities above the 3/4-storage threshold on many approaches (preemption by queue length) and
     a non-default saturation headway."""

@@ -4,8 +4,10 @@ it from a temporary copy (the oracle's own source and library are never touched)
 part it changes against that library (ORC_LIB). The pins must fail. An unmodified copy built the same way
 must pass them, which shows that the harness itself works. No GPU.
 
-Not planted: `key < best_key` against `key <= best_key` in the best-route rule. Keys are unique
-(T, iteration, ant), so the two are equivalent and no test can tell them apart.
+Not planted, because each is equivalent to the original and no test can tell them apart:
+- `key < best_key` against `key <= best_key` in the best-route rule: keys (T, iteration, ant) are unique;
+- a default step cap of N instead of N - 1: a walk that has taken N - 1 roads on distinct nodes stands
+  on the destination, so the cap of N - 1 never binds (the 4096 ceiling does, and is planted).
 """
 import concurrent.futures as cf
 import os
@@ -58,6 +60,14 @@ MUTANTS = [
     ("wait_at_destination", "if (v != q->dst && g->n_phases[v] > 0) {", "if (g->n_phases[v] > 0) {", [SOLVE]),
     ("time_without_wait", "t += (uint64_t)S->tt[e] + S->waitv[pick];", "t += (uint64_t)S->tt[e];", [SOLVE]),
     ("no_visited_rule", "if (!S->visited[g->col[e]])", "if (1)", [SOLVE]),
+    ("step_cap_early", "if (steps == S->max_steps)", "if (steps + 1 == S->max_steps)", [SOLVE]),
+    ("default_step_cap", "uint32_t def_steps = N - 1 < 4096u ? N - 1 : 4096u;",
+     "uint32_t def_steps = N - 1 < 4095u ? N - 1 : 4095u;", [SOLVE]),
+    ("time_cap_halved", "if (t > ORC_T_CAP)", "if (t > ORC_T_CAP / 2)", [SOLVE]),
+    ("congested_all_dropped", "if (n_ok > 0 && n_ok < n) {", "if (n_ok < n) {", [SOLVE]),
+    ("tie_rule_ant_major", "| ((uint64_t)it * q->n_ants + k);", "| ((uint64_t)k * q->n_iter + it);", [SOLVE]),
+    ("beta_fraction_ignored", "*frac = floorf(q->alpha) != q->alpha || floorf(q->beta) != q->beta;",
+     "*frac = floorf(q->alpha) != q->alpha;", [FRAC]),
     # pheromone: initial value, evaporation, deposits
     ("random_tau_word", "tau[e] = ((uint64_t)1 << 31) + o[0];", "tau[e] = ((uint64_t)1 << 31) + o[1];", [PRIM]),
     ("rho_fix_scale", "ldexp((double)rho, 32)", "ldexp((double)rho, 31)", [PRIM, SOLVE]),
@@ -77,11 +87,18 @@ MUTANTS = [
     # exact Calc_Dist
     ("dijkstra_relaxation", "uint64_t nd = dist[u] + tt[e];", "uint64_t nd = dist[u] + tt[e] + 1;", [EXACT]),
     ("dijkstra_heap_order", "if (l < n_heap && hk[l] < hk[m])", "if (l < n_heap && hk[l] > hk[m])", [EXACT]),
+    ("dijkstra_no_clamp", "h[v] = dist[v] > ORC_H_CLAMP ? ORC_H_CLAMP : (uint32_t)dist[v];", "h[v] = (uint32_t)dist[v];",
+     [EXACT]),
     # serving tick
     ("tick_discharge_clock", "(uint64_t)g->lanes[e] * (t_now + dt) / hsat - (uint64_t)g->lanes[e] * t_now / hsat",
      "(uint64_t)g->lanes[e] * dt / hsat", [TICK]),
     ("tick_split_remainder", "(j < K[u] % d ? 1u : 0u)", "(j + 1 < K[u] % d ? 1u : 0u)", [TICK]),
     ("tick_red_empty_phase", "p == gph[v] || Q[i] == 0)", "p == gph[v])", [TICK]),
+    ("tick_red_wraps", "r > 0xFFFFFFFFu - dt ? 0xFFFFFFFFu : r + dt", "r + dt", [TICK]),
+    ("tick_green_window_end", "c < start + green[p])", "c <= start + green[p])", [TICK]),
+    ("red_time_phase_index", "g->red_ms[(size_t)v * ORC_MAX_PHASES + p]", "g->red_ms[(size_t)v * ORC_MAX_PHASES]",
+     [PRIM, TICK]),
+    ("wait_window_start", "start += green[order[i]];", "start += green[i];", [PRIM]),
 ]
 
 

@@ -231,6 +231,21 @@ def test_step_cap(orc):
     assert r["status"] == 0 and r["route_len"] == 7
 
 
+def test_default_step_cap_is_4096(orc):
+    """With max_steps = 0 the cap is min(N - 1, 4096) roads (Q12's reading). On a line of 4200 nodes
+    the only walk from one end to the other has 4199 roads, so it stops after exactly 4096; with the
+    cap raised to 4199 it arrives."""
+    roads = [(i, i + 1, 1000, 50) for i in range(4199)]
+    net, sig, veh = NB.build(4200, roads)
+    onet = orc.Net(net, sig, veh)
+    q = Q(0, 4199, 2, 1, 1.0, 2.0, 0.1, 0)
+    r = orc.solve(onet, orc.Params(), q, want_log=True)
+    assert r["status"] == orc.ERR_NO_ROUTE
+    assert (r["log"][:, :, 0] == orc.ANT_STEP_CAP).all() and (r["log"][:, :, 1] == 4096).all()
+    r = orc.solve(onet, orc.Params(max_steps=4199), q)
+    assert r["status"] == 0 and r["route_len"] == 4200
+
+
 def test_time_cap(orc):
     """Roads whose free-flow time clamps at 2^26 ms: 16 of them take exactly 2^30 ms (allowed),
     the 17th exceeds the 2^30 ms cap and the ant fails."""

@@ -36,6 +36,22 @@ def test_hand_worked_junction(orc):
     assert list(new_order[2][:2]) == [1, 0]
 
 
+def test_red_time_saturates(orc):
+    """The red-time accumulator of a queued phase that is not green grows by dt and stops at 2^32 - 1
+    instead of wrapping; the green phase's accumulator resets to 0."""
+    net, sig, veh = _junction()
+    red0 = np.zeros((5, 8), np.uint32)
+    red0[2][:2] = [123, 2**32 - 1 - 500]
+    onet = orc.Net(net, sig, veh, red0)
+    order = orc.queue_preempt(onet)
+    order[2][:2] = [0, 1]  # phase 0 green at t = 1 s
+    _, red, _ = orc.tick(onet, orc.Params(), 1000, 2000, order)
+    assert red[2][0] == 0 and red[2][1] == 2**32 - 1
+    red0[2][1] = 2**32 - 1 - 2000  # exactly reaches the top
+    _, red, _ = orc.tick(orc.Net(net, sig, veh, red0), orc.Params(), 1000, 2000, order)
+    assert red[2][1] == 2**32 - 1
+
+
 def test_green_phase_follows_the_programme(orc):
     """A star node with P phases, one loaded approach each: the approach that discharges is the one of
     the phase that a millisecond-by-millisecond simulation of the programme shows green."""
