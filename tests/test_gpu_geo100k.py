@@ -1,25 +1,17 @@
 """The 100k-node planar graph at full size: 512 colonies x 256 ants x 100 iterations in one job (visited
-sets in global memory, 16 concurrent chains). Three colonies spread over the chains are re-solved by the
-oracle and must agree bit for bit; every route found is checked for validity. (On this sparse planar
-graph with 20-400 hop pairs most ants end in dead ends under the simple-path rule, so few or no colonies
-find a route; the counts of steps and successes still pin the whole walk.)"""
-import multiprocessing as mp
-
+sets in global memory, 16 concurrent chains, sparse pheromone). Every colony is re-solved by the oracle
+(a pool of spawned processes over the host cores) and must agree bit for bit: status, best route, travel
+and wait times, ant-step and success counts, best (iteration, ant) and the final pheromone table (by
+digest). Every route found is also checked for validity. (On this sparse planar graph with 20-400 hop
+pairs most ants end in dead ends under the simple-path rule, so few colonies find a route. The counts of
+steps and successes and the pheromone tables still pin the whole walk.)"""
 import numpy as np
 import pytest
 
 from paper_2010_14244_gb300 import workloads as W
+from tests import oracle_pool
 
 pytestmark = pytest.mark.gpu
-
-SAMPLE = (0, 255, 511)
-
-
-def _oracle_one(qi):
-    from oracle import oracle as orc
-
-    wl = W.geo100k()
-    return orc.solve(orc.Net.from_workload(wl), orc.Params(), wl.queries[qi], want_tau=False)
 
 
 @pytest.fixture(scope="module")
@@ -30,34 +22,38 @@ def gm():
     return gmacop
 
 
-def test_geo100k_full_size_sampled(gm):
-    # the oracle processes start before the first GPU call (spawn: no CUDA state is inherited)
-    pool = mp.get_context("spawn").Pool(len(SAMPLE))
-    pending = pool.map_async(_oracle_one, SAMPLE)
-    wl = W.geo100k()
-    ctx = gm.Context(0)
+N_COLONIES = 512
+
+
+def test_geo100k_full_size_full_parity(gm):
+    # the workers build the workload while this process builds its own and runs the job
+    pool, pending = oracle_pool.start("geo100k", range(N_COLONIES))
     try:
-        ctx.load_workload(wl)
-        res = ctx.solve_batch(wl.queries)
+        wl = W.geo100k()
+        assert len(wl.queries) == N_COLONIES
+        ctx = gm.Context(0)
+        try:
+            ctx.load_workload(wl)
+            res = ctx.solve_batch(wl.queries)
+            digests = [oracle_pool.tau_digest(ctx.pheromone(i)) for i in range(len(wl.queries))]
+        finally:
+            ctx.close()
+        net = wl.net
+        for q, r in zip(wl.queries, res):
+            assert r["ant_steps"] > 0 and r["status"] in (0, gm.ERR_NO_ROUTE)
+            if r["status"] != 0:
+                continue
+            route = r["route"]
+            assert route[0] == q.src and route[-1] == q.dst and len(set(route.tolist())) == len(route)
+            for a, b in zip(route[:-1], route[1:]):
+                row = net.col[net.row_ptr[a]:net.row_ptr[a + 1]]
+                assert b in row
+        oracle = pending.get(timeout=3000)
     finally:
-        ctx.close()
-    net = wl.net
-    for q, r in zip(wl.queries, res):
-        assert r["ant_steps"] > 0 and r["status"] in (0, gm.ERR_NO_ROUTE)
-        if r["status"] != 0:
-            continue
-        route = r["route"]
-        assert route[0] == q.src and route[-1] == q.dst and len(set(route.tolist())) == len(route)
-        for a, b in zip(route[:-1], route[1:]):
-            row = net.col[net.row_ptr[a]:net.row_ptr[a + 1]]
-            assert b in row
-    oracle = pending.get(timeout=1800)
-    pool.close()
-    for qi, o in zip(SAMPLE, oracle):
-        r = res[qi]
-        assert r["status"] == o["status"]
-        for k in ("travel_ms", "wait_ms", "ant_steps", "n_success"):
-            assert r[k] == o[k], (qi, k, r[k], o[k])
-        if o["status"] == 0:
-            assert r["best_iter"] == o["best_iter"] and r["best_ant"] == o["best_ant"]
-            np.testing.assert_array_equal(r["route"], o["route"])
+        pool.close()
+        pool.join()
+    assert [qi for qi, _ in oracle] == list(range(N_COLONIES))
+    for qi, o in oracle:
+        oracle_pool.check(res[qi], o)
+        assert digests[qi] == o["tau_sha256"], qi
+    assert sum(r["status"] == 0 for r in res) > 0

@@ -11,6 +11,7 @@ import pytest
 
 from paper_2010_14244_gb300 import workloads as W
 from tests import netbuild as NB
+from tests import oracle_pool
 
 pytestmark = pytest.mark.gpu
 
@@ -177,10 +178,22 @@ def test_ragged_batch_equals_solo(gm, ctx, orc, sched):
         _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
 
 
+@pytest.fixture(scope="module")
+def grid64_oracle():
+    """The oracle's solves of all 16 benchmark colonies, in spawned processes over the host cores."""
+    pool, pending = oracle_pool.start("grid64", range(16))
+    try:
+        out = pending.get(timeout=3000)
+    finally:
+        pool.close()
+        pool.join()
+    return [o for _, o in out]
+
+
 @pytest.mark.parametrize("mode", [1, 2])
-def test_grid64_full_size_sampled(gm, ctx, orc, mode):
-    """The benchmark's job (16 colonies x 1024 ants x 200 iterations, one launch): three colonies are
-    re-solved by the oracle and must agree exactly, including the final pheromone table."""
+def test_grid64_full_size_full_parity(gm, ctx, orc, grid64_oracle, mode):
+    """The benchmark's job (16 colonies x 1024 ants x 200 iterations, one launch) in the chained and the
+    persistent form: every colony equals the oracle's solve exactly, final pheromone table included."""
     wl = W.grid64()
     ctx.load_workload(wl)
     ctx.set_params(mode=mode)  # the benchmark's launch configuration (no timing events)
@@ -194,9 +207,9 @@ def test_grid64_full_size_sampled(gm, ctx, orc, mode):
     for a, b in zip(res0, res):  # events around every kernel change nothing
         assert a["travel_ms"] == b["travel_ms"] and a["ant_steps"] == b["ant_steps"]
         np.testing.assert_array_equal(a["route"], b["route"])
-    onet = orc.Net.from_workload(wl)
-    for i in (0, 7, 15):
-        _compare(orc, onet, orc.Params(), wl.queries[i], res[i], ctx, i)
+    assert len(grid64_oracle) == len(wl.queries) == 16
+    for i, o in enumerate(grid64_oracle):
+        oracle_pool.check(res[i], o, ctx.pheromone(i))
     assert all(r["status"] == 0 for r in res)
     # a second launch of the staged batch starts from fresh pheromone: identical results
     ctx.launch()
