@@ -17,23 +17,26 @@ _ONET = None
 def _make(name):
     from paper_2010_14244_gb300 import workloads as W
 
-    return {"grid64": W.grid64, "geo100k": W.geo100k}[name]()
+    return {"grid64": W.grid64, "geo100k": W.geo100k, "city_batch": W.city_batch}[name]()
 
 
 def _init(name):
     global _WL, _ONET
-    from oracle import oracle as orc
-
     _WL = _make(name)
-    _ONET = orc.Net.from_workload(_WL)
+    _ONET = {}
 
 
-def _solve(qi):
+def _solve(item):
+    """item: a colony index, or (graph, colony) for a list of workloads such as city_batch."""
     from oracle import oracle as orc
 
-    o = orc.solve(_ONET, orc.Params(), _WL.queries[qi], want_tau=True)
+    g, qi = item if isinstance(item, tuple) else (None, item)
+    wl = _WL if g is None else _WL[g]
+    if g not in _ONET:
+        _ONET[g] = orc.Net.from_workload(wl)
+    o = orc.solve(_ONET[g], orc.Params(), wl.queries[qi], want_tau=True)
     o["tau_sha256"] = tau_digest(o.pop("tau"))
-    return qi, o
+    return item, o
 
 
 def tau_digest(tau) -> str:
@@ -41,8 +44,8 @@ def tau_digest(tau) -> str:
 
 
 def start(name: str, indices, processes: int | None = None):
-    """Start solving colonies `indices` of workload `name`; returns (pool, pending). pending.get()
-    gives [(index, oracle result)] in the order of `indices`."""
+    """Start solving colonies `indices` of workload `name` (for city_batch: (graph, colony) pairs);
+    returns (pool, pending). pending.get() gives [(index, oracle result)] in the order of `indices`."""
     indices = list(indices)
     n = processes or max(1, min(len(indices), os.cpu_count() or 1))
     pool = mp.get_context("spawn").Pool(n, initializer=_init, initargs=(name,))

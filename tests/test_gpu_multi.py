@@ -1,11 +1,13 @@
 """Many road graphs in one launch: every colony of every graph equals its graph's batch launched alone,
-and a sample equals the oracle bit for bit."""
+and a sample equals the oracle bit for bit; at full size (64 city graphs), every colony of one graph per
+size bucket equals the oracle."""
 import dataclasses
 
 import numpy as np
 import pytest
 
 from paper_2010_14244_gb300 import workloads as W
+from tests import oracle_pool
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +62,49 @@ def test_city_batch_one_launch(gm, orc):
         m.close()
         for c in ctxs:
             c.close()
+
+
+def test_city_batch_full_size(gm):
+    """The 64-graph workload (1.1k-198k nodes, 2268 colonies of 128-1024 ants, 50 iterations) in one
+    launch. In each size bucket of node counts (1k-4k, 4k-16k, 16k-64k, 64k-200k) the first graph has
+    every colony re-solved by the oracle, and each must agree bit for bit, final pheromone table included.
+    Every route of every graph is valid."""
+    cities = W.city_batch()
+    ns = [wl.net.n_nodes for wl in cities]
+    edges = [1000, 4000, 16000, 64000, 200001]
+    pick = [next(g for g in range(len(cities)) if lo <= ns[g] < hi) for lo, hi in zip(edges[:-1], edges[1:])]
+    items = [(g, qi) for g in pick for qi in range(len(cities[g].queries))]
+    pool, pending = oracle_pool.start("city_batch", items)
+    ctxs = []
+    m = gm.Multi(0)
+    try:
+        for wl in cities:
+            c = gm.Context(0)
+            c.load_workload(wl)
+            ctxs.append(c)
+        res = m.solve(ctxs, [wl.queries for wl in cities])
+        digests = {(g, qi): oracle_pool.tau_digest(ctxs[g].pheromone(qi)) for g, qi in items}
+        for wl, rs in zip(cities, res):
+            assert len(rs) == len(wl.queries)
+            for q, r in zip(wl.queries, rs):
+                assert r["ant_steps"] > 0 and r["status"] in (0, gm.ERR_NO_ROUTE)
+                if r["status"] != 0:
+                    continue
+                route = r["route"]
+                assert route[0] == q.src and route[-1] == q.dst and len(set(route.tolist())) == len(route)
+                for a, b in zip(route[:-1], route[1:]):
+                    assert b in wl.net.col[wl.net.row_ptr[a]:wl.net.row_ptr[a + 1]]
+        oracle = pending.get(timeout=3000)
+    finally:
+        pool.close()
+        pool.join()
+        m.close()
+        for c in ctxs:
+            c.close()
+    assert [it for it, _ in oracle] == items
+    for (g, qi), o in oracle:
+        oracle_pool.check(res[g][qi], o)
+        assert digests[(g, qi)] == o["tau_sha256"], (g, qi)
 
 
 def test_multi_refuses(gm):
