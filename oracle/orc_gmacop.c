@@ -23,12 +23,21 @@
  *   orc_score_frac        pinned: error bound against double-precision powers, chi-square frequencies
  *   orc_exact_heuristic   pinned: scipy's Dijkstra on the reversed graph, brute force over simple paths,
  *                         the clamp for nodes that cannot reach the destination
+ *   orc_queue_preempt     pinned: a hand-built junction on both sides of the 3/4-storage threshold
+ *   orc_heuristic_ms      pinned: hand-worked straight-line bounds
  *   orc_quantize          pinned: exact rational arithmetic (Python fractions)
+ *   orc_roulette_pick     pinned: hand-worked picks, 128-bit products, chi-square frequencies
+ *   orc_rho_fix, orc_evaporate  pinned: hand-worked values, tau never below 1
+ *   orc_init_tau          pinned: word 0 of the Philox block keyed by the road, its range
  *   orc_walk_one          pinned: hand-worked single-ant steps, chi-square frequency checks
  *   orc_solve             pinned: Dijkstra / time-dependent Dijkstra / brute-force simple-path
  *                         enumeration on tiny graphs, route validity, pheromone conservation identity,
- *                         closed forms of the unit-deposit / unused-only-evaporation variant;
- *                         the best route on large graphs is parity-unpinned (a metaheuristic optimum)
+ *                         closed forms of the unit-deposit / unused-only-evaporation variant, the step
+ *                         and time caps; the best route on large graphs is parity-unpinned (a
+ *                         metaheuristic optimum)
+ *   orc_tick              pinned: a hand-worked junction, a millisecond simulation of the programme,
+ *                         conservation of vehicles, sinks, red-time growth and saturation
+ * A test plants 53 single mistakes in copies of this file; each fails the pins of the part it changes.
  */
 #include <float.h>
 #include <math.h>
