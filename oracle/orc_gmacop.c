@@ -37,7 +37,7 @@
  *                         metaheuristic optimum)
  *   orc_tick              pinned: a hand-worked junction, a millisecond simulation of the programme,
  *                         conservation of vehicles, sinks, red-time growth and saturation
- * A test plants 53 single mistakes in copies of this file; each fails the pins of the part it changes.
+ * A test plants 67 single mistakes in copies of this file; each fails the pins of the part it changes.
  */
 #include <float.h>
 #include <math.h>

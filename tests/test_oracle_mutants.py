@@ -8,6 +8,8 @@ Not planted, because each is equivalent to the original and no test can tell the
 - `key < best_key` against `key <= best_key` in the best-route rule: keys (T, iteration, ant) are unique;
 - a default step cap of N instead of N - 1: a walk that has taken N - 1 roads on distinct nodes stands
   on the destination, so the cap of N - 1 never binds (the 4096 ceiling does, and is planted).
+- dropping the per-iteration queue update of a solve: densities and red times are fixed during a solve,
+  so it recomputes the order it already holds.
 """
 import concurrent.futures as cf
 import os
@@ -27,6 +29,7 @@ MUTANTS = [
     ("philox_multiplier", "M0 = 0xD2511F53u", "M0 = 0xD2511F55u", [PRIM]),
     ("philox_key_schedule", "k1 += W1;", "k1 += W0;", [PRIM]),
     ("philox_word_swap", "uint32_t y0 = hi1 ^ x1 ^ k0;", "uint32_t y0 = hi1 ^ x1 ^ k1;", [PRIM]),
+    ("philox_key_bump_first", "if (round > 0) {", "if (round >= 0) {", [PRIM]),
     ("draw_counter_order", "uint32_t c[4] = {it, ant, step, stream};", "uint32_t c[4] = {ant, it, step, stream};",
      [SOLVE]),
     # road attributes and the straight-line bound
@@ -45,6 +48,12 @@ MUTANTS = [
      [PRIM]),
     ("starvation_not_strict", "if (red_ms[p] > T_max)", "if (red_ms[p] >= T_max)", [PRIM, TICK]),
     ("empty_phases_not_last", "if (!used[p] && Q[p] > 0) {", "if (!used[p]) {", [PRIM]),
+    ("starved_shortest_first", "red_ms[p] > T_max && (best < 0 || red_ms[p] > red_ms[best])",
+     "red_ms[p] > T_max && (best < 0 || red_ms[p] < red_ms[best])", [PRIM]),
+    ("longest_queue_tie_high", "if (Q[p] > 0 && (best < 0 || Q[p] > Q[best]))", "if (Q[p] > 0 && (best < 0 || Q[p] >= Q[best]))",
+     [PRIM]),
+    ("wait_wraps_wrongly", "return (uint32_t)((start + cycle - c) % cycle);", "return (uint32_t)((start + cycle - c - 1) % cycle);",
+     [PRIM]),
     ("green_window_end", "if (c >= start && c < start + green[phase])", "if (c >= start && c <= start + green[phase])",
      [PRIM]),
     ("signal_offset_sign", "(arr_ms % cycle + cycle - (offset % cycle)) % cycle", "(arr_ms % cycle + (offset % cycle)) % cycle",
@@ -68,6 +77,17 @@ MUTANTS = [
     ("tie_rule_ant_major", "| ((uint64_t)it * q->n_ants + k);", "| ((uint64_t)k * q->n_iter + it);", [SOLVE]),
     ("beta_fraction_ignored", "*frac = floorf(q->alpha) != q->alpha || floorf(q->beta) != q->beta;",
      "*frac = floorf(q->alpha) != q->alpha;", [FRAC]),
+    ("visited_not_marked", "S->visited[u] = 1;\n        route_edges", "route_edges", [SOLVE]),
+    ("draw_words_swapped", "return (uint64_t)o[0] | ((uint64_t)o[1] << 32);", "return (uint64_t)o[1] | ((uint64_t)o[0] << 32);",
+     [PRIM, SOLVE]),
+    ("best_wait_is_time", "best_W = W;", "best_W = T;", [SOLVE]),
+    ("no_score_saturation", "if (p > FLT_MAX)", "if (0)", [LIT]),
+    ("weight_floor_dropped", "w[i] = q < 1 ? 1 : q;", "w[i] = q;", [PRIM]),
+    ("zero_scores_zero_weights", "            w[i] = 1;", "            w[i] = 0;", [PRIM]),
+    ("heuristic_scale_shift", "uint64_t h = (orc_isqrt64(d2) * kappa) >> 16;", "uint64_t h = (orc_isqrt64(d2) * kappa) >> 15;",
+     [PRIM]),
+    ("frac_cost_plus_one", "float B = beta * orc_log2((float)c_ms);", "float B = beta * orc_log2((float)c_ms + 1.0f);",
+     [FRAC]),
     # pheromone: initial value, evaporation, deposits
     ("random_tau_word", "tau[e] = ((uint64_t)1 << 31) + o[0];", "tau[e] = ((uint64_t)1 << 31) + o[1];", [PRIM]),
     ("rho_fix_scale", "ldexp((double)rho, 32)", "ldexp((double)rho, 31)", [PRIM, SOLVE]),
@@ -76,6 +96,8 @@ MUTANTS = [
     ("deposit_numerator", "(uint64_t)(S.h[q->src] > 0 ? S.h[q->src] : 1u) << 32",
      "(uint64_t)(S.h[q->src] > 0 ? S.h[q->src] : 1u) << 31", [SOLVE]),
     ("deposit_denominator", "dep_num / T;", "dep_num / (T + 1);", [SOLVE]),
+    ("deposit_before_evaporation", "tau[e] = orc_evaporate(tau[e], rho_fix) + D[e];",
+     "tau[e] = orc_evaporate(tau[e] + D[e], rho_fix);", [SOLVE]),
     # the paper-literal variant
     ("repulsive_not_reciprocal", "return (flags & ORC_FLAG_REPULSIVE) ? 1.0f / tf : tf;", "return tf;", [LIT]),
     ("unit_deposit_half", "uint64_t delta = unit ? (uint64_t)1 << 32", "uint64_t delta = unit ? (uint64_t)1 << 31", [LIT]),
@@ -95,6 +117,8 @@ MUTANTS = [
     ("tick_split_remainder", "(j < K[u] % d ? 1u : 0u)", "(j + 1 < K[u] % d ? 1u : 0u)", [TICK]),
     ("tick_red_empty_phase", "p == gph[v] || Q[i] == 0)", "p == gph[v])", [TICK]),
     ("tick_red_wraps", "r > 0xFFFFFFFFu - dt ? 0xFFFFFFFFu : r + dt", "r + dt", [TICK]),
+    ("tick_arrivals_lost", "veh_out[e] = (uint32_t)(g->vehicles[e] - leave[e] + in);",
+     "veh_out[e] = (uint32_t)(g->vehicles[e] - leave[e]);", [TICK]),
     ("tick_green_window_end", "c < start + green[p])", "c <= start + green[p])", [TICK]),
     ("red_time_phase_index", "g->red_ms[(size_t)v * ORC_MAX_PHASES + p]", "g->red_ms[(size_t)v * ORC_MAX_PHASES]",
      [PRIM, TICK]),
