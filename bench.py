@@ -522,7 +522,9 @@ def run_gpu(args, rank, world, local_rank):
                      "bytes_per_ant_step": bytes_per_step,
                      "time": "job device time (construction launches of concurrent chains overlap)",
                      "construct_launches_per_job": construct_launches,
-                     "avg_launch_ms_summed_over_chains": kt["construct"] / (K * max(construct_launches, 1))},
+                     "avg_launch_ms_summed_over_chains": kt["construct"] / (K * max(construct_launches, 1)),
+                     "binding_limit": "the dependent step chain of the slowest colony (critical_path), not HBM: "
+                                      "the graph and pheromone tables are L2-resident"},
         "critical_path": critical,
         "gpu_launches": launches * K,
         "clocks": clocks,
