@@ -137,3 +137,40 @@ def test_generators_are_deterministic(make):
         np.testing.assert_array_equal(getattr(a.signals, f), getattr(b.signals, f))
     np.testing.assert_array_equal(a.vehicles, b.vehicles)
     assert a.queries == b.queries
+
+
+def test_city_batch_recipe():
+    """64 independent city graphs: node counts log-uniform in [1k, 200k] from the same planar generator,
+    60 % signalised, mean density U[0.5, 3] vehicles per road, 8-64 uniform OD queries of 128-1024 ants."""
+    cities = W.city_batch()
+    assert len(cities) == 64
+    ns = np.array([wl.net.n_nodes for wl in cities])
+    assert ns.min() >= 900 and ns.max() <= 200_000
+    logs = np.log(ns)
+    assert logs.std() > 0.8  # spread over the decades, not clustered
+    for wl in cities:
+        net = wl.net
+        _csr_ok(net)
+        assert abs(net.n_edges / net.n_nodes - 2.8) < 0.05
+        assert 8 <= len(wl.queries) <= 64
+        assert all(128 <= q.n_ants <= 1024 and q.n_iter == 50 and q.src != q.dst for q in wl.queries)
+        assert 0.4 <= float(wl.vehicles.mean()) <= 3.2
+        frac = np.count_nonzero(wl.signals.n_phases) / net.n_nodes
+        assert abs(frac - 0.6) < 0.08
+    assert sum(len(wl.queries) for wl in cities) == 2268
+
+
+def test_serving_requests():
+    """Uniform OD requests, src != dst, 128 ants x 30 iterations; request i's seed is
+    1,000,003 * i + the stream seed, so every request has its own Philox key."""
+    from paper_2010_14244_gb300 import serving
+
+    make = serving.uniform_requests(1000, 128, 30, seed=5)
+    qs = [make(i) for i in range(4000)]
+    assert all(q.src != q.dst and 0 <= q.src < 1000 and 0 <= q.dst < 1000 for q in qs)
+    assert all((q.n_ants, q.n_iter, q.alpha, q.beta, q.rho) == (128, 30, 1.0, 2.0, 0.1) for q in qs)
+    assert [q.seed for q in qs[:3]] == [5, 1_000_008, 2_000_011]
+    counts = np.bincount([q.src for q in qs], minlength=1000)
+    assert counts.max() < 16  # uniform: about 4 per node
+    again = serving.uniform_requests(1000, 128, 30, seed=5)
+    assert [again(i) for i in range(50)] == qs[:50]
