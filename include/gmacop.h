@@ -154,7 +154,10 @@ int gmp_load_graph(gmp_ctx *ctx, uint32_t n_nodes, uint32_t n_edges, const uint3
 int gmp_set_signals(gmp_ctx *ctx, const uint8_t *n_phases, const uint32_t *cycle_ms, const uint32_t *offset_ms,
                     const uint32_t *green_ms, const uint8_t *edge_phase);
 
-/* Red-time accumulators t_p of Fig. 3 ("waiting time of vehicle at phase"), N*8 entries in ms. */
+/* Red-time accumulators t_p of Fig. 3 (how long each phase's vehicles have waited), host array of N*8
+ * entries in ms (node*8 + phase; entries at or above a node's phase count do not enter the order), copied by the
+ * call. Recomputes the phase order on the device. Synchronous. Errors: INVALID_ARG, STATE (no graph),
+ * CUDA. */
 int gmp_set_red_times(gmp_ctx *ctx, const uint32_t *red_ms);
 
 /* Vehicles currently on each road (Sec. 4.2: densities from road sensors; Calc_Dens). Recomputes edge
@@ -162,7 +165,9 @@ int gmp_set_red_times(gmp_ctx *ctx, const uint32_t *red_ms);
  * Errors: STATE, CUDA. */
 int gmp_set_densities(gmp_ctx *ctx, const uint32_t *vehicles);
 
-/* Same from device memory (E entries), asynchronous on the context's stream. */
+/* Same from device memory (E entries of the context's GPU), asynchronous on the context's stream: the
+ * caller keeps d_vehicles unchanged until that stream has passed the call. Errors: INVALID_ARG, STATE,
+ * CUDA. */
 int gmp_set_densities_async(gmp_ctx *ctx, const uint32_t *d_vehicles);
 
 /* Read back the vehicles on each road (host array of E entries) and the red-time accumulators (host
@@ -327,9 +332,13 @@ int gmp_solve(gmp_ctx *ctx, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_
 int gmp_solve_batch(gmp_ctx *ctx, uint32_t n, const gmp_query *queries, gmp_result *results);
 
 /* The three phases of gmp_solve_batch, for callers that keep inputs and outputs on the device:
- *   gmp_batch_stage   validates and uploads n queries, reserves the device workspace (synchronous);
- *   gmp_batch_launch  issues the whole job on the stream and returns (no host synchronisation, no copies);
- *   gmp_batch_collect waits for the job and copies results[0..n) back (routes into caller buffers).
+ *   gmp_batch_stage   validates and uploads n queries (host array, copied), reserves the device
+ *                     workspace (synchronous). Errors: INVALID_ARG, UNSUPPORTED, STATE, OOM, CUDA;
+ *   gmp_batch_launch  issues the whole job on the stream and returns (no host synchronisation, no copies).
+ *                     Errors: INVALID_ARG, STATE (nothing staged), CUDA;
+ *   gmp_batch_collect waits for the job and copies results[0..n) back (host array of n; routes into the
+ *                     buffers each result names). Errors: INVALID_ARG, STATE (nothing launched), TIMEOUT
+ *                     (a bounded device wait expired), CUDA.
  * gmp_batch_launch may be called repeatedly on a staged batch; every launch starts from fresh pheromone. */
 int gmp_batch_stage(gmp_ctx *ctx, uint32_t n, const gmp_query *queries);
 int gmp_batch_launch(gmp_ctx *ctx);
@@ -347,24 +356,30 @@ int gmp_batch_reserve(gmp_ctx *ctx, uint32_t n, uint64_t total_ants, uint32_t ma
  * Errors: INVALID_ARG, STATE (nothing launched), CUDA (the job failed). */
 int gmp_batch_ready(gmp_ctx *ctx, int *ready);
 
-/* Pheromone of query `slot` of the last batch after its final iteration: E entries, Q32.32. */
+/* Pheromone of query `slot` of the last batch after its final iteration: host array of E entries, Q32.32
+ * (rebuilt from the baseline and the registered roads in the sparse layout). Synchronous.
+ * Errors: INVALID_ARG (slot out of range), STATE (no batch ran), OOM, CUDA. */
 int gmp_get_pheromone(gmp_ctx *ctx, uint32_t slot, uint64_t *out_tau);
 
 /* Per-(iteration, ant) log of query `slot` (needs GMP_FLAG_ANT_LOG when the batch ran):
- * n_iter*n_ants*4 entries {status, steps, T, W}; status 0 success, 1 dead end, 2 step cap, 3 time cap. */
+ * n_iter*n_ants*4 entries {status, steps, T, W}; status 0 success, 1 dead end, 2 step cap, 3 time cap.
+ * Host array of capacity_entries. Errors: INVALID_ARG, STATE (no log), BUFFER (capacity too small), CUDA. */
 int gmp_get_ant_log(gmp_ctx *ctx, uint32_t slot, uint32_t *out, uint64_t capacity_entries);
 
-/* Current per-node phase order (N*8 entries; positions >= n_phases hold p) -- the preemptive plan. */
+/* Current per-node phase order (host array of N*8 entries; positions >= n_phases hold p) -- the
+ * preemptive plan. Synchronous. Errors: INVALID_ARG, STATE (no graph), CUDA. */
 int gmp_get_phase_order(gmp_ctx *ctx, uint8_t *out);
 
-/* Current congested travel time and queue delay per road (E entries each; either may be NULL). */
+/* Current congested travel time and queue delay per road (host arrays of E entries each; either may be
+ * NULL). Synchronous. Errors: INVALID_ARG, STATE (no graph), CUDA. */
 int gmp_get_edge_times(gmp_ctx *ctx, uint32_t *tt_ms, uint32_t *qd_ms);
 
 /* Device time of the last launched job (staged with the per-kernel timing flag), in ms: out[0] construction,
  * out[1] iteration end (evaporation + deposit, best-route tracking and queue/preemption in one kernel),
  * both summed over the concurrent colony chains (which overlap in time), out[2] initialisation + result
  * rows, out[3] 0, out[4] whole job. In the persistent job everything but initialisation and the result
- * rows is one kernel, reported as out[0]. Needs the stream idle. */
+ * rows is one kernel, reported as out[0]. Waits for the stream. Errors: INVALID_ARG, STATE (no job staged with
+ * the timing flag has run), CUDA. */
 int gmp_get_kernel_times(gmp_ctx *ctx, float *out_ms5);
 
 /* Count of kernel launches issued by the last gmp_batch_launch. */
