@@ -5,8 +5,9 @@
  * Smart Transportation"): ants build origin-to-destination routes over a road graph by choosing the next
  * road from pheromone and a congestion/signal-aware travel-time heuristic (Sec. 4.1, Fig. 3), successful
  * ants deposit pheromone and all roads evaporate (Fig. 3; Algorithm 2), and each signalised
- * intersection reorders its phases by the preemptive rule (Fig. 3 signal block; Algorithm 2). Algorithm 1 (allocate, copy in, launch, copy out, free) is the host driver this API replaces
- * with persistent device state: the graph, signals and densities stay resident between calls.
+ * intersection reorders its phases by the preemptive rule (Fig. 3 signal block; Algorithm 2).
+ * Algorithm 1 (allocate, copy in, launch, copy out, free) is the host driver this API replaces with
+ * persistent device state: the graph, signals and densities stay resident between calls.
  *
  * Conventions for every entry point:
  *   - Return value: GMP_OK (0) or a GMP_ERR_* code; gmp_strerror() names it, gmp_last_error() gives the
