@@ -138,7 +138,7 @@ int gmp_set_stream(gmp_ctx *ctx, void *cuda_stream);
  * this GPU), STATE (the context already holds device memory). */
 int gmp_bind_workspace(gmp_ctx *ctx, void *dev_ptr, uint64_t bytes);
 
-/* Road graph G(N, E) (Fig. 3 "G(N,E) = graph"; Sec. 5: roads with lanes) in CSR form: the roads leaving
+/* Road graph G(N, E) (the graph of Fig. 3; Sec. 5: roads with lanes) in CSR form: the roads leaving
  * node u are row_ptr[u] .. row_ptr[u+1]-1, in the order that breaks ties between equal choices.
  * col[e]: head node; length_dm[e] >= 1; speed_kmh[e] >= 1; lanes[e] >= 1; x_dm, y_dm: node coordinates,
  * |x|, |y| <= 2^27. Derives free-flow times and jam capacities on the device. Replaces any previous graph
@@ -147,7 +147,7 @@ int gmp_load_graph(gmp_ctx *ctx, uint32_t n_nodes, uint32_t n_edges, const uint3
                    const uint32_t *length_dm, const uint16_t *speed_kmh, const uint8_t *lanes, const int32_t *x_dm,
                    const int32_t *y_dm);
 
-/* Fixed-time signal programmes (Fig. 3 "L: Light, P: Phase"; Algorithm 1 arguments traffic_light, phases).
+/* Fixed-time signal programmes (the lights and phases of Fig. 3; Algorithm 1 arguments traffic_light, phases).
  * Per node v: n_phases[v] in 0..8 (0 = unsignalised), cycle_ms[v] in 1..2^24-1, offset_ms[v] < cycle,
  * green_ms[v*8 + p] >= 1 for p < n_phases with sum == cycle. edge_phase[e]: approach phase of road e at
  * its head (< n_phases of the head when signalised). Resets the red-time accumulators to 0 and recomputes

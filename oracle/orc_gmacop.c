@@ -368,7 +368,7 @@ uint32_t orc_heuristic_ms(int32_t x, int32_t y, int32_t xd, int32_t yd, uint64_t
 }
 
 /* ------------------------------------------------------------------------------------------------ */
-/* Next-node rule (Fig. 3 "select node"; Algorithm 2): roulette over tau^alpha * eta^beta.     */
+/* Next-node rule (Fig. 3's node selection; Algorithm 2): roulette over tau^alpha * eta^beta.   */
 /* ------------------------------------------------------------------------------------------------ */
 static float pow_int(float x, uint32_t k)
 {
@@ -791,7 +791,7 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
         for (uint32_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; ++e)
             if (!S->visited[g->col[e]])
                 S->cand[n++] = e;
-        /* congestion threshold (Fig. 3 "if N_t > threshold"): congested roads drop out unless all are */
+        /* congestion threshold (Fig. 3's test of N_t): congested roads drop out unless all are */
         if (S->thr != ORC_THR_OFF && n > 0) {
             uint32_t n_ok = 0;
             for (uint32_t i = 0; i < n; ++i) {

@@ -1,7 +1,7 @@
 """Vehicle-level MACO-P loop (Fig. 3 over n vehicles) on top of the colony and the serving tick.
 
 Every vehicle is either at a node, waiting to choose its next road, or between two nodes on a road it
-has chosen (Fig. 3's "in between the nodes": it keeps going to that road's head). Time advances in steps
+has chosen (Fig. 3's vehicle between two nodes: it keeps going to that road's head). Time advances in steps
 of dt (1 s). Per step at clock t:
 
   1. the roads' vehicle counts are the simulated vehicles on them (the traffic this experiment studies);
