@@ -151,6 +151,24 @@ def test_grid10_route_validity_and_recomputed_times(orc):
     _check_route(orc, wl.net, wl.signals, onet, r2, q, p)
 
 
+def test_grid64_full_size_best_routes_valid_and_bounded(orc):
+    """Properties that hold at any size, on two benchmark colonies at full size (1024 ants x 200
+    iterations; colony 11 has the job's longest walks): the best route is a simple path from src to dst
+    along roads; its travel and wait times, recomputed road by road from the pinned primitives, equal
+    the reported ones; and it is no faster than the time-dependent Dijkstra optimum (waits are FIFO, so
+    that optimum is exact)."""
+    wl = W.grid64()
+    onet = orc.Net.from_workload(wl)
+    for qi in (0, 11):
+        q = wl.queries[qi]
+        r = orc.solve(onet, orc.Params(), q, want_tau=False)
+        assert r["status"] == 0 and r["n_success"] > 0
+        _check_route(orc, wl.net, wl.signals, onet, r, q)
+        timing = NB.Timing(orc, onet, wl.net, wl.signals, q.dst)
+        opt = NB.td_dijkstra(wl.net, timing, q.src, q.dst)
+        assert opt is not None and r["travel_ms"] >= opt
+
+
 def _deposit(h_src, T):
     return (max(h_src, 1) << 32) // T
 
