@@ -18,15 +18,21 @@ from .workloads import Query
 
 def make_server(wl, n_slots: int, max_batch: int, max_ants: int, max_iter: int, mem_budget: int = 0,
                 device: int = 0, params: dict | None = None):
-    """Slot contexts holding replicas of the workload's traffic state, and a server over them."""
+    """Slot contexts holding replicas of the workload's traffic state, and a server over them. On any
+    failure the contexts created so far are closed before the error propagates."""
     slots = []
-    for _ in range(n_slots):
-        c = G.Context(device, mem_budget)
-        c.load_workload(wl)
-        if params:
-            c.set_params(**params)
-        slots.append(c)
-    return G.Server(slots, max_batch, max_ants, max_iter), slots
+    try:
+        for _ in range(n_slots):
+            c = G.Context(device, mem_budget)
+            slots.append(c)
+            c.load_workload(wl)
+            if params:
+                c.set_params(**params)
+        return G.Server(slots, max_batch, max_ants, max_iter), slots
+    except Exception:
+        for c in slots:
+            c.close()
+        raise
 
 
 @dataclass
