@@ -406,7 +406,9 @@ typedef struct {
  * the call returns without waiting; synchronise that stream before reading the outputs. The first call
  * on a device looks the array's address up, so make it before any stream capture. Every call reuses the
  * same array (which keeps the previous call's data; each call re-initialises what it needs), so calls
- * that overlap on the GPU race. The colony runs like gmp_solve (same results, the ant log excepted).
+ * that overlap on the GPU race. The colony runs like gmp_solve (same results, the ant log excepted),
+ * always in the dense pheromone layout (both layouts give the same results, so tau_layout is not read),
+ * in warp lockstep unless the context's parameters turn lockstep off.
  * Errors: INVALID_ARG, UNSUPPORTED, STATE, CUDA; BUFFER when route_cap is short or when the colony's
  * temporaries (about 24 bytes per road plus 4 * n_ants * max_steps bytes) exceed the array. */
 int gmp_solve_static(gmp_ctx *ctx, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha,

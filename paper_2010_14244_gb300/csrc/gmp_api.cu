@@ -15,6 +15,7 @@
 #include <string>
 #include <iterator>
 #include <map>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -1699,7 +1700,11 @@ namespace {
 static __device__ __align__(256) unsigned char g_static_scratch[GMP_STATIC_SCRATCH_BYTES];
 
 constexpr int kStaticMaxDevices = 64;
+// Device address of the array on each device, looked up once per device (call_once keeps two host
+// threads making their first call on a device at the same time from racing on the entry).
 void* g_static_ptr[kStaticMaxDevices] = {nullptr};
+std::once_flag g_static_once[kStaticMaxDevices];
+cudaError_t g_static_err[kStaticMaxDevices] = {};
 
 __global__ void k_static_query(DevQuery q, DevQuery* __restrict__ dq, uint32_t* __restrict__ prefix) {
     dq[0] = q;
@@ -1735,16 +1740,17 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     if ((uint32_t)construct_max_degree(lanes) < c->maxdeg || c->maxdeg > 128u || lanes == 1)
         return fail(c, GMP_ERR_UNSUPPORTED, "out-degree %u is beyond the static solve's kernels", c->maxdeg);
     GMP_CUDA(c, cudaSetDevice(c->device));
-    if (!g_static_ptr[c->device]) {  // first call on this device: where the scratch array lives
+    std::call_once(g_static_once[c->device], [&] {  // first call on this device: where the array lives
         void* p = nullptr;
-        GMP_CUDA(c, cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_err[c->device] = cudaGetSymbolAddress(&p, g_static_scratch);
         g_static_ptr[c->device] = p;
-    }
+    });
+    GMP_CUDA(c, g_static_err[c->device]);
     const uint32_t S = std::max<uint32_t>(default_max_steps(c), 1u);
     if (route_cap < S + 1u)
         return fail(c, GMP_ERR_BUFFER, "route buffer needs %u entries (max_steps + 1)", S + 1u);
     KernelConfig kc{};
-    if (lanes <= 16 && c->maxdeg <= (uint32_t)(2 * lanes) && lanes * (c->maxdeg <= (uint32_t)lanes ? 1 : 2) <= 16)
+    if (!(c->prm.flags & kFlagNoLockstep) && lockstep_fits(lanes, c->maxdeg))
         GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, n_ants,
                                               floorf(alpha) != alpha || floorf(beta) != beta, &kc));
     else
@@ -1829,6 +1835,10 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
         GMP_CUDA(c, launch_construct(s, kc, a, it));
         e.it = it;
         GMP_CUDA(c, launch_iter_end(s, e));
+        if (c->max_phases > 2)  // the iteration end updated the intersections with <= 2 phases only
+            GMP_CUDA(c, launch_queue_preempt(s, c->N, 3u, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle,
+                                             c->offset, c->green, c->ephase, c->veh, c->cap, c->red, c->order,
+                                             c->rec));
     }
     GMP_CUDA(c, launch_finalize(s, 1, dq, qs, best_route, c->col, S, reinterpret_cast<DevResult*>(d_result), d_route));
     return GMP_OK;
