@@ -94,7 +94,7 @@ def lib():
             "orc_evaporate": (u64, [u64, u64]),
             "orc_init_tau": (None, [u32, u64, u32, vp]),
             "orc_prepare": (C.c_int, [vp, vp, u32, vp, vp, vp, vp, vp, vp]),
-            "orc_walk_one": (C.c_int, [vp, vp, vp, vp, u32, u32, vp, vp, vp, vp]),
+            "orc_walk_one": (C.c_int, [vp, vp, vp, vp, u32, u32, vp, vp, vp, vp, vp]),
             "orc_solve": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp]),
             "orc_tick": (C.c_int, [vp, vp, u64, u32, vp, vp, vp, vp]),
         }
@@ -291,15 +291,24 @@ def tick(net: Net, params: Params, t_now: int, dt: int, order):
 
 
 def walk_one(net: Net, params: Params, query, tau, it=0, ant=0):
+    """One ant: its status, route (roads; ``steps`` of them), moves (forward and back), T and W."""
     tau = np.ascontiguousarray(tau, np.uint64)
-    route = np.zeros(max(net.n_nodes, 1), np.uint32)
-    steps, T, W = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    route = np.zeros(max(2 * net.n_nodes, params.max_steps, 4096) + 1, np.uint32)  # >= the move cap
+    steps, moves, T, W = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint32()
     pr, q = params.c(), _query(query)
     st = lib().orc_walk_one(C.addressof(net.c), C.addressof(pr), C.addressof(q), _p(tau), it, ant, _p(route),
-                            C.byref(steps), C.byref(T), C.byref(W))
+                            C.byref(steps), C.byref(moves), C.byref(T), C.byref(W))
     if st < 0:
         raise ValueError(f"orc_walk_one rejected the query: {-st}")
-    return dict(status=st, route_edges=route[: steps.value].copy(), steps=steps.value, T=T.value, W=W.value)
+    return dict(status=st, route_edges=route[: steps.value].copy(), steps=steps.value, moves=moves.value, T=T.value,
+                W=W.value)
+
+
+def log_fields(log):
+    """Split an ant log (..., 4) into (status, roads in the route, moves, T, W) arrays."""
+    log = np.asarray(log)
+    w0 = log[..., 0].astype(np.uint32)
+    return w0 & 0xFF, w0 >> 8, log[..., 1], log[..., 2], log[..., 3]
 
 
 def solve(net: Net, params: Params, query, route_cap=None, want_tau=True, want_log=False) -> dict:

@@ -29,7 +29,8 @@
  *   orc_roulette_pick     pinned: hand-worked picks, 128-bit products, chi-square frequencies
  *   orc_rho_fix, orc_evaporate  pinned: hand-worked values, tau never below 1
  *   orc_init_tau          pinned: word 0 of the Philox block keyed by the road, its range
- *   orc_walk_one          pinned: hand-worked single-ant steps, chi-square frequency checks
+ *   orc_walk_one          pinned: hand-worked single-ant steps and steps back at dead ends, chi-square
+ *                         frequency checks
  *   orc_solve             pinned: Dijkstra / time-dependent Dijkstra / brute-force simple-path
  *                         enumeration on tiny graphs, route validity, pheromone conservation identity,
  *                         closed forms of the unit-deposit / unused-only-evaporation variant, the step
@@ -84,7 +85,7 @@ typedef struct {
 } orc_net;
 
 typedef struct {
-    uint32_t max_steps;    /* 0 = min(N-1, 4096) */
+    uint32_t max_steps;    /* moves per ant (forward and back); 0 = min(2(N-1), 4096) */
     uint32_t h_sat_ms;     /* 0 = 2000 ms saturation headway */
     uint32_t thr_permille; /* occupancy threshold in vehicles per 1000 capacity; 0xFFFFFFFF = off */
     uint32_t flags;        /* ORC_FLAG_* */
@@ -687,6 +688,7 @@ typedef struct {
     float *score;
     uint32_t *waitv;
     uint64_t *w;
+    uint32_t *wait_at; /* wait taken at each position of the current route */
 } orc_state;
 
 static void state_free(orc_state *S)
@@ -702,6 +704,7 @@ static void state_free(orc_state *S)
     free(S->score);
     free(S->waitv);
     free(S->w);
+    free(S->wait_at);
 }
 
 static int state_init(orc_state *S, const orc_net *g, const orc_params *prm, uint32_t dst)
@@ -757,23 +760,37 @@ static int state_init(orc_state *S, const orc_net *g, const orc_params *prm, uin
         state_free(S);
         return rc;
     }
-    uint32_t def_steps = N - 1 < 4096u ? N - 1 : 4096u;
+    /* a depth-first walk reaches every node it can reach, and returns, within 2(N-1) moves */
+    uint64_t two_n = 2ull * (N - 1u);
+    uint32_t def_steps = two_n < 4096u ? (uint32_t)two_n : 4096u;
     S->max_steps = (prm && prm->max_steps) ? prm->max_steps : def_steps;
     S->thr = prm ? prm->thr_permille : ORC_THR_OFF;
     S->t_dep = prm ? prm->t_dep_ms : 0u;
     S->flags = prm ? prm->flags : 0u;
+    /* a route never has more roads than moves were made (nor, being a simple path, more than N - 1) */
+    S->wait_at = malloc(sizeof(uint32_t) * ((size_t)S->max_steps + 1));
+    if (!S->wait_at) {
+        state_free(S);
+        return ORC_ERR_OOM;
+    }
     return ORC_OK;
 }
 
-/* One ant of iteration `it`: builds a simple path from src (Fig. 3 body for one vehicle, with the
- * roulette next-node rule). Writes the roads taken to route_edges; returns the ant status. */
+/* One ant of iteration `it` (Fig. 3 body for one vehicle, with the roulette next-node rule). The ant keeps
+ * a visited set, so its route is a simple path. At a node where no road leads to an unvisited node it
+ * steps back along its route to the previous node: that node's elapsed time and wait come back, the node
+ * it left stays visited, and the step back counts as a move. It fails when it is back at src with no
+ * road left, after max_steps moves, or when its elapsed time exceeds 2^30 ms. The draw of a forward move
+ * is keyed by the move's index. A road's cost is the time it adds over the remaining lower bound:
+ * c = tt + wait + h(v) - h(u), at least 1 ms. Writes the route's roads to route_edges; returns the ant
+ * status. */
 static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta, int frac, const uint64_t *tau,
-                uint32_t it, uint32_t ant, uint32_t *route_edges, uint32_t *steps_out, uint32_t *T_out,
-                uint32_t *W_out)
+                uint32_t it, uint32_t ant, uint32_t *route_edges, uint32_t *len_out, uint32_t *moves_out,
+                uint32_t *T_out, uint32_t *W_out)
 {
     const orc_net *g = S->g;
     memset(S->visited, 0, g->n_nodes);
-    uint32_t u = q->src, steps = 0;
+    uint32_t u = q->src, moves = 0, len = 0;
     uint64_t t = 0, W = 0;
     int status;
     S->visited[u] = 1;
@@ -782,7 +799,7 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
             status = ANT_SUCCESS;
             break;
         }
-        if (steps == S->max_steps) {
+        if (moves == S->max_steps) {
             status = ANT_STEP_CAP;
             break;
         }
@@ -810,10 +827,20 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
             }
         }
         if (n == 0) {
-            status = ANT_DEAD_END;
-            break;
+            if (len == 0) {
+                status = ANT_DEAD_END;
+                break;
+            }
+            /* dead end: back to the previous node of the route, with the time and wait it had there */
+            len--;
+            uint32_t e = route_edges[len];
+            t -= (uint64_t)S->tt[e] + S->wait_at[len];
+            W -= S->wait_at[len];
+            u = len ? g->col[route_edges[len - 1]] : q->src;
+            moves++;
+            continue;
         }
-        /* Eval_Rout: travel time, signal wait + queue delay at the head, remaining lower bound */
+        /* Eval_Rout: travel time, signal wait + queue delay at the head, change of the remaining bound */
         for (uint32_t i = 0; i < n; ++i) {
             uint32_t e = S->cand[i], v = g->col[e];
             uint32_t w = 0;
@@ -823,26 +850,30 @@ static int walk(orc_state *S, const orc_query *q, uint32_t alpha, uint32_t beta,
                                        S->order + (size_t)v * ORC_MAX_PHASES, g->n_phases[v], g->edge_phase[e]) +
                     S->qd[e];
             }
-            uint32_t c = S->tt[e] + w + S->h[v];
+            int64_t cost = (int64_t)S->tt[e] + w + S->h[v] - S->h[u];
+            uint32_t c = cost < 1 ? 1u : (uint32_t)cost;
             S->waitv[i] = w;
             S->score[i] = frac ? orc_score_frac(tau[e], q->alpha, c, q->beta, S->flags)
                                : orc_score_f(tau[e], alpha, c, beta, S->flags);
         }
         orc_quantize(n, S->score, S->w);
-        uint32_t pick = orc_roulette_pick(n, S->w, draw64(q->seed, it, ant, steps, 0));
+        uint32_t pick = orc_roulette_pick(n, S->w, draw64(q->seed, it, ant, moves, 0));
         uint32_t e = S->cand[pick];
         /* position update */
         t += (uint64_t)S->tt[e] + S->waitv[pick];
         W += S->waitv[pick];
         u = g->col[e];
         S->visited[u] = 1;
-        route_edges[steps++] = e;
+        S->wait_at[len] = S->waitv[pick];
+        route_edges[len++] = e;
+        moves++;
         if (t > ORC_T_CAP) {
             status = ANT_TIME_CAP;
             break;
         }
     }
-    *steps_out = steps;
+    *len_out = len;
+    *moves_out = moves;
     *T_out = (uint32_t)t;
     *W_out = (uint32_t)W;
     return status;
@@ -890,9 +921,10 @@ int orc_prepare(const orc_net *g, const orc_params *prm, uint32_t dst, uint32_t 
     return ORC_OK;
 }
 
-/* One ant walk against a given pheromone table (for hand-worked tests). */
+/* One ant walk against a given pheromone table (for hand-worked tests): route_edges receives the route
+ * (*len roads), *moves counts its forward moves and steps back. */
 int orc_walk_one(const orc_net *g, const orc_params *prm, const orc_query *q, const uint64_t *tau, uint32_t it,
-                 uint32_t ant, uint32_t *route_edges, uint32_t *steps, uint32_t *T, uint32_t *W)
+                 uint32_t ant, uint32_t *route_edges, uint32_t *len, uint32_t *moves, uint32_t *T, uint32_t *W)
 {
     uint32_t alpha, beta;
     int frac;
@@ -903,7 +935,7 @@ int orc_walk_one(const orc_net *g, const orc_params *prm, const orc_query *q, co
     rc = state_init(&S, g, prm, q->dst);
     if (rc != ORC_OK)
         return -rc;
-    int st = walk(&S, q, alpha, beta, frac, tau, it, ant, route_edges, steps, T, W);
+    int st = walk(&S, q, alpha, beta, frac, tau, it, ant, route_edges, len, moves, T, W);
     state_free(&S);
     return st;
 }
@@ -933,7 +965,8 @@ void orc_init_tau(uint32_t E, uint64_t seed, uint32_t flags, uint64_t *tau)
  * (Updt_Pher before Evap_Pher, which decrements unused roads); ORC_FLAG_REPULSIVE acts in the walk.
  * route_nodes receives the best route (min T, then lowest (iteration, ant)) as node ids, src first.
  * tau_out (E entries, may be NULL) receives the final pheromone. ant_log (may be NULL) receives per
- * (iteration, ant) {status, steps, T, W}.
+ * (iteration, ant) {status | roads in the route << 8, moves, T, W}; res->ant_steps counts every move of
+ * every ant, forward or back.
  */
 int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint32_t *route_nodes, uint32_t route_cap,
               uint64_t *tau_out, uint32_t *ant_log, orc_result *res)
@@ -953,10 +986,14 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
     uint32_t E = g->n_edges;
     uint64_t *tau = malloc(sizeof(uint64_t) * (E + 1));
     uint64_t *D = malloc(sizeof(uint64_t) * (E + 1));
-    uint32_t *route = malloc(sizeof(uint32_t) * (g->n_nodes + 1));
-    uint32_t *best_route = malloc(sizeof(uint32_t) * (g->n_nodes + 1));
     orc_state S;
-    if (!tau || !D || !route || !best_route || state_init(&S, g, prm, q->dst) != ORC_OK) {
+    int init_rc = state_init(&S, g, prm, q->dst);
+    size_t route_max = init_rc == ORC_OK ? (size_t)S.max_steps + 1 : 1;
+    uint32_t *route = malloc(sizeof(uint32_t) * route_max);
+    uint32_t *best_route = malloc(sizeof(uint32_t) * route_max);
+    if (init_rc == ORC_OK && (!tau || !D || !route || !best_route))
+        state_free(&S);
+    if (!tau || !D || !route || !best_route || init_rc != ORC_OK) {
         free(tau);
         free(D);
         free(route);
@@ -977,13 +1014,13 @@ int orc_solve(const orc_net *g, const orc_params *prm, const orc_query *q, uint3
         for (uint32_t it = 0; it < q->n_iter; ++it) {
             memset(D, 0, sizeof(uint64_t) * E);
             for (uint32_t k = 0; k < q->n_ants; ++k) {
-                uint32_t steps, T, W;
-                int st = walk(&S, q, alpha, beta, frac, tau, it, k, route, &steps, &T, &W);
-                res->ant_steps += steps;
+                uint32_t steps, moves, T, W;
+                int st = walk(&S, q, alpha, beta, frac, tau, it, k, route, &steps, &moves, &T, &W);
+                res->ant_steps += moves;
                 if (ant_log) {
                     uint32_t *l = ant_log + 4 * ((size_t)it * q->n_ants + k);
-                    l[0] = (uint32_t)st;
-                    l[1] = steps;
+                    l[0] = (uint32_t)st | (steps << 8);
+                    l[1] = moves;
                     l[2] = T;
                     l[3] = W;
                 }

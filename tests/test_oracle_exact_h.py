@@ -111,6 +111,7 @@ def test_exact_h_deposit_numerator(orc):
     prm = orc.Params(flags=orc.FLAG_EXACT_H)
     h_src = int(orc.prepare(onet, prm, q.dst)["h"][q.src])
     r = orc.solve(onet, prm, q, want_log=True)
-    dep = sum(int(s) * ((max(h_src, 1) << 32) // int(T)) for st, s, T, _ in r["log"][0] if st == 0)
+    st, length, _, T, _ = orc.log_fields(r["log"][0])
+    dep = sum(int(n) * ((max(h_src, 1) << 32) // int(t)) for n, t in zip(length[st == 0], T[st == 0]))
     assert dep > 0
     assert int(r["tau"].sum()) == wl.net.n_edges * orc.evaporate(2 ** 32, orc.rho_fix(q.rho)) + dep

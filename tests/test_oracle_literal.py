@@ -91,7 +91,8 @@ def test_repulsive_frequencies_chi_square(orc):
 
 def _line_with_spur():
     """0 - 1 - 2 - 3 with a spur 1 - 4 (both directions). Node 4 is a dead end for an ant coming from
-    1, so the only route 0 -> 3 is 0, 1, 2, 3 and ants that enter the spur fail."""
+    1, so the only route 0 -> 3 is 0, 1, 2, 3; an ant that enters the spur steps back to 1, which
+    takes it 5 moves in all instead of 3."""
     roads = [(0, 1, 512, 45), (1, 2, 512, 45), (2, 3, 512, 45), (1, 4, 512, 45)]
     coords = [(0, 0), (512, 0), (1024, 0), (1536, 0), (512, 512)]
     return NB.build(5, roads, coords)
@@ -102,15 +103,19 @@ def test_single_route_closed_form(orc, flags):
     """Every successful ant takes the same three roads with the same T. Per iteration with n successes:
     route roads: tau <- evap(tau) + n*delta, or with unused-only evaporation tau + n*delta when n > 0
     and evap(tau) when n = 0; every other road evaporates every iteration. delta = 1.0 with unit
-    deposits, else floor(max(h(src),1) * 2^32 / T)."""
+    deposits, else floor(max(h(src),1) * 2^32 / T). A cap of 4 moves makes the ants that enter the
+    spur fail, so iterations with no success occur; beta = 0 keeps the spur as likely as the road on
+    (the heuristic would rule it out)."""
     net, sig, veh = _line_with_spur()
     onet = orc.Net(net, sig, veh)
-    q = Q(0, 3, 6, 12, 1.0, 1.0, 0.25, 9)
-    prm = orc.Params(flags=flags)
+    q = Q(0, 3, 6, 12, 1.0, 0.0, 0.25, 9)
+    prm = orc.Params(flags=flags, max_steps=4)
     r = orc.solve(onet, prm, q, want_log=True)
+    st, _, moves, _, _ = orc.log_fields(r["log"])
     log = r["log"]
-    ok = log[:, :, 0] == 0
-    assert ok.any() and (~ok).any()  # some ants die in the spur
+    ok = st == 0
+    assert ok.any() and (~ok).any()  # ants that enter the spur run out of moves
+    assert (moves[ok] == 3).all() and (st[~ok] == orc.ANT_STEP_CAP).all()
     T = {int(t) for t in log[:, :, 2][ok]}
     assert len(T) == 1
     T = T.pop()
@@ -138,8 +143,8 @@ def test_literal_one_iteration_identity_grid10(orc):
     onet = orc.Net.from_workload(wl)
     q = wl.queries[0]
     r = orc.solve(onet, orc.Params(flags=orc.FLAG_PAPER_LITERAL), q, want_log=True)
-    log = r["log"][0]
-    uses = int(sum(int(s) for st, s, _, _ in log if st == 0))
+    st, length, _, _, _ = orc.log_fields(r["log"][0])
+    uses = int(length[st == 0].sum())
     assert uses > 0
     tau = r["tau"].astype(object)
     low = orc.evaporate(2**32, orc.rho_fix(q.rho))

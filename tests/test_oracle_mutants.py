@@ -6,8 +6,6 @@ must pass them, which shows that the harness itself works. No GPU.
 
 Not planted, because each is equivalent to the original and no test can tell them apart:
 - `key < best_key` against `key <= best_key` in the best-route rule: keys (T, iteration, ant) are unique;
-- a default step cap of N instead of N - 1: a walk that has taken N - 1 roads on distinct nodes stands
-  on the destination, so the cap of N - 1 never binds (the 4096 ceiling does, and is planted).
 - dropping the per-iteration queue update of a solve: densities and red times are fixed during a solve,
   so it recomputes the order it already holds.
 """
@@ -65,19 +63,35 @@ MUTANTS = [
      [PRIM, SOLVE]),
     ("weight_scale", "floor(ldexp((double)s[i], 22 - E))", "floor(ldexp((double)s[i], 21 - E))", [PRIM]),
     ("roulette_not_strict", "if (acc > r)", "if (acc >= r)", [PRIM, SOLVE]),
-    ("cost_without_heuristic", "uint32_t c = S->tt[e] + w + S->h[v];", "uint32_t c = S->tt[e] + w;", [SOLVE]),
+    ("cost_without_heuristic", "int64_t cost = (int64_t)S->tt[e] + w + S->h[v] - S->h[u];",
+     "int64_t cost = (int64_t)S->tt[e] + w;", [SOLVE]),
+    ("cost_without_current_bound", "+ w + S->h[v] - S->h[u];", "+ w + S->h[v];", [SOLVE]),
+    ("cost_bound_of_source", "+ w + S->h[v] - S->h[u];", "+ w + S->h[v] - S->h[q->src];", [SOLVE]),
+    ("cost_floor_two", "uint32_t c = cost < 1 ? 1u : (uint32_t)cost;", "uint32_t c = cost < 2 ? 2u : (uint32_t)cost;",
+     [SOLVE]),
     ("wait_at_destination", "if (v != q->dst && g->n_phases[v] > 0) {", "if (g->n_phases[v] > 0) {", [SOLVE]),
     ("time_without_wait", "t += (uint64_t)S->tt[e] + S->waitv[pick];", "t += (uint64_t)S->tt[e];", [SOLVE]),
     ("no_visited_rule", "if (!S->visited[g->col[e]])", "if (1)", [SOLVE]),
-    ("step_cap_early", "if (steps == S->max_steps)", "if (steps + 1 == S->max_steps)", [SOLVE]),
-    ("default_step_cap", "uint32_t def_steps = N - 1 < 4096u ? N - 1 : 4096u;",
-     "uint32_t def_steps = N - 1 < 4095u ? N - 1 : 4095u;", [SOLVE]),
+    ("step_cap_early", "if (moves == S->max_steps)", "if (moves + 1 == S->max_steps)", [SOLVE]),
+    ("default_step_cap", "uint32_t def_steps = two_n < 4096u ? (uint32_t)two_n : 4096u;",
+     "uint32_t def_steps = two_n < 4095u ? (uint32_t)two_n : 4095u;", [SOLVE]),
+    ("default_step_cap_one_pass", "uint64_t two_n = 2ull * (N - 1u);", "uint64_t two_n = N - 1u;", [SOLVE]),
+    # the step back at a dead end
+    ("dead_end_fails_at_once", "if (len == 0) {", "if (1) {", [SOLVE]),
+    ("back_keeps_wait_in_time", "t -= (uint64_t)S->tt[e] + S->wait_at[len];", "t -= (uint64_t)S->tt[e];", [SOLVE]),
+    ("back_keeps_wait", "W -= S->wait_at[len];", "W -= 0;", [SOLVE]),
+    ("back_to_source", "u = len ? g->col[route_edges[len - 1]] : q->src;", "u = q->src;", [SOLVE]),
+    ("back_not_a_move", "            moves++;\n            continue;", "            continue;", [SOLVE]),
+    ("back_forgets_node", "            len--;\n            uint32_t e = route_edges[len];",
+     "            S->visited[u] = 0;\n            len--;\n            uint32_t e = route_edges[len];", [SOLVE]),
+    ("draw_keyed_by_depth", "draw64(q->seed, it, ant, moves, 0)", "draw64(q->seed, it, ant, len, 0)", [SOLVE]),
+    ("log_moves_as_roads", "res->ant_steps += moves;", "res->ant_steps += steps;", [SOLVE]),
     ("time_cap_halved", "if (t > ORC_T_CAP)", "if (t > ORC_T_CAP / 2)", [SOLVE]),
     ("congested_all_dropped", "if (n_ok > 0 && n_ok < n) {", "if (n_ok < n) {", [SOLVE]),
     ("tie_rule_ant_major", "| ((uint64_t)it * q->n_ants + k);", "| ((uint64_t)k * q->n_iter + it);", [SOLVE]),
     ("beta_fraction_ignored", "*frac = floorf(q->alpha) != q->alpha || floorf(q->beta) != q->beta;",
      "*frac = floorf(q->alpha) != q->alpha;", [FRAC]),
-    ("visited_not_marked", "S->visited[u] = 1;\n        route_edges", "route_edges", [SOLVE]),
+    ("visited_not_marked", "S->visited[u] = 1;\n        S->wait_at[len]", "S->wait_at[len]", [SOLVE]),
     ("draw_words_swapped", "return (uint64_t)o[0] | ((uint64_t)o[1] << 32);", "return (uint64_t)o[1] | ((uint64_t)o[0] << 32);",
      [PRIM, SOLVE]),
     ("best_wait_is_time", "best_W = W;", "best_W = T;", [SOLVE]),

@@ -74,6 +74,166 @@ def test_hand_worked_step_with_signal_queue_and_heuristic(orc):
     assert set(heads) == {0, 1, 2}
 
 
+def _line_net(orc, xs, roads, dst_first=False):
+    """Nodes on the x axis at xs (dm); roads (a, b, length_dm) both ways at 45 km/h, the fastest road, so
+    the straight-line bound is exactly 8 ms per dm and a road of L dm takes exactly 8*L ms."""
+    net, sig, veh = NB.build(len(xs), [(a, b, L, 45) for a, b, L in roads], [(x, 0) for x in xs])
+    return net, orc.Net(net, sig, veh)
+
+
+def test_hand_worked_step_reduced_cost(orc):
+    """Q2's reading: a road costs the time it adds over the remaining bound, c = tt + wait + h(v) - h(u).
+    src 0 at x = 512, node 1 at 768, node 2 at 0, destination 3 at 1536; roads 0-1 and 0-2 of 512 dm
+    (4096 ms). h(0) = 1024*8 = 8192, h(1) = 6144, h(2) = 12288, so c(0->1) = 4096 + 6144 - 8192 = 2048
+    and c(0->2) = 4096 + 12288 - 8192 = 8192: scores 2^-11 and 2^-13, weights 2^22 and 2^20, chances
+    4/5 and 1/5 (without the -h(u) term they would be 10240 and 16384). Via 1 the ant takes road 1-3
+    (768 dm, 6144 ms), via 2 road 2-3 (1536 dm, 12288 ms)."""
+    net, onet = _line_net(orc, [512, 768, 0, 1536], [(0, 1, 512), (0, 2, 512), (1, 3, 768), (2, 3, 1536)])
+    prep = orc.prepare(onet, orc.Params(), 3)
+    assert list(prep["h"]) == [8192, 6144, 12288, 0]
+    assert [int(net.col[e]) for e in range(net.row_ptr[0], net.row_ptr[1])] == [1, 2]
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+    weights = _exact_weights([np.float32(2.0**-11), np.float32(2.0**-13)])
+    assert weights == [2**22, 2**20]
+    picks = []
+    for ant in range(200):
+        w = orc.walk_one(onet, orc.Params(), Q(0, 3, 200, 1, 1.0, 1.0, 0.1, 21), tau, it=0, ant=ant)
+        pick = _expected_pick(orc, weights, 21, 0, ant, 0)
+        assert [int(net.col[e]) for e in w["route_edges"]] == [[1, 3], [2, 3]][pick]
+        assert w["T"] == [4096 + 6144, 4096 + 12288][pick] and w["moves"] == 2
+        picks.append(pick)
+    assert 0 < sum(picks) < 200
+
+
+def test_hand_worked_cost_floor_at_one(orc):
+    """A road that makes full progress at the fastest speed adds nothing over the bound: its cost is
+    floored at 1 ms. src 0 at x = 512, node 1 at 1024, node 2 at 1536, destination 3 at 2048. The first
+    move 0 -> 1 is forced. At 1 (h = 8192): road 1-2 of 512 dm gives c = 4096 + 4096 - 8192 = 0 -> 1,
+    road 1-3 of 1025 dm (8200 ms) gives c = 8200 - 8192 = 8. Scores 1 and 1/8, weights 2^22 and 2^19:
+    chances 8/9 and 1/9, drawn with the draw of move 1. The bound subtracted is the current node's
+    (with src's, 12288, both costs would floor to 1)."""
+    net, onet = _line_net(orc, [512, 1024, 1536, 2048], [(0, 1, 512), (1, 2, 512), (1, 3, 1025), (2, 3, 512)])
+    assert [int(net.col[e]) for e in range(net.row_ptr[1], net.row_ptr[2])] == [0, 2, 3]
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+    weights = _exact_weights([np.float32(1.0), np.float32(0.125)])
+    assert weights == [2**22, 2**19]
+    picks = []
+    for ant in range(300):
+        w = orc.walk_one(onet, orc.Params(), Q(0, 3, 300, 1, 1.0, 1.0, 0.1, 4), tau, it=0, ant=ant)
+        pick = _expected_pick(orc, weights, 4, 0, ant, 1)
+        assert [int(net.col[e]) for e in w["route_edges"]] == [[1, 2, 3], [1, 3]][pick]
+        assert w["T"] == [4096 * 3, 4096 + 8200][pick]
+        picks.append(pick)
+    assert 0 < sum(picks) < 300
+
+
+def _spur_junction():
+    """Directed roads: 0 -> {1, 2, 3}, 1 -> 0 (node 1 is a dead end once 0 is visited), 2 -> {1, 4},
+    3 -> 4; destination 4. Nodes 1, 2 and 3 are signalised, so every arrival time changes the waits
+    that follow; an ant entering the dead end waits there (it arrives at 8400 ms, 3400 ms into the cycle,
+    and its phase turns green at 20000 ms). All coordinates are equal (h = 0)."""
+    roads = [(0, 1, 700, 30, 3, 1), (1, 0, 700, 30, 3, 0), (0, 2, 1200, 50, 3, 0), (0, 3, 900, 50, 3, 1),
+             (2, 1, 800, 50, 3, 1), (2, 4, 1500, 70, 3, 0), (3, 4, 1300, 50, 3, 0)]
+    signals = {1: (60_000, 5_000, [20_000, 40_000]), 2: (90_000, 30_000, [50_000, 40_000]),
+               3: (75_000, 0, [30_000, 45_000])}
+    return NB.build(5, roads, signals=signals, vehicles={(0, 2): 7, (2, 4): 3}, bidirectional=False)
+
+
+def test_hand_worked_step_back_at_dead_end(orc):
+    """Uniform choices (alpha = beta = 0). An ant that takes 0 -> 1 finds no unvisited node (1 -> 0 leads
+    back), steps back to 0 with the clock and wait it had there, and draws again with the draw of move
+    2 among {2, 3} (1 stays visited). An ant at 2 that takes 2 -> 1 steps back to 2 and must take 2 -> 4.
+    Expected routes, move counts, T and W follow from the Philox draws and the pinned road times."""
+    net, sig, veh = _spur_junction()
+    onet = orc.Net(net, sig, veh)
+    timing = NB.Timing(orc, onet, net, sig, 4)
+    tau = np.full(net.n_edges, 2**32, np.uint64)
+
+    def timed(route):
+        t = Wt = 0
+        for a, b in zip(route[:-1], route[1:]):
+            t, w = timing.after(NB.edge_id(net, a, b), t)
+            Wt += w
+        return t, Wt
+
+    seen = set()
+    for ant in range(256):
+        p0 = _expected_pick(orc, [1, 1, 1], 13, 0, ant, 0)
+        if p0 == 0:  # into the dead end, back to 0, then 2 or 3 by the draw of move 2
+            mid = [2, 3][_expected_pick(orc, [1, 1], 13, 0, ant, 2)]
+            route, moves = [0, mid, 4], 4
+        elif p0 == 1 and _expected_pick(orc, [1, 1], 13, 0, ant, 1) == 0:  # 0 -> 2 -> 1, back to 2, -> 4
+            route, moves = [0, 2, 4], 4
+        else:
+            route, moves = [0, [1, 2, 3][p0], 4], 2
+        w = orc.walk_one(onet, orc.Params(), Q(0, 4, 256, 1, 0.0, 0.0, 0.1, 13), tau, it=0, ant=ant)
+        assert w["status"] == orc.ANT_SUCCESS
+        assert [0] + [int(net.col[e]) for e in w["route_edges"]] == route, ant
+        assert w["moves"] == moves and w["steps"] == 2
+        assert (w["T"], w["W"]) == timed(route)
+        seen.add((tuple(route), moves))
+    assert len(seen) == 4  # both kinds of step back, and both direct routes, occurred
+    assert timing.after(NB.edge_id(net, 0, 1), 0) == (8400 + 16600, 16600)
+
+
+def _reachable(net, src):
+    seen, stack = {src}, [src]
+    while stack:
+        u = stack.pop()
+        for e in range(int(net.row_ptr[u]), int(net.row_ptr[u + 1])):
+            v = int(net.col[e])
+            if v not in seen:
+                seen.add(v)
+                stack.append(v)
+    return seen
+
+
+@pytest.mark.parametrize("gseed", range(8))
+def test_depth_first_walk_closed_forms(orc, gseed):
+    """With the default cap of 2(N - 1) moves an ant is a depth-first search: it reaches any destination
+    reachable from src, and when there is none it ends back at src with a dead end after exactly
+    2(R - 1) moves, R = the number of nodes reachable from src (each is entered once and left once).
+    Tree-like graphs with spurs, and directed graphs with sinks."""
+    rng = np.random.Generator(np.random.PCG64(700 + gseed))
+    n = int(rng.integers(6, 14))
+    net, sig = W.random_small(n, n - 1 + int(rng.integers(0, 3)), rng, signalised_frac=0.5)
+    if gseed % 2:  # keep one direction of a random half of the roads
+        keep = rng.random(net.n_edges) < 0.6
+        tails = net.tails()
+        net = W.csr_from_roads(n, tails[keep], net.col[keep], net.length_dm[keep], net.speed_kmh[keep],
+                               net.lanes[keep], net.orient[keep], net.x_dm, net.y_dm, bidirectional=False)
+        sig = W.two_phase_signals(net, sig.n_phases > 0, rng)
+    veh = rng.integers(0, 8, net.n_edges).astype(np.uint32)
+    onet = orc.Net(net, sig, veh)
+    src = 0
+    R = _reachable(net, src)
+    for dst in range(1, n):
+        r = orc.solve(onet, orc.Params(), Q(src, dst, 8, 3, 1.0, 2.0, 0.1, gseed), want_tau=False, want_log=True)
+        st, length, moves, _, _ = orc.log_fields(r["log"])
+        if dst in R:
+            assert (st == orc.ANT_SUCCESS).all() and r["status"] == 0
+            assert (moves >= length).all() and ((moves - length) % 2 == 0).all()  # each step back undoes a move
+        else:
+            assert (st == orc.ANT_DEAD_END).all() and (moves == 2 * (len(R) - 1)).all() and (length == 0).all()
+            assert r["status"] == orc.ERR_NO_ROUTE
+
+
+@pytest.mark.parametrize("gseed", range(6))
+def test_spur_graphs_best_equals_brute_force(orc, gseed):
+    """Trees with one or two extra links (many spurs and dead ends), signals at half the nodes: the
+    colony's best route equals the time-dependent Dijkstra optimum and the brute-force minimum."""
+    rng = np.random.Generator(np.random.PCG64(800 + gseed))
+    net, sig = W.random_small(8, 8 + gseed % 2, rng, signalised_frac=0.5)
+    veh = rng.integers(0, 10, net.n_edges).astype(np.uint32)
+    onet = orc.Net(net, sig, veh)
+    src, dst = 0, 7
+    timing = NB.Timing(orc, onet, net, sig, dst)
+    opt = NB.td_dijkstra(net, timing, src, dst)
+    assert opt == NB.brute_force_min(net, timing, src, dst)
+    r = orc.solve(onet, orc.Params(), Q(src, dst, 64, 30, 1.0, 2.0, 0.1, gseed))
+    assert r["status"] == 0 and r["travel_ms"] == opt
+
+
 def test_first_step_frequencies_chi_square(orc):
     """Scores 2^-12, 2^-13, 2^-11 -> probabilities 2/7, 1/7, 4/7 over Philox draws; and alpha=beta=0
     gives a uniform choice."""
@@ -182,7 +342,8 @@ def test_pheromone_conservation_identity(orc):
     rfix = orc.rho_fix(q.rho)
     r1 = orc.solve(onet, orc.Params(), q, want_log=True)
     log = r1["log"][0]
-    dep = sum(int(s) * _deposit(h_src, int(T)) for st, s, T, _ in log if st == 0)
+    st, length, _, T, _ = orc.log_fields(log)
+    dep = sum(int(n) * _deposit(h_src, int(t)) for n, t in zip(length[st == 0], T[st == 0]))
     assert dep > 0
     E = wl.net.n_edges
     assert int(r1["tau"].sum()) == E * orc.evaporate(2**32, rfix) + dep
@@ -191,7 +352,8 @@ def test_pheromone_conservation_identity(orc):
     q2 = W.Query(q.src, q.dst, q.n_ants, 2, q.alpha, q.beta, q.rho, q.seed)
     r2 = orc.solve(onet, orc.Params(), q2, want_log=True)
     assert (r2["log"][0] == log).all()
-    dep2 = sum(int(s) * _deposit(h_src, int(T)) for st, s, T, _ in r2["log"][1] if st == 0)
+    st2, length2, _, T2, _ = orc.log_fields(r2["log"][1])
+    dep2 = sum(int(n) * _deposit(h_src, int(t)) for n, t in zip(length2[st2 == 0], T2[st2 == 0]))
     assert int(r2["tau"].sum()) == sum(orc.evaporate(int(t), rfix) for t in r1["tau"]) + dep2
     assert int(r2["tau"].min()) >= 1
 
@@ -211,13 +373,13 @@ def test_best_is_min_T_then_lowest_iteration_ant(orc, case):
     """The reported best is the minimum T; among equal T (many on the star graph), the lowest
     (iteration, ant)."""
     r = _star_solve(orc) if case == "star" else _grid_solve(orc)
-    log = r["log"]
-    ok = log[:, :, 0] == 0
-    Ts = np.where(ok, log[:, :, 2].astype(np.int64), np.iinfo(np.int64).max)
+    st, length, _, T, W_ = orc.log_fields(r["log"])
+    ok = st == 0
+    Ts = np.where(ok, T.astype(np.int64), np.iinfo(np.int64).max)
     tmin = Ts.min()
     it, ant = [int(v) for v in np.argwhere(Ts == tmin)[0]]  # row-major: lowest (it, ant)
     assert r["travel_ms"] == tmin and (r["best_iter"], r["best_ant"]) == (it, ant)
-    assert r["wait_ms"] == log[it, ant, 3] and r["route_len"] == log[it, ant, 1] + 1
+    assert r["wait_ms"] == W_[it, ant] and r["route_len"] == length[it, ant] + 1
     assert r["n_success"] == int(ok.sum())
     if case == "star":
         assert (Ts == tmin).sum() > 10
@@ -232,10 +394,14 @@ def test_src_equals_dst(orc):
 
 
 def test_unreachable_destination(orc):
+    """Node 3 is isolated. Every ant walks 0 -> 1 -> 2, finds no road left, steps back twice and ends at
+    src with nothing left to try: 4 moves, a dead end, no route."""
     net, sig, veh = NB.build(4, [(0, 1, 1000, 50), (1, 2, 1000, 50)])  # node 3 isolated
     r = orc.solve(orc.Net(net, sig, veh), orc.Params(), Q(0, 3, 8, 4, 1.0, 2.0, 0.1, 0), want_log=True)
     assert r["status"] == orc.ERR_NO_ROUTE
-    assert set(np.unique(r["log"][:, :, 0])) == {orc.ANT_DEAD_END}
+    st, length, moves, _, _ = orc.log_fields(r["log"])
+    assert set(np.unique(st)) == {orc.ANT_DEAD_END} and (moves == 4).all() and (length == 0).all()
+    assert r["ant_steps"] == 4 * 8 * 4
 
 
 def test_step_cap(orc):
@@ -244,13 +410,14 @@ def test_step_cap(orc):
     onet = orc.Net(net, sig, veh)
     r = orc.solve(onet, orc.Params(max_steps=5), Q(0, 6, 4, 2, 1.0, 2.0, 0.1, 0), want_log=True)
     assert r["status"] == orc.ERR_NO_ROUTE
-    assert (r["log"][:, :, 0] == orc.ANT_STEP_CAP).all() and (r["log"][:, :, 1] == 5).all()
+    st, length, moves, _, _ = orc.log_fields(r["log"])
+    assert (st == orc.ANT_STEP_CAP).all() and (moves == 5).all() and (length == 5).all()
     r = orc.solve(onet, orc.Params(max_steps=6), Q(0, 6, 4, 2, 1.0, 2.0, 0.1, 0))
     assert r["status"] == 0 and r["route_len"] == 7
 
 
 def test_default_step_cap_is_4096(orc):
-    """With max_steps = 0 the cap is min(N - 1, 4096) roads (Q12's reading). On a line of 4200 nodes
+    """With max_steps = 0 the cap is min(2(N - 1), 4096) moves (Q12's reading). On a line of 4200 nodes
     the only walk from one end to the other has 4199 roads, so it stops after exactly 4096; with the
     cap raised to 4199 it arrives."""
     roads = [(i, i + 1, 1000, 50) for i in range(4199)]
@@ -259,7 +426,8 @@ def test_default_step_cap_is_4096(orc):
     q = Q(0, 4199, 2, 1, 1.0, 2.0, 0.1, 0)
     r = orc.solve(onet, orc.Params(), q, want_log=True)
     assert r["status"] == orc.ERR_NO_ROUTE
-    assert (r["log"][:, :, 0] == orc.ANT_STEP_CAP).all() and (r["log"][:, :, 1] == 4096).all()
+    st, _, moves, _, _ = orc.log_fields(r["log"])
+    assert (st == orc.ANT_STEP_CAP).all() and (moves == 4096).all()
     r = orc.solve(onet, orc.Params(max_steps=4199), q)
     assert r["status"] == 0 and r["route_len"] == 4200
 
@@ -273,7 +441,7 @@ def test_time_cap(orc):
     r = orc.solve(onet, orc.Params(), Q(0, 16, 2, 1, 1.0, 2.0, 0.1, 0))
     assert r["status"] == 0 and r["travel_ms"] == 2**30
     r = orc.solve(onet, orc.Params(), Q(0, 17, 2, 1, 1.0, 2.0, 0.1, 0), want_log=True)
-    assert r["status"] == orc.ERR_NO_ROUTE and (r["log"][:, :, 0] == orc.ANT_TIME_CAP).all()
+    assert r["status"] == orc.ERR_NO_ROUTE and (orc.log_fields(r["log"])[0] == orc.ANT_TIME_CAP).all()
 
 
 def test_congestion_threshold_mask(orc):
