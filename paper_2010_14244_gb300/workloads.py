@@ -283,16 +283,44 @@ def grid64(n_queries=16, n_ants=1024, n_iter=200) -> Workload:
                     "2000 Zipf(1.2) vehicles, uniform OD pairs")
 
 
-def geometric_network(n_rows, n_cols, rng, avg_out_degree=2.8, cell_dm=2000, jitter=0.35, lanes=3):
-    """Planar road graph on a jittered lattice.
+def thin_lattice(n_nodes, a, b, order, target):
+    """Links kept when the links a[i]-b[i] of a connected graph are tried for removal in the order
+    ``order`` and each one that is not a bridge of the remaining graph is removed, until ``target``
+    links remain.
 
-    One point per cell (jitter +-0.35 cell), 4-neighbour candidate links. A random spanning tree keeps
-    the graph connected; random further links are added until the average out-degree (directed roads
-    per node) reaches ``avg_out_degree``. Length = straight-line distance x U[1.0, 1.4].
+    Trying links in a fixed order and removing the non-bridges is reverse-delete (Kruskal 1956) with
+    the links tried first as the heaviest: run to the end it leaves the minimum spanning tree of those
+    weights, and a link it keeps stays a bridge from then on. Stopped early, it has removed the non-tree
+    links it reached, so what remains is that tree plus the non-tree links it had not reached yet. Those
+    are the ones tried last, i.e. the lightest. That is computed here in O(E log E): a Kruskal spanning
+    tree, then the lightest non-tree links until ``target`` links remain.
     """
     from scipy.sparse import coo_matrix
     from scipy.sparse.csgraph import minimum_spanning_tree
 
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    m = a.size
+    weight = np.empty(m, np.float64)
+    weight[np.asarray(order)] = np.arange(m, 0, -1, dtype=np.float64)  # tried first = heaviest
+    mst = minimum_spanning_tree(coo_matrix((weight, (a, b)), shape=(n_nodes, n_nodes))).tocoo()
+    key = np.minimum(a, b) * n_nodes + np.maximum(a, b)
+    tree_key = np.minimum(mst.row, mst.col).astype(np.int64) * n_nodes + np.maximum(mst.row, mst.col)
+    in_tree = np.isin(key, tree_key)
+    rest = np.flatnonzero(~in_tree)
+    rest = rest[np.argsort(weight[rest])]  # lightest (tried last) first
+    n_rest = max(0, int(target) - int(in_tree.sum()))
+    return np.sort(np.concatenate([np.flatnonzero(in_tree), rest[:n_rest]]))
+
+
+def geometric_network(n_rows, n_cols, rng, avg_out_degree=2.8, cell_dm=2000, jitter=0.35, lanes=3):
+    """Planar road graph on a jittered lattice.
+
+    One point per 200 m cell (jitter +-0.35 cell) with links to its 4 lattice neighbours; random links
+    that are not bridges are removed, one at a time, until the average out-degree (directed roads per
+    node) is ``avg_out_degree`` (``thin_lattice``). Length = straight-line distance x U[1.0, 1.4];
+    speed limits U{30, 50, 70} km/h.
+    """
     n = n_rows * n_cols
     gx = (np.arange(n) % n_cols).astype(np.float64)
     gy = (np.arange(n) // n_cols).astype(np.float64)
@@ -301,15 +329,7 @@ def geometric_network(n_rows, n_cols, rng, avg_out_degree=2.8, cell_dm=2000, jit
     ids = np.arange(n).reshape(n_rows, n_cols)
     a = np.concatenate([ids[:, :-1].ravel(), ids[:-1, :].ravel()])
     b = np.concatenate([ids[:, 1:].ravel(), ids[1:, :].ravel()])
-    w = rng.random(a.size) + 1e-9
-    mst = minimum_spanning_tree(coo_matrix((w, (a, b)), shape=(n, n))).tocoo()
-    tree = set(zip(np.minimum(mst.row, mst.col).tolist(), np.maximum(mst.row, mst.col).tolist()))
-    in_tree = np.array([(min(p, q), max(p, q)) in tree for p, q in zip(a.tolist(), b.tolist())])
-    target = int(round(avg_out_degree * n / 2))
-    extra_pool = np.flatnonzero(~in_tree)
-    n_extra = max(0, target - int(in_tree.sum()))
-    extra = rng.choice(extra_pool, size=min(n_extra, extra_pool.size), replace=False)
-    sel = np.concatenate([np.flatnonzero(in_tree), extra])
+    sel = thin_lattice(n, a, b, rng.permutation(a.size), int(round(avg_out_degree * n / 2)))
     a, b = a[sel], b[sel]
     dx = (x[b] - x[a]).astype(np.float64)
     dy = (y[b] - y[a]).astype(np.float64)

@@ -65,7 +65,7 @@ def test_city_batch_one_launch(gm, orc):
 
 
 def test_city_batch_full_size(gm):
-    """The 64-graph workload (1.1k-198k nodes, 2268 colonies of 128-1024 ants, 50 iterations) in one
+    """The 64-graph workload (1.1k-187k nodes, 2362 colonies of 128-1024 ants, 50 iterations) in one
     launch. In each size bucket of node counts (1k-4k, 4k-16k, 16k-64k, 64k-200k) the first graph has
     every colony re-solved by the oracle, and each must agree bit for bit, final pheromone table included.
     Every route of every graph is valid."""

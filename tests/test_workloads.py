@@ -117,6 +117,43 @@ def test_geo100k_recipe():
     assert all((q.n_ants, q.n_iter) == (256, 100) for q in wl.queries)
 
 
+def _thin_literally(n, a, b, order, target):
+    """The recipe as stated: try the links in `order`; remove a link when it is not a bridge of what
+    remains (the graph stays connected without it); stop when `target` links remain."""
+    import networkx as nx
+
+    g = nx.MultiGraph()
+    g.add_nodes_from(range(n))
+    for i, (p, q) in enumerate(zip(a, b)):
+        g.add_edge(int(p), int(q), key=i)
+    kept = set(range(len(a)))
+    for i in order:
+        if len(kept) == target:
+            break
+        g.remove_edge(int(a[i]), int(b[i]), key=int(i))
+        if nx.is_connected(g):
+            kept.discard(int(i))
+        else:
+            g.add_edge(int(a[i]), int(b[i]), key=int(i))
+    return np.array(sorted(kept))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_thin_lattice_equals_one_at_a_time_removal(seed):
+    """The spanning-tree form of the planar generator keeps exactly the links that removing random
+    non-bridge links one at a time keeps, for the same order of tries."""
+    rng = np.random.default_rng(seed)
+    rows, cols = int(rng.integers(3, 8)), int(rng.integers(3, 9))
+    n = rows * cols
+    ids = np.arange(n).reshape(rows, cols)
+    a = np.concatenate([ids[:, :-1].ravel(), ids[:-1, :].ravel()])
+    b = np.concatenate([ids[:, 1:].ravel(), ids[1:, :].ravel()])
+    order = rng.permutation(a.size)
+    for target in (n - 1, int(round(1.2 * n)), int(round(1.4 * n)), a.size):
+        target = min(target, a.size)
+        np.testing.assert_array_equal(W.thin_lattice(n, a, b, order, target), _thin_literally(n, a, b, order, target))
+
+
 def test_city52_recipe():
     wl = W.city52()
     net = wl.net
@@ -157,7 +194,7 @@ def test_city_batch_recipe():
         assert 0.4 <= float(wl.vehicles.mean()) <= 3.2
         frac = np.count_nonzero(wl.signals.n_phases) / net.n_nodes
         assert abs(frac - 0.6) < 0.08
-    assert sum(len(wl.queries) for wl in cities) == 2268
+    assert sum(len(wl.queries) for wl in cities) == 2362
 
 
 def test_serving_requests():
