@@ -42,7 +42,7 @@ extern "C" {
 #define GMP_MAX_PHASES 8
 #define GMP_THRESHOLD_OFF 0xFFFFFFFFu
 #define GMP_FLAG_RANDOM_TAU 1u /* initial pheromone 0.5 + u/2^32, u = Philox(road, 0, 0, 1) word 0 */
-#define GMP_FLAG_ANT_LOG 2u    /* keep a per-(iteration, ant) log {status, steps, T, W} for inspection */
+#define GMP_FLAG_ANT_LOG 2u    /* keep a per-(iteration, ant) log {status | length << 8, moves, T, W} */
 /* The paper's own MACO-P pheromone variant (Sec. 4.1 bullets, Fig. 3, Algorithm 2), one flag per part;
  * every kernel shape and both pheromone layouts honour them. */
 #define GMP_FLAG_REPULSIVE 32u    /* next-node rule prefers less pheromone: scores use (1/tau)^alpha */
@@ -63,7 +63,8 @@ typedef struct gmp_ctx gmp_ctx;
 
 /* Tunables of the colony (Fig. 3 leaves all of them unstated). Zero means "default" where noted. */
 typedef struct {
-    uint32_t max_steps;     /* roads per ant before it gives up; 0 = min(N-1, 4096) */
+    uint32_t max_steps;     /* moves per ant (forward or back) before it gives up; 0 = min(2(N-1), 4096),
+                               enough for a complete depth-first walk; at most 2^24 */
     uint32_t h_sat_ms;      /* saturation headway per lane for queue delays; 0 = 2000 ms */
     uint32_t thr_permille;  /* Fig. 3 congestion threshold: a road with vehicles*1000 > thr*capacity is
                                avoided unless every candidate is; GMP_THRESHOLD_OFF disables it */
@@ -104,7 +105,7 @@ typedef struct {
     uint32_t route_len; /* nodes in the best route (required size if status == GMP_ERR_BUFFER) */
     uint64_t travel_ms; /* T of the best route: min T over all ants, ties to lowest (iteration, ant) */
     uint64_t wait_ms;   /* signal waits + queue delays along that route */
-    uint64_t ant_steps; /* roads taken by all ants of all iterations, failed ants included */
+    uint64_t ant_steps; /* moves of all ants of all iterations (forward and back), failed ants included */
     uint64_t n_success; /* ant walks that reached the destination */
     uint32_t best_iter, best_ant;
     int32_t status;     /* GMP_OK, GMP_ERR_NO_ROUTE or GMP_ERR_BUFFER */
@@ -322,7 +323,13 @@ int gmp_set_params(gmp_ctx *ctx, const gmp_params *params);
 int gmp_get_params(const gmp_ctx *ctx, gmp_params *params);
 
 /* One colony (Algorithm 2 for one origin-destination pair): n_iter iterations of n_ants ants each,
- * then the best route. Synchronous; equivalent to gmp_solve_batch with one query.
+ * then the best route. Each ant (Fig. 3's body for one vehicle) starts at src with a visited set; at each
+ * node it draws the next road among those leading to unvisited nodes by a roulette over tau^alpha *
+ * (1/c)^beta, c = the time the road adds over the remaining lower bound (travel time + signal wait and
+ * queue delay at its head + h(head) - h(here), at least 1 ms). At a node with no such road it steps
+ * back to the previous node of its route (whose clock and wait come back; the node it left stays
+ * visited). It ends at dst, back at src with nothing left, after max_steps moves, or past 2^30 ms.
+ * Synchronous; equivalent to gmp_solve_batch with one query.
  * Errors: INVALID_ARG, UNSUPPORTED, STATE, OOM, CUDA, TIMEOUT; NO_ROUTE / BUFFER via out->status too. */
 int gmp_solve(gmp_ctx *ctx, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha, float beta,
               float rho, uint64_t seed, gmp_result *out);
@@ -363,7 +370,8 @@ int gmp_batch_ready(gmp_ctx *ctx, int *ready);
 int gmp_get_pheromone(gmp_ctx *ctx, uint32_t slot, uint64_t *out_tau);
 
 /* Per-(iteration, ant) log of query `slot` (needs GMP_FLAG_ANT_LOG when the batch ran):
- * n_iter*n_ants*4 entries {status, steps, T, W}; status 0 success, 1 dead end, 2 step cap, 3 time cap.
+ * n_iter*n_ants*4 entries {status | roads in the route << 8, moves, T, W}; status 0 success, 1 dead end
+ * (back at src with no road left), 2 step cap, 3 time cap.
  * Host array of capacity_entries. Errors: INVALID_ARG, STATE (no log), BUFFER (capacity too small), CUDA. */
 int gmp_get_ant_log(gmp_ctx *ctx, uint32_t slot, uint32_t *out, uint64_t capacity_entries);
 
@@ -401,8 +409,8 @@ typedef struct {
  * counterpart: this is for callers that cannot call cudaMalloc while they solve (a loop that must never
  * wait on the allocator, an exhausted memory pool or quota, a framework that owns every allocation).
  * Every temporary lives in a device array of GMP_STATIC_SCRATCH_BYTES that the library defines at file
- * scope; the caller passes the outputs: d_result (one row) and d_route (route_cap >= max_steps + 1
- * entries), both device memory of the context's GPU. The work is issued on the context's stream and
+ * scope; the caller passes the outputs: d_result (one row) and d_route (route_cap >= min(N, max_steps + 1)
+ * entries, the nodes of the longest possible route), both device memory of the context's GPU. The work is issued on the context's stream and
  * the call returns without waiting; synchronise that stream before reading the outputs. The first call
  * on a device looks the array's address up, so make it before any stream capture. Every call reuses the
  * same array (which keeps the previous call's data; each call re-initialises what it needs), so calls
@@ -410,7 +418,7 @@ typedef struct {
  * always in the dense pheromone layout (both layouts give the same results, so tau_layout is not read),
  * in warp lockstep unless the context's parameters turn lockstep off.
  * Errors: INVALID_ARG, UNSUPPORTED, STATE, CUDA; BUFFER when route_cap is short or when the colony's
- * temporaries (about 24 bytes per road plus 4 * n_ants * max_steps bytes) exceed the array. */
+ * temporaries (about 24 bytes per road plus 8 * n_ants * max_steps bytes) exceed the array. */
 int gmp_solve_static(gmp_ctx *ctx, uint32_t src, uint32_t dst, uint32_t n_ants, uint32_t n_iter, float alpha,
                      float beta, float rho, uint64_t seed, gmp_device_result *d_result, uint32_t *d_route,
                      uint32_t route_cap);

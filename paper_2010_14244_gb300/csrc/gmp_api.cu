@@ -418,10 +418,12 @@ bool use_sparse(const gmp_ctx* c) {
     return c->E >= kSparseMinEdges;
 }
 
+// Moves per ant, forward and back: min(2(N - 1), 4096) unless set, the length of a complete
+// depth-first walk over the graph.
 uint32_t default_max_steps(const gmp_ctx* c) {
     if (c->prm.max_steps) return c->prm.max_steps;
-    const uint32_t n1 = c->N > 0 ? c->N - 1 : 0;
-    return n1 < 4096u ? n1 : 4096u;
+    const uint64_t n2 = c->N > 0 ? 2ull * (c->N - 1u) : 0ull;
+    return n2 < 4096u ? (uint32_t)n2 : 4096u;
 }
 
 int pick_lanes(const gmp_ctx* c) {
@@ -566,6 +568,7 @@ ConstructArgs construct_args(gmp_ctx* c) {
     a.dep = b.dep;
     a.qs = b.qs;
     a.routes = b.routes;
+    a.rwait = b.routes + (size_t)b.total_ants * b.max_steps;
     a.ant_steps = b.ant_steps;
     a.ant_wait = b.ant_wait;
     a.ant_log = b.log_entries ? b.ant_log : nullptr;  // sized at staging
@@ -1072,7 +1075,7 @@ int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI
         }
     }
     GMP_TRY(ensure(c, &b.qs, n));
-    GMP_TRY(ensure(c, &b.routes, (size_t)total_ants * max_steps));
+    GMP_TRY(ensure(c, &b.routes, 2 * (size_t)total_ants * max_steps));  // routes, then their waits
     GMP_TRY(ensure(c, &b.ant_steps, (size_t)total_ants));
     GMP_TRY(ensure(c, &b.ant_wait, (size_t)total_ants));
     GMP_TRY(ensure(c, &b.best_route, (size_t)n * max_steps));
@@ -1747,8 +1750,9 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     });
     GMP_CUDA(c, g_static_err[c->device]);
     const uint32_t S = std::max<uint32_t>(default_max_steps(c), 1u);
-    if (route_cap < S + 1u)
-        return fail(c, GMP_ERR_BUFFER, "route buffer needs %u entries (max_steps + 1)", S + 1u);
+    const uint32_t route_need = std::min<uint32_t>(c->N, S + 1u);  // nodes of the longest possible route
+    if (route_cap < route_need)
+        return fail(c, GMP_ERR_BUFFER, "route buffer needs %u entries (min(N, max_steps + 1))", route_need);
     KernelConfig kc{};
     if (!(c->prm.flags & kFlagNoLockstep) && lockstep_fits(lanes, c->maxdeg))
         GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, n_ants,
@@ -1765,7 +1769,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     };
     const size_t o_dq = take(sizeof(DevQuery)), o_prefix = take(8), o_qs = take(sizeof(QueryState));
     const size_t o_tickets = take((size_t)n_iter * 4), o_tau = take(E * 8), o_th = take(E * 8), o_dep = take(E * 8);
-    const size_t o_routes = take((size_t)n_ants * S * 4), o_steps = take((size_t)n_ants * 4);
+    const size_t o_routes = take((size_t)n_ants * S * 8), o_steps = take((size_t)n_ants * 4);  // routes, waits
     const size_t o_wait = take((size_t)n_ants * 4), o_best = take((size_t)S * 4);
     const size_t o_tabu = kc.tabu_in_smem ? 0 : take((size_t)kc.grid * (kc.block / kc.lanes) * words * 4);
     if (off > GMP_STATIC_SCRATCH_BYTES)
@@ -1816,6 +1820,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     a.dep = dep;
     a.qs = qs;
     a.routes = routes;
+    a.rwait = routes + (size_t)n_ants * S;
     a.ant_steps = ant_steps;
     a.ant_wait = ant_wait;
     a.ant_log = nullptr;

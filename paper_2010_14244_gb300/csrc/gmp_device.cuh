@@ -62,7 +62,8 @@ struct __align__(16) QueryState {
     unsigned long long nsucc;     // successful walks
     uint32_t best_len;            // roads in the best route
     uint32_t best_W;              // waits along the best route
-    uint32_t pad[2];
+    uint32_t h_src;               // h(src): the remaining bound where every walk starts
+    uint32_t pad;
     // sparse pheromone layout: every road without a deposit so far holds the same value, the baseline
     unsigned long long base_tau;  // baseline tau of the current iteration (Q32.32)
     uint32_t base_tf;             // its binary32 image (bits)
@@ -267,6 +268,12 @@ __device__ __forceinline__ float score_f(float tf, uint32_t alpha, uint32_t c, u
 
 // The score of a colony: integer exponents by score_f, others (frac) by score_frac with alpha and beta
 // as binary32 bits.
+// Cost of a road in the score: the time it adds over the remaining lower bound, from the sum
+// tt + wait + h(head) (below 2^29) and h of the node the ant stands on; at least 1 ms.
+__device__ __forceinline__ uint32_t reduced_cost(uint32_t c_through, uint32_t h_here) {
+    return c_through > h_here ? c_through - h_here : 1u;
+}
+
 __device__ __forceinline__ float score_q(float tf, uint32_t alpha, uint32_t c, uint32_t beta, bool frac) {
     if (frac) return score_frac(tf, __uint_as_float(alpha), c, __uint_as_float(beta));
     return score_f(tf, alpha, c, beta);

@@ -24,7 +24,10 @@ struct ConstructArgs {
                                  // 2^-32) and the heuristic of the road's head towards the destination
     unsigned long long* dep;     // Q * E deposit accumulators
     QueryState* qs;
-    uint32_t* routes;            // total_ants * max_steps road ids
+    uint32_t* routes;            // total_ants * max_steps road ids: an ant's route from the front; the
+                                 // nodes its steps back left, from the back (route length + steps back
+                                 // <= moves <= max_steps, so the two never meet)
+    uint32_t* rwait;             // total_ants * max_steps: the wait taken at each position of the route
     uint32_t* ant_steps;         // total_ants
     uint32_t* ant_wait;          // total_ants
     uint32_t* ant_log;           // optional: 4 words per (query, iteration, ant)

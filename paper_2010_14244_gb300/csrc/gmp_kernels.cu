@@ -322,7 +322,8 @@ k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restr
         S.nsucc = 0;
         S.best_len = 0;
         S.best_W = 0;
-        S.pad[0] = S.pad[1] = 0;
+        S.h_src = h;
+        S.pad = 0;
         S.base_tau = 1ull << 32;
         S.base_tf = tau_word(1ull << 32, REP ? GMP_FLAG_REPULSIVE : 0u);
         S.n_touched = 0;
@@ -397,12 +398,14 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
     bool frac = false;  // non-integer exponents (FRAC instantiations only): alpha and beta are binary32 bits
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
+    uint32_t len = 0, pops = 0, hu = 0;  // roads in the route, steps back so far, remaining bound at u
     // Philox draws of the next G steps, one per lane: lane l holds the draw of step rb_base + l
     uint32_t rb_base = 0, rb_x = 0, rb_y = 0;
     bool rb_valid = false;
     const uint2* th = a.th;
     float base_tf = 0.0f;  // sparse layout: the colony's baseline pheromone of this iteration
     uint32_t* route = a.routes;
+    uint32_t* rwait = a.rwait;
     bool want = true;  // warp-uniform: some group may need a ticket (at the start, after an ant ended)
     // the next step's candidate loads, issued as soon as the ant moves (software pipelining)
     uint4 p0[K], p1[K];
@@ -448,10 +451,12 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         th = a.th + (size_t)qi * a.n_edges;
                         base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
                         route = a.routes + (size_t)slot * a.max_steps;
+                        rwait = a.rwait + (size_t)slot * a.max_steps;
                         u = src;
                         beg = __ldg(a.row_ptr + u);
                         end = __ldg(a.row_ptr + u + 1);
-                        t = W = steps = 0;
+                        hu = a.qs[qi].h_src;
+                        t = W = steps = len = pops = 0;
                         rb_valid = false;
                         pre = false;
                         if (leader) atomicOr(tabu + (u >> 5), 1u << (u & 31));
@@ -473,10 +478,6 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
         } else if (active && steps == a.max_steps) {
             done = true;
             status = kAntStepCap;
-        }
-        if (active && !done && end == beg) {  // a node without out-roads ends the walk here
-            done = true;
-            status = kAntDeadEnd;
         }
         const bool stepping = active && !done;
         const uint32_t deg = stepping ? end - beg : 0u;
@@ -529,7 +530,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 const uint32_t sw = signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
                 const uint32_t w = (v != dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
                 wv[j] = w;
-                sb[j] = __float_as_uint(score_q(tf[j], alpha, r0[j].z + w + he[j], beta, frac));
+                sb[j] = __float_as_uint(score_q(tf[j], alpha, reduced_cost(r0[j].z + w + he[j], hu), beta, frac));
             }
             constexpr uint32_t kGroupBits = G == 32 ? FULL : ((1u << (G & 31)) - 1u);
             const uint32_t gshift = wl & ~(uint32_t)(G - 1);
@@ -539,7 +540,8 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 if ((g_ok & kGroupBits) && (g_cg & kGroupBits)) cmask &= ~cong;
             }
             const bool has = ((__ballot_sync(FULL, cmask != 0u) >> gshift) & kGroupBits) != 0u;
-            if (stepping && !has) {
+            const bool back = stepping && !has && len > 0u;  // no way on: step back along the route
+            if (stepping && !has && len == 0u) {              // back at src with no road left
                 done = true;
                 status = kAntDeadEnd;
             }
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             for (int i = 0; i < NC; ++i) pick += incl[i] <= r ? 1 : 0;
             pick = min(pick, NC - 1);  // groups without candidates: any in-range slot (result unused)
             const int pick_lane = pick % G, pick_slot = pick / G;
-            uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
+            uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0, c_he = 0;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const bool sel = pick_slot == j;
@@ -576,26 +578,47 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                 c_ve = sel ? r0[j].y + (r1[j].x >> 24) : c_ve;
                 c_tt = sel ? r0[j].z : c_tt;
                 c_w = sel ? wv[j] : c_w;
+                c_he = sel ? he[j] : c_he;
             }
             c_h = __shfl_sync(FULL, c_h, pick_lane, G);
             c_vb = __shfl_sync(FULL, c_vb, pick_lane, G);
             c_ve = __shfl_sync(FULL, c_ve, pick_lane, G);
             c_tt = __shfl_sync(FULL, c_tt, pick_lane, G);
             c_w = __shfl_sync(FULL, c_w, pick_lane, G);
-            if (stepping && !done) {
-                if (leader) {
-                    route[steps] = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
-                    atomicOr(tabu + (c_h >> 5), 1u << (c_h & 31));
-                }
-                t += c_tt + c_w;
-                W += c_w;
-                u = c_h;
-                beg = c_vb;
-                end = c_ve;
+            c_he = __shfl_sync(FULL, c_he, pick_lane, G);
+            if (back) {  // leave u (it stays visited, noted at the back of the route buffer) with its clock
+                if (leader) route[a.max_steps - 1u - pops] = u;
+                ++pops;
+                --len;
+                const uint32_t e_in = route[len], w_in = rwait[len];
+                t -= __ldg(&a.rec[e_in].tt) + w_in;
+                W -= w_in;
+                const StandPoint p = stand_after_back(a, th, route, len, src, qi);
+                u = p.u;
+                beg = p.beg;
+                end = p.end;
+                hu = p.h;
                 ++steps;
-                if (t > kTCap) {
-                    done = true;
-                    status = kAntTimeCap;
+            }
+            if ((stepping && !done) || back) {
+                if (!back) {
+                    if (leader) {
+                        route[len] = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
+                        rwait[len] = c_w;
+                        atomicOr(tabu + (c_h >> 5), 1u << (c_h & 31));
+                    }
+                    t += c_tt + c_w;
+                    W += c_w;
+                    u = c_h;
+                    beg = c_vb;
+                    end = c_ve;
+                    hu = c_he;
+                    ++len;
+                    ++steps;
+                    if (t > kTCap) {
+                        done = true;
+                        status = kAntTimeCap;
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < K; ++j) {  // the rows of the next step, read past the masked slots as road 0
@@ -619,18 +642,18 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             if (done) {
                 QueryState* S = a.qs + qi;
                 if (leader) {
-                    a.ant_steps[slot] = steps;
+                    a.ant_steps[slot] = len;
                     a.ant_wait[slot] = W;
                     atomicAdd(&S->steps, (unsigned long long)steps);
                     if (a.ant_log) {
                         uint32_t* l = a.ant_log + 4ull * (log_base + (uint64_t)it * n_ants + k);
-                        *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
+                        *reinterpret_cast<uint4*>(l) = make_uint4(status | (len << 8), steps, t, W);
                     }
                 }
                 if (status == kAntSuccess) {  // Updt_Pher: deposit ant_deposit() on every road of the route
                     const unsigned long long delta = ant_deposit(S->dep_num, t);
                     unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
-                    for (uint32_t i = lane; i < steps; i += G) {
+                    for (uint32_t i = lane; i < len; i += G) {
                         atomicAdd(D + route[i], delta);
                         if (a.sparse) register_road(a, qi, S, route[i]);
                     }
@@ -639,15 +662,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                         atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * n_ants + k));
                     }
                 }
-                if (a.tabu_words <= 2u * (steps + 1u)) {
-                    for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
-                } else {
-                    if (leader) atomicAnd(tabu + (src >> 5), ~(1u << (src & 31)));
-                    for (uint32_t i = lane; i < steps; i += G) {
-                        const uint32_t v = __ldg(a.col + route[i]);
-                        atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
-                    }
-                }
+                forget_visited(a, tabu, route, src, len, pops, steps, lane, G);
                 active = false;
             }
             __syncwarp();
@@ -683,9 +698,11 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
     bool frac = false;  // non-integer exponents: alpha and beta are binary32 bits
     uint64_t log_base = 0;
     uint32_t u = 0, beg = 0, end = 0, t = 0, W = 0, steps = 0, status = 0;
+    uint32_t len = 0, hu = 0;  // roads in the route, remaining bound at u
     const uint2* th = a.th;
     float base_tf = 0.0f;  // sparse layout: the colony's baseline pheromone of this iteration
     uint32_t* route = a.routes;
+    uint32_t* rwait = a.rwait;
     const uint32_t n_threads = gridDim.x * blockDim.x;
     for (;;) {
         // 1. threads without an ant take the next ticket (the first one statically, no atomic)
@@ -730,10 +747,12 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                         th = a.th + (size_t)qi * a.n_edges;
                         base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
                         route = a.routes + (size_t)slot * a.max_steps;
+                        rwait = a.rwait + (size_t)slot * a.max_steps;
                         u = src;
                         beg = __ldg(a.row_ptr + u);
                         end = __ldg(a.row_ptr + u + 1);
-                        t = W = steps = 0;
+                        hu = a.qs[qi].h_src;
+                        t = W = steps = len = 0;
                         tw[tabu_index(u >> 5, lane)] |= 1u << (u & 31);
                     }
                 }
@@ -750,13 +769,12 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
             done = true;
             status = kAntStepCap;
         }
-        if (active && !done && end == beg) {  // a node without out-roads ends the walk here
-            done = true;
-            status = kAntDeadEnd;
-        }
         const bool stepping = active && !done;
         const uint32_t deg = stepping ? end - beg : 0u;
         const uint32_t wmax = __reduce_max_sync(FULL, deg);
+        uint32_t cmask = 0;  // candidates of this thread's ant (none when every row of the warp is empty)
+        int js = 0;
+        uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0, c_he = 0;
         if (wmax > 0u) {
             uint4 r0[K], r1[K];
             float tf[K];
@@ -779,7 +797,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
             }
             const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
             const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-            uint32_t cmask = 0, cong = 0;
+            uint32_t cong = 0;
             uint32_t sb[K], wv[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) {
@@ -793,14 +811,10 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                         signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
                     const uint32_t w = (v != dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
                     wv[j] = w;
-                    sb[j] = __float_as_uint(score_q(tf[j], alpha, r0[j].z + w + he[j], beta, frac));
+                    sb[j] = __float_as_uint(score_q(tf[j], alpha, reduced_cost(r0[j].z + w + he[j], hu), beta, frac));
                 }
             }
             if (a.thr_on && (cmask & ~cong) && (cmask & cong)) cmask &= ~cong;
-            if (stepping && cmask == 0u) {
-                done = true;
-                status = kAntDeadEnd;
-            }
             uint32_t mb = 0;
 #pragma unroll
             for (int j = 0; j < K; ++j) mb = max(mb, (cmask >> j & 1u) ? sb[j] : 0u);
@@ -812,7 +826,6 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 incl[j] = S;
             }
             const uint32_t r = draw_index(rnd, S);
-            int js = 0;
             bool found = false;
 #pragma unroll
             for (int j = 0; j < K; ++j) {  // first candidate whose running weight exceeds r
@@ -820,7 +833,6 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 js = hit ? j : js;
                 found |= hit;
             }
-            uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const bool sel = js == j;
@@ -829,20 +841,40 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 c_ve = sel ? r0[j].y + (r1[j].x >> 24) : c_ve;
                 c_tt = sel ? r0[j].z : c_tt;
                 c_w = sel ? wv[j] : c_w;
+                c_he = sel ? he[j] : c_he;
             }
-            if (stepping && !done) {
-                route[steps] = beg + (uint32_t)js;
-                t += c_tt + c_w;
-                W += c_w;
-                u = c_h;
-                beg = c_vb;
-                end = c_ve;
-                tw[tabu_index(u >> 5, lane)] |= 1u << (u & 31);
+        }
+        if (stepping && cmask == 0u) {
+            if (len == 0u) {  // back at src with no road left
+                done = true;
+                status = kAntDeadEnd;
+            } else {  // step back along the route with the clock it had there (u stays visited)
+                --len;
+                const uint32_t e_in = route[len], w_in = rwait[len];
+                t -= __ldg(&a.rec[e_in].tt) + w_in;
+                W -= w_in;
+                const StandPoint p = stand_after_back(a, th, route, len, src, qi);
+                u = p.u;
+                beg = p.beg;
+                end = p.end;
+                hu = p.h;
                 ++steps;
-                if (t > kTCap) {
-                    done = true;
-                    status = kAntTimeCap;
-                }
+            }
+        } else if (stepping) {
+            route[len] = beg + (uint32_t)js;
+            rwait[len] = c_w;
+            t += c_tt + c_w;
+            W += c_w;
+            u = c_h;
+            beg = c_vb;
+            end = c_ve;
+            hu = c_he;
+            tw[tabu_index(u >> 5, lane)] |= 1u << (u & 31);
+            ++len;
+            ++steps;
+            if (t > kTCap) {
+                done = true;
+                status = kAntTimeCap;
             }
         }
         // 3. ants that ended: per-ant records by their own lane, deposits and bitmap reset by the warp
@@ -851,12 +883,12 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
             unsigned long long delta = 0;
             if (done) {
                 QueryState* S = a.qs + qi;
-                a.ant_steps[slot] = steps;
+                a.ant_steps[slot] = len;
                 a.ant_wait[slot] = W;
                 atomicAdd(&S->steps, (unsigned long long)steps);
                 if (a.ant_log) {
                     uint32_t* l = a.ant_log + 4ull * (log_base + (uint64_t)it * n_ants + k);
-                    *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
+                    *reinterpret_cast<uint4*>(l) = make_uint4(status | (len << 8), steps, t, W);
                 }
                 if (status == kAntSuccess) {
                     atomicAdd(&S->nsucc, 1ull);
@@ -869,7 +901,7 @@ __global__ void __launch_bounds__(64) k_construct_lock(ConstructArgs a, uint32_t
                 const int f = __ffs(fmask) - 1;
                 fmask &= fmask - 1u;
                 const unsigned long long fd = __shfl_sync(FULL, delta, f);
-                const uint32_t fsteps = __shfl_sync(FULL, steps, f);
+                const uint32_t fsteps = __shfl_sync(FULL, len, f);
                 const uint32_t fqi = __shfl_sync(FULL, qi, f);
                 const uint32_t fslot = __shfl_sync(FULL, slot, f);
                 if (fd) {  // Updt_Pher: deposit ant_deposit() on every road of the route

@@ -205,11 +205,60 @@ __device__ __forceinline__ void register_road(const ConstructArgs& a, uint32_t q
     a.list_tau[(size_t)qi * a.n_edges + idx] = S->base_tau;
 }
 
+// Where an ant stands after stepping back to position `len` of its route (len > 0: the head of road
+// route[len - 1]; len = 0: src): the node, its CSR row and its remaining bound h. Every lane of the
+// group reads the same words; route[] was written by the group's lane 0 before a __syncwarp.
+struct StandPoint {
+    uint32_t u, beg, end, h;
+};
+__device__ __forceinline__ StandPoint stand_after_back(const ConstructArgs& a, const uint2* th, const uint32_t* route,
+                                                       uint32_t len, uint32_t src, uint32_t qi) {
+    StandPoint p;
+    if (len == 0u) {
+        p.u = src;
+        p.beg = __ldg(a.row_ptr + src);
+        p.end = __ldg(a.row_ptr + src + 1);
+        p.h = a.qs[qi].h_src;
+    } else {
+        const uint32_t e = route[len - 1u];
+        const uint4 r = __ldg(reinterpret_cast<const uint4*>(a.rec + e));
+        const uint32_t cd = __ldg(&a.rec[e].cyc_deg);
+        p.u = r.x;
+        p.beg = r.y;
+        p.end = r.y + (cd >> 24);
+        p.h = __ldg(&th[e].y);
+    }
+    return p;
+}
+
+// Bits of the nodes a finished walk visited, cleared so the bitmap is clean for the next ant: the whole
+// bitmap when that is cheaper, else src, the heads of the route's roads and the nodes its steps back left
+// (kept at the back of the route buffer).
+__device__ __forceinline__ void forget_visited(const ConstructArgs& a, uint32_t* tabu, const uint32_t* route,
+                                               uint32_t src, uint32_t len, uint32_t pops, uint32_t moves,
+                                               uint32_t lane, uint32_t G) {
+    if (a.tabu_words <= 2u * (moves + 1u)) {
+        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
+        return;
+    }
+    if (lane == 0) atomicAnd(tabu + (src >> 5), ~(1u << (src & 31)));
+    for (uint32_t i = lane; i < len; i += G) {
+        const uint32_t v = __ldg(a.col + route[i]);
+        atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
+    }
+    for (uint32_t i = lane; i < pops; i += G) {
+        const uint32_t v = route[a.max_steps - 1u - i];
+        atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Ant construction. G lanes of a warp serve one ant (sub-warp group); lane l holds the candidates
 // l, l+G, ..., l+(K-1)G of the current node's CSR row. Per step: one round of independent 16-byte
 // record loads and pheromone loads, scores, a group max, integer weights, a shuffle prefix sum,
-// one Philox draw, a ballot to find the chosen road and shuffles to broadcast it.
+// one Philox draw, a ballot to find the chosen road and shuffles to broadcast it. At a node with no
+// candidate the ant steps back to the previous node of its route (its clock and wait come back; the node
+// it leaves stays visited and is noted at the back of the route buffer).
 // Groups take ants from a per-iteration ticket counter, so short walks free lanes for waiting ants.
 // ------------------------------------------------------------------------------------------------
 template <int G, int K>
@@ -222,10 +271,12 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     const bool frac = (q.active & kQueryFracExp) != 0u;
     const uint32_t slot = q.ant_base + k;
     uint32_t* route = a.routes + (size_t)slot * a.max_steps;
+    uint32_t* rwait = a.rwait + (size_t)slot * a.max_steps;
     const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
     uint32_t u = q.src;
     uint32_t beg = __ldg(a.row_ptr + u), end = __ldg(a.row_ptr + u + 1);
-    uint32_t t = 0, W = 0, steps = 0, status;
+    uint32_t hu = a.qs[qi].h_src;  // remaining bound where the ant stands
+    uint32_t t = 0, W = 0, steps = 0, len = 0, pops = 0, status;
     if (lane == 0) atomicOr(tabu + (u >> 5), 1u << (u & 31));
     __syncwarp(gmask);
     for (;;) {
@@ -257,7 +308,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             tf[j] = ph.x ? __uint_as_float(ph.x) : base_tf;  // 0: the road still holds the baseline
             he[j] = ph.y;
         }
-        // 2. the draw of this step depends on (iteration, ant, step) only: overlaps the loads
+        // 2. the draw of this step depends on (iteration, ant, move) only: overlaps the loads
         const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
         const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
         // 3. candidates, waits, scores
@@ -272,19 +323,36 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             const uint32_t sw = signal_wait(a.t_dep + t + r0[j].z, cy | (cy == 0u), r1[j].w, r1[j].y, r1[j].z);
             const uint32_t w = (v != q.dst && cy != 0u) ? sw + (r0[j].w & kQdMask) : 0u;
             wv[j] = w;
-            sb[j] = __float_as_uint(score_q(tf[j], q.alpha, r0[j].z + w + he[j], q.beta, frac));
+            sb[j] = __float_as_uint(score_q(tf[j], q.alpha, reduced_cost(r0[j].z + w + he[j], hu), q.beta, frac));
         }
         if (a.thr_on) {  // congested roads drop out unless every candidate is congested
             const uint32_t any_ok = __ballot_sync(gmask, (cmask & ~cong) != 0u) & gmask;
             const uint32_t any_cg = __ballot_sync(gmask, (cmask & cong) != 0u) & gmask;
             if (any_ok && any_cg) cmask &= ~cong;
         }
-        int pick_lane, pick_slot;
-        if constexpr (kGather) {
-            if ((__ballot_sync(gmask, cmask != 0u) & gmask) == 0u) {
+        if ((__ballot_sync(gmask, cmask != 0u) & gmask) == 0u) {
+            if (len == 0) {  // back at src with no road left
                 status = kAntDeadEnd;
                 break;
             }
+            // step back: leave u (it stays visited), return to the tail of route[len - 1] with its clock
+            if (lane == 0) route[a.max_steps - 1u - pops] = u;
+            ++pops;
+            --len;
+            const uint32_t e_in = route[len], w_in = rwait[len];
+            t -= __ldg(&a.rec[e_in].tt) + w_in;
+            W -= w_in;
+            const StandPoint p = stand_after_back(a, th, route, len, q.src, qi);
+            u = p.u;
+            beg = p.beg;
+            end = p.end;
+            hu = p.h;
+            ++steps;
+            __syncwarp(gmask);
+            continue;
+        }
+        int pick_lane, pick_slot;
+        if constexpr (kGather) {
             // 4. largest candidate score of the group (non-negative floats order like their bits)
             uint32_t mb = 0;
 #pragma unroll
@@ -313,10 +381,6 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             pick_lane = pick % G;
             pick_slot = pick / G;
         } else {
-            if ((__ballot_sync(gmask, cmask != 0u) & gmask) == 0u) {
-                status = kAntDeadEnd;
-                break;
-            }
             // 4. largest score of the group (non-negative floats order like their bit patterns)
             uint32_t mb = 0;
 #pragma unroll
@@ -354,7 +418,7 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             pick_slot = __shfl_sync(gmask, js, pick_lane, G);
         }
         // 6. the chosen candidate's data from the lane that evaluated it
-        uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0;
+        uint32_t c_h = 0, c_vb = 0, c_ve = 0, c_tt = 0, c_w = 0, c_he = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j)
             if (pick_slot == j) {
@@ -363,12 +427,14 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
                 c_ve = r0[j].y + (r1[j].x >> 24);
                 c_tt = r0[j].z;
                 c_w = wv[j];
+                c_he = he[j];
             }
         c_h = __shfl_sync(gmask, c_h, pick_lane, G);
         c_vb = __shfl_sync(gmask, c_vb, pick_lane, G);
         c_ve = __shfl_sync(gmask, c_ve, pick_lane, G);
         c_tt = __shfl_sync(gmask, c_tt, pick_lane, G);
         c_w = __shfl_sync(gmask, c_w, pick_lane, G);
+        c_he = __shfl_sync(gmask, c_he, pick_lane, G);
         // 7. position update
         const uint32_t e = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
         t += c_tt + c_w;
@@ -376,10 +442,13 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         u = c_h;
         beg = c_vb;
         end = c_ve;
+        hu = c_he;
         if (lane == 0) {
-            route[steps] = e;
+            route[len] = e;
+            rwait[len] = c_w;
             atomicOr(tabu + (u >> 5), 1u << (u & 31));
         }
+        ++len;
         ++steps;
         __syncwarp(gmask);
         if (t > kTCap) {
@@ -389,34 +458,25 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     }
     QueryState* S = a.qs + qi;
     if (lane == 0) {
-        a.ant_steps[slot] = steps;
+        a.ant_steps[slot] = len;
         a.ant_wait[slot] = W;
         atomicAdd(&S->steps, (unsigned long long)steps);
         if (status == kAntSuccess) atomicAdd(&S->nsucc, 1ull);
         if (a.ant_log) {
             uint32_t* l = a.ant_log + 4ull * (q.log_base + (uint64_t)it * q.n_ants + k);
-            *reinterpret_cast<uint4*>(l) = make_uint4(status, steps, t, W);
+            *reinterpret_cast<uint4*>(l) = make_uint4(status | (len << 8), steps, t, W);
         }
     }
     if (status == kAntSuccess) {  // Updt_Pher: deposit ant_deposit() on every road of the route
         const unsigned long long delta = ant_deposit(S->dep_num, t);
         unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
-        for (uint32_t i = lane; i < steps; i += G) {
+        for (uint32_t i = lane; i < len; i += G) {
             atomicAdd(D + route[i], delta);
             if (a.sparse) register_road(a, qi, S, route[i]);
         }
         if (lane == 0) atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * q.n_ants + k));
     }
-    // forget the visited set: whole bitmap when small, else just the nodes of this walk
-    if (a.tabu_words <= 2u * (steps + 1u)) {
-        for (uint32_t w = lane; w < a.tabu_words; w += G) tabu[w] = 0;
-    } else {
-        if (lane == 0) atomicAnd(tabu + (q.src >> 5), ~(1u << (q.src & 31)));
-        for (uint32_t i = lane; i < steps; i += G) {
-            const uint32_t v = __ldg(a.col + route[i]);
-            atomicAnd(tabu + (v >> 5), ~(1u << (v & 31)));
-        }
-    }
+    forget_visited(a, tabu, route, q.src, len, pops, steps, lane, G);
     __syncwarp(gmask);
 }
 

@@ -2,9 +2,9 @@
 sets in global memory, 16 concurrent chains, sparse pheromone). Every colony is re-solved by the oracle
 (a pool of spawned processes over the host cores) and must agree bit for bit: status, best route, travel
 and wait times, ant-step and success counts, best (iteration, ant) and the final pheromone table (by
-digest). Every route found is also checked for validity. (On this sparse planar graph with 20-400 hop
-pairs most ants end in dead ends under the simple-path rule, so few colonies find a route. The counts of
-steps and successes and the pheromone tables still pin the whole walk.)"""
+digest). Every route found is also checked for validity, and at least 90 % of the colonies must find
+one: ants step back out of dead ends, so on this sparse planar graph (20-400 hop pairs, 8 % of nodes
+with one road out) nearly every ant reaches its destination."""
 import numpy as np
 import pytest
 
@@ -56,4 +56,6 @@ def test_geo100k_full_size_full_parity(gm):
     for qi, o in oracle:
         oracle_pool.check(res[qi], o)
         assert digests[qi] == o["tau_sha256"], qi
-    assert sum(r["status"] == 0 for r in res) > 0
+    routed = sum(r["status"] == 0 for r in res)
+    assert routed >= 0.9 * N_COLONIES, routed
+    assert sum(r["n_success"] for r in res) >= 0.5 * sum(q.n_ants * q.n_iter for q in wl.queries)

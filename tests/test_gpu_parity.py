@@ -258,7 +258,7 @@ def test_edge_cases(gm, ctx, orc):
     ctx.set_signals(sig)
     ctx.set_densities(veh)
     r = ctx.solve(0, 3, 8, 3)
-    assert r["status"] == gm.ERR_NO_ROUTE and r["ant_steps"] == 3 * 8 * 2
+    assert r["status"] == gm.ERR_NO_ROUTE and r["ant_steps"] == 3 * 8 * 4  # 0 -> 1 -> 2, back, back
     r = ctx.solve(2, 2, 8, 3)
     assert r["status"] == 0 and list(r["route"]) == [2] and r["travel_ms"] == 0 and r["ant_steps"] == 0
     r = ctx.solve(0, 2, 8, 3, route_cap=2)
