@@ -307,9 +307,9 @@ def test_memory_budget(gm, orc):
 
 @pytest.mark.parametrize("sched", ["lanes1", "lanes4", "lanes8", "lanes16", "lanes32", "persistent"])
 def test_directed_graph_with_sinks(gm, ctx, orc, sched):
-    """One-way roads and nodes without out-roads: ants that reach a sink end as dead ends (Fig. 3 gives
-    an ant no way out of such a node), under every kernel shape, including warps whose every ant sits at
-    a sink in the same step."""
+    """One-way roads and nodes without out-roads: an ant that reaches a sink steps back along its route,
+    under every kernel shape, including warps whose every ant sits at a sink in the same step. The
+    per-ant logs (status, route length, moves, T, W) agree with the oracle's."""
     rng = np.random.default_rng(17)
     roads = []
     for u in range(45):
@@ -323,13 +323,16 @@ def test_directed_graph_with_sinks(gm, ctx, orc, sched):
     ctx.set_signals(sig)
     ctx.set_densities(veh)
     kw = dict(mode=2, lanes_per_ant=8) if sched == "persistent" else dict(mode=1, lanes_per_ant=int(sched[5:]))
-    ctx.set_params(**kw)
+    ctx.set_params(flags=gm.FLAG_ANT_LOG, **kw)
     qs = [Q(s, d, 48, 5, 1.0, 2.0, 0.1, 100 + i) for i, (s, d) in enumerate([(0, 50), (3, 44), (7, 59), (10, 20)])]
     res = ctx.solve_batch(qs)
     onet = orc.Net(net, sig, veh)
+    backs = 0
     for i, q in enumerate(qs):
-        o = _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
-        assert o["n_success"] < q.n_ants * q.n_iter  # some ants die at sinks or dead ends
+        o = _compare(orc, onet, orc.Params(), q, res[i], ctx, i, ctx.ant_log(i))
+        _, length, moves, _, _ = orc.log_fields(o["log"])
+        backs += int((moves - length).sum()) // 2
+    assert backs > 0  # ants stepped back out of sinks and dead ends
 
 
 def test_sparse_layout_refusals(gm, ctx):
