@@ -151,55 +151,99 @@ def max_over_ranks(x: float, world: int) -> float:
 
 # ------------------------------------------------------------------------------------------ CPU oracle
 _WL = None
+_WL_NAME = None
 
 
-def _pool_init():
-    global _WL
-    _WL = workload()
+def _make_workload(name):
+    from paper_2010_14244_gb300 import workloads
+
+    if name == "grid64":
+        return workload()
+    if name == "geo100k":
+        return workloads.geo100k()
+    if name == "city_batch":
+        return workloads.city_batch()
+    if name == "geo1m":
+        return workloads.geo1m_serving()
+    raise ValueError(name)
 
 
-def _pool_solve(qi):
+def _pool_init(name="grid64"):
+    global _WL, _WL_NAME
+    _WL_NAME = name
+    _WL = _make_workload(name)
+
+
+def _pool_query(item):
+    """item: a colony index; (graph, colony) for the city batch; ("req", i) for a serving request."""
+    if _WL_NAME == "city_batch":
+        g, qi = item
+        return _WL[g], _WL[g].queries[qi]
+    if _WL_NAME == "geo1m":  # request i of the serving stream (the stream draws its pairs in order)
+        from paper_2010_14244_gb300 import serving
+
+        make = serving.uniform_requests(_WL.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
+        return _WL, [make(j) for j in range(item[1] + 1)][-1]
+    return _WL, _WL.queries[item]
+
+
+_ONETS = {}
+
+
+def _pool_solve(item):
     from oracle import oracle as orc
 
-    r = orc.solve_workload_query(_WL, qi, want_tau=False)
-    return r["ant_steps"], r["status"]
+    wl, q = _pool_query(item)
+    if id(wl) not in _ONETS:
+        _ONETS[id(wl)] = orc.Net.from_workload(wl)
+    r = orc.solve(_ONETS[id(wl)], orc.Params(), q, want_tau=False)
+    return r["ant_steps"], r["status"], r["n_success"], q.n_ants * q.n_iter
 
 
-def oracle_run(pool, n_queries):
+def oracle_run(pool, items):
     t0 = time.perf_counter()
-    out = pool.map(_pool_solve, range(n_queries))
+    out = pool.map(_pool_solve, items, chunksize=1)
     dt = time.perf_counter() - t0
-    return sum(s for s, _ in out), dt
+    return out, dt
 
 
-def make_pool():
+def make_pool(name="grid64", want=16):
     import multiprocessing as mp
 
-    cores = len(os.sched_getaffinity(0))
-    return mp.get_context("spawn").Pool(min(cores, 16), initializer=_pool_init), min(cores, 16)
+    cores = min(len(os.sched_getaffinity(0)), want)
+    return mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(name,)), cores
 
 
-def _one_core_solve(qi):
+def _one_core_solve(item):
     t0 = time.perf_counter()
-    steps, _ = _pool_solve(qi)
-    return steps, time.perf_counter() - t0
+    steps, status, *_ = _pool_solve(item)
+    return steps, status, time.perf_counter() - t0
 
 
-def cpu_baseline_line(n_queries):
-    pool, cores = make_pool()
+def oracle_baseline(name, items, what):
+    """The oracle as it stands on the host cores, on a bounded sample of a workload: one warm-up pass (the
+    workers build the workload and load the oracle), then the timed pass, one colony per process."""
+    pool, cores = make_pool(name, len(items))
     try:
-        steps, dt = oracle_run(pool, n_queries)
-        # one colony alone in one process (one core), the same oracle
-        one_steps, one_dt = pool.apply(_one_core_solve, (0,))
+        oracle_run(pool, items[:cores])  # warm-up: workers build the workload and load the library
+        out, dt = oracle_run(pool, items)
+        one_steps, _, one_dt = pool.apply(_one_core_solve, (items[0],))
     finally:
         pool.close()
         pool.join()
+    steps = sum(o[0] for o in out)
+    routed = sum(o[1] == 0 for o in out)
     return {"value": steps / dt, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"all {n_queries} colonies of the workload (full size), one colony per process, "
-                      f"{cores} processes, {dt:.1f} s wall",
-            "queries_per_s": n_queries / dt,
+            "sample": f"{what}: {len(items)} colonies, one per process over {cores} processes, after a warm-up "
+                      f"pass; {dt:.1f} s wall",
+            "queries_per_s": len(items) / dt, "routed_queries_per_s": routed / dt,
+            "success_fraction": sum(o[2] for o in out) / max(1, sum(o[3] for o in out)),
             "one_core": {"value": one_steps / one_dt, "unit": "ant-steps/s", "queries_per_s": 1.0 / one_dt,
-                         "sample": f"colony 0 of the workload alone in one process, {one_dt:.2f} s"}}
+                         "sample": f"the first colony of the sample alone in one process, {one_dt:.2f} s"}}
+
+
+def cpu_baseline_line(n_queries):
+    return oracle_baseline("grid64", list(range(n_queries)), f"all {n_queries} colonies of the workload, full size")
 
 
 def run_reference(args, rank, world):
@@ -208,13 +252,15 @@ def run_reference(args, rank, world):
     wl = workload()
     nq = len(wl.queries)
     pool, cores = make_pool()
+    routed = 0
     try:
         for _ in range(args.warmup):
-            oracle_run(pool, nq)
+            oracle_run(pool, list(range(nq)))
         tot_steps, tot_t = 0, 0.0
         for _ in range(args.steps):
-            s, dt = oracle_run(pool, nq)
-            tot_steps += s
+            out, dt = oracle_run(pool, list(range(nq)))
+            tot_steps += sum(o[0] for o in out)
+            routed += sum(o[1] == 0 for o in out)
             tot_t += dt
     finally:
         pool.close()
@@ -224,19 +270,62 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
             "data": "synthetic", "config": workload_config(wl),
-            "queries_per_s": nq * args.steps / tot_t,
+            "queries_per_s": nq * args.steps / tot_t, "routed_queries_per_s": routed / tot_t,
             "cpu_baseline": {"value": v, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: all {nq} colonies at full size over {cores} processes"},
             "e2e": {"value": v, "unit": "ant-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------------------------------ serving
+# ------------------------------------------------------------------------------------------ legs
 SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S, SERVE_MAX_BATCH = 16, 5000.0, 2.0, 0.5, 64
 SERVE_ANTS, SERVE_ITERS = 128, 30
 
 
-def geo100k_leg():
+def bytes_per_ant_step(n_nodes, n_edges):
+    """Algorithmic bytes of one construction step: the row bounds (8) and per candidate its 32-byte road
+    record, its 8-byte pheromone/heuristic pair and the head's 16-byte signal window (d = E/N candidates),
+    plus the route write (4): 12 + 56 d."""
+    return 12.0 + 56.0 * n_edges / n_nodes
+
+
+def routed_summary(results, queries, seconds):
+    """Colonies that found a route per second, and what fraction of colonies and ant walks succeeded."""
+    routed = int(sum(r["status"] == 0 for r in results))
+    walks = sum(q.n_ants * q.n_iter for q in queries)
+    return {"routed": routed, "routed_queries_per_s": routed / seconds, "routed_fraction": routed / max(1, len(results)),
+            "success_fraction": sum(int(r["n_success"]) for r in results) / max(1, walks)}
+
+
+def leg_roofline(bpa, steps, seconds, peak, peak_kind, what):
+    achieved = bpa * steps / seconds / 1e9
+    return {"bound": "hbm", "kernel": "construct", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None, "bytes_per_ant_step": bpa,
+            "time": what}
+
+
+def timed_launches(launch, stream, n_warm=2, n_timed=3):
+    """Median device time (ms) of a launch callable on `stream`, L2 flushed before each timed launch."""
+    import torch
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    times = []
+    with torch.cuda.stream(stream):
+        for _ in range(n_warm):
+            launch()
+        stream.synchronize()
+        for _ in range(n_timed):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def geo100k_leg(with_cpu):
     """The batched job on the 100k-node planar graph: 512 colonies x 256 ants x 100 iterations in one job
     (autotuned schedule; the sparse pheromone layout applies at this size)."""
     import torch
@@ -250,32 +339,66 @@ def geo100k_leg():
         ctx.load_workload(wl)
         tune = ctx.autotune(wl.queries, probe_iter=8)
         ctx.stage(wl.queries)
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        times = []
-        with torch.cuda.stream(stream):
-            for _ in range(2):
-                ctx.launch()
-            stream.synchronize()
-            for _ in range(3):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                ctx.launch()
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
+        ms = timed_launches(ctx.launch, stream)
         res = ctx.collect()
     finally:
         ctx.close()
-    ms = statistics.median(times)
     steps = sum(r["ant_steps"] for r in res)
-    return {"workload": "geo100k: 100k-node planar graph, 280k roads, 512 OD colonies x 256 ants x 100 iterations",
-            "ms_per_job": ms, "ant_steps_per_s": steps / (ms / 1e3), "queries_per_s": len(res) / (ms / 1e3),
-            "routes_found": int(sum(r["status"] == 0 for r in res)),
-            "schedule": {k: tune[k] for k in ("lanes_per_ant", "mode", "branches", "lockstep")}}
+    peak, kind = peaks()
+    out = {"workload": f"geo100k: 100k-node planar graph, {wl.net.n_edges} roads, 512 OD colonies x 256 ants x "
+                       "100 iterations", "ms_per_job": ms, "ant_steps_per_job": steps,
+           "ant_steps_per_s": steps / (ms / 1e3), "queries_per_s": len(res) / (ms / 1e3),
+           **routed_summary(res, wl.queries, ms / 1e3),
+           "roofline": leg_roofline(bytes_per_ant_step(wl.net.n_nodes, wl.net.n_edges), steps, ms / 1e3, peak, kind,
+                                    "job device time, median of 3, L2 flushed"),
+           "schedule": {k: tune[k] for k in ("lanes_per_ant", "mode", "branches", "lockstep")}}
+    if with_cpu:
+        out["cpu_baseline"] = oracle_baseline("geo100k", list(range(0, 512, 32)),
+                                              "every 32nd colony of the same job, full size")
+    return out
 
 
-def serving_leg_1m():
+def city_batch_leg(with_cpu):
+    """64 independent city graphs (1k-200k nodes) with all their colonies in one launch, 50 iterations."""
+    import torch
+
+    from paper_2010_14244_gb300 import gmacop, workloads
+
+    cities = workloads.city_batch()
+    stream = torch.cuda.Stream()
+    ctxs = []
+    m = gmacop.Multi(0)
+    try:
+        for wl in cities:
+            c = gmacop.Context(0, stream=stream)
+            c.load_workload(wl)
+            c.stage(wl.queries)
+            ctxs.append(c)
+        ms = timed_launches(lambda: m.launch(ctxs), stream)
+        res = [c.collect() for c in ctxs]
+    finally:
+        m.close()
+        for c in ctxs:
+            c.close()
+    flat = [r for rs in res for r in rs]
+    queries = [q for wl in cities for q in wl.queries]
+    steps = sum(r["ant_steps"] for r in flat)
+    n_nodes = sum(wl.net.n_nodes for wl in cities)
+    n_edges = sum(wl.net.n_edges for wl in cities)
+    peak, kind = peaks()
+    out = {"workload": f"city batch: 64 planar city graphs, {n_nodes} nodes, {n_edges} roads, {len(flat)} colonies "
+                       "of 128-1024 ants x 50 iterations, one launch", "ms_per_job": ms, "ant_steps_per_job": steps,
+           "ant_steps_per_s": steps / (ms / 1e3), "queries_per_s": len(flat) / (ms / 1e3),
+           **routed_summary(flat, queries, ms / 1e3),
+           "roofline": leg_roofline(bytes_per_ant_step(n_nodes, n_edges), steps, ms / 1e3, peak, kind,
+                                    "job device time, median of 3, L2 flushed")}
+    if with_cpu:
+        items = [(g, 0) for g in range(0, 64, 4)]
+        out["cpu_baseline"] = oracle_baseline("city_batch", items, "the first colony of every 4th city, full size")
+    return out
+
+
+def serving_leg_1m(with_cpu):
     """Route requests on a 1M-node planar road graph with 5M vehicles: Poisson arrivals at 20k req/s with
     uniform origin-destination pairs, 128 ants x 30 iterations each, 1 s traffic ticks, 16 slots."""
     from paper_2010_14244_gb300 import serving, workloads
@@ -291,9 +414,15 @@ def serving_leg_1m():
         for c in slots:
             c.close()
     out = rep.summary()
+    peak, kind = peaks()
     out.update(slots=16, ants=SERVE_ANTS, iterations=SERVE_ITERS, arrivals="poisson, uniform OD",
                network=f"{wl.net.n_nodes} nodes, {wl.net.n_edges} roads, 5M vehicles",
-               tick="1 s (queue/preemption update with vehicle discharge)")
+               tick="1 s (queue/preemption update with vehicle discharge)",
+               roofline=leg_roofline(bytes_per_ant_step(wl.net.n_nodes, wl.net.n_edges), rep.ant_steps,
+                                     rep.window_s, peak, kind, "serving window (wall time)"))
+    if with_cpu:
+        out["cpu_baseline"] = oracle_baseline("geo1m", [("req", i) for i in range(16)],
+                                              "the first 16 requests of the stream, against the traffic at clock 0")
     return out
 
 
@@ -376,7 +505,6 @@ def run_gpu(args, rank, world, local_rank):
     times, _ = timed_region(0)
     clocks = sampler.stop()
     res = ctx.collect()
-    assert all(r["status"] == gmacop.OK for r in res), [r["status"] for r in res]
     steps_per_job = sum(r["ant_steps"] for r in res)
     launches = ctx.launch_count()
     # timed region 2: the same job with event records around every kernel (per-kernel durations)
@@ -390,7 +518,7 @@ def run_gpu(args, rank, world, local_rank):
     # another; the slowest colony bounds the job
     ctx.set_params(**dict(sched, flags=sched["flags"] | gmacop.FLAG_ANT_LOG))
     ctx.solve_batch(wl.queries)
-    longest = [int(ctx.ant_log(i)[:, :, 1].max(axis=1).sum()) for i in range(nq)]
+    longest = [int(ctx.ant_log(i)[:, :, 1].max(axis=1).sum()) for i in range(nq)]  # moves of the longest walk
     crit_steps = max(longest)
     slow = int(np.argmax(longest))
     # the slowest colony alone, as its own job in the same schedule (not timed with the rest): its walks are
@@ -426,11 +554,11 @@ def run_gpu(args, rank, world, local_rank):
             ctx.solve_batch(wl.queries[:1])  # warm (captures the one-colony job graph)
             stream.synchronize()
             t0 = time.perf_counter()
-            plain_steps = 0
-            for q in wl.queries:
-                plain_steps += ctx.solve_batch([q])[0]["ant_steps"]
+            plain_res = [ctx.solve_batch([q])[0] for q in wl.queries]
             plain_t = time.perf_counter() - t0
+        plain_steps = sum(r["ant_steps"] for r in plain_res)
         plain = {"queries_per_s": nq / plain_t, "ant_steps_per_s": plain_steps / plain_t, "ms": plain_t * 1e3,
+                 **routed_summary(plain_res, wl.queries, plain_t),
                  "how": f"the same {nq} colonies, each solved as its own job (stage, launch, collect) in sequence"}
 
     # end to end through the public API: densities and queries from pinned host memory, results back
@@ -438,7 +566,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_e2e:
         veh = torch.from_numpy(wl.vehicles.astype(np.uint32)).pin_memory()
         veh_np = veh.numpy()
-        e2e_t, e2e_steps, d2h = 0.0, 0, 0
+        e2e_t, e2e_steps, d2h, e2e_routed = 0.0, 0, 0, 0
         ctx.set_params(**sched)
         with torch.cuda.stream(stream):
             ctx.set_densities(veh_np)
@@ -451,10 +579,11 @@ def run_gpu(args, rank, world, local_rank):
                 out = ctx.solve_batch(wl.queries)
                 e2e_t += time.perf_counter() - t0
                 e2e_steps += sum(r["ant_steps"] for r in out)
+                e2e_routed += sum(r["status"] == gmacop.OK for r in out)
                 d2h = nq * 48 + sum(4 * r["route_len"] for r in out)
         e2e = {"value": e2e_steps / e2e_t, "unit": "ant-steps/s",
                "h2d_bytes_per_step": int(wl.net.n_edges * 4 + nq * 40), "d2h_bytes_per_step": int(d2h),
-               "queries_per_s": nq * args.steps / e2e_t}
+               "queries_per_s": nq * args.steps / e2e_t, "routed_queries_per_s": e2e_routed / e2e_t}
     # the same colonies with the exact heuristic (a different colony, so not the headline): its job time,
     # ant-steps and routes next to the default straight-line bound's
     exact = None
@@ -484,11 +613,13 @@ def run_gpu(args, rank, world, local_rank):
                  "mean_best_travel_s_default": float(np.mean([r["travel_ms"] for r in res]) / 1e3)}
         ctx.set_params(**sched)
     ctx.close()
-    serving = serving_1m = geo = None
+    serving = serving_1m = geo = city = None
+    with_cpu = world == 1 and not args.no_cpu_baseline
     if not args.no_serving and rank == 0:
         serving = serving_leg(wl)
-        serving_1m = serving_leg_1m()
-        geo = geo100k_leg()
+        serving_1m = serving_leg_1m(with_cpu)
+        geo = geo100k_leg(with_cpu)
+        city = city_batch_leg(with_cpu)
     if rank != 0:
         return
     K = args.steps
@@ -512,6 +643,8 @@ def run_gpu(args, rank, world, local_rank):
                        lockstep=None if tune is None else tune["lockstep"],
                        schedule_source="autotuned" if tune is not None else "command line"),
         "queries_per_s": world * nq * K / (total_ms / 1e3),
+        **{k: (v * world if k == "routed_queries_per_s" else v)
+           for k, v in routed_summary(res, wl.queries, total_ms / 1e3 / K).items()},
         "ant_steps_per_step": steps_per_job,
         "kernel_ms_per_step": {k: v / K for k, v in kt.items()},
         "ms_per_step_with_kernel_events": sum(times_k) / K,
@@ -541,9 +674,11 @@ def run_gpu(args, rank, world, local_rank):
         line["serving_1m_nodes"] = serving_1m
     if geo:
         line["batched_geo100k"] = geo
+    if city:
+        line["batched_city_graphs"] = city
     if exact:
         line["exact_heuristic"] = exact
-    if world == 1 and not args.no_cpu_baseline:
+    if with_cpu:
         line["cpu_baseline"] = cpu_baseline_line(nq)
     print(json.dumps(line), flush=True)
 

@@ -46,17 +46,26 @@ class ServeReport:
     jobs: int
     ticks: int
     mean_batch: float
+    routed: int = 0          # completed requests that found a route
+    ant_walks: int = 0       # ants x iterations of the completed requests
+    successes: int = 0       # ant walks that reached the destination
+    unfinished: int = 0      # requests of the window still queued or running when the drain ended
     results: list = field(repr=False, default_factory=list)
 
     def summary(self) -> dict:
         lat = self.latencies_ms
+        per_s = (lambda n: n / self.window_s) if self.window_s else (lambda n: 0.0)
         return {
             "offered_req_per_s": self.offered_per_s,
             "window_s": self.window_s,
             "submitted": self.submitted,
             "completed": self.completed,
-            "queries_per_s": self.completed / self.window_s if self.window_s else 0.0,
-            "ant_steps_per_s": self.ant_steps / self.window_s if self.window_s else 0.0,
+            "unfinished": self.unfinished,
+            "queries_per_s": per_s(self.completed),
+            "routed_queries_per_s": per_s(self.routed),
+            "routed_fraction": self.routed / self.completed if self.completed else 0.0,
+            "success_fraction": self.successes / self.ant_walks if self.ant_walks else 0.0,
+            "ant_steps_per_s": per_s(self.ant_steps),
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "mean_batch": self.mean_batch,
@@ -87,6 +96,7 @@ def run_poisson(server: G.Server, make_request, rate_per_s: float, duration_s: f
     total = warmup_s + duration_s
     t0 = time.perf_counter_ns()
     arrivals: dict[int, int] = {}  # tag -> scheduled arrival (ns, monotonic)
+    walks: dict[int, int] = {}     # tag -> ants x iterations
     next_arr = rng.exponential(1.0 / rate_per_s)
     next_tick = tick_ms / 1000.0
     clock = clock_start_ms
@@ -99,6 +109,7 @@ def run_poisson(server: G.Server, make_request, rate_per_s: float, duration_s: f
         while next_arr <= now and next_arr < total:
             q = make_request(tag)
             arrivals[tag] = t0 + int(next_arr * 1e9)
+            walks[tag] = q.n_ants * q.n_iter
             server.submit(q, tag)
             tag += 1
             next_arr += rng.exponential(1.0 / rate_per_s)
@@ -119,9 +130,12 @@ def run_poisson(server: G.Server, make_request, rate_per_s: float, duration_s: f
     lat = np.array([(r["t_done_ns"] - arrivals[r["tag"]]) * 1e-6 for r in win], np.float64)
     last_done = max((r["t_done_ns"] for r in win), default=w1)
     window = (max(w1, last_done) - w0) * 1e-9
-    return ServeReport(offered_per_s=rate_per_s, window_s=window,
-                       submitted=sum(1 for a in arrivals.values() if w0 <= a < w1), completed=len(win),
+    submitted = sum(1 for a in arrivals.values() if w0 <= a < w1)
+    return ServeReport(offered_per_s=rate_per_s, window_s=window, submitted=submitted, completed=len(win),
                        latencies_ms=lat, ant_steps=int(sum(r["ant_steps"] for r in win)),
                        jobs=int(st["jobs"]), ticks=ticks,
                        mean_batch=float(np.mean([r["batch_size"] for r in win])) if win else 0.0,
+                       routed=sum(1 for r in win if r["status"] == 0),
+                       ant_walks=sum(walks[r["tag"]] for r in win),
+                       successes=int(sum(r["n_success"] for r in win)), unfinished=submitted - len(win),
                        results=done if keep_results else [])
