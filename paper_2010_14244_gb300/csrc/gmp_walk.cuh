@@ -277,6 +277,8 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     uint32_t beg = __ldg(a.row_ptr + u), end = __ldg(a.row_ptr + u + 1);
     uint32_t hu = a.qs[qi].h_src;  // remaining bound where the ant stands
     uint32_t t = 0, W = 0, steps = 0, len = 0, pops = 0, status;
+    uint32_t rb_base = 0, rb_x = 0, rb_y = 0;  // lane l holds the draw of move rb_base + l
+    bool rb_valid = false;
     if (lane == 0) atomicOr(tabu + (u >> 5), 1u << (u & 31));
     __syncwarp(gmask);
     for (;;) {
@@ -308,9 +310,19 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             tf[j] = ph.x ? __uint_as_float(ph.x) : base_tf;  // 0: the road still holds the baseline
             he[j] = ph.y;
         }
-        // 2. the draw of this step depends on (iteration, ant, move) only: overlaps the loads
-        const uint4 o = philox4x32_10(make_uint4(it, k, steps, 0u), s0, s1);
-        const unsigned long long rnd = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+        // 2. the draw of this move depends on (iteration, ant, move) only: the group's lanes compute the
+        //    draws of the next G moves together, one each (overlapping the loads), and a move takes its
+        //    draw with a shuffle
+        if (!rb_valid || steps - rb_base >= (uint32_t)G) {
+            const uint4 o = philox4x32_10(make_uint4(it, k, steps + lane, 0u), s0, s1);
+            rb_x = o.x;
+            rb_y = o.y;
+            rb_base = steps;
+            rb_valid = true;
+        }
+        const uint32_t rsrc = steps - rb_base;
+        const unsigned long long rnd = (unsigned long long)__shfl_sync(gmask, rb_x, rsrc, G) |
+                                       ((unsigned long long)__shfl_sync(gmask, rb_y, rsrc, G) << 32);
         // 3. candidates, waits, scores
         uint32_t cmask = 0, cong = 0;
         uint32_t sb[K], wv[K];
