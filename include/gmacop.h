@@ -77,6 +77,10 @@ typedef struct {
     uint32_t branches;      /* iterative mode: the colonies are split into this many contiguous ranges that
                                run as concurrent chains of launches; 0 = min(colonies, 16), at most 64 */
     uint32_t tau_layout;    /* pheromone tables: GMP_TAU_AUTO, GMP_TAU_DENSE or GMP_TAU_SPARSE (same results) */
+    uint32_t poll_limit;    /* persistent mode: polls a group waiting for its colony's next phase makes before
+                               the job stops and reports GMP_ERR_TIMEOUT; 0 = 2^23 (seconds) */
+    uint32_t level_limit;   /* GMP_FLAG_EXACT_H: relaxation levels before the heuristic's pass stops and the
+                               job reports GMP_ERR_TIMEOUT; 0 = 4N + 4096 */
 } gmp_params;
 
 /* Pheromone layouts. Dense: every road's pheromone is evaporated every iteration. Sparse: roads that never

@@ -42,7 +42,7 @@ constexpr uint32_t kTickDtMax = 1u << 30;
 
 struct BatchKey {
     uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0,
-             chunk = 0, branches = 0, sparse = 0;
+             chunk = 0, branches = 0, sparse = 0, poll_limit = 0, level_limit = 0;
     uint64_t log_entries = 0;
     const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
@@ -504,6 +504,7 @@ int enqueue_exact_h(gmp_ctx* c) {
     if (!b.exact_h) return GMP_OK;
     GMP_CUDA(c, cudaMemsetAsync(b.misc + 2, 0, 4, c->stream));
     GMP_CUDA(c, launch_exact_h(c->stream, b.Q, c->N, b.dq, c->in_ptr, c->in_edge, c->in_tail, c->rec, c->h_delta,
+                               c->prm.level_limit,
                                b.hdist, b.hqueue, b.hstamp, b.misc + 2));
     return GMP_OK;
 }
@@ -546,7 +547,7 @@ int enqueue_persistent(gmp_ctx* c) {
     p.max_iter = b.maxI;
     p.flags = c->prm.flags;
     p.node_chunk = c->prm.queue_chunk ? c->prm.queue_chunk : 16u;
-    p.spin_limit = 1u << 23;  // idle polls of ~0.3 us each (seconds) before the job reports a timeout
+    p.spin_limit = c->prm.poll_limit ? c->prm.poll_limit : 1u << 23;  // idle polls (~0.3 us each) before a timeout
     GMP_CUDA(c, launch_persistent(s, b.kc, p));
     if (timed) GMP_TRY(record(c, b, 2));
     GMP_CUDA(c, launch_finalize(s, b.Q, b.dq, b.qs, b.best_route, c->col, b.max_steps, b.res, b.route_out));
@@ -714,6 +715,8 @@ BatchKey key_of(const gmp_ctx* c) {
     BatchKey k{};
     k.Q = b.Q;
     k.chunk = c->prm.queue_chunk;
+    k.poll_limit = c->prm.poll_limit;
+    k.level_limit = c->prm.level_limit;
     k.branches = (uint32_t)b.br.size();
     k.sparse = b.sparse ? 1u : 0u;
     k.maxI = b.maxI;

@@ -142,7 +142,7 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
 // if a colony ran past its level guard.
 cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,
                            const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t delta,
-                           uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err);
+                           uint32_t level_limit, uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err);
 cudaError_t launch_materialize_tau(cudaStream_t s, uint32_t E, const QueryState* qs, const uint32_t* list_e,
                                    const uint64_t* list_tau, uint64_t* out);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);

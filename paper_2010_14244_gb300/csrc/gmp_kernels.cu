@@ -169,7 +169,7 @@ constexpr uint32_t kExactHBlock = 512;
 __global__ void __launch_bounds__(kExactHBlock, 4)
 k_exact_h(uint32_t N, const DevQuery* __restrict__ q, const uint32_t* __restrict__ in_ptr,
           const uint32_t* __restrict__ in_edge, const uint32_t* __restrict__ in_tail, const EdgeRec* __restrict__ rec,
-          uint32_t delta, uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err) {
+          uint32_t delta, uint32_t level_limit, uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err) {
     const uint32_t qi = blockIdx.x;
     const uint32_t dst = q[qi].dst;
     uint32_t* dist = hdist + (size_t)qi * N;
@@ -196,7 +196,7 @@ k_exact_h(uint32_t N, const DevQuery* __restrict__ q, const uint32_t* __restrict
         fmin = 0xFFFFFFFFu;
     }
     __syncthreads();
-    const uint32_t guard = N > (1u << 29) ? 0xFFFFFFFFu : 4u * N + 4096u;
+    const uint32_t guard = level_limit ? level_limit : (N > (1u << 29) ? 0xFFFFFFFFu : 4u * N + 4096u);
     uint32_t T = delta, epoch = 0, fsel = 0;
     for (uint32_t level = 0;; ++level) {
         if (level > guard) {
@@ -1109,9 +1109,10 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
 
 cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuery* q, const uint32_t* in_ptr,
                            const uint32_t* in_edge, const uint32_t* in_tail, const EdgeRec* rec, uint32_t delta,
-                           uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err) {
+                           uint32_t level_limit, uint32_t* hdist, uint32_t* queue, uint32_t* stamps, uint32_t* err) {
     if (Q == 0 || N == 0) return cudaSuccess;
-    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, delta, hdist, queue, stamps, err);
+    k_exact_h<<<Q, kExactHBlock, 0, s>>>(N, q, in_ptr, in_edge, in_tail, rec, delta, level_limit, hdist, queue,
+                                         stamps, err);
     return cudaGetLastError();
 }
 
