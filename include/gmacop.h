@@ -143,6 +143,19 @@ int gmp_set_stream(gmp_ctx *ctx, void *cuda_stream);
  * this GPU), STATE (the context already holds device memory). */
 int gmp_bind_workspace(gmp_ctx *ctx, void *dev_ptr, uint64_t bytes);
 
+/* Make ctx a view of owner's road graph: ctx reads owner's static arrays (topology, road attributes,
+ * coordinates, signal programmes) in place, without a copy, and with own_state = 0 also owner's traffic
+ * state (vehicles, red times, phase order, road records); with own_state = 1 it gets a copy of that
+ * state which it may change (gmp_set_densities, gmp_set_red_times, gmp_tick) without touching owner's.
+ * ctx keeps its own parameters, stream and batch workspace, and drops whatever graph it held before. A
+ * view cannot change the signal programmes, nor (with own_state = 0) the traffic state, its threshold or
+ * headway (GMP_ERR_STATE). owner must outlive its views; while it has views it cannot load another graph
+ * or change its signals (GMP_ERR_STATE), and changes to its traffic state reach views that share it.
+ * Synchronous. The paper has no counterpart (a server's slots share one graph this way).
+ * Errors: INVALID_ARG (same context, other device), STATE (owner holds no graph, ctx has views), OOM,
+ * CUDA. */
+int gmp_share_graph(gmp_ctx *ctx, gmp_ctx *owner, int own_state);
+
 /* Road graph G(N, E) (the graph of Fig. 3; Sec. 5: roads with lanes) in CSR form: the roads leaving
  * node u are row_ptr[u] .. row_ptr[u+1]-1, in the order that breaks ties between equal choices.
  * col[e]: head node; length_dm[e] >= 1; speed_kmh[e] >= 1; lanes[e] >= 1; x_dm, y_dm: node coordinates,
@@ -257,10 +270,11 @@ int gmp_multi_launch(gmp_multi *multi, gmp_ctx *const *ctxs, uint32_t n);
 typedef struct gmp_server gmp_server;
 
 typedef struct {
-    uint32_t max_batch; /* requests per job at most (a slot's memory budget may admit fewer) */
-    uint32_t max_ants;  /* largest n_ants a request may ask for */
-    uint32_t max_iter;  /* largest n_iter a request may ask for */
-    uint32_t reserved;
+    uint32_t max_batch;      /* requests per job at most (memory may admit fewer) */
+    uint32_t max_ants;       /* largest n_ants a request may ask for */
+    uint32_t max_iter;       /* largest n_iter a request may ask for */
+    uint32_t mem_budget_mib; /* device memory all slots' batch workspaces may hold together, in MiB; 0 = no
+                                bound beyond the memory the GPU has free */
 } gmp_server_config;
 
 /* One finished request. Times are host steady-clock nanoseconds. */
@@ -287,28 +301,34 @@ typedef struct {
     uint64_t rejected;     /* requests refused at submission */
 } gmp_server_stats;
 
-/* Create a server over n_slots contexts. Each context must already hold the same road graph, signals,
- * densities, red times and parameters (one replica per slot; the server does not copy them); the
- * server uses them exclusively until it is destroyed, and does not destroy them. For every slot the
- * server reserves (gmp_batch_reserve) the workspace of a job of `cap` requests with max_ants ants and
- * max_iter iterations each, where cap starts at max_batch and shrinks until the context's memory budget
- * admits it: that is the slot's admission limit. Errors: INVALID_ARG, STATE, OOM (not even one request
- * fits), and those of gmp_batch_reserve. */
-int gmp_server_create(gmp_server **out, gmp_ctx *const *slots, uint32_t n_slots, const gmp_server_config *cfg);
+/* Create a server with n_slots slots over the road graph of `graph` (a context holding the loaded graph,
+ * signals, densities, red times and parameters, with a traffic state of its own). The slots are views of
+ * that graph (gmp_share_graph): its static arrays exist once on the GPU. The server keeps two versions of
+ * the traffic state, graph's own and a copy of its own, so that a tick never stops running jobs (see
+ * gmp_server_tick). Each slot has a batch workspace and a CUDA stream of its own; workspaces grow through
+ * the stream-ordered allocator. graph must outlive the server and must not be changed while it exists
+ * (the server changes its traffic state at ticks). Admission is per job: an idle slot takes up to
+ * max_batch requests from the head of the queue, fewer when their workspace would not fit the server's
+ * memory budget together with the other slots' workspaces, or the memory the GPU has free; requests that
+ * do not fit wait. Errors: INVALID_ARG, STATE (no graph, or graph reads another context's state), OOM,
+ * CUDA. */
+int gmp_server_create(gmp_server **out, gmp_ctx *graph, uint32_t n_slots, const gmp_server_config *cfg);
 void gmp_server_destroy(gmp_server *srv);
 const char *gmp_server_last_error(const gmp_server *srv);
 
-/* Requests per job admitted on a slot. */
-int gmp_server_slot_capacity(const gmp_server *srv, uint32_t slot, uint32_t *requests_per_job);
+/* Device memory the slots' batch workspaces hold together, and the server's budget (0 = none). */
+int gmp_server_memory(const gmp_server *srv, uint64_t *slots_bytes, uint64_t *budget_bytes);
 
 /* Queue one request (FIFO). Checked at once: a request that a job would refuse, or one above max_ants
  * or max_iter, is refused here with that error and counted as rejected. */
 int gmp_server_submit(gmp_server *srv, const gmp_query *query, uint64_t tag);
 
-/* Issue the traffic tick gmp_tick(t_now_ms, dt_ms) on every slot's stream: it runs after the slot's job
- * on the GPU, if any, and before its next one. The serving clock becomes t_now_ms + dt_ms; every job
- * launched afterwards departs at that clock (the server sets the slot's t_dep_ms), so the clock must stay
- * below 2^30 ms. Errors: INVALID_ARG, and those of gmp_tick. */
+/* Advance the traffic state by one tick gmp_tick(t_now_ms, dt_ms): the server copies the current version
+ * of the state into the other one and ticks that copy, on its own stream, after the jobs still reading
+ * the version it overwrites (those launched before the previous tick); running jobs on the current
+ * version are not waited for. Jobs launched afterwards run on the new version, after the tick, and depart
+ * at the new serving clock t_now_ms + dt_ms (the server sets the slot's t_dep_ms), so the clock must stay
+ * below 2^30 ms. Asynchronous. Errors: INVALID_ARG, CUDA, and those of gmp_tick. */
 int gmp_server_tick(gmp_server *srv, uint64_t t_now_ms, uint32_t dt_ms);
 
 /* One non-blocking round of the loop: collect every job that has finished, then give every idle slot

@@ -16,6 +16,7 @@
 #include <iterator>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -166,6 +167,15 @@ struct gmp_ctx {
     uint32_t* tick_leave = nullptr;        // serving tick: discharge of each road (E)
     unsigned long long* tick_K = nullptr;  // serving tick: discharge of each node (N)
     std::vector<int32_t> hx, hy;  // host copy of node coordinates (destination lookups at staging)
+    // A context may view another context's road graph (gmp_share_graph): the static arrays always, the
+    // traffic state (vehicles, red times, phase order, road records, tick scratch) too unless it keeps a
+    // state of its own. What a view borrowed is never freed by it.
+    gmp_ctx* lender = nullptr;        // owner of the static arrays, or nullptr
+    gmp_ctx* state_lender = nullptr;  // holder of the traffic state this context reads, or nullptr (own)
+    bool own_state = true;            // the traffic-state arrays are this context's allocations
+    int views = 0;                    // contexts that borrow this context's static arrays or state
+    bool stream_alloc = false;        // device memory from the stream-ordered allocator on `stream` (no
+                                      // device-wide synchronisation when a workspace grows)
     Batch b;
     std::vector<cudaStream_t> bstreams;  // streams of the concurrent colony chains
     std::vector<cudaEvent_t> bjoin;      // one join event per chain
@@ -270,7 +280,7 @@ int dalloc(gmp_ctx* c, T** p, size_t n) {
         q = arena_take(c, bytes);
         if (!q) return fail(c, GMP_ERR_OOM, "bound workspace exhausted: no free run of %zu bytes", bytes);
     } else {
-        cudaError_t e = cudaMalloc(&q, bytes);
+        cudaError_t e = c->stream_alloc ? cudaMallocAsync(&q, bytes, c->stream) : cudaMalloc(&q, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(c, GMP_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
@@ -291,6 +301,7 @@ void dfree(gmp_ctx* c, T** p) {
             c->sizes.erase(it);
         }
         if (c->arena_blocks.count((void*)*p)) arena_give(c, (void*)*p);
+        else if (c->stream_alloc) cudaFreeAsync((void*)*p, c->stream);
         else cudaFree((void*)*p);
         *p = nullptr;
     }
@@ -363,8 +374,31 @@ void free_batch(gmp_ctx* c) {
     b.staged = b.ran = false;
 }
 
+// Forget (without freeing) what a view borrowed.
+void drop_borrowed(gmp_ctx* c) {
+    if (c->lender) {
+        c->row_ptr = c->col = c->len = c->in_ptr = c->in_edge = c->in_tail = c->ff = c->cap = nullptr;
+        c->speed = nullptr;
+        c->lanes = nullptr;
+        c->x = c->y = nullptr;
+        c->nph = c->ephase = nullptr;
+        c->cycle = c->offset = c->green = nullptr;
+    }
+    if (!c->own_state) {
+        c->order = nullptr;
+        c->red = c->veh = c->tick_leave = nullptr;
+        c->rec = nullptr;
+        c->tick_K = nullptr;
+    }
+    if (c->lender) --c->lender->views;
+    if (c->state_lender) --c->state_lender->views;
+    c->lender = c->state_lender = nullptr;
+    c->own_state = true;
+}
+
 void free_graph(gmp_ctx* c) {
     free_batch(c);
+    drop_borrowed(c);
     dfree(c, &c->row_ptr);
     dfree(c, &c->col);
     dfree(c, &c->len);
@@ -405,6 +439,18 @@ int refresh_dynamic(gmp_ctx* c) {
 
 int sync(gmp_ctx* c) {
     GMP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GMP_OK;
+}
+
+// Copy src's traffic state (vehicles, red times, phase order, road records) into dst's own arrays, on
+// dst's stream. Both contexts share one static graph.
+int copy_state(gmp_ctx* dst, const gmp_ctx* src) {
+    cudaStream_t s = dst->stream;
+    GMP_CUDA(dst, cudaMemcpyAsync(dst->veh, src->veh, std::max<size_t>(dst->E, 1) * 4, cudaMemcpyDeviceToDevice, s));
+    GMP_CUDA(dst, cudaMemcpyAsync(dst->red, src->red, (size_t)dst->N * kMaxPhases * 4, cudaMemcpyDeviceToDevice, s));
+    GMP_CUDA(dst, cudaMemcpyAsync(dst->order, src->order, (size_t)dst->N * kMaxPhases, cudaMemcpyDeviceToDevice, s));
+    GMP_CUDA(dst, cudaMemcpyAsync(dst->rec, src->rec, std::max<size_t>(dst->E, 1) * sizeof(EdgeRec),
+                                  cudaMemcpyDeviceToDevice, s));
     return GMP_OK;
 }
 
@@ -861,6 +907,7 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
             for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) tail_of[e] = u;
         for (uint32_t i = 0; i < E; ++i) in_tail[i] = tail_of[in_edge[i]];
     }
+    if (c->views) return fail(c, GMP_ERR_STATE, "other contexts view this context's graph");
     cudaSetDevice(c->device);
     sync(c);
     free_graph(c);
@@ -923,12 +970,77 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     return GMP_OK;
 }
 
+int gmp_share_graph(gmp_ctx* c, gmp_ctx* owner, int own_state) {
+    if (!c || !owner || c == owner) return GMP_ERR_INVALID_ARG;
+    if (!owner->has_graph) return fail(c, GMP_ERR_STATE, "the owner holds no graph");
+    if (owner->device != c->device) return fail(c, GMP_ERR_INVALID_ARG, "both contexts must be on one device");
+    if (c->views) return fail(c, GMP_ERR_STATE, "other contexts view this context's graph");
+    cudaSetDevice(c->device);
+    sync(c);
+    free_graph(c);
+    gmp_ctx* root = owner->lender ? owner->lender : owner;
+    c->N = owner->N;
+    c->E = owner->E;
+    c->maxdeg = owner->maxdeg;
+    c->kappa = owner->kappa;
+    c->h_delta = owner->h_delta;
+    c->max_phases = owner->max_phases;
+    c->hx = owner->hx;
+    c->hy = owner->hy;
+    c->row_ptr = owner->row_ptr;
+    c->col = owner->col;
+    c->len = owner->len;
+    c->in_ptr = owner->in_ptr;
+    c->in_edge = owner->in_edge;
+    c->in_tail = owner->in_tail;
+    c->ff = owner->ff;
+    c->cap = owner->cap;
+    c->speed = owner->speed;
+    c->lanes = owner->lanes;
+    c->x = owner->x;
+    c->y = owner->y;
+    c->nph = owner->nph;
+    c->ephase = owner->ephase;
+    c->cycle = owner->cycle;
+    c->offset = owner->offset;
+    c->green = owner->green;
+    c->lender = root;
+    ++root->views;
+    c->prm.thr_permille = owner->prm.thr_permille;
+    c->prm.h_sat_ms = owner->prm.h_sat_ms;
+    if (own_state) {  // a copy of the owner's traffic state, ordered after the owner's queued work
+        c->own_state = true;
+        GMP_TRY(dalloc(c, &c->order, (size_t)c->N * kMaxPhases));
+        GMP_TRY(dalloc(c, &c->red, (size_t)c->N * kMaxPhases));
+        GMP_TRY(dalloc(c, &c->veh, c->E));
+        GMP_TRY(dalloc(c, &c->rec, c->E));
+        GMP_TRY(dalloc(c, &c->tick_leave, c->E));
+        GMP_TRY(dalloc(c, &c->tick_K, c->N));
+        GMP_CUDA(c, cudaStreamSynchronize(owner->stream));
+        GMP_TRY(copy_state(c, owner));
+        GMP_TRY(sync(c));
+    } else {
+        c->own_state = false;
+        c->state_lender = owner;
+        ++owner->views;
+        c->order = owner->order;
+        c->red = owner->red;
+        c->veh = owner->veh;
+        c->rec = owner->rec;
+        c->tick_leave = owner->tick_leave;
+        c->tick_K = owner->tick_K;
+    }
+    c->has_graph = true;
+    return GMP_OK;
+}
+
 int gmp_set_signals(gmp_ctx* c, const uint8_t* n_phases, const uint32_t* cycle_ms, const uint32_t* offset_ms,
                     const uint32_t* green_ms, const uint8_t* edge_phase) {
     if (!c) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
     if (!n_phases || !cycle_ms || !offset_ms || !green_ms || (c->E && !edge_phase))
         return fail(c, GMP_ERR_INVALID_ARG, "null array");
+    if (c->lender || c->views) return fail(c, GMP_ERR_STATE, "signal programmes of a shared graph are fixed");
     std::vector<uint32_t> row(c->N + 1);
     for (uint32_t v = 0; v < c->N; ++v) {
         const uint32_t P = n_phases[v];
@@ -969,6 +1081,7 @@ int gmp_set_signals(gmp_ctx* c, const uint8_t* n_phases, const uint32_t* cycle_m
 int gmp_set_red_times(gmp_ctx* c, const uint32_t* red_ms) {
     if (!c || !red_ms) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     cudaSetDevice(c->device);
     GMP_TRY(upload(c, c->red, red_ms, (size_t)c->N * kMaxPhases));
     GMP_TRY(refresh_dynamic(c));
@@ -978,6 +1091,7 @@ int gmp_set_red_times(gmp_ctx* c, const uint32_t* red_ms) {
 int gmp_set_densities(gmp_ctx* c, const uint32_t* vehicles) {
     if (!c || (!vehicles && c->E)) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     cudaSetDevice(c->device);
     GMP_TRY(upload(c, c->veh, vehicles, c->E));
     GMP_TRY(refresh_dynamic(c));
@@ -987,6 +1101,7 @@ int gmp_set_densities(gmp_ctx* c, const uint32_t* vehicles) {
 int gmp_set_densities_async(gmp_ctx* c, const uint32_t* d_vehicles) {
     if (!c || (!d_vehicles && c->E)) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     cudaSetDevice(c->device);
     if (c->E) GMP_CUDA(c, cudaMemcpyAsync(c->veh, d_vehicles, c->E * 4ull, cudaMemcpyDeviceToDevice, c->stream));
     return refresh_dynamic(c);
@@ -1006,6 +1121,8 @@ int gmp_set_params(gmp_ctx* c, const gmp_params* p) {
     if (p->tau_layout > GMP_TAU_SPARSE) return fail(c, GMP_ERR_INVALID_ARG, "unknown tau_layout");
     if (p->max_steps > (1u << 24)) return fail(c, GMP_ERR_INVALID_ARG, "max_steps must be <= 2^24");
     const bool dyn = p->thr_permille != c->prm.thr_permille || p->h_sat_ms != c->prm.h_sat_ms;
+    if (dyn && c->has_graph && !c->own_state)
+        return fail(c, GMP_ERR_STATE, "the threshold and headway of another context's traffic state are its own");
     c->prm = *p;
     if (dyn && c->has_graph) {
         cudaSetDevice(c->device);
@@ -1020,6 +1137,8 @@ int gmp_get_params(const gmp_ctx* c, gmp_params* p) {
     *p = c->prm;
     return GMP_OK;
 }
+
+}  // extern "C"
 
 namespace {
 
@@ -1046,62 +1165,85 @@ int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc, boo
     return GMP_OK;
 }
 
-// Device workspace of a job with n colonies, total_ants ants per iteration and at most maxI iterations
-// (buffers only grow, so a reservation for the largest job makes later staging allocation-free).
-int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI, uint64_t log_entries,
-                      const KernelConfig& kc) {
+// Every device buffer of a job with n colonies, total_ants ants per iteration and at most maxI iterations,
+// handed to f(&buffer, entries): reserve_workspace allocates them, workspace_bytes adds them up.
+template <class F>
+int for_each_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI, uint64_t log_entries,
+                       const KernelConfig& kc, F&& f) {
     Batch& b = c->b;
     const bool persistent = c->prm.mode == GMP_MODE_PERSISTENT;
     const size_t words = (c->N + 31u) / 32u;
     const size_t max_steps = std::max<uint32_t>(default_max_steps(c), 1u);
-    if (persistent && (uint64_t)kc.grid < n)
-        return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs at least one resident block per colony");
-    GMP_TRY(ensure(c, &b.dq, n));
-    GMP_TRY(ensure(c, &b.prefix, n + 1));
+    GMP_TRY(f(&b.dq, n));
+    GMP_TRY(f(&b.prefix, n + 1));
     if (use_sparse(c)) {
-        GMP_TRY(ensure(c, &b.tflag, (size_t)n * tflag_words(c)));
-        GMP_TRY(ensure(c, &b.list_e, (size_t)n * c->E));
-        GMP_TRY(ensure(c, &b.list_tau, (size_t)n * c->E));
+        GMP_TRY(f(&b.tflag, (size_t)n * tflag_words(c)));
+        GMP_TRY(f(&b.list_e, (size_t)n * c->E));
+        GMP_TRY(f(&b.list_tau, (size_t)n * c->E));
     } else {
-        GMP_TRY(ensure(c, &b.tau, (size_t)n * c->E));
+        GMP_TRY(f(&b.tau, (size_t)n * c->E));
     }
-    GMP_TRY(ensure(c, &b.th, (size_t)n * c->E));
-    // deposit accumulators: zeroed when allocated (or after a job that may have stopped mid-iteration);
-    // iterative jobs then keep them zero without clearing them at init
-    {
-        unsigned long long* before = b.dep;
-        const size_t have = before ? c->sizes[(void*)before] : 0;
-        GMP_TRY(ensure(c, &b.dep, (size_t)n * c->E));
-        if (b.dep != before || c->sizes[(void*)b.dep] != have || b.dep_dirty) {
-            GMP_CUDA(c, cudaMemsetAsync(b.dep, 0, c->sizes[(void*)b.dep], c->stream));
-            b.dep_dirty = false;
-        }
-    }
-    GMP_TRY(ensure(c, &b.qs, n));
-    GMP_TRY(ensure(c, &b.routes, 2 * (size_t)total_ants * max_steps));  // routes, then their waits
-    GMP_TRY(ensure(c, &b.ant_steps, (size_t)total_ants));
-    GMP_TRY(ensure(c, &b.ant_wait, (size_t)total_ants));
-    GMP_TRY(ensure(c, &b.best_route, (size_t)n * max_steps));
-    GMP_TRY(ensure(c, &b.route_out, (size_t)n * (max_steps + 1)));
-    GMP_TRY(ensure(c, &b.tickets, (size_t)maxI * branch_count(c, n)));
-    GMP_TRY(ensure(c, &b.res, n));
+    GMP_TRY(f(&b.th, (size_t)n * c->E));
+    GMP_TRY(f(&b.dep, (size_t)n * c->E));
+    GMP_TRY(f(&b.qs, n));
+    GMP_TRY(f(&b.routes, 2 * (size_t)total_ants * max_steps));  // routes, then their waits
+    GMP_TRY(f(&b.ant_steps, (size_t)total_ants));
+    GMP_TRY(f(&b.ant_wait, (size_t)total_ants));
+    GMP_TRY(f(&b.best_route, (size_t)n * max_steps));
+    GMP_TRY(f(&b.route_out, (size_t)n * (max_steps + 1)));
+    GMP_TRY(f(&b.tickets, (size_t)maxI * branch_count(c, n)));
+    GMP_TRY(f(&b.res, n));
     if (persistent) {
-        GMP_TRY(ensure(c, &b.ctr, (size_t)n * maxI));
-        GMP_TRY(ensure(c, &b.qstate, n));
-        GMP_TRY(ensure(c, &b.qflag, maxI));
+        GMP_TRY(f(&b.ctr, (size_t)n * maxI));
+        GMP_TRY(f(&b.qstate, n));
+        GMP_TRY(f(&b.qflag, maxI));
     }
-    if (persistent || (c->prm.flags & GMP_FLAG_EXACT_H)) GMP_TRY(ensure(c, &b.misc, 3));
+    if (persistent || (c->prm.flags & GMP_FLAG_EXACT_H)) GMP_TRY(f(&b.misc, 3));
     if (c->prm.flags & GMP_FLAG_EXACT_H) {
-        GMP_TRY(ensure(c, &b.hdist, (size_t)n * c->N));
-        GMP_TRY(ensure(c, &b.hqueue, (size_t)n * 4 * c->N));
-        GMP_TRY(ensure(c, &b.hstamp, (size_t)n * 2 * c->N));
+        GMP_TRY(f(&b.hdist, (size_t)n * c->N));
+        GMP_TRY(f(&b.hqueue, (size_t)n * 4 * c->N));
+        GMP_TRY(f(&b.hstamp, (size_t)n * 2 * c->N));
     }
-    if (log_entries) GMP_TRY(ensure(c, &b.ant_log, (size_t)log_entries * 4));
+    if (log_entries) GMP_TRY(f(&b.ant_log, (size_t)log_entries * 4));
     // visited bitmaps in global memory: the job's grid plus one block per concurrent chain (chain grids
     // are shares of the job's grid, rounded up)
-    if (!kc.tabu_in_smem)
-        GMP_TRY(ensure(c, &b.tabu, ((size_t)kc.grid + branch_count(c, n)) * (kc.block / kc.lanes) * words));
+    if (!kc.tabu_in_smem) GMP_TRY(f(&b.tabu, ((size_t)kc.grid + branch_count(c, n)) * (kc.block / kc.lanes) * words));
     return GMP_OK;
+}
+
+// Device workspace of a job (buffers only grow, so a reservation for the largest job makes later staging
+// allocation-free).
+int reserve_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI, uint64_t log_entries,
+                      const KernelConfig& kc) {
+    Batch& b = c->b;
+    if (c->prm.mode == GMP_MODE_PERSISTENT && (uint64_t)kc.grid < n)
+        return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs at least one resident block per colony");
+    // deposit accumulators: zeroed when allocated (or after a job that may have stopped mid-iteration);
+    // iterative jobs then keep them zero without clearing them at init
+    unsigned long long* dep_before = b.dep;
+    const size_t dep_have = dep_before ? c->sizes[(void*)dep_before] : 0;
+    GMP_TRY(for_each_workspace(c, n, total_ants, maxI, log_entries, kc,
+                               [&](auto** p, size_t count) { return ensure(c, p, count); }));
+    if (b.dep != dep_before || c->sizes[(void*)b.dep] != dep_have || b.dep_dirty) {
+        GMP_CUDA(c, cudaMemsetAsync(b.dep, 0, c->sizes[(void*)b.dep], c->stream));
+        b.dep_dirty = false;
+    }
+    return GMP_OK;
+}
+
+// Bytes the context would hold after reserving the workspace of such a job (nothing is allocated): what it
+// holds now, minus each buffer that would be replaced, plus its new size.
+uint64_t workspace_bytes(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t maxI, const KernelConfig& kc) {
+    uint64_t total = c->used;
+    for_each_workspace(c, n, total_ants, maxI, 0, kc, [&](auto** p, size_t count) {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        const auto it = *p ? c->sizes.find((void*)*p) : c->sizes.end();
+        const size_t have = it != c->sizes.end() ? it->second : 0;
+        if (have < bytes) total += bytes - have;
+        return GMP_OK;
+    });
+    return total;
 }
 
 // Split the staged job into concurrent chains of contiguous colonies. Each chain's construction grid is
@@ -1141,6 +1283,8 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
 }
 
 }  // namespace
+
+extern "C" {
 
 int gmp_batch_reserve(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max_iter) {
     if (!c) return GMP_ERR_INVALID_ARG;
@@ -1457,6 +1601,7 @@ int gmp_get_red_times(gmp_ctx* c, uint32_t* red_ms) {
 int gmp_tick(gmp_ctx* c, uint64_t t_now_ms, uint32_t dt_ms) {
     if (!c) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
+    if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     if (t_now_ms > kTickClockMax || dt_ms > kTickDtMax)
         return fail(c, GMP_ERR_INVALID_ARG, "tick clock must be <= 2^48 ms and dt <= 2^30 ms");
     cudaSetDevice(c->device);
@@ -1855,5 +2000,40 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
 namespace gmp {
 
 int ctx_check_query(gmp_ctx* c, const gmp_query& q) { return check_query(c, q, 0); }
+
+void ctx_set_stream_alloc(gmp_ctx* c) { c->stream_alloc = true; }
+
+int ctx_rebind_state(gmp_ctx* c, gmp_ctx* holder) {
+    if (c->own_state || !c->lender || !holder->own_state)
+        return fail(c, GMP_ERR_STATE, "only a view of another context's traffic state can be moved to another");
+    if ((holder->lender ? holder->lender : holder) != c->lender)
+        return fail(c, GMP_ERR_INVALID_ARG, "the traffic state belongs to another road graph");
+    if (c->state_lender == holder) return GMP_OK;
+    --c->state_lender->views;
+    ++holder->views;
+    c->state_lender = holder;
+    c->order = holder->order;
+    c->red = holder->red;
+    c->veh = holder->veh;
+    c->rec = holder->rec;
+    c->tick_leave = holder->tick_leave;
+    c->tick_K = holder->tick_K;
+    return GMP_OK;
+}
+
+cudaEvent_t ctx_done_event(const gmp_ctx* c) { return c->b.ran ? c->b.done : nullptr; }
+
+bool ctx_owns_state(const gmp_ctx* c) { return c->own_state; }
+
+int ctx_copy_state(gmp_ctx* dst, const gmp_ctx* src) {
+    cudaSetDevice(dst->device);
+    return copy_state(dst, src);
+}
+
+uint64_t ctx_job_bytes(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max_iter) {
+    KernelConfig kc{};
+    if (job_config(c, pick_lanes(c), total_ants, &kc) != GMP_OK) return ~0ull;
+    return workspace_bytes(c, n, total_ants, max_iter, kc);
+}
 
 }  // namespace gmp

@@ -180,5 +180,15 @@ int ctx_fail(gmp_ctx* c, int code, const char* msg);
 uint32_t default_lanes(uint32_t maxdeg);  // lanes per ant when the parameters leave it open
 bool lockstep_fits(int lanes, uint32_t maxdeg);  // the warp-lockstep construction kernel covers this shape
 int ctx_check_query(gmp_ctx* c, const gmp_query& q);  // the checks gmp_batch_stage applies to one query
+// Server support: stream-ordered allocations for a context (before it allocates anything); move a view
+// of another context's traffic state onto another holder of the same road graph; the event recorded
+// after the context's last launch (nullptr before any); copy one traffic state into another context's own
+// (on dst's stream); the bytes the context would hold after reserving a job of n colonies.
+void ctx_set_stream_alloc(gmp_ctx* c);
+int ctx_rebind_state(gmp_ctx* c, gmp_ctx* holder);
+cudaEvent_t ctx_done_event(const gmp_ctx* c);
+bool ctx_owns_state(const gmp_ctx* c);
+int ctx_copy_state(gmp_ctx* dst, const gmp_ctx* src);
+uint64_t ctx_job_bytes(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max_iter);
 
 }  // namespace gmp

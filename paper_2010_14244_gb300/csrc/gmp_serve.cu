@@ -1,20 +1,25 @@
 // Route server with continuous batching (gmp_server_*, declared in include/gmacop.h).
 //
 // The paper routes vehicles one request at a time (Fig. 3); a deployment receives route requests
-// continuously while the traffic state changes. The server keeps that state resident on the device
-// and runs colonies as they arrive:
-//   - slots: each slot is a context holding its own replica of the road graph, signals and traffic
-//     state, on its own CUDA stream, so jobs of different slots overlap on the GPU and never share a
-//     buffer another job writes;
-//   - admission by memory: each slot reserves, once, the workspace of its largest job; the number of
-//     requests a job may hold is what the slot's memory budget admits (up to max_batch);
-//   - continuous batching: whenever a slot is idle, everything waiting (up to that capacity) becomes
-//     the slot's next job, launched without waiting for any other slot;
-//   - ticks: a traffic tick is issued on every slot's stream, so it lands between that slot's jobs;
-//     each request departs at, and records, the traffic clock of the state it was solved on.
-// A request's result depends only on the request and that state (Philox streams are keyed by the
-// request's own seed), so it is the same alone and in any mix. The server is single-threaded: the
-// caller drives it with gmp_server_pump.
+// continuously while the traffic state changes. The server keeps one road graph and its traffic state
+// resident on the device and runs colonies as they arrive:
+//   - one road graph: the caller's context holds it; every slot is a view of it (gmp_share_graph), so
+//     the static arrays exist once on the GPU whatever the number of slots;
+//   - two versions of the traffic state: the caller's and a copy the server keeps. A tick copies the
+//     current version into the other one and advances that copy in place, on its own stream, after
+//     the jobs still reading the version it overwrites; jobs launched afterwards run on the new version
+//     (their streams wait for the tick). Running jobs never wait for a tick, nor a tick for them beyond
+//     the previous version's jobs;
+//   - slots: each slot has its own batch workspace and CUDA stream, so jobs of different slots overlap
+//     on the GPU; workspaces grow through the stream-ordered allocator (no device-wide synchronisation);
+//   - admission by memory, per job: when a slot is idle it takes what waits at the head of the queue,
+//     up to max_batch requests, cut down until the job's workspace fits both the server's memory budget
+//     (shared by all slots) and the memory the GPU has free at that moment; requests that do not fit
+//     wait for a later job;
+//   - continuous batching: every pump collects finished jobs and starts jobs on idle slots at once.
+// A request's result depends only on the request and the traffic state it ran on (Philox streams are
+// keyed by the request's own seed), so it is the same alone and in any mix. The server is
+// single-threaded: the caller drives it with gmp_server_pump.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -44,9 +49,9 @@ struct Request {
 };
 
 struct Slot {
-    gmp_ctx* ctx = nullptr;
-    uint32_t cap = 0;  // requests per job the slot's memory admits
+    gmp_ctx* ctx = nullptr;  // a view of the road graph with a batch workspace of its own
     bool busy = false;
+    uint32_t version = 0;  // traffic-state version its job runs on
     std::vector<Request> job;
     uint64_t t_launch = 0, clock_ms = 0;
     std::vector<uint32_t> routes;  // job.size() * route_cap
@@ -61,11 +66,16 @@ struct Done {
 }  // namespace
 
 struct gmp_server {
+    gmp_ctx* state[2] = {nullptr, nullptr};     // [0] the caller's context, [1] the server's copy
+    cudaEvent_t ready[2] = {nullptr, nullptr};  // recorded after the tick that produced each version
+    bool has_ready[2] = {false, false};
+    uint32_t cur = 0;  // the version new jobs run on
     std::vector<Slot> slots;
     std::deque<Request> queue;
     std::deque<Done> done;
     gmp_server_config cfg{};
-    uint32_t route_cap = 0;  // max_steps + 1 of the graph
+    uint64_t budget = 0;     // bytes all slots' workspaces may hold together; 0 = no bound
+    uint32_t route_cap = 0;  // nodes of the longest possible route
     uint64_t clock_ms = 0;   // end of the last tick
     uint64_t jobs = 0, completed = 0, rejected = 0;
     std::string err;
@@ -78,44 +88,121 @@ int sfail(gmp_server* s, int code, const std::string& msg) {
     return code;
 }
 
+void release(gmp_server* s) {
+    for (Slot& sl : s->slots)
+        if (sl.ctx) gmp_destroy(sl.ctx);  // views: free their workspaces only
+    s->slots.clear();
+    if (s->state[1]) gmp_destroy(s->state[1]);
+    s->state[1] = nullptr;
+    for (cudaEvent_t& e : s->ready)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+}
+
+uint64_t held_by_slots(const gmp_server* s) {
+    uint64_t sum = 0;
+    for (const Slot& sl : s->slots) sum += ctx_info(sl.ctx).used;
+    return sum;
+}
+
+// Every request of a job that failed as a whole completes with the error.
+void fail_job(gmp_server* s, uint32_t k, const std::vector<Request>& job, int rc) {
+    const uint64_t t = now_ns();
+    for (const Request& r : job) {
+        Done d{};
+        d.s.tag = r.tag;
+        d.s.t_submit_ns = r.t_submit;
+        d.s.t_launch_ns = t;
+        d.s.t_done_ns = t;
+        d.s.clock_ms = s->clock_ms;
+        d.s.slot = k;
+        d.s.batch_size = (uint32_t)job.size();
+        d.s.result.status = rc;
+        s->done.push_back(std::move(d));
+    }
+    s->completed += job.size();
+}
+
+// Admission: the number of requests at the head of the queue whose job fits the memory budget and the
+// GPU's free memory on slot k (0: none fits right now).
+uint32_t admit(gmp_server* s, uint32_t k) {
+    gmp_ctx* c = s->slots[k].ctx;
+    const uint64_t held = ctx_info(c).used;
+    const uint64_t others = held_by_slots(s) - held;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    uint32_t n = (uint32_t)std::min<size_t>(s->cfg.max_batch, s->queue.size());
+    while (n >= 1) {
+        uint64_t ants = 0;
+        uint32_t maxI = 1;
+        for (uint32_t i = 0; i < n; ++i) {
+            ants += s->queue[i].q.n_ants;
+            maxI = std::max(maxI, s->queue[i].q.n_iter);
+        }
+        const uint64_t need = ctx_job_bytes(c, n, ants, maxI);  // what the slot would hold
+        const uint64_t grow = need > held ? need - held : 0;
+        const bool in_budget = !s->budget || others + need <= s->budget;
+        // leave a small margin of the free memory for the allocator's own rounding
+        if (need != ~0ull && in_budget && grow + (grow >> 4) <= (uint64_t)free_b) return n;
+        n = n > 1 ? n - std::max<uint32_t>(1u, n / 4u) : 0u;
+    }
+    return 0;
+}
+
 // Launch a job on an idle slot from the head of the queue.
 int launch_slot(gmp_server* s, uint32_t k) {
     Slot& sl = s->slots[k];
-    const uint32_t n = (uint32_t)std::min<size_t>(sl.cap, s->queue.size());
-    if (n == 0) return GMP_OK;
+    uint32_t n = admit(s, k);
+    if (n == 0) {
+        bool any_busy = false;
+        for (const Slot& o : s->slots) any_busy |= o.busy;
+        if (any_busy) return GMP_OK;  // memory frees up as running jobs finish
+        // nothing runs and not even one request fits: that request cannot be served
+        std::vector<Request> one(1, s->queue.front());
+        s->queue.pop_front();
+        fail_job(s, k, one, GMP_ERR_OOM);
+        return GMP_OK;
+    }
     sl.job.assign(s->queue.begin(), s->queue.begin() + n);
     s->queue.erase(s->queue.begin(), s->queue.begin() + n);
     std::vector<gmp_query> qs(n);
     for (uint32_t i = 0; i < n; ++i) qs[i] = sl.job[i].q;
-    // the job departs at the traffic clock of the state it runs on
+    // the job reads the current traffic-state version, after the tick that produced it, and departs at
+    // the clock of that state
+    const uint32_t v = s->cur;
+    int rc = ctx_rebind_state(sl.ctx, s->state[v]);
+    const CtxInfo ci = ctx_info(sl.ctx);
+    if (rc == GMP_OK && s->has_ready[v] && cudaStreamWaitEvent(ci.stream, s->ready[v], 0) != cudaSuccess) {
+        cudaGetLastError();
+        rc = GMP_ERR_CUDA;
+    }
     gmp_params p{};
     gmp_get_params(sl.ctx, &p);
-    int rc = GMP_OK;
-    if (p.t_dep_ms != (uint32_t)s->clock_ms) {
+    if (rc == GMP_OK && p.t_dep_ms != (uint32_t)s->clock_ms) {
         p.t_dep_ms = (uint32_t)s->clock_ms;
         rc = gmp_set_params(sl.ctx, &p);
     }
     if (rc == GMP_OK) rc = gmp_batch_stage(sl.ctx, n, qs.data());
     if (rc == GMP_OK) rc = gmp_batch_launch(sl.ctx);
-    if (rc != GMP_OK) {  // the whole job fails: every request completes with the error
-        const uint64_t t = now_ns();
-        for (const Request& r : sl.job) {
-            Done d{};
-            d.s.tag = r.tag;
-            d.s.t_submit_ns = r.t_submit;
-            d.s.t_launch_ns = t;
-            d.s.t_done_ns = t;
-            d.s.clock_ms = s->clock_ms;
-            d.s.slot = k;
-            d.s.batch_size = n;
-            d.s.result.status = rc;
-            s->done.push_back(std::move(d));
+    if (rc != GMP_OK) {
+        bool any_busy = false;
+        for (const Slot& o : s->slots) any_busy |= o.busy;
+        if (rc == GMP_ERR_OOM && any_busy) {  // the allocator disagreed with the estimate: retry later
+            s->queue.insert(s->queue.begin(), sl.job.begin(), sl.job.end());
+            sl.job.clear();
+            return GMP_OK;
         }
-        s->completed += n;
+        fail_job(s, k, sl.job, rc);
         sl.job.clear();
         return GMP_OK;
     }
     sl.busy = true;
+    sl.version = v;
     sl.t_launch = now_ns();
     sl.clock_ms = s->clock_ms;
     ++s->jobs;
@@ -163,57 +250,65 @@ int finish_slot(gmp_server* s, uint32_t k) {
 
 extern "C" {
 
-int gmp_server_create(gmp_server** out, gmp_ctx* const* slots, uint32_t n_slots, const gmp_server_config* cfg) {
-    if (!out || !slots || !cfg || n_slots == 0) return GMP_ERR_INVALID_ARG;
+int gmp_server_create(gmp_server** out, gmp_ctx* graph, uint32_t n_slots, const gmp_server_config* cfg) {
+    if (!out || !graph || !cfg || n_slots == 0) return GMP_ERR_INVALID_ARG;
     *out = nullptr;
     if (cfg->max_batch == 0 || cfg->max_ants == 0 || cfg->max_iter == 0) return GMP_ERR_INVALID_ARG;
+    const CtxInfo gi = ctx_info(graph);
+    if (!gi.has_graph) return ctx_fail(graph, GMP_ERR_STATE, "the server needs the road graph loaded");
+    if (!ctx_owns_state(graph)) return ctx_fail(graph, GMP_ERR_STATE, "the server's context must own its traffic state");
+    gmp_params gp{};
+    gmp_get_params(graph, &gp);
     gmp_server* s = new gmp_server();
     s->cfg = *cfg;
-    uint32_t N = 0, E = 0;
+    s->budget = (uint64_t)cfg->mem_budget_mib << 20;
+    s->state[0] = graph;
+    const uint32_t max_steps = gp.max_steps ? gp.max_steps : std::min<uint32_t>(2u * (gi.N - 1u), 4096u);
+    s->route_cap = std::min<uint32_t>(gi.N, std::max<uint32_t>(max_steps, 1u) + 1u);
+    auto fail_create = [&](int rc, gmp_ctx* blame) {
+        if (blame) ctx_fail(graph, rc, gmp_last_error(blame));
+        release(s);
+        delete s;
+        return rc;
+    };
+    int rc = gmp_create(&s->state[1], gi.device, 0, nullptr);
+    if (rc != GMP_OK) return fail_create(rc, nullptr);
+    rc = gmp_share_graph(s->state[1], graph, 1);
+    if (rc == GMP_OK) rc = gmp_set_params(s->state[1], &gp);
+    if (rc != GMP_OK) return fail_create(rc, s->state[1]);
+    for (cudaEvent_t& e : s->ready)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_create(GMP_ERR_CUDA, nullptr);
+        }
     for (uint32_t k = 0; k < n_slots; ++k) {
-        if (!slots[k]) {
-            delete s;
-            return GMP_ERR_INVALID_ARG;
-        }
-        const CtxInfo ci = ctx_info(slots[k]);
-        if (!ci.has_graph) {
-            delete s;
-            return ctx_fail(slots[k], GMP_ERR_STATE, "every slot needs the road graph loaded");
-        }
-        if (k > 0 && (ci.N != N || ci.E != E)) {
-            delete s;
-            return ctx_fail(slots[k], GMP_ERR_INVALID_ARG, "slots must hold the same road graph");
-        }
-        N = ci.N;
-        E = ci.E;
-        gmp_params p{};
-        gmp_get_params(slots[k], &p);
-        const uint32_t max_steps = p.max_steps ? p.max_steps : std::min<uint32_t>(N > 0 ? N - 1 : 0, 4096u);
-        s->route_cap = std::max<uint32_t>(max_steps, 1u) + 1u;
-        // admission by memory: the largest job this slot's budget holds, up to max_batch requests
-        uint32_t cap = cfg->max_batch;
-        int rc = GMP_ERR_OOM;
-        while (cap >= 1) {
-            rc = gmp_batch_reserve(slots[k], cap, (uint64_t)cap * cfg->max_ants, cfg->max_iter);
-            if (rc != GMP_ERR_OOM) break;
-            cap = cap > 1 ? cap - std::max<uint32_t>(1u, cap / 4u) : 0u;
-        }
-        if (rc != GMP_OK) {
-            delete s;
-            return rc;
-        }
         Slot sl;
-        sl.ctx = slots[k];
-        sl.cap = cap;
-        s->slots.push_back(std::move(sl));
+        rc = gmp_create(&sl.ctx, gi.device, 0, nullptr);
+        if (rc != GMP_OK) return fail_create(rc, nullptr);
+        s->slots.push_back(sl);
+        ctx_set_stream_alloc(sl.ctx);
+        rc = gmp_share_graph(sl.ctx, graph, 0);
+        if (rc == GMP_OK) rc = gmp_set_params(sl.ctx, &gp);
+        if (rc != GMP_OK) return fail_create(rc, sl.ctx);
     }
     *out = s;
     return GMP_OK;
 }
 
-void gmp_server_destroy(gmp_server* s) { delete s; }
+void gmp_server_destroy(gmp_server* s) {
+    if (!s) return;
+    release(s);
+    delete s;
+}
 
 const char* gmp_server_last_error(const gmp_server* s) { return s ? s->err.c_str() : "null server"; }
+
+int gmp_server_memory(const gmp_server* s, uint64_t* slots_bytes, uint64_t* budget_bytes) {
+    if (!s) return GMP_ERR_INVALID_ARG;
+    if (slots_bytes) *slots_bytes = held_by_slots(s);
+    if (budget_bytes) *budget_bytes = s->budget;
+    return GMP_OK;
+}
 
 int gmp_server_submit(gmp_server* s, const gmp_query* q, uint64_t tag) {
     if (!s || !q) return GMP_ERR_INVALID_ARG;
@@ -234,10 +329,32 @@ int gmp_server_tick(gmp_server* s, uint64_t t_now_ms, uint32_t dt_ms) {
     if (!s) return GMP_ERR_INVALID_ARG;
     if (t_now_ms + dt_ms >= (1ull << 30))
         return sfail(s, GMP_ERR_INVALID_ARG, "the serving clock (departure time) must stay below 2^30 ms");
-    for (Slot& sl : s->slots) {
-        const int rc = gmp_tick(sl.ctx, t_now_ms, dt_ms);
-        if (rc != GMP_OK) return sfail(s, rc, gmp_last_error(sl.ctx));
+    const uint32_t nx = s->cur ^ 1u;
+    gmp_ctx* next = s->state[nx];
+    cudaStream_t st = ctx_info(next).stream;
+    // the version about to be overwritten: after every job still reading it; the version copied: after
+    // the tick that produced it
+    for (const Slot& sl : s->slots)
+        if (sl.busy && sl.version == nx) {
+            const cudaEvent_t e = ctx_done_event(sl.ctx);
+            if (e && cudaStreamWaitEvent(st, e, 0) != cudaSuccess) {
+                cudaGetLastError();
+                return sfail(s, GMP_ERR_CUDA, "ordering the tick after running jobs failed");
+            }
+        }
+    if (s->has_ready[s->cur] && cudaStreamWaitEvent(st, s->ready[s->cur], 0) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(s, GMP_ERR_CUDA, "ordering the tick after the previous one failed");
     }
+    int rc = ctx_copy_state(next, s->state[s->cur]);
+    if (rc == GMP_OK) rc = gmp_tick(next, t_now_ms, dt_ms);
+    if (rc != GMP_OK) return sfail(s, rc, gmp_last_error(next));
+    if (cudaEventRecord(s->ready[nx], st) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(s, GMP_ERR_CUDA, "recording the tick failed");
+    }
+    s->has_ready[nx] = true;
+    s->cur = nx;
     s->clock_ms = t_now_ms + dt_ms;
     return GMP_OK;
 }
@@ -269,12 +386,6 @@ int gmp_server_pump(gmp_server* s, gmp_server_stats* st) {
         st->completed = s->completed;
         st->rejected = s->rejected;
     }
-    return GMP_OK;
-}
-
-int gmp_server_slot_capacity(const gmp_server* s, uint32_t slot, uint32_t* requests_per_job) {
-    if (!s || !requests_per_job || slot >= s->slots.size()) return GMP_ERR_INVALID_ARG;
-    *requests_per_job = s->slots[slot].cap;
     return GMP_OK;
 }
 

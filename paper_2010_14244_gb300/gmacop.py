@@ -39,7 +39,7 @@ class TuneResult(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_batch", C.c_uint32), ("max_ants", C.c_uint32), ("max_iter", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("mem_budget_mib", C.c_uint32)]
 
 
 class ServerStats(C.Structure):
@@ -109,10 +109,11 @@ SIGNATURES = {
     "gmp_multi_last_error": (C.c_char_p, [_vp]),
     "gmp_multi_launch": (_i32, [_vp, C.POINTER(_vp), _u32]),
     "gmp_batch_ready": (_i32, [_vp, C.POINTER(C.c_int)]),
-    "gmp_server_create": (_i32, [C.POINTER(_vp), C.POINTER(_vp), _u32, C.POINTER(ServerConfig)]),
+    "gmp_server_create": (_i32, [C.POINTER(_vp), _vp, _u32, C.POINTER(ServerConfig)]),
     "gmp_server_destroy": (None, [_vp]),
     "gmp_server_last_error": (C.c_char_p, [_vp]),
-    "gmp_server_slot_capacity": (_i32, [_vp, _u32, C.POINTER(_u32)]),
+    "gmp_server_memory": (_i32, [_vp, C.POINTER(_u64), C.POINTER(_u64)]),
+    "gmp_share_graph": (_i32, [_vp, _vp, C.c_int]),
     "gmp_server_submit": (_i32, [_vp, C.POINTER(Query), _u64]),
     "gmp_server_tick": (_i32, [_vp, _u64, _u32]),
     "gmp_server_pump": (_i32, [_vp, C.POINTER(ServerStats)]),
@@ -184,6 +185,11 @@ class Context:
     def set_stream(self, stream=None):
         handle = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._check(lib().gmp_set_stream(self._h, handle))
+
+    def share_graph(self, owner, own_state: bool = False):
+        """gmp_share_graph: read owner's road graph in place (and its traffic state, unless own_state)."""
+        self._check(lib().gmp_share_graph(self._h, owner._h, int(bool(own_state))))
+        self.n_nodes, self.n_edges = owner.n_nodes, owner.n_edges
 
     def bind_workspace(self, dev_ptr: int, nbytes: int):
         """gmp_bind_workspace: carve every later device allocation of this context from caller-owned
@@ -368,17 +374,17 @@ class Context:
 
 
 class Server:
-    """gmp_server: continuous batching over slot contexts that hold replicas of one traffic state."""
+    """gmp_server: continuous batching over n_slots slots that share the road graph and traffic state of
+    one context (`graph`, which must outlive the server)."""
 
-    def __init__(self, slots, max_batch: int, max_ants: int, max_iter: int):
-        self.slots = list(slots)
-        arr = (_vp * len(self.slots))(*[c._h.value for c in self.slots])
-        cfg = ServerConfig(max_batch, max_ants, max_iter, 0)
+    def __init__(self, graph, n_slots: int, max_batch: int, max_ants: int, max_iter: int, mem_budget_mib: int = 0):
+        self.graph = graph
+        cfg = ServerConfig(max_batch, max_ants, max_iter, mem_budget_mib)
         self._h = C.c_void_p()
-        rc = lib().gmp_server_create(C.byref(self._h), arr, len(self.slots), C.byref(cfg))
+        rc = lib().gmp_server_create(C.byref(self._h), graph._h, n_slots, C.byref(cfg))
         if rc != OK:
-            raise GmpError(rc, lib().gmp_last_error(self.slots[0]._h).decode())
-        self.route_cap = self.slots[0].n_nodes + 1
+            raise GmpError(rc, lib().gmp_last_error(graph._h).decode())
+        self.route_cap = graph.n_nodes + 1
         self._buf = np.zeros(1 << 16, np.uint32)
         self._out = (Served * 256)()
 
@@ -397,10 +403,11 @@ class Server:
         if rc != OK:
             raise GmpError(rc, lib().gmp_server_last_error(self._h).decode())
 
-    def capacity(self, slot: int) -> int:
-        n = _u32()
-        self._check(lib().gmp_server_slot_capacity(self._h, slot, C.byref(n)))
-        return int(n.value)
+    def memory(self) -> tuple[int, int]:
+        """(bytes the slots' workspaces hold together, the server's budget in bytes; 0 = none)."""
+        held, budget = _u64(), _u64()
+        self._check(lib().gmp_server_memory(self._h, C.byref(held), C.byref(budget)))
+        return int(held.value), int(budget.value)
 
     def submit(self, q, tag: int):
         cq = Context._cq(q)

@@ -1,7 +1,7 @@
 """Serving loop on the C ABI: Poisson route requests, periodic traffic ticks, continuous batching.
 
 The loop only marshals: arrivals are submitted to the native server (gmp_server_*), which admits them
-into jobs on idle slots; ticks advance the device-resident traffic state on every slot; finished
+into jobs on idle slots; ticks advance the device-resident traffic state the slots share; finished
 requests are taken back with their host timestamps. Latency is measured from each request's scheduled
 arrival time to the moment the server saw its job finish (both on the host's monotonic clock).
 """
@@ -18,20 +18,18 @@ from .workloads import Query
 
 def make_server(wl, n_slots: int, max_batch: int, max_ants: int, max_iter: int, mem_budget: int = 0,
                 device: int = 0, params: dict | None = None):
-    """Slot contexts holding replicas of the workload's traffic state, and a server over them. On any
-    failure the contexts created so far are closed before the error propagates."""
-    slots = []
+    """A context holding the workload's road graph and traffic state, and a server of n_slots slots over it
+    (the slots share that graph; mem_budget bounds their workspaces together, in bytes). Returns (server,
+    [graph context]); the context must be closed after the server. On failure the context is closed
+    before the error propagates."""
+    graph = G.Context(device)
     try:
-        for _ in range(n_slots):
-            c = G.Context(device, mem_budget)
-            slots.append(c)
-            c.load_workload(wl)
-            if params:
-                c.set_params(**params)
-        return G.Server(slots, max_batch, max_ants, max_iter), slots
+        graph.load_workload(wl)
+        if params:
+            graph.set_params(**params)
+        return G.Server(graph, n_slots, max_batch, max_ants, max_iter, mem_budget >> 20), [graph]
     except Exception:
-        for c in slots:
-            c.close()
+        graph.close()
         raise
 
 

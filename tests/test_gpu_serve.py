@@ -2,7 +2,8 @@
 
 Each served result must equal the same request solved alone on a context whose traffic state went
 through the same ticks (and departing at the same clock), bit for bit; a sample is also checked against
-the oracle's tick chain and colony. Admission follows the slots' memory budgets."""
+the oracle's tick chain and colony. The slots share one road graph and traffic state; admission follows
+the server's memory budget."""
 import dataclasses
 
 import numpy as np
@@ -114,35 +115,70 @@ def test_served_equals_alone_and_oracle(gm, orc):
 
 
 def test_admission_follows_memory_budget(gm):
+    """The server's budget bounds the memory the slots' workspaces hold together: with room for a few
+    requests' tables and routes, jobs are cut down to what fits next to the other slot's, no pump ever
+    finds the slots above the budget, and every request still completes."""
     from paper_2010_14244_gb300 import serving
 
     wl = W.grid64(n_queries=1)
-    per_query = wl.net.n_edges * 24  # pheromone, its float copy, deposits and heuristic
-    probe = gm.Context(0)
-    probe.load_workload(wl)
-    base = probe.get_params()
-    probe.close()
-    assert base["mode"] == 0
     budget = 64 << 20
     srv, slots = serving.make_server(wl, n_slots=2, max_batch=512, max_ants=256, max_iter=10, mem_budget=budget)
     try:
-        cap = srv.capacity(0)
-        assert 1 <= cap < 512
-        assert cap * per_query < budget
-        reqs = _mixed_requests(wl.net.n_nodes, 3 * cap, seed=4)
+        assert srv.memory() == (0, budget)
+        reqs = _mixed_requests(wl.net.n_nodes, 200, seed=4)
         for i, q in enumerate(reqs):
             srv.submit(dataclasses.replace(q, n_iter=2), i)
-        done = []
+        done, peak = [], 0
         for _ in range(200000):
             st = srv.pump()
             done += srv.take()
+            peak = max(peak, srv.memory()[0])
+            assert srv.memory()[0] <= budget
             if st["queued"] == 0 and st["in_flight"] == 0 and st["done_waiting"] == 0:
                 break
-        assert len(done) == len(reqs)
-        assert max(r["batch_size"] for r in done) <= cap
+        assert len(done) == len(reqs) and all(r["status"] == gm.OK for r in done)
+        assert 1 <= max(r["batch_size"] for r in done) < 200
+        assert peak > budget // 4
     finally:
         srv.close()
         for c in slots:
+            c.close()
+
+
+def test_views_share_one_graph(gm, orc):
+    """gmp_share_graph: a view reads its owner's road graph and traffic state in place and solves exactly
+    like it; a view with a traffic state of its own ticks without touching the owner's; what a view may not
+    change is refused; an owner with views cannot load another graph."""
+    wl = W.grid10()
+    owner, view, twin, ref = gm.Context(0), gm.Context(0), gm.Context(0), gm.Context(0)
+    try:
+        owner.load_workload(wl)
+        ref.load_workload(wl)
+        view.share_graph(owner)
+        twin.share_graph(owner, own_state=True)
+        q = wl.queries[0]
+        base = owner.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed)
+        for c in (view, twin):
+            _same(c.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed), base)
+        for call in (lambda: view.set_densities(wl.vehicles), lambda: view.tick(0, 1000),
+                     lambda: view.set_params(h_sat_ms=2500), lambda: twin.set_signals(wl.signals),
+                     lambda: owner.load_workload(wl)):
+            with pytest.raises(gm.GmpError) as e:
+                call()
+            assert e.value.code == gm.ERR_STATE
+        # the twin's own traffic state moves on alone: it equals a separate context ticked the same way
+        twin.tick(0, 1000)
+        ref.tick(0, 1000)
+        np.testing.assert_array_equal(twin.densities(), ref.densities())
+        np.testing.assert_array_equal(twin.phase_order(), ref.phase_order())
+        twin.set_params(t_dep_ms=1000)
+        ref.set_params(t_dep_ms=1000)
+        _same(twin.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed),
+              ref.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed))
+        np.testing.assert_array_equal(owner.densities(), wl.vehicles)
+        _same(view.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed), base)
+    finally:
+        for c in (view, twin, owner, ref):
             c.close()
 
 
