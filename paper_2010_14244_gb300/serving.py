@@ -48,6 +48,8 @@ class ServeReport:
     ant_walks: int = 0       # ants x iterations of the completed requests
     successes: int = 0       # ant walks that reached the destination
     unfinished: int = 0      # requests of the window still queued or running when the drain ended
+    served_in_window: int = 0  # requests (of any arrival time) that finished inside the window
+    window_only_s: float = 0.0  # length of the window alone
     results: list = field(repr=False, default_factory=list)
 
     def summary(self) -> dict:
@@ -60,6 +62,7 @@ class ServeReport:
             "completed": self.completed,
             "unfinished": self.unfinished,
             "queries_per_s": per_s(self.completed),
+            "served_per_s_in_window": self.served_in_window / self.window_only_s if self.window_only_s else 0.0,
             "routed_queries_per_s": per_s(self.routed),
             "routed_fraction": self.routed / self.completed if self.completed else 0.0,
             "success_fraction": self.successes / self.ant_walks if self.ant_walks else 0.0,
@@ -136,4 +139,5 @@ def run_poisson(server: G.Server, make_request, rate_per_s: float, duration_s: f
                        routed=sum(1 for r in win if r["status"] == 0),
                        ant_walks=sum(walks[r["tag"]] for r in win),
                        successes=int(sum(r["n_success"] for r in win)), unfinished=submitted - len(win),
-                       results=done if keep_results else [])
+                       served_in_window=sum(1 for r in done if w0 <= r["t_done_ns"] < w1),
+                       window_only_s=(w1 - w0) * 1e-9, results=done if keep_results else [])
