@@ -4,6 +4,7 @@
     python -m paper_2010_14244_gb300.run_workload geo100k --queries 64 --iterations 4
     python -m paper_2010_14244_gb300.run_workload geo1m --queries 64 --ants 128 --iterations 30 --ticks 3
     python -m paper_2010_14244_gb300.run_workload grid64 --flags 256      # exact heuristic
+    python -m paper_2010_14244_gb300.run_workload grid10 --mode 2 --lanes 8  # the persistent job
 
 Prints one JSON line per run with the job's device time (CUDA events on the library's stream) and the
 library's per-kernel-group times of that job with --kernel-times (construction, iteration end,
@@ -29,6 +30,9 @@ def main():
     p.add_argument("--tau-layout", type=int, default=0)
     p.add_argument("--flags", type=int, default=0, help="GMP_FLAG_* bits (e.g. 256: exact heuristic)")
     p.add_argument("--kernel-times", action="store_true", help="events around every kernel; report their times")
+    p.add_argument("--alpha", type=float, default=0.0, help="pheromone exponent of every colony (0 = its own)")
+    p.add_argument("--free-running", action="store_true", help="sub-warp ants without warp lockstep")
+    p.add_argument("--pheromone", action="store_true", help="read colony 0's pheromone table after each run")
     args = p.parse_args()
 
     import dataclasses
@@ -50,11 +54,14 @@ def main():
         make = serving.uniform_requests(wl.net.n_nodes, args.ants or 128, args.iterations or 30, seed=9)
         wl.queries = [make(i) for i in range(args.queries or 64)]
     qs = wl.queries[: args.queries] if args.queries else wl.queries
-    qs = [dataclasses.replace(q, n_ants=args.ants or q.n_ants, n_iter=args.iterations or q.n_iter) for q in qs]
+    qs = [dataclasses.replace(q, n_ants=args.ants or q.n_ants, n_iter=args.iterations or q.n_iter,
+                              alpha=args.alpha or q.alpha) for q in qs]
     stream = torch.cuda.Stream()
     ctx = gmacop.Context(0, stream=stream)
     ctx.load_workload(wl)
-    ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, tau_layout=args.tau_layout, flags=args.flags | (gmacop.FLAG_KERNEL_TIMING if args.kernel_times else 0))
+    flags = args.flags | (gmacop.FLAG_KERNEL_TIMING if args.kernel_times else 0)
+    flags |= gmacop.FLAG_NO_LOCKSTEP if args.free_running else 0
+    ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, tau_layout=args.tau_layout, flags=flags)
     ctx.stage(qs)
     clock = 0
     for r in range(args.repeat):
@@ -69,6 +76,8 @@ def main():
             e1.record(stream)
             e1.synchronize()
         res = ctx.collect()
+        if args.pheromone:
+            ctx.pheromone(0)
         print(json.dumps({"run": r, "workload": args.workload, "colonies": len(qs), "job_ms": e0.elapsed_time(e1),
                           "kernel_ms": ctx.kernel_times() if args.kernel_times else None,
                           "host_ms": (time.perf_counter() - t0) * 1e3,
