@@ -15,6 +15,7 @@
 #include <string>
 #include <iterator>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
@@ -157,16 +158,23 @@ struct gmp_ctx {
     uint32_t max_phases = 0;  // most phases at any intersection (above 2: the iteration end's general pass)
     uint32_t *row_ptr = nullptr, *col = nullptr, *len = nullptr, *in_ptr = nullptr, *in_edge = nullptr;
     uint32_t* in_tail = nullptr;  // tail of each in_edge entry (exact Calc_Dist relaxes towards tails)
-    uint32_t *ff = nullptr, *cap = nullptr;
+    // Per-approach tables are in slot order (slot i = road in_edge[i], so an intersection's approaches
+    // are contiguous); phase tables are phase-major (entry p * N + v). The C ABI speaks road order and
+    // node-major phase rows; the calls that take or return those tables convert.
+    uint32_t *ff = nullptr, *cap = nullptr;  // per slot: free-flow time, jam capacity
     uint16_t* speed = nullptr;
-    uint8_t* lanes = nullptr;
+    uint8_t* lanes = nullptr;     // per road
+    uint8_t* lanes_in = nullptr;  // per slot
     int32_t *x = nullptr, *y = nullptr;
-    uint8_t *nph = nullptr, *ephase = nullptr, *order = nullptr;
-    uint32_t *cycle = nullptr, *offset = nullptr, *green = nullptr, *red = nullptr, *veh = nullptr;
+    uint8_t *nph = nullptr, *ephase = nullptr, *order = nullptr;  // ephase per slot, order node-major
+    uint32_t *cycle = nullptr, *offset = nullptr, *green = nullptr, *red = nullptr;  // green, red phase-major
+    uint32_t* veh = nullptr;      // per slot
+    bool red_high = false;        // red planes at or above max_phases may hold non-zero values
     EdgeRec* rec = nullptr;
-    uint32_t* tick_leave = nullptr;        // serving tick: discharge of each road (E)
+    uint32_t* tick_leave = nullptr;        // serving tick: discharge of each slot (E); density upload scratch
     unsigned long long* tick_K = nullptr;  // serving tick: discharge of each node (N)
     std::vector<int32_t> hx, hy;  // host copy of node coordinates (destination lookups at staging)
+    std::shared_ptr<const std::vector<uint32_t>> hin_edge;  // host copy of in_edge (road-order conversions)
     // A context may view another context's road graph (gmp_share_graph): the static arrays always, the
     // traffic state (vehicles, red times, phase order, road records, tick scratch) too unless it keeps a
     // state of its own. What a view borrowed is never freed by it.
@@ -379,7 +387,7 @@ void drop_borrowed(gmp_ctx* c) {
     if (c->lender) {
         c->row_ptr = c->col = c->len = c->in_ptr = c->in_edge = c->in_tail = c->ff = c->cap = nullptr;
         c->speed = nullptr;
-        c->lanes = nullptr;
+        c->lanes = c->lanes_in = nullptr;
         c->x = c->y = nullptr;
         c->nph = c->ephase = nullptr;
         c->cycle = c->offset = c->green = nullptr;
@@ -409,6 +417,7 @@ void free_graph(gmp_ctx* c) {
     dfree(c, &c->cap);
     dfree(c, &c->speed);
     dfree(c, &c->lanes);
+    dfree(c, &c->lanes_in);
     dfree(c, &c->x);
     dfree(c, &c->y);
     dfree(c, &c->nph);
@@ -424,16 +433,42 @@ void free_graph(gmp_ctx* c) {
     dfree(c, &c->tick_K);
     c->has_graph = false;
     c->N = c->E = 0;
+    c->hin_edge.reset();
+    c->red_high = false;
 }
 
 uint32_t hsat_of(const gmp_ctx* c) { return c->prm.h_sat_ms ? c->prm.h_sat_ms : kHsatDefault; }
 
-// Densities or signals or params changed: rebuild road records and the phase order.
+// What the intersection passes read and write, on this context's graph and traffic state.
+QueueTables queue_tables(const gmp_ctx* c) {
+    QueueTables t{};
+    t.n_nodes = c->N;
+    t.h_sat = hsat_of(c);
+    t.thr = c->prm.thr_permille;
+    t.row_ptr = c->row_ptr;
+    t.in_ptr = c->in_ptr;
+    t.in_edge = c->in_edge;
+    t.in_tail = c->in_tail;
+    t.nph = c->nph;
+    t.cycle = c->cycle;
+    t.offset = c->offset;
+    t.green = c->green;
+    t.ephase = c->ephase;
+    t.lanes = c->lanes_in;
+    t.cap = c->cap;
+    t.ff = c->ff;
+    t.veh = c->veh;
+    t.red = c->red;
+    t.order = c->order;
+    t.rec = c->rec;
+    t.leave = c->tick_leave;
+    t.K = c->tick_K;
+    return t;
+}
+
+// Densities or signals or params changed: rebuild the phase orders and every road record.
 int refresh_dynamic(gmp_ctx* c) {
-    GMP_CUDA(c, launch_edge_dynamic(c->stream, c->E, c->row_ptr, c->col, c->ff, c->cap, c->lanes, c->veh, c->nph,
-                                    hsat_of(c), c->prm.thr_permille, c->rec));
-    GMP_CUDA(c, launch_queue_preempt(c->stream, c->N, 0u, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
-                                     c->ephase, c->veh, c->cap, c->red, c->order, c->rec));
+    GMP_CUDA(c, launch_queue(c->stream, queue_tables(c), c->max_phases, QueuePass::kRefresh));
     return GMP_OK;
 }
 
@@ -451,6 +486,7 @@ int copy_state(gmp_ctx* dst, const gmp_ctx* src) {
     GMP_CUDA(dst, cudaMemcpyAsync(dst->order, src->order, (size_t)dst->N * kMaxPhases, cudaMemcpyDeviceToDevice, s));
     GMP_CUDA(dst, cudaMemcpyAsync(dst->rec, src->rec, std::max<size_t>(dst->E, 1) * sizeof(EdgeRec),
                                   cudaMemcpyDeviceToDevice, s));
+    dst->red_high = src->red_high;
     return GMP_OK;
 }
 
@@ -528,19 +564,7 @@ IterEndArgs iter_end_args(gmp_ctx* c, uint32_t Q, const DevQuery* dq, uint64_t* 
     e.ant_steps = ant_steps;
     e.ant_wait = ant_wait;
     e.best_route = best_route;
-    e.row_ptr = c->row_ptr;
-    e.in_ptr = c->in_ptr;
-    e.in_edge = c->in_edge;
-    e.nph = c->nph;
-    e.cycle = c->cycle;
-    e.offset = c->offset;
-    e.green = c->green;
-    e.ephase = c->ephase;
-    e.veh = c->veh;
-    e.cap = c->cap;
-    e.red = c->red;
-    e.order = c->order;
-    e.rec = c->rec;
+    e.qt = queue_tables(c);
     return e;
 }
 
@@ -577,18 +601,7 @@ int enqueue_persistent(gmp_ctx* c) {
     p.tau = b.tau;
     p.th = b.th;
     p.best_route = b.best_route;
-    p.in_ptr = c->in_ptr;
-    p.in_edge = c->in_edge;
-    p.nph = c->nph;
-    p.cycle = c->cycle;
-    p.offset = c->offset;
-    p.green = c->green;
-    p.ephase = c->ephase;
-    p.veh = c->veh;
-    p.cap = c->cap;
-    p.red = c->red;
-    p.order = c->order;
-    p.rec = c->rec;
+    p.qt = queue_tables(c);
     p.n_nodes = c->N;
     p.max_iter = b.maxI;
     p.flags = c->prm.flags;
@@ -735,9 +748,7 @@ int enqueue_job(gmp_ctx* c) {
             e.n_nodes = (it % B == j) ? n_nodes : 0u;
             GMP_CUDA(c, launch_iter_end(bs, e));
             if (e.n_nodes && b.queue_general) {  // the iteration end updated the intersections with <= 2 phases
-                GMP_CUDA(c, launch_queue_preempt(bs, c->N, 3u, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle,
-                                                 c->offset, c->green, c->ephase, c->veh, c->cap, c->red, c->order,
-                                                 c->rec));
+                GMP_CUDA(c, launch_queue_general(bs, e.qt, QueuePass::kIterate));
                 ++n;
             }
             if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 2 + 2 * it], bs, cudaEventRecordExternal));
@@ -933,6 +944,7 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     GMP_TRY(dalloc(c, &c->cap, E));
     GMP_TRY(dalloc(c, &c->speed, E));
     GMP_TRY(dalloc(c, &c->lanes, E));
+    GMP_TRY(dalloc(c, &c->lanes_in, E));
     GMP_TRY(dalloc(c, &c->x, N));
     GMP_TRY(dalloc(c, &c->y, N));
     GMP_TRY(dalloc(c, &c->nph, N));
@@ -963,9 +975,11 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     GMP_CUDA(c, cudaMemsetAsync(c->green, 0, N * 4ull * kMaxPhases, c->stream));
     GMP_CUDA(c, cudaMemsetAsync(c->red, 0, N * 4ull * kMaxPhases, c->stream));
     GMP_CUDA(c, cudaMemsetAsync(c->veh, 0, std::max<size_t>(E, 1) * 4, c->stream));
-    GMP_CUDA(c, launch_edge_static(c->stream, E, c->len, c->speed, c->lanes, c->ff, c->cap));
+    GMP_CUDA(c, launch_edge_static(c->stream, E, c->in_edge, c->len, c->speed, c->lanes, c->ff, c->cap, c->lanes_in));
     GMP_TRY(refresh_dynamic(c));
     GMP_TRY(sync(c));
+    c->hin_edge = std::make_shared<const std::vector<uint32_t>>(std::move(in_edge));
+    c->red_high = false;
     c->has_graph = true;
     return GMP_OK;
 }
@@ -997,6 +1011,8 @@ int gmp_share_graph(gmp_ctx* c, gmp_ctx* owner, int own_state) {
     c->cap = owner->cap;
     c->speed = owner->speed;
     c->lanes = owner->lanes;
+    c->lanes_in = owner->lanes_in;
+    c->hin_edge = owner->hin_edge;
     c->x = owner->x;
     c->y = owner->y;
     c->nph = owner->nph;
@@ -1066,14 +1082,22 @@ int gmp_set_signals(gmp_ctx* c, const uint8_t* n_phases, const uint32_t* cycle_m
             return fail(c, GMP_ERR_INVALID_ARG, "road %u: approach phase %u beyond the head's %u phases", e, edge_phase[e], P);
     }
     sync(c);
+    // phase-major greens, approach phases in slot order (host staging, waited for below)
+    std::vector<uint32_t> planes((size_t)c->N * kMaxPhases);
+    for (uint32_t v = 0; v < c->N; ++v)
+        for (uint32_t p = 0; p < kMaxPhases; ++p) planes[(size_t)p * c->N + v] = green_ms[(size_t)v * kMaxPhases + p];
+    std::vector<uint8_t> slot_phase(c->E);
+    const std::vector<uint32_t>& ie = *c->hin_edge;
+    for (uint32_t i = 0; i < c->E; ++i) slot_phase[i] = edge_phase[ie[i]];
     GMP_TRY(upload(c, c->nph, n_phases, c->N));
     c->max_phases = 0;
     for (uint32_t v = 0; v < c->N; ++v) c->max_phases = std::max<uint32_t>(c->max_phases, n_phases[v]);
     GMP_TRY(upload(c, c->cycle, cycle_ms, c->N));
     GMP_TRY(upload(c, c->offset, offset_ms, c->N));
-    GMP_TRY(upload(c, c->green, green_ms, (size_t)c->N * kMaxPhases));
-    GMP_TRY(upload(c, c->ephase, edge_phase, c->E));
+    GMP_TRY(upload(c, c->green, planes.data(), planes.size()));
+    GMP_TRY(upload(c, c->ephase, slot_phase.data(), c->E));
     GMP_CUDA(c, cudaMemsetAsync(c->red, 0, c->N * 4ull * kMaxPhases, c->stream));
+    c->red_high = false;
     GMP_TRY(refresh_dynamic(c));
     return sync(c);
 }
@@ -1083,7 +1107,16 @@ int gmp_set_red_times(gmp_ctx* c, const uint32_t* red_ms) {
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
     if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     cudaSetDevice(c->device);
-    GMP_TRY(upload(c, c->red, red_ms, (size_t)c->N * kMaxPhases));
+    std::vector<uint32_t> planes((size_t)c->N * kMaxPhases);
+    bool high = false;  // a non-zero entry in a plane the tick's node pass does not visit
+    for (uint32_t v = 0; v < c->N; ++v)
+        for (uint32_t p = 0; p < kMaxPhases; ++p) {
+            const uint32_t r = red_ms[(size_t)v * kMaxPhases + p];
+            planes[(size_t)p * c->N + v] = r;
+            high |= p >= c->max_phases && r != 0;
+        }
+    GMP_TRY(upload(c, c->red, planes.data(), planes.size()));
+    c->red_high = high;
     GMP_TRY(refresh_dynamic(c));
     return sync(c);
 }
@@ -1093,7 +1126,8 @@ int gmp_set_densities(gmp_ctx* c, const uint32_t* vehicles) {
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
     if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     cudaSetDevice(c->device);
-    GMP_TRY(upload(c, c->veh, vehicles, c->E));
+    GMP_TRY(upload(c, c->tick_leave, vehicles, c->E));  // road order, then into slot order
+    GMP_CUDA(c, launch_gather_u32(c->stream, c->E, c->in_edge, c->tick_leave, c->veh));
     GMP_TRY(refresh_dynamic(c));
     return sync(c);
 }
@@ -1103,7 +1137,7 @@ int gmp_set_densities_async(gmp_ctx* c, const uint32_t* d_vehicles) {
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
     if (!c->own_state) return fail(c, GMP_ERR_STATE, "this context reads another context's traffic state");
     cudaSetDevice(c->device);
-    if (c->E) GMP_CUDA(c, cudaMemcpyAsync(c->veh, d_vehicles, c->E * 4ull, cudaMemcpyDeviceToDevice, c->stream));
+    GMP_CUDA(c, launch_gather_u32(c->stream, c->E, c->in_edge, d_vehicles, c->veh));
     return refresh_dynamic(c);
 }
 
@@ -1586,16 +1620,24 @@ int gmp_get_densities(gmp_ctx* c, uint32_t* vehicles) {
     if (!c || (!vehicles && c->E)) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
     cudaSetDevice(c->device);
-    if (c->E) GMP_CUDA(c, cudaMemcpyAsync(vehicles, c->veh, c->E * 4ull, cudaMemcpyDeviceToHost, c->stream));
-    return sync(c);
+    std::vector<uint32_t> slots(c->E);
+    if (c->E) GMP_CUDA(c, cudaMemcpyAsync(slots.data(), c->veh, c->E * 4ull, cudaMemcpyDeviceToHost, c->stream));
+    GMP_TRY(sync(c));
+    const std::vector<uint32_t>& ie = *c->hin_edge;
+    for (uint32_t i = 0; i < c->E; ++i) vehicles[ie[i]] = slots[i];
+    return GMP_OK;
 }
 
 int gmp_get_red_times(gmp_ctx* c, uint32_t* red_ms) {
     if (!c || !red_ms) return GMP_ERR_INVALID_ARG;
     if (!c->has_graph) return fail(c, GMP_ERR_STATE, "load a graph first");
     cudaSetDevice(c->device);
-    GMP_CUDA(c, cudaMemcpyAsync(red_ms, c->red, (size_t)c->N * kMaxPhases * 4, cudaMemcpyDeviceToHost, c->stream));
-    return sync(c);
+    std::vector<uint32_t> planes((size_t)c->N * kMaxPhases);
+    GMP_CUDA(c, cudaMemcpyAsync(planes.data(), c->red, planes.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    GMP_TRY(sync(c));
+    for (uint32_t v = 0; v < c->N; ++v)
+        for (uint32_t p = 0; p < kMaxPhases; ++p) red_ms[(size_t)v * kMaxPhases + p] = planes[(size_t)p * c->N + v];
+    return GMP_OK;
 }
 
 int gmp_tick(gmp_ctx* c, uint64_t t_now_ms, uint32_t dt_ms) {
@@ -1605,10 +1647,15 @@ int gmp_tick(gmp_ctx* c, uint64_t t_now_ms, uint32_t dt_ms) {
     if (t_now_ms > kTickClockMax || dt_ms > kTickDtMax)
         return fail(c, GMP_ERR_INVALID_ARG, "tick clock must be <= 2^48 ms and dt <= 2^30 ms");
     cudaSetDevice(c->device);
-    GMP_CUDA(c, launch_tick(c->stream, c->N, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle, c->offset, c->green,
-                            c->ephase, c->lanes, c->veh, c->order, t_now_ms, dt_ms, hsat_of(c), c->tick_leave,
-                            c->tick_K, c->red));
-    return refresh_dynamic(c);
+    const QueueTables t = queue_tables(c);
+    GMP_CUDA(c, launch_tick_node(c->stream, t, t_now_ms, dt_ms, c->max_phases, c->tick_leave, c->tick_K));
+    if (c->red_high) {  // the planes the node pass does not visit: every phase there is >= the node's count
+        GMP_CUDA(c, cudaMemsetAsync(c->red + (size_t)c->max_phases * c->N, 0,
+                                    (size_t)(kMaxPhases - c->max_phases) * c->N * 4, c->stream));
+        c->red_high = false;
+    }
+    GMP_CUDA(c, launch_queue(c->stream, t, c->max_phases, QueuePass::kTick));
+    return GMP_OK;
 }
 
 int gmp_get_edge_times(gmp_ctx* c, uint32_t* tt_ms, uint32_t* qd_ms) {
@@ -1989,9 +2036,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
         e.it = it;
         GMP_CUDA(c, launch_iter_end(s, e));
         if (c->max_phases > 2)  // the iteration end updated the intersections with <= 2 phases only
-            GMP_CUDA(c, launch_queue_preempt(s, c->N, 3u, c->row_ptr, c->in_ptr, c->in_edge, c->nph, c->cycle,
-                                             c->offset, c->green, c->ephase, c->veh, c->cap, c->red, c->order,
-                                             c->rec));
+            GMP_CUDA(c, launch_queue_general(s, e.qt, QueuePass::kIterate));
     }
     GMP_CUDA(c, launch_finalize(s, 1, dq, qs, best_route, c->col, S, reinterpret_cast<DevResult*>(d_result), d_route));
     return GMP_OK;

@@ -97,10 +97,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// floor(sqrt(n)) for n < 2^58: a binary32 estimate corrected to the exact integer root (below 2^29, so
-// the checks are single 32 x 32 -> 64-bit products).
+// floor(sqrt(n)) for n < 2^58: a binary32 estimate (n from its two 32-bit halves, the hardware's
+// approximate square root) corrected to the exact integer root. The root is below 2^29, so the checks
+// are single 32 x 32 -> 64-bit products. The estimate is within about r / 2^22 of the root r: under two
+// units, so at most two turns of the loops, for distances below 2^22 dm (about 420 km).
 __device__ __forceinline__ uint32_t isqrt_u64(uint64_t n) {
-    uint32_t r = (uint32_t)__fsqrt_rn(__ull2float_rn(n));
+    const float f = __fmaf_rn(__uint2float_rn((uint32_t)(n >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)n));
+    float s;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(f));
+    uint32_t r = __float2uint_rz(s);
     while ((uint64_t)r * r > n) --r;
     while ((uint64_t)(r + 1u) * (r + 1u) <= n) ++r;
     return r;
@@ -347,12 +352,18 @@ __device__ __forceinline__ uint32_t roulette_weight_f(uint32_t sbits, const Weig
     return (sc.mzero || w == 0u) ? 1u : w;
 }
 
+// floor(a * b / d) for 32-bit operands and d >= 1: a 32-bit division when the product fits 32 bits.
+__device__ __forceinline__ uint64_t mul_div_u32(uint32_t a, uint32_t b, uint32_t d) {
+    const uint64_t p = (uint64_t)a * b;
+    return (p >> 32) == 0 ? (uint64_t)((uint32_t)p / d) : p / d;
+}
+
 // Congested travel time ff * cap / max(cap - n, max(1, cap / 20)), saturating at 2^26 ms.
 __device__ __forceinline__ uint32_t edge_time_ms(uint32_t ff, uint32_t cap, uint32_t n) {
     uint32_t fl = cap / 20u;
     if (fl < 1u) fl = 1u;
     const uint32_t den = (n < cap && cap - n > fl) ? cap - n : fl;
-    const uint64_t t = (uint64_t)ff * cap / den;
+    const uint64_t t = mul_div_u32(ff, cap, den);
     return t > kTimeClamp ? kTimeClamp : (uint32_t)t;
 }
 

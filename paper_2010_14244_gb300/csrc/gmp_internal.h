@@ -12,6 +12,29 @@
 
 namespace gmp {
 
+// What the per-intersection passes read and write: the queue / preemption update (Calc_Dens, Comp_Thres)
+// and the serving tick. Approaches are addressed by in-slot: slot i (in_ptr[v] <= i < in_ptr[v + 1]) is
+// road in_edge[i] into v, and every per-approach table below is stored in slot order, so one
+// intersection's approaches are contiguous. Phase tables are phase-major (entry p * n_nodes + v), so a
+// warp over consecutive intersections reads one contiguous run per phase.
+struct QueueTables {
+    uint32_t n_nodes;
+    uint32_t h_sat;                          // saturation headway per lane, ms
+    uint32_t thr;                            // congestion threshold, per mille of capacity (kThrOff: off)
+    const uint32_t *row_ptr, *in_ptr, *in_edge, *in_tail;
+    const uint8_t* nph;                      // phases per intersection (0: unsignalised)
+    const uint32_t *cycle, *offset;
+    const uint32_t* green;                   // phase-major green times
+    const uint8_t *ephase, *lanes;           // per slot: approach phase at the head, lanes
+    const uint32_t *cap, *ff;                // per slot: jam capacity, free-flow time (ms)
+    uint32_t* veh;                           // per slot: vehicles on the road (traffic state)
+    uint32_t* red;                           // phase-major red-time accumulators (traffic state)
+    uint8_t* order;                          // 8 per intersection: phases in plan order (traffic state)
+    EdgeRec* rec;                            // per road (by road id): the records the walk reads
+    const uint32_t* leave;                   // tick: vehicles each slot's road discharged
+    const unsigned long long* K;             // tick: vehicles each intersection discharged
+};
+
 // Arguments of the construction kernel (one iteration over every ant of the batch).
 struct ConstructArgs {
     const EdgeRec* rec;
@@ -63,13 +86,7 @@ struct IterEndArgs {
     QueryState* qs;
     const uint32_t *routes, *ant_steps, *ant_wait;
     uint32_t* best_route;
-    const uint32_t *row_ptr, *in_ptr, *in_edge;
-    const uint8_t* nph;
-    const uint32_t *cycle, *offset, *green;
-    const uint8_t* ephase;
-    const uint32_t *veh, *cap, *red;
-    uint8_t* order;
-    EdgeRec* rec;
+    QueueTables qt;  // the per-iteration queue update (n_nodes above says whether this launch runs it)
 };
 
 // Per-(colony, iteration) counters of the persistent job.
@@ -91,13 +108,7 @@ struct PersistentArgs {
     uint64_t* tau;
     uint2* th;
     uint32_t* best_route;
-    const uint32_t *in_ptr, *in_edge;
-    const uint8_t* nph;
-    const uint32_t *cycle, *offset, *green;
-    const uint8_t* ephase;
-    const uint32_t *veh, *cap, *red;
-    uint8_t* order;
-    EdgeRec* rec;
+    QueueTables qt;
     uint32_t n_nodes, max_iter, spin_limit;
     uint32_t flags;       // GMP_FLAG_* of the context
     uint32_t node_chunk;  // intersections per queue-update chunk (8..64)
@@ -116,22 +127,27 @@ struct KernelConfig {
 };
 
 // Launchers (gmp_kernels.cu).
-cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* len, const uint16_t* speed,
-                               const uint8_t* lanes, uint32_t* ff, uint32_t* cap);
-cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
-                                const uint32_t* ff, const uint32_t* cap, const uint8_t* lanes, const uint32_t* veh,
-                                const uint8_t* nph, uint32_t h_sat, uint32_t thr, EdgeRec* rec);
-// The queue / preemption update of the intersections with at least min_phases phases (0: all).
-cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, uint32_t min_phases, const uint32_t* row_ptr,
-                                 const uint32_t* in_ptr, const uint32_t* in_edge,
-                                 const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
-                                 const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
-                                 const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec);
-cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
-                        const uint32_t* in_edge, const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
-                        const uint32_t* green, const uint8_t* ephase, const uint8_t* lanes, uint32_t* veh,
-                        const uint8_t* order, uint64_t t_now, uint32_t dt, uint32_t h_sat, uint32_t* leave,
-                        unsigned long long* K, uint32_t* red);
+// Per-slot road constants (slot i is road in_edge[i]): free-flow time, jam capacity and lanes.
+cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* in_edge, const uint32_t* len,
+                               const uint16_t* speed, const uint8_t* lanes_by_road, uint32_t* ff, uint32_t* cap,
+                               uint8_t* lanes);
+// dst[i] = src[idx[i]] for i < n (road order into slot order), and its inverse.
+cudaError_t launch_gather_u32(cudaStream_t s, uint32_t n, const uint32_t* idx, const uint32_t* src, uint32_t* dst);
+cudaError_t launch_gather_u8(cudaStream_t s, uint32_t n, const uint32_t* idx, const uint8_t* src, uint8_t* dst);
+// How a queue pass treats the state it finds.
+enum class QueuePass {
+    kRefresh,  // vehicles, red times or signals changed: every approach's whole record is rewritten
+    kTick,     // kRefresh after applying the tick's discharge (leave, K) to the vehicles
+    kIterate,  // within a job: recompute every order, rewrite an intersection only where it changed
+};
+// The queue / preemption update of every intersection (max_phases: most phases at any of them).
+cudaError_t launch_queue(cudaStream_t s, const QueueTables& t, uint32_t max_phases, QueuePass pass);
+// The same for the intersections with more than two phases only (the iteration end covers the rest).
+cudaError_t launch_queue_general(cudaStream_t s, const QueueTables& t, QueuePass pass);
+// Tick node pass: green phase at t_now, discharge of every approach (leave, K) and the red-time update of
+// phases below red_planes (the others are left as they are).
+cudaError_t launch_tick_node(cudaStream_t s, const QueueTables& t, uint64_t t_now, uint32_t dt,
+                             uint32_t red_planes, uint32_t* leave, unsigned long long* K);
 cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQuery* q, const uint32_t* col,
                               const int32_t* x, const int32_t* y, uint32_t kappa, uint32_t flags, uint64_t* tau,
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,

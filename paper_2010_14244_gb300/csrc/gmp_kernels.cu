@@ -1,9 +1,10 @@
 // sm_103a kernels of the MACO-P route colony (Jindal & Bedi, GMACO-P, Sec. 4.2, Algorithm 2).
 //
-//   k_edge_static     road free-flow time and jam capacity                         (graph load)
-//   k_edge_dynamic    congested travel time, queue delay, threshold flag per road   (Calc_Dens inputs)
-//   k_queue_preempt   per-intersection phase order by the preemptive rule         (Calc_Dens, Comp_Thres)
-//   k_init_batch      initial pheromone, per-colony state                          (Algorithm 2)       
+//   k_edge_static     road free-flow time and jam capacity, per approach slot           (graph load)
+//   k_queue_small     per-intersection phase order by the preemptive rule, and the road records of
+//   k_queue_general   its approaches (congested time, queue delay, green window)     (Calc_Dens, Comp_Thres)
+//   k_tick_node       serving tick: discharge of every approach and red-time update  (Fig. 3 signal block)
+//   k_init_batch      initial pheromone, per-colony state                          (Algorithm 2)
 //   k_construct<G,K>  ant walks: Adj_Neigh, next-node roulette, Eval_Rout, position update, deposits
 //   k_iter_end        Evap_Pher fused with the deposits of Updt_Pher, best-route tracking and the
 //                     per-iteration queue/preemption update, in one launch
@@ -18,136 +19,126 @@
 namespace gmp {
 
 // ------------------------------------------------------------------------------------------------
-// Road attributes
+// Road attributes, per approach slot (slot i holds road in_edge[i])
 // ------------------------------------------------------------------------------------------------
-__global__ void k_edge_static(uint32_t E, const uint32_t* __restrict__ len, const uint16_t* __restrict__ speed,
-                              const uint8_t* __restrict__ lanes, uint32_t* __restrict__ ff, uint32_t* __restrict__ cap) {
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const uint64_t L = len[e], v = speed[e];
+__global__ void k_edge_static(uint32_t E, const uint32_t* __restrict__ in_edge, const uint32_t* __restrict__ len,
+                              const uint16_t* __restrict__ speed, const uint8_t* __restrict__ lanes_by_road,
+                              uint32_t* __restrict__ ff, uint32_t* __restrict__ cap, uint8_t* __restrict__ lanes) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= E) return;
+    const uint32_t e = in_edge[i];
+    const uint64_t L = len[e], v = speed[e], ln = lanes_by_road[e];
     uint64_t f = (L * 360u + v / 2u) / v;  // length / speed in ms, rounded half up
     f = f < 1u ? 1u : (f > kTimeClamp ? kTimeClamp : f);
-    ff[e] = (uint32_t)f;
-    const uint64_t c = (uint64_t)lanes[e] * L / 75u;  // one vehicle per 7.5 m of lane
-    cap[e] = c < 1u ? 1u : (uint32_t)c;
+    ff[i] = (uint32_t)f;
+    const uint64_t c = ln * L / 75u;  // one vehicle per 7.5 m of lane
+    cap[i] = c < 1u ? 1u : (uint32_t)c;
+    lanes[i] = (uint8_t)ln;
 }
 
-__global__ void k_edge_dynamic(uint32_t E, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-                               const uint32_t* __restrict__ ff, const uint32_t* __restrict__ cap,
-                               const uint8_t* __restrict__ lanes, const uint32_t* __restrict__ veh,
-                               const uint8_t* __restrict__ nph, uint32_t h_sat, uint32_t thr,
-                               EdgeRec* __restrict__ rec) {
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const uint32_t v = col[e], n = veh[e], c = cap[e];
-    uint32_t qd = 0;
-    if (nph[v] > 0) {
-        const uint64_t d = (uint64_t)n * h_sat / lanes[e];
-        qd = d > kTimeClamp ? kTimeClamp : (uint32_t)d;
-    }
-    const uint32_t fl = (thr != kThrOff && (uint64_t)n * 1000u > (uint64_t)thr * c) ? 1u : 0u;
-    uint4* r = reinterpret_cast<uint4*>(rec + e);  // first half of the record (see EdgeRec)
-    *r = make_uint4(v, row_ptr[v], edge_time_ms(ff[e], c, n), qd | (fl << 31));
+template <class T>
+__global__ void k_gather(uint32_t n, const uint32_t* __restrict__ idx, const T* __restrict__ src, T* __restrict__ dst) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
 }
 
 // ------------------------------------------------------------------------------------------------
-// Preemptive phase order, one thread per intersection (queue_node in gmp_walk.cuh), for the
-// intersections with at least min_phases phases.
+// Preemptive phase order, one thread per intersection (queue_node_small / queue_node in gmp_walk.cuh):
+// the small kernel covers the intersections with at most two phases, the general one the others.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_queue_preempt(uint32_t N, uint32_t min_phases, const uint32_t* __restrict__ row_ptr,
-                                const uint32_t* __restrict__ in_ptr,
-                                const uint32_t* __restrict__ in_edge,
-                                const uint8_t* __restrict__ nph, const uint32_t* __restrict__ cycle,
-                                const uint32_t* __restrict__ offset, const uint32_t* __restrict__ green,
-                                const uint8_t* __restrict__ ephase, const uint32_t* __restrict__ veh,
-                                const uint32_t* __restrict__ cap, const uint32_t* __restrict__ red,
-                                uint8_t* __restrict__ order, EdgeRec* __restrict__ rec) {
+template <bool FULL, bool TICK>
+__global__ void __launch_bounds__(128) k_queue_small(QueueTables t) {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= N || nph[v] < min_phases) return;
-    queue_node(v, row_ptr, in_ptr, in_edge, nph, cycle, offset, green, ephase, veh, cap, red, order, rec);
+    if (v < t.n_nodes) queue_node_small<FULL, TICK>(v, t);
+}
+
+template <bool FULL, bool TICK>
+__global__ void __launch_bounds__(128) k_queue_general(QueueTables t) {
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < t.n_nodes && t.nph[v] > 2u) queue_node<FULL, TICK>(v, t);
 }
 
 // ------------------------------------------------------------------------------------------------
 // Serving tick: the queue/preemption update with dt > 0 (Fig. 3 signal block, Calc_Dens and Comp_Thres
-// of Sec. 4.2 applied to moving vehicles). Two passes, then the usual refresh of road records and
-// phase orders from the new vehicles and red times.
+// of Sec. 4.2 applied to moving vehicles). The node pass below, then a queue pass that first moves the
+// discharged vehicles on (approach_vehicles in gmp_walk.cuh) and rebuilds the phase orders and records.
 // ------------------------------------------------------------------------------------------------
+// Saturation discharge of one lane count over the tick, lanes * (t + dt) / h_sat - lanes * t / h_sat
+// vehicles (the whole clock counts), per lane count 0..255, capped at 2^32 - 1.
+struct TickCap {
+    uint32_t cap[256];
+};
+
 // Node pass (one thread per node, over its approaches): the phase green at t_now under the current
-// order (every approach is served at an unsignalised node), the discharge of every served approach
-// (saturation flow counted on the whole clock), the node's total discharge, and its red-time update
-// (0 for the green phase and empty phases, + dt saturating otherwise; queues before the discharge).
-__global__ void k_tick_node(uint32_t N, const uint32_t* __restrict__ in_ptr, const uint32_t* __restrict__ in_edge,
-                            const uint8_t* __restrict__ nph, const uint32_t* __restrict__ cycle,
-                            const uint32_t* __restrict__ offset, const uint32_t* __restrict__ green,
-                            const uint8_t* __restrict__ ephase, const uint8_t* __restrict__ lanes,
-                            const uint32_t* __restrict__ veh, const uint8_t* __restrict__ order, uint64_t t_now,
-                            uint32_t dt, uint32_t h_sat, uint32_t* __restrict__ leave,
-                            unsigned long long* __restrict__ K, uint32_t* __restrict__ red) {
+// order (every approach is served at an unsignalised node), the discharge of every served approach, the
+// node's total discharge, and its red-time update for phases below red_planes: 0 for the green phase, for
+// phases without a queue and at or above the node's phase count, + dt saturating otherwise (queues
+// before the discharge). The node's own words (its phase planes below red_planes exist for every node)
+// are loaded together, then its approaches four at a time.
+__global__ void __launch_bounds__(128) k_tick_node(QueueTables t, uint64_t t_now, uint32_t dt, uint32_t red_planes,
+                                                   TickCap tc, uint32_t* __restrict__ leave,
+                                                   unsigned long long* __restrict__ K) {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= N) return;
-    const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
+    if (v >= t.n_nodes) return;
+    const uint32_t N = t.n_nodes;
+    const uint32_t P = t.nph[v], ib = t.in_ptr[v], ie = t.in_ptr[v + 1];
+    const uint32_t cy = t.cycle[v], off = t.offset[v];
+    const uint2 o = *reinterpret_cast<const uint2*>(t.order + (size_t)v * kMaxPhases);
+    uint32_t g[kMaxPhases], rd[kMaxPhases];
+#pragma unroll
+    for (uint32_t p = 0; p < kMaxPhases; ++p) {
+        g[p] = p < red_planes ? t.green[(size_t)p * N + v] : 0u;
+        rd[p] = p < red_planes ? t.red[(size_t)p * N + v] : 0u;
+    }
     uint32_t gph = 0xFFFFFFFFu;
     if (P) {
-        const uint32_t cy = cycle[v];
-        const uint32_t c = (uint32_t)((t_now % cy + cy - offset[v] % cy) % cy);  // position in the cycle
+        const uint32_t c = (uint32_t)((t_now % cy + cy - off % cy) % cy);  // position in the cycle
         uint32_t start = 0;
-        for (uint32_t i = 0; i < P; ++i) {
-            const uint32_t p = order[(size_t)v * kMaxPhases + i];
-            const uint32_t g = green[(size_t)v * kMaxPhases + p];
-            if (c >= start && c < start + g) {
-                gph = p;
-                break;
+#pragma unroll
+        for (uint32_t i = 0; i < kMaxPhases; ++i) {
+            if (i < P && gph == 0xFFFFFFFFu) {
+                const uint32_t p = ((i < 4u ? o.x : o.y) >> (8u * (i & 3u))) & 0xFFu;
+                uint32_t gp = 0;
+#pragma unroll
+                for (uint32_t q = 0; q < kMaxPhases; ++q) gp = q == p ? g[q] : gp;
+                if (c >= start && c < start + gp) gph = p;
+                start += gp;
             }
-            start += g;
         }
     }
-    uint64_t Q[kMaxPhases];  // registers: indexed at compile-time indices only (unrolled, masked)
-#pragma unroll
-    for (uint32_t q = 0; q < kMaxPhases; ++q) Q[q] = 0;
+    uint32_t nonempty = 0;  // phases with vehicles on some approach
     unsigned long long k = 0;
-    for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const uint32_t n = veh[e], p = ephase[e];
-        uint32_t out = 0;
-        if (P) {
+    for (uint32_t i0 = ib; i0 < ie; i0 += 4) {
+        const uint32_t m = ie - i0 < 4u ? ie - i0 : 4u;
+        uint32_t n[4], ph[4], ln[4];
 #pragma unroll
-            for (uint32_t q = 0; q < kMaxPhases; ++q) Q[q] += (p & (kMaxPhases - 1)) == q ? n : 0u;
+        for (uint32_t j = 0; j < 4; ++j) {
+            const bool ok = j < m;
+            n[j] = ok ? t.veh[i0 + j] : 0u;
+            ph[j] = ok ? t.ephase[i0 + j] : 0u;
+            ln[j] = ok ? t.lanes[i0 + j] : 0u;
         }
-        if (P == 0 || p == gph) {
-            const uint64_t L = lanes[e];
-            const uint64_t cap = L * (t_now + dt) / h_sat - L * t_now / h_sat;
-            out = n < cap ? n : (uint32_t)cap;
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            if (j < m) {
+                nonempty |= (n[j] > 0u ? 1u : 0u) << (ph[j] & (kMaxPhases - 1));
+                uint32_t out = 0;
+                if (P == 0 || ph[j] == gph) {
+                    const uint32_t cap = tc.cap[ln[j]];
+                    out = n[j] < cap ? n[j] : cap;
+                }
+                leave[i0 + j] = out;
+                k += out;
+            }
         }
-        leave[e] = out;
-        k += out;
     }
     K[v] = k;
 #pragma unroll
     for (uint32_t p = 0; p < kMaxPhases; ++p) {
-        uint32_t& r = red[(size_t)v * kMaxPhases + p];
-        if (P == 0 || p >= P || p == gph || Q[p] == 0)
-            r = 0;
-        else
-            r = r > 0xFFFFFFFFu - dt ? 0xFFFFFFFFu : r + dt;
-    }
-}
-
-// Scatter pass (one thread per node, over its out-roads): a road keeps what it did not discharge and
-// gains its share of its tail node's discharge, K/d each and one more for the first K mod d roads in
-// CSR order. Vehicles that reach a node without out-roads leave the network.
-__global__ void k_tick_scatter(uint32_t N, const uint32_t* __restrict__ row_ptr,
-                               const unsigned long long* __restrict__ K, const uint32_t* __restrict__ leave,
-                               uint32_t* __restrict__ veh) {
-    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= N) return;
-    const uint32_t b = row_ptr[u], d = row_ptr[u + 1] - b;
-    if (d == 0) return;
-    const unsigned long long k = K[u];
-    const unsigned long long share = k / d;
-    const uint32_t extra = (uint32_t)(k - share * d);
-    for (uint32_t j = 0; j < d; ++j) {
-        const uint32_t e = b + j;
-        veh[e] = (uint32_t)(veh[e] - leave[e] + share + (j < extra ? 1u : 0u));
+        if (p < red_planes) {
+            const bool keep = P != 0 && p < P && p != gph && (nonempty >> p & 1u);
+            t.red[(size_t)p * N + v] = keep ? (rd[p] > 0xFFFFFFFFu - dt ? 0xFFFFFFFFu : rd[p] + dt) : 0u;
+        }
     }
 }
 
@@ -281,6 +272,8 @@ k_exact_h(uint32_t N, const DevQuery* __restrict__ q, const uint32_t* __restrict
 // and REP (GMP_FLAG_REPULSIVE: the pheromone word is a reciprocal) are template parameters so that the
 // default instantiation keeps its small register footprint: this kernel writes every road of every
 // colony and needs the occupancy.
+constexpr uint32_t kInitPer = 4;
+
 template <bool EXACT, bool REP>
 __global__ void __launch_bounds__(256, 8)
 k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
@@ -297,18 +290,34 @@ k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restr
     unsigned long long* D = dep + (size_t)qi * E;
     uint2* TH = th + (size_t)qi * E;
     const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        const uint32_t v = col[e];
-        const uint32_t h = EXACT ? hrow[v] : heuristic_ms(x[v], y[v], Q.xd, Q.yd, kappa);
-        if (zero_dep) D[e] = 0;
-        if (sparse) {  // no road has a deposit yet: every road holds the baseline
-            TH[e] = make_uint2(0u, h);
-            continue;
+    // kInitPer roads per thread, a grid stride apart: every head and coordinate load of the batch is
+    // issued before the heuristics are computed and the pairs written
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < E; e0 += stride * kInitPer) {
+        uint32_t hv[kInitPer];
+#pragma unroll
+        for (uint32_t j = 0; j < kInitPer; ++j) {
+            const uint32_t e = e0 + j * stride;
+            hv[j] = e < E ? col[e] : 0u;  // past the end: node 0, computed and not stored
         }
-        uint64_t t0 = 1ull << 32;
-        if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
-        T[e] = t0;
-        TH[e] = make_uint2(tau_word(t0, REP ? GMP_FLAG_REPULSIVE : 0u), h);
+#pragma unroll
+        for (uint32_t j = 0; j < kInitPer; ++j)
+            hv[j] = EXACT ? hrow[hv[j]] : heuristic_ms(x[hv[j]], y[hv[j]], Q.xd, Q.yd, kappa);
+#pragma unroll
+        for (uint32_t j = 0; j < kInitPer; ++j) {
+            const uint32_t e = e0 + j * stride;
+            if (e >= E) continue;
+            const uint32_t h = hv[j];
+            if (zero_dep) D[e] = 0;
+            if (sparse) {  // no road has a deposit yet: every road holds the baseline
+                TH[e] = make_uint2(0u, h);
+                continue;
+            }
+            uint64_t t0 = 1ull << 32;
+            if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
+            T[e] = t0;
+            TH[e] = make_uint2(tau_word(t0, REP ? GMP_FLAG_REPULSIVE : 0u), h);
+        }
     }
     if (sparse)
         for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
@@ -1011,9 +1020,8 @@ __global__ void __launch_bounds__(kIterEndBlock) k_iter_end(IterEndArgs a) {
     }
     b -= a.n_queries;
     const uint32_t v = b * blockDim.x + threadIdx.x;
-    if (v < a.n_nodes)  // intersections with more than two phases: a separate launch (queue_node)
-        queue_node_small(v, a.row_ptr, a.in_ptr, a.in_edge, a.nph, a.cycle, a.offset, a.green, a.ephase, a.veh, a.cap,
-                         a.red, a.order, a.rec);
+    if (v < a.n_nodes)  // intersections with more than two phases: a separate launch (k_queue_general)
+        queue_node_small<false, false>(v, a.qt);
 }
 
 __global__ void k_finalize(const DevQuery* __restrict__ q, const QueryState* __restrict__ qs,
@@ -1048,41 +1056,55 @@ __global__ void k_finalize(const DevQuery* __restrict__ q, const QueryState* __r
 // ------------------------------------------------------------------------------------------------
 static inline unsigned blocks_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
-cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* len, const uint16_t* speed,
-                               const uint8_t* lanes, uint32_t* ff, uint32_t* cap) {
+cudaError_t launch_edge_static(cudaStream_t s, uint32_t E, const uint32_t* in_edge, const uint32_t* len,
+                               const uint16_t* speed, const uint8_t* lanes_by_road, uint32_t* ff, uint32_t* cap,
+                               uint8_t* lanes) {
     if (E == 0) return cudaSuccess;
-    k_edge_static<<<blocks_for(E, 256), 256, 0, s>>>(E, len, speed, lanes, ff, cap);
+    k_edge_static<<<blocks_for(E, 256), 256, 0, s>>>(E, in_edge, len, speed, lanes_by_road, ff, cap, lanes);
     return cudaGetLastError();
 }
 
-cudaError_t launch_edge_dynamic(cudaStream_t s, uint32_t E, const uint32_t* row_ptr, const uint32_t* col,
-                                const uint32_t* ff, const uint32_t* cap, const uint8_t* lanes, const uint32_t* veh,
-                                const uint8_t* nph, uint32_t h_sat, uint32_t thr, EdgeRec* rec) {
-    if (E == 0) return cudaSuccess;
-    k_edge_dynamic<<<blocks_for(E, 256), 256, 0, s>>>(E, row_ptr, col, ff, cap, lanes, veh, nph, h_sat, thr, rec);
+cudaError_t launch_gather_u32(cudaStream_t s, uint32_t n, const uint32_t* idx, const uint32_t* src, uint32_t* dst) {
+    if (n == 0) return cudaSuccess;
+    k_gather<uint32_t><<<blocks_for(n, 256), 256, 0, s>>>(n, idx, src, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_queue_preempt(cudaStream_t s, uint32_t N, uint32_t min_phases, const uint32_t* row_ptr,
-                                 const uint32_t* in_ptr, const uint32_t* in_edge,
-                                 const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
-                                 const uint32_t* green, const uint8_t* ephase, const uint32_t* veh,
-                                 const uint32_t* cap, const uint32_t* red, uint8_t* order, EdgeRec* rec) {
-    if (N == 0) return cudaSuccess;
-    k_queue_preempt<<<blocks_for(N, 128), 128, 0, s>>>(N, min_phases, row_ptr, in_ptr, in_edge, nph, cycle, offset,
-                                                        green, ephase, veh, cap, red, order, rec);
+cudaError_t launch_gather_u8(cudaStream_t s, uint32_t n, const uint32_t* idx, const uint8_t* src, uint8_t* dst) {
+    if (n == 0) return cudaSuccess;
+    k_gather<uint8_t><<<blocks_for(n, 256), 256, 0, s>>>(n, idx, src, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tick(cudaStream_t s, uint32_t N, const uint32_t* row_ptr, const uint32_t* in_ptr,
-                        const uint32_t* in_edge, const uint8_t* nph, const uint32_t* cycle, const uint32_t* offset,
-                        const uint32_t* green, const uint8_t* ephase, const uint8_t* lanes, uint32_t* veh,
-                        const uint8_t* order, uint64_t t_now, uint32_t dt, uint32_t h_sat, uint32_t* leave,
-                        unsigned long long* K, uint32_t* red) {
-    if (N == 0) return cudaSuccess;
-    k_tick_node<<<blocks_for(N, 128), 128, 0, s>>>(N, in_ptr, in_edge, nph, cycle, offset, green, ephase, lanes, veh,
-                                                    order, t_now, dt, h_sat, leave, K, red);
-    k_tick_scatter<<<blocks_for(N, 128), 128, 0, s>>>(N, row_ptr, K, leave, veh);
+cudaError_t launch_queue_general(cudaStream_t s, const QueueTables& t, QueuePass pass) {
+    if (t.n_nodes == 0) return cudaSuccess;
+    const unsigned g = blocks_for(t.n_nodes, 128);
+    if (pass == QueuePass::kRefresh) k_queue_general<true, false><<<g, 128, 0, s>>>(t);
+    else if (pass == QueuePass::kTick) k_queue_general<true, true><<<g, 128, 0, s>>>(t);
+    else k_queue_general<false, false><<<g, 128, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_queue(cudaStream_t s, const QueueTables& t, uint32_t max_phases, QueuePass pass) {
+    if (t.n_nodes == 0) return cudaSuccess;
+    const unsigned g = blocks_for(t.n_nodes, 128);
+    if (pass == QueuePass::kRefresh) k_queue_small<true, false><<<g, 128, 0, s>>>(t);
+    else if (pass == QueuePass::kTick) k_queue_small<true, true><<<g, 128, 0, s>>>(t);
+    else k_queue_small<false, false><<<g, 128, 0, s>>>(t);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && max_phases > 2) err = launch_queue_general(s, t, pass);
+    return err;
+}
+
+cudaError_t launch_tick_node(cudaStream_t s, const QueueTables& t, uint64_t t_now, uint32_t dt,
+                             uint32_t red_planes, uint32_t* leave, unsigned long long* K) {
+    if (t.n_nodes == 0) return cudaSuccess;
+    TickCap tc;
+    for (uint32_t L = 0; L < 256; ++L) {
+        const uint64_t c = (uint64_t)L * (t_now + dt) / t.h_sat - (uint64_t)L * t_now / t.h_sat;
+        tc.cap[L] = c > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)c;
+    }
+    k_tick_node<<<blocks_for(t.n_nodes, 128), 128, 0, s>>>(t, t_now, dt, red_planes, tc, leave, K);
     return cudaGetLastError();
 }
 
@@ -1091,7 +1113,7 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
                               const uint32_t* hdist, uint32_t N, bool zero_dep) {
-    dim3 grid(blocks_for(E ? E : 1, 1024), Q);
+    dim3 grid(blocks_for(E ? E : 1, 256 * kInitPer), Q);
 #define GMP_INIT(EX_, REP_)                                                                                 \
     k_init_batch<EX_, REP_><<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, \
                                                  sparse, tflag, tflag_words, hdist, N, zero_dep ? 1u : 0u)

@@ -172,9 +172,7 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
                     }
                 } else {  // queue / preemption update of intersections [v0, v1) (densities fixed: same order)
                     const uint32_t v0 = (c - n_edge_chunks) * node_chunk, v1 = min(p.n_nodes, v0 + node_chunk);
-                    for (uint32_t v = v0 + lane; v < v1; v += G)
-                        queue_node(v, a.row_ptr, p.in_ptr, p.in_edge, p.nph, p.cycle, p.offset, p.green, p.ephase, p.veh,
-                                   p.cap, p.red, p.order, p.rec);
+                    for (uint32_t v = v0 + lane; v < v1; v += G) queue_node<false, false>(v, p.qt);
                 }
                 __threadfence();
                 __syncwarp(gmask);

@@ -10,49 +10,112 @@
 
 namespace gmp {
 
-// Preemptive phase order of intersection v (Calc_Dens / Comp_Thres; Fig. 3 signal block): queues and
-// storage per phase from the node's in-edges; order (1) phases whose queue exceeds 3/4 of their
-// storage, longest first; else (2) phases red for longer than a cycle, longest first; else (3) the
-// longest non-empty queue; then the remaining non-empty phases, then the empty ones, each in index
-// order. Every in-edge's record then gets its approach's green window under that order.
-__device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restrict__ row_ptr,
-                                           const uint32_t* __restrict__ in_ptr,
-                                           const uint32_t* __restrict__ in_edge, const uint8_t* __restrict__ nph,
-                                           const uint32_t* __restrict__ cycle, const uint32_t* __restrict__ offset,
-                                           const uint32_t* __restrict__ green, const uint8_t* __restrict__ ephase,
-                                           const uint32_t* __restrict__ veh, const uint32_t* __restrict__ cap,
-                                           const uint32_t* __restrict__ red, uint8_t* __restrict__ order,
-                                           EdgeRec* __restrict__ rec) {
-    const uint32_t P = nph[v], ib = in_ptr[v], ie = in_ptr[v + 1];
-    const uint32_t deg = min(row_ptr[v + 1] - row_ptr[v], 255u) << 24;  // out-degree of v (at most 128 runs)
+// ------------------------------------------------------------------------------------------------
+// Queue / preemption update of one intersection (Calc_Dens / Comp_Thres; Fig. 3 signal block).
+// Queues and storage per phase come from the intersection's approaches; the phase order is (1) phases
+// whose queue exceeds 3/4 of their storage, longest first; else (2) phases red for longer than a cycle,
+// longest first; else (3) the longest non-empty queue; then the remaining non-empty phases, then the
+// empty ones, each in index order. Every approach's record then gets its green window under that order.
+//
+// FULL passes (densities, red times or signals changed) rewrite each approach's whole 32-byte record,
+// so no record is left half written; TICK passes first apply the tick's discharge to the vehicles. The
+// other passes (the per-iteration update within a job, where densities and red times are fixed)
+// recompute the order and rewrite an intersection's order and green windows only where the order
+// differs from the stored one: the records are a function of the order and of the fixed tables.
+// ------------------------------------------------------------------------------------------------
+
+// Vehicles on the road of approach slot i. In a tick pass the road first loses what it discharged
+// (leave) and gains its share of its tail's discharge K: K / d each for the tail's d out-roads and one
+// more for the first K mod d of them in CSR order. The new count is stored (modulo 2^32, like the word).
+template <bool TICK>
+__device__ __forceinline__ uint32_t approach_vehicles(const QueueTables& t, uint32_t i) {
+    if (!TICK) return t.veh[i];
+    const uint32_t u = t.in_tail[i], e = t.in_edge[i];
+    const uint32_t rb = t.row_ptr[u], d = t.row_ptr[u + 1] - rb;  // d >= 1: road e leaves u
+    const unsigned long long k = t.K[u];
+    uint32_t share, extra;
+    if ((k >> 32) == 0) {
+        share = (uint32_t)k / d;
+        extra = (uint32_t)k - share * d;
+    } else {
+        const unsigned long long q = k / d;
+        share = (uint32_t)q;
+        extra = (uint32_t)(k - q * d);
+    }
+    const uint32_t n = t.veh[i] - t.leave[i] + share + (e - rb < extra ? 1u : 0u);
+    t.veh[i] = n;
+    return n;
+}
+
+// First half of a road's record (see EdgeRec) for a road into v carrying n vehicles, with jam capacity
+// c, free-flow time ff and `lanes` lanes: the head, its CSR row, the congested travel time, the queue
+// delay at a signalised head and the congestion flag.
+__device__ __forceinline__ uint4 road_front(const QueueTables& t, uint32_t v, uint32_t vbeg, bool signalised,
+                                            uint32_t n, uint32_t c, uint32_t ff, uint32_t lanes) {
+    uint32_t qd = 0;
+    if (signalised) {
+        const uint64_t d = mul_div_u32(n, t.h_sat, lanes);
+        qd = d > kTimeClamp ? kTimeClamp : (uint32_t)d;
+    }
+    const uint32_t fl = (t.thr != kThrOff && (uint64_t)n * 1000u > (uint64_t)t.thr * c) ? 1u : 0u;
+    return make_uint4(v, vbeg, edge_time_ms(ff, c, n), qd | (fl << 31));
+}
+
+// The same for approach slot i, from the slot tables.
+__device__ __forceinline__ uint4 record_front(const QueueTables& t, uint32_t i, uint32_t v, uint32_t vbeg,
+                                              bool signalised, uint32_t n) {
+    return road_front(t, v, vbeg, signalised, n, t.cap[i], t.ff[i], t.lanes[i]);
+}
+
+constexpr uint32_t kOrderId0 = 0x03020100u, kOrderId1 = 0x07060504u;  // identity order, 4 phases a word
+
+// An unsignalised intersection: identity order, no wait, and its out-degree in every approach's record.
+template <bool FULL, bool TICK>
+__device__ __forceinline__ void queue_unsignalised(const QueueTables& t, uint32_t v, uint32_t vb, uint32_t deg,
+                                                   uint32_t ib, uint32_t ie, uint2* ord) {
+    if (!FULL) {
+        const uint2 o = *ord;
+        if (o.x == kOrderId0 && o.y == kOrderId1) return;
+    }
+    *ord = make_uint2(kOrderId0, kOrderId1);
+    for (uint32_t i = ib; i < ie; ++i) {
+        uint4* r = reinterpret_cast<uint4*>(t.rec + t.in_edge[i]);
+        if (FULL) r[0] = record_front(t, i, v, vb, false, approach_vehicles<TICK>(t, i));
+        r[1] = make_uint4(deg, 0u, 0u, 0u);
+    }
+}
+
+// Any intersection (up to 8 phases). Phase-indexed values stay in registers: they are read and written
+// at compile-time indices only (loops over the 8 possible phases are unrolled and masked).
+template <bool FULL, bool TICK>
+__device__ __forceinline__ void queue_node(uint32_t v, const QueueTables& t) {
+    static_assert(FULL || !TICK, "a tick pass rewrites whole records");
+    const uint32_t N = t.n_nodes, P = t.nph[v], ib = t.in_ptr[v], ie = t.in_ptr[v + 1];
+    const uint32_t vb = t.row_ptr[v];
+    const uint32_t deg = min(t.row_ptr[v + 1] - vb, 255u) << 24;  // out-degree of v (at most 128 runs)
+    uint2* const ord = reinterpret_cast<uint2*>(t.order + (size_t)v * kMaxPhases);
     if (P == 0) {
-        for (uint32_t i = 0; i < kMaxPhases; ++i) order[(size_t)v * kMaxPhases + i] = (uint8_t)i;
-        for (uint32_t i = ib; i < ie; ++i)  // second half of the record (see EdgeRec)
-            reinterpret_cast<uint4*>(rec + in_edge[i])[1] = make_uint4(deg, 0u, 0u, 0u);
+        queue_unsignalised<FULL, TICK>(t, v, vb, deg, ib, ie, ord);
         return;
     }
-    // everything below stays in registers: phase-indexed values are only read and written at
-    // compile-time indices (loops over the 8 possible phases are unrolled and masked)
     uint64_t Q[kMaxPhases], S[kMaxPhases];
 #pragma unroll
     for (uint32_t k = 0; k < kMaxPhases; ++k) Q[k] = S[k] = 0;
     for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const uint32_t p = ephase[e] & (kMaxPhases - 1);
-        const uint32_t n = veh[e], c = cap[e];
+        const uint32_t n = approach_vehicles<TICK>(t, i);
+        const uint32_t p = t.ephase[i] & (kMaxPhases - 1), c = t.cap[i];
 #pragma unroll
         for (uint32_t k = 0; k < kMaxPhases; ++k) {
             Q[k] += p == k ? n : 0u;
             S[k] += p == k ? c : 0u;
         }
     }
-    const uint32_t cy = cycle[v];
+    const uint32_t cy = t.cycle[v];
     uint32_t over = 0, starved = 0, nonempty = 0;
-    uint32_t rd[kMaxPhases], gr[kMaxPhases];
+    uint32_t rd[kMaxPhases];
 #pragma unroll
     for (uint32_t k = 0; k < kMaxPhases; ++k) {
-        rd[k] = k < P ? red[(size_t)v * kMaxPhases + k] : 0u;
-        gr[k] = k < P ? green[(size_t)v * kMaxPhases + k] : 0u;
+        rd[k] = k < P ? t.red[(size_t)k * N + v] : 0u;
         if (k < P) {
             if (Q[k] > S[k] * 3u / 4u) over |= 1u << k;
             if (rd[k] > cy) starved |= 1u << k;
@@ -79,7 +142,8 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
         prio = 1u << best;
     }
     // sort key per phase: prioritised phases by value descending, then the other non-empty phases, then
-    // the empty ones, each in index order; the position of a phase in the plan is its rank by key
+    // the empty ones, each in index order; a phase's position in the plan is its rank by key, and the
+    // phases at or above P keep their own positions
     constexpr uint64_t kVmax = (1ull << 48) - 1;
     uint64_t key[kMaxPhases];
 #pragma unroll
@@ -88,106 +152,227 @@ __device__ __forceinline__ void queue_node(uint32_t v, const uint32_t* __restric
         const uint64_t grp = (prio >> k & 1u) ? 0u : ((nonempty >> k & 1u) ? 1u : 2u);
         key[k] = (grp << 60) | (grp == 0 ? (kVmax - (val < kVmax ? val : kVmax)) << 4 : 0u) | k;
     }
-    uint32_t start[kMaxPhases];
+    uint32_t before[kMaxPhases];  // per phase: the phases ahead of it in the plan
+    uint32_t lo = 0, hi = 0;      // the plan, one byte per position
 #pragma unroll
     for (uint32_t k = 0; k < kMaxPhases; ++k) {
-        uint32_t rank = 0, st = 0;
+        uint32_t rank = 0, bm = 0;
 #pragma unroll
         for (uint32_t q = 0; q < kMaxPhases; ++q)
             if (q < P && key[q] < key[k]) {
                 ++rank;
-                st += gr[q];
+                bm |= 1u << q;
             }
-        start[k] = st;
-        if (k < P) order[(size_t)v * kMaxPhases + rank] = (uint8_t)k;
-        else order[(size_t)v * kMaxPhases + k] = (uint8_t)k;
+        before[k] = bm;
+        const uint32_t pos = k < P ? rank : k;
+        if (pos < 4u) lo |= k << (8u * pos);
+        else hi |= k << (8u * (pos - 4u));
     }
-    const uint32_t off = offset[v];
+    if (!FULL) {
+        const uint2 o = *ord;
+        if (o.x == lo && o.y == hi) return;
+    }
+    *ord = make_uint2(lo, hi);
+    uint32_t gr[kMaxPhases], start[kMaxPhases];
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxPhases; ++k) gr[k] = k < P ? t.green[(size_t)k * N + v] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxPhases; ++k) {
+        uint32_t st = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < kMaxPhases; ++q) st += (before[k] >> q & 1u) ? gr[q] : 0u;
+        start[k] = st;
+    }
+    const uint32_t off = t.offset[v];
     const uint32_t magic = 0xFFFFFFFFu / cy;
     for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const uint32_t p = ephase[e] & (kMaxPhases - 1);
+        const uint32_t p = t.ephase[i] & (kMaxPhases - 1);
         uint32_t st = 0, gl = 0;
 #pragma unroll
         for (uint32_t k = 0; k < kMaxPhases; ++k) {
             st = p == k ? start[k] : st;
             gl = p == k ? gr[k] : gl;
         }
-        reinterpret_cast<uint4*>(rec + e)[1] = make_uint4(cy | deg, (off + st) % cy, gl, magic);
+        uint4* r = reinterpret_cast<uint4*>(t.rec + t.in_edge[i]);
+        if (FULL) r[0] = record_front(t, i, v, vb, true, t.veh[i]);
+        r[1] = make_uint4(cy | deg, (off + st) % cy, gl, magic);
     }
 }
 
-// queue_node for a node with at most two phases (unsignalised nodes, and every junction the generators
-// build), with the same results in far fewer registers: two keys decide the whole order. Returns false,
-// doing nothing, for a node with more phases (queue_node handles those). Phase p of a road into a
-// signalised node is below its phase count and the greens add up to the cycle (both checked when the
-// signals are set), so only phases 0 and 1 occur here.
-__device__ __forceinline__ bool queue_node_small(uint32_t v, const uint32_t* __restrict__ row_ptr,
-                                                 const uint32_t* __restrict__ in_ptr,
-                                                 const uint32_t* __restrict__ in_edge, const uint8_t* __restrict__ nph,
-                                                 const uint32_t* __restrict__ cycle,
-                                                 const uint32_t* __restrict__ offset,
-                                                 const uint32_t* __restrict__ green,
-                                                 const uint8_t* __restrict__ ephase,
-                                                 const uint32_t* __restrict__ veh, const uint32_t* __restrict__ cap,
-                                                 const uint32_t* __restrict__ red, uint8_t* __restrict__ order,
-                                                 EdgeRec* __restrict__ rec) {
-    const uint32_t P = nph[v];
+// Up to four approach slots of one intersection, in registers.
+struct ApproachBatch {
+    uint32_t n[4], cap[4], ph[4];  // vehicles, jam capacity, approach phase
+    uint32_t e[4], ff[4], ln[4];   // road id, free-flow time, lanes (whole-record passes only)
+};
+
+// Load slots [i0, i0 + cnt), cnt <= 4, issuing every load of the batch before any is used. In a tick pass
+// the discharge is then applied and the new vehicle counts are stored (as approach_vehicles does).
+template <bool FULL, bool TICK>
+__device__ __forceinline__ void load_batch(const QueueTables& t, uint32_t i0, uint32_t cnt, ApproachBatch& b) {
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        const bool ok = j < cnt;
+        const uint32_t i = i0 + j;
+        b.n[j] = ok ? t.veh[i] : 0u;
+        b.cap[j] = ok ? t.cap[i] : 0u;
+        b.ph[j] = ok ? t.ephase[i] : 0u;
+        b.e[j] = (FULL && ok) ? t.in_edge[i] : 0u;
+        b.ff[j] = (FULL && ok) ? t.ff[i] : 0u;
+        b.ln[j] = (FULL && ok) ? t.lanes[i] : 1u;
+    }
+    if (TICK) {
+        uint32_t u[4], lv[4], rb[4], re[4];
+        unsigned long long k[4];
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            const bool ok = j < cnt;
+            u[j] = ok ? t.in_tail[i0 + j] : 0u;
+            lv[j] = ok ? t.leave[i0 + j] : 0u;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            const bool ok = j < cnt;
+            rb[j] = ok ? t.row_ptr[u[j]] : 0u;
+            re[j] = ok ? t.row_ptr[u[j] + 1] : 1u;
+            k[j] = ok ? t.K[u[j]] : 0ull;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            if (j < cnt) {
+                const uint32_t d = re[j] - rb[j];  // >= 1: the slot's road leaves u
+                uint32_t share, extra;
+                if ((k[j] >> 32) == 0) {
+                    share = (uint32_t)k[j] / d;
+                    extra = (uint32_t)k[j] - share * d;
+                } else {
+                    const unsigned long long q = k[j] / d;
+                    share = (uint32_t)q;
+                    extra = (uint32_t)(k[j] - q * d);
+                }
+                b.n[j] = b.n[j] - lv[j] + share + (b.e[j] - rb[j] < extra ? 1u : 0u);
+                t.veh[i0 + j] = b.n[j];
+            }
+        }
+    }
+}
+
+// Queues and storage of phases 0 and 1 from a batch.
+__device__ __forceinline__ void add_batch(const ApproachBatch& b, uint32_t cnt, uint64_t& Q0, uint64_t& Q1, uint64_t& S0,
+                                          uint64_t& S1) {
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        if (j < cnt) {
+            const bool p1 = (b.ph[j] & (kMaxPhases - 1)) != 0u;
+            Q0 += p1 ? 0u : b.n[j];
+            S0 += p1 ? 0u : b.cap[j];
+            Q1 += p1 ? b.n[j] : 0u;
+            S1 += p1 ? b.cap[j] : 0u;
+        }
+    }
+}
+
+// Write the records of a batch: the whole record in FULL passes, the green window (back half) otherwise;
+// back0 / back1 are the back halves of phase 0 and phase 1 approaches.
+template <bool FULL>
+__device__ __forceinline__ void write_batch(const QueueTables& t, uint32_t i0, uint32_t cnt, const ApproachBatch& b,
+                                            uint32_t v, uint32_t vb, bool signalised, uint4 back0, uint4 back1) {
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        if (j < cnt) {
+            const uint32_t e = FULL ? b.e[j] : t.in_edge[i0 + j];
+            uint4* r = reinterpret_cast<uint4*>(t.rec + e);
+            if (FULL) r[0] = road_front(t, v, vb, signalised, b.n[j], b.cap[j], b.ff[j], b.ln[j]);
+            r[1] = (b.ph[j] & (kMaxPhases - 1)) != 0u ? back1 : back0;
+        }
+    }
+}
+
+// queue_node for an intersection with at most two phases (unsignalised nodes, and every junction the
+// generators build), with the same results in far fewer registers: two keys decide the whole order.
+// Returns false, doing nothing, for an intersection with more phases (queue_node handles those). The
+// phase of a road into a signalised node is below its phase count and the greens add up to the cycle
+// (both checked when the signals are set), so only phases 0 and 1 occur here. The intersection's own
+// words (its phase planes exist for every node) and its first four approaches are loaded up front, so
+// the pass costs about two memory round trips per intersection.
+template <bool FULL, bool TICK>
+__device__ __forceinline__ bool queue_node_small(uint32_t v, const QueueTables& t) {
+    static_assert(FULL || !TICK, "a tick pass rewrites whole records");
+    const uint32_t N = t.n_nodes;
+    uint2* const ord = reinterpret_cast<uint2*>(t.order + (size_t)v * kMaxPhases);
+    const uint32_t P = t.nph[v], ib = t.in_ptr[v], ie = t.in_ptr[v + 1];
+    const uint32_t cy = t.cycle[v];
+    const uint32_t rd0 = t.red[v], rd1 = t.red[(size_t)N + v];
+    const uint2 old = FULL ? make_uint2(0u, 0u) : *ord;
+    uint32_t vb = 0, ve = 0, g0 = 0, g1 = 0, off = 0;
+    if (FULL) {
+        vb = t.row_ptr[v];
+        ve = t.row_ptr[v + 1];
+        g0 = t.green[v];
+        g1 = t.green[(size_t)N + v];
+        off = t.offset[v];
+    }
     if (P > 2) return false;
-    const uint32_t ib = in_ptr[v], ie = in_ptr[v + 1];
-    const uint32_t deg = min(row_ptr[v + 1] - row_ptr[v], 255u) << 24;  // out-degree of v (at most 128 runs)
-    uint2* const ord = reinterpret_cast<uint2*>(order + (size_t)v * kMaxPhases);
-    if (P == 0) {
-        *ord = make_uint2(0x03020100u, 0x07060504u);  // identity order
-        for (uint32_t i = ib; i < ie; ++i)  // second half of the record (see EdgeRec)
-            reinterpret_cast<uint4*>(rec + in_edge[i])[1] = make_uint4(deg, 0u, 0u, 0u);
-        return true;
-    }
+    const uint32_t cnt = ie - ib, c0 = cnt < 4u ? cnt : 4u;
+    ApproachBatch a;
+    load_batch<FULL, TICK>(t, ib, c0, a);
     uint64_t Q0 = 0, Q1 = 0, S0 = 0, S1 = 0;
-    for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const bool p1 = (ephase[e] & (kMaxPhases - 1)) != 0u;
-        const uint32_t n = veh[e], c = cap[e];
-        Q0 += p1 ? 0u : n;
-        S0 += p1 ? 0u : c;
-        Q1 += p1 ? n : 0u;
-        S1 += p1 ? c : 0u;
+    add_batch(a, c0, Q0, Q1, S0, S1);
+    for (uint32_t i0 = ib + 4; i0 < ie; i0 += 4) {  // intersections with more than four approaches
+        ApproachBatch b;
+        const uint32_t m = ie - i0 < 4u ? ie - i0 : 4u;
+        load_batch<FULL, TICK>(t, i0, m, b);
+        add_batch(b, m, Q0, Q1, S0, S1);
     }
-    const uint32_t cy = cycle[v];
-    const uint32_t rd0 = red[(size_t)v * kMaxPhases], g0 = green[(size_t)v * kMaxPhases];
-    const uint32_t rd1 = P > 1 ? red[(size_t)v * kMaxPhases + 1] : 0u;
-    const uint32_t g1 = P > 1 ? green[(size_t)v * kMaxPhases + 1] : 0u;
-    const uint32_t valid = P > 1 ? 3u : 1u;
-    const uint32_t over = ((Q0 > S0 * 3u / 4u ? 1u : 0u) | (Q1 > S1 * 3u / 4u ? 2u : 0u)) & valid;
-    const uint32_t starved = ((rd0 > cy ? 1u : 0u) | (rd1 > cy ? 2u : 0u)) & valid;
-    const uint32_t nonempty = ((Q0 > 0 ? 1u : 0u) | (Q1 > 0 ? 2u : 0u)) & valid;
-    uint32_t prio = 0;
-    bool by_q = true;
-    if (over) {
-        prio = over;
-    } else if (starved) {
-        prio = starved;
-        by_q = false;
-    } else if (nonempty) {  // the longest non-empty queue, phase 0 on ties
-        prio = ((nonempty & 1u) && (!(nonempty & 2u) || Q0 >= Q1)) ? 1u : 2u;
+    uint32_t lo = kOrderId0;  // unsignalised: identity order
+    bool first0 = true;
+    if (P > 0) {
+        const uint32_t valid = P > 1 ? 3u : 1u;
+        const uint32_t over = ((Q0 > S0 * 3u / 4u ? 1u : 0u) | (Q1 > S1 * 3u / 4u ? 2u : 0u)) & valid;
+        const uint32_t starved = ((rd0 > cy ? 1u : 0u) | (rd1 > cy ? 2u : 0u)) & valid;
+        const uint32_t nonempty = ((Q0 > 0 ? 1u : 0u) | (Q1 > 0 ? 2u : 0u)) & valid;
+        uint32_t prio = 0;
+        bool by_q = true;
+        if (over) {
+            prio = over;
+        } else if (starved) {
+            prio = starved;
+            by_q = false;
+        } else if (nonempty) {  // the longest non-empty queue, phase 0 on ties
+            prio = ((nonempty & 1u) && (!(nonempty & 2u) || Q0 >= Q1)) ? 1u : 2u;
+        }
+        // the sort keys of queue_node; phase 0 goes first when its key is the smaller one
+        constexpr uint64_t kVmax = (1ull << 48) - 1;
+        const uint64_t v0 = by_q ? Q0 : (uint64_t)rd0, v1 = by_q ? Q1 : (uint64_t)rd1;
+        const uint64_t grp0 = (prio & 1u) ? 0u : ((nonempty & 1u) ? 1u : 2u);
+        const uint64_t grp1 = (prio & 2u) ? 0u : ((nonempty & 2u) ? 1u : 2u);
+        const uint64_t key0 = (grp0 << 60) | (grp0 == 0 ? (kVmax - (v0 < kVmax ? v0 : kVmax)) << 4 : 0u);
+        const uint64_t key1 = (grp1 << 60) | (grp1 == 0 ? (kVmax - (v1 < kVmax ? v1 : kVmax)) << 4 : 0u) | 1u;
+        first0 = P == 1 || key0 < key1;
+        lo = first0 ? kOrderId0 : 0x03020001u;
     }
-    // the sort keys of queue_node; phase 0 goes first when its key is the smaller one
-    constexpr uint64_t kVmax = (1ull << 48) - 1;
-    const uint64_t v0 = by_q ? Q0 : (uint64_t)rd0, v1 = by_q ? Q1 : (uint64_t)rd1;
-    const uint64_t grp0 = (prio & 1u) ? 0u : ((nonempty & 1u) ? 1u : 2u);
-    const uint64_t grp1 = (prio & 2u) ? 0u : ((nonempty & 2u) ? 1u : 2u);
-    const uint64_t key0 = (grp0 << 60) | (grp0 == 0 ? (kVmax - (v0 < kVmax ? v0 : kVmax)) << 4 : 0u);
-    const uint64_t key1 = (grp1 << 60) | (grp1 == 0 ? (kVmax - (v1 < kVmax ? v1 : kVmax)) << 4 : 0u) | 1u;
-    const bool first0 = P == 1 || key0 < key1;
-    *ord = make_uint2(first0 ? 0x03020100u : 0x03020001u, 0x07060504u);
-    const uint32_t st0 = first0 ? 0u : g1, st1 = first0 ? g0 : 0u;  // green-window starts in plan order
-    const uint32_t off = offset[v];
-    const uint32_t magic = 0xFFFFFFFFu / cy;
-    for (uint32_t i = ib; i < ie; ++i) {
-        const uint32_t e = in_edge[i];
-        const bool p1 = (ephase[e] & (kMaxPhases - 1)) != 0u;
-        reinterpret_cast<uint4*>(rec + e)[1] =
-            make_uint4(cy | deg, (off + (p1 ? st1 : st0)) % cy, p1 ? g1 : g0, magic);
+    if (!FULL) {
+        if (old.x == lo && old.y == kOrderId1) return true;
+        vb = t.row_ptr[v];  // the order changed: what the green windows need
+        ve = t.row_ptr[v + 1];
+        g0 = t.green[v];
+        g1 = t.green[(size_t)N + v];
+        off = t.offset[v];
+    }
+    *ord = make_uint2(lo, kOrderId1);
+    const uint32_t deg = min(ve - vb, 255u) << 24;  // out-degree of v (at most 128 runs)
+    uint4 back0 = make_uint4(deg, 0u, 0u, 0u), back1 = back0;
+    if (P > 0) {
+        const uint32_t st0 = first0 ? 0u : g1, st1 = first0 ? g0 : 0u;  // green-window starts in plan order
+        const uint32_t magic = 0xFFFFFFFFu / cy;
+        back0 = make_uint4(cy | deg, (off + st0) % cy, g0, magic);
+        back1 = make_uint4(cy | deg, (off + st1) % cy, g1, magic);
+    }
+    write_batch<FULL>(t, ib, c0, a, v, vb, P > 0, back0, back1);
+    for (uint32_t i0 = ib + 4; i0 < ie; i0 += 4) {
+        ApproachBatch b;
+        const uint32_t m = ie - i0 < 4u ? ie - i0 : 4u;
+        load_batch<FULL, false>(t, i0, m, b);  // vehicles as the first round left them
+        write_batch<FULL>(t, i0, m, b, v, vb, P > 0, back0, back1);
     }
     return true;
 }
