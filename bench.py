@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--impl", default="gmacop", choices=["gmacop", "reference"])
     p.add_argument("--mode", type=int, default=0, help="0 auto, 1 iterative, 2 persistent")
     p.add_argument("--lanes", type=int, default=0, help="lanes per ant (0 = autotune)")
+    p.add_argument("--free-running", action="store_true",
+                   help="with --lanes/--mode: sub-warp ants without warp lockstep (the tuner's pick for grid64)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-colony-per-launch comparison")
@@ -280,6 +282,8 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------------ legs
 SERVE_SLOTS, SERVE_RATE, SERVE_WINDOW_S, SERVE_WARMUP_S, SERVE_MAX_BATCH = 16, 2000.0, 2.0, 0.5, 64
 SERVE_1M_SLOTS = 8
+SERVE_1M_SAT_S = 6.0  # window of the saturated 1M-node run: a job there takes a few hundred ms, so a short
+                      # window counts too few completions to be steady
 SERVE_ANTS, SERVE_ITERS = 128, 30
 
 
@@ -414,7 +418,7 @@ def serving_leg_1m(with_cpu):
                                     max_iter=SERVE_ITERS)
     try:
         make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
-        sat = serving.run_poisson(srv, make, rate_per_s=20000.0, duration_s=SERVE_WINDOW_S, warmup_s=1.0,
+        sat = serving.run_poisson(srv, make, rate_per_s=20000.0, duration_s=SERVE_1M_SAT_S, warmup_s=1.0,
                                   tick_ms=1000, drain_s=0.0).summary()
     finally:
         srv.close()
@@ -487,7 +491,8 @@ def run_gpu(args, rank, world, local_rank):
     if args.lanes == 0 and args.mode == 0:
         tune = ctx.autotune(wl.queries, probe_iter=32)
     else:
-        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes)
+        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes,
+                       flags=gmacop.FLAG_NO_LOCKSTEP if args.free_running else 0)
     sched = {k: v for k, v in ctx.get_params().items()
              if k in ("mode", "lanes_per_ant", "queue_chunk", "branches", "tau_layout", "flags")}
 

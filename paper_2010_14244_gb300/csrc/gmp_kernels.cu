@@ -272,58 +272,50 @@ k_exact_h(uint32_t N, const DevQuery* __restrict__ q, const uint32_t* __restrict
 // and REP (GMP_FLAG_REPULSIVE: the pheromone word is a reciprocal) are template parameters so that the
 // default instantiation keeps its small register footprint: this kernel writes every road of every
 // colony and needs the occupancy.
-constexpr uint32_t kInitPer = 4;
+constexpr uint32_t kInitCols = 8;  // colonies per thread: a road's head and coordinates are read once for them
 
+// One thread per road and group of kInitCols colonies (blockIdx.y): the head and its coordinates are
+// loaded once, then each colony's bound and pair are computed and written (each colony's pairs are
+// contiguous, so a warp's writes for one colony are one run).
 template <bool EXACT, bool REP>
-__global__ void __launch_bounds__(256, 8)
-k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
+__global__ void __launch_bounds__(256, EXACT ? 6 : 8)
+k_init_batch(uint32_t Qn, uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restrict__ col,
              const int32_t* __restrict__ x, const int32_t* __restrict__ y, uint32_t kappa,
              uint32_t flags, uint64_t* __restrict__ tau, uint2* __restrict__ th,
              unsigned long long* __restrict__ dep, QueryState* __restrict__ qs,
              uint32_t* __restrict__ tickets, uint32_t n_tickets, uint32_t sparse,
              uint32_t* __restrict__ tflag, uint32_t tflag_words,
              const uint32_t* __restrict__ hdist, uint32_t N, uint32_t zero_dep) {
-    const uint32_t qi = blockIdx.y;
-    const uint32_t* hrow = EXACT ? hdist + (size_t)qi * N : nullptr;
-    const DevQuery Q = q[qi];
-    uint64_t* T = tau + (size_t)qi * E;
-    unsigned long long* D = dep + (size_t)qi * E;
-    uint2* TH = th + (size_t)qi * E;
-    const uint32_t s0 = (uint32_t)Q.seed, s1 = (uint32_t)(Q.seed >> 32);
-    // kInitPer roads per thread, a grid stride apart: every head and coordinate load of the batch is
-    // issued before the heuristics are computed and the pairs written
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < E; e0 += stride * kInitPer) {
-        uint32_t hv[kInitPer];
-#pragma unroll
-        for (uint32_t j = 0; j < kInitPer; ++j) {
-            const uint32_t e = e0 + j * stride;
-            hv[j] = e < E ? col[e] : 0u;  // past the end: node 0, computed and not stored
-        }
-#pragma unroll
-        for (uint32_t j = 0; j < kInitPer; ++j)
-            hv[j] = EXACT ? hrow[hv[j]] : heuristic_ms(x[hv[j]], y[hv[j]], Q.xd, Q.yd, kappa);
-#pragma unroll
-        for (uint32_t j = 0; j < kInitPer; ++j) {
-            const uint32_t e = e0 + j * stride;
-            if (e >= E) continue;
-            const uint32_t h = hv[j];
-            if (zero_dep) D[e] = 0;
+    const uint32_t q0 = blockIdx.y * kInitCols, q1 = min(Qn, q0 + kInitCols);
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < E) {
+        const uint32_t v = col[e];
+        const int32_t xv = EXACT ? 0 : x[v], yv = EXACT ? 0 : y[v];
+        for (uint32_t qi = q0; qi < q1; ++qi) {
+            const uint32_t h = EXACT ? hdist[(size_t)qi * N + v] : heuristic_ms(xv, yv, q[qi].xd, q[qi].yd, kappa);
+            const size_t o = (size_t)qi * E + e;
+            if (zero_dep) dep[o] = 0;
             if (sparse) {  // no road has a deposit yet: every road holds the baseline
-                TH[e] = make_uint2(0u, h);
+                th[o] = make_uint2(0u, h);
                 continue;
             }
             uint64_t t0 = 1ull << 32;
-            if (flags & GMP_FLAG_RANDOM_TAU) t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), s0, s1).x;
-            T[e] = t0;
-            TH[e] = make_uint2(tau_word(t0, REP ? GMP_FLAG_REPULSIVE : 0u), h);
+            if (flags & GMP_FLAG_RANDOM_TAU) {
+                const uint64_t seed = q[qi].seed;
+                t0 = (1ull << 31) + philox4x32_10(make_uint4(e, 0u, 0u, 1u), (uint32_t)seed, (uint32_t)(seed >> 32)).x;
+            }
+            tau[o] = t0;
+            th[o] = make_uint2(tau_word(t0, REP ? GMP_FLAG_REPULSIVE : 0u), h);
         }
     }
     if (sparse)
-        for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
-            tflag[(size_t)qi * tflag_words + w] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t h = EXACT ? hrow[Q.src] : heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
+        for (uint32_t qi = q0; qi < q1; ++qi)
+            for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < tflag_words; w += gridDim.x * blockDim.x)
+                tflag[(size_t)qi * tflag_words + w] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < q1 - q0) {
+        const uint32_t qi = q0 + threadIdx.x;
+        const DevQuery Q = q[qi];
+        const uint32_t h = EXACT ? hdist[(size_t)qi * N + Q.src] : heuristic_ms(x[Q.src], y[Q.src], Q.xd, Q.yd, kappa);
         QueryState S;
         S.best_key = Q.active ? kNoKey : 0ull;
         S.dep_num = (flags & GMP_FLAG_UNIT_DEPOSIT) ? 0ull : (unsigned long long)(h > 0 ? h : 1u) << 32;
@@ -338,7 +330,7 @@ k_init_batch(uint32_t E, const DevQuery* __restrict__ q, const uint32_t* __restr
         S.n_touched = 0;
         qs[qi] = S;
     }
-    if (qi == 0 && blockIdx.x == 0)
+    if (blockIdx.y == 0 && blockIdx.x == 0)
         for (uint32_t i = threadIdx.x; i < n_tickets; i += blockDim.x) tickets[i] = 0;
 }
 
@@ -1113,9 +1105,10 @@ cudaError_t launch_init_batch(cudaStream_t s, uint32_t Q, uint32_t E, const DevQ
                               uint2* th, unsigned long long* dep, QueryState* qs, uint32_t* tickets,
                               uint32_t n_tickets, uint32_t sparse, uint32_t* tflag, uint32_t tflag_words,
                               const uint32_t* hdist, uint32_t N, bool zero_dep) {
-    dim3 grid(blocks_for(E ? E : 1, 256 * kInitPer), Q);
+    if (Q == 0) return cudaSuccess;
+    dim3 grid(blocks_for(E ? E : 1, 256), (Q + kInitCols - 1) / kInitCols);
 #define GMP_INIT(EX_, REP_)                                                                                 \
-    k_init_batch<EX_, REP_><<<grid, 256, 0, s>>>(E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, \
+    k_init_batch<EX_, REP_><<<grid, 256, 0, s>>>(Q, E, q, col, x, y, kappa, flags, tau, th, dep, qs, tickets, n_tickets, \
                                                  sparse, tflag, tflag_words, hdist, N, zero_dep ? 1u : 0u)
     const bool rep = (flags & GMP_FLAG_REPULSIVE) != 0;
     if (hdist) {
