@@ -28,9 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6772.9
-# DRAM bytes per construction launch from the ncu capture summarised in
-# profiles/construct_grid64.md (None until a capture of the current kernel exists).
-CONSTRUCT_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one construction launch of this workload's kernel and schedule, from an ncu
+# capture of the current kernel (one chain's launch of 1024 walks, alone and with cold caches): the graph
+# and the pheromone tables stay in L2, so DRAM carries the cold start only. Set to None when the kernel
+# changes, until it is captured again.
+CONSTRUCT_TRAFFIC_BYTES = 774_400
 
 
 def parse():
@@ -408,7 +410,7 @@ def city_batch_leg(with_cpu):
 def serving_leg_1m(with_cpu):
     """Route requests on a 1M-node planar road graph with 5M vehicles: uniform origin-destination pairs,
     128 ants x 30 iterations each, 1 s traffic ticks, 8 slots sharing the graph. First Poisson arrivals at
-    20k req/s, far above what the GPU completes (each request is about 8 M ant-steps): the figure is the
+    20k req/s, far above what the GPU completes (each request is about 7 M ant-steps): the figure is the
     saturated throughput, requests finished per second inside the window whenever they arrived. Then
     arrivals at 70 % of that throughput, where the latency percentiles describe the service itself."""
     from paper_2010_14244_gb300 import serving, workloads
@@ -676,6 +678,8 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "construct (all colony chains)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": CONSTRUCT_TRAFFIC_BYTES,
+                     "traffic_scope": "DRAM bytes of one construction launch (ncu, one chain alone, cold caches)",
+                     "algorithmic_bytes_per_launch": bytes_per_step * steps_per_job / max(construct_launches, 1),
                      "algorithmic_bytes_per_job": bytes_per_step * steps_per_job,
                      "bytes_per_ant_step": bytes_per_step,
                      "time": "job device time (construction launches of concurrent chains overlap)",
