@@ -70,6 +70,33 @@ def test_edge_times_and_phase_order(gm, ctx, orc):
         np.testing.assert_array_equal(ctx.phase_order(), prep["order"])
 
 
+def test_densities_from_device_memory_and_red_time_round_trip(gm, ctx, orc):
+    """Densities written from a device array (gathered into the library's slot order by a kernel) give the
+    same road times, queue delays, phase orders and read-back vehicles as the oracle on those vehicles;
+    red times written with non-zero entries in every phase slot (also those above a node's phase count,
+    which the library keeps in planes the tick does not visit) read back unchanged."""
+    torch = pytest.importorskip("torch")
+    wl = W.grid64(n_queries=1)
+    ctx.load_workload(wl)
+    rng = np.random.default_rng(17)
+    veh = rng.integers(0, 40, wl.net.n_edges).astype(np.uint32)
+    dev = torch.from_numpy(veh.astype(np.int32)).to("cuda:0")
+    torch.cuda.synchronize()
+    ctx.set_densities_device(dev.data_ptr())
+    tt, qd = ctx.edge_times()  # synchronises the context's stream
+    del dev
+    onet = orc.Net(wl.net, wl.signals, veh)
+    prep = orc.prepare(onet, orc.Params(), 0)
+    np.testing.assert_array_equal(tt, prep["tt"])
+    np.testing.assert_array_equal(qd, prep["qd"])
+    np.testing.assert_array_equal(ctx.phase_order(), prep["order"])
+    np.testing.assert_array_equal(ctx.densities(), veh)
+    red = rng.integers(0, 300_000, size=(wl.net.n_nodes, 8)).astype(np.uint32)
+    ctx.set_red_times(red)
+    np.testing.assert_array_equal(ctx.red_times(), red)
+    np.testing.assert_array_equal(ctx.phase_order(), orc.queue_preempt(orc.Net(wl.net, wl.signals, veh, red)))
+
+
 def test_phase_order_with_red_times_and_queues(gm, ctx, orc):
     rng = np.random.default_rng(5)
     net, sig = W.random_small(60, 120, rng, signalised_frac=0.7)
