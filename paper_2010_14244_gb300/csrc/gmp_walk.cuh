@@ -287,6 +287,35 @@ __device__ __forceinline__ void write_batch(const QueueTables& t, uint32_t i0, u
     }
 }
 
+// The plan of an intersection with at most two phases, as the first word of its order (the second word
+// is always the identity): the rule of queue_node reduced to two sort keys, from the queues and storages
+// of phases 0 and 1 and their red times. Phase 0 goes first when its key is the smaller one.
+__device__ __forceinline__ uint32_t small_plan(uint32_t P, uint64_t Q0, uint64_t Q1, uint64_t S0, uint64_t S1,
+                                               uint32_t rd0, uint32_t rd1, uint32_t cy) {
+    if (P == 0) return kOrderId0;  // unsignalised: identity order
+    const uint32_t valid = P > 1 ? 3u : 1u;
+    const uint32_t over = ((Q0 > S0 * 3u / 4u ? 1u : 0u) | (Q1 > S1 * 3u / 4u ? 2u : 0u)) & valid;
+    const uint32_t starved = ((rd0 > cy ? 1u : 0u) | (rd1 > cy ? 2u : 0u)) & valid;
+    const uint32_t nonempty = ((Q0 > 0 ? 1u : 0u) | (Q1 > 0 ? 2u : 0u)) & valid;
+    uint32_t prio = 0;
+    bool by_q = true;
+    if (over) {
+        prio = over;
+    } else if (starved) {
+        prio = starved;
+        by_q = false;
+    } else if (nonempty) {  // the longest non-empty queue, phase 0 on ties
+        prio = ((nonempty & 1u) && (!(nonempty & 2u) || Q0 >= Q1)) ? 1u : 2u;
+    }
+    constexpr uint64_t kVmax = (1ull << 48) - 1;
+    const uint64_t v0 = by_q ? Q0 : (uint64_t)rd0, v1 = by_q ? Q1 : (uint64_t)rd1;
+    const uint64_t grp0 = (prio & 1u) ? 0u : ((nonempty & 1u) ? 1u : 2u);
+    const uint64_t grp1 = (prio & 2u) ? 0u : ((nonempty & 2u) ? 1u : 2u);
+    const uint64_t key0 = (grp0 << 60) | (grp0 == 0 ? (kVmax - (v0 < kVmax ? v0 : kVmax)) << 4 : 0u);
+    const uint64_t key1 = (grp1 << 60) | (grp1 == 0 ? (kVmax - (v1 < kVmax ? v1 : kVmax)) << 4 : 0u) | 1u;
+    return (P == 1 || key0 < key1) ? kOrderId0 : 0x03020001u;
+}
+
 // queue_node for an intersection with at most two phases (unsignalised nodes, and every junction the
 // generators build), with the same results in far fewer registers: two keys decide the whole order.
 // Returns false, doing nothing, for an intersection with more phases (queue_node handles those). The
@@ -323,33 +352,8 @@ __device__ __forceinline__ bool queue_node_small(uint32_t v, const QueueTables& 
         load_batch<FULL, TICK>(t, i0, m, b);
         add_batch(b, m, Q0, Q1, S0, S1);
     }
-    uint32_t lo = kOrderId0;  // unsignalised: identity order
-    bool first0 = true;
-    if (P > 0) {
-        const uint32_t valid = P > 1 ? 3u : 1u;
-        const uint32_t over = ((Q0 > S0 * 3u / 4u ? 1u : 0u) | (Q1 > S1 * 3u / 4u ? 2u : 0u)) & valid;
-        const uint32_t starved = ((rd0 > cy ? 1u : 0u) | (rd1 > cy ? 2u : 0u)) & valid;
-        const uint32_t nonempty = ((Q0 > 0 ? 1u : 0u) | (Q1 > 0 ? 2u : 0u)) & valid;
-        uint32_t prio = 0;
-        bool by_q = true;
-        if (over) {
-            prio = over;
-        } else if (starved) {
-            prio = starved;
-            by_q = false;
-        } else if (nonempty) {  // the longest non-empty queue, phase 0 on ties
-            prio = ((nonempty & 1u) && (!(nonempty & 2u) || Q0 >= Q1)) ? 1u : 2u;
-        }
-        // the sort keys of queue_node; phase 0 goes first when its key is the smaller one
-        constexpr uint64_t kVmax = (1ull << 48) - 1;
-        const uint64_t v0 = by_q ? Q0 : (uint64_t)rd0, v1 = by_q ? Q1 : (uint64_t)rd1;
-        const uint64_t grp0 = (prio & 1u) ? 0u : ((nonempty & 1u) ? 1u : 2u);
-        const uint64_t grp1 = (prio & 2u) ? 0u : ((nonempty & 2u) ? 1u : 2u);
-        const uint64_t key0 = (grp0 << 60) | (grp0 == 0 ? (kVmax - (v0 < kVmax ? v0 : kVmax)) << 4 : 0u);
-        const uint64_t key1 = (grp1 << 60) | (grp1 == 0 ? (kVmax - (v1 < kVmax ? v1 : kVmax)) << 4 : 0u) | 1u;
-        first0 = P == 1 || key0 < key1;
-        lo = first0 ? kOrderId0 : 0x03020001u;
-    }
+    const uint32_t lo = small_plan(P, Q0, Q1, S0, S1, rd0, rd1, cy);
+    const bool first0 = lo == kOrderId0;
     if (!FULL) {
         if (old.x == lo && old.y == kOrderId1) return true;
         vb = t.row_ptr[v];  // the order changed: what the green windows need
