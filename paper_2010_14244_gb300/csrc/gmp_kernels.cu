@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             c_w = __shfl_sync(FULL, c_w, pick_lane, G);
             c_he = __shfl_sync(FULL, c_he, pick_lane, G);
             if (back) {  // leave u (it stays visited, noted at the back of the route buffer) with its clock
-                if (leader) route[a.max_steps - 1u - pops] = u;
+                route[a.max_steps - 1u - pops] = u;  // every lane of the group, the same word
                 ++pops;
                 --len;
                 const uint32_t e_in = route[len], w_in = rwait[len];
@@ -603,11 +603,10 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
             }
             if ((stepping && !done) || back) {
                 if (!back) {
-                    if (leader) {
-                        route[len] = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
-                        rwait[len] = c_w;
-                        atomicOr(tabu + (c_h >> 5), 1u << (c_h & 31));
-                    }
+                    // every lane of the group writes the same words: no lane-dependent branch per step
+                    route[len] = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
+                    rwait[len] = c_w;
+                    atomicOr(tabu + (c_h >> 5), 1u << (c_h & 31));
                     t += c_tt + c_w;
                     W += c_w;
                     u = c_h;
