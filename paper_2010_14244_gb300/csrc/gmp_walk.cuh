@@ -396,7 +396,7 @@ __device__ __forceinline__ void register_road(const ConstructArgs& a, uint32_t q
 
 // Where an ant stands after stepping back to position `len` of its route (len > 0: the head of road
 // route[len - 1]; len = 0: src): the node, its CSR row and its remaining bound h. Every lane of the
-// group reads the same words; route[] was written by the group's lane 0 before a __syncwarp.
+// group reads the same words, which every lane of the group wrote itself.
 struct StandPoint {
     uint32_t u, beg, end, h;
 };
