@@ -111,6 +111,42 @@ def test_tick_sinks_and_unsignalised(gm, ctx, orc):
     assert int(veh2.sum()) < int(veh.sum())  # vehicles left through nodes 40..59's missing out-roads
 
 
+def test_tick_high_in_degree_and_many_phases(gm, ctx, orc):
+    """Intersections with up to 14 approaches (several rounds of four in the intersection passes) and 1 to
+    6 phases (the two-phase rule and the general one), through a tick sequence: vehicles, red times,
+    phase orders and road records after every tick equal the oracle's."""
+    rng = np.random.default_rng(21)
+    n = 80
+    hubs = list(range(0, n, 10))
+    roads = {}
+    for h in hubs:
+        for u in rng.choice([x for x in range(n) if x != h], size=int(rng.integers(6, 15)), replace=False):
+            roads[(int(u), h)] = (int(rng.integers(300, 4000)), 50, int(rng.integers(1, 4)), int(rng.integers(0, 2)))
+    for u in range(n):
+        for v in rng.choice(n, size=2, replace=False):
+            if int(v) != u and (u, int(v)) not in roads:
+                roads[(u, int(v))] = (int(rng.integers(300, 4000)), 60, int(rng.integers(1, 4)), int(rng.integers(0, 2)))
+    sigs = {}
+    for k, h in enumerate(hubs):
+        g = [int(x) for x in rng.integers(5000, 20000, [1, 2, 2, 3, 4, 5, 6, 2][k])]
+        sigs[h] = (sum(g), int(rng.integers(0, sum(g))), g)
+    for v in range(1, n, 3):
+        sigs.setdefault(v, (20_000, int(rng.integers(0, 20_000)), [12_000, 8_000]))
+    net, sig, veh = NB.build(n, [(a, b, *r) for (a, b), r in sorted(roads.items())], signals=sigs,
+                             bidirectional=False)
+    ep = sig.edge_phase.copy()
+    for e in range(net.n_edges):  # approaches spread over every phase of their head
+        P = int(sig.n_phases[net.col[e]])
+        ep[e] = rng.integers(0, P) if P > 2 else (0 if P == 1 else ep[e])
+    sig = W.SignalTiming(sig.n_phases, sig.cycle_ms, sig.offset_ms, sig.green_ms, ep)
+    assert np.bincount(net.col, minlength=n).max() > 8
+    veh[:] = rng.integers(0, 60, size=veh.size)
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    _run_ticks(ctx, orc, net, sig, veh.copy(), 30, seed=15)
+
+
 def test_solve_after_ticks_matches_oracle(gm, ctx, orc):
     wl = W.grid10()
     ctx.load_workload(wl)
