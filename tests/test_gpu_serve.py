@@ -176,6 +176,8 @@ def test_views_share_one_graph(gm, orc):
         _same(twin.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed),
               ref.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed))
         np.testing.assert_array_equal(owner.densities(), wl.vehicles)
+        np.testing.assert_array_equal(view.densities(), wl.vehicles)  # read through the owner's tables
+        np.testing.assert_array_equal(twin.red_times(), ref.red_times())
         _same(view.solve(q.src, q.dst, q.n_ants, q.n_iter, q.alpha, q.beta, q.rho, q.seed), base)
     finally:
         for c in (view, twin, owner, ref):
