@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="lanes per ant (0 = autotune)")
     p.add_argument("--free-running", action="store_true",
                    help="with --lanes/--mode: sub-warp ants without warp lockstep (the tuner's pick for grid64)")
+    p.add_argument("--handoff", type=int, default=0,
+                   help="with --lanes/--mode: hand walks longer than this many moves to the tail kernel")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-colony-per-launch comparison")
@@ -358,7 +360,7 @@ def geo100k_leg(with_cpu):
            **routed_summary(res, wl.queries, ms / 1e3),
            "roofline": leg_roofline(bytes_per_ant_step(wl.net.n_nodes, wl.net.n_edges), steps, ms / 1e3, peak, kind,
                                     "job device time, median of 3, L2 flushed"),
-           "schedule": {k: tune[k] for k in ("lanes_per_ant", "mode", "branches", "lockstep")}}
+           "schedule": {k: tune[k] for k in ("lanes_per_ant", "mode", "branches", "lockstep", "handoff_moves")}}
     if with_cpu:
         out["cpu_baseline"] = oracle_baseline("geo100k", list(range(0, 512, 32)),
                                               "every 32nd colony of the same job, full size")
@@ -493,10 +495,10 @@ def run_gpu(args, rank, world, local_rank):
     if args.lanes == 0 and args.mode == 0:
         tune = ctx.autotune(wl.queries, probe_iter=32)
     else:
-        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes,
+        ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, handoff_moves=args.handoff,
                        flags=gmacop.FLAG_NO_LOCKSTEP if args.free_running else 0)
     sched = {k: v for k, v in ctx.get_params().items()
-             if k in ("mode", "lanes_per_ant", "queue_chunk", "branches", "tau_layout", "flags")}
+             if k in ("mode", "lanes_per_ant", "queue_chunk", "branches", "tau_layout", "flags", "handoff_moves")}
 
     def timed_region(flags):
         """K steps, each bracketed by CUDA events on the library's stream, L2 flushed in between."""
@@ -666,7 +668,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
         "config": dict(workload_config(wl), l2="flushed between timed steps (256 MB write)",
                        schedule={k: sched[k] for k in ("mode", "lanes_per_ant", "queue_chunk", "branches",
-                                                        "tau_layout")},
+                                                        "tau_layout", "handoff_moves")},
                        lockstep=None if tune is None else tune["lockstep"],
                        schedule_source="autotuned" if tune is not None else "command line"),
         "queries_per_s": world * nq * K / (total_ms / 1e3),

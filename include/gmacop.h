@@ -81,6 +81,11 @@ typedef struct {
                                the job stops and reports GMP_ERR_TIMEOUT; 0 = 2^23 (seconds) */
     uint32_t level_limit;   /* GMP_FLAG_EXACT_H: relaxation levels before the heuristic's pass stops and the
                                job reports GMP_ERR_TIMEOUT; 0 = 4N + 4096 */
+    uint32_t handoff_moves; /* iterative mode with sub-warp groups that do not step in lockstep, on graphs
+                               whose visited sets fit in shared memory and whose nodes have at most 8
+                               out-roads: a walk still going after this many moves is suspended and finished
+                               by a pipelined kernel with one ant per warp (the same walks, sooner); 0 = off;
+                               ignored where it does not apply */
 } gmp_params;
 
 /* Pheromone layouts. Dense: every road's pheromone is evaporated every iteration. Sparse: roads that never
@@ -225,17 +230,21 @@ typedef struct {
     float best_ms;          /* probe job time of the chosen schedule (0 from the cache) */
     float default_ms;       /* probe job time of the untuned schedule (0 from the cache) */
     uint32_t bucket[4];     /* size bucket: SM count, ceil(log2 N), max out-degree, ceil(log2 probe ants) */
+    uint32_t handoff_moves; /* iterative mode: moves after which a walk is handed to the tail kernel (0 = off) */
 } gmp_tune_result;
 
 /* Autotuner for the batched job (no counterpart in the paper, whose kernels have one fixed shape). All
  * schedules give the same results bit for bit, so only speed differs. The first call for a size bucket
  * times a probe job (the n probe queries with n_iter clamped to probe_iter, 0 = 8) under every schedule
  * the graph admits: lanes per ant 1/4/8/16/32, warp lockstep or free-running groups, the iterative or
- * the persistent job with queue chunks 8/16/32/64, and then, for the best iterative schedule, 1, 4, 32 or
- * 64 concurrent colony chains instead of the default. Each is run once to warm up, then twice timed on
+ * the persistent job with queue chunks 8/16/32/64, free-running groups that hand walks longer than 512
+ * moves to the tail kernel (where gmp_params.handoff_moves applies), and then, for the best iterative
+ * schedule, 1, 4, 32 or 64 concurrent colony chains instead of the default and, if it hands walks off,
+ * 256 or 2048 moves instead of 512. Each is run once to warm up, then twice timed on
  * the context's stream (best of two); the untuned schedule is timed first and a schedule replaces the
  * best so far only when it is at least 3% faster. The choice is cached for the process by bucket and written
- * into the context's parameters (lanes_per_ant, mode, queue_chunk, branches, the lockstep flag); later calls in
+ * into the context's parameters (lanes_per_ant, mode, queue_chunk, branches, handoff_moves, the lockstep
+ * flag); later calls in
  * the same bucket apply the cached choice without timing. Replaces any staged batch. Synchronous.
  * Errors: INVALID_ARG, STATE, UNSUPPORTED (no schedule ran), and those of gmp_batch_stage. */
 int gmp_autotune(gmp_ctx *ctx, uint32_t n, const gmp_query *probe, uint32_t probe_iter, gmp_tune_result *out);

@@ -44,7 +44,7 @@ constexpr uint32_t kTickDtMax = 1u << 30;
 
 struct BatchKey {
     uint32_t Q = 0, maxI = 0, total_ants = 0, max_steps = 0, flags = 0, lanes = 0, grid = 0, thr_on = 0, t_dep = 0,
-             chunk = 0, branches = 0, sparse = 0, poll_limit = 0, level_limit = 0;
+             chunk = 0, branches = 0, sparse = 0, poll_limit = 0, level_limit = 0, handoff = 0;
     uint64_t log_entries = 0;
     const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool operator==(const BatchKey& o) const { return memcmp(this, &o, sizeof(BatchKey)) == 0; }
@@ -77,6 +77,11 @@ struct Batch {
     uint32_t* ant_log = nullptr;
     uint32_t* tabu = nullptr;
     DevResult* res = nullptr;
+    // hand-off of long walks to the tail kernel (handoff: the move count, 0 = off for this job)
+    uint32_t handoff = 0;
+    uint32_t* tail_list = nullptr;    // total_ants: suspended walks, per chain from its first ant on
+    WalkState* tail_state = nullptr;  // total_ants
+    uint32_t* tail_tabu = nullptr;    // total_ants * visited-bitmap words
     // persistent job
     bool persistent = false;
     IterCounters* ctr = nullptr;
@@ -101,6 +106,7 @@ struct Batch {
     struct Branch {
         uint32_t q0, q1, ants, ticket_base, maxI;
         KernelConfig kc;
+        KernelConfig kc_tail;  // the tail kernel of this chain (hand-off)
         size_t tabu_off;  // words into the global visited-bitmap pool
     };
     std::vector<Branch> br;
@@ -112,6 +118,7 @@ struct Batch {
 // iteration counts and kernel shapes. Jobs with equal topology differ only in kernel parameters.
 std::vector<uint32_t> topology_of(const Batch& b) {
     std::vector<uint32_t> t{b.persistent ? 1u : 0u, b.timed ? 1u : 0u, b.exact_h ? 1u : 0u, b.queue_general ? 1u : 0u,
+                            b.handoff ? 1u : 0u,
                             (uint32_t)b.br.size(), b.maxI,
                             (uint32_t)b.kc.lanes, (uint32_t)b.kc.slots, b.kc.lockstep ? 1u : 0u,
                             b.kc.tabu_in_smem ? 1u : 0u, (uint32_t)b.kc.block, b.kc.frac ? 1u : 0u};
@@ -131,7 +138,8 @@ bool same_plan(const std::vector<Batch::Branch>& x, const std::vector<Batch::Bra
         if (a.q0 != b.q0 || a.q1 != b.q1 || a.ants != b.ants || a.ticket_base != b.ticket_base || a.maxI != b.maxI ||
             a.tabu_off != b.tabu_off || a.kc.grid != b.kc.grid || a.kc.block != b.kc.block ||
             a.kc.lanes != b.kc.lanes || a.kc.slots != b.kc.slots || a.kc.smem != b.kc.smem ||
-            a.kc.tabu_in_smem != b.kc.tabu_in_smem || a.kc.lockstep != b.kc.lockstep || a.kc.frac != b.kc.frac)
+            a.kc.tabu_in_smem != b.kc.tabu_in_smem || a.kc.lockstep != b.kc.lockstep || a.kc.frac != b.kc.frac ||
+            a.kc_tail.grid != b.kc_tail.grid || a.kc_tail.smem != b.kc_tail.smem)
             return false;
     }
     return true;
@@ -379,6 +387,9 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.hdist);
     dfree(c, &b.hqueue);
     dfree(c, &b.hstamp);
+    dfree(c, &b.tail_list);
+    dfree(c, &b.tail_state);
+    dfree(c, &b.tail_tabu);
     b.staged = b.ran = false;
 }
 
@@ -648,6 +659,10 @@ ConstructArgs construct_args(gmp_ctx* c) {
     a.tflag = b.tflag;
     a.list_e = b.list_e;
     a.list_tau = b.list_tau;
+    a.handoff_moves = b.handoff;
+    a.tail_list = b.tail_list;
+    a.tail_state = b.tail_state;
+    a.tail_tabu = b.tail_tabu;
     return a;
 }
 
@@ -694,7 +709,8 @@ int enqueue_job(gmp_ctx* c) {
     GMP_TRY(enqueue_exact_h(c));
     if (b.exact_h) ++n;
     GMP_CUDA(c, launch_init_batch(s, b.Q, c->E, b.dq, c->col, c->x, c->y, c->kappa, c->prm.flags, b.tau, b.th,
-                                  b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B, b.sparse ? 1u : 0u, b.tflag,
+                                  b.dep, b.qs, b.tickets, b.maxI * (uint32_t)B * (b.handoff ? 3u : 1u),
+                                  b.sparse ? 1u : 0u, b.tflag,
                                   tflag_words(c), b.exact_h ? b.hdist : nullptr, c->N, false));
     ++n;
     if (timed) GMP_TRY(record(c, b, 1));
@@ -720,6 +736,10 @@ int enqueue_job(gmp_ctx* c) {
         a.dep = b.dep + co;
         a.qs = b.qs + r.q0;
         a.tickets = b.tickets + (size_t)j * b.maxI;
+        if (b.handoff) {  // the tail counters follow the tickets: B * maxI suspended, then B * maxI taken up
+            a.tail_count = b.tickets + ((size_t)B + j) * b.maxI;
+            a.tail_claim = b.tickets + (2 * (size_t)B + j) * b.maxI;
+        }
         if (b.sparse) {
             a.tflag = b.tflag + (size_t)r.q0 * a.tflag_words;
             a.list_e = b.list_e + co;
@@ -741,6 +761,10 @@ int enqueue_job(gmp_ctx* c) {
         }
         for (uint32_t it = 0; it < r.maxI; ++it) {
             GMP_CUDA(c, launch_construct(bs, r.kc, a, it));
+            if (b.handoff) {  // the walks the construction launch suspended
+                GMP_CUDA(c, launch_construct_tail(bs, r.kc_tail, a, it));
+                ++n;
+            }
             if (timed) GMP_CUDA(c, cudaEventRecordWithFlags(b.ev[eb + 1 + 2 * it], bs, cudaEventRecordExternal));
             e.it = it;
             // the queue update of iteration `it` runs once, in chain it mod B (densities are fixed during a
@@ -786,6 +810,7 @@ BatchKey key_of(const gmp_ctx* c) {
     k.thr_on = c->prm.thr_permille != kThrOff;
     k.t_dep = c->prm.t_dep_ms;
     k.log_entries = b.log_entries;
+    k.handoff = b.handoff;
     k.ptrs[0] = b.tau;
     k.ptrs[1] = b.routes;
     k.ptrs[2] = b.tabu;
@@ -1185,6 +1210,16 @@ uint32_t branch_count(const gmp_ctx* c, uint32_t n) {
 
 // Launch shape of the job for the context's parameters and `total_ants` ants per iteration; `frac` when
 // some colony of the job has non-integer exponents.
+// The hand-off move count of a job run with kernel configuration kc, or 0 where it does not apply: it
+// needs the iterative job, groups that do not step in lockstep, visited sets in shared memory (the tail
+// kernel copies them whole) and rows of at most eight roads (the pipelined walk's sub-groups).
+uint32_t handoff_of(const gmp_ctx* c, const KernelConfig& kc) {
+    if (!c->prm.handoff_moves || c->prm.mode == GMP_MODE_PERSISTENT || kc.lockstep || kc.lanes < 4 ||
+        !kc.tabu_in_smem || c->maxdeg > 8u)
+        return 0;
+    return c->prm.handoff_moves;
+}
+
 int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc, bool frac = false) {
     *kc = KernelConfig{};
     const uint32_t ants = (uint32_t)std::min<uint64_t>(total_ants, 0xFFFFFFFFull);
@@ -1225,7 +1260,13 @@ int for_each_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max
     GMP_TRY(f(&b.ant_wait, (size_t)total_ants));
     GMP_TRY(f(&b.best_route, (size_t)n * max_steps));
     GMP_TRY(f(&b.route_out, (size_t)n * (max_steps + 1)));
-    GMP_TRY(f(&b.tickets, (size_t)maxI * branch_count(c, n)));
+    const uint32_t handoff = handoff_of(c, kc);
+    GMP_TRY(f(&b.tickets, (size_t)maxI * branch_count(c, n) * (handoff ? 3u : 1u)));
+    if (handoff) {
+        GMP_TRY(f(&b.tail_list, (size_t)total_ants));
+        GMP_TRY(f(&b.tail_state, (size_t)total_ants));
+        GMP_TRY(f(&b.tail_tabu, (size_t)total_ants * words));
+    }
     GMP_TRY(f(&b.res, n));
     if (persistent) {
         GMP_TRY(f(&b.ctr, (size_t)n * maxI));
@@ -1310,6 +1351,7 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
         }
         r.tabu_off = off;
         if (!r.kc.tabu_in_smem) off += (size_t)r.kc.grid * (r.kc.block / r.kc.lanes) * words;
+        if (b.handoff) GMP_CUDA(c, construct_tail_config(c->device, c->N, std::max<uint32_t>(r.ants, 1u), &r.kc_tail));
         b.br.push_back(r);
     }
     b.tabu_used = off;
@@ -1408,6 +1450,7 @@ int gmp_batch_stage(gmp_ctx* c, uint32_t n, const gmp_query* queries) {
     bool frac = false;
     for (uint32_t i = 0; i < n; ++i) frac = frac || (hdq[i].active & kQueryFracExp) != 0u;
     GMP_TRY(job_config(c, lanes, b.total_ants, &b.kc, frac));
+    b.handoff = handoff_of(c, b.kc);
     GMP_TRY(plan_branches(c, lanes, prefix));
     GMP_TRY(reserve_workspace(c, n, b.total_ants, maxI, b.log_entries, b.kc));
     GMP_TRY(upload(c, b.dq, hdq.data(), n));

@@ -35,6 +35,15 @@ struct QueueTables {
     const unsigned long long* K;             // tick: vehicles each intersection discharged
 };
 
+// A walk suspended by the construction kernel, to be finished by the tail kernel: where it stands and
+// what it has done (its route, waits and popped nodes stay in the route buffer, its visited set is copied
+// out beside this record).
+struct __align__(16) WalkState {
+    uint32_t u, beg, end, hu;  // node, its CSR row, remaining bound
+    uint32_t t, W, steps, len;  // clock, waits, moves, route length
+    uint32_t pops, qi, k, pad;  // steps back so far, colony (within the launch's range), ant
+};
+
 // Arguments of the construction kernel (one iteration over every ant of the batch).
 struct ConstructArgs {
     const EdgeRec* rec;
@@ -69,6 +78,14 @@ struct ConstructArgs {
     uint32_t* tflag;             // Q * tflag_words
     uint32_t* list_e;            // Q * E registered roads
     uint64_t* list_tau;          // Q * E their tau
+    // hand-off of long walks (shared-memory visited sets only): a walk still going after handoff_moves
+    // moves is suspended; the tail kernel finishes it with one ant per warp (0: off)
+    uint32_t handoff_moves;
+    uint32_t* tail_count;        // per iteration: walks suspended (this launch range's counters)
+    uint32_t* tail_claim;        // per iteration: suspended walks taken up by the tail kernel
+    uint32_t* tail_list;         // suspended walks' ant slots, from ticket_base on
+    WalkState* tail_state;       // per ant slot of the job
+    uint32_t* tail_tabu;         // per ant slot of the job: tabu_words of its visited set
 };
 
 // Arguments of the fused iteration-end kernel (evaporation + deposits, best route, queue update).
@@ -162,6 +179,9 @@ cudaError_t launch_exact_h(cudaStream_t s, uint32_t Q, uint32_t N, const DevQuer
 cudaError_t launch_materialize_tau(cudaStream_t s, uint32_t E, const QueryState* qs, const uint32_t* list_e,
                                    const uint64_t* list_tau, uint64_t* out);
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
+// The walks the construction launch of iteration it suspended, finished one per warp (pipelined walk).
+cudaError_t launch_construct_tail(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it);
+cudaError_t construct_tail_config(int device, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out);
 cudaError_t launch_iter_end(cudaStream_t s, const IterEndArgs& a);
 cudaError_t launch_finalize(cudaStream_t s, uint32_t Q, const DevQuery* q, const QueryState* qs,
                             const uint32_t* best_route, const uint32_t* col, uint32_t max_steps, DevResult* res,

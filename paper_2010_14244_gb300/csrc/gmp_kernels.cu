@@ -6,6 +6,8 @@
 //   k_tick_node       serving tick: discharge of every approach and red-time update  (Fig. 3 signal block)
 //   k_init_batch      initial pheromone, per-colony state                          (Algorithm 2)
 //   k_construct<G,K>  ant walks: Adj_Neigh, next-node roulette, Eval_Rout, position update, deposits
+//   k_construct_tail  the walks a construction launch handed off after handoff_moves moves, finished
+//                     one per warp by the pipelined walk (walk_ant_spec)
 //   k_iter_end        Evap_Pher fused with the deposits of Updt_Pher, best-route tracking and the
 //                     per-iteration queue/preemption update, in one launch
 //   k_finalize        best route as node ids + counters
@@ -363,7 +365,31 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
         }
         const DevQuery q = a.queries[lo];
         if (!q.active || it >= q.n_iter) continue;
-        walk_ant<G, K>(a, q, lo, tg - q.ant_base, it, tabu, lane, gmask, gbase);
+        walk_ant<G, K, SMEM>(a, q, lo, tg - q.ant_base, it, tabu, lane, gmask, gbase);  // hand-off: shared bitmaps
+    }
+}
+
+// Tail of an iteration's construction (handoff_moves != 0): the walks the construction launch suspended,
+// finished one per warp by the pipelined walk. Warps take walks from a counter; each copies its walk's
+// visited set into its slice of shared memory first.
+__global__ void __launch_bounds__(128) k_construct_tail(ConstructArgs a, uint32_t it) {
+    extern __shared__ uint32_t smem[];
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t* tabu = smem + (size_t)(threadIdx.x >> 5) * a.tabu_words;
+    const uint32_t n = a.tail_count[it];  // final: the construction launch before this one wrote it
+    for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(a.tail_claim + it, 1u);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= n) break;
+        const uint32_t slot = a.tail_list[a.ticket_base + i];
+        const WalkState ws = a.tail_state[slot];
+        const uint32_t* in = a.tail_tabu + (size_t)slot * a.tabu_words;
+        for (uint32_t w = lane; w < a.tabu_words; w += 32u) tabu[w] = in[w];
+        __syncwarp();
+        const DevQuery q = a.queries[ws.qi];
+        walk_ant_spec(a, q, ws.qi, ws.k, it, tabu, lane, ws);
     }
 }
 
@@ -1322,6 +1348,31 @@ cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, u
     if (lanes == 8 && k == 2) return config_gl<8, 2>(device, n_nodes, total_ants, frac, out);
     if (lanes == 16 && k == 1) return config_gl<16, 1>(device, n_nodes, total_ants, frac, out);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t construct_tail_config(int device, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out) {
+    KernelConfig kc{};
+    kc.lanes = 32;
+    kc.slots = 1;
+    kc.block = 128;
+    kc.tabu_in_smem = true;
+    kc.smem = (size_t)(kc.block / 32) * ((n_nodes + 31u) / 32u) * 4u;
+    cudaError_t err = cudaSuccess;
+    if (kc.smem > 48u * 1024u)
+        err = cudaFuncSetAttribute(k_construct_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kc.smem);
+    if (err != cudaSuccess) return err;
+    // suspended walks are a few of the launch's ants: a modest grid whose warps loop over them
+    const uint32_t warps = total_ants < 256u ? total_ants : 256u;
+    kc.grid = (int)((warps + 3u) / 4u);
+    if (kc.grid < 1) kc.grid = 1;
+    (void)device;
+    *out = kc;
+    return cudaSuccess;
+}
+
+cudaError_t launch_construct_tail(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it) {
+    k_construct_tail<<<kc.grid, kc.block, kc.smem, s>>>(a, it);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it) {

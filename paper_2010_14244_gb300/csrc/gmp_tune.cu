@@ -1,8 +1,9 @@
 // Schedule autotuner (gmp_autotune, declared in include/gmacop.h).
 //
 // Every schedule computes the same results bit for bit: lanes per ant (ants per warp = 32 / lanes),
-// warp lockstep or free-running groups, the iterative job or the persistent job, and the persistent
-// job's queue-update chunk change only how the same arithmetic is laid onto the GPU. So the tuner may
+// warp lockstep or free-running groups, the hand-off of long walks to the tail kernel, the iterative
+// job or the persistent job, and the persistent job's queue-update chunk change only how the same
+// arithmetic is laid onto the GPU. So the tuner may
 // pick whatever runs fastest. It times a short probe job (the caller's queries with their iteration
 // counts clamped) under every schedule the graph admits and keeps the fastest, once per size bucket
 // of the process: (SM count, ceil(log2 N), maximum out-degree, ceil(log2 ants per iteration)).
@@ -24,12 +25,13 @@ using namespace gmp;
 namespace {
 
 struct Schedule {
-    uint32_t lanes, mode, chunk, free_running, branches;
+    uint32_t lanes, mode, chunk, free_running, branches, handoff;
 };
 
 using Bucket = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
 
 constexpr float kMargin = 0.03f;  // relative speed-up a schedule needs over the best so far
+constexpr uint32_t kHandoffMoves = 512;  // hand-off candidates: walks longer than this go to the tail kernel
 
 std::mutex g_mu;
 std::map<Bucket, Schedule> g_cache;
@@ -44,7 +46,7 @@ uint32_t ceil_log2(uint64_t x) {
 // where the lockstep kernel covers the shape.
 Schedule default_schedule(uint32_t maxdeg) {
     const uint32_t g = default_lanes(maxdeg);
-    return {g, GMP_MODE_ITERATIVE, 0, 0, 0};
+    return {g, GMP_MODE_ITERATIVE, 0, 0, 0, 0};
 }
 
 uint32_t runs_lockstep(const Schedule& s, uint32_t maxdeg) {
@@ -56,16 +58,17 @@ std::vector<Schedule> candidates(uint32_t n_nodes, uint32_t maxdeg) {
     std::vector<Schedule> out{d};  // timed first
     auto add = [&](Schedule s) {
         if (!(s.lanes == d.lanes && s.mode == d.mode && s.chunk == d.chunk && s.free_running == d.free_running &&
-              s.branches == d.branches))
+              s.branches == d.branches && s.handoff == d.handoff))
             out.push_back(s);
     };
     if (construct_thread_fits(n_nodes) && (uint32_t)construct_max_degree(1) >= maxdeg)
-        add({1, GMP_MODE_ITERATIVE, 0, 0, 0});
+        add({1, GMP_MODE_ITERATIVE, 0, 0, 0, 0});
     for (uint32_t g : {4u, 8u, 16u, 32u}) {
         if ((uint32_t)construct_max_degree((int)g) < maxdeg) continue;
-        add({g, GMP_MODE_ITERATIVE, 0, 0, 0});
-        if (lockstep_fits((int)g, maxdeg)) add({g, GMP_MODE_ITERATIVE, 0, 1, 0});
-        for (uint32_t ch : {8u, 16u, 32u, 64u}) add({g, GMP_MODE_PERSISTENT, ch, 0, 0});
+        add({g, GMP_MODE_ITERATIVE, 0, 0, 0, 0});
+        if (lockstep_fits((int)g, maxdeg)) add({g, GMP_MODE_ITERATIVE, 0, 1, 0, 0});
+        if (g < 32u && maxdeg <= 8u) add({g, GMP_MODE_ITERATIVE, 0, 1, 0, kHandoffMoves});
+        for (uint32_t ch : {8u, 16u, 32u, 64u}) add({g, GMP_MODE_PERSISTENT, ch, 0, 0, 0});
     }
     return out;
 }
@@ -75,6 +78,7 @@ gmp_params with_schedule(gmp_params p, const Schedule& s) {
     p.mode = s.mode;
     p.queue_chunk = s.chunk;
     p.branches = s.branches;
+    p.handoff_moves = s.handoff;
     p.flags = (p.flags & ~kFlagNoLockstepBit) | (s.free_running ? kFlagNoLockstepBit : 0u);
     return p;
 }
@@ -140,6 +144,7 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
             out->queue_chunk = s.chunk;
             out->lockstep = runs_lockstep(s, info.maxdeg);
             out->branches = s.branches;
+            out->handoff_moves = s.handoff;
             out->from_cache = 1;
             return GMP_OK;
         }
@@ -174,6 +179,14 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
             v.branches = br;
             try_schedule(v, false);
         }
+        if (best.handoff) {  // then the hand-off move count
+            const Schedule b1 = best;
+            for (uint32_t m : {256u, 2048u}) {
+                Schedule v = b1;
+                v.handoff = m;
+                try_schedule(v, false);
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -193,6 +206,7 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
     out->queue_chunk = best.chunk;
     out->lockstep = runs_lockstep(best, info.maxdeg);
     out->branches = best.branches;
+    out->handoff_moves = best.handoff;
     out->best_ms = best_ms;
     return GMP_OK;
 }

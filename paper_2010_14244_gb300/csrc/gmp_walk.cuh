@@ -450,7 +450,7 @@ __device__ __forceinline__ void forget_visited(const ConstructArgs& a, uint32_t*
 // it leaves stays visited and is noted at the back of the route buffer).
 // Groups take ants from a per-iteration ticket counter, so short walks free lanes for waiting ants.
 // ------------------------------------------------------------------------------------------------
-template <int G, int K>
+template <int G, int K, bool HANDOFF>
 __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery& q, uint32_t qi, uint32_t k,
                                          uint32_t it, uint32_t* tabu, uint32_t lane, uint32_t gmask, uint32_t gbase) {
     constexpr int NC = G * K;              // candidate slots of the group
@@ -478,6 +478,32 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         if (steps == a.max_steps) {
             status = kAntStepCap;
             break;
+        }
+        if (HANDOFF && a.handoff_moves && steps == a.handoff_moves) {  // a long walk: the tail kernel finishes it
+            if (lane == 0) {
+                const uint32_t idx = atomicAdd(a.tail_count + it, 1u);
+                a.tail_list[a.ticket_base + idx] = slot;
+                WalkState ws;
+                ws.u = u;
+                ws.beg = beg;
+                ws.end = end;
+                ws.hu = hu;
+                ws.t = t;
+                ws.W = W;
+                ws.steps = steps;
+                ws.len = len;
+                ws.pops = pops;
+                ws.qi = qi;
+                ws.k = k;
+                ws.pad = 0;
+                a.tail_state[slot] = ws;
+            }
+            uint32_t* out = a.tail_tabu + (size_t)slot * a.tabu_words;
+            for (uint32_t w = lane; w < a.tabu_words; w += G) out[w] = tabu[w];
+            __syncwarp(gmask);  // the copy is complete before the bits are cleared for the group's next ant
+            forget_visited(a, tabu, route, q.src, len, pops, steps, lane, G);
+            __syncwarp(gmask);
+            return;
         }
         const uint32_t deg = end - beg;
         const int nslots = K == 1 ? 1 : (int)((deg + G - 1) / G);  // group-uniform
@@ -679,6 +705,234 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
     }
     forget_visited(a, tabu, route, q.src, len, pops, steps, lane, G);
     __syncwarp(gmask);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pipelined walk, one ant per warp in four sub-groups of eight lanes. While the roulette of move k runs
+// on the scores of the node the ant stands on (held by sub-group g, lane 8g + l for road l of the
+// row), sub-group j evaluates the row of candidate j as if the ant had moved there: its loads, visited
+// checks, waits and scores, at the clock and bound the ant would have there. Move k then takes sub-group
+// p's evaluation as the next current row, so a move's dependent chain is the longer of the two halves
+// instead of their sum. A pick beyond the fourth candidate, a step back and the start evaluate the
+// stand point's row directly. The arithmetic, its inputs and the draws are walk_ant's, so the walks are
+// the same. It continues a walk that walk_ant suspended (its state, route buffer and visited set), on a
+// graph whose nodes have at most eight out-roads; the visited set is in the caller's shared memory.
+// ------------------------------------------------------------------------------------------------
+struct RowEval {  // one lane's road of a row: the fields a move needs and its score
+    uint32_t head, vbeg, vend, tt, w, he, sb;
+    bool ok;  // a road of the row, to an unvisited node
+    bool cg;  // over the congestion threshold
+};
+
+struct RowLoad {  // the loads of one lane's road of a row
+    uint4 r0, r1;
+    uint2 ph;
+    bool in;
+};
+
+__device__ __forceinline__ RowLoad load_road(const ConstructArgs& a, const uint2* th, uint32_t vbeg, uint32_t deg,
+                                             uint32_t l) {
+    RowLoad x;
+    x.in = l < deg;
+    const uint32_t e = x.in ? vbeg + l : 0u;  // past the row: road 0 (always in bounds), masked
+    const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+    x.r0 = __ldg(rp);
+    x.r1 = __ldg(rp + 1);
+    x.ph = __ldg(th + e);
+    return x;
+}
+
+__device__ __forceinline__ RowEval finish_road(const ConstructArgs& a, const DevQuery& q, float base_tf, bool frac,
+                                               const uint32_t* tabu, const RowLoad& ld, uint32_t t_at,
+                                               uint32_t h_at) {
+    const uint4 r0 = ld.r0, r1 = ld.r1;
+    const uint2 ph = ld.ph;
+    const float tf = ph.x ? __uint_as_float(ph.x) : base_tf;
+    RowEval x;
+    x.head = r0.x;
+    x.vbeg = r0.y;
+    x.vend = r0.y + (r1.x >> 24);
+    x.tt = r0.z;
+    x.he = ph.y;
+    const uint32_t cy = r1.x & kCycleMask;
+    x.ok = ld.in && !((tabu[x.head >> 5] >> (x.head & 31)) & 1u);
+    x.cg = (r0.w >> 31) != 0u;
+    const uint32_t sw = signal_wait(a.t_dep + t_at + r0.z, cy | (cy == 0u), r1.w, r1.y, r1.z);
+    x.w = (x.head != q.dst && cy != 0u) ? sw + (r0.w & kQdMask) : 0u;
+    x.sb = __float_as_uint(score_q(tf, q.alpha, reduced_cost(r0.z + x.w + x.he, h_at), q.beta, frac));
+    return x;
+}
+
+__device__ __forceinline__ RowEval eval_road(const ConstructArgs& a, const DevQuery& q, const uint2* th,
+                                             float base_tf, bool frac, const uint32_t* tabu, uint32_t vbeg,
+                                             uint32_t deg, uint32_t l, uint32_t t_at, uint32_t h_at) {
+    const bool in = l < deg;
+    const uint32_t e = in ? vbeg + l : 0u;  // past the row: road 0 (always in bounds), masked
+    const uint4* rp = reinterpret_cast<const uint4*>(a.rec + e);
+    const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    const uint2 ph = __ldg(th + e);
+    const float tf = ph.x ? __uint_as_float(ph.x) : base_tf;
+    RowEval x;
+    x.head = r0.x;
+    x.vbeg = r0.y;
+    x.vend = r0.y + (r1.x >> 24);
+    x.tt = r0.z;
+    x.he = ph.y;
+    const uint32_t cy = r1.x & kCycleMask;
+    x.ok = in && !((tabu[x.head >> 5] >> (x.head & 31)) & 1u);
+    x.cg = (r0.w >> 31) != 0u;
+    const uint32_t sw = signal_wait(a.t_dep + t_at + r0.z, cy | (cy == 0u), r1.w, r1.y, r1.z);
+    x.w = (x.head != q.dst && cy != 0u) ? sw + (r0.w & kQdMask) : 0u;
+    x.sb = __float_as_uint(score_q(tf, q.alpha, reduced_cost(r0.z + x.w + x.he, h_at), q.beta, frac));
+    return x;
+}
+
+__device__ __forceinline__ void walk_ant_spec(const ConstructArgs& a, const DevQuery& q, uint32_t qi, uint32_t k,
+                                              uint32_t it, uint32_t* tabu, uint32_t lane, const WalkState& ws) {
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t sg = lane >> 3, sl = lane & 7u;  // sub-group, lane in it
+    const uint2* __restrict__ th = a.th + (size_t)qi * a.n_edges;
+    const float base_tf = a.sparse ? __uint_as_float(a.qs[qi].base_tf) : 0.0f;
+    const bool frac = (q.active & kQueryFracExp) != 0u;
+    const uint32_t slot = q.ant_base + k;
+    uint32_t* route = a.routes + (size_t)slot * a.max_steps;
+    uint32_t* rwait = a.rwait + (size_t)slot * a.max_steps;
+    const uint32_t s0 = (uint32_t)q.seed, s1 = (uint32_t)(q.seed >> 32);
+    uint32_t u = ws.u, beg = ws.beg, end = ws.end, hu = ws.hu;  // where the suspended walk stands
+    uint32_t t = ws.t, W = ws.W, steps = ws.steps, len = ws.len, pops = ws.pops, status;
+    uint32_t rb_base = 0, rb_x = 0, rb_y = 0;  // lane l holds the draw of move rb_base + l
+    bool rb_valid = false;
+    uint32_t g = 0;  // the sub-group holding the current row
+    RowEval cur = eval_road(a, q, th, base_tf, frac, tabu, beg, end - beg, sl, t, hu);
+    for (;;) {
+        if (u == q.dst) {
+            status = kAntSuccess;
+            break;
+        }
+        if (steps == a.max_steps) {
+            status = kAntStepCap;
+            break;
+        }
+        const uint32_t gshift = 8u * g;
+        bool cand = cur.ok;
+        if (a.thr_on) {  // congested roads drop out unless every candidate is congested
+            const uint32_t okb = (__ballot_sync(FULL, cur.ok && !cur.cg) >> gshift) & 0xFFu;
+            const uint32_t cgb = (__ballot_sync(FULL, cur.ok && cur.cg) >> gshift) & 0xFFu;
+            if (okb && cgb) cand = cur.ok && !cur.cg;
+        }
+        if (((__ballot_sync(FULL, cand) >> gshift) & 0xFFu) == 0u) {
+            if (len == 0) {  // back at src with no road left
+                status = kAntDeadEnd;
+                break;
+            }
+            route[a.max_steps - 1u - pops] = u;
+            ++pops;
+            --len;
+            const uint32_t e_in = route[len], w_in = rwait[len];
+            t -= __ldg(&a.rec[e_in].tt) + w_in;
+            W -= w_in;
+            const StandPoint sp = stand_after_back(a, th, route, len, q.src, qi);
+            u = sp.u;
+            beg = sp.beg;
+            end = sp.end;
+            hu = sp.h;
+            ++steps;
+            __syncwarp();
+            cur = eval_road(a, q, th, base_tf, frac, tabu, beg, end - beg, sl, t, hu);
+            g = 0;
+            continue;
+        }
+        if (!rb_valid || steps - rb_base >= 32u) {
+            const uint4 o = philox4x32_10(make_uint4(it, k, steps + lane, 0u), s0, s1);
+            rb_x = o.x;
+            rb_y = o.y;
+            rb_base = steps;
+            rb_valid = true;
+        }
+        const uint32_t rsrc = steps - rb_base;
+        const unsigned long long rnd = (unsigned long long)__shfl_sync(FULL, rb_x, rsrc) |
+                                       ((unsigned long long)__shfl_sync(FULL, rb_y, rsrc) << 32);
+        // speculation: sub-group j evaluates the row of candidate j of the current row
+        const uint32_t src = gshift + sg;
+        const uint32_t s_vbeg = __shfl_sync(FULL, cur.vbeg, src);
+        const uint32_t s_vend = __shfl_sync(FULL, cur.vend, src);
+        const uint32_t s_tt = __shfl_sync(FULL, cur.tt, src);
+        const uint32_t s_w = __shfl_sync(FULL, cur.w, src);
+        const uint32_t s_he = __shfl_sync(FULL, cur.he, src);
+        const RowLoad sld = load_road(a, th, s_vbeg, s_vend - s_vbeg, sl);
+        // roulette on the current row, in every sub-group (sub-group g's is the move's)
+        uint32_t mb = cand ? cur.sb : 0u;
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(FULL, mb, off, 8));
+        const WeightScale sc = weight_scale(mb);
+        const uint32_t mine = cand ? roulette_weight_f(cur.sb, sc) : 0u;
+        const RowEval spec = finish_road(a, q, base_tf, frac, tabu, sld, t + s_tt + s_w, s_he);
+        uint32_t incl[8];
+#pragma unroll
+        for (int l = 0; l < 8; ++l) incl[l] = __shfl_sync(FULL, mine, l, 8);
+#pragma unroll
+        for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+            for (int i = 7; i >= h; --i) incl[i] += incl[i - h];
+        const uint32_t r = draw_index(rnd, incl[7]);
+        uint32_t pick = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pick += incl[i] <= r ? 1u : 0u;
+        const uint32_t p = __shfl_sync(FULL, pick, gshift);
+        const uint32_t cl = gshift + p;
+        const uint32_t c_h = __shfl_sync(FULL, cur.head, cl);
+        const uint32_t c_vb = __shfl_sync(FULL, cur.vbeg, cl);
+        const uint32_t c_ve = __shfl_sync(FULL, cur.vend, cl);
+        const uint32_t c_tt = __shfl_sync(FULL, cur.tt, cl);
+        const uint32_t c_w = __shfl_sync(FULL, cur.w, cl);
+        const uint32_t c_he = __shfl_sync(FULL, cur.he, cl);
+        const uint32_t e = beg + p;
+        t += c_tt + c_w;
+        W += c_w;
+        u = c_h;
+        beg = c_vb;
+        end = c_ve;
+        hu = c_he;
+        route[len] = e;
+        rwait[len] = c_w;
+        atomicOr(tabu + (u >> 5), 1u << (u & 31));
+        ++len;
+        ++steps;
+        __syncwarp();
+        if (p < 4u) {  // sub-group p evaluated the new stand point's row
+            cur = spec;
+            g = p;
+        } else {
+            cur = eval_road(a, q, th, base_tf, frac, tabu, beg, end - beg, sl, t, hu);
+            g = 0;
+        }
+        if (t > kTCap) {
+            status = kAntTimeCap;
+            break;
+        }
+    }
+    QueryState* S = a.qs + qi;
+    if (lane == 0) {
+        a.ant_steps[slot] = len;
+        a.ant_wait[slot] = W;
+        atomicAdd(&S->steps, (unsigned long long)steps);
+        if (status == kAntSuccess) atomicAdd(&S->nsucc, 1ull);
+        if (a.ant_log) {
+            uint32_t* l = a.ant_log + 4ull * (q.log_base + (uint64_t)it * q.n_ants + k);
+            *reinterpret_cast<uint4*>(l) = make_uint4(status | (len << 8), steps, t, W);
+        }
+    }
+    if (status == kAntSuccess) {  // Updt_Pher: deposit ant_deposit() on every road of the route
+        const unsigned long long delta = ant_deposit(S->dep_num, t);
+        unsigned long long* D = a.dep + (size_t)qi * a.n_edges;
+        for (uint32_t i = lane; i < len; i += 32u) {
+            atomicAdd(D + route[i], delta);
+            if (a.sparse) register_road(a, qi, S, route[i]);
+        }
+        if (lane == 0) atomicMin(&S->best_key, ((unsigned long long)t << 32) | ((unsigned long long)it * q.n_ants + k));
+    }
+    forget_visited(a, tabu, route, q.src, len, pops, steps, lane, 32u);
+    __syncwarp();
 }
 
 }  // namespace gmp

@@ -34,7 +34,8 @@ class TuneResult(C.Structure):
     _fields_ = [("lanes_per_ant", C.c_uint32), ("mode", C.c_uint32), ("queue_chunk", C.c_uint32),
                 ("lockstep", C.c_uint32), ("branches", C.c_uint32), ("from_cache", C.c_uint32),
                 ("n_tried", C.c_uint32),
-                ("best_ms", C.c_float), ("default_ms", C.c_float), ("bucket", C.c_uint32 * 4)]
+                ("best_ms", C.c_float), ("default_ms", C.c_float), ("bucket", C.c_uint32 * 4),
+                ("handoff_moves", C.c_uint32)]
 
 
 class ServerConfig(C.Structure):
@@ -52,7 +53,8 @@ class Params(C.Structure):
     _fields_ = [("max_steps", C.c_uint32), ("h_sat_ms", C.c_uint32), ("thr_permille", C.c_uint32),
                 ("flags", C.c_uint32), ("t_dep_ms", C.c_uint32), ("lanes_per_ant", C.c_uint32),
                 ("mode", C.c_uint32), ("queue_chunk", C.c_uint32), ("branches", C.c_uint32),
-                ("tau_layout", C.c_uint32), ("poll_limit", C.c_uint32), ("level_limit", C.c_uint32)]
+                ("tau_layout", C.c_uint32), ("poll_limit", C.c_uint32), ("level_limit", C.c_uint32),
+                ("handoff_moves", C.c_uint32)]
 
 
 class Query(C.Structure):
@@ -232,9 +234,9 @@ class Context:
 
     def set_params(self, max_steps=0, h_sat_ms=0, thr_permille=THRESHOLD_OFF, flags=0, t_dep_ms=0,
                    lanes_per_ant=0, mode=MODE_AUTO, queue_chunk=0, branches=0, tau_layout=TAU_AUTO, poll_limit=0,
-                   level_limit=0):
+                   level_limit=0, handoff_moves=0):
         p = Params(max_steps, h_sat_ms, thr_permille, flags, t_dep_ms, lanes_per_ant, mode, queue_chunk, branches,
-                   tau_layout, poll_limit, level_limit)
+                   tau_layout, poll_limit, level_limit, handoff_moves)
         self._check(lib().gmp_set_params(self._h, C.byref(p)))
 
     def get_params(self) -> dict:

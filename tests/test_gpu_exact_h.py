@@ -11,7 +11,7 @@ import pytest
 
 from paper_2010_14244_gb300 import workloads as W
 from tests import netbuild as NB
-from tests.test_gpu_parity import SCHEDULES, _compare
+from tests.test_gpu_parity import SCHEDULES, _compare, _with_flags
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def ctx(gm):
 def test_grid10_exact_h(gm, ctx, orc, sched):
     wl = W.grid10(n_ants=32, n_iter=12)
     ctx.load_workload(wl)
-    ctx.set_params(flags=EXACT | gm.FLAG_ANT_LOG, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, EXACT | gm.FLAG_ANT_LOG))
     q = wl.queries[0]
     r = ctx.solve_batch([q])[0]
     _compare(orc, orc.Net.from_workload(wl), orc.Params(flags=EXACT), q, r, ctx, 0, ctx.ant_log(0))
@@ -48,7 +48,7 @@ def test_grid10_exact_h(gm, ctx, orc, sched):
 def test_grid64_exact_h_batch(gm, ctx, orc, sched):
     wl = W.grid64(n_queries=4, n_ants=256, n_iter=12)
     ctx.load_workload(wl)
-    ctx.set_params(flags=EXACT | gm.FLAG_ANT_LOG, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, EXACT | gm.FLAG_ANT_LOG))
     res = ctx.solve_batch(wl.queries)
     onet = orc.Net.from_workload(wl)
     for i, q in enumerate(wl.queries):

@@ -6,7 +6,7 @@ import dataclasses
 import pytest
 
 from paper_2010_14244_gb300 import workloads as W
-from tests.test_gpu_parity import SCHEDULES, _compare
+from tests.test_gpu_parity import SCHEDULES, _compare, _with_flags
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,7 @@ def ctx(gm):
 def test_grid10_fractional_exponents(gm, ctx, orc, ab, sched):
     wl = W.grid10(n_ants=32, n_iter=12)
     ctx.load_workload(wl)
-    ctx.set_params(flags=gm.FLAG_ANT_LOG, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, gm.FLAG_ANT_LOG))
     q = Q(wl.queries[0].src, wl.queries[0].dst, 32, 12, ab[0], ab[1], 0.15, 31)
     r = ctx.solve_batch([q])[0]
     _compare(orc, orc.Net.from_workload(wl), orc.Params(), q, r, ctx, 0, ctx.ant_log(0))

@@ -5,7 +5,7 @@ import pytest
 
 from paper_2010_14244_gb300 import workloads as W
 from tests import netbuild as NB
-from tests.test_gpu_parity import SCHEDULES, _compare
+from tests.test_gpu_parity import SCHEDULES, _compare, _with_flags
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def test_grid10_literal_flags(gm, ctx, orc, which, sched):
     wl = W.grid10(n_ants=32, n_iter=15)
     ctx.load_workload(wl)
     flags = _flag_sets(gm)[which]
-    ctx.set_params(flags=flags | gm.FLAG_ANT_LOG, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, flags | gm.FLAG_ANT_LOG))
     q = wl.queries[0]
     r = ctx.solve_batch([q])[0]
     _compare(orc, orc.Net.from_workload(wl), orc.Params(flags=flags), q, r, ctx, 0, ctx.ant_log(0))
@@ -82,7 +82,7 @@ def test_saturated_attractive_scores(gm, ctx, orc, sched):
     ctx.load_graph(net)
     ctx.set_signals(sig)
     ctx.set_densities(veh)
-    ctx.set_params(flags=flags, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, flags))
     r = ctx.solve_batch([q])[0]
     _compare(orc, onet, orc.Params(flags=flags), q, r, ctx)
 
@@ -98,7 +98,7 @@ def test_saturated_repulsive_scores(gm, ctx, orc, sched):
     o = orc.solve(onet, orc.Params(flags=flags), q)
     assert int(o["tau"].min()) < 2**16
     ctx.load_workload(wl)
-    ctx.set_params(flags=flags, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, flags))
     r = ctx.solve_batch([q])[0]
     _compare(orc, onet, orc.Params(flags=flags), q, r, ctx)
 

@@ -35,9 +35,18 @@ def ctx(gm):
 
 # job schedules: the iterative job as one chain, as two and as the default number of concurrent colony
 # chains, and the persistent job
+FREE = 16  # gmacop.FLAG_NO_LOCKSTEP: sub-warp groups that do not step in lockstep
 SCHEDULES = {"chains1": dict(mode=1, branches=1), "chains2": dict(mode=1, branches=2),
              "chains_default": dict(mode=1), "persistent": dict(mode=2),
-             "sparse_tau": dict(mode=1, tau_layout=2), "dense_tau": dict(mode=1, tau_layout=1)}
+             "sparse_tau": dict(mode=1, tau_layout=2), "dense_tau": dict(mode=1, tau_layout=1),
+             # walks longer than 3 moves finish in the tail kernel (pipelined, one ant per warp)
+             "handoff": dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3)}
+
+
+def _with_flags(sched, flags):
+    kw = dict(SCHEDULES[sched])
+    kw["flags"] = kw.get("flags", 0) | flags
+    return kw
 
 
 def _oparams(orc, **kw):
@@ -180,7 +189,7 @@ def test_grid64_batch_parity_reduced(gm, ctx, orc, sched):
     """Four colonies of 256 ants x 20 iterations in one job; each equals its solo oracle solve."""
     wl = W.grid64(n_queries=4, n_ants=256, n_iter=20)
     ctx.load_workload(wl)
-    ctx.set_params(flags=gm.FLAG_ANT_LOG, **SCHEDULES[sched])
+    ctx.set_params(**_with_flags(sched, gm.FLAG_ANT_LOG))
     res = ctx.solve_batch(wl.queries)
     onet = orc.Net.from_workload(wl)
     for i, q in enumerate(wl.queries):
@@ -217,17 +226,24 @@ def grid64_oracle():
     return [o for _, o in out]
 
 
-@pytest.mark.parametrize("mode", [1, 2])
-def test_grid64_full_size_full_parity(gm, ctx, orc, grid64_oracle, mode):
-    """The benchmark's job (16 colonies x 1024 ants x 200 iterations, one launch) in the chained and the
-    persistent form: every colony equals the oracle's solve exactly, final pheromone table included."""
+FULL_SIZE = {"chains": dict(mode=1), "persistent": dict(mode=2),
+             "handoff": dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=512)}
+
+
+@pytest.mark.parametrize("form", list(FULL_SIZE))
+def test_grid64_full_size_full_parity(gm, ctx, orc, grid64_oracle, form):
+    """The benchmark's job (16 colonies x 1024 ants x 200 iterations, one launch) in the chained form,
+    the persistent form and the chained form that hands walks longer than 512 moves to the tail kernel:
+    every colony equals the oracle's solve exactly, final pheromone table included."""
     wl = W.grid64()
     ctx.load_workload(wl)
-    ctx.set_params(mode=mode)  # the benchmark's launch configuration (no timing events)
+    kw = FULL_SIZE[form]
+    mode = kw["mode"]
+    ctx.set_params(**kw)  # the benchmark's launch configuration (no timing events)
     ctx.stage(wl.queries)
     ctx.launch()
     res0 = ctx.collect()
-    ctx.set_params(flags=gm.FLAG_KERNEL_TIMING, mode=mode)
+    ctx.set_params(**dict(kw, flags=kw.get("flags", 0) | gm.FLAG_KERNEL_TIMING))
     ctx.stage(wl.queries)
     ctx.launch()
     res = ctx.collect()
