@@ -33,6 +33,8 @@ def main():
     p.add_argument("--alpha", type=float, default=0.0, help="pheromone exponent of every colony (0 = its own)")
     p.add_argument("--free-running", action="store_true", help="sub-warp ants without warp lockstep")
     p.add_argument("--pheromone", action="store_true", help="read colony 0's pheromone table after each run")
+    p.add_argument("--handoff", type=int, default=0,
+                   help="hand walks longer than this many moves to the tail kernel (0 = off)")
     args = p.parse_args()
 
     import dataclasses
@@ -61,7 +63,8 @@ def main():
     ctx.load_workload(wl)
     flags = args.flags | (gmacop.FLAG_KERNEL_TIMING if args.kernel_times else 0)
     flags |= gmacop.FLAG_NO_LOCKSTEP if args.free_running else 0
-    ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, tau_layout=args.tau_layout, flags=flags)
+    ctx.set_params(mode=args.mode, lanes_per_ant=args.lanes, tau_layout=args.tau_layout, flags=flags,
+                   handoff_moves=args.handoff)
     ctx.stage(qs)
     clock = 0
     for r in range(args.repeat):
