@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
                     // every lane of the group writes the same words: no lane-dependent branch per step
                     route[len] = beg + (uint32_t)pick_lane + (uint32_t)pick_slot * G;
                     rwait[len] = c_w;
-                    atomicOr(tabu + (c_h >> 5), 1u << (c_h & 31));
+                    mark_visited(tabu, c_h);
                     t += c_tt + c_w;
                     W += c_w;
                     u = c_h;

