@@ -82,10 +82,10 @@ typedef struct {
     uint32_t level_limit;   /* GMP_FLAG_EXACT_H: relaxation levels before the heuristic's pass stops and the
                                job reports GMP_ERR_TIMEOUT; 0 = 4N + 4096 */
     uint32_t handoff_moves; /* iterative mode with sub-warp groups that do not step in lockstep, on graphs
-                               whose visited sets fit in shared memory and whose nodes have at most 8
-                               out-roads: a walk still going after this many moves is suspended and finished
-                               by a pipelined kernel with one ant per warp (the same walks, sooner); 0 = off;
-                               ignored where it does not apply */
+                               whose visited sets fit in shared memory, whose nodes have at most 8 out-roads
+                               and that have no road from a node to itself: a walk still going after this
+                               many moves is suspended and finished by a pipelined kernel with one ant per
+                               warp (the same walks, sooner); 0 = off; ignored where it does not apply */
 } gmp_params;
 
 /* Pheromone layouts. Dense: every road's pheromone is evaporated every iteration. Sparse: roads that never

@@ -164,6 +164,7 @@ struct gmp_ctx {
     uint32_t N = 0, E = 0, maxdeg = 0, kappa = 0;
     uint32_t h_delta = 1;  // exact heuristic: near-far threshold step, 16 x the mean free-flow road time (ms)
     uint32_t max_phases = 0;  // most phases at any intersection (above 2: the iteration end's general pass)
+    bool self_loops = false;  // some road leads from a node back to itself
     uint32_t *row_ptr = nullptr, *col = nullptr, *len = nullptr, *in_ptr = nullptr, *in_edge = nullptr;
     uint32_t* in_tail = nullptr;  // tail of each in_edge entry (exact Calc_Dist relaxes towards tails)
     // Per-approach tables are in slot order (slot i = road in_edge[i], so an intersection's approaches
@@ -950,6 +951,9 @@ int gmp_load_graph(gmp_ctx* c, uint32_t N, uint32_t E, const uint32_t* row_ptr, 
     c->N = N;
     c->E = E;
     c->maxdeg = maxdeg;
+    c->self_loops = false;
+    for (uint32_t v = 0; v < N && !c->self_loops; ++v)
+        for (uint32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) c->self_loops = c->self_loops || col[e] == v;
     c->hx.assign(x_dm, x_dm + N);
     c->hy.assign(y_dm, y_dm + N);
     c->kappa = (uint32_t)((360ull << 16) / vmax);
@@ -1021,6 +1025,7 @@ int gmp_share_graph(gmp_ctx* c, gmp_ctx* owner, int own_state) {
     c->N = owner->N;
     c->E = owner->E;
     c->maxdeg = owner->maxdeg;
+    c->self_loops = owner->self_loops;
     c->kappa = owner->kappa;
     c->h_delta = owner->h_delta;
     c->max_phases = owner->max_phases;
@@ -1212,10 +1217,12 @@ uint32_t branch_count(const gmp_ctx* c, uint32_t n) {
 // some colony of the job has non-integer exponents.
 // The hand-off move count of a job run with kernel configuration kc, or 0 where it does not apply: it
 // needs the iterative job, groups that do not step in lockstep, visited sets in shared memory (the tail
-// kernel copies them whole) and rows of at most eight roads (the pipelined walk's sub-groups).
+// kernel copies them whole), rows of at most eight roads (the pipelined walk's sub-groups) and no road
+// from a node to itself (the pipelined walk scores a candidate's row before the candidate is marked
+// visited, so such a road would count as a way on; no walk ever takes one).
 uint32_t handoff_of(const gmp_ctx* c, const KernelConfig& kc) {
     if (!c->prm.handoff_moves || c->prm.mode == GMP_MODE_PERSISTENT || kc.lockstep || kc.lanes < 4 ||
-        !kc.tabu_in_smem || c->maxdeg > 8u)
+        !kc.tabu_in_smem || c->maxdeg > 8u || c->self_loops)
         return 0;
     return c->prm.handoff_moves;
 }

@@ -378,6 +378,36 @@ def test_directed_graph_with_sinks(gm, ctx, orc, sched):
     assert backs > 0  # ants stepped back out of sinks and dead ends
 
 
+@pytest.mark.parametrize("sched", ["handoff", "lanes8", "lanes4", "persistent"])
+def test_roads_from_a_node_to_itself(gm, ctx, orc, sched):
+    """A road that leads from a node back to itself is never a way on (the node is visited once the ant
+    stands on it). Every kernel shape, the hand-off schedule included, agrees with the oracle on a graph
+    where a third of the nodes carry such a road."""
+    rng = np.random.default_rng(23)
+    roads = []
+    for u in range(48):
+        for v in ((u + 1) % 48, (u + 7) % 48):
+            L = int(rng.integers(300, 3000))
+            roads += [(u, v, L, 50, 3, 0), (v, u, L, 50, 3, 1)]
+    for u in range(0, 48, 3):
+        roads.append((u, u, int(rng.integers(100, 400)), 50, 3, 0))
+    sigs = {v: (30_000, int(rng.integers(0, 30_000)), [18_000, 12_000]) for v in range(0, 48, 5)}
+    net, sig, veh = NB.build(48, roads, signals=sigs, bidirectional=False)
+    veh[:] = rng.integers(0, 20, size=veh.size)
+    assert int(np.diff(net.row_ptr).max()) <= 8
+    ctx.load_graph(net)
+    ctx.set_signals(sig)
+    ctx.set_densities(veh)
+    kw = {"handoff": dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3),
+          "persistent": dict(mode=2, lanes_per_ant=8)}.get(sched, dict(mode=1, lanes_per_ant=int(sched[5:])))
+    ctx.set_params(**kw)
+    qs = [Q(s, d, 40, 6, 1.0, 2.0, 0.1, 300 + i) for i, (s, d) in enumerate([(0, 47), (3, 30), (9, 21)])]
+    res = ctx.solve_batch(qs)
+    onet = orc.Net(net, sig, veh)
+    for i, q in enumerate(qs):
+        _compare(orc, onet, orc.Params(), q, res[i], ctx, i)
+
+
 def test_sparse_layout_refusals(gm, ctx):
     ctx.load_workload(W.grid10())
     q = W.grid10().queries[0]
