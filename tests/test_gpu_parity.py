@@ -398,8 +398,12 @@ def test_roads_from_a_node_to_itself(gm, ctx, orc, sched):
     ctx.load_graph(net)
     ctx.set_signals(sig)
     ctx.set_densities(veh)
-    kw = {"handoff": dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3),
-          "persistent": dict(mode=2, lanes_per_ant=8)}.get(sched, dict(mode=1, lanes_per_ant=int(sched[5:])))
+    if sched == "handoff":
+        kw = dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3)
+    elif sched == "persistent":
+        kw = dict(mode=2, lanes_per_ant=8)
+    else:
+        kw = dict(mode=1, lanes_per_ant=int(sched[5:]))
     ctx.set_params(**kw)
     qs = [Q(s, d, 40, 6, 1.0, 2.0, 0.1, 300 + i) for i, (s, d) in enumerate([(0, 47), (3, 30), (9, 21)])]
     res = ctx.solve_batch(qs)
