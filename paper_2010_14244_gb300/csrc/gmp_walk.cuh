@@ -382,7 +382,9 @@ __device__ __forceinline__ bool queue_node_small(uint32_t v, const QueueTables& 
 }
 
 // Marks node v visited in the bitmap of a walk whose lanes all call this with the same v: every lane
-// reads the word and writes it back with the bit set, so the lanes write one value to one address.
+// reads the word and writes it back with the bit set, so the lanes write one value to one address, and
+// whichever order their reads and writes take, the word ends with the bit set and every other bit as it
+// was (no other walk writes this bitmap; the group's next reads follow a __syncwarp).
 // Measured against an atomicOr by every lane (same-address atomics serialise): groups of four lanes in
 // lockstep with bitmaps in global memory, 64 colonies of the 100k-node graph x 20 iterations, 106 ->
 // 91 ms; the pipelined walk, 2 % less. Groups that do not step in lockstep keep the atomic: with bitmaps in global memory
