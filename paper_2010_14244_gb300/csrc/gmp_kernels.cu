@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(128) k_construct(ConstructArgs a, uint32_t it)
         }
         const DevQuery q = a.queries[lo];
         if (!q.active || it >= q.n_iter) continue;
-        walk_ant<G, K, SMEM>(a, q, lo, tg - q.ant_base, it, tabu, lane, gmask, gbase);  // hand-off: shared bitmaps
+        walk_ant<G, K, SMEM, SMEM>(a, q, lo, tg - q.ant_base, it, tabu, lane, gmask, gbase);  // hand-off: shared bitmaps
     }
 }
 

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128) k_persistent(PersistentArgs p) {
             // first ant by rank, further ants from the iteration's counter (groups that finish early
             // take the ants left over when the colony has more ants than groups)
             for (uint32_t k = j; k < q.n_ants;) {
-                walk_ant<G, K, false>(a, q, qi, k, it, tabu, lane, gmask, gbase);
+                walk_ant<G, K, false, SMEM>(a, q, qi, k, it, tabu, lane, gmask, gbase);
                 __threadfence();  // this ant's route, records and deposits before it counts as done
                 __syncwarp(gmask);
                 uint32_t d = 0;

@@ -463,7 +463,7 @@ __device__ __forceinline__ void forget_visited(const ConstructArgs& a, uint32_t*
 // it leaves stays visited and is noted at the back of the route buffer).
 // Groups take ants from a per-iteration ticket counter, so short walks free lanes for waiting ants.
 // ------------------------------------------------------------------------------------------------
-template <int G, int K, bool HANDOFF>
+template <int G, int K, bool HANDOFF, bool SMEM_TABU>
 __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery& q, uint32_t qi, uint32_t k,
                                          uint32_t it, uint32_t* tabu, uint32_t lane, uint32_t gmask, uint32_t gbase) {
     constexpr int NC = G * K;              // candidate slots of the group
@@ -687,7 +687,8 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
         // (measured faster than a store by one lane, for bitmaps in shared and in global memory alike)
         route[len] = e;
         rwait[len] = c_w;
-        atomicOr(tabu + (u >> 5), 1u << (u & 31));
+        if constexpr (SMEM_TABU) mark_visited(tabu, u);  // a bitmap in global memory keeps the atomic
+        else atomicOr(tabu + (u >> 5), 1u << (u & 31));
         ++len;
         ++steps;
         __syncwarp(gmask);
