@@ -87,9 +87,9 @@ typedef struct {
                                many moves is suspended and finished by a pipelined kernel with one ant per
                                warp (the same walks). Free-running groups hand off from visited sets in
                                shared memory, groups in warp lockstep (integer exponents) from shared or
-                               global memory. Each chain of a job saves at most a bounded number of walks
-                               (256 MiB of visited sets per job); a walk that finds no room goes on where it
-                               is. 0 = off; ignored where it does not apply */
+                               global memory; each lockstep chain of a job saves at most a bounded number
+                               of walks (256 MiB of visited sets per job) and a walk that finds no room goes
+                               on where it is. 0 = off; ignored where it does not apply */
 } gmp_params;
 
 /* Pheromone layouts. Dense: every road's pheromone is evaporated every iteration. Sparse: roads that never

@@ -1213,9 +1213,10 @@ uint32_t branch_count(const gmp_ctx* c, uint32_t n) {
     return std::max<uint32_t>(1u, std::min(n, want));
 }
 
-// Entries of a chain's save pool for suspended walks (of a job with n colonies): the visited sets saved
-// for the tail kernel stay within kTailSaveBytes per job; a walk that finds its chain's pool full goes on
-// in the construction kernel.
+// Entries of a chain's save pool for suspended walks (of a job with n colonies) when its groups step in
+// lockstep: the visited sets saved for the tail kernel stay within kTailSaveBytes per job, and a walk that
+// finds its chain's pool full goes on in the construction kernel. Free-running groups (visited sets in
+// shared memory, so at most a few KB each) have an entry per ant.
 constexpr uint64_t kTailSaveBytes = 256ull << 20;
 uint32_t tail_pool_cap(const gmp_ctx* c, uint32_t n) {
     const uint64_t bytes = (uint64_t)branch_count(c, n) * ((c->N + 31u) / 32u) * 4u;
@@ -1282,7 +1283,9 @@ int for_each_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max
     const uint32_t handoff = handoff_of(c, kc);
     GMP_TRY(f(&b.tickets, (size_t)maxI * branch_count(c, n) * (handoff ? 3u : 1u)));
     if (handoff) {
-        const uint64_t pool = std::min<uint64_t>(total_ants, (uint64_t)branch_count(c, n) * tail_pool_cap(c, n));
+        // groups in lockstep share bounded pools; free-running groups have an entry per ant
+        const uint64_t pool = kc.lockstep ? std::min<uint64_t>(total_ants, (uint64_t)branch_count(c, n) * tail_pool_cap(c, n))
+                                          : total_ants;
         GMP_TRY(f(&b.tail_state, (size_t)pool));
         GMP_TRY(f(&b.tail_tabu, (size_t)pool * words));
     }
@@ -1373,7 +1376,7 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
         r.tabu_off = off;
         if (!r.kc.tabu_in_smem) off += (size_t)r.kc.grid * (r.kc.block / r.kc.lanes) * words;
         r.tail_base = tail_off;
-        r.tail_cap = std::min(r.ants, pool_cap);
+        r.tail_cap = b.kc.lockstep ? std::min(r.ants, pool_cap) : r.ants;
         tail_off += r.tail_cap;
         if (b.handoff) GMP_CUDA(c, construct_tail_config(c->device, c->N, std::max<uint32_t>(r.ants, 1u), &r.kc_tail));
         b.br.push_back(r);

@@ -513,19 +513,19 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             break;
         }
         if (HANDOFF && a.handoff_moves && steps == a.handoff_moves) {  // a long walk: the tail kernel finishes it
+            // free-running groups' chains have a pool entry for every ant (tail_cap >= the chain's ants), so
+            // the walk always finds one here (a check would keep the walk's state live across the hand-off
+            // and cost the kernel registers)
             uint32_t idx = 0;
             if (lane == 0) idx = atomicAdd(a.tail_count + it, 1u);
-            idx = __shfl_sync(gmask, idx, 0, G);
-            if (idx < a.tail_cap) {  // else the pool is full and the walk goes on here
-                const uint32_t pe = a.tail_base + idx;
-                if (lane == 0) a.tail_state[pe] = walk_state(u, beg, end, hu, t, W, steps, len, pops, qi, k);
-                uint32_t* out = a.tail_tabu + (size_t)pe * a.tabu_words;
-                for (uint32_t w = lane; w < a.tabu_words; w += G) out[w] = tabu[w];
-                __syncwarp(gmask);  // the copy is complete before the bits are cleared for the group's next ant
-                forget_visited(a, tabu, route, q.src, len, pops, steps, lane, G);
-                __syncwarp(gmask);
-                return;
-            }
+            const uint32_t pe = a.tail_base + __shfl_sync(gmask, idx, 0, G);
+            if (lane == 0) a.tail_state[pe] = walk_state(u, beg, end, hu, t, W, steps, len, pops, qi, k);
+            uint32_t* out = a.tail_tabu + (size_t)pe * a.tabu_words;
+            for (uint32_t w = lane; w < a.tabu_words; w += G) out[w] = tabu[w];
+            __syncwarp(gmask);  // the copy is complete before the bits are cleared for the group's next ant
+            forget_visited(a, tabu, route, q.src, len, pops, steps, lane, G);
+            __syncwarp(gmask);
+            return;
         }
         const uint32_t deg = end - beg;
         const int nslots = K == 1 ? 1 : (int)((deg + G - 1) / G);  // group-uniform
