@@ -32,7 +32,7 @@ HBM_FALLBACK_GBS = 6772.9
 # capture of the current kernel (one chain's launch of 1024 walks, alone and with cold caches): the graph
 # and the pheromone tables stay in L2, so DRAM carries the cold start only. Set to None when the kernel
 # changes, until it is captured again.
-CONSTRUCT_TRAFFIC_BYTES = 807_936
+CONSTRUCT_TRAFFIC_BYTES = 803_072
 
 
 def parse():

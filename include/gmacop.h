@@ -81,15 +81,11 @@ typedef struct {
                                the job stops and reports GMP_ERR_TIMEOUT; 0 = 2^23 (seconds) */
     uint32_t level_limit;   /* GMP_FLAG_EXACT_H: relaxation levels before the heuristic's pass stops and the
                                job reports GMP_ERR_TIMEOUT; 0 = 4N + 4096 */
-    uint32_t handoff_moves; /* iterative mode with sub-warp groups, on graphs whose nodes have at most 8
-                               out-roads, that have no road from a node to itself and whose visited sets fit
-                               one kernel's shared memory (up to 1.6 M nodes): a walk still going after this
+    uint32_t handoff_moves; /* iterative mode with sub-warp groups that do not step in lockstep, on graphs
+                               whose visited sets fit in shared memory, whose nodes have at most 8 out-roads
+                               and that have no road from a node to itself: a walk still going after this
                                many moves is suspended and finished by a pipelined kernel with one ant per
-                               warp (the same walks). Free-running groups hand off from visited sets in
-                               shared memory, groups in warp lockstep (integer exponents) from shared or
-                               global memory; each lockstep chain of a job saves at most a bounded number
-                               of walks (256 MiB of visited sets per job) and a walk that finds no room goes
-                               on where it is. 0 = off; ignored where it does not apply */
+                               warp (the same walks, sooner); 0 = off; ignored where it does not apply */
 } gmp_params;
 
 /* Pheromone layouts. Dense: every road's pheromone is evaporated every iteration. Sparse: roads that never

@@ -79,8 +79,9 @@ struct Batch {
     DevResult* res = nullptr;
     // hand-off of long walks to the tail kernel (handoff: the move count, 0 = off for this job)
     uint32_t handoff = 0;
-    WalkState* tail_state = nullptr;  // the save pool of suspended walks: each chain's entries in turn
-    uint32_t* tail_tabu = nullptr;    // per pool entry: visited-bitmap words
+    uint32_t* tail_list = nullptr;    // total_ants: suspended walks, per chain from its first ant on
+    WalkState* tail_state = nullptr;  // total_ants
+    uint32_t* tail_tabu = nullptr;    // total_ants * visited-bitmap words
     // persistent job
     bool persistent = false;
     IterCounters* ctr = nullptr;
@@ -104,7 +105,6 @@ struct Batch {
     // iterative job: contiguous colony ranges run as concurrent chains of launches
     struct Branch {
         uint32_t q0, q1, ants, ticket_base, maxI;
-        uint32_t tail_base, tail_cap;  // the chain's entries of the save pool of suspended walks
         KernelConfig kc;
         KernelConfig kc_tail;  // the tail kernel of this chain (hand-off)
         size_t tabu_off;  // words into the global visited-bitmap pool
@@ -388,6 +388,7 @@ void free_batch(gmp_ctx* c) {
     dfree(c, &b.hdist);
     dfree(c, &b.hqueue);
     dfree(c, &b.hstamp);
+    dfree(c, &b.tail_list);
     dfree(c, &b.tail_state);
     dfree(c, &b.tail_tabu);
     b.staged = b.ran = false;
@@ -660,6 +661,7 @@ ConstructArgs construct_args(gmp_ctx* c) {
     a.list_e = b.list_e;
     a.list_tau = b.list_tau;
     a.handoff_moves = b.handoff;
+    a.tail_list = b.tail_list;
     a.tail_state = b.tail_state;
     a.tail_tabu = b.tail_tabu;
     return a;
@@ -738,8 +740,6 @@ int enqueue_job(gmp_ctx* c) {
         if (b.handoff) {  // the tail counters follow the tickets: B * maxI suspended, then B * maxI taken up
             a.tail_count = b.tickets + ((size_t)B + j) * b.maxI;
             a.tail_claim = b.tickets + (2 * (size_t)B + j) * b.maxI;
-            a.tail_base = r.tail_base;
-            a.tail_cap = r.tail_cap;
         }
         if (b.sparse) {
             a.tflag = b.tflag + (size_t)r.q0 * a.tflag_words;
@@ -1213,29 +1213,17 @@ uint32_t branch_count(const gmp_ctx* c, uint32_t n) {
     return std::max<uint32_t>(1u, std::min(n, want));
 }
 
-// Entries of a chain's save pool for suspended walks (of a job with n colonies) when its groups step in
-// lockstep: the visited sets saved for the tail kernel stay within kTailSaveBytes per job, and a walk that
-// finds its chain's pool full goes on in the construction kernel. Free-running groups (visited sets in
-// shared memory, so at most a few KB each) have an entry per ant.
-constexpr uint64_t kTailSaveBytes = 256ull << 20;
-uint32_t tail_pool_cap(const gmp_ctx* c, uint32_t n) {
-    const uint64_t bytes = (uint64_t)branch_count(c, n) * ((c->N + 31u) / 32u) * 4u;
-    return (uint32_t)std::max<uint64_t>(64, std::min<uint64_t>(kTailSaveBytes / std::max<uint64_t>(bytes, 1), 1u << 30));
-}
-
 // Launch shape of the job for the context's parameters and `total_ants` ants per iteration; `frac` when
 // some colony of the job has non-integer exponents.
 // The hand-off move count of a job run with kernel configuration kc, or 0 where it does not apply: it
-// needs the iterative job with sub-warp groups, rows of at most eight roads (the pipelined walk's
-// sub-groups), no road from a node to itself (the pipelined walk scores a candidate's row before the
-// candidate is marked visited, so such a road would count as a way on; no walk ever takes one) and a
-// visited set that fits the tail kernel's shared memory. Groups in lockstep hand off with integer
-// exponents, from visited sets in shared or global memory; free-running groups from shared memory.
+// needs the iterative job, groups that do not step in lockstep, visited sets in shared memory (the tail
+// kernel copies them whole), rows of at most eight roads (the pipelined walk's sub-groups) and no road
+// from a node to itself (the pipelined walk scores a candidate's row before the candidate is marked
+// visited, so such a road would count as a way on; no walk ever takes one).
 uint32_t handoff_of(const gmp_ctx* c, const KernelConfig& kc) {
-    if (!c->prm.handoff_moves || c->prm.mode == GMP_MODE_PERSISTENT || kc.lanes < 4 || c->maxdeg > 8u ||
-        c->self_loops || !construct_tail_fits(c->N))
+    if (!c->prm.handoff_moves || c->prm.mode == GMP_MODE_PERSISTENT || kc.lockstep || kc.lanes < 4 ||
+        !kc.tabu_in_smem || c->maxdeg > 8u || c->self_loops)
         return 0;
-    if (kc.lockstep ? kc.frac : !kc.tabu_in_smem) return 0;
     return c->prm.handoff_moves;
 }
 
@@ -1246,8 +1234,7 @@ int job_config(gmp_ctx* c, int lanes, uint64_t total_ants, KernelConfig* kc, boo
         if (lanes == 1) return fail(c, GMP_ERR_UNSUPPORTED, "the persistent job needs 4, 8, 16 or 32 lanes per ant");
         GMP_CUDA(c, persistent_config(c->device, lanes, c->N, c->maxdeg, kc));
     } else if (lanes != 1 && !(c->prm.flags & kFlagNoLockstep) && lockstep_fits(lanes, c->maxdeg)) {
-        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, ants, frac,
-                                              c->prm.handoff_moves != 0, kc));
+        GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, ants, frac, kc));
     } else {
         GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, ants, kc));
     }
@@ -1283,11 +1270,9 @@ int for_each_workspace(gmp_ctx* c, uint32_t n, uint64_t total_ants, uint32_t max
     const uint32_t handoff = handoff_of(c, kc);
     GMP_TRY(f(&b.tickets, (size_t)maxI * branch_count(c, n) * (handoff ? 3u : 1u)));
     if (handoff) {
-        // groups in lockstep share bounded pools; free-running groups have an entry per ant
-        const uint64_t pool = kc.lockstep ? std::min<uint64_t>(total_ants, (uint64_t)branch_count(c, n) * tail_pool_cap(c, n))
-                                          : total_ants;
-        GMP_TRY(f(&b.tail_state, (size_t)pool));
-        GMP_TRY(f(&b.tail_tabu, (size_t)pool * words));
+        GMP_TRY(f(&b.tail_list, (size_t)total_ants));
+        GMP_TRY(f(&b.tail_state, (size_t)total_ants));
+        GMP_TRY(f(&b.tail_tabu, (size_t)total_ants * words));
     }
     GMP_TRY(f(&b.res, n));
     if (persistent) {
@@ -1355,9 +1340,7 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
     }
     const uint32_t B = branch_count(c, b.Q);
     const size_t words = (c->N + 31u) / 32u;
-    const uint32_t pool_cap = tail_pool_cap(c, b.Q);
     size_t off = 0;
-    uint32_t tail_off = 0;
     for (uint32_t j = 0; j < B; ++j) {
         Batch::Branch r{};
         r.q0 = (uint32_t)((uint64_t)b.Q * j / B);
@@ -1375,9 +1358,6 @@ int plan_branches(gmp_ctx* c, int lanes, const std::vector<uint32_t>& prefix) {
         }
         r.tabu_off = off;
         if (!r.kc.tabu_in_smem) off += (size_t)r.kc.grid * (r.kc.block / r.kc.lanes) * words;
-        r.tail_base = tail_off;
-        r.tail_cap = b.kc.lockstep ? std::min(r.ants, pool_cap) : r.ants;
-        tail_off += r.tail_cap;
         if (b.handoff) GMP_CUDA(c, construct_tail_config(c->device, c->N, std::max<uint32_t>(r.ants, 1u), &r.kc_tail));
         b.br.push_back(r);
     }
@@ -2021,7 +2001,7 @@ extern "C" int gmp_solve_static(gmp_ctx* c, uint32_t src, uint32_t dst, uint32_t
     KernelConfig kc{};
     if (!(c->prm.flags & kFlagNoLockstep) && lockstep_fits(lanes, c->maxdeg))
         GMP_CUDA(c, construct_config_lockstep(c->device, lanes, c->N, c->maxdeg, n_ants,
-                                              floorf(alpha) != alpha || floorf(beta) != beta, false, &kc));
+                                              floorf(alpha) != alpha || floorf(beta) != beta, &kc));
     else
         GMP_CUDA(c, construct_config(c->device, lanes, c->N, c->maxdeg, n_ants, &kc));
     // carve the scratch array

@@ -78,16 +78,14 @@ struct ConstructArgs {
     uint32_t* tflag;             // Q * tflag_words
     uint32_t* list_e;            // Q * E registered roads
     uint64_t* list_tau;          // Q * E their tau
-    // hand-off of long walks: a walk still going after handoff_moves moves is suspended into an entry of
-    // this launch range's save pool, while the pool has one free; the tail kernel finishes it with one ant
-    // per warp (0: off)
+    // hand-off of long walks (shared-memory visited sets only): a walk still going after handoff_moves
+    // moves is suspended; the tail kernel finishes it with one ant per warp (0: off)
     uint32_t handoff_moves;
-    uint32_t* tail_count;        // per iteration: walks that asked for a pool entry (this range's counters)
+    uint32_t* tail_count;        // per iteration: walks suspended (this launch range's counters)
     uint32_t* tail_claim;        // per iteration: suspended walks taken up by the tail kernel
-    uint32_t tail_base;          // this range's pool: entries [tail_base, tail_base + tail_cap) of the job's
-    uint32_t tail_cap;
-    WalkState* tail_state;       // per pool entry: where the walk stands
-    uint32_t* tail_tabu;         // per pool entry: tabu_words of its visited set
+    uint32_t* tail_list;         // suspended walks' ant slots, from ticket_base on
+    WalkState* tail_state;       // per ant slot of the job
+    uint32_t* tail_tabu;         // per ant slot of the job: tabu_words of its visited set
 };
 
 // Arguments of the fused iteration-end kernel (evaporation + deposits, best route, queue update).
@@ -199,8 +197,7 @@ cudaError_t launch_persistent(cudaStream_t s, const KernelConfig& kc, const Pers
 cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t max_degree, uint32_t total_ants,
                              KernelConfig* out);
 cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, uint32_t max_degree,
-                                      uint32_t total_ants, bool frac, bool handoff, KernelConfig* out);
-bool construct_tail_fits(uint32_t n_nodes);  // the tail kernel holds one visited set in shared memory
+                                      uint32_t total_ants, bool frac, KernelConfig* out);
 int construct_max_degree(int lanes);
 bool construct_thread_fits(uint32_t n_nodes);
 

@@ -377,14 +377,15 @@ __global__ void __launch_bounds__(128) k_construct_tail(ConstructArgs a, uint32_
     constexpr uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t* tabu = smem + (size_t)(threadIdx.x >> 5) * a.tabu_words;
-    const uint32_t n = min(a.tail_count[it], a.tail_cap);  // final: the construction launch wrote it
+    const uint32_t n = a.tail_count[it];  // final: the construction launch before this one wrote it
     for (;;) {
         uint32_t i = 0;
         if (lane == 0) i = atomicAdd(a.tail_claim + it, 1u);
         i = __shfl_sync(FULL, i, 0);
         if (i >= n) break;
-        const WalkState ws = a.tail_state[a.tail_base + i];
-        const uint32_t* in = a.tail_tabu + (size_t)(a.tail_base + i) * a.tabu_words;
+        const uint32_t slot = a.tail_list[a.ticket_base + i];
+        const WalkState ws = a.tail_state[slot];
+        const uint32_t* in = a.tail_tabu + (size_t)slot * a.tabu_words;
         for (uint32_t w = lane; w < a.tabu_words; w += 32u) tabu[w] = in[w];
         __syncwarp();
         const DevQuery q = a.queries[ws.qi];
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(128) k_construct_tail(ConstructArgs a, uint32_
 // come from one warp-aggregated atomic per round. The loads of an ant's next row are issued as soon as
 // it moves, so their latency overlaps the end of the step and the loop's bookkeeping.
 // ------------------------------------------------------------------------------------------------
-template <int G, int K, bool SMEM, bool FRAC, bool HANDOFF>
+template <int G, int K, bool SMEM, bool FRAC>
 __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t it) {
     extern __shared__ uint32_t smem[];
     constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -504,29 +505,6 @@ __global__ void __launch_bounds__(128) k_construct_gl(ConstructArgs a, uint32_t 
         } else if (active && steps == a.max_steps) {
             done = true;
             status = kAntStepCap;
-        }
-        if (HANDOFF && a.handoff_moves) {  // a long walk moves to the tail kernel while its chain's pool has room
-            const bool ask = active && !done && steps == a.handoff_moves;
-            if (__any_sync(FULL, ask)) {
-                uint32_t idx = 0;
-                if (ask && leader) idx = atomicAdd(a.tail_count + it, 1u);
-                idx = __shfl_sync(FULL, idx, 0, G);
-                const bool suspend = ask && idx < a.tail_cap;
-                if (suspend) {
-                    const uint32_t pe = a.tail_base + idx;
-                    if (leader) a.tail_state[pe] = walk_state(u, beg, end, hu, t, W, steps, len, pops, qi, k);
-                    uint32_t* out = a.tail_tabu + (size_t)pe * a.tabu_words;
-                    for (uint32_t w = lane; w < a.tabu_words; w += G) out[w] = tabu[w];
-                }
-                __syncwarp();  // the copy is complete before the bits are cleared for the group's next ant
-                if (suspend) {
-                    forget_visited(a, tabu, route, src, len, pops, steps, lane, G);
-                    active = false;
-                    pre = false;
-                }
-                __syncwarp();
-                want = want || __any_sync(FULL, suspend);
-            }
         }
         const bool stepping = active && !done;
         const uint32_t deg = stepping ? end - beg : 0u;
@@ -1315,37 +1293,33 @@ cudaError_t construct_config(int device, int lanes, uint32_t n_nodes, uint32_t m
     return cudaErrorInvalidValue;
 }
 
-// The lockstep kernel's instance for bitmaps in shared memory or not, non-integer exponents or not, and
-// hand-off of long walks or not (hand-off is built for integer exponents).
-template <int G, int K, bool SMEM>
-static const void* gl_kernel(bool frac, bool handoff) {
-    if (frac) return (const void*)k_construct_gl<G, K, SMEM, true, false>;
-    if (handoff) return (const void*)k_construct_gl<G, K, SMEM, false, true>;
-    return (const void*)k_construct_gl<G, K, SMEM, false, false>;
-}
-
 template <int G, int K>
-static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, bool frac, bool handoff,
-                             KernelConfig* out) {
+static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, bool frac, KernelConfig* out) {
     const int block = 128;
     const int groups = block / G;
     const uint32_t words = (n_nodes + 31u) / 32u;
     const size_t smem = (size_t)groups * words * 4u;
     const bool in_smem = smem <= 64u * 1024u;
     const size_t dyn = in_smem ? smem : 0;
-    cudaError_t err = cudaSuccess;
+    cudaError_t err;
     int per_sm = 0, sms = 0;
     if (in_smem) {
         if (dyn > 48u * 1024u) {
             // per kernel function, shared by every context: the cap of in-smem bitmaps, not this size
-            for (int v = 0; v < 3 && err == cudaSuccess; ++v)
-                err = cudaFuncSetAttribute(gl_kernel<G, K, true>(v == 1, v == 2),
+            err = cudaFuncSetAttribute(k_construct_gl<G, K, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       64 * 1024);
+            if (err == cudaSuccess)
+                err = cudaFuncSetAttribute(k_construct_gl<G, K, true, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
             if (err != cudaSuccess) return err;
         }
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gl_kernel<G, K, true>(frac, handoff), block, dyn);
+        err = frac ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true, true>, block, dyn)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, true, false>, block,
+                                                                   dyn);
     } else {
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gl_kernel<G, K, false>(frac, handoff), block, 0);
+        err = frac ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, false, true>, block, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_construct_gl<G, K, false, false>, block,
+                                                                   0);
     }
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -1366,39 +1340,30 @@ static cudaError_t config_gl(int device, uint32_t n_nodes, uint32_t total_ants, 
 }
 
 cudaError_t construct_config_lockstep(int device, int lanes, uint32_t n_nodes, uint32_t max_degree,
-                                      uint32_t total_ants, bool frac, bool handoff, KernelConfig* out) {
+                                      uint32_t total_ants, bool frac, KernelConfig* out) {
     const int k = (uint32_t)lanes >= max_degree ? 1 : ((uint32_t)(2 * lanes) >= max_degree ? 2 : 0);
-    handoff = handoff && !frac;
-    if (lanes == 4 && k == 1) return config_gl<4, 1>(device, n_nodes, total_ants, frac, handoff, out);
-    if (lanes == 4 && k == 2) return config_gl<4, 2>(device, n_nodes, total_ants, frac, handoff, out);
-    if (lanes == 8 && k == 1) return config_gl<8, 1>(device, n_nodes, total_ants, frac, handoff, out);
-    if (lanes == 8 && k == 2) return config_gl<8, 2>(device, n_nodes, total_ants, frac, handoff, out);
-    if (lanes == 16 && k == 1) return config_gl<16, 1>(device, n_nodes, total_ants, frac, handoff, out);
+    if (lanes == 4 && k == 1) return config_gl<4, 1>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 4 && k == 2) return config_gl<4, 2>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 8 && k == 1) return config_gl<8, 1>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 8 && k == 2) return config_gl<8, 2>(device, n_nodes, total_ants, frac, out);
+    if (lanes == 16 && k == 1) return config_gl<16, 1>(device, n_nodes, total_ants, frac, out);
     return cudaErrorInvalidValue;
 }
 
-// The tail kernel keeps each warp's visited set in shared memory: up to four warps per block, as many as
-// kTailSmem holds.
-constexpr size_t kTailSmem = 200u * 1024u;
-bool construct_tail_fits(uint32_t n_nodes) { return (size_t)((n_nodes + 31u) / 32u) * 4u <= kTailSmem; }
-
 cudaError_t construct_tail_config(int device, uint32_t n_nodes, uint32_t total_ants, KernelConfig* out) {
     KernelConfig kc{};
-    const size_t per_warp = (size_t)((n_nodes + 31u) / 32u) * 4u;
-    if (per_warp > kTailSmem) return cudaErrorInvalidValue;
-    const int warps_per_block = (int)std::max<size_t>(1, std::min<size_t>(4, kTailSmem / std::max<size_t>(per_warp, 1)));
     kc.lanes = 32;
     kc.slots = 1;
-    kc.block = 32 * warps_per_block;
+    kc.block = 128;
     kc.tabu_in_smem = true;
-    kc.smem = (size_t)warps_per_block * per_warp;
+    kc.smem = (size_t)(kc.block / 32) * ((n_nodes + 31u) / 32u) * 4u;
     cudaError_t err = cudaSuccess;
     if (kc.smem > 48u * 1024u)
-        err = cudaFuncSetAttribute(k_construct_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+        err = cudaFuncSetAttribute(k_construct_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kc.smem);
     if (err != cudaSuccess) return err;
     // suspended walks are a few of the launch's ants: a modest grid whose warps loop over them
     const uint32_t warps = total_ants < 256u ? total_ants : 256u;
-    kc.grid = (int)((warps + warps_per_block - 1) / warps_per_block);
+    kc.grid = (int)((warps + 3u) / 4u);
     if (kc.grid < 1) kc.grid = 1;
     (void)device;
     *out = kc;
@@ -1412,19 +1377,16 @@ cudaError_t launch_construct_tail(cudaStream_t s, const KernelConfig& kc, const 
 
 cudaError_t launch_construct(cudaStream_t s, const KernelConfig& kc, const ConstructArgs& a, uint32_t it) {
     if (kc.lockstep) {
-#define GMP_LAUNCH_GL(G_, K_)                                                                                  \
-    if (kc.lanes == G_ && kc.slots == K_) {                                                                    \
-        if (kc.frac) {                                                                                         \
-            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, true, false><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
-            else k_construct_gl<G_, K_, false, true, false><<<kc.grid, kc.block, 0, s>>>(a, it);              \
-        } else if (a.handoff_moves) {                                                                          \
-            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, false, true><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
-            else k_construct_gl<G_, K_, false, false, true><<<kc.grid, kc.block, 0, s>>>(a, it);              \
-        } else {                                                                                               \
-            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, false, false><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
-            else k_construct_gl<G_, K_, false, false, false><<<kc.grid, kc.block, 0, s>>>(a, it);             \
-        }                                                                                                      \
-        return cudaGetLastError();                                                                             \
+#define GMP_LAUNCH_GL(G_, K_)                                                                            \
+    if (kc.lanes == G_ && kc.slots == K_) {                                                              \
+        if (kc.frac) {                                                                                   \
+            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, true><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
+            else k_construct_gl<G_, K_, false, true><<<kc.grid, kc.block, 0, s>>>(a, it);               \
+        } else {                                                                                         \
+            if (kc.tabu_in_smem) k_construct_gl<G_, K_, true, false><<<kc.grid, kc.block, kc.smem, s>>>(a, it); \
+            else k_construct_gl<G_, K_, false, false><<<kc.grid, kc.block, 0, s>>>(a, it);              \
+        }                                                                                                \
+        return cudaGetLastError();                                                                       \
     }
         GMP_LAUNCH_GL(4, 1) GMP_LAUNCH_GL(4, 2) GMP_LAUNCH_GL(8, 1) GMP_LAUNCH_GL(8, 2) GMP_LAUNCH_GL(16, 1)
 #undef GMP_LAUNCH_GL

@@ -32,7 +32,6 @@ using Bucket = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
 
 constexpr float kMargin = 0.03f;  // relative speed-up a schedule needs over the best so far
 constexpr uint32_t kHandoffMoves = 512;  // hand-off candidates: walks longer than this go to the tail kernel
-constexpr uint32_t kHandoffLockstep = 2048;  // the same for groups in lockstep (many more walks pass 512 there)
 
 std::mutex g_mu;
 std::map<Bucket, Schedule> g_cache;
@@ -69,8 +68,6 @@ std::vector<Schedule> candidates(uint32_t n_nodes, uint32_t maxdeg) {
         add({g, GMP_MODE_ITERATIVE, 0, 0, 0, 0});
         if (lockstep_fits((int)g, maxdeg)) add({g, GMP_MODE_ITERATIVE, 0, 1, 0, 0});
         if (g < 32u && maxdeg <= 8u) add({g, GMP_MODE_ITERATIVE, 0, 1, 0, kHandoffMoves});
-        if (lockstep_fits((int)g, maxdeg) && maxdeg <= 8u && construct_tail_fits(n_nodes))
-            add({g, GMP_MODE_ITERATIVE, 0, 0, 0, kHandoffLockstep});
         for (uint32_t ch : {8u, 16u, 32u, 64u}) add({g, GMP_MODE_PERSISTENT, ch, 0, 0, 0});
     }
     return out;
@@ -184,7 +181,7 @@ int gmp_autotune(gmp_ctx* c, uint32_t n, const gmp_query* probe, uint32_t probe_
         }
         if (best.handoff) {  // then the hand-off move count
             const Schedule b1 = best;
-            for (uint32_t m : {b1.handoff / 2u, b1.handoff * 4u}) {  // 512: 256 and 2048
+            for (uint32_t m : {256u, 2048u}) {
                 Schedule v = b1;
                 v.handoff = m;
                 try_schedule(v, false);

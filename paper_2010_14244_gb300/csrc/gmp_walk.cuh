@@ -454,26 +454,6 @@ __device__ __forceinline__ void forget_visited(const ConstructArgs& a, uint32_t*
     }
 }
 
-// A suspended walk's state, for the tail kernel.
-__device__ __forceinline__ WalkState walk_state(uint32_t u, uint32_t beg, uint32_t end, uint32_t hu, uint32_t t,
-                                                uint32_t W, uint32_t steps, uint32_t len, uint32_t pops, uint32_t qi,
-                                                uint32_t k) {
-    WalkState ws;
-    ws.u = u;
-    ws.beg = beg;
-    ws.end = end;
-    ws.hu = hu;
-    ws.t = t;
-    ws.W = W;
-    ws.steps = steps;
-    ws.len = len;
-    ws.pops = pops;
-    ws.qi = qi;
-    ws.k = k;
-    ws.pad = 0;
-    return ws;
-}
-
 // ------------------------------------------------------------------------------------------------
 // Ant construction. G lanes of a warp serve one ant (sub-warp group); lane l holds the candidates
 // l, l+G, ..., l+(K-1)G of the current node's CSR row. Per step: one round of independent 16-byte
@@ -513,14 +493,25 @@ __device__ __forceinline__ void walk_ant(const ConstructArgs& a, const DevQuery&
             break;
         }
         if (HANDOFF && a.handoff_moves && steps == a.handoff_moves) {  // a long walk: the tail kernel finishes it
-            // free-running groups' chains have a pool entry for every ant (tail_cap >= the chain's ants), so
-            // the walk always finds one here (a check would keep the walk's state live across the hand-off
-            // and cost the kernel registers)
-            uint32_t idx = 0;
-            if (lane == 0) idx = atomicAdd(a.tail_count + it, 1u);
-            const uint32_t pe = a.tail_base + __shfl_sync(gmask, idx, 0, G);
-            if (lane == 0) a.tail_state[pe] = walk_state(u, beg, end, hu, t, W, steps, len, pops, qi, k);
-            uint32_t* out = a.tail_tabu + (size_t)pe * a.tabu_words;
+            if (lane == 0) {
+                const uint32_t idx = atomicAdd(a.tail_count + it, 1u);
+                a.tail_list[a.ticket_base + idx] = slot;
+                WalkState ws;
+                ws.u = u;
+                ws.beg = beg;
+                ws.end = end;
+                ws.hu = hu;
+                ws.t = t;
+                ws.W = W;
+                ws.steps = steps;
+                ws.len = len;
+                ws.pops = pops;
+                ws.qi = qi;
+                ws.k = k;
+                ws.pad = 0;
+                a.tail_state[slot] = ws;
+            }
+            uint32_t* out = a.tail_tabu + (size_t)slot * a.tabu_words;
             for (uint32_t w = lane; w < a.tabu_words; w += G) out[w] = tabu[w];
             __syncwarp(gmask);  // the copy is complete before the bits are cleared for the group's next ant
             forget_visited(a, tabu, route, q.src, len, pops, steps, lane, G);

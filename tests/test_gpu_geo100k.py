@@ -24,50 +24,38 @@ def gm():
 
 N_COLONIES = 512
 
-# the default schedule (groups of 4 lanes in warp lockstep), and the same groups handing walks longer than
-# 2048 moves (the tuner's candidate) or 64 moves (most walks: the chains' save pools overflow and the walks
-# that find no entry go on in the construction kernel) to the tail kernel
-SCHEDULES = {"default": {}, "handoff_2048": dict(mode=1, lanes_per_ant=4, handoff_moves=2048),
-             "handoff_64": dict(mode=1, lanes_per_ant=4, handoff_moves=64)}
 
-
-@pytest.fixture(scope="module")
-def geo_oracle():
-    """The oracle's solves of all 512 colonies, in spawned processes over the host cores."""
+def test_geo100k_full_size_full_parity(gm):
+    # the workers build the workload while this process builds its own and runs the job
     pool, pending = oracle_pool.start("geo100k", range(N_COLONIES))
     try:
-        out = pending.get(timeout=3000)
+        wl = W.geo100k()
+        assert len(wl.queries) == N_COLONIES
+        ctx = gm.Context(0)
+        try:
+            ctx.load_workload(wl)
+            res = ctx.solve_batch(wl.queries)
+            digests = [oracle_pool.tau_digest(ctx.pheromone(i)) for i in range(len(wl.queries))]
+        finally:
+            ctx.close()
+        net = wl.net
+        for q, r in zip(wl.queries, res):
+            assert r["ant_steps"] > 0 and r["status"] in (0, gm.ERR_NO_ROUTE)
+            if r["status"] != 0:
+                continue
+            route = r["route"]
+            assert route[0] == q.src and route[-1] == q.dst and len(set(route.tolist())) == len(route)
+            for a, b in zip(route[:-1], route[1:]):
+                row = net.col[net.row_ptr[a]:net.row_ptr[a + 1]]
+                assert b in row
+        oracle = pending.get(timeout=3000)
     finally:
         pool.close()
         pool.join()
-    assert [qi for qi, _ in out] == list(range(N_COLONIES))
-    return out
-
-
-@pytest.mark.parametrize("sched", list(SCHEDULES))
-def test_geo100k_full_size_full_parity(gm, geo_oracle, sched):
-    wl = W.geo100k()
-    assert len(wl.queries) == N_COLONIES
-    ctx = gm.Context(0)
-    try:
-        ctx.load_workload(wl)
-        ctx.set_params(**SCHEDULES[sched])
-        res = ctx.solve_batch(wl.queries)
-        digests = [oracle_pool.tau_digest(ctx.pheromone(i)) for i in range(len(wl.queries))]
-    finally:
-        ctx.close()
-    net = wl.net
-    for q, r in zip(wl.queries, res):
-        assert r["ant_steps"] > 0 and r["status"] in (0, gm.ERR_NO_ROUTE)
-        if r["status"] != 0:
-            continue
-        route = r["route"]
-        assert route[0] == q.src and route[-1] == q.dst and len(set(route.tolist())) == len(route)
-        for a, b in zip(route[:-1], route[1:]):
-            row = net.col[net.row_ptr[a]:net.row_ptr[a + 1]]
-            assert b in row
-    for qi, o in geo_oracle:
+    assert [qi for qi, _ in oracle] == list(range(N_COLONIES))
+    for qi, o in oracle:
         oracle_pool.check(res[qi], o)
         assert digests[qi] == o["tau_sha256"], qi
     routed = sum(r["status"] == 0 for r in res)
     assert routed >= 0.9 * N_COLONIES, routed
+    assert sum(r["n_success"] for r in res) >= 0.5 * sum(q.n_ants * q.n_iter for q in wl.queries)

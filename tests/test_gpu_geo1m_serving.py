@@ -91,26 +91,3 @@ def test_geo1m_served_sample_matches_oracle(gm):
             assert r[k] == o[k], (tag, k, r[k], o[k])
         np.testing.assert_array_equal(r["route"], o["route"])
     assert sum(r["status"] == 0 for r in done) >= 0.9 * N_REQ
-
-
-def test_geo1m_lockstep_handoff_matches_oracle(gm):
-    """Groups of four lanes in warp lockstep hand walks longer than 64 moves to the tail kernel, whose
-    warps each hold a 1M-node visited set (125 KB) in shared memory: every 64th request at clock 0, solved
-    as one job, equals the oracle's solve of it."""
-    wl = W.geo1m_serving()
-    reqs = _requests(wl.net.n_nodes)
-    sample = list(range(0, N_REQ, EVERY))
-    ctx = gm.Context(0)
-    try:
-        ctx.load_workload(wl)
-        ctx.set_params(mode=1, lanes_per_ant=4, handoff_moves=64)
-        res = ctx.solve_batch([reqs[tag] for tag in sample])
-    finally:
-        ctx.close()
-    with mp.get_context("spawn").Pool(len(sample)) as pool:
-        oracle = pool.map(_oracle_one, [(tag, 0) for tag in sample])
-    for tag, r, o in zip(sample, res, oracle):
-        assert o["status"] == 0, (tag, o["status"])
-        for k in ("status", "travel_ms", "wait_ms", "ant_steps", "n_success"):
-            assert r[k] == o[k], (tag, k, r[k], o[k])
-        np.testing.assert_array_equal(r["route"], o["route"])

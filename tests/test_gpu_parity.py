@@ -39,10 +39,8 @@ FREE = 16  # gmacop.FLAG_NO_LOCKSTEP: sub-warp groups that do not step in lockst
 SCHEDULES = {"chains1": dict(mode=1, branches=1), "chains2": dict(mode=1, branches=2),
              "chains_default": dict(mode=1), "persistent": dict(mode=2),
              "sparse_tau": dict(mode=1, tau_layout=2), "dense_tau": dict(mode=1, tau_layout=1),
-             # walks longer than 3 moves finish in the tail kernel (pipelined, one ant per warp), handed
-             # off by free-running groups or by groups in warp lockstep
-             "handoff": dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3),
-             "handoff_lockstep": dict(mode=1, lanes_per_ant=4, handoff_moves=3)}
+             # walks longer than 3 moves finish in the tail kernel (pipelined, one ant per warp)
+             "handoff": dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3)}
 
 
 def _with_flags(sched, flags):
@@ -380,7 +378,7 @@ def test_directed_graph_with_sinks(gm, ctx, orc, sched):
     assert backs > 0  # ants stepped back out of sinks and dead ends
 
 
-@pytest.mark.parametrize("sched", ["handoff", "handoff_lockstep", "lanes8", "lanes4", "persistent"])
+@pytest.mark.parametrize("sched", ["handoff", "lanes8", "lanes4", "persistent"])
 def test_roads_from_a_node_to_itself(gm, ctx, orc, sched):
     """A road that leads from a node back to itself is never a way on (the node is visited once the ant
     stands on it). Every kernel shape, the hand-off schedule included, agrees with the oracle on a graph
@@ -400,8 +398,8 @@ def test_roads_from_a_node_to_itself(gm, ctx, orc, sched):
     ctx.load_graph(net)
     ctx.set_signals(sig)
     ctx.set_densities(veh)
-    if sched.startswith("handoff"):
-        kw = dict(SCHEDULES[sched])
+    if sched == "handoff":
+        kw = dict(mode=1, lanes_per_ant=8, flags=FREE, handoff_moves=3)
     elif sched == "persistent":
         kw = dict(mode=2, lanes_per_ant=8)
     else:
