@@ -502,3 +502,34 @@ def test_queue_preempt_on_network(orc):
     red[2, 2] = 90_001
     net, sig, veh = NB.build(4, roads, signals=sigs, vehicles={(0, 2): 25, (3, 2): 12}, bidirectional=False)
     assert list(orc.queue_preempt(orc.Net(net, sig, veh, red))[2][:3]) == [2, 0, 1]
+
+
+def test_roads_from_a_node_to_itself_are_never_taken(orc):
+    """A road from a node back to itself is never a way on: the node is visited from the moment the ant
+    stands on it. On a ring-and-chord graph where every third node carries such a road, the best routes are
+    simple paths whose times recompute road by road, and no such road ever receives a deposit: its final
+    pheromone is 1.0 evaporated once per iteration, exactly."""
+    rng = np.random.default_rng(23)
+    roads = []
+    for u in range(48):
+        for v in ((u + 1) % 48, (u + 7) % 48):
+            L = int(rng.integers(300, 3000))
+            roads += [(u, v, L, 50, 3, 0), (v, u, L, 50, 3, 1)]
+    for u in range(0, 48, 3):
+        roads.append((u, u, int(rng.integers(100, 400)), 50, 3, 0))
+    sigs = {v: (30_000, int(rng.integers(0, 30_000)), [18_000, 12_000]) for v in range(0, 48, 5)}
+    net, sig, veh = NB.build(48, roads, signals=sigs, bidirectional=False)
+    veh[:] = rng.integers(0, 20, size=veh.size)
+    onet = orc.Net(net, sig, veh)
+    loops = np.flatnonzero(net.tails() == net.col)
+    assert loops.size == 16
+    for i, (s, d) in enumerate([(0, 47), (3, 30), (9, 21)]):
+        q = Q(s, d, 40, 6, 1.0, 2.0, 0.1, 300 + i)
+        r = orc.solve(onet, orc.Params(), q)
+        assert r["status"] == 0
+        _check_route(orc, net, sig, onet, r, q)
+        rho_fix = round(float(np.float32(q.rho)) * 2**32)  # the query's rho is binary32
+        tau = 1 << 32
+        for _ in range(q.n_iter):
+            tau -= (tau * rho_fix) >> 32
+        assert (np.asarray(r["tau"])[loops] == tau).all()
