@@ -289,6 +289,7 @@ SERVE_1M_SLOTS = 8
 SERVE_1M_SAT_S = 6.0  # window of the saturated 1M-node run: a job there takes a few hundred ms, so a short
                       # window counts too few completions to be steady
 SERVE_ANTS, SERVE_ITERS = 128, 30
+SERVE_TUNE_PROBE = 32  # requests in the probe job that picks the serving slots' schedule
 
 
 def bytes_per_ant_step(n_nodes, n_edges):
@@ -418,10 +419,13 @@ def serving_leg_1m(with_cpu):
     from paper_2010_14244_gb300 import serving, workloads
 
     wl = workloads.geo1m_serving()
+    make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
+    # the slots' schedule: the autotuner's choice on a probe job of 32 requests from the same stream
+    probe = [make(i) for i in range(SERVE_TUNE_PROBE)]
     srv, keep = serving.make_server(wl, n_slots=SERVE_1M_SLOTS, max_batch=128, max_ants=SERVE_ANTS,
-                                    max_iter=SERVE_ITERS)
+                                    max_iter=SERVE_ITERS, tune_probe=probe)
+    schedule = schedule_of(keep[0])
     try:
-        make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
         sat = serving.run_poisson(srv, make, rate_per_s=20000.0, duration_s=SERVE_1M_SAT_S, warmup_s=1.0,
                                   tick_ms=1000, drain_s=0.0).summary()
     finally:
@@ -430,7 +434,7 @@ def serving_leg_1m(with_cpu):
             c.close()
     capacity = sat["served_per_s_in_window"]
     srv, keep = serving.make_server(wl, n_slots=SERVE_1M_SLOTS, max_batch=128, max_ants=SERVE_ANTS,
-                                    max_iter=SERVE_ITERS)
+                                    max_iter=SERVE_ITERS, tune_probe=probe)
     try:
         make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
         rep = serving.run_poisson(srv, make, rate_per_s=max(1.0, 0.7 * capacity), duration_s=SERVE_WINDOW_S,
@@ -442,6 +446,7 @@ def serving_leg_1m(with_cpu):
     out = rep.summary()
     peak, kind = peaks()
     out.update(slots=SERVE_1M_SLOTS, ants=SERVE_ANTS, iterations=SERVE_ITERS, arrivals="poisson, uniform OD",
+               schedule=schedule, schedule_source=f"autotuned on a probe job of {SERVE_TUNE_PROBE} requests",
                network=f"{wl.net.n_nodes} nodes, {wl.net.n_edges} roads, 5M vehicles",
                tick="1 s (queue/preemption update with vehicle discharge)",
                at_20k_offered={k: sat[k] for k in ("offered_req_per_s", "served_per_s_in_window", "submitted",
@@ -459,8 +464,11 @@ def serving_leg(wl):
     128 ants x 30 iterations each, traffic ticks every second, continuous batching over slot contexts."""
     from paper_2010_14244_gb300 import serving
 
+    make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=5)
+    probe = [make(i) for i in range(SERVE_TUNE_PROBE)]  # the slots' schedule: autotuned on a probe job
     srv, slots = serving.make_server(wl, n_slots=SERVE_SLOTS, max_batch=SERVE_MAX_BATCH, max_ants=SERVE_ANTS,
-                                     max_iter=SERVE_ITERS)
+                                     max_iter=SERVE_ITERS, tune_probe=probe)
+    schedule = schedule_of(slots[0])
     try:
         make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=5)
         rep = serving.run_poisson(srv, make, rate_per_s=SERVE_RATE, duration_s=SERVE_WINDOW_S,
@@ -471,8 +479,15 @@ def serving_leg(wl):
             c.close()
     out = rep.summary()
     out.update(slots=SERVE_SLOTS, ants=SERVE_ANTS, iterations=SERVE_ITERS, arrivals="poisson, uniform OD",
+               schedule=schedule, schedule_source=f"autotuned on a probe job of {SERVE_TUNE_PROBE} requests",
                tick="1 s (queue/preemption update with vehicle discharge)")
     return out
+
+
+def schedule_of(ctx):
+    """The schedule a context runs (the parameters the autotuner sets)."""
+    p = ctx.get_params()
+    return {k: p[k] for k in ("mode", "lanes_per_ant", "branches", "handoff_moves", "flags", "tau_layout")}
 
 
 # ------------------------------------------------------------------------------------------ GPU

@@ -17,16 +17,20 @@ from .workloads import Query
 
 
 def make_server(wl, n_slots: int, max_batch: int, max_ants: int, max_iter: int, mem_budget: int = 0,
-                device: int = 0, params: dict | None = None):
+                device: int = 0, params: dict | None = None, tune_probe=None, tune_iter: int = 8):
     """A context holding the workload's road graph and traffic state, and a server of n_slots slots over it
     (the slots share that graph; mem_budget bounds their workspaces together, in bytes). Returns (server,
     [graph context]); the context must be closed after the server. On failure the context is closed
-    before the error propagates."""
+    before the error propagates. With tune_probe (requests shaped like a typical job), the autotuner picks
+    the slots' schedule on that probe, tune_iter iterations, before the server starts; every schedule
+    gives the same results."""
     graph = G.Context(device)
     try:
         graph.load_workload(wl)
         if params:
             graph.set_params(**params)
+        if tune_probe:
+            graph.autotune(list(tune_probe), probe_iter=tune_iter)
         return G.Server(graph, n_slots, max_batch, max_ants, max_iter, mem_budget >> 20), [graph]
     except Exception:
         graph.close()
