@@ -290,6 +290,7 @@ SERVE_1M_SAT_S = 6.0  # window of the saturated 1M-node run: a job there takes a
                       # window counts too few completions to be steady
 SERVE_ANTS, SERVE_ITERS = 128, 30
 SERVE_TUNE_PROBE = 32  # requests in the probe job that picks the serving slots' schedule
+SERVE_1M_TUNE_PROBE = 64
 
 
 def bytes_per_ant_step(n_nodes, n_edges):
@@ -420,8 +421,9 @@ def serving_leg_1m(with_cpu):
 
     wl = workloads.geo1m_serving()
     make = serving.uniform_requests(wl.net.n_nodes, SERVE_ANTS, SERVE_ITERS, seed=9)
-    # the slots' schedule: the autotuner's choice on a probe job of 32 requests from the same stream
-    probe = [make(i) for i in range(SERVE_TUNE_PROBE)]
+    # the slots' schedule: the autotuner's choice on a probe job of 64 requests from the same stream (the
+    # saturated run's jobs are large; a 32-request probe picked a schedule slower on them)
+    probe = [make(i) for i in range(SERVE_1M_TUNE_PROBE)]
     srv, keep = serving.make_server(wl, n_slots=SERVE_1M_SLOTS, max_batch=128, max_ants=SERVE_ANTS,
                                     max_iter=SERVE_ITERS, tune_probe=probe)
     schedule = schedule_of(keep[0])
@@ -446,7 +448,7 @@ def serving_leg_1m(with_cpu):
     out = rep.summary()
     peak, kind = peaks()
     out.update(slots=SERVE_1M_SLOTS, ants=SERVE_ANTS, iterations=SERVE_ITERS, arrivals="poisson, uniform OD",
-               schedule=schedule, schedule_source=f"autotuned on a probe job of {SERVE_TUNE_PROBE} requests",
+               schedule=schedule, schedule_source=f"autotuned on a probe job of {SERVE_1M_TUNE_PROBE} requests",
                network=f"{wl.net.n_nodes} nodes, {wl.net.n_edges} roads, 5M vehicles",
                tick="1 s (queue/preemption update with vehicle discharge)",
                at_20k_offered={k: sat[k] for k in ("offered_req_per_s", "served_per_s_in_window", "submitted",
