@@ -218,6 +218,38 @@ def test_depth_first_walk_closed_forms(orc, gseed):
             assert r["status"] == orc.ERR_NO_ROUTE
 
 
+@pytest.mark.parametrize("gseed", range(4))
+def test_depth_first_walk_ignores_roads_to_themselves(orc, gseed):
+    """The closed forms of the depth-first walk hold unchanged when every third node also has a road back
+    to itself: such a road never becomes a way on, so an ant with no destination in reach still ends back
+    at src after exactly 2(R - 1) moves, and one with a destination in reach still gets there."""
+    rng = np.random.Generator(np.random.PCG64(900 + gseed))
+    n = int(rng.integers(6, 14))
+    base, _ = W.random_small(n, n - 1 + int(rng.integers(0, 3)), rng, signalised_frac=0.5)
+    tails = base.tails()
+    loops = np.arange(0, n, 3)
+    net = W.csr_from_roads(n, np.concatenate([tails, loops]), np.concatenate([base.col, loops]),
+                           np.concatenate([base.length_dm, np.full(loops.size, 300)]),
+                           np.concatenate([base.speed_kmh, np.full(loops.size, 50)]),
+                           np.concatenate([base.lanes, np.full(loops.size, 3)]),
+                           np.concatenate([base.orient, np.zeros(loops.size, base.orient.dtype)]),
+                           base.x_dm, base.y_dm, bidirectional=False)
+    assert int((net.tails() == net.col).sum()) == loops.size
+    sig = W.two_phase_signals(net, rng.random(n) < 0.5, rng)
+    veh = rng.integers(0, 8, net.n_edges).astype(np.uint32)
+    onet = orc.Net(net, sig, veh)
+    R = _reachable(net, 0)
+    for dst in range(1, n):
+        r = orc.solve(onet, orc.Params(), Q(0, dst, 8, 3, 1.0, 2.0, 0.1, gseed), want_tau=False, want_log=True)
+        st, length, moves, _, _ = orc.log_fields(r["log"])
+        if dst in R:
+            assert (st == orc.ANT_SUCCESS).all() and r["status"] == 0
+            route = [int(v) for v in r["route"]]
+            assert len(set(route)) == len(route)
+        else:
+            assert (st == orc.ANT_DEAD_END).all() and (moves == 2 * (len(R) - 1)).all() and (length == 0).all()
+
+
 @pytest.mark.parametrize("gseed", range(6))
 def test_spur_graphs_best_equals_brute_force(orc, gseed):
     """Trees with one or two extra links (many spurs and dead ends), signals at half the nodes: the
