@@ -72,6 +72,8 @@ MUTANTS = [
     ("wait_at_destination", "if (v != q->dst && g->n_phases[v] > 0) {", "if (g->n_phases[v] > 0) {", [SOLVE]),
     ("time_without_wait", "t += (uint64_t)S->tt[e] + S->waitv[pick];", "t += (uint64_t)S->tt[e];", [SOLVE]),
     ("no_visited_rule", "if (!S->visited[g->col[e]])", "if (1)", [SOLVE]),
+    ("road_to_itself_a_way_on", "if (!S->visited[g->col[e]])", "if (!S->visited[g->col[e]] || g->col[e] == u)",
+     [SOLVE]),
     ("step_cap_early", "if (moves == S->max_steps)", "if (moves + 1 == S->max_steps)", [SOLVE]),
     ("default_step_cap", "uint32_t def_steps = two_n < 4096u ? (uint32_t)two_n : 4096u;",
      "uint32_t def_steps = two_n < 4095u ? (uint32_t)two_n : 4095u;", [SOLVE]),
